@@ -1,0 +1,224 @@
+/*
+ * combo.h -- C ABI of libcombo.so: GB300 (sm_103a) FFT-based finite-strain
+ * homogenization with composite boxels (ComBo).
+ *
+ * Method: Keshav, Fritzen, Kabel, "FFT-based homogenization at finite strains
+ * using composite boxels (ComBo)", arXiv 2204.13624.
+ *
+ * The library solves the homogenization problem (HOM) of Sec. 2: for a
+ * periodic RVE discretised by n1 x n2 x n3 voxels and a prescribed
+ * macroscopic deformation gradient Fbar, find the compatible deformation
+ * gradient field F with <F> = Fbar and Div P(F) = 0, and return the effective
+ * first Piola-Kirchhoff stress Pbar = <P> (Eq. Pbar).  It uses the
+ * finite-strain Lippmann-Schwinger equation of Sec. 3 (Eq. nonlinearLSE) with
+ * the Green operator Gamma0 = Grad G0 Div (Eq. Gamma0) applied in Fourier
+ * space.  Voxels cut by the material interface ("composite boxels") follow the
+ * rank-one laminate law of Sec. 4 (Eqs. Fpm, tractionbalance, Peff:Seff),
+ * solved per boxel by Newton-Raphson with selective back-projection
+ * (Algorithms 1 and 2).  Both phases are compressible Neo-Hookean (Sec. 6.1).
+ *
+ * Conventions
+ *   - 2-tensors are 9-vectors in row-major order F = [F11 F12 F13 F21 ... F33]
+ *     (Sec. 1.5, Eq. vector:not).
+ *   - Fields are component-major: X[c * V + v], V = n1 n2 n3, voxel index
+ *     v = i + n1 (j + n2 k), i along x (fastest).
+ *   - Phase codes: 0 = matrix ("-"), 1 = inclusion ("+"), 2 = composite boxel.
+ *     Material index 0 is the matrix, 1 the inclusion.  A boxel's normal N
+ *     points out of the inclusion into the matrix (Sec. 1.5, Sec. 5.1) and its
+ *     c+ is the inclusion volume fraction.
+ *
+ * Ownership: the caller owns every pointer it passes.  combo_solve_begin and
+ * combo_solve copy the problem during the call and keep no caller pointer.
+ * Result arrays are caller-allocated and written before the call returns.
+ *
+ * Errors: every entry point returns COMBO_OK (0) or a negative COMBO_E_* code
+ * and never throws; combo_last_error() gives a message for the calling
+ * thread.  Numerical failures are status codes, never traps.
+ */
+#ifndef COMBO_H
+#define COMBO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define COMBO_OK 0
+#define COMBO_E_INVALID_ARG (-1)
+#define COMBO_E_OOM (-2)
+#define COMBO_E_NOT_CONVERGED (-3)
+#define COMBO_E_LAMINATE (-4)     /* a boxel Newton-Raphson did not converge */
+#define COMBO_E_INADMISSIBLE (-5) /* det F <= 0 that step halving could not cure */
+#define COMBO_E_NAN (-6)
+#define COMBO_E_TIMEOUT (-7)
+#define COMBO_E_CUDA (-8)
+
+/* Where the pointers of a problem / result live. */
+#define COMBO_MEM_HOST 0
+#define COMBO_MEM_DEVICE 1
+
+/* precision */
+#define COMBO_FP64 0          /* every field and operator in FP64 */
+#define COMBO_FP32_REFINED 1  /* FP32 Krylov iterations, FP64 residual, F, laminates, norms */
+/* kspace: discrete derivative of the Green operator */
+#define COMBO_ROTATED 0  /* Willot's rotated scheme (HEX8R), Sec. 3 and Sec. 6.3 */
+#define COMBO_SPECTRAL 1 /* Moulinec-Suquet trigonometric polynomials, Sec. 3 */
+/* solver */
+#define COMBO_FIXED_POINT 0 /* basic scheme on the nonlinear LSE, Sec. 3 */
+#define COMBO_NEWTON_CG 1   /* Newton with conjugate gradients on the linearised LSE, Sec. 3 */
+
+typedef struct combo_ctx combo_ctx;
+typedef struct combo_solve_state combo_solve_state;
+
+typedef struct {
+    int32_t device;  /* CUDA device ordinal */
+    void* stream;    /* cudaStream_t to launch on; NULL = the library creates its own */
+} combo_ctx_opts;
+
+/*
+ * Problem statement (Sec. 2 HOM with the boxel data of Sec. 4).
+ *   n[3]       grid n1, n2, n3; each 2^a 3^b, 2 <= n <= 1024, n1 even.
+ *   l[3]       RVE edge lengths (voxel edge h_j = l_j / n_j; boxels may be
+ *              non-equiaxed).
+ *   phase      [V] phase codes (see above).
+ *   n_boxels   number of composite boxels, == count of phase code 2.
+ *   boxel_idx  [n_boxels] voxel index of each boxel, strictly increasing.
+ *   boxel_N    [n_boxels][3] interface normal, normalised by the library;
+ *              |N| < 1e-12 is rejected.
+ *   boxel_c    [n_boxels] inclusion volume fraction c+ in (0, 1); boxels with
+ *              c+ < c_min or c+ > 1 - c_min are evaluated as the pure phase.
+ *   mu, lambda [2] Lame parameters of the Neo-Hookean phases; mu > 0,
+ *              lambda > -2 mu / 3.
+ *   Fbar       [9] macroscopic deformation gradient, det Fbar > 0.
+ *   n_steps    load steps: Fbar_n = I + (n / n_steps)(Fbar - I), n = 1..n_steps.
+ *   mem        COMBO_MEM_HOST or COMBO_MEM_DEVICE for phase/boxel_* pointers.
+ */
+typedef struct {
+    int32_t n[3];
+    double l[3];
+    const uint8_t* phase;
+    int64_t n_boxels;
+    const int64_t* boxel_idx;
+    const double* boxel_N;
+    const double* boxel_c;
+    double mu[2];
+    double lambda[2];
+    double Fbar[9];
+    int32_t n_steps;
+    int32_t mem;
+} combo_problem;
+
+/*
+ * Solver options; combo_options_default() fills the defaults given here.
+ *   precision        COMBO_FP64 (default) or COMBO_FP32_REFINED
+ *   kspace           COMBO_ROTATED (default) or COMBO_SPECTRAL
+ *   solver           COMBO_NEWTON_CG (default) or COMBO_FIXED_POINT
+ *   tol              equilibrium tolerance on ||G[P]||_rms / |<P>|  (1e-8)
+ *   max_iter         outer iterations per load step (200 Newton / 100000 fixed point)
+ *   fixed_iterations > 0: run exactly this many outer iterations per load step
+ *   cg_tol           CG stops at ||r|| <= cg_tol ||b||  (1e-3)
+ *   cg_max_iter      (2000)
+ *   cg_fixed_iterations > 0: exactly this many CG iterations per Newton step
+ *   nr_tol_rel, nr_tol_abs  laminate NR stops at |f| <= rel (|P+N| + |P-N|) + abs mu_max (1e-12, 1e-14)
+ *   nr_max_iter      laminate NR cap (50)
+ *   c_min            boxel volume-fraction snap (1e-6)
+ *   mu0              reference shear modulus of the fixed point; <= 0 picks
+ *                    (min mu + max(lambda + 2 mu)) / 2
+ */
+typedef struct {
+    int32_t precision;
+    int32_t kspace;
+    int32_t solver;
+    double tol;
+    int32_t max_iter;
+    int32_t fixed_iterations;
+    double cg_tol;
+    int32_t cg_max_iter;
+    int32_t cg_fixed_iterations;
+    double nr_tol_rel;
+    double nr_tol_abs;
+    int32_t nr_max_iter;
+    double c_min;
+    double mu0;
+} combo_options;
+
+/*
+ * Results, caller-allocated.  Pbar [n_steps][9] is required; every other
+ * pointer may be NULL.
+ *   F_out, P_out  [9][V] FP64 fields of the last completed step, in `mem`.
+ *   a_out         [n_boxels][3] laminate jump vectors, in `mem`.
+ *   iters         [n_steps] outer (Newton / fixed-point) iterations.
+ *   cg_iters      [n_steps] CG iterations.
+ *   resid         [n_steps] final equilibrium residual.
+ * Counters are totals over the solve.  steps_done is the number of load
+ * steps completed (partial results are valid up to it on failure).
+ */
+typedef struct {
+    double* Pbar;
+    double* F_out;
+    double* P_out;
+    double* a_out;
+    int32_t* iters;
+    int32_t* cg_iters;
+    double* resid;
+    int32_t mem;
+    int32_t steps_done;
+    int64_t nr_iters;
+    int64_t n_backproj;
+    int64_t n_laminate_evals;
+    int64_t n_operator; /* operator applications; voxel-iterations = n_operator * V */
+    int64_t n_operator_fp64;
+} combo_result;
+
+/* Context: owns the device, the stream and the library's device memory.
+ * Returns COMBO_E_CUDA if the device cannot be used.  opts may be NULL
+ * (device 0, own stream). */
+int combo_ctx_create(const combo_ctx_opts* opts, combo_ctx** out);
+void combo_ctx_destroy(combo_ctx* ctx);
+
+/* Message of the last error of the calling thread (never NULL). */
+const char* combo_last_error(void);
+
+void combo_options_default(combo_options* o);
+
+/* Bytes of device memory one solve of this problem and options will hold. */
+int64_t combo_solve_footprint(const combo_problem* p, const combo_options* o);
+
+/* Full solve: copy the problem in, run every load step, write results. */
+int combo_solve(combo_ctx* ctx, const combo_problem* p, const combo_options* o, combo_result* r);
+
+/*
+ * Incremental interface (used for timing and by the serving loop):
+ *   begin    validates and copies the problem to the device, allocates the
+ *            solve's fields; nothing runs yet.
+ *   advance  runs at most max_operator operator applications (<= 0: no
+ *            limit) and returns COMBO_OK when every load step is done,
+ *            COMBO_PENDING (1) when the limit stopped it, or an error.
+ *   finish   writes the results; end frees the state.
+ */
+#define COMBO_PENDING 1
+int combo_solve_begin(combo_ctx* ctx, const combo_problem* p, const combo_options* o, combo_solve_state** s);
+int combo_solve_advance(combo_solve_state* s, int64_t max_operator);
+int combo_solve_finish(combo_solve_state* s, combo_result* r);
+void combo_solve_end(combo_solve_state* s);
+
+/*
+ * Unit-level entry points (same kernels as the solve).
+ *
+ * combo_apply_G: Y = G[X] = mu0 Gamma0[X] (Eq. Gamma0 with C0 = mu0 I),
+ *   X, Y [9][V] FP64 in `mem`; precision selects the FFT precision;
+ *   *sumsq receives sum_x |Y(x)|^2.
+ * combo_constitutive: P[9][V] (FP64) of the field F[9][V] (FP64): pure
+ *   voxels Neo-Hookean (Sec. 6.1), boxels the laminate (Algorithms 1-2)
+ *   started from a_io[n_boxels][3] (updated in place).  All in `mem`.
+ */
+int combo_apply_G(combo_ctx* ctx, const int32_t n[3], const double l[3], int32_t kspace, int32_t precision,
+                  const double* X, double* Y, double* sumsq, int32_t mem);
+int combo_constitutive(combo_ctx* ctx, const combo_problem* p, const combo_options* o, const double* F,
+                       double* a_io, double* P, int32_t mem);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

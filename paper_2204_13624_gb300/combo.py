@@ -1,0 +1,319 @@
+"""Thin ctypes binding of libcombo.so (include/combo.h).
+
+Argument marshalling only: every step of a solve runs in the CUDA library.
+Host arrays are numpy arrays; device arrays are torch CUDA tensors (torch is
+used only for device memory and streams).  There is no CPU fallback: if the
+library is missing or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcombo.so")
+
+OK, PENDING = 0, 1
+E_NAMES = {-1: "invalid argument", -2: "out of memory", -3: "not converged", -4: "laminate Newton failed",
+           -5: "inadmissible (det F <= 0)", -6: "NaN", -7: "timeout", -8: "CUDA error"}
+FP64, FP32_REFINED = 0, 1
+ROTATED, SPECTRAL = 0, 1
+FIXED_POINT, NEWTON_CG = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+
+
+class ComboError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"combo error {code} ({E_NAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class CtxOpts(C.Structure):
+    _fields_ = [("device", C.c_int32), ("stream", C.c_void_p)]
+
+
+class ProblemS(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("l", C.c_double * 3), ("phase", C.c_void_p), ("n_boxels", C.c_int64),
+                ("boxel_idx", C.c_void_p), ("boxel_N", C.c_void_p), ("boxel_c", C.c_void_p),
+                ("mu", C.c_double * 2), ("lam", C.c_double * 2), ("Fbar", C.c_double * 9), ("n_steps", C.c_int32),
+                ("mem", C.c_int32)]
+
+
+class OptionsS(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("kspace", C.c_int32), ("solver", C.c_int32), ("tol", C.c_double),
+                ("max_iter", C.c_int32), ("fixed_iterations", C.c_int32), ("cg_tol", C.c_double),
+                ("cg_max_iter", C.c_int32), ("cg_fixed_iterations", C.c_int32), ("nr_tol_rel", C.c_double),
+                ("nr_tol_abs", C.c_double), ("nr_max_iter", C.c_int32), ("c_min", C.c_double), ("mu0", C.c_double)]
+
+
+class ResultS(C.Structure):
+    _fields_ = [("Pbar", C.c_void_p), ("F_out", C.c_void_p), ("P_out", C.c_void_p), ("a_out", C.c_void_p),
+                ("iters", C.c_void_p), ("cg_iters", C.c_void_p), ("resid", C.c_void_p), ("mem", C.c_int32),
+                ("steps_done", C.c_int32), ("nr_iters", C.c_int64), ("n_backproj", C.c_int64),
+                ("n_laminate_evals", C.c_int64), ("n_operator", C.c_int64), ("n_operator_fp64", C.c_int64)]
+
+
+EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_options_default",
+           "combo_solve_footprint", "combo_solve", "combo_solve_begin", "combo_solve_advance", "combo_solve_finish",
+           "combo_solve_end", "combo_apply_G", "combo_constitutive"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcombo.so (raises if it is missing; never falls back)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ComboError(-8, f"{path} is missing: build it with paper_2204_13624_gb300.build.build()")
+    L = C.CDLL(path)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    L.combo_ctx_create.argtypes = [vp, C.POINTER(vp)]
+    L.combo_ctx_create.restype = C.c_int
+    L.combo_ctx_destroy.argtypes = [vp]
+    L.combo_last_error.restype = C.c_char_p
+    L.combo_options_default.argtypes = [vp]
+    L.combo_solve_footprint.argtypes = [vp, vp]
+    L.combo_solve_footprint.restype = i64
+    L.combo_solve.argtypes = [vp, vp, vp, vp]
+    L.combo_solve.restype = C.c_int
+    L.combo_solve_begin.argtypes = [vp, vp, vp, C.POINTER(vp)]
+    L.combo_solve_begin.restype = C.c_int
+    L.combo_solve_advance.argtypes = [vp, i64]
+    L.combo_solve_advance.restype = C.c_int
+    L.combo_solve_finish.argtypes = [vp, vp]
+    L.combo_solve_finish.restype = C.c_int
+    L.combo_solve_end.argtypes = [vp]
+    L.combo_apply_G.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, i32]
+    L.combo_apply_G.restype = C.c_int
+    L.combo_constitutive.argtypes = [vp, vp, vp, vp, vp, vp, i32]
+    L.combo_constitutive.restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc < 0:
+        raise ComboError(rc, load().combo_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _is_dev(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+class Context:
+    """A device, its stream and the library's memory (combo_ctx)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        L = load()
+        o = CtxOpts(device, stream)
+        h = C.c_void_p()
+        _check(L.combo_ctx_create(C.byref(o), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            load().combo_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_ctx = None
+
+
+def default_context() -> Context:
+    global _default_ctx
+    if _default_ctx is None:
+        _default_ctx = Context(0)
+    return _default_ctx
+
+
+def options(**kw) -> OptionsS:
+    o = OptionsS()
+    load().combo_options_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Problem:
+    """Marshals a problem dict (see microstructure.make_problem) into combo_problem.
+
+    Arrays stay referenced by this object for the lifetime of the struct.
+    Numpy arrays are host memory; torch CUDA tensors device memory."""
+
+    def __init__(self, prob: dict):
+        self.keep = []
+        dev = _is_dev(prob["phase"])
+
+        def arr(x, dt):
+            if dev:
+                return x.contiguous()
+            return np.ascontiguousarray(x, dtype=dt)
+
+        phase = arr(prob["phase"], np.uint8)
+        bidx = arr(prob["boxel_idx"], np.int64)
+        bN = arr(prob["boxel_N"], np.float64)
+        bc = arr(prob["boxel_c"], np.float64)
+        self.keep += [phase, bidx, bN, bc]
+        s = ProblemS()
+        s.n = (C.c_int32 * 3)(*[int(v) for v in prob["n"]])
+        s.l = (C.c_double * 3)(*[float(v) for v in prob.get("l", (1.0, 1.0, 1.0))])
+        s.phase = _ptr(phase)
+        s.n_boxels = int(bidx.numel() if dev else bidx.size)
+        s.boxel_idx = _ptr(bidx) if s.n_boxels else None
+        s.boxel_N = _ptr(bN) if s.n_boxels else None
+        s.boxel_c = _ptr(bc) if s.n_boxels else None
+        s.mu = (C.c_double * 2)(*[float(v) for v in prob["mu"]])
+        s.lam = (C.c_double * 2)(*[float(v) for v in prob["lam"]])
+        s.Fbar = (C.c_double * 9)(*[float(v) for v in np.asarray(prob["Fbar"], dtype=np.float64).reshape(9)])
+        s.n_steps = int(prob.get("n_steps", 1))
+        s.mem = MEM_DEVICE if dev else MEM_HOST
+        self.s = s
+        self.n = tuple(int(v) for v in prob["n"])
+        self.V = self.n[0] * self.n[1] * self.n[2]
+        self.n_steps = s.n_steps
+        self.n_boxels = s.n_boxels
+
+
+def _result_buffers(pb: Problem, fields: bool, device: bool):
+    S, V, nb = pb.n_steps, pb.V, pb.n_boxels
+    out = dict(Pbar=np.zeros((S, 9)), iters=np.zeros(S, np.int32), cg_iters=np.zeros(S, np.int32),
+               resid=np.zeros(S))
+    r = ResultS()
+    r.Pbar = _ptr(out["Pbar"])
+    r.iters = _ptr(out["iters"])
+    r.cg_iters = _ptr(out["cg_iters"])
+    r.resid = _ptr(out["resid"])
+    if fields:
+        if device:
+            import torch
+
+            out["F"] = torch.empty((9, V), dtype=torch.float64, device="cuda")
+            out["P"] = torch.empty((9, V), dtype=torch.float64, device="cuda")
+            out["a"] = torch.empty((max(nb, 1), 3), dtype=torch.float64, device="cuda")
+            r.mem = MEM_DEVICE
+            # Pbar etc. are host arrays; with mem = device the library expects
+            # device pointers for every array, so keep scalars on the device too
+            for k in ("Pbar", "iters", "cg_iters", "resid"):
+                out[k] = torch.as_tensor(out[k]).cuda()
+            r.Pbar, r.iters, r.cg_iters, r.resid = (_ptr(out[k]) for k in ("Pbar", "iters", "cg_iters", "resid"))
+        else:
+            out["F"] = np.zeros((9, V))
+            out["P"] = np.zeros((9, V))
+            out["a"] = np.zeros((max(nb, 1), 3))
+            r.mem = MEM_HOST
+        r.F_out = _ptr(out["F"])
+        r.P_out = _ptr(out["P"])
+        r.a_out = _ptr(out["a"])
+    return out, r
+
+
+def _collect(out, r, nb):
+    out.update(steps_done=r.steps_done, nr_iters=r.nr_iters, n_backproj=r.n_backproj,
+               n_laminate_evals=r.n_laminate_evals, n_operator=r.n_operator, n_operator_fp64=r.n_operator_fp64)
+    if "a" in out:
+        out["a"] = out["a"][:nb]
+    return out
+
+
+def solve(prob: dict, ctx: Context | None = None, fields: bool = True, device_results: bool = False, **opts):
+    """combo_solve: full solve of every load step; returns Pbar per step,
+    iteration counts, residuals, counters and (optionally) F, P, a."""
+    ctx = ctx or default_context()
+    pb = Problem(prob)
+    o = options(**opts)
+    out, r = _result_buffers(pb, fields, device_results)
+    _check(load().combo_solve(ctx.h, C.byref(pb.s), C.byref(o), C.byref(r)))
+    return _collect(out, r, pb.n_boxels)
+
+
+class Solve:
+    """Incremental solve (combo_solve_begin / advance / finish / end)."""
+
+    def __init__(self, prob: dict, ctx: Context | None = None, **opts):
+        self.ctx = ctx or default_context()
+        self.pb = Problem(prob)
+        self.o = options(**opts)
+        h = C.c_void_p()
+        _check(load().combo_solve_begin(self.ctx.h, C.byref(self.pb.s), C.byref(self.o), C.byref(h)))
+        self.h = h
+
+    def advance(self, max_operator: int = 0) -> bool:
+        """Run up to max_operator operator applications; True when finished."""
+        return _check(load().combo_solve_advance(self.h, int(max_operator))) == OK
+
+    def finish(self, fields: bool = True, device_results: bool = False):
+        out, r = _result_buffers(self.pb, fields, device_results)
+        _check(load().combo_solve_finish(self.h, C.byref(r)))
+        return _collect(out, r, self.pb.n_boxels)
+
+    def close(self):
+        if self.h:
+            load().combo_solve_end(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def footprint(prob: dict, **opts) -> int:
+    pb = Problem(prob)
+    o = options(**opts)
+    return int(load().combo_solve_footprint(C.byref(pb.s), C.byref(o)))
+
+
+def apply_G(X, n, l=(1.0, 1.0, 1.0), kspace=ROTATED, precision=FP64, ctx: Context | None = None):
+    """Y = G[X] (mu0 Gamma0) of a real field X[9][V]; returns (Y, sum |Y|^2)."""
+    ctx = ctx or default_context()
+    dev = _is_dev(X)
+    if dev:
+        import torch
+
+        X = X.contiguous().to(torch.float64)
+        Y = torch.empty_like(X)
+    else:
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Y = np.zeros_like(X)
+    nn = (C.c_int32 * 3)(*[int(v) for v in n])
+    ll = (C.c_double * 3)(*[float(v) for v in l])
+    ss = C.c_double(0.0)
+    _check(load().combo_apply_G(ctx.h, nn, ll, kspace, precision, _ptr(X), _ptr(Y), C.byref(ss),
+                                MEM_DEVICE if dev else MEM_HOST))
+    return Y, ss.value
+
+
+def constitutive(prob: dict, F, a=None, ctx: Context | None = None, **opts):
+    """P[9][V] of a field F[9][V] (pure Neo-Hookean + boxel laminates); a is
+    the [n_boxels][3] warm start, returned updated."""
+    ctx = ctx or default_context()
+    pb = Problem(prob)
+    o = options(**opts)
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(9, -1)
+    nb = pb.n_boxels
+    a = np.zeros((max(nb, 1), 3)) if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1, 3).copy()
+    P = np.zeros_like(F)
+    _check(load().combo_constitutive(ctx.h, C.byref(pb.s), C.byref(o), _ptr(F), _ptr(a), _ptr(P), MEM_HOST))
+    return P, a[:nb]

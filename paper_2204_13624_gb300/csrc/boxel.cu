@@ -1,0 +1,263 @@
+// boxel.cu -- rank-one laminate law of the composite boxels (paper Sec. 4), FP64.
+//
+// One thread per boxel:
+//   F(+/-) = F_box +/- (1/c(+/-)) a (x) N                     (Eq. Fpm)
+//   f(a)   = (P+ - P-) N                                      (Eq. tractionbalance)
+//   Newton-Raphson on a (Algorithm 1) with the Hessian of Eq. (hessian),
+//   selective back-projection of inadmissible iterates (Algorithm 2, Sec. 4.2),
+//   P_box = c+ P+ + c- P-                                     (Eq. Peff:Seff)
+//   A_box = c+ A+ + c- A- - dA D Delta^{-1} D^T dA            (Sec. 4.1; the
+//   volume average c+ A+ + c- A- is used in the first term, as in the
+//   cheat-sheet table -- the printed "c- A+" is read as a typo).
+//
+// For the Neo-Hookean law (Sec. 6.1) with G = F^{-1}, g = G^T N, m = mu - lam ln J:
+//   N.A.N      = mu |N|^2 I + (lam + m) g (x) g
+//   (A D)_(iJ),k = mu d_ik N_J + lam G_Ji g_k + m G_Jk g_i
+// so the Hessian and the tangent correction need no 9x9 products.
+#include "combo_internal.cuh"
+#include "../../include/combo.h"
+
+namespace combo {
+
+struct Phase {
+    double F[9], G[9], g[3], P[9], lnJ, J;
+};
+
+__device__ __forceinline__ bool nh_phase(Phase& s, double mu, double lam, const double N[3])
+{
+    const double* F = s.F;
+    const double c0 = F[4] * F[8] - F[5] * F[7];
+    const double c1 = F[5] * F[6] - F[3] * F[8];
+    const double c2 = F[3] * F[7] - F[4] * F[6];
+    const double J = F[0] * c0 + F[1] * c1 + F[2] * c2;
+    s.J = J;
+    if (!(J > 0.0)) return false;
+    const double iJ = 1.0 / J;
+    s.G[0] = c0 * iJ;
+    s.G[1] = (F[2] * F[7] - F[1] * F[8]) * iJ;
+    s.G[2] = (F[1] * F[5] - F[2] * F[4]) * iJ;
+    s.G[3] = c1 * iJ;
+    s.G[4] = (F[0] * F[8] - F[2] * F[6]) * iJ;
+    s.G[5] = (F[2] * F[3] - F[0] * F[5]) * iJ;
+    s.G[6] = c2 * iJ;
+    s.G[7] = (F[1] * F[6] - F[0] * F[7]) * iJ;
+    s.G[8] = (F[0] * F[4] - F[1] * F[3]) * iJ;
+    s.lnJ = log(J);
+    const double k = lam * s.lnJ - mu;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+#pragma unroll
+        for (int j = 0; j < 3; j++) s.P[3 * i + j] = mu * F[3 * i + j] + k * s.G[3 * j + i];
+        s.g[i] = s.G[i] * N[0] + s.G[3 + i] * N[1] + s.G[6 + i] * N[2];
+    }
+    return true;
+}
+
+struct LamEval {
+    Phase p, m;
+    double f[3];
+    double err, eps;
+};
+
+__device__ __forceinline__ bool lam_eval(LamEval& e, const double Fb[9], const double N[3], double cp, double cm,
+                                         const double a[3], const double mu[2], const double lam[2], double tol_rel,
+                                         double tol_abs)
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            e.p.F[3 * i + j] = Fb[3 * i + j] + a[i] * N[j] / cp;
+            e.m.F[3 * i + j] = Fb[3 * i + j] - a[i] * N[j] / cm;
+        }
+    if (!nh_phase(e.p, mu[1], lam[1], N)) return false;
+    if (!nh_phase(e.m, mu[0], lam[0], N)) return false;
+    double tp = 0.0, tm = 0.0, ff = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const double a1 = e.p.P[3 * i] * N[0] + e.p.P[3 * i + 1] * N[1] + e.p.P[3 * i + 2] * N[2];
+        const double a2 = e.m.P[3 * i] * N[0] + e.m.P[3 * i + 1] * N[1] + e.m.P[3 * i + 2] * N[2];
+        e.f[i] = a1 - a2;
+        tp += a1 * a1;
+        tm += a2 * a2;
+        ff += e.f[i] * e.f[i];
+    }
+    e.err = sqrt(ff);
+    e.eps = tol_rel * (sqrt(tp) + sqrt(tm)) + tol_abs * fmax(mu[0], mu[1]);
+    return true;
+}
+
+// Delta = sum_phase (1/c) [mu I + (lam + mu - lam ln J) g g^T]   (|N| = 1)
+__device__ __forceinline__ void hessian(const LamEval& e, double cp, double cm, const double mu[2],
+                                        const double lam[2], double D[9])
+{
+    const double wp = 1.0 / cp, wm = 1.0 / cm;
+    const double sp = (lam[1] + mu[1] - lam[1] * e.p.lnJ) * wp;
+    const double sm = (lam[0] + mu[0] - lam[0] * e.m.lnJ) * wm;
+    const double d = mu[1] * wp + mu[0] * wm;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            D[3 * i + k] = (i == k ? d : 0.0) + sp * e.p.g[i] * e.p.g[k] + sm * e.m.g[i] * e.m.g[k];
+}
+
+__device__ __forceinline__ bool inv3(const double A[9], double B[9])
+{
+    const double c0 = A[4] * A[8] - A[5] * A[7];
+    const double c1 = A[5] * A[6] - A[3] * A[8];
+    const double c2 = A[3] * A[7] - A[4] * A[6];
+    const double det = A[0] * c0 + A[1] * c1 + A[2] * c2;
+    if (det == 0.0 || !isfinite(det)) return false;
+    const double id = 1.0 / det;
+    B[0] = c0 * id;
+    B[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    B[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    B[3] = c1 * id;
+    B[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    B[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    B[6] = c2 * id;
+    B[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    B[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    return true;
+}
+
+// (A D)_(iJ),k for one Neo-Hookean phase
+__device__ __forceinline__ double AD(const Phase& s, double mu, double lam, const double N[3], int i, int Jx, int k)
+{
+    const double m = mu - lam * s.lnJ;
+    return (i == k ? mu * N[Jx] : 0.0) + lam * s.G[3 * Jx + i] * s.g[k] + m * s.G[3 * Jx + k] * s.g[i];
+}
+
+// A_iJkL for one Neo-Hookean phase
+__device__ __forceinline__ double Aent(const Phase& s, double mu, double lam, int i, int Jx, int k, int L)
+{
+    const double m = mu - lam * s.lnJ;
+    return ((i == k && Jx == L) ? mu : 0.0) + lam * s.G[3 * Jx + i] * s.G[3 * L + k] + m * s.G[3 * Jx + k] * s.G[3 * L + i];
+}
+
+template <typename Tc>
+__global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
+{
+    if (A.guard == 2 && A.sc->outer_done) return;
+    __shared__ double red[64];
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double its = 0.0, nbp = 0.0, nev = 0.0;
+    if (b < A.nb) {
+        nev = 1.0;
+        const int64_t v = A.bidx[b];
+        double Fb[9], N[3], a[3];
+#pragma unroll
+        for (int c = 0; c < 9; c++) Fb[c] = A.F[c * A.V + v];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            N[i] = A.bN[3 * b + i];
+            a[i] = A.ba[3 * b + i];
+        }
+        const double cp = A.bc[b], cm = 1.0 - cp;
+        const double mu[2] = {A.mu[0], A.mu[1]}, lam[2] = {A.lam[0], A.lam[1]};
+        int status = 0;
+        // m_beta = F^{-T} N / |F^{-T} N|, beta_c(+/-) = -/+ c(+/-) / |F^{-T} N|  (Sec. 4.2)
+        Phase box;
+#pragma unroll
+        for (int c = 0; c < 9; c++) box.F[c] = Fb[c];
+        if (!nh_phase(box, mu[0], lam[0], N)) status = COMBO_E_INADMISSIBLE;
+        LamEval e;
+        double Dl[9], Di[9];
+        if (!status) {
+            const double ng = sqrt(box.g[0] * box.g[0] + box.g[1] * box.g[1] + box.g[2] * box.g[2]);
+            const double m[3] = {box.g[0] / ng, box.g[1] / ng, box.g[2] / ng};
+            const double bcp = -cp / ng, bcm = cm / ng;
+            double beta = a[0] * m[0] + a[1] * m[1] + a[2] * m[2];
+            if (!(beta > bcp && beta < bcm)) a[0] = a[1] = a[2] = 0.0;
+            if (!lam_eval(e, Fb, N, cp, cm, a, mu, lam, A.tol_rel, A.tol_abs)) status = COMBO_E_LAMINATE;
+            int it = 0;
+            while (!status && e.err > e.eps) {
+                if (it >= A.max_iter) {
+                    status = COMBO_E_LAMINATE;
+                    break;
+                }
+                hessian(e, cp, cm, mu, lam, Dl);
+                if (!inv3(Dl, Di)) {
+                    status = COMBO_E_LAMINATE;
+                    break;
+                }
+                double a1[3];
+#pragma unroll
+                for (int i = 0; i < 3; i++) a1[i] = a[i] - (Di[3 * i] * e.f[0] + Di[3 * i + 1] * e.f[1] + Di[3 * i + 2] * e.f[2]);
+                const double b1 = a1[0] * m[0] + a1[1] * m[1] + a1[2] * m[2];
+                if (!(b1 > bcp && b1 < bcm)) {
+                    // Algorithm 2: keep M_perp a1, move the m_beta coordinate to the
+                    // midpoint between the admissible beta0 and the crossed bound
+                    const double b0 = a[0] * m[0] + a[1] * m[1] + a[2] * m[2];
+                    const double bc = (b1 <= bcp) ? bcp : bcm;
+                    const double bs = 0.5 * (b0 + bc);
+#pragma unroll
+                    for (int i = 0; i < 3; i++) a1[i] = (a1[i] - b1 * m[i]) + bs * m[i];
+                    nbp += 1.0;
+                }
+                a[0] = a1[0];
+                a[1] = a1[1];
+                a[2] = a1[2];
+                it++;
+                if (!lam_eval(e, Fb, N, cp, cm, a, mu, lam, A.tol_rel, A.tol_abs)) status = COMBO_E_LAMINATE;
+            }
+            its = it;
+        }
+        if (status) {
+            raise_status(A.sc, status);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 9; c++) A.bP[9 * b + c] = cp * e.p.P[c] + cm * e.m.P[c];
+#pragma unroll
+            for (int i = 0; i < 3; i++) A.ba[3 * b + i] = a[i];
+            if (A.bA) {
+                hessian(e, cp, cm, mu, lam, Dl);
+                if (!inv3(Dl, Di)) {
+                    raise_status(A.sc, COMBO_E_LAMINATE);
+                } else {
+                    // B = dA D (9x3), W = B Delta^{-1}
+                    double B[27], W[27];
+#pragma unroll
+                    for (int r = 0; r < 9; r++)
+#pragma unroll
+                        for (int k = 0; k < 3; k++)
+                            B[3 * r + k] = AD(e.p, mu[1], lam[1], N, r / 3, r % 3, k) - AD(e.m, mu[0], lam[0], N, r / 3, r % 3, k);
+#pragma unroll
+                    for (int r = 0; r < 9; r++)
+#pragma unroll
+                        for (int k = 0; k < 3; k++)
+                            W[3 * r + k] = B[3 * r] * Di[k] + B[3 * r + 1] * Di[3 + k] + B[3 * r + 2] * Di[6 + k];
+                    for (int r = 0; r < 9; r++)
+                        for (int s = 0; s < 9; s++) {
+                            const double avg = cp * Aent(e.p, mu[1], lam[1], r / 3, r % 3, s / 3, s % 3) +
+                                               cm * Aent(e.m, mu[0], lam[0], r / 3, r % 3, s / 3, s % 3);
+                            const double corr = W[3 * r] * B[3 * s] + W[3 * r + 1] * B[3 * s + 1] + W[3 * r + 2] * B[3 * s + 2];
+                            A.bA[(int64_t)(r * 9 + s) * A.nb + b] = (Tc)(avg - corr);
+                        }
+                }
+            }
+        }
+    }
+    const double s1 = block_sum(its, red);
+    const double s2 = block_sum(nbp, red + 32);
+    __syncthreads();
+    const double s3 = block_sum(nev, red);
+    if (threadIdx.x == 0) {
+        atomicAdd(&A.sc->nr_iters, (unsigned long long)s1);
+        atomicAdd(&A.sc->n_backproj, (unsigned long long)s2);
+        atomicAdd(&A.sc->n_lam, (unsigned long long)s3);
+    }
+}
+
+template <typename Tc> void launch_boxel(const BoxelArgs<Tc>& a, cudaStream_t st)
+{
+    if (a.nb <= 0) return;
+    const int grid = (int)((a.nb + 127) / 128);
+    k_boxel<Tc><<<grid, 128, 0, st>>>(a);
+}
+
+template void launch_boxel<double>(const BoxelArgs<double>&, cudaStream_t);
+template void launch_boxel<float>(const BoxelArgs<float>&, cudaStream_t);
+
+}  // namespace combo

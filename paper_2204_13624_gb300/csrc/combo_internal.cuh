@@ -1,0 +1,298 @@
+// combo_internal.cuh -- device-side types, FFT core and kernel launchers of
+// libcombo.so (GB300, sm_103a).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace combo {
+
+template <typename T> struct CxT;
+template <> struct CxT<float> { typedef float2 type; };
+template <> struct CxT<double> { typedef double2 type; };
+template <typename T> using cx = typename CxT<T>::type;
+
+template <typename V> __device__ __forceinline__ V c_add(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
+template <typename V> __device__ __forceinline__ V c_sub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
+template <typename V> __device__ __forceinline__ V c_mul(V a, V b)
+{
+    return V{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename V> __device__ __forceinline__ V c_conj(V a) { return V{a.x, -a.y}; }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV, typename V> __device__ __forceinline__ V c_rot(V a)
+{
+    return INV ? V{-a.y, a.x} : V{a.y, -a.x};
+}
+template <typename V, typename S> __device__ __forceinline__ V c_scale(V a, S s) { return V{a.x * s, a.y * s}; }
+
+constexpr int kMaxStages = 12;
+
+// Mixed-radix Stockham plan for one line length (product of radices 2,3,4,8).
+struct Plan {
+    int n;
+    int nst;
+    int R[kMaxStages];
+    int Ns[kMaxStages];  // product of the radices of the stages before this one
+};
+
+struct GridDims {
+    int n1, n2, n3;
+    int M;     // n1 / 2: complex length of the packed x transform
+    int nh;    // M + 1 stored x frequencies (Hermitian half)
+    int nhp;   // pitch of the x-frequency axis in the spectrum (>= nh)
+    int64_t V;   // voxels
+    int64_t Vs;  // complex entries per spectrum component: n3 * n2 * nhp
+};
+
+// Solver scalars that live on the device between kernels.
+struct Scalars {
+    double resid2;    // sum over the half spectrum of w |ghat|^2
+    double dc[9];     // zero-frequency coefficients of the last residual operand
+    double Pbar[9];   // <P> of the last evaluation
+    double eps;       // equilibrium residual ||G[P]||_rms / |<P>|
+    double rr, rr0, pAp, alpha, beta;
+    int32_t outer_iter, outer_done;
+    int32_t cg_iter, cg_done;
+    int32_t admissible;
+    int32_t status;  // first error code (COMBO_E_*) raised by a kernel
+    unsigned long long nr_iters, n_backproj, n_lam;
+    unsigned long long n_operator, n_operator64;
+};
+
+// ---------------------------------------------------------------- FFT core
+// Radix-R butterflies, DFT_R(v) with sign -1 (forward) or +1 (inverse).
+template <bool INV, typename V> __device__ __forceinline__ void dft2(V* v)
+{
+    V a = v[0], b = v[1];
+    v[0] = c_add(a, b);
+    v[1] = c_sub(a, b);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft4(V* v)
+{
+    V t0 = c_add(v[0], v[2]), t1 = c_sub(v[0], v[2]);
+    V t2 = c_add(v[1], v[3]), t3 = c_rot<INV>(c_sub(v[1], v[3]));
+    v[0] = c_add(t0, t2);
+    v[2] = c_sub(t0, t2);
+    v[1] = c_add(t1, t3);
+    v[3] = c_sub(t1, t3);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft3(V* v)
+{
+    typedef decltype(v[0].x) S;
+    const S h = (S)0.86602540378443864676;  // sin(2 pi / 3)
+    V s = c_add(v[1], v[2]), d = c_sub(v[1], v[2]);
+    V t = V{v[0].x - (S)0.5 * s.x, v[0].y - (S)0.5 * s.y};
+    V u = c_rot<INV>(c_scale(d, h));
+    v[0] = c_add(v[0], s);
+    v[1] = c_add(t, u);
+    v[2] = c_sub(t, u);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft8(V* v)
+{
+    typedef decltype(v[0].x) S;
+    const S c = (S)0.70710678118654752440;  // cos(pi / 4)
+    V e[4] = {v[0], v[2], v[4], v[6]};
+    V o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<INV>(e);
+    dft4<INV>(o);
+    // o[k] *= exp(-/+ 2 pi i k / 8)
+    V o1 = o[1], o3 = o[3];
+    if (!INV) {
+        o[1] = V{c * (o1.x + o1.y), c * (o1.y - o1.x)};
+        o[2] = V{o[2].y, -o[2].x};
+        o[3] = V{c * (o3.y - o3.x), -c * (o3.x + o3.y)};
+    } else {
+        o[1] = V{c * (o1.x - o1.y), c * (o1.x + o1.y)};
+        o[2] = V{-o[2].y, o[2].x};
+        o[3] = V{-c * (o3.x + o3.y), c * (o3.x - o3.y)};
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        v[k] = c_add(e[k], o[k]);
+        v[k + 4] = c_sub(e[k], o[k]);
+    }
+}
+
+// One self-sorting Stockham stage (decimation in time) over nl lines.
+// Element e of line q is at buf[q * ls + e * es].  tw[t] = exp(-2 pi i t / n).
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void fft_stage(const cx<T>* __restrict__ src, cx<T>* __restrict__ dst, int n, int Ns,
+                                          int nl, int ls, int es, const cx<T>* __restrict__ tw, int tid, int nthr)
+{
+    const int nbut = n / R;
+    const int total = nbut * nl;
+    const int tstep = n / (Ns * R);
+    for (int b = tid; b < total; b += nthr) {
+        const int q = b % nl;
+        const int j = b / nl;
+        const int k = j % Ns;
+        cx<T> v[R];
+        const cx<T>* s = src + (size_t)q * ls;
+#pragma unroll
+        for (int t = 0; t < R; t++) v[t] = s[(size_t)(j + t * nbut) * es];
+        if (Ns > 1) {
+#pragma unroll
+            for (int t = 1; t < R; t++) {
+                cx<T> w = tw[t * k * tstep];
+                if (INV) w.y = -w.y;
+                v[t] = c_mul(v[t], w);
+            }
+        }
+        if (R == 2) dft2<INV>(v);
+        if (R == 3) dft3<INV>(v);
+        if (R == 4) dft4<INV>(v);
+        if (R == 8) dft8<INV>(v);
+        const int idxD = (j / Ns) * Ns * R + k;
+        cx<T>* d = dst + (size_t)q * ls;
+#pragma unroll
+        for (int t = 0; t < R; t++) d[(size_t)(idxD + t * Ns) * es] = v[t];
+    }
+}
+
+// Full transform of nl lines: data starts in b0, ends in (nst odd ? b1 : b0).
+// Returns the buffer holding the result.  Ends with __syncthreads().
+template <typename T, bool INV>
+__device__ cx<T>* fft_lines(cx<T>* b0, cx<T>* b1, const Plan& p, int nl, int ls, int es, const cx<T>* tw)
+{
+    cx<T>* src = b0;
+    cx<T>* dst = b1;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int s = 0; s < p.nst; s++) {
+        switch (p.R[s]) {
+            case 2: fft_stage<T, 2, INV>(src, dst, p.n, p.Ns[s], nl, ls, es, tw, tid, nthr); break;
+            case 3: fft_stage<T, 3, INV>(src, dst, p.n, p.Ns[s], nl, ls, es, tw, tid, nthr); break;
+            case 4: fft_stage<T, 4, INV>(src, dst, p.n, p.Ns[s], nl, ls, es, tw, tid, nthr); break;
+            default: fft_stage<T, 8, INV>(src, dst, p.n, p.Ns[s], nl, ls, es, tw, tid, nthr); break;
+        }
+        __syncthreads();
+        cx<T>* t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
+// Block-wide sum of one double per thread (result valid in thread 0).
+__device__ __forceinline__ double block_sum(double v, double* red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = 0; i < nw; i++) s += red[i];
+    }
+    return s;
+}
+
+__device__ __forceinline__ void raise_status(Scalars* sc, int code)
+{
+    atomicCAS(&sc->status, 0, code);
+}
+
+// ---------------------------------------------------------------- launchers
+enum XfwdMode { XF_RESID = 0, XF_TANGENT = 1 };
+enum XinvMode { XI_FIXEDPOINT = 0, XI_RHS = 1, XI_CG = 2, XI_PLAIN = 3 };
+
+template <typename T, typename Tc> struct XfwdArgs {
+    GridDims g;
+    Plan plan;           // length M
+    const cx<T>* tw;     // [M] exp(-2 pi i t / M)
+    const cx<T>* tw2;    // [M + 1] exp(-2 pi i k / n1)
+    cx<T>* spec;         // [9][n3][n2][nhp]
+    int lines_per_block;
+    int mode;
+    const uint8_t* phase;
+    const int32_t* vox2box;
+    double mu[2], lam[2];
+    // XF_RESID
+    const double* F;     // [9][V]
+    const double* bP;    // [nb][9]
+    Tc* tc;              // [10][V] tangent cache (F^{-1}, mu - lam ln J), may be null
+    // XF_TANGENT
+    const Tc* r;
+    Tc* p;
+    const Tc* bA;        // [81][nb]
+    int64_t nb;
+    // plain operand (no constitutive law): X [9][V] real
+    const double* X;
+    double* partial;     // [gridDim.x] pAp partials
+    Scalars* sc;
+};
+
+template <typename T, typename Tc> struct XinvArgs {
+    GridDims g;
+    Plan plan;
+    const cx<T>* tw;
+    const cx<T>* tw2;
+    const cx<T>* spec;
+    int lines_per_block;
+    int mode;
+    double inv_mu0;
+    double* F;       // XI_FIXEDPOINT
+    Tc* x;           // XI_RHS / XI_CG
+    Tc* r;
+    const Tc* p;
+    double* Y;       // XI_PLAIN: real output [9][V]
+    double* partial;
+    Scalars* sc;
+};
+
+template <typename T> struct YArgs {
+    GridDims g;
+    Plan plan;
+    const cx<T>* tw;
+    cx<T>* spec;
+    int tx;
+    const Scalars* sc;
+    int guard;  // 0 none, 1 skip if cg_done, 2 skip if outer_done
+};
+
+template <typename T> struct ZArgs {
+    GridDims g;
+    Plan plan;
+    const cx<T>* tw;
+    cx<T>* spec;
+    int tx;
+    const T* sa[3];  // symbol tables: k_j(xi) = sa[j][xi_j] * prod_{m != j} sb[m][xi_m]
+    const T* sb[3];
+    T scale;         // 2 / V
+    int want_norm;   // accumulate sum w |G X|^2 and the zero frequency
+    double* partial; // [gridDim.x * gridDim.y * gridDim.z]
+    Scalars* sc;
+    int guard;
+};
+
+template <typename T, typename Tc> void launch_xfwd(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st);
+template <typename T, typename Tc> void launch_xinv(const XinvArgs<T, Tc>& a, int guard, cudaStream_t st);
+template <typename T, bool INV> void launch_ypass(const YArgs<T>& a, cudaStream_t st);
+template <typename T> void launch_zpass(const ZArgs<T>& a, cudaStream_t st);
+size_t xpass_smem(const GridDims& g, int lines, size_t cxbytes);
+int xpass_lines(const GridDims& g, size_t cxbytes);
+
+// boxel laminate Newton solve
+template <typename Tc> struct BoxelArgs {
+    int64_t nb;
+    int64_t V;
+    const int32_t* bidx;
+    const double* bN;
+    const double* bc;
+    double* ba;    // [nb][3] jump vectors (warm start in, converged out)
+    double* bP;    // [nb][9]
+    Tc* bA;        // [81][nb] or null
+    const double* F;
+    double mu[2], lam[2];
+    double tol_rel, tol_abs;
+    int max_iter;
+    Scalars* sc;
+    int guard;
+};
+template <typename Tc> void launch_boxel(const BoxelArgs<Tc>& a, cudaStream_t st);
+
+}  // namespace combo

@@ -1,0 +1,1222 @@
+// runtime.cu -- C ABI of libcombo.so: contexts, per-solve device state, the
+// solver state machine (load steps, fixed point, Newton-CG with FP32 Krylov
+// iterations and FP64 residuals) and the small solver kernels.
+//
+// Paper: arXiv 2204.13624.  Sec. 2 (HOM, Pbar = <P>), Sec. 3 (Lippmann-
+// Schwinger equation, Green operator, fixed point / Newton with a fast linear
+// solver), Sec. 4 (composite boxels), Sec. 6.1 (Neo-Hookean phases).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <type_traits>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/combo.h"
+#include "combo_internal.cuh"
+
+using namespace combo;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                        \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) return fail(COMBO_E_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" const char* combo_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ context
+struct combo_ctx {
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+};
+
+extern "C" int combo_ctx_create(const combo_ctx_opts* o, combo_ctx** out)
+{
+    if (!out) return fail(COMBO_E_INVALID_ARG, "null output pointer");
+    int dev = o ? o->device : 0;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (dev < 0 || dev >= ndev) return fail(COMBO_E_INVALID_ARG, "no such CUDA device");
+    CK(cudaSetDevice(dev));
+    combo_ctx* c = new combo_ctx();
+    c->device = dev;
+    if (o && o->stream) {
+        c->stream = (cudaStream_t)o->stream;
+        c->own_stream = false;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(COMBO_E_CUDA, cudaGetErrorString(e));
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+    return COMBO_OK;
+}
+
+extern "C" void combo_ctx_destroy(combo_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+extern "C" void combo_options_default(combo_options* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = COMBO_FP64;
+    o->kspace = COMBO_ROTATED;
+    o->solver = COMBO_NEWTON_CG;
+    o->tol = 1e-8;
+    o->max_iter = 0;  // solver default
+    o->fixed_iterations = 0;
+    o->cg_tol = 1e-3;
+    o->cg_max_iter = 2000;
+    o->cg_fixed_iterations = 0;
+    o->nr_tol_rel = 1e-12;
+    o->nr_tol_abs = 1e-14;
+    o->nr_max_iter = 50;
+    o->c_min = 1e-6;
+    o->mu0 = 0.0;
+}
+
+// ------------------------------------------------------------------ plans and tables
+static bool is_23(int n)
+{
+    if (n < 1) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+static Plan make_plan(int n)
+{
+    Plan p{};
+    p.n = n;
+    int a = 0, b = 0, m = n;
+    while (m % 2 == 0) {
+        m /= 2;
+        a++;
+    }
+    while (m % 3 == 0) {
+        m /= 3;
+        b++;
+    }
+    std::vector<int> R;
+    int p8 = a / 3, rem = a % 3;
+    if (rem == 1 && p8 >= 1) {
+        p8 -= 1;
+        R.push_back(4);
+        R.push_back(4);
+    } else if (rem == 1) {
+        R.push_back(2);
+    } else if (rem == 2) {
+        R.push_back(4);
+    }
+    for (int i = 0; i < p8; i++) R.insert(R.begin(), 8);
+    for (int i = 0; i < b; i++) R.push_back(3);
+    p.nst = (int)R.size();
+    int Ns = 1;
+    for (int s = 0; s < p.nst; s++) {
+        p.R[s] = R[s];
+        p.Ns[s] = Ns;
+        Ns *= R[s];
+    }
+    return p;
+}
+
+template <typename T> struct DevTables {
+    cx<T>* twM = nullptr;   // [M]
+    cx<T>* tw2 = nullptr;   // [M + 1]
+    cx<T>* twy = nullptr;   // [n2]
+    cx<T>* twz = nullptr;   // [n3]
+    T* sa[3] = {nullptr, nullptr, nullptr};
+    T* sb[3] = {nullptr, nullptr, nullptr};
+};
+
+template <typename T> static int upload_tw(cx<T>** d, int n, int denom)
+{
+    std::vector<cx<T>> h(std::max(n, 1));
+    for (int t = 0; t < n; t++) {
+        const double ang = 2.0 * M_PI * (double)t / (double)denom;
+        h[t].x = (T)std::cos(ang);
+        h[t].y = (T)(-std::sin(ang));
+    }
+    CK(cudaMalloc(d, sizeof(cx<T>) * h.size()));
+    CK(cudaMemcpy(*d, h.data(), sizeof(cx<T>) * h.size(), cudaMemcpyHostToDevice));
+    return COMBO_OK;
+}
+
+// Discrete derivative symbol in product form k_j = sa_j[xi_j] prod_{m != j} sb_m[xi_m].
+//   rotated (Willot, HEX8R): sa = (2/h) sin(pi xi / n), sb = cos(pi xi / n), sb := 0 at Nyquist;
+//     this is the rotated-scheme symbol up to the common phase i e^{i sum theta/2},
+//     which cancels in k k^H / |k|^2.
+//   spectral (Moulinec-Suquet): sa = 2 pi xi_signed / l (0 at Nyquist), sb = 1.
+template <typename T> static int upload_symbols(DevTables<T>& t, const int n[3], const double l[3], int kspace)
+{
+    for (int j = 0; j < 3; j++) {
+        std::vector<T> a(n[j]), b(n[j]);
+        const double h = l[j] / n[j];
+        for (int x = 0; x < n[j]; x++) {
+            const bool nyq = (2 * x == n[j]);
+            if (kspace == COMBO_ROTATED) {
+                a[x] = (T)((2.0 / h) * std::sin(M_PI * (double)x / n[j]));
+                b[x] = nyq ? (T)0 : (T)std::cos(M_PI * (double)x / n[j]);
+            } else {
+                const int xs = (2 * x > n[j]) ? x - n[j] : x;
+                a[x] = nyq ? (T)0 : (T)(2.0 * M_PI * (double)xs / l[j]);
+                b[x] = (T)1;
+            }
+        }
+        CK(cudaMalloc(&t.sa[j], sizeof(T) * n[j]));
+        CK(cudaMalloc(&t.sb[j], sizeof(T) * n[j]));
+        CK(cudaMemcpy(t.sa[j], a.data(), sizeof(T) * n[j], cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(t.sb[j], b.data(), sizeof(T) * n[j], cudaMemcpyHostToDevice));
+    }
+    return COMBO_OK;
+}
+
+template <typename T> static int make_tables(DevTables<T>& t, const GridDims& g, const double l[3], int kspace)
+{
+    int rc;
+    if ((rc = upload_tw<T>(&t.twM, g.M, g.M))) return rc;
+    if ((rc = upload_tw<T>(&t.tw2, g.M + 1, g.n1))) return rc;
+    if ((rc = upload_tw<T>(&t.twy, g.n2, g.n2))) return rc;
+    if ((rc = upload_tw<T>(&t.twz, g.n3, g.n3))) return rc;
+    const int n[3] = {g.n1, g.n2, g.n3};
+    return upload_symbols<T>(t, n, l, kspace);
+}
+
+template <typename T> static void free_tables(DevTables<T>& t)
+{
+    cudaFree(t.twM);
+    cudaFree(t.tw2);
+    cudaFree(t.twy);
+    cudaFree(t.twz);
+    for (int j = 0; j < 3; j++) {
+        cudaFree(t.sa[j]);
+        cudaFree(t.sb[j]);
+    }
+}
+
+static int tx_for(int n, size_t cxbytes, size_t budget, int comps)
+{
+    int tx = 16;
+    while (tx > 1 && 2 * (size_t)comps * n * tx * cxbytes > budget) tx /= 2;
+    return tx;
+}
+
+static GridDims make_dims(const int32_t n[3])
+{
+    GridDims g{};
+    g.n1 = n[0];
+    g.n2 = n[1];
+    g.n3 = n[2];
+    g.M = n[0] / 2;
+    g.nh = g.M + 1;
+    g.nhp = (g.nh + 3) / 4 * 4;
+    g.V = (int64_t)n[0] * n[1] * n[2];
+    g.Vs = (int64_t)n[2] * n[1] * g.nhp;
+    return g;
+}
+
+// ------------------------------------------------------------------ operator engine
+// One FFT + Green-operator pipeline in precision T.
+template <typename T> struct Engine {
+    GridDims g;
+    DevTables<T> tab;
+    Plan pM, py, pz;
+    int lines, txy, txz;
+    cx<T>* spec = nullptr;  // not owned
+    int init(const GridDims& gd, const double l[3], int kspace)
+    {
+        g = gd;
+        pM = make_plan(g.M);
+        py = make_plan(g.n2);
+        pz = make_plan(g.n3);
+        lines = xpass_lines(g, sizeof(cx<T>));
+        txy = tx_for(g.n2, sizeof(cx<T>), 64 * 1024, 1);
+        txz = tx_for(g.n3, sizeof(cx<T>), 96 * 1024, 3);
+        return make_tables<T>(tab, g, l, kspace);
+    }
+    void release() { free_tables<T>(tab); }
+
+    template <typename Tc> XfwdArgs<T, Tc> xf() const
+    {
+        XfwdArgs<T, Tc> a{};
+        a.g = g;
+        a.plan = pM;
+        a.tw = tab.twM;
+        a.tw2 = tab.tw2;
+        a.spec = spec;
+        a.lines_per_block = lines;
+        return a;
+    }
+    template <typename Tc> XinvArgs<T, Tc> xi() const
+    {
+        XinvArgs<T, Tc> a{};
+        a.g = g;
+        a.plan = pM;
+        a.tw = tab.twM;
+        a.tw2 = tab.tw2;
+        a.spec = spec;
+        a.lines_per_block = lines;
+        return a;
+    }
+    // y forward, z forward + projection + z inverse, y inverse
+    void yz(Scalars* sc, int guard, bool want_norm, double* partial, cudaStream_t st) const
+    {
+        YArgs<T> y{};
+        y.g = g;
+        y.plan = py;
+        y.tw = tab.twy;
+        y.spec = spec;
+        y.tx = txy;
+        y.sc = sc;
+        y.guard = guard;
+        launch_ypass<T, false>(y, st);
+        ZArgs<T> z{};
+        z.g = g;
+        z.plan = pz;
+        z.tw = tab.twz;
+        z.spec = spec;
+        z.tx = txz;
+        for (int j = 0; j < 3; j++) {
+            z.sa[j] = tab.sa[j];
+            z.sb[j] = tab.sb[j];
+        }
+        z.scale = (T)(2.0 / (double)g.V);
+        z.want_norm = want_norm ? 1 : 0;
+        z.partial = partial;
+        z.sc = sc;
+        z.guard = guard;
+        launch_zpass<T>(z, st);
+        launch_ypass<T, true>(y, st);
+    }
+    int zblocks() const { return ((g.nh + txz - 1) / txz) * g.n2 * 3; }
+    int xblocks() const { return (g.n2 * g.n3 + lines - 1) / lines; }
+};
+
+// ------------------------------------------------------------------ small kernels
+__global__ void k_fill_identity(double* F, int64_t V)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 9 * V; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / V);
+        F[i] = (c == 0 || c == 4 || c == 8) ? 1.0 : 0.0;
+    }
+}
+
+struct Mat9 {
+    double v[9];
+};
+
+__global__ void k_add_uniform(double* F, int64_t V, Mat9 d)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 9 * V; i += (int64_t)gridDim.x * blockDim.x)
+        F[i] += d.v[i / V];
+}
+
+__global__ void k_vox2box(int32_t* map, const int32_t* bidx, int64_t nb)
+{
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b < nb) map[bidx[b]] = (int32_t)b;
+}
+
+// deterministic fixed-order sum of n partials by one block
+__device__ double sum_partials(const double* p, int n, double* red)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
+    // fixed tree over the block (same order every launch)
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    return red[0];
+}
+
+// residual of the current evaluation; fixed-point bookkeeping (mode 1)
+__global__ void k_fin_resid(Scalars* sc, const double* part, int n, double V, double tol, int fixed, int max_iter,
+                            int fixed_point)
+{
+    __shared__ double red[256];
+    if (fixed_point && sc->outer_done) return;
+    const double s = sum_partials(part, n, red);
+    if (threadIdx.x != 0) return;
+    sc->resid2 = s;
+    double pn = 0.0;
+    for (int c = 0; c < 9; c++) {
+        sc->Pbar[c] = sc->dc[c] / V;
+        pn += sc->Pbar[c] * sc->Pbar[c];
+    }
+    pn = sqrt(pn);
+    const double eps = sqrt(s) / V / (pn > 0.0 ? pn : 1.0);
+    sc->eps = eps;
+    sc->n_operator64 += 1;
+    if (!isfinite(eps)) {
+        atomicCAS(&sc->status, 0, COMBO_E_NAN);
+        sc->outer_done = 1;
+        return;
+    }
+    if (fixed_point) {
+        const int it = sc->outer_iter;
+        if (fixed > 0 ? it >= fixed : eps <= tol) {
+            sc->outer_done = 1;
+        } else if (it >= max_iter) {
+            atomicCAS(&sc->status, 0, COMBO_E_NOT_CONVERGED);
+            sc->outer_done = 1;
+        } else {
+            sc->outer_iter = it + 1;
+            sc->n_operator += 1;
+        }
+    }
+}
+
+__global__ void k_fin_rhs(Scalars* sc, const double* part, int n, int cg_fixed, int cg_max)
+{
+    __shared__ double red[256];
+    const double s = sum_partials(part, n, red);
+    if (threadIdx.x != 0) return;
+    sc->rr = s;
+    sc->rr0 = s;
+    sc->cg_iter = 0;
+    sc->beta = 0.0;
+    const bool stop = (cg_fixed <= 0) && (cg_max <= 0);
+    sc->cg_done = (s == 0.0 || stop) ? 1 : 0;
+}
+
+__global__ void k_fin_alpha(Scalars* sc, const double* part, int n)
+{
+    __shared__ double red[256];
+    if (sc->cg_done) return;
+    const double s = sum_partials(part, n, red);
+    if (threadIdx.x != 0) return;
+    sc->pAp = s;
+    if (!(s > 0.0)) {
+        sc->cg_done = 1;  // loss of positive curvature: stop with the current iterate
+        return;
+    }
+    sc->alpha = sc->rr / s;
+}
+
+__global__ void k_fin_beta(Scalars* sc, const double* part, int n, double cg_tol, int cg_max, int cg_fixed)
+{
+    __shared__ double red[256];
+    if (sc->cg_done) return;
+    const double s = sum_partials(part, n, red);
+    if (threadIdx.x != 0) return;
+    sc->beta = s / sc->rr;
+    sc->rr = s;
+    const int j = sc->cg_iter + 1;
+    sc->cg_iter = j;
+    sc->n_operator += 1;
+    bool stop;
+    if (cg_fixed > 0)
+        stop = j >= cg_fixed;
+    else
+        stop = (sqrt(s) <= cg_tol * sqrt(sc->rr0)) || j >= cg_max;
+    if (stop || s == 0.0) sc->cg_done = 1;
+}
+
+// F += d * x, then admissibility (det F > 0) of every voxel
+template <typename Tc> __global__ void k_update_F(double* F, const Tc* x, double d, int64_t V, Scalars* sc)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        double f[9];
+#pragma unroll
+        for (int c = 0; c < 9; c++) {
+            f[c] = F[c * V + v] + d * (double)x[c * V + v];
+            F[c * V + v] = f[c];
+        }
+        const double J = f[0] * (f[4] * f[8] - f[5] * f[7]) - f[1] * (f[3] * f[8] - f[5] * f[6]) +
+                         f[2] * (f[3] * f[7] - f[4] * f[6]);
+        if (!(J > 0.0)) sc->admissible = 0;
+    }
+}
+
+// P field of F (pure voxels Neo-Hookean, boxels from the laminate stresses)
+__global__ void k_eval_P(const double* F, const uint8_t* phase, const int32_t* vox2box, const double* bP, Mat9 mat,
+                         double* P, int64_t V, Scalars* sc)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        const int ph = phase[v];
+        if (ph == 2) {
+            const int b = vox2box[v];
+            for (int c = 0; c < 9; c++) P[c * V + v] = bP[(int64_t)b * 9 + c];
+            continue;
+        }
+        double f[9];
+        for (int c = 0; c < 9; c++) f[c] = F[c * V + v];
+        const double mu = mat.v[ph], lam = mat.v[2 + ph];
+        const double c0 = f[4] * f[8] - f[5] * f[7], c1 = f[5] * f[6] - f[3] * f[8], c2 = f[3] * f[7] - f[4] * f[6];
+        const double J = f[0] * c0 + f[1] * c1 + f[2] * c2;
+        if (!(J > 0.0)) {
+            atomicCAS(&sc->status, 0, COMBO_E_INADMISSIBLE);
+            continue;
+        }
+        const double iJ = 1.0 / J;
+        double G[9] = {c0 * iJ,
+                       (f[2] * f[7] - f[1] * f[8]) * iJ,
+                       (f[1] * f[5] - f[2] * f[4]) * iJ,
+                       c1 * iJ,
+                       (f[0] * f[8] - f[2] * f[6]) * iJ,
+                       (f[2] * f[3] - f[0] * f[5]) * iJ,
+                       c2 * iJ,
+                       (f[1] * f[6] - f[0] * f[7]) * iJ,
+                       (f[0] * f[4] - f[1] * f[3]) * iJ};
+        const double k = lam * log(J) - mu;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) P[(3 * i + j) * V + v] = mu * f[3 * i + j] + k * G[3 * j + i];
+    }
+}
+
+static int grid_for(int64_t n, int block = 256)
+{
+    int64_t g = (n + block - 1) / block;
+    return (int)std::min<int64_t>(std::max<int64_t>(g, 1), 152 * 16);
+}
+
+// ------------------------------------------------------------------ validated host copy of a problem
+struct HostProblem {
+    int32_t n[3];
+    double l[3];
+    std::vector<uint8_t> phase;
+    std::vector<int32_t> bidx;
+    std::vector<double> bN, bc;
+    double mu[2], lam[2], Fbar[9];
+    int32_t n_steps;
+};
+
+static double det9(const double* F)
+{
+    return F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) + F[2] * (F[3] * F[7] - F[4] * F[6]);
+}
+
+static int validate_dims(const int32_t n[3])
+{
+    for (int j = 0; j < 3; j++)
+        if (n[j] < 2 || n[j] > 1024 || !is_23(n[j])) return fail(COMBO_E_INVALID_ARG, "grid sides must be 2^a 3^b in [2, 1024]");
+    if (n[0] % 2) return fail(COMBO_E_INVALID_ARG, "n1 must be even");
+    if ((int64_t)n[0] * n[1] * n[2] >= (int64_t)1 << 31) return fail(COMBO_E_INVALID_ARG, "grid too large");
+    return COMBO_OK;
+}
+
+static int load_problem(const combo_problem* p, const combo_options* o, HostProblem& h)
+{
+    if (!p || !o) return fail(COMBO_E_INVALID_ARG, "null problem or options");
+    int rc = validate_dims(p->n);
+    if (rc) return rc;
+    for (int j = 0; j < 3; j++) {
+        h.n[j] = p->n[j];
+        h.l[j] = p->l[j];
+        if (!(p->l[j] > 0.0)) return fail(COMBO_E_INVALID_ARG, "RVE lengths must be positive");
+    }
+    for (int i = 0; i < 2; i++) {
+        h.mu[i] = p->mu[i];
+        h.lam[i] = p->lambda[i];
+        if (!(p->mu[i] > 0.0) || !(p->lambda[i] > -2.0 * p->mu[i] / 3.0))
+            return fail(COMBO_E_INVALID_ARG, "need mu > 0 and lambda > -2 mu / 3");
+    }
+    std::memcpy(h.Fbar, p->Fbar, sizeof(h.Fbar));
+    if (!(det9(h.Fbar) > 0.0)) return fail(COMBO_E_INVALID_ARG, "det Fbar must be positive");
+    if (p->n_steps < 1) return fail(COMBO_E_INVALID_ARG, "n_steps must be >= 1");
+    h.n_steps = p->n_steps;
+    const int64_t V = (int64_t)p->n[0] * p->n[1] * p->n[2];
+    const int64_t nb = p->n_boxels;
+    if (nb < 0 || nb > V) return fail(COMBO_E_INVALID_ARG, "bad n_boxels");
+    if (!p->phase || (nb > 0 && (!p->boxel_idx || !p->boxel_N || !p->boxel_c)))
+        return fail(COMBO_E_INVALID_ARG, "null problem array");
+    h.phase.resize(V);
+    std::vector<int64_t> idx(nb);
+    std::vector<double> N(3 * nb), c(nb);
+    const cudaMemcpyKind kind = (p->mem == COMBO_MEM_DEVICE) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    CK(cudaMemcpy(h.phase.data(), p->phase, V, kind));
+    if (nb > 0) {
+        CK(cudaMemcpy(idx.data(), p->boxel_idx, 8 * nb, kind));
+        CK(cudaMemcpy(N.data(), p->boxel_N, 24 * nb, kind));
+        CK(cudaMemcpy(c.data(), p->boxel_c, 8 * nb, kind));
+    }
+    int64_t cnt2 = 0;
+    for (int64_t v = 0; v < V; v++) {
+        const uint8_t ph = h.phase[v];
+        if (ph > 2) return fail(COMBO_E_INVALID_ARG, "phase codes must be 0, 1 or 2");
+        cnt2 += (ph == 2);
+    }
+    if (cnt2 != nb) return fail(COMBO_E_INVALID_ARG, "n_boxels differs from the number of phase-2 voxels");
+    h.bidx.reserve(nb);
+    h.bN.reserve(3 * nb);
+    h.bc.reserve(nb);
+    for (int64_t b = 0; b < nb; b++) {
+        if (idx[b] < 0 || idx[b] >= V || (b > 0 && idx[b] <= idx[b - 1]))
+            return fail(COMBO_E_INVALID_ARG, "boxel_idx must be strictly increasing voxel indices");
+        if (h.phase[idx[b]] != 2) return fail(COMBO_E_INVALID_ARG, "boxel_idx points at a non-boxel voxel");
+        const double nn = std::sqrt(N[3 * b] * N[3 * b] + N[3 * b + 1] * N[3 * b + 1] + N[3 * b + 2] * N[3 * b + 2]);
+        if (!(nn >= 1e-12)) return fail(COMBO_E_INVALID_ARG, "boxel normal of zero length");
+        const double cb = c[b];
+        if (!(cb > 0.0 && cb < 1.0)) return fail(COMBO_E_INVALID_ARG, "boxel volume fraction outside (0, 1)");
+        if (cb < o->c_min) {
+            h.phase[idx[b]] = 0;  // evaluated as the pure matrix
+            continue;
+        }
+        if (cb > 1.0 - o->c_min) {
+            h.phase[idx[b]] = 1;  // evaluated as the pure inclusion
+            continue;
+        }
+        h.bidx.push_back((int32_t)idx[b]);
+        for (int i = 0; i < 3; i++) h.bN.push_back(N[3 * b + i] / nn);
+        h.bc.push_back(cb);
+    }
+    return COMBO_OK;
+}
+
+static int check_options(combo_options& o)
+{
+    if (o.precision != COMBO_FP64 && o.precision != COMBO_FP32_REFINED) return fail(COMBO_E_INVALID_ARG, "bad precision");
+    if (o.kspace != COMBO_ROTATED && o.kspace != COMBO_SPECTRAL) return fail(COMBO_E_INVALID_ARG, "bad kspace");
+    if (o.solver != COMBO_FIXED_POINT && o.solver != COMBO_NEWTON_CG) return fail(COMBO_E_INVALID_ARG, "bad solver");
+    if (o.solver == COMBO_FIXED_POINT && o.precision != COMBO_FP64)
+        return fail(COMBO_E_INVALID_ARG, "the fixed point runs in FP64 only");
+    if (o.max_iter <= 0) o.max_iter = (o.solver == COMBO_FIXED_POINT) ? 100000 : 200;
+    if (!(o.tol >= 0.0) || !(o.cg_tol >= 0.0)) return fail(COMBO_E_INVALID_ARG, "negative tolerance");
+    if (o.nr_max_iter <= 0) o.nr_max_iter = 50;
+    if (!(o.c_min >= 0.0 && o.c_min < 0.5)) return fail(COMBO_E_INVALID_ARG, "c_min outside [0, 0.5)");
+    return COMBO_OK;
+}
+
+// ------------------------------------------------------------------ solve state
+struct SolveBase {
+    virtual ~SolveBase() {}
+    virtual int advance(int64_t max_ops) = 0;
+    virtual int finish(combo_result* r) = 0;
+};
+
+struct combo_solve_state {
+    SolveBase* impl;
+};
+
+template <typename Tc> struct Solve : SolveBase {
+    combo_ctx* ctx;
+    combo_options opt;
+    HostProblem hp;
+    GridDims g;
+    int64_t nb = 0;
+    cudaStream_t st;
+    Engine<double> e64;
+    Engine<Tc> ec;  // Krylov precision (same as e64 when Tc = double)
+    // device memory
+    uint8_t* d_phase = nullptr;
+    int32_t* d_v2b = nullptr;
+    int32_t* d_bidx = nullptr;
+    double *d_bN = nullptr, *d_bc = nullptr, *d_ba = nullptr, *d_bP = nullptr;
+    Tc* d_bA = nullptr;
+    double* d_F = nullptr;
+    void* d_spec = nullptr;
+    Tc *d_tc = nullptr, *d_x = nullptr, *d_r = nullptr, *d_p = nullptr;
+    double* d_part = nullptr;
+    Scalars* d_sc = nullptr;
+    double mu0 = 0.0;
+    // host state machine
+    enum { ST_STEP, ST_RESID, ST_CG, ST_UPDATE, ST_FP, ST_DONE } state = ST_STEP;
+    int step = 0;  // completed load steps
+    int outer = 0;
+    int cg_step_total = 0;
+    double Fprev[9];
+    std::vector<double> Pbar, resid;
+    std::vector<int32_t> iters, cg_iters;
+    int64_t ops_done = 0;
+    int error = 0;
+
+    ~Solve() override
+    {
+        cudaFree(d_phase);
+        cudaFree(d_v2b);
+        cudaFree(d_bidx);
+        cudaFree(d_bN);
+        cudaFree(d_bc);
+        cudaFree(d_ba);
+        cudaFree(d_bP);
+        cudaFree(d_bA);
+        cudaFree(d_F);
+        cudaFree(d_spec);
+        cudaFree(d_tc);
+        cudaFree(d_x);
+        cudaFree(d_r);
+        cudaFree(d_p);
+        cudaFree(d_part);
+        cudaFree(d_sc);
+        e64.release();
+        ec.release();
+    }
+
+    bool newton() const { return opt.solver == COMBO_NEWTON_CG; }
+
+    int init(combo_ctx* c, HostProblem&& h, const combo_options& o)
+    {
+        ctx = c;
+        st = c->stream;
+        opt = o;
+        hp = std::move(h);
+        g = make_dims(hp.n);
+        nb = (int64_t)hp.bidx.size();
+        const int64_t V = g.V;
+        int rc;
+        if ((rc = e64.init(g, hp.l, opt.kspace))) return rc;
+        if ((rc = ec.init(g, hp.l, opt.kspace))) return rc;
+        CK(cudaMalloc(&d_phase, V));
+        CK(cudaMalloc(&d_v2b, 4 * V));
+        CK(cudaMalloc(&d_F, 8 * 9 * V));
+        CK(cudaMalloc(&d_spec, sizeof(double2) * 9 * g.Vs));
+        CK(cudaMemsetAsync(d_spec, 0, sizeof(double2) * 9 * g.Vs, st));
+        const int nbuf = std::max(std::max(e64.xblocks(), e64.zblocks()), std::max(ec.xblocks(), ec.zblocks()));
+        CK(cudaMalloc(&d_part, 8 * (size_t)nbuf));
+        CK(cudaMalloc(&d_sc, sizeof(Scalars)));
+        CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars), st));
+        const size_t nbs = std::max<int64_t>(nb, 1);
+        CK(cudaMalloc(&d_bidx, 4 * nbs));
+        CK(cudaMalloc(&d_bN, 24 * nbs));
+        CK(cudaMalloc(&d_bc, 8 * nbs));
+        CK(cudaMalloc(&d_ba, 24 * nbs));
+        CK(cudaMalloc(&d_bP, 72 * nbs));
+        if (newton()) {
+            CK(cudaMalloc(&d_bA, sizeof(Tc) * 81 * nbs));
+            CK(cudaMalloc(&d_tc, sizeof(Tc) * 10 * V));
+            CK(cudaMalloc(&d_x, sizeof(Tc) * 9 * V));
+            CK(cudaMalloc(&d_r, sizeof(Tc) * 9 * V));
+            CK(cudaMalloc(&d_p, sizeof(Tc) * 9 * V));
+        }
+        e64.spec = (cx<double>*)d_spec;
+        ec.spec = (cx<Tc>*)d_spec;
+        CK(cudaMemcpyAsync(d_phase, hp.phase.data(), V, cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(d_v2b, 0xff, 4 * V, st));
+        if (nb > 0) {
+            CK(cudaMemcpyAsync(d_bidx, hp.bidx.data(), 4 * nb, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(d_bN, hp.bN.data(), 24 * nb, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(d_bc, hp.bc.data(), 8 * nb, cudaMemcpyHostToDevice, st));
+            CK(cudaMemsetAsync(d_ba, 0, 24 * nb, st));
+            k_vox2box<<<(int)((nb + 255) / 256), 256, 0, st>>>(d_v2b, d_bidx, nb);
+        }
+        k_fill_identity<<<grid_for(9 * V), 256, 0, st>>>(d_F, V);
+        CK(cudaGetLastError());
+        mu0 = opt.mu0;
+        if (!(mu0 > 0.0))
+            mu0 = 0.5 * (std::min(hp.mu[0], hp.mu[1]) + std::max(hp.lam[0] + 2 * hp.mu[0], hp.lam[1] + 2 * hp.mu[1]));
+        for (int c = 0; c < 9; c++) Fprev[c] = (c == 0 || c == 4 || c == 8) ? 1.0 : 0.0;
+        Pbar.assign(9 * (size_t)hp.n_steps, 0.0);
+        resid.assign(hp.n_steps, 0.0);
+        iters.assign(hp.n_steps, 0);
+        cg_iters.assign(hp.n_steps, 0);
+        CK(cudaStreamSynchronize(st));
+        return COMBO_OK;
+    }
+
+    // --- kernel sequences
+    void boxels(bool tangent, int guard)
+    {
+        if (nb == 0) return;
+        BoxelArgs<Tc> a{};
+        a.nb = nb;
+        a.V = g.V;
+        a.bidx = d_bidx;
+        a.bN = d_bN;
+        a.bc = d_bc;
+        a.ba = d_ba;
+        a.bP = d_bP;
+        a.bA = tangent ? d_bA : nullptr;
+        a.F = d_F;
+        a.mu[0] = hp.mu[0];
+        a.mu[1] = hp.mu[1];
+        a.lam[0] = hp.lam[0];
+        a.lam[1] = hp.lam[1];
+        a.tol_rel = opt.nr_tol_rel;
+        a.tol_abs = opt.nr_tol_abs;
+        a.max_iter = opt.nr_max_iter;
+        a.sc = d_sc;
+        a.guard = guard;
+        launch_boxel<Tc>(a, st);
+    }
+
+    // FP64 residual operator: G[P(F)]; mode: XI_FIXEDPOINT (update F) or XI_RHS (r = -G[P], x = 0)
+    void resid_operator(int xi_mode, int guard)
+    {
+        auto xf = e64.template xf<Tc>();
+        xf.mode = XF_RESID;
+        xf.phase = d_phase;
+        xf.vox2box = d_v2b;
+        for (int i = 0; i < 2; i++) {
+            xf.mu[i] = hp.mu[i];
+            xf.lam[i] = hp.lam[i];
+        }
+        xf.F = d_F;
+        xf.bP = d_bP;
+        xf.tc = (xi_mode == XI_RHS) ? d_tc : nullptr;
+        xf.nb = nb;
+        xf.sc = d_sc;
+        launch_xfwd<double, Tc>(xf, guard, st);
+        e64.yz(d_sc, guard, true, d_part, st);
+        k_fin_resid<<<1, 256, 0, st>>>(d_sc, d_part, e64.zblocks(), (double)g.V, opt.tol, opt.fixed_iterations,
+                                       opt.max_iter, xi_mode == XI_FIXEDPOINT ? 1 : 0);
+        auto xi = e64.template xi<Tc>();
+        xi.mode = xi_mode;
+        xi.inv_mu0 = 1.0 / mu0;
+        xi.F = d_F;
+        xi.x = d_x;
+        xi.r = d_r;
+        xi.partial = d_part;
+        xi.sc = d_sc;
+        launch_xinv<double, Tc>(xi, guard, st);
+        if (xi_mode == XI_RHS)
+            k_fin_rhs<<<1, 256, 0, st>>>(d_sc, d_part, e64.xblocks(), opt.cg_fixed_iterations, opt.cg_max_iter);
+    }
+
+    // one CG iteration in precision Tc, guarded by cg_done
+    void cg_iteration()
+    {
+        auto xf = ec.template xf<Tc>();
+        xf.mode = XF_TANGENT;
+        xf.phase = d_phase;
+        xf.vox2box = d_v2b;
+        for (int i = 0; i < 2; i++) {
+            xf.mu[i] = hp.mu[i];
+            xf.lam[i] = hp.lam[i];
+        }
+        xf.tc = d_tc;
+        xf.r = d_r;
+        xf.p = d_p;
+        xf.bA = d_bA;
+        xf.nb = std::max<int64_t>(nb, 1);
+        xf.partial = d_part;
+        xf.sc = d_sc;
+        launch_xfwd<Tc, Tc>(xf, 1, st);
+        k_fin_alpha<<<1, 256, 0, st>>>(d_sc, d_part, ec.xblocks());
+        ec.yz(d_sc, 1, false, nullptr, st);
+        auto xi = ec.template xi<Tc>();
+        xi.mode = XI_CG;
+        xi.x = d_x;
+        xi.r = d_r;
+        xi.p = d_p;
+        xi.partial = d_part;
+        xi.sc = d_sc;
+        launch_xinv<Tc, Tc>(xi, 1, st);
+        k_fin_beta<<<1, 256, 0, st>>>(d_sc, d_part, ec.xblocks(), opt.cg_tol, opt.cg_max_iter,
+                                      opt.cg_fixed_iterations);
+    }
+
+    int read_scalars(Scalars& s)
+    {
+        CK(cudaMemcpyAsync(&s, d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return COMBO_OK;
+    }
+
+    int set_flag(size_t offset, int32_t value)
+    {
+        CK(cudaMemcpyAsync((char*)d_sc + offset, &value, 4, cudaMemcpyHostToDevice, st));
+        return COMBO_OK;
+    }
+
+    int begin_step()
+    {
+        double Fn[9];
+        Mat9 d;
+        const double s = (double)(step + 1) / hp.n_steps;
+        for (int c = 0; c < 9; c++) {
+            const double I = (c == 0 || c == 4 || c == 8) ? 1.0 : 0.0;
+            Fn[c] = I + s * (hp.Fbar[c] - I);
+            d.v[c] = Fn[c] - Fprev[c];
+        }
+        std::memcpy(Fprev, Fn, sizeof(Fn));
+        k_add_uniform<<<grid_for(9 * g.V), 256, 0, st>>>(d_F, g.V, d);
+        CK(cudaGetLastError());
+        outer = 0;
+        cg_step_total = 0;
+        int rc;
+        if ((rc = set_flag(offsetof(Scalars, outer_done), 0))) return rc;
+        if ((rc = set_flag(offsetof(Scalars, outer_iter), 0))) return rc;
+        return COMBO_OK;
+    }
+
+    void record_step(const Scalars& s)
+    {
+        for (int c = 0; c < 9; c++) Pbar[9 * step + c] = s.Pbar[c];
+        resid[step] = s.eps;
+        iters[step] = newton() ? outer : s.outer_iter;
+        cg_iters[step] = cg_step_total;
+        step++;
+    }
+
+    int advance(int64_t max_ops) override
+    {
+        if (error) return error;
+        const int64_t limit = (max_ops > 0) ? ops_done + max_ops : INT64_MAX;
+        CK(cudaSetDevice(ctx->device));
+        Scalars s;
+        int rc;
+        while (true) {
+            if (state == ST_DONE) return COMBO_OK;
+            if (ops_done >= limit) return COMBO_PENDING;
+            switch (state) {
+                case ST_STEP:
+                    if (step >= hp.n_steps) {
+                        state = ST_DONE;
+                        break;
+                    }
+                    if ((rc = begin_step())) return error = rc;
+                    state = newton() ? ST_RESID : ST_FP;
+                    break;
+                case ST_FP: {
+                    // a chunk of fixed-point iterations; kernels skip once converged
+                    const int chunk = 16;
+                    for (int k = 0; k < chunk; k++) {
+                        boxels(false, 2);
+                        resid_operator(XI_FIXEDPOINT, 2);
+                    }
+                    CK(cudaGetLastError());
+                    if ((rc = read_scalars(s))) return error = rc;
+                    ops_done = (int64_t)s.n_operator;
+                    if (s.status) return error = fail(s.status, "fixed point failed");
+                    if (s.outer_done) {
+                        record_step(s);
+                        state = ST_STEP;
+                    }
+                    break;
+                }
+                case ST_RESID: {
+                    boxels(true, 0);
+                    resid_operator(XI_RHS, 0);
+                    CK(cudaGetLastError());
+                    if ((rc = read_scalars(s))) return error = rc;
+                    if (s.status) return error = fail(s.status, "residual evaluation failed");
+                    const bool conv = (opt.fixed_iterations > 0) ? (outer >= opt.fixed_iterations) : (s.eps <= opt.tol);
+                    if (conv) {
+                        record_step(s);
+                        state = ST_STEP;
+                    } else if (outer >= opt.max_iter) {
+                        return error = fail(COMBO_E_NOT_CONVERGED, "Newton did not converge");
+                    } else {
+                        state = ST_CG;
+                    }
+                    break;
+                }
+                case ST_CG: {
+                    const int chunk = 8;
+                    for (int k = 0; k < chunk; k++) cg_iteration();
+                    CK(cudaGetLastError());
+                    if ((rc = read_scalars(s))) return error = rc;
+                    ops_done = (int64_t)s.n_operator;
+                    if (s.status) return error = fail(s.status, "CG failed");
+                    if (s.cg_done) {
+                        cg_step_total += s.cg_iter;
+                        state = ST_UPDATE;
+                    }
+                    break;
+                }
+                case ST_UPDATE: {
+                    double d = 1.0;
+                    bool ok = false;
+                    for (int h = 0; h <= 10; h++) {
+                        if ((rc = set_flag(offsetof(Scalars, admissible), 1))) return error = rc;
+                        k_update_F<Tc><<<grid_for(g.V), 256, 0, st>>>(d_F, d_x, d, g.V, d_sc);
+                        if ((rc = read_scalars(s))) return error = rc;
+                        if (s.admissible) {
+                            ok = true;
+                            break;
+                        }
+                        d = -std::ldexp(1.0, -(h + 1));  // F_old + 2^-(h+1) x
+                    }
+                    if (!ok) return error = fail(COMBO_E_INADMISSIBLE, "det F <= 0 after 10 step halvings");
+                    outer++;
+                    state = ST_RESID;
+                    break;
+                }
+                default:
+                    return COMBO_OK;
+            }
+        }
+    }
+
+    int finish(combo_result* r) override
+    {
+        if (!r || !r->Pbar) return fail(COMBO_E_INVALID_ARG, "result needs Pbar");
+        CK(cudaSetDevice(ctx->device));
+        Scalars s;
+        int rc;
+        if ((rc = read_scalars(s))) return rc;
+        const bool dev = (r->mem == COMBO_MEM_DEVICE);
+        const cudaMemcpyKind h2x = dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+        const cudaMemcpyKind d2x = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        CK(cudaMemcpy(r->Pbar, Pbar.data(), 8 * Pbar.size(), h2x));
+        if (r->iters) CK(cudaMemcpy(r->iters, iters.data(), 4 * iters.size(), h2x));
+        if (r->cg_iters) CK(cudaMemcpy(r->cg_iters, cg_iters.data(), 4 * cg_iters.size(), h2x));
+        if (r->resid) CK(cudaMemcpy(r->resid, resid.data(), 8 * resid.size(), h2x));
+        const int64_t V = g.V;
+        if (r->F_out) CK(cudaMemcpyAsync(r->F_out, d_F, 8 * 9 * V, d2x, st));
+        if (r->P_out) {
+            double* P = dev ? r->P_out : nullptr;
+            if (!dev) CK(cudaMalloc(&P, 8 * 9 * V));
+            Mat9 m{};
+            m.v[0] = hp.mu[0];
+            m.v[1] = hp.mu[1];
+            m.v[2] = hp.lam[0];
+            m.v[3] = hp.lam[1];
+            k_eval_P<<<grid_for(V), 256, 0, st>>>(d_F, d_phase, d_v2b, d_bP, m, P, V, d_sc);
+            if (!dev) {
+                CK(cudaMemcpyAsync(r->P_out, P, 8 * 9 * V, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                cudaFree(P);
+            }
+        }
+        if (r->a_out && nb > 0) CK(cudaMemcpyAsync(r->a_out, d_ba, 24 * nb, d2x, st));
+        CK(cudaStreamSynchronize(st));
+        r->steps_done = step;
+        r->nr_iters = (int64_t)s.nr_iters;
+        r->n_backproj = (int64_t)s.n_backproj;
+        r->n_laminate_evals = (int64_t)s.n_lam;
+        r->n_operator = (int64_t)s.n_operator;
+        r->n_operator_fp64 = (int64_t)s.n_operator64;
+        return error;
+    }
+};
+
+// ------------------------------------------------------------------ C ABI: solves
+extern "C" int64_t combo_solve_footprint(const combo_problem* p, const combo_options* o)
+{
+    if (!p || !o) return -1;
+    const int64_t V = (int64_t)p->n[0] * p->n[1] * p->n[2];
+    const GridDims g = make_dims(p->n);
+    const int64_t nb = std::max<int64_t>(p->n_boxels, 1);
+    const int64_t tc = (o->precision == COMBO_FP32_REFINED) ? 4 : 8;
+    int64_t b = V * (1 + 4 + 72) + 16 * 9 * g.Vs + nb * (4 + 24 + 8 + 24 + 72);
+    if (o->solver == COMBO_NEWTON_CG) b += tc * (81 * nb + 37 * V);
+    return b;
+}
+
+extern "C" int combo_solve_begin(combo_ctx* ctx, const combo_problem* p, const combo_options* o_in,
+                                 combo_solve_state** out)
+{
+    if (!ctx || !out) return fail(COMBO_E_INVALID_ARG, "null context or output");
+    combo_options o;
+    if (o_in)
+        o = *o_in;
+    else
+        combo_options_default(&o);
+    int rc = check_options(o);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device));
+    HostProblem h;
+    if ((rc = load_problem(p, &o, h))) return rc;
+    SolveBase* impl = nullptr;
+    if (o.precision == COMBO_FP64) {
+        auto* s = new Solve<double>();
+        rc = s->init(ctx, std::move(h), o);
+        impl = s;
+    } else {
+        auto* s = new Solve<float>();
+        rc = s->init(ctx, std::move(h), o);
+        impl = s;
+    }
+    if (rc) {
+        std::string msg = g_err;
+        delete impl;
+        cudaGetLastError();
+        g_err = msg;
+        return (rc == COMBO_E_CUDA && msg.find("memory") != std::string::npos) ? COMBO_E_OOM : rc;
+    }
+    *out = new combo_solve_state{impl};
+    return COMBO_OK;
+}
+
+extern "C" int combo_solve_advance(combo_solve_state* s, int64_t max_ops)
+{
+    if (!s) return fail(COMBO_E_INVALID_ARG, "null solve");
+    return s->impl->advance(max_ops);
+}
+
+extern "C" int combo_solve_finish(combo_solve_state* s, combo_result* r)
+{
+    if (!s) return fail(COMBO_E_INVALID_ARG, "null solve");
+    return s->impl->finish(r);
+}
+
+extern "C" void combo_solve_end(combo_solve_state* s)
+{
+    if (!s) return;
+    delete s->impl;
+    delete s;
+}
+
+extern "C" int combo_solve(combo_ctx* ctx, const combo_problem* p, const combo_options* o, combo_result* r)
+{
+    combo_solve_state* s = nullptr;
+    int rc = combo_solve_begin(ctx, p, o, &s);
+    if (rc) return rc;
+    rc = combo_solve_advance(s, 0);
+    const std::string msg = g_err;
+    const int rc2 = combo_solve_finish(s, r);
+    combo_solve_end(s);
+    if (rc) {
+        g_err = msg;
+        return rc;
+    }
+    return rc2;
+}
+
+// ------------------------------------------------------------------ C ABI: unit entry points
+template <typename T> static int apply_G_impl(combo_ctx* ctx, const int32_t n[3], const double l[3], int kspace,
+                                              const double* X, double* Y, double* sumsq, int mem)
+{
+    const GridDims g = make_dims(n);
+    const int64_t V = g.V;
+    Engine<T> e;
+    int rc = e.init(g, l, kspace);
+    if (rc) return rc;
+    cudaStream_t st = ctx->stream;
+    double *dX = nullptr, *dY = nullptr, *part = nullptr;
+    void* spec = nullptr;
+    Scalars* sc = nullptr;
+    const bool dev = (mem == COMBO_MEM_DEVICE);
+    auto cleanup = [&]() {
+        if (!dev) {
+            cudaFree(dX);
+            cudaFree(dY);
+        }
+        cudaFree(part);
+        cudaFree(spec);
+        cudaFree(sc);
+        e.release();
+    };
+#define CKC(call)                                                                                             \
+    do {                                                                                                      \
+        cudaError_t e_ = (call);                                                                              \
+        if (e_ != cudaSuccess) {                                                                              \
+            cleanup();                                                                                        \
+            return fail(COMBO_E_CUDA, std::string(#call ": ") + cudaGetErrorString(e_));                     \
+        }                                                                                                     \
+    } while (0)
+    if (dev) {
+        dX = const_cast<double*>(X);
+        dY = Y;
+    } else {
+        CKC(cudaMalloc(&dX, 72 * V));
+        CKC(cudaMalloc(&dY, 72 * V));
+        CKC(cudaMemcpyAsync(dX, X, 72 * V, cudaMemcpyHostToDevice, st));
+    }
+    CKC(cudaMalloc(&spec, sizeof(cx<T>) * 9 * g.Vs));
+    CKC(cudaMemsetAsync(spec, 0, sizeof(cx<T>) * 9 * g.Vs, st));
+    CKC(cudaMalloc(&part, 8 * (size_t)std::max(e.xblocks(), e.zblocks())));
+    CKC(cudaMalloc(&sc, sizeof(Scalars)));
+    CKC(cudaMemsetAsync(sc, 0, sizeof(Scalars), st));
+    e.spec = (cx<T>*)spec;
+    auto xf = e.template xf<T>();
+    xf.X = dX;
+    xf.sc = sc;
+    launch_xfwd<T, T>(xf, 0, st);
+    e.yz(sc, 0, true, part, st);
+    k_fin_resid<<<1, 256, 0, st>>>(sc, part, e.zblocks(), (double)V, 0.0, 0, 0, 0);
+    auto xi = e.template xi<T>();
+    xi.mode = XI_PLAIN;
+    xi.Y = dY;
+    xi.sc = sc;
+    launch_xinv<T, T>(xi, 0, st);
+    CKC(cudaGetLastError());
+    Scalars s;
+    CKC(cudaMemcpyAsync(&s, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+    if (!dev) CKC(cudaMemcpyAsync(Y, dY, 72 * V, cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+    if (sumsq) *sumsq = s.resid2 / (double)V;
+    cleanup();
+#undef CKC
+    return COMBO_OK;
+}
+
+extern "C" int combo_apply_G(combo_ctx* ctx, const int32_t n[3], const double l[3], int32_t kspace, int32_t precision,
+                             const double* X, double* Y, double* sumsq, int32_t mem)
+{
+    if (!ctx || !n || !l || !X || !Y) return fail(COMBO_E_INVALID_ARG, "null argument");
+    int rc = validate_dims(n);
+    if (rc) return rc;
+    if (kspace != COMBO_ROTATED && kspace != COMBO_SPECTRAL) return fail(COMBO_E_INVALID_ARG, "bad kspace");
+    CK(cudaSetDevice(ctx->device));
+    if (precision == COMBO_FP64) return apply_G_impl<double>(ctx, n, l, kspace, X, Y, sumsq, mem);
+    if (precision == COMBO_FP32_REFINED) return apply_G_impl<float>(ctx, n, l, kspace, X, Y, sumsq, mem);
+    return fail(COMBO_E_INVALID_ARG, "bad precision");
+}
+
+extern "C" int combo_constitutive(combo_ctx* ctx, const combo_problem* p, const combo_options* o_in, const double* F,
+                                  double* a_io, double* P, int32_t mem)
+{
+    if (!ctx || !F || !P) return fail(COMBO_E_INVALID_ARG, "null argument");
+    combo_options o;
+    if (o_in)
+        o = *o_in;
+    else
+        combo_options_default(&o);
+    o.precision = COMBO_FP64;
+    o.solver = COMBO_FIXED_POINT;
+    int rc = check_options(o);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device));
+    HostProblem h;
+    if ((rc = load_problem(p, &o, h))) return rc;
+    // boxel order after snapping: map back to the caller's boxel list
+    const int64_t nb_in = p->n_boxels;
+    std::vector<int64_t> idx_in(nb_in);
+    if (nb_in > 0)
+        CK(cudaMemcpy(idx_in.data(), p->boxel_idx, 8 * nb_in,
+                      p->mem == COMBO_MEM_DEVICE ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    Solve<double> s;
+    if ((rc = s.init(ctx, std::move(h), o))) return rc;
+    const int64_t V = s.g.V;
+    const bool dev = (mem == COMBO_MEM_DEVICE);
+    const cudaMemcpyKind in = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(s.d_F, F, 72 * V, in, s.st));
+    std::vector<double> a_all(3 * std::max<int64_t>(nb_in, 1), 0.0), a_kept(3 * std::max<int64_t>(s.nb, 1), 0.0);
+    if (a_io && nb_in > 0) {
+        CK(cudaMemcpy(a_all.data(), a_io, 24 * nb_in, dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    }
+    // kept boxels are the subsequence of idx_in that survived the snap
+    std::vector<int64_t> pos(s.nb);
+    for (int64_t b = 0, k = 0; b < nb_in && k < s.nb; b++)
+        if (idx_in[b] == s.hp.bidx[k]) {
+            pos[k] = b;
+            for (int i = 0; i < 3; i++) a_kept[3 * k + i] = a_all[3 * b + i];
+            k++;
+        }
+    if (s.nb > 0) CK(cudaMemcpyAsync(s.d_ba, a_kept.data(), 24 * s.nb, cudaMemcpyHostToDevice, s.st));
+    s.boxels(false, 0);
+    combo_result r{};
+    std::vector<double> pb(9 * (size_t)s.hp.n_steps);
+    r.Pbar = pb.data();
+    r.P_out = P;
+    r.mem = mem;
+    if ((rc = s.finish(&r))) return rc;
+    Scalars sc;
+    if ((rc = s.read_scalars(sc))) return rc;
+    if (sc.status) return fail(sc.status, "constitutive evaluation failed");
+    if (a_io && s.nb > 0) {
+        CK(cudaMemcpy(a_kept.data(), s.d_ba, 24 * s.nb, cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < s.nb; k++)
+            for (int i = 0; i < 3; i++) a_all[3 * pos[k] + i] = a_kept[3 * k + i];
+        CK(cudaMemcpy(a_io, a_all.data(), 24 * nb_in, dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    }
+    return COMBO_OK;
+}

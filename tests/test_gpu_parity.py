@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (max-abs error relative to the max-abs reference value):
+  FP64 fields after equal iterations  <= 1e-10, Pbar <= 1e-9
+  FP32 Green operator                  <= 2e-6 (single-precision FFT rounding)
+  FP32-refined converged solve: Pbar <= 1e-5, local F <= 1e-4
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cb():
+    from paper_2204_13624_gb300 import build, combo
+
+    build.build()
+    combo.load()
+    return combo
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+SHAPES = [(4, 4, 4), (2, 3, 4), (6, 9, 8), (8, 12, 18), (32, 16, 24), (24, 27, 6), (16, 32, 36), (64, 8, 16)]
+
+
+@pytest.mark.parametrize("kspace", [0, 1])
+@pytest.mark.parametrize("n", SHAPES)
+def test_green_operator_fp64(cb, orc, n, kspace):
+    rng = np.random.default_rng(sum(n) + kspace)
+    V = n[0] * n[1] * n[2]
+    l = (1.0, 0.8, 1.3)
+    X = rng.normal(size=(9, V))
+    Yo, sso = orc.apply_G(X, n, l, kspace)
+    Yg, ssg = cb.apply_G(X, n, l, kspace, cb.FP64)
+    assert rel(Yg, Yo) < 1e-12
+    assert abs(ssg - sso) <= 1e-11 * sso
+
+
+@pytest.mark.parametrize("n", SHAPES)
+def test_green_operator_fp32(cb, orc, n):
+    rng = np.random.default_rng(sum(n))
+    V = n[0] * n[1] * n[2]
+    X = rng.normal(size=(9, V))
+    Yo, sso = orc.apply_G(X, n, (1.0, 1.0, 1.0), 0)
+    Yg, ssg = cb.apply_G(X, n, (1.0, 1.0, 1.0), 0, cb.FP32_REFINED)
+    assert rel(Yg, Yo) < 2e-6
+    assert abs(ssg - sso) <= 1e-5 * sso
+
+
+def test_constitutive_matches_oracle(cb, orc):
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.random_boxels((8, 6, 10), seed=3, boxel_frac=0.3, incl_frac=0.3, contrast=10.0)
+    rng = np.random.default_rng(4)
+    V = 8 * 6 * 10
+    F = np.eye(3).reshape(9, 1) + 0.08 * rng.uniform(-1, 1, (9, V))
+    a0 = 0.01 * rng.normal(size=(p["boxel_idx"].size, 3))
+    Pg, ag = cb.constitutive(p, F, a=a0)
+    Po, ao = orc.constitutive_field(p, F, a=a0)
+    assert rel(Pg, Po) < 1e-13
+    assert rel(ag, ao) < 1e-10
+
+
+def solve_both(cb, orc, p, **o):
+    g = cb.solve(p, **o)
+    om = dict(solver=o.get("solver", 1), kspace=o.get("kspace", 0), tol=o.get("tol", 1e-8),
+              fixed_iter=o.get("fixed_iterations", 0), cg_fixed_iter=o.get("cg_fixed_iterations", 0),
+              cg_tol=o.get("cg_tol", 1e-3), max_iter=o.get("max_iter", 200 if o.get("solver", 1) else 100000))
+    r = orc.solve(p, om)
+    return g, r
+
+
+def problems():
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    return [
+        ms.centred_sphere((12, 12, 12), 0.2, 10.0, np.diag([1.04, 1.0, 0.99]), 2),
+        ms.random_boxels((10, 6, 12), seed=7, contrast=10.0, n_steps=2),
+        ms.layered((8, 4, 6), axis=1, m_incl=1, c_boxel=0.3, n_steps=1),
+    ]
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_fixed_point_parity(cb, orc, k):
+    p = problems()[k]
+    g, r = solve_both(cb, orc, p, solver=0, fixed_iterations=6)
+    assert rel(g["F"], r["F"]) < 1e-10
+    assert rel(g["Pbar"], r["Pbar"]) < 1e-9
+    assert rel(g["a"], r["a"]) < 1e-9 if len(r["a"]) else True
+    assert list(g["iters"]) == list(r["iters"])
+    assert g["n_operator"] == r["n_operator"]
+
+
+@pytest.mark.parametrize("kspace", [0, 1])
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_newton_cg_parity(cb, orc, k, kspace):
+    p = problems()[k]
+    g, r = solve_both(cb, orc, p, solver=1, kspace=kspace, fixed_iterations=2, cg_fixed_iterations=12)
+    assert rel(g["F"], r["F"]) < 1e-10
+    assert rel(g["P"], r["P"]) < 1e-10
+    assert rel(g["Pbar"], r["Pbar"]) < 1e-9
+    assert list(g["cg_iters"]) == list(r["cg_iters"])
+    assert g["nr_iters"] == r["nr_iters"] and g["n_backproj"] == r["n_backproj"]
+
+
+def test_sphere_32_converged_fp64(cb, orc):
+    """32^3 centred sphere, vf 0.2, contrast 10, Fbar = diag(1.05,1,1) in 5 steps, tol 1e-8."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.sphere_32()
+    g, r = solve_both(cb, orc, p, solver=1, tol=1e-8)
+    assert g["steps_done"] == 5
+    assert np.all(g["resid"] <= 1e-8)
+    assert list(g["iters"]) == list(r["iters"])
+    assert list(g["cg_iters"]) == list(r["cg_iters"])
+    assert rel(g["Pbar"], r["Pbar"]) < 1e-9
+    assert rel(g["F"], r["F"]) < 1e-9
+
+
+def test_sphere_32_refined_fp32(cb, orc):
+    """FP32 Krylov iterations with FP64 residual refinement against the FP64 oracle."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.sphere_32()
+    g = cb.solve(p, solver=1, precision=cb.FP32_REFINED, tol=1e-8)
+    r = orc.solve(p, dict(solver=1, tol=1e-10, cg_tol=1e-4))
+    assert g["steps_done"] == 5 and np.all(g["resid"] <= 1e-8)
+    assert rel(g["Pbar"], r["Pbar"]) < 1e-5
+    assert rel(g["F"], r["F"]) < 1e-4
+
+
+def test_layered_laminate_exact_on_gpu(cb, orc):
+    from paper_2204_13624_gb300 import microstructure as ms
+    import test_oracle_solve as tos
+
+    tos.orc_mod = orc
+    p = ms.layered((4, 8, 4), axis=1, m_incl=3, c_boxel=0.37)
+    g = cb.solve(p, solver=1, tol=1e-12, cg_tol=1e-8, max_iter=60)
+    FA, FB, c, line = tos.exact_laminate(p, 1)
+    F = g["F"].reshape(9, 4, 8, 4)
+    for layer, ph in enumerate(line):
+        want = FA if ph == 1 else (FB if ph == 0 else c * FA + (1 - c) * FB)
+        assert np.allclose(F[:, :, layer, :].reshape(9, -1), want.reshape(9, 1), atol=1e-10)
+
+
+def test_homogeneous_one_iteration_gpu(cb):
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.homogeneous((6, 4, 8))
+    for solver in (0, 1):
+        g = cb.solve(p, solver=solver, fixed_iterations=1)
+        assert np.allclose(g["F"], p["Fbar"].reshape(9, 1), atol=1e-15)
+        assert g["resid"][0] < 1e-14
+
+
+def test_invalid_inputs_are_rejected(cb):
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    base = ms.random_boxels((6, 4, 4), seed=1)
+    bad = []
+    q = dict(base)
+    q["n"] = (7, 4, 4)
+    bad.append(q)
+    q = dict(base)
+    q["n"] = (3, 4, 8)
+    bad.append(q)
+    q = dict(base)
+    q["boxel_c"] = base["boxel_c"].copy()
+    q["boxel_c"][0] = 1.5
+    bad.append(q)
+    q = dict(base)
+    q["boxel_N"] = base["boxel_N"].copy()
+    q["boxel_N"][0] = 0.0
+    bad.append(q)
+    q = dict(base)
+    q["Fbar"] = np.diag([-1.0, 1.0, 1.0]).reshape(9)
+    bad.append(q)
+    q = dict(base)
+    q["mu"] = (0.0, 1.0)
+    bad.append(q)
+    for q in bad:
+        with pytest.raises(cb.ComboError) as e:
+            cb.solve(q, fixed_iterations=1)
+        assert e.value.code == -1
+
+
+def test_full_size_256_sampled(cb, orc):
+    """The 256^3 ball workload in the benchmark's launch configuration: after
+    one refined Newton step, the stress at sampled voxels equals the oracle's
+    per-voxel constitutive law evaluated at the GPU's F; the Green operator at
+    that size is idempotent and keeps HEX8R gradients."""
+    import torch
+
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.spheres_256()
+    s = cb.Solve(p, solver=1, precision=cb.FP32_REFINED, tol=1e-8)
+    s.advance(40)
+    out = s.finish(fields=True)
+    s.close()
+    F, P, a = out["F"], out["P"], out["a"]
+    rng = np.random.default_rng(0)
+    V = 256 ** 3
+    vox = rng.integers(0, V, 3000)
+    vb = {int(v): i for i, v in enumerate(p["boxel_idx"])}
+    mat = (p["mu"][0], p["lam"][0], p["mu"][1], p["lam"][1])
+    for v in vox:
+        ph = int(p["phase"][v])
+        if ph == 2:
+            b = vb[int(v)]
+            Po = orc.laminate(F[:, v], p["boxel_N"][b], p["boxel_c"][b], mat, a0=a[b])["P"]
+        else:
+            Po = orc.neohooke(F[:, v], p["mu"][ph], p["lam"][ph], False)
+        assert np.allclose(P[:, v], Po, rtol=1e-12, atol=1e-12 * max(1.0, np.abs(Po).max()))
+    # Green operator at full size: idempotent, zero mean
+    n = (256, 256, 256)
+    X = torch.randn((9, V), dtype=torch.float64, device="cuda")
+    for prec, tol in ((cb.FP64, 1e-12), (cb.FP32_REFINED, 2e-6)):
+        Y, _ = cb.apply_G(X, n, precision=prec)
+        Z, _ = cb.apply_G(Y, n, precision=prec)
+        err = (Z - Y).abs().max().item() / Y.abs().max().item()
+        assert err < tol
+        assert Y.mean(dim=1).abs().max().item() < tol
