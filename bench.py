@@ -1,0 +1,376 @@
+"""Benchmark: voxel-iterations/s of the ComBo FFT homogenization hot path on GB300.
+
+Workload (default): 256^3 periodic grid of seeded random non-overlapping
+balls of radius 12 voxels at volume fraction 0.25, Neo-Hookean contrast 100,
+uniaxial stretch to Fbar11 = 1.10 in 10 load steps; Newton-CG with FP32
+Krylov iterations, FP64 laminate solves, FP64 residuals and norms
+(``--precision fp64`` runs every operator in FP64).
+
+A step is one operator application of the solve -- one voxel-iteration per
+voxel: tangent (or constitutive law + boxel laminates), forward FFT, Green
+operator, inverse FFT, Krylov update -- with the amortised FP64 residual
+evaluations and laminate solves the solver interleaves.  ``value`` counts
+the operator applications the solve actually ran inside the timed region
+(steps advance in chunks of the solver's device-side loop).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl combo|reference]
+
+N > 1 runs N independent replicas, one per GPU (the path does not shard; no
+data-path collective), under torchrun; rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iterations/s"
+WORKLOAD = "spheres_256"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=24)
+    ap.add_argument("--impl", default="combo", choices=["combo", "reference"])
+    ap.add_argument("--precision", default="refined", choices=["refined", "fp64"])
+    ap.add_argument("--n", type=int, default=256, help="grid side (256 = the benchmark workload)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-json", default=None, help="write the per-kernel table here")
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    if n == 256:
+        return ms.spheres_256()
+    return ms.spheres_256(n=n, vf=0.25 if n >= 192 else 0.1)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, nm in enumerate(names):
+                if len(s) > 5 + k and s[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------- roofline
+def algorithmic_bytes(kernel, p, krylov_bytes):
+    """Bytes the method must move per launch of a kernel class (reads + writes
+    of the fields it touches, each once), for the roofline."""
+    n1, n2, n3 = p["n"]
+    V = n1 * n2 * n3
+    nb = int(p["boxel_idx"].size)
+    nh = n1 // 2 + 1
+    spec_c = 9 * n3 * n2 * nh  # stored half-spectrum complex entries
+    w = krylov_bytes
+    if kernel in ("yfwd_krylov", "zgamma_krylov", "yinv_krylov"):
+        return 2 * spec_c * 2 * w
+    if kernel in ("yfwd_fp64", "zgamma_fp64", "yinv_fp64"):
+        return 2 * spec_c * 16
+    if kernel == "xfwd_tangent":
+        # r, p read; p written; tangent cache (9 + 1 words) at pure voxels; phase byte;
+        # boxel index and 81-entry tangent at boxels; spectrum written
+        return V * (27 * w + 1) + (V - nb) * 10 * w + nb * (4 + 81 * w) + spec_c * 2 * w
+    if kernel == "xinv_cg":
+        # spectrum read; x, r read + written; p read
+        return spec_c * 2 * w + V * 45 * w
+    if kernel == "xfwd_resid_fp64":
+        # F read (FP64), phase, P_box at boxels, tangent cache written, spectrum written
+        return V * (72 + 1) + nb * (4 + 72) + (V - nb) * 10 * w + spec_c * 16
+    if kernel == "xinv_fp64":
+        return spec_c * 16 + V * 18 * w
+    if kernel == "boxel_laminate":
+        return nb * (4 + 72 + 24 + 8 + 24 * 2 + 72 + 81 * w)
+    return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    with the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("csrc_hash") != csrc_hash():
+        return None
+    v = d.get("per_launch_bytes_full_size", {}).get(kernel)
+    return float(v) if v is not None else None
+
+
+def csrc_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2204_13624_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------- CPU baseline
+def cpu_baseline(p, iters=1):
+    """The oracle as it stands (FP64 fixed point, OpenMP over the host cores)
+    on the same workload for a bounded number of operator applications."""
+    import oracle
+
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    r = oracle.solve(dict(p, n_steps=1), dict(solver=0, fixed_iter=iters, nthreads=cores), fields=False)
+    dt = time.perf_counter() - t0
+    V = p["n"][0] * p["n"][1] * p["n"][2]
+    ops = int(r["n_operator"])
+    return {"value": ops * V / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{ops} fixed-point iteration(s) of the {WORKLOAD} workload, first load step, FP64, "
+                      f"including setup and the final residual evaluation ({dt:.1f} s)",
+            "seconds": dt}
+
+
+# ---------------------------------------------------------------- main
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2204_13624_gb300 import build as cbuild
+    from paper_2204_13624_gb300 import combo
+
+    if rank == 0 or world == 1:
+        cbuild.build()
+    if dist:
+        dist.barrier()
+    combo.load()
+    p = workload(args.n)
+    V = p["n"][0] * p["n"][1] * p["n"][2]
+    stream = torch.cuda.current_stream()
+    ctx = combo.Context(local, stream.cuda_stream)
+    prec = combo.FP32_REFINED if args.precision == "refined" else combo.FP64
+    s = combo.Solve(p, ctx=ctx, solver=combo.NEWTON_CG, precision=prec, tol=1e-8)
+    s.advance(max(args.warmup, 3))
+    torch.cuda.synchronize()
+    ops0 = s.finish(fields=False)["n_operator"]
+    s.profile(True)
+    clk = ClockSampler(local)
+    clk.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    done = s.advance(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1)
+    res = s.finish(fields=False)
+    ops = res["n_operator"] - ops0
+    prof = s.profile_read()
+    s.profile(False)
+    s.close()
+    t_max = ms
+    ops_all = ops
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        o = torch.tensor([ops], device="cuda", dtype=torch.float64)
+        dist.all_reduce(o, op=dist.ReduceOp.SUM)
+        ops_all = int(o.item())
+    value = ops_all * V / (t_max / 1e3)
+
+    # per-kernel table and the dominant kernel's roofline
+    kb = 4 if prec == combo.FP32_REFINED else 8
+    peak, peak_kind = peaks()
+    table = {}
+    for k, (kms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        b = algorithmic_bytes(k, p, kb)
+        per = kms / cnt if cnt else 0.0
+        table[k] = {"ms_total": kms, "launches": cnt, "ms_per_launch": per,
+                    "alg_bytes_per_launch": b, "GBps": (b / (per / 1e3) / 1e9) if (b and per > 0) else None}
+    hot = {k: v for k, v in table.items() if v["alg_bytes_per_launch"] and k not in ("boxel_laminate",)}
+    dom = max(hot, key=lambda k: hot[k]["ms_total"]) if hot else None
+    launches = int(sum(v["launches"] for v in table.values()))
+    roof = None
+    if dom:
+        ach = table[dom]["GBps"]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_kind": peak_kind,
+                "traffic": ncu_traffic(dom), "alg_bytes_per_launch": table[dom]["alg_bytes_per_launch"]}
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = run_e2e(p, prec, combo, ctx, V)
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_baseline(p)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / max(ops, 1), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if prec == combo.FP32_REFINED else "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD if args.n == 256 else f"spheres_{args.n}",
+                           "grid": list(p["n"]), "voxels": V, "boxels": int(p["boxel_idx"].size),
+                           "microstructure": "seeded RSA balls r=12 vox, vf 0.25, contrast 100",
+                           "load": "Fbar11 = 1.10 in 10 steps",
+                           "solver": "Newton-CG, tol 1e-8, cg_tol 1e-3",
+                           "precision": "FP32 Krylov + FP64 residual/laminates/norms" if prec else "FP64",
+                           "kspace": "rotated (HEX8R)",
+                           "operator_applications": int(ops), "solve_finished_in_timed_region": bool(done),
+                           "l2": "inputs larger than L2 (each 9-field >= 604 MB)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "kernels": table}
+        if args.profile_json:
+            json.dump(line, open(args.profile_json, "w"), indent=1)
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(p, prec, combo, ctx, V):
+    """The user's call: combo_solve of the full problem from host buffers
+    (inputs copied in, Pbar and the F and P fields copied out), wall clock."""
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = combo.solve(p, ctx=ctx, fields=True, solver=combo.NEWTON_CG, precision=prec, tol=1e-8)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ops = int(r["n_operator"])
+    nb = int(p["boxel_idx"].size)
+    h2d = V + nb * (8 + 24 + 8)
+    d2h = 9 * 8 * len(r["Pbar"]) + 2 * 72 * V + 24 * nb
+    return {"value": ops * V / dt, "unit": METRIC, "h2d_bytes_per_step": h2d / max(ops, 1),
+            "d2h_bytes_per_step": d2h / max(ops, 1), "solve_seconds": dt, "operator_applications": ops,
+            "fp64_residuals": int(r["n_operator_fp64"]), "load_steps": int(r["steps_done"]),
+            "newton_iterations": [int(v) for v in r["iters"]], "cg_iterations": [int(v) for v in r["cg_iters"]],
+            "Pbar_final": [float(v) for v in r["Pbar"][-1]],
+            "note": "one full combo_solve from host buffers; per-step bytes = totals / operator applications"}
+
+
+def run_reference(args, rank, world):
+    """The oracle (FP64 CPU) timed on the host cores.  One oracle iteration of
+    the full 256^3 grid takes ~15 s, so each step is one fixed-point iteration
+    on a 64^3 RVE of the same microstructure family (balls of radius 12
+    voxels, vf 0.25, contrast 100, Fbar11 = 1.10), keeping the whole run
+    within minutes."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    oracle.build()
+    p = ms.random_spheres((64, 64, 64), 12.0, 0.25, ms.SEED_BASE + 1, 100.0, np.diag([1.10, 1.0, 1.0]), 10)
+    V = p["n"][0] * p["n"][1] * p["n"][2]
+    cores = len(os.sched_getaffinity(0))
+    total = args.steps + args.warmup
+    t0 = time.perf_counter()
+    r0 = oracle.solve(dict(p, n_steps=1), dict(solver=0, fixed_iter=args.warmup, nthreads=cores), fields=False)
+    t1 = time.perf_counter()
+    r1 = oracle.solve(dict(p, n_steps=1), dict(solver=0, fixed_iter=total, nthreads=cores), fields=False)
+    t2 = time.perf_counter()
+    # time of `steps` iterations = difference of the two runs (setup cancels)
+    dt = (t2 - t1) - (t1 - t0)
+    ops = int(r1["n_operator"] - r0["n_operator"])
+    value = ops * V / dt if dt > 0 else None
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(ops, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_grid": list(p["n"]),
+                       "solver": "FP64 oracle fixed point (basic scheme)"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+                             "sample": f"{ops} fixed-point iterations on a 64^3 RVE of the {WORKLOAD} family "
+                                       "(r = 12 vox balls, vf 0.25, contrast 100); difference of two runs, "
+                                       "setup cancelled"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -204,6 +204,19 @@ int combo_solve_finish(combo_solve_state* s, combo_result* r);
 void combo_solve_end(combo_solve_state* s);
 
 /*
+ * Per-kernel timing of a solve (instrumentation, no effect on results).
+ *   combo_solve_profile(s, 1) resets the counters and records a CUDA event
+ *   pair around every kernel launch of the solve on its stream; 0 stops.
+ *   combo_solve_profile_read fills, for up to max_classes launch classes,
+ *   names (32 chars each, may be NULL), total milliseconds and launch counts,
+ *   and returns the number of classes.  Launch counts are kept also while
+ *   timing is off.
+ */
+int combo_solve_profile(combo_solve_state* s, int32_t enable);
+int combo_solve_profile_read(combo_solve_state* s, int32_t max_classes, char* names, double* ms,
+                             int64_t* launches);
+
+/*
  * Unit-level entry points (same kernels as the solve).
  *
  * combo_apply_G: Y = G[X] = mu0 Gamma0[X] (Eq. Gamma0 with C0 = mu0 I),

@@ -57,7 +57,8 @@ class ResultS(C.Structure):
 
 EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_options_default",
            "combo_solve_footprint", "combo_solve", "combo_solve_begin", "combo_solve_advance", "combo_solve_finish",
-           "combo_solve_end", "combo_apply_G", "combo_constitutive"]
+           "combo_solve_end", "combo_solve_profile", "combo_solve_profile_read", "combo_apply_G",
+           "combo_constitutive"]
 
 _lib = None
 
@@ -87,6 +88,10 @@ def load(path: str = LIB_PATH):
     L.combo_solve_finish.argtypes = [vp, vp]
     L.combo_solve_finish.restype = C.c_int
     L.combo_solve_end.argtypes = [vp]
+    L.combo_solve_profile.argtypes = [vp, i32]
+    L.combo_solve_profile.restype = C.c_int
+    L.combo_solve_profile_read.argtypes = [vp, i32, vp, vp, vp]
+    L.combo_solve_profile_read.restype = C.c_int
     L.combo_apply_G.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, i32]
     L.combo_apply_G.restype = C.c_int
     L.combo_constitutive.argtypes = [vp, vp, vp, vp, vp, vp, i32]
@@ -266,6 +271,24 @@ class Solve:
         out, r = _result_buffers(self.pb, fields, device_results)
         _check(load().combo_solve_finish(self.h, C.byref(r)))
         return _collect(out, r, self.pb.n_boxels)
+
+    def profile(self, enable: bool = True):
+        """Start (reset) or stop per-kernel CUDA-event timing."""
+        _check(load().combo_solve_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel class: (total ms, launches)}"""
+        n = 32
+        names = C.create_string_buffer(32 * n)
+        ms = np.zeros(n)
+        cnt = np.zeros(n, np.int64)
+        k = _check(load().combo_solve_profile_read(self.h, n, names, _ptr(ms), _ptr(cnt)))
+        raw = names.raw
+        out = {}
+        for i in range(k):
+            nm = raw[32 * i: 32 * i + 32].split(b"\0")[0].decode()
+            out[nm] = (float(ms[i]), int(cnt[i]))
+        return out
 
     def close(self):
         if self.h:

@@ -238,6 +238,100 @@ static GridDims make_dims(const int32_t n[3])
     return g;
 }
 
+// ------------------------------------------------------------------ per-kernel timing
+// Optional CUDA-event timing of every kernel launch class of a solve, on the
+// solve's stream; pairs are read back at the solver's own sync points.
+enum KClass {
+    K_BOXEL = 0,
+    K_XFWD_RESID,
+    K_YFWD_64,
+    K_ZGAMMA_64,
+    K_YINV_64,
+    K_XINV_64,
+    K_XFWD_TANGENT,
+    K_YFWD_C,
+    K_ZGAMMA_C,
+    K_YINV_C,
+    K_XINV_CG,
+    K_FINALIZE,
+    K_UPDATE,
+    K_NCLASS
+};
+static const char* kclass_name[K_NCLASS] = {"boxel_laminate", "xfwd_resid_fp64", "yfwd_fp64", "zgamma_fp64",
+                                             "yinv_fp64", "xinv_fp64", "xfwd_tangent", "yfwd_krylov",
+                                             "zgamma_krylov", "yinv_krylov", "xinv_cg", "finalize", "update_F"};
+
+struct Profiler {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<cudaEvent_t> pool;
+    struct Rec {
+        int k;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> pending;
+    double ms[K_NCLASS] = {0};
+    long long launches[K_NCLASS] = {0};
+    int open_k = -1;
+    cudaEvent_t open_a = nullptr;
+    cudaEvent_t get()
+    {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void begin(int k)
+    {
+        if (!on) {
+            launches[k]++;
+            return;
+        }
+        open_k = k;
+        open_a = get();
+        cudaEventRecord(open_a, st);
+    }
+    void end()
+    {
+        if (!on) return;
+        cudaEvent_t b = get();
+        cudaEventRecord(b, st);
+        pending.push_back({open_k, open_a, b});
+        open_k = -1;
+    }
+    // call after the stream has been synchronised
+    void collect()
+    {
+        for (auto& r : pending) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.k] += t;
+            launches[r.k]++;
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        pending.clear();
+    }
+    void reset()
+    {
+        for (int k = 0; k < K_NCLASS; k++) {
+            ms[k] = 0;
+            launches[k] = 0;
+        }
+    }
+    ~Profiler()
+    {
+        for (auto& r : pending) {
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
 // ------------------------------------------------------------------ operator engine
 // One FFT + Green-operator pipeline in precision T.
 template <typename T> struct Engine {
@@ -282,7 +376,8 @@ template <typename T> struct Engine {
         return a;
     }
     // y forward, z forward + projection + z inverse, y inverse
-    void yz(Scalars* sc, int guard, bool want_norm, double* partial, cudaStream_t st) const
+    void yz(Scalars* sc, int guard, bool want_norm, double* partial, cudaStream_t st, Profiler* pr = nullptr,
+            int kbase = 0) const
     {
         YArgs<T> y{};
         y.g = g;
@@ -292,7 +387,9 @@ template <typename T> struct Engine {
         y.tx = txy;
         y.sc = sc;
         y.guard = guard;
+        if (pr) pr->begin(kbase);
         launch_ypass<T, false>(y, st);
+        if (pr) pr->end();
         ZArgs<T> z{};
         z.g = g;
         z.plan = pz;
@@ -308,8 +405,12 @@ template <typename T> struct Engine {
         z.partial = partial;
         z.sc = sc;
         z.guard = guard;
+        if (pr) pr->begin(kbase + 1);
         launch_zpass<T>(z, st);
+        if (pr) pr->end();
+        if (pr) pr->begin(kbase + 2);
         launch_ypass<T, true>(y, st);
+        if (pr) pr->end();
     }
     int zblocks() const { return ((g.nh + txz - 1) / txz) * g.n2 * 3; }
     int xblocks() const { return (g.n2 * g.n3 + lines - 1) / lines; }
@@ -608,6 +709,7 @@ struct SolveBase {
     virtual ~SolveBase() {}
     virtual int advance(int64_t max_ops) = 0;
     virtual int finish(combo_result* r) = 0;
+    virtual Profiler& profiler() = 0;
 };
 
 struct combo_solve_state {
@@ -635,6 +737,7 @@ template <typename Tc> struct Solve : SolveBase {
     double* d_part = nullptr;
     Scalars* d_sc = nullptr;
     double mu0 = 0.0;
+    Profiler prof;
     // host state machine
     enum { ST_STEP, ST_RESID, ST_CG, ST_UPDATE, ST_FP, ST_DONE } state = ST_STEP;
     int step = 0;  // completed load steps
@@ -674,6 +777,7 @@ template <typename Tc> struct Solve : SolveBase {
     {
         ctx = c;
         st = c->stream;
+        prof.st = st;
         opt = o;
         hp = std::move(h);
         g = make_dims(hp.n);
@@ -752,7 +856,9 @@ template <typename Tc> struct Solve : SolveBase {
         a.max_iter = opt.nr_max_iter;
         a.sc = d_sc;
         a.guard = guard;
+        prof.begin(K_BOXEL);
         launch_boxel<Tc>(a, st);
+        prof.end();
     }
 
     // FP64 residual operator: G[P(F)]; mode: XI_FIXEDPOINT (update F) or XI_RHS (r = -G[P], x = 0)
@@ -771,10 +877,14 @@ template <typename Tc> struct Solve : SolveBase {
         xf.tc = (xi_mode == XI_RHS) ? d_tc : nullptr;
         xf.nb = nb;
         xf.sc = d_sc;
+        prof.begin(K_XFWD_RESID);
         launch_xfwd<double, Tc>(xf, guard, st);
-        e64.yz(d_sc, guard, true, d_part, st);
+        prof.end();
+        e64.yz(d_sc, guard, true, d_part, st, &prof, K_YFWD_64);
+        prof.begin(K_FINALIZE);
         k_fin_resid<<<1, 256, 0, st>>>(d_sc, d_part, e64.zblocks(), (double)g.V, opt.tol, opt.fixed_iterations,
                                        opt.max_iter, xi_mode == XI_FIXEDPOINT ? 1 : 0);
+        prof.end();
         auto xi = e64.template xi<Tc>();
         xi.mode = xi_mode;
         xi.inv_mu0 = 1.0 / mu0;
@@ -783,9 +893,14 @@ template <typename Tc> struct Solve : SolveBase {
         xi.r = d_r;
         xi.partial = d_part;
         xi.sc = d_sc;
+        prof.begin(K_XINV_64);
         launch_xinv<double, Tc>(xi, guard, st);
-        if (xi_mode == XI_RHS)
+        prof.end();
+        if (xi_mode == XI_RHS) {
+            prof.begin(K_FINALIZE);
             k_fin_rhs<<<1, 256, 0, st>>>(d_sc, d_part, e64.xblocks(), opt.cg_fixed_iterations, opt.cg_max_iter);
+            prof.end();
+        }
     }
 
     // one CG iteration in precision Tc, guarded by cg_done
@@ -806,9 +921,13 @@ template <typename Tc> struct Solve : SolveBase {
         xf.nb = std::max<int64_t>(nb, 1);
         xf.partial = d_part;
         xf.sc = d_sc;
+        prof.begin(K_XFWD_TANGENT);
         launch_xfwd<Tc, Tc>(xf, 1, st);
+        prof.end();
+        prof.begin(K_FINALIZE);
         k_fin_alpha<<<1, 256, 0, st>>>(d_sc, d_part, ec.xblocks());
-        ec.yz(d_sc, 1, false, nullptr, st);
+        prof.end();
+        ec.yz(d_sc, 1, false, nullptr, st, &prof, K_YFWD_C);
         auto xi = ec.template xi<Tc>();
         xi.mode = XI_CG;
         xi.x = d_x;
@@ -816,15 +935,20 @@ template <typename Tc> struct Solve : SolveBase {
         xi.p = d_p;
         xi.partial = d_part;
         xi.sc = d_sc;
+        prof.begin(K_XINV_CG);
         launch_xinv<Tc, Tc>(xi, 1, st);
+        prof.end();
+        prof.begin(K_FINALIZE);
         k_fin_beta<<<1, 256, 0, st>>>(d_sc, d_part, ec.xblocks(), opt.cg_tol, opt.cg_max_iter,
                                       opt.cg_fixed_iterations);
+        prof.end();
     }
 
     int read_scalars(Scalars& s)
     {
         CK(cudaMemcpyAsync(&s, d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        prof.collect();
         return COMBO_OK;
     }
 
@@ -845,7 +969,9 @@ template <typename Tc> struct Solve : SolveBase {
             d.v[c] = Fn[c] - Fprev[c];
         }
         std::memcpy(Fprev, Fn, sizeof(Fn));
+        prof.begin(K_UPDATE);
         k_add_uniform<<<grid_for(9 * g.V), 256, 0, st>>>(d_F, g.V, d);
+        prof.end();
         CK(cudaGetLastError());
         outer = 0;
         cg_step_total = 0;
@@ -935,7 +1061,9 @@ template <typename Tc> struct Solve : SolveBase {
                     bool ok = false;
                     for (int h = 0; h <= 10; h++) {
                         if ((rc = set_flag(offsetof(Scalars, admissible), 1))) return error = rc;
+                        prof.begin(K_UPDATE);
                         k_update_F<Tc><<<grid_for(g.V), 256, 0, st>>>(d_F, d_x, d, g.V, d_sc);
+                        prof.end();
                         if ((rc = read_scalars(s))) return error = rc;
                         if (s.admissible) {
                             ok = true;
@@ -953,6 +1081,8 @@ template <typename Tc> struct Solve : SolveBase {
             }
         }
     }
+
+    Profiler& profiler() override { return prof; }
 
     int finish(combo_result* r) override
     {
@@ -1055,6 +1185,35 @@ extern "C" int combo_solve_finish(combo_solve_state* s, combo_result* r)
 {
     if (!s) return fail(COMBO_E_INVALID_ARG, "null solve");
     return s->impl->finish(r);
+}
+
+extern "C" int combo_solve_profile(combo_solve_state* s, int32_t enable)
+{
+    if (!s) return fail(COMBO_E_INVALID_ARG, "null solve");
+    Profiler& p = s->impl->profiler();
+    p.collect();
+    p.reset();
+    p.on = enable != 0;
+    return COMBO_OK;
+}
+
+extern "C" int combo_solve_profile_read(combo_solve_state* s, int32_t max_classes, char* names, double* ms,
+                                        int64_t* launches)
+{
+    if (!s) return fail(COMBO_E_INVALID_ARG, "null solve");
+    Profiler& p = s->impl->profiler();
+    CK(cudaStreamSynchronize(p.st));
+    p.collect();
+    const int n = std::min<int>(max_classes, K_NCLASS);
+    for (int k = 0; k < n; k++) {
+        if (names) {
+            std::strncpy(names + 32 * k, kclass_name[k], 31);
+            names[32 * k + 31] = 0;
+        }
+        if (ms) ms[k] = p.ms[k];
+        if (launches) launches[k] = p.launches[k];
+    }
+    return K_NCLASS;
 }
 
 extern "C" void combo_solve_end(combo_solve_state* s)
