@@ -57,7 +57,7 @@ def workload(n):
 
     if n == 256:
         return ms.spheres_256()
-    return ms.spheres_256(n=n, vf=0.25 if n >= 192 else 0.1)
+    return ms.spheres_256(n=n, vf=0.2 if n >= 128 else 0.1)
 
 
 # ---------------------------------------------------------------- clocks
