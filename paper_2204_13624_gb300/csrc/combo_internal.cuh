@@ -57,6 +57,7 @@ struct Scalars {
     int32_t status;  // first error code (COMBO_E_*) raised by a kernel
     unsigned long long nr_iters, n_backproj, n_lam;
     unsigned long long n_operator, n_operator64;
+    unsigned int ticket[4];  // last-block counters of fused reductions
 };
 
 // ---------------------------------------------------------------- FFT core
@@ -196,6 +197,78 @@ __device__ __forceinline__ void raise_status(Scalars* sc, int code)
     atomicCAS(&sc->status, 0, code);
 }
 
+// Deterministic sum of n partials by one block: fixed strided accumulation
+// (4 independent chains) then a fixed tree.  red: >= blockDim.x doubles.
+// All threads call it; every thread gets the total.
+__device__ __forceinline__ double sum_partials_fixed(const double* p, int n, double* red)
+{
+    const int bd = blockDim.x, tid = threadIdx.x;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int i = tid;
+    for (; i + 3 * bd < n; i += 4 * bd) {
+        a0 += __ldcg(p + i);
+        a1 += __ldcg(p + i + bd);
+        a2 += __ldcg(p + i + 2 * bd);
+        a3 += __ldcg(p + i + 3 * bd);
+    }
+    for (; i < n; i += bd) a0 += __ldcg(p + i);
+    __syncthreads();
+    red[tid] = (a0 + a1) + (a2 + a3);
+    __syncthreads();
+    for (int o = bd / 2; o > 0; o >>= 1) {
+        if (tid < o) red[tid] += red[tid + o];
+        __syncthreads();
+    }
+    const double s = red[0];
+    __syncthreads();
+    return s;
+}
+
+// True in every thread of the block that finishes last (after its partial
+// was written by thread 0).  ticket is reset by that block.
+__device__ __forceinline__ bool last_block(unsigned int* ticket, int* flag_smem)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int t = atomicAdd(ticket, 1u);
+        const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
+        *flag_smem = (t == nblocks - 1) ? 1 : 0;
+        if (*flag_smem) *ticket = 0u;
+    }
+    __syncthreads();
+    const bool last = *flag_smem != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+// CG scalars (called by one thread).  Loss of positive curvature stops CG
+// with the current iterate.
+__device__ __forceinline__ void cg_alpha(Scalars* sc, double pAp)
+{
+    sc->pAp = pAp;
+    if (!(pAp > 0.0)) {
+        sc->cg_done = 1;
+        return;
+    }
+    sc->alpha = sc->rr / pAp;
+}
+
+__device__ __forceinline__ void cg_beta(Scalars* sc, double rr_new, double cg_tol, int cg_max, int cg_fixed)
+{
+    sc->beta = rr_new / sc->rr;
+    sc->rr = rr_new;
+    const int j = sc->cg_iter + 1;
+    sc->cg_iter = j;
+    sc->n_operator += 1;
+    bool stop;
+    if (cg_fixed > 0)
+        stop = j >= cg_fixed;
+    else
+        stop = (sqrt(rr_new) <= cg_tol * sqrt(sc->rr0)) || j >= cg_max;
+    if (stop || rr_new == 0.0) sc->cg_done = 1;
+}
+
 // ---------------------------------------------------------------- launchers
 enum XfwdMode { XF_RESID = 0, XF_TANGENT = 1 };
 enum XinvMode { XI_FIXEDPOINT = 0, XI_RHS = 1, XI_CG = 2, XI_PLAIN = 3 };
@@ -224,6 +297,7 @@ template <typename T, typename Tc> struct XfwdArgs {
     const double* X;
     double* partial;     // [gridDim.x] pAp partials
     Scalars* sc;
+    int fuse;            // last block turns the pAp partials into alpha
 };
 
 template <typename T, typename Tc> struct XinvArgs {
@@ -242,6 +316,9 @@ template <typename T, typename Tc> struct XinvArgs {
     double* Y;       // XI_PLAIN: real output [9][V]
     double* partial;
     Scalars* sc;
+    int fuse;        // last block turns the (r, r) partials into beta / stop (XI_CG)
+    double cg_tol;
+    int cg_max, cg_fixed;
 };
 
 template <typename T> struct YArgs {
@@ -275,6 +352,8 @@ template <typename T, bool INV> void launch_ypass(const YArgs<T>& a, cudaStream_
 template <typename T> void launch_zpass(const ZArgs<T>& a, cudaStream_t st);
 size_t xpass_smem(const GridDims& g, int lines, size_t cxbytes);
 int xpass_lines(const GridDims& g, size_t cxbytes);
+int ypass_tx(int n, size_t cxbytes);  // columns per y-pass block (must match the launcher)
+int zpass_tx(int n, size_t cxbytes);  // columns per z-pass block (sets the partial count)
 
 // boxel laminate Newton solve
 template <typename Tc> struct BoxelArgs {

@@ -12,16 +12,19 @@
 //
 // Data layout: real fields [9][n3][n2][n1] (x fastest); the half spectrum is
 // [9][n3][n2][nhp] complex, nhp >= n1/2 + 1.  Every pass reads and writes
-// each element once; tiles are staged in shared memory and transformed with a
-// mixed-radix Stockham FFT (combo_internal.cuh).
+// each element once.  Power-of-two line lengths use the compile-time plans
+// of fft_fast.cuh (y/z passes go global -> registers -> one shared-memory
+// exchange -> global); other lengths use the runtime mixed-radix Stockham of
+// combo_internal.cuh.
 #include "combo_internal.cuh"
+#include "fft_fast.cuh"
 #include "../../include/combo.h"
 
 namespace combo {
 
 size_t xpass_smem(const GridDims& g, int lines, size_t cxbytes)
 {
-    return 2 * (size_t)9 * lines * (g.M + 1) * cxbytes + 64 * sizeof(double);
+    return 2 * (size_t)9 * lines * (g.M + 1) * cxbytes + 256 * sizeof(double) + 16;
 }
 
 int xpass_lines(const GridDims& g, size_t cxbytes)
@@ -34,8 +37,18 @@ int xpass_lines(const GridDims& g, size_t cxbytes)
     return lines;
 }
 
+// x-pass FFT of the nl lines held in shared memory: compile-time plan when MF > 0
+template <typename T, int MF, bool INV>
+__device__ __forceinline__ cx<T>* xpass_fft(cx<T>* b0, cx<T>* b1, const Plan& plan, int nl, int ls, const cx<T>* tw)
+{
+    if constexpr (MF > 0)
+        return fft_lines_fast<T, MF, INV>(b0, b1, nl, ls, tw);
+    else
+        return fft_lines<T, INV>(b0, b1, plan, nl, ls, 1, tw);
+}
+
 // ------------------------------------------------------------- x forward
-template <typename T, typename Tc>
+template <typename T, typename Tc, int MF>
 __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
 {
     if (guard == 1 && a.sc->cg_done) return;
@@ -47,6 +60,7 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
     cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
     cx<T>* buf1 = buf0 + (size_t)9 * LB * ls;
     double* red = reinterpret_cast<double*>(buf1 + (size_t)9 * LB * ls);
+    int* flag = reinterpret_cast<int*>(red + 256);
     T* rb = reinterpret_cast<T*>(buf0);
     const int L0 = blockIdx.x * LB;
     const int nlines = g.n2 * g.n3;
@@ -86,7 +100,7 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
                     for (int c = 0; c < 9; c++) out[c] = (T)0;
                 } else {
                     const double iJ = 1.0 / J;
-                    // G = F^{-1}; G^T stored row-major as Gt[3 i + J] = G_Ji
+                    // G = F^{-1} (row-major); P = mu F + (lam ln J - mu) G^T
                     double G[9];
                     G[0] = c0 * iJ;
                     G[1] = (F[2] * F[7] - F[1] * F[8]) * iJ;
@@ -168,7 +182,7 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
     __syncthreads();
 
     const int nl = 9 * LB;
-    cx<T>* Z = fft_lines<T, false>(buf0, buf1, a.plan, nl, ls, 1, a.tw);
+    cx<T>* Z = xpass_fft<T, MF, false>(buf0, buf1, a.plan, nl, ls, a.tw);
 
     // Hermitian split of the packed transform: X[k] = Ze + W^k Zo, k = 0..M
     const int M = g.M;
@@ -188,7 +202,6 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
         }
         const int k2 = M - k;
         const cx<T> A = z[k], B = z[k2];
-        // X[k]
         {
             const cx<T> Bc = c_conj(B);
             const cx<T> Ze = c_scale(c_add(A, Bc), (T)0.5);
@@ -207,11 +220,15 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
     if (a.mode == XF_TANGENT && a.partial) {
         const double s = block_sum(acc, red);
         if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
+        if (a.fuse && last_block(&a.sc->ticket[0], flag)) {
+            const double tot = sum_partials_fixed(a.partial, gridDim.x, red);
+            if (threadIdx.x == 0) cg_alpha(a.sc, tot);
+        }
     }
 }
 
 // ------------------------------------------------------------- x inverse
-template <typename T, typename Tc>
+template <typename T, typename Tc, int MF>
 __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
 {
     if (guard == 1 && a.sc->cg_done) return;
@@ -224,6 +241,7 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
     cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
     cx<T>* buf1 = buf0 + (size_t)9 * LB * ls;
     double* red = reinterpret_cast<double*>(buf1 + (size_t)9 * LB * ls);
+    int* flag = reinterpret_cast<int*>(red + 256);
     const int L0 = blockIdx.x * LB;
     const int nlines = g.n2 * g.n3;
     const int nl = 9 * LB;
@@ -246,7 +264,7 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
         buf1[(size_t)q * ls + k] = cx<T>{Ze.x - Zo.y, Ze.y + Zo.x};
     }
     __syncthreads();
-    cx<T>* Zr = fft_lines<T, true>(buf1, buf0, a.plan, nl, ls, 1, a.tw);
+    cx<T>* Zr = xpass_fft<T, MF, true>(buf1, buf0, a.plan, nl, ls, a.tw);
     const T* rb = reinterpret_cast<const T*>(Zr);
 
     double acc = 0.0;
@@ -281,10 +299,14 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
     if ((a.mode == XI_RHS || a.mode == XI_CG) && a.partial) {
         const double s = block_sum(acc, red);
         if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
+        if (a.mode == XI_CG && a.fuse && last_block(&a.sc->ticket[1], flag)) {
+            const double tot = sum_partials_fixed(a.partial, gridDim.x, red);
+            if (threadIdx.x == 0) cg_beta(a.sc, tot, a.cg_tol, a.cg_max, a.cg_fixed);
+        }
     }
 }
 
-// ------------------------------------------------------------- y pass
+// ------------------------------------------------------------- y pass (generic)
 template <typename T, bool INV>
 __global__ void __launch_bounds__(256) k_ypass(YArgs<T> a)
 {
@@ -311,7 +333,31 @@ __global__ void __launch_bounds__(256) k_ypass(YArgs<T> a)
     }
 }
 
-// ------------------------------------------------------------- z pass + Gamma
+// ------------------------------------------------------------- y pass (power of two)
+// Block: TX columns x TPL threads; column fastest in the thread index so that
+// every global access of a warp covers TX consecutive complex values.
+template <typename T, int N, int TX, bool INV>
+__global__ void __launch_bounds__(TX * FastPlan<N>::TPL) k_ypass_fast(YArgs<T> a)
+{
+    if (a.guard == 1 && a.sc->cg_done) return;
+    if (a.guard == 2 && a.sc->outer_done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* ex = reinterpret_cast<cx<T>*>(smem_raw);
+    const GridDims g = a.g;
+    const int line = threadIdx.x % TX, tau = threadIdx.x / TX;
+    const int x0 = blockIdx.x * TX;
+    const bool valid = x0 + line < g.nh;
+    cx<T>* base = a.spec + blockIdx.z * g.Vs + (int64_t)blockIdx.y * N * g.nhp + x0 + line;
+    const int64_t st = g.nhp;
+    fft_fast<T, N, INV>([&](int e) { return valid ? base[e * st] : cx<T>{(T)0, (T)0}; },
+                        [&](int e, cx<T> v) {
+                            if (valid) base[e * st] = v;
+                        },
+                        [&](int e) { return ex[e * TX + line]; }, [&](int e, cx<T> v) { ex[e * TX + line] = v; }, tau,
+                        a.tw);
+}
+
+// ------------------------------------------------------------- z pass + Gamma (generic)
 template <typename T>
 __global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
 {
@@ -391,54 +437,220 @@ __global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
     }
 }
 
-// ------------------------------------------------------------- launchers
-template <typename T, typename Tc> void launch_xfwd(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st)
+// ------------------------------------------------------------- z pass + Gamma (power of two)
+// Block: TX columns x TPL threads.  Each of the 3 components of tensor row i
+// is transformed forward into the park tile [3][N][TX]; the last forward
+// stage leaves every thread holding whole frequency triples, so the
+// projection runs in place, and the inverse starts from the same positions.
+template <typename T, int N, int TX>
+__global__ void __launch_bounds__(TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<T> a)
+{
+    if (a.guard == 1 && a.sc->cg_done) return;
+    if (a.guard == 2 && a.sc->outer_done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TPL = FastPlan<N>::TPL;
+    cx<T>* park = reinterpret_cast<cx<T>*>(smem_raw);  // [3][N][TX]
+    cx<T>* ex = park + 3 * N * TX;                      // [N][TX]
+    double* red = reinterpret_cast<double*>(ex + N * TX);
+    const GridDims g = a.g;
+    const int line = threadIdx.x % TX, tau = threadIdx.x / TX;
+    const int x0 = blockIdx.x * TX;
+    const int xi1 = x0 + line;
+    const bool valid = xi1 < g.nh;
+    const int y = blockIdx.y;
+    const int row = blockIdx.z;
+    const int64_t zst = (int64_t)g.n2 * g.nhp;
+    cx<T>* base = a.spec + (int64_t)(3 * row) * g.Vs + (int64_t)y * g.nhp + x0 + line;
+    auto lx = [&](int e) { return ex[e * TX + line]; };
+    auto sx = [&](int e, cx<T> v) { ex[e * TX + line] = v; };
+
+#pragma unroll 1
+    for (int c = 0; c < 3; c++) {
+        cx<T>* bc = base + c * g.Vs;
+        cx<T>* pc = park + c * N * TX + line;
+        fft_fast<T, N, false>([&](int e) { return valid ? bc[e * zst] : cx<T>{(T)0, (T)0}; },
+                              [&](int e, cx<T> v) { pc[e * TX] = v; }, lx, sx, tau, a.tw);
+        __syncthreads();
+    }
+
+    // projection on this thread's frequencies xi3 = j + t (N / R_last)
+    using LS = LastStage<N>;
+    double acc = 0.0;
+    const T ay = a.sa[1][y], by = a.sb[1][y];
+    const T ax = valid ? a.sa[0][xi1] : (T)0, bx = valid ? a.sb[0][xi1] : (T)0;
+    const double wgt = (xi1 == 0 || xi1 == g.M) ? 1.0 : 2.0;
+#pragma unroll
+    for (int u = 0; u < LS::U; u++) {
+#pragma unroll
+        for (int t = 0; t < LS::R; t++) {
+            const int z = tau + TPL * u + t * LS::B;
+            cx<T>* p = park + z * TX + line;
+            const cx<T> X0 = p[0], X1 = p[N * TX], X2 = p[2 * N * TX];
+            const T az = a.sa[2][z], bz = a.sb[2][z];
+            const T k0 = ax * by * bz, k1 = ay * bx * bz, k2 = az * bx * by;
+            const T kk = k0 * k0 + k1 * k1 + k2 * k2;
+            if (a.want_norm && xi1 == 0 && y == 0 && z == 0) {
+                a.sc->dc[3 * row + 0] = (double)X0.x;
+                a.sc->dc[3 * row + 1] = (double)X1.x;
+                a.sc->dc[3 * row + 2] = (double)X2.x;
+            }
+            cx<T> o0{(T)0, (T)0}, o1{(T)0, (T)0}, o2{(T)0, (T)0};
+            if (valid && kk > (T)0) {
+                const T sr = (k0 * X0.x + k1 * X1.x + k2 * X2.x) / kk;
+                const T si = (k0 * X0.y + k1 * X1.y + k2 * X2.y) / kk;
+                o0 = cx<T>{k0 * sr, k0 * si};
+                o1 = cx<T>{k1 * sr, k1 * si};
+                o2 = cx<T>{k2 * sr, k2 * si};
+                if (a.want_norm)
+                    acc += wgt * ((double)o0.x * o0.x + (double)o0.y * o0.y + (double)o1.x * o1.x +
+                                  (double)o1.y * o1.y + (double)o2.x * o2.x + (double)o2.y * o2.y);
+            }
+            p[0] = c_scale(o0, a.scale);
+            p[N * TX] = c_scale(o1, a.scale);
+            p[2 * N * TX] = c_scale(o2, a.scale);
+        }
+    }
+
+#pragma unroll 1
+    for (int c = 0; c < 3; c++) {
+        cx<T>* bc = base + c * g.Vs;
+        cx<T>* pc = park + c * N * TX + line;
+        fft_fast<T, N, true>([&](int e) { return pc[e * TX]; },
+                             [&](int e, cx<T> v) {
+                                 if (valid) bc[e * zst] = v;
+                             },
+                             lx, sx, tau, a.tw);
+        __syncthreads();
+    }
+    if (a.want_norm && a.partial) {
+        const double s = block_sum(acc, red);
+        if (threadIdx.x == 0) a.partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+    }
+}
+
+// ------------------------------------------------------------- launch configuration
+template <typename T> int ytx_fast(int n) { return sizeof(T) == 4 ? 16 : 8; }
+template <typename T> int ztx_fast(int n)
+{
+    if (n == 512) return sizeof(T) == 4 ? 4 : 2;
+    return sizeof(T) == 4 ? 8 : 4;
+}
+
+int zpass_tx(int n, size_t cxbytes)
+{
+    if (fast_size(n)) return cxbytes == 8 ? ztx_fast<float>(n) : ztx_fast<double>(n);
+    int tx = 16;
+    while (tx > 1 && 2 * (size_t)3 * n * tx * cxbytes > 96 * 1024) tx /= 2;
+    return tx;
+}
+
+int ypass_tx(int n, size_t cxbytes)
+{
+    if (fast_size(n)) return cxbytes == 8 ? ytx_fast<float>(n) : ytx_fast<double>(n);
+    int tx = 16;
+    while (tx > 1 && 2 * (size_t)n * tx * cxbytes > 64 * 1024) tx /= 2;
+    return tx;
+}
+
+template <typename K> static void allow_smem(K kernel, bool& done)
+{
+    if (!done) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        done = true;
+    }
+}
+
+template <typename T, typename Tc, int MF> static void xfwd_launch(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st)
 {
     const int nlines = a.g.n2 * a.g.n3;
     const int grid = (nlines + a.lines_per_block - 1) / a.lines_per_block;
     const size_t sm = xpass_smem(a.g, a.lines_per_block, sizeof(cx<T>));
     static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_xfwd<T, Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
+    allow_smem(k_xfwd<T, Tc, MF>, attr);
+    k_xfwd<T, Tc, MF><<<grid, 256, sm, st>>>(a, guard);
+}
+
+template <typename T, typename Tc> void launch_xfwd(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st)
+{
+    switch (a.g.M) {
+        case 32: xfwd_launch<T, Tc, 32>(a, guard, st); break;
+        case 64: xfwd_launch<T, Tc, 64>(a, guard, st); break;
+        case 128: xfwd_launch<T, Tc, 128>(a, guard, st); break;
+        case 256: xfwd_launch<T, Tc, 256>(a, guard, st); break;
+        default: xfwd_launch<T, Tc, 0>(a, guard, st); break;
     }
-    k_xfwd<T, Tc><<<grid, 256, sm, st>>>(a, guard);
+}
+
+template <typename T, typename Tc, int MF> static void xinv_launch(const XinvArgs<T, Tc>& a, int guard, cudaStream_t st)
+{
+    const int nlines = a.g.n2 * a.g.n3;
+    const int grid = (nlines + a.lines_per_block - 1) / a.lines_per_block;
+    const size_t sm = xpass_smem(a.g, a.lines_per_block, sizeof(cx<T>));
+    static bool attr = false;
+    allow_smem(k_xinv<T, Tc, MF>, attr);
+    k_xinv<T, Tc, MF><<<grid, 256, sm, st>>>(a, guard);
 }
 
 template <typename T, typename Tc> void launch_xinv(const XinvArgs<T, Tc>& a, int guard, cudaStream_t st)
 {
-    const int nlines = a.g.n2 * a.g.n3;
-    const int grid = (nlines + a.lines_per_block - 1) / a.lines_per_block;
-    const size_t sm = xpass_smem(a.g, a.lines_per_block, sizeof(cx<T>));
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_xinv<T, Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
+    switch (a.g.M) {
+        case 32: xinv_launch<T, Tc, 32>(a, guard, st); break;
+        case 64: xinv_launch<T, Tc, 64>(a, guard, st); break;
+        case 128: xinv_launch<T, Tc, 128>(a, guard, st); break;
+        case 256: xinv_launch<T, Tc, 256>(a, guard, st); break;
+        default: xinv_launch<T, Tc, 0>(a, guard, st); break;
     }
-    k_xinv<T, Tc><<<grid, 256, sm, st>>>(a, guard);
+}
+
+template <typename T, int N, bool INV> static void ypass_fast_launch(const YArgs<T>& a, cudaStream_t st)
+{
+    constexpr int TX = sizeof(T) == 4 ? 16 : 8;
+    dim3 grid((a.g.nh + TX - 1) / TX, a.g.n3, 9);
+    const size_t sm = (size_t)N * TX * sizeof(cx<T>);
+    static bool attr = false;
+    allow_smem(k_ypass_fast<T, N, TX, INV>, attr);
+    k_ypass_fast<T, N, TX, INV><<<grid, TX * FastPlan<N>::TPL, sm, st>>>(a);
 }
 
 template <typename T, bool INV> void launch_ypass(const YArgs<T>& a, cudaStream_t st)
 {
+    switch (a.g.n2) {
+        case 64: ypass_fast_launch<T, 64, INV>(a, st); return;
+        case 128: ypass_fast_launch<T, 128, INV>(a, st); return;
+        case 256: ypass_fast_launch<T, 256, INV>(a, st); return;
+        case 512: ypass_fast_launch<T, 512, INV>(a, st); return;
+        default: break;
+    }
     dim3 grid((a.g.nh + a.tx - 1) / a.tx, a.g.n3, 9);
     const size_t sm = 2 * (size_t)a.g.n2 * a.tx * sizeof(cx<T>);
     static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_ypass<T, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    allow_smem(k_ypass<T, INV>, attr);
     k_ypass<T, INV><<<grid, 256, sm, st>>>(a);
+}
+
+template <typename T, int N> static void zpass_fast_launch(const ZArgs<T>& a, cudaStream_t st)
+{
+    constexpr int TX = (N == 512) ? (sizeof(T) == 4 ? 4 : 2) : (sizeof(T) == 4 ? 8 : 4);
+    dim3 grid((a.g.nh + TX - 1) / TX, a.g.n2, 3);
+    const size_t sm = (size_t)4 * N * TX * sizeof(cx<T>) + 64 * sizeof(double);
+    static bool attr = false;
+    allow_smem(k_zpass_fast<T, N, TX>, attr);
+    k_zpass_fast<T, N, TX><<<grid, TX * FastPlan<N>::TPL, sm, st>>>(a);
 }
 
 template <typename T> void launch_zpass(const ZArgs<T>& a, cudaStream_t st)
 {
+    switch (a.g.n3) {
+        case 64: zpass_fast_launch<T, 64>(a, st); return;
+        case 128: zpass_fast_launch<T, 128>(a, st); return;
+        case 256: zpass_fast_launch<T, 256>(a, st); return;
+        case 512: zpass_fast_launch<T, 512>(a, st); return;
+        default: break;
+    }
     dim3 grid((a.g.nh + a.tx - 1) / a.tx, a.g.n2, 3);
     const size_t sm = 2 * (size_t)a.g.n3 * 3 * a.tx * sizeof(cx<T>) + 64 * sizeof(double);
     static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_zpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    allow_smem(k_zpass<T>, attr);
     k_zpass<T><<<grid, 256, sm, st>>>(a);
 }
 

@@ -347,8 +347,8 @@ template <typename T> struct Engine {
         py = make_plan(g.n2);
         pz = make_plan(g.n3);
         lines = xpass_lines(g, sizeof(cx<T>));
-        txy = tx_for(g.n2, sizeof(cx<T>), 64 * 1024, 1);
-        txz = tx_for(g.n3, sizeof(cx<T>), 96 * 1024, 3);
+        txy = ypass_tx(g.n2, sizeof(cx<T>));
+        txz = zpass_tx(g.n3, sizeof(cx<T>));
         return make_tables<T>(tab, g, l, kspace);
     }
     void release() { free_tables<T>(tab); }
@@ -442,19 +442,7 @@ __global__ void k_vox2box(int32_t* map, const int32_t* bidx, int64_t nb)
 }
 
 // deterministic fixed-order sum of n partials by one block
-__device__ double sum_partials(const double* p, int n, double* red)
-{
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
-    // fixed tree over the block (same order every launch)
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    return red[0];
-}
+__device__ double sum_partials(const double* p, int n, double* red) { return sum_partials_fixed(p, n, red); }
 
 // residual of the current evaluation; fixed-point bookkeeping (mode 1)
 __global__ void k_fin_resid(Scalars* sc, const double* part, int n, double V, double tol, int fixed, int max_iter,
@@ -504,39 +492,6 @@ __global__ void k_fin_rhs(Scalars* sc, const double* part, int n, int cg_fixed, 
     sc->beta = 0.0;
     const bool stop = (cg_fixed <= 0) && (cg_max <= 0);
     sc->cg_done = (s == 0.0 || stop) ? 1 : 0;
-}
-
-__global__ void k_fin_alpha(Scalars* sc, const double* part, int n)
-{
-    __shared__ double red[256];
-    if (sc->cg_done) return;
-    const double s = sum_partials(part, n, red);
-    if (threadIdx.x != 0) return;
-    sc->pAp = s;
-    if (!(s > 0.0)) {
-        sc->cg_done = 1;  // loss of positive curvature: stop with the current iterate
-        return;
-    }
-    sc->alpha = sc->rr / s;
-}
-
-__global__ void k_fin_beta(Scalars* sc, const double* part, int n, double cg_tol, int cg_max, int cg_fixed)
-{
-    __shared__ double red[256];
-    if (sc->cg_done) return;
-    const double s = sum_partials(part, n, red);
-    if (threadIdx.x != 0) return;
-    sc->beta = s / sc->rr;
-    sc->rr = s;
-    const int j = sc->cg_iter + 1;
-    sc->cg_iter = j;
-    sc->n_operator += 1;
-    bool stop;
-    if (cg_fixed > 0)
-        stop = j >= cg_fixed;
-    else
-        stop = (sqrt(s) <= cg_tol * sqrt(sc->rr0)) || j >= cg_max;
-    if (stop || s == 0.0) sc->cg_done = 1;
 }
 
 // F += d * x, then admissibility (det F > 0) of every voxel
@@ -921,11 +876,9 @@ template <typename Tc> struct Solve : SolveBase {
         xf.nb = std::max<int64_t>(nb, 1);
         xf.partial = d_part;
         xf.sc = d_sc;
+        xf.fuse = 1;  // the last block computes alpha
         prof.begin(K_XFWD_TANGENT);
         launch_xfwd<Tc, Tc>(xf, 1, st);
-        prof.end();
-        prof.begin(K_FINALIZE);
-        k_fin_alpha<<<1, 256, 0, st>>>(d_sc, d_part, ec.xblocks());
         prof.end();
         ec.yz(d_sc, 1, false, nullptr, st, &prof, K_YFWD_C);
         auto xi = ec.template xi<Tc>();
@@ -935,12 +888,12 @@ template <typename Tc> struct Solve : SolveBase {
         xi.p = d_p;
         xi.partial = d_part;
         xi.sc = d_sc;
+        xi.fuse = 1;  // the last block computes beta and the stopping test
+        xi.cg_tol = opt.cg_tol;
+        xi.cg_max = opt.cg_max_iter;
+        xi.cg_fixed = opt.cg_fixed_iterations;
         prof.begin(K_XINV_CG);
         launch_xinv<Tc, Tc>(xi, 1, st);
-        prof.end();
-        prof.begin(K_FINALIZE);
-        k_fin_beta<<<1, 256, 0, st>>>(d_sc, d_part, ec.xblocks(), opt.cg_tol, opt.cg_max_iter,
-                                      opt.cg_fixed_iterations);
         prof.end();
     }
 

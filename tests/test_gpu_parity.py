@@ -26,7 +26,8 @@ def rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-SHAPES = [(4, 4, 4), (2, 3, 4), (6, 9, 8), (8, 12, 18), (32, 16, 24), (24, 27, 6), (16, 32, 36), (64, 8, 16)]
+SHAPES = [(4, 4, 4), (2, 3, 4), (6, 9, 8), (8, 12, 18), (32, 16, 24), (24, 27, 6), (16, 32, 36), (64, 8, 16),
+          (64, 64, 64), (128, 256, 16), (256, 64, 128), (32, 128, 512), (512, 16, 64)]
 
 
 @pytest.mark.parametrize("kspace", [0, 1])
@@ -110,6 +111,19 @@ def test_newton_cg_parity(cb, orc, k, kspace):
     # within rounding (the two sides form Delta and f differently)
     assert abs(g["nr_iters"] - r["nr_iters"]) <= max(2, 1e-3 * r["nr_iters"])
     assert abs(g["n_backproj"] - r["n_backproj"]) <= max(2, 1e-3 * r["n_backproj"])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_newton_cg_parity_fast_sizes(cb, orc, prec):
+    """64^3 and 128 x 64 x 256 grids run the compile-time FFT plans in every pass."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    for n in [(64, 64, 64), (128, 64, 256)]:
+        p = ms.random_spheres(n, 5.0, 0.15, 11, 10.0, np.diag([1.03, 1.0, 1.0]) + 0.01, 1)
+        g, r = solve_both(cb, orc, p, solver=1, precision=prec, fixed_iterations=1, cg_fixed_iterations=10)
+        tol = 1e-10 if prec == 0 else 2e-5
+        assert rel(g["F"], r["F"]) < tol
+        assert rel(g["Pbar"], r["Pbar"]) < (1e-9 if prec == 0 else 2e-5)
 
 
 def test_sphere_32_converged_fp64(cb, orc):
