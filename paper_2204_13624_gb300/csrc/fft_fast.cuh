@@ -143,10 +143,13 @@ __device__ __forceinline__ void stage_store(cx<T> (&v)[(N / R) / TPL][R], const 
 
 // Whole transform of one line by the TPL threads tau = 0..TPL-1 of a group.
 // lg / sg: first-stage input and last-stage output accessors; lx / sx: the
-// exchange buffer of this line.  Every thread of the block must call it (it
-// holds __syncthreads); the caller synchronises before reusing the exchange
-// buffer.
-template <typename T, int N, bool INV, class LG, class SG, class LX, class SX>
+// exchange buffer of this line.  SYNC_FIRST / SYNC_LAST put a block barrier
+// between the loads and the stores of the first / last stage, for when lg or
+// sg alias the exchange buffer.  Every thread of the block must call it with
+// the same plan (it holds __syncthreads); the caller synchronises before
+// reusing the exchange buffer.
+template <typename T, int N, bool INV, bool SYNC_FIRST = false, bool SYNC_LAST = false, class LG, class SG, class LX,
+          class SX>
 __device__ __forceinline__ void fft_fast(const LG& lg, const SG& sg, const LX& lx, const SX& sx, int tau,
                                          const cx<T>* __restrict__ tw)
 {
@@ -158,12 +161,14 @@ __device__ __forceinline__ void fft_fast(const LG& lg, const SG& sg, const LX& l
         {
             cx<T> v[(N / RA) / TPL][RA];
             stage_load<T, N, RA, 1, TPL, INV>(v, lg, tau, tw);
+            if constexpr (SYNC_FIRST) __syncthreads();
             stage_store<T, N, RA, 1, TPL>(v, sx, tau);
         }
         __syncthreads();
         {
             cx<T> v[(N / RB) / TPL][RB];
             stage_load<T, N, RB, RA, TPL, INV>(v, lx, tau, tw);
+            if constexpr (SYNC_LAST) __syncthreads();
             stage_store<T, N, RB, RA, TPL>(v, sg, tau);
         }
     } else {
@@ -172,6 +177,7 @@ __device__ __forceinline__ void fft_fast(const LG& lg, const SG& sg, const LX& l
         {
             cx<T> v[(N / RA) / TPL][RA];
             stage_load<T, N, RA, 1, TPL, INV>(v, lg, tau, tw);
+            if constexpr (SYNC_FIRST) __syncthreads();
             stage_store<T, N, RA, 1, TPL>(v, sx, tau);
         }
         __syncthreads();
@@ -185,6 +191,7 @@ __device__ __forceinline__ void fft_fast(const LG& lg, const SG& sg, const LX& l
         {
             cx<T> v[(N / RC) / TPL][RC];
             stage_load<T, N, RC, RA * RB, TPL, INV>(v, lx, tau, tw);
+            if constexpr (SYNC_LAST) __syncthreads();
             stage_store<T, N, RC, RA * RB, TPL>(v, sg, tau);
         }
     }

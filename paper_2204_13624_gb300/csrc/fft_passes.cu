@@ -29,12 +29,26 @@ size_t xpass_smem(const GridDims& g, int lines, size_t cxbytes)
 
 int xpass_lines(const GridDims& g, size_t cxbytes)
 {
-    // keep the two ping-pong buffers under ~48 KB while covering >= 256 voxels
+    // keep the two ping-pong buffers under ~48 KB while covering >= 512 voxels
     int lines = 1;
-    while (lines * g.n1 < 256 && xpass_smem(g, lines * 2, cxbytes) <= 48 * 1024 &&
+    while (lines * g.n1 < 512 && xpass_smem(g, lines * 2, cxbytes) <= 48 * 1024 &&
            (g.n2 * g.n3) % (lines * 2) == 0)
         lines *= 2;
     return lines;
+}
+
+// x-pass grid: a few resident blocks per SM stride over the line groups, so
+// that the fused reductions see few partials and few tickets.
+int xpass_grid(const GridDims& g, int lines)
+{
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
+    }
+    const int groups = (g.n2 * g.n3 + lines - 1) / lines;
+    return groups < 4 * nsm ? groups : 4 * nsm;
 }
 
 // x-pass FFT of the nl lines held in shared memory: compile-time plan when MF > 0
@@ -62,14 +76,17 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
     double* red = reinterpret_cast<double*>(buf1 + (size_t)9 * LB * ls);
     int* flag = reinterpret_cast<int*>(red + 256);
     T* rb = reinterpret_cast<T*>(buf0);
-    const int L0 = blockIdx.x * LB;
     const int nlines = g.n2 * g.n3;
+    const int ngroups = (nlines + LB - 1) / LB;
     const int64_t V = g.V;
     double acc = 0.0;
 
     const bool first = (a.mode == XF_TANGENT) ? (a.sc->cg_iter == 0) : false;
     const double beta = (a.mode == XF_TANGENT && !first) ? a.sc->beta : 0.0;
 
+    // grid-stride over groups of LB x-lines (a few blocks per SM)
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const int L0 = grp * LB;
     for (int e = threadIdx.x; e < LB * g.n1; e += blockDim.x) {
         const int l = e / g.n1, x = e - l * g.n1;
         const int L = L0 + l;
@@ -188,7 +205,7 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
     const int M = g.M;
     const int half = M / 2;
     for (int e = threadIdx.x; e < nl * (half + 1); e += blockDim.x) {
-        const int q = e % nl, k = e / nl;
+        const int q = e / (half + 1), k = e - q * (half + 1);  // k fastest: coalesced stores
         const int c = q / LB, l = q - c * LB;
         const int L = L0 + l;
         if (L >= nlines) continue;
@@ -217,6 +234,8 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
             o[k2] = c_add(Ze, c_mul(a.tw2[k2], Zo));
         }
     }
+    __syncthreads();  // the next group reuses the shared buffers
+    }
     if (a.mode == XF_TANGENT && a.partial) {
         const double s = block_sum(acc, red);
         if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
@@ -242,11 +261,17 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
     cx<T>* buf1 = buf0 + (size_t)9 * LB * ls;
     double* red = reinterpret_cast<double*>(buf1 + (size_t)9 * LB * ls);
     int* flag = reinterpret_cast<int*>(red + 256);
-    const int L0 = blockIdx.x * LB;
     const int nlines = g.n2 * g.n3;
+    const int ngroups = (nlines + LB - 1) / LB;
     const int nl = 9 * LB;
     const int64_t V = g.V;
+    double acc = 0.0;
+    const bool skip_update = (a.mode == XI_FIXEDPOINT) && a.sc->outer_done;
+    const double alpha = (a.mode == XI_CG) ? a.sc->alpha : 0.0;
 
+    // grid-stride over groups of LB x-lines (a few blocks per SM)
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const int L0 = grp * LB;
     for (int e = threadIdx.x; e < nl * (M + 1); e += blockDim.x) {
         const int q = e / (M + 1), k = e - q * (M + 1);
         const int c = q / LB, l = q - c * LB;
@@ -267,9 +292,6 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
     cx<T>* Zr = xpass_fft<T, MF, true>(buf1, buf0, a.plan, nl, ls, a.tw);
     const T* rb = reinterpret_cast<const T*>(Zr);
 
-    double acc = 0.0;
-    const bool skip_update = (a.mode == XI_FIXEDPOINT) && a.sc->outer_done;
-    const double alpha = (a.mode == XI_CG) ? a.sc->alpha : 0.0;
     for (int e = threadIdx.x; e < LB * g.n1; e += blockDim.x) {
         const int l = e / g.n1, x = e - l * g.n1;
         const int L = L0 + l;
@@ -295,6 +317,8 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
                 a.Y[w] = (double)gv;
             }
         }
+    }
+    __syncthreads();  // the next group reuses the shared buffers
     }
     if ((a.mode == XI_RHS || a.mode == XI_CG) && a.partial) {
         const double s = block_sum(acc, red);
@@ -438,90 +462,87 @@ __global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
 }
 
 // ------------------------------------------------------------- z pass + Gamma (power of two)
-// Block: TX columns x TPL threads.  Each of the 3 components of tensor row i
-// is transformed forward into the park tile [3][N][TX]; the last forward
-// stage leaves every thread holding whole frequency triples, so the
-// projection runs in place, and the inverse starts from the same positions.
+// Block: 3 groups (one per component of tensor row i) x TX columns x TPL
+// threads; the three components are transformed concurrently.  The tile
+// [3][N][TX] is both the exchange buffer and the place where the forward
+// transform ends; after a barrier every frequency's three components are in
+// shared memory, the projection runs in place, and each group's inverse
+// transform starts from the positions its own last forward stage wrote.
 template <typename T, int N, int TX>
-__global__ void __launch_bounds__(TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<T> a)
+__global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<T> a)
 {
     if (a.guard == 1 && a.sc->cg_done) return;
     if (a.guard == 2 && a.sc->outer_done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TPL = FastPlan<N>::TPL;
+    constexpr int GS = TX * TPL;  // threads per component group
     cx<T>* park = reinterpret_cast<cx<T>*>(smem_raw);  // [3][N][TX]
-    cx<T>* ex = park + 3 * N * TX;                      // [N][TX]
-    double* red = reinterpret_cast<double*>(ex + N * TX);
+    double* red = reinterpret_cast<double*>(park + 3 * N * TX);
     const GridDims g = a.g;
-    const int line = threadIdx.x % TX, tau = threadIdx.x / TX;
+    const int c = threadIdx.x / GS;
+    const int r = threadIdx.x - c * GS;
+    const int line = r % TX, tau = r / TX;
     const int x0 = blockIdx.x * TX;
-    const int xi1 = x0 + line;
-    const bool valid = xi1 < g.nh;
+    const bool valid = x0 + line < g.nh;
     const int y = blockIdx.y;
     const int row = blockIdx.z;
     const int64_t zst = (int64_t)g.n2 * g.nhp;
-    cx<T>* base = a.spec + (int64_t)(3 * row) * g.Vs + (int64_t)y * g.nhp + x0 + line;
-    auto lx = [&](int e) { return ex[e * TX + line]; };
-    auto sx = [&](int e, cx<T> v) { ex[e * TX + line] = v; };
+    cx<T>* bc = a.spec + (int64_t)(3 * row + c) * g.Vs + (int64_t)y * g.nhp + x0 + line;
+    cx<T>* pc = park + c * N * TX + line;
+    auto lp = [&](int e) { return pc[e * TX]; };
+    auto sp = [&](int e, cx<T> v) { pc[e * TX] = v; };
 
-#pragma unroll 1
-    for (int c = 0; c < 3; c++) {
-        cx<T>* bc = base + c * g.Vs;
-        cx<T>* pc = park + c * N * TX + line;
-        fft_fast<T, N, false>([&](int e) { return valid ? bc[e * zst] : cx<T>{(T)0, (T)0}; },
-                              [&](int e, cx<T> v) { pc[e * TX] = v; }, lx, sx, tau, a.tw);
-        __syncthreads();
-    }
+    // forward along z, ending in the tile (in place: barrier inside the last stage)
+    fft_fast<T, N, false, false, true>([&](int e) { return valid ? bc[e * zst] : cx<T>{(T)0, (T)0}; }, sp, lp, sp,
+                                       tau, a.tw);
+    __syncthreads();
 
-    // projection on this thread's frequencies xi3 = j + t (N / R_last)
-    using LS = LastStage<N>;
+    // projection: row i of G X at every (xi3, column) = k (k . X_i) / |k|^2
     double acc = 0.0;
     const T ay = a.sa[1][y], by = a.sb[1][y];
-    const T ax = valid ? a.sa[0][xi1] : (T)0, bx = valid ? a.sb[0][xi1] : (T)0;
-    const double wgt = (xi1 == 0 || xi1 == g.M) ? 1.0 : 2.0;
-#pragma unroll
-    for (int u = 0; u < LS::U; u++) {
-#pragma unroll
-        for (int t = 0; t < LS::R; t++) {
-            const int z = tau + TPL * u + t * LS::B;
-            cx<T>* p = park + z * TX + line;
-            const cx<T> X0 = p[0], X1 = p[N * TX], X2 = p[2 * N * TX];
-            const T az = a.sa[2][z], bz = a.sb[2][z];
-            const T k0 = ax * by * bz, k1 = ay * bx * bz, k2 = az * bx * by;
-            const T kk = k0 * k0 + k1 * k1 + k2 * k2;
-            if (a.want_norm && xi1 == 0 && y == 0 && z == 0) {
-                a.sc->dc[3 * row + 0] = (double)X0.x;
-                a.sc->dc[3 * row + 1] = (double)X1.x;
-                a.sc->dc[3 * row + 2] = (double)X2.x;
-            }
-            cx<T> o0{(T)0, (T)0}, o1{(T)0, (T)0}, o2{(T)0, (T)0};
-            if (valid && kk > (T)0) {
-                const T sr = (k0 * X0.x + k1 * X1.x + k2 * X2.x) / kk;
-                const T si = (k0 * X0.y + k1 * X1.y + k2 * X2.y) / kk;
-                o0 = cx<T>{k0 * sr, k0 * si};
-                o1 = cx<T>{k1 * sr, k1 * si};
-                o2 = cx<T>{k2 * sr, k2 * si};
-                if (a.want_norm)
-                    acc += wgt * ((double)o0.x * o0.x + (double)o0.y * o0.y + (double)o1.x * o1.x +
-                                  (double)o1.y * o1.y + (double)o2.x * o2.x + (double)o2.y * o2.y);
-            }
-            p[0] = c_scale(o0, a.scale);
-            p[N * TX] = c_scale(o1, a.scale);
-            p[2 * N * TX] = c_scale(o2, a.scale);
+    for (int f = threadIdx.x; f < N * TX; f += blockDim.x) {
+        const int z = f / TX, ln = f - z * TX;
+        const int xi1 = x0 + ln;
+        cx<T>* p = park + f;
+        if (xi1 >= g.nh) {
+            p[0] = p[N * TX] = p[2 * N * TX] = cx<T>{(T)0, (T)0};
+            continue;
         }
+        const cx<T> X0 = p[0], X1 = p[N * TX], X2 = p[2 * N * TX];
+        const T ax = a.sa[0][xi1], bx = a.sb[0][xi1];
+        const T az = a.sa[2][z], bz = a.sb[2][z];
+        const T k0 = ax * by * bz, k1 = ay * bx * bz, k2 = az * bx * by;
+        const T kk = k0 * k0 + k1 * k1 + k2 * k2;
+        if (a.want_norm && xi1 == 0 && y == 0 && z == 0) {
+            a.sc->dc[3 * row + 0] = (double)X0.x;
+            a.sc->dc[3 * row + 1] = (double)X1.x;
+            a.sc->dc[3 * row + 2] = (double)X2.x;
+        }
+        cx<T> o0{(T)0, (T)0}, o1{(T)0, (T)0}, o2{(T)0, (T)0};
+        if (kk > (T)0) {
+            const T sr = (k0 * X0.x + k1 * X1.x + k2 * X2.x) / kk;
+            const T si = (k0 * X0.y + k1 * X1.y + k2 * X2.y) / kk;
+            o0 = cx<T>{k0 * sr, k0 * si};
+            o1 = cx<T>{k1 * sr, k1 * si};
+            o2 = cx<T>{k2 * sr, k2 * si};
+            if (a.want_norm) {
+                const double wgt = (xi1 == 0 || xi1 == g.M) ? 1.0 : 2.0;
+                acc += wgt * ((double)o0.x * o0.x + (double)o0.y * o0.y + (double)o1.x * o1.x + (double)o1.y * o1.y +
+                              (double)o2.x * o2.x + (double)o2.y * o2.y);
+            }
+        }
+        p[0] = c_scale(o0, a.scale);
+        p[N * TX] = c_scale(o1, a.scale);
+        p[2 * N * TX] = c_scale(o2, a.scale);
     }
+    __syncthreads();
 
-#pragma unroll 1
-    for (int c = 0; c < 3; c++) {
-        cx<T>* bc = base + c * g.Vs;
-        cx<T>* pc = park + c * N * TX + line;
-        fft_fast<T, N, true>([&](int e) { return pc[e * TX]; },
-                             [&](int e, cx<T> v) {
-                                 if (valid) bc[e * zst] = v;
-                             },
-                             lx, sx, tau, a.tw);
-        __syncthreads();
-    }
+    // inverse along z from the tile (in place: barrier inside the first stage)
+    fft_fast<T, N, true, true, false>(lp,
+                                      [&](int e, cx<T> v) {
+                                          if (valid) bc[e * zst] = v;
+                                      },
+                                      lp, sp, tau, a.tw);
     if (a.want_norm && a.partial) {
         const double s = block_sum(acc, red);
         if (threadIdx.x == 0) a.partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
@@ -530,11 +551,13 @@ __global__ void __launch_bounds__(TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<T> a
 
 // ------------------------------------------------------------- launch configuration
 template <typename T> int ytx_fast(int n) { return sizeof(T) == 4 ? 16 : 8; }
-template <typename T> int ztx_fast(int n)
+// z-pass columns per block: 3 * N * TX complex values of shared memory (48 KB
+// at N >= 256)
+template <typename T> constexpr int ztx_const(int n)
 {
-    if (n == 512) return sizeof(T) == 4 ? 4 : 2;
-    return sizeof(T) == 4 ? 8 : 4;
+    return sizeof(T) == 4 ? (n == 512 ? 4 : (n == 256 ? 8 : 16)) : (n == 512 ? 2 : (n == 256 ? 4 : 8));
 }
+template <typename T> int ztx_fast(int n) { return ztx_const<T>(n); }
 
 int zpass_tx(int n, size_t cxbytes)
 {
@@ -562,8 +585,7 @@ template <typename K> static void allow_smem(K kernel, bool& done)
 
 template <typename T, typename Tc, int MF> static void xfwd_launch(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st)
 {
-    const int nlines = a.g.n2 * a.g.n3;
-    const int grid = (nlines + a.lines_per_block - 1) / a.lines_per_block;
+    const int grid = xpass_grid(a.g, a.lines_per_block);
     const size_t sm = xpass_smem(a.g, a.lines_per_block, sizeof(cx<T>));
     static bool attr = false;
     allow_smem(k_xfwd<T, Tc, MF>, attr);
@@ -583,8 +605,7 @@ template <typename T, typename Tc> void launch_xfwd(const XfwdArgs<T, Tc>& a, in
 
 template <typename T, typename Tc, int MF> static void xinv_launch(const XinvArgs<T, Tc>& a, int guard, cudaStream_t st)
 {
-    const int nlines = a.g.n2 * a.g.n3;
-    const int grid = (nlines + a.lines_per_block - 1) / a.lines_per_block;
+    const int grid = xpass_grid(a.g, a.lines_per_block);
     const size_t sm = xpass_smem(a.g, a.lines_per_block, sizeof(cx<T>));
     static bool attr = false;
     allow_smem(k_xinv<T, Tc, MF>, attr);
@@ -630,12 +651,12 @@ template <typename T, bool INV> void launch_ypass(const YArgs<T>& a, cudaStream_
 
 template <typename T, int N> static void zpass_fast_launch(const ZArgs<T>& a, cudaStream_t st)
 {
-    constexpr int TX = (N == 512) ? (sizeof(T) == 4 ? 4 : 2) : (sizeof(T) == 4 ? 8 : 4);
+    constexpr int TX = ztx_const<T>(N);
     dim3 grid((a.g.nh + TX - 1) / TX, a.g.n2, 3);
-    const size_t sm = (size_t)4 * N * TX * sizeof(cx<T>) + 64 * sizeof(double);
+    const size_t sm = (size_t)3 * N * TX * sizeof(cx<T>) + 64 * sizeof(double);
     static bool attr = false;
     allow_smem(k_zpass_fast<T, N, TX>, attr);
-    k_zpass_fast<T, N, TX><<<grid, TX * FastPlan<N>::TPL, sm, st>>>(a);
+    k_zpass_fast<T, N, TX><<<grid, 3 * TX * FastPlan<N>::TPL, sm, st>>>(a);
 }
 
 template <typename T> void launch_zpass(const ZArgs<T>& a, cudaStream_t st)

@@ -413,7 +413,7 @@ template <typename T> struct Engine {
         if (pr) pr->end();
     }
     int zblocks() const { return ((g.nh + txz - 1) / txz) * g.n2 * 3; }
-    int xblocks() const { return (g.n2 * g.n3 + lines - 1) / lines; }
+    int xblocks() const { return xpass_grid(g, lines); }
 };
 
 // ------------------------------------------------------------------ small kernels
