@@ -46,15 +46,20 @@ def parse():
     ap.add_argument("--impl", default="combo", choices=["combo", "reference"])
     ap.add_argument("--precision", default="refined", choices=["refined", "fp64"])
     ap.add_argument("--n", type=int, default=256, help="grid side (256 = the benchmark workload)")
+    ap.add_argument("--shape", default=None, help="n1,n2,n3 of a smaller ball grid (profiling captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel table here")
     return ap.parse_args()
 
 
-def workload(n):
+def workload(n, shape=None):
     from paper_2204_13624_gb300 import microstructure as ms
 
+    if shape:
+        dims = tuple(int(v) for v in shape.split(","))
+        return ms.random_spheres(dims, 12.0 * max(dims) / 256.0, 0.2, ms.SEED_BASE + 1, 100.0,
+                                 np.diag([1.10, 1.0, 1.0]), 10)
     if n == 256:
         return ms.spheres_256()
     return ms.spheres_256(n=n, vf=0.2 if n >= 128 else 0.1)
@@ -218,7 +223,7 @@ def main():
     if dist:
         dist.barrier()
     combo.load()
-    p = workload(args.n)
+    p = workload(args.n, args.shape)
     V = p["n"][0] * p["n"][1] * p["n"][2]
     stream = torch.cuda.current_stream()
     ctx = combo.Context(local, stream.cuda_stream)
@@ -293,7 +298,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if prec == combo.FP32_REFINED else "f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD if args.n == 256 else f"spheres_{args.n}",
+                "config": {"workload": (f"spheres_{args.shape.replace(',', 'x')}" if args.shape else
+                                        (WORKLOAD if args.n == 256 else f"spheres_{args.n}")),
                            "grid": list(p["n"]), "voxels": V, "boxels": int(p["boxel_idx"].size),
                            "microstructure": "seeded RSA balls r=12 vox, vf 0.25, contrast 100",
                            "load": "Fbar11 = 1.10 in 10 steps",

@@ -122,19 +122,30 @@ __device__ __forceinline__ bool inv3(const double A[9], double B[9])
     return true;
 }
 
-// (A D)_(iJ),k for one Neo-Hookean phase
-__device__ __forceinline__ double AD(const Phase& s, double mu, double lam, const double N[3], int i, int Jx, int k)
-{
-    const double m = mu - lam * s.lnJ;
-    return (i == k ? mu * N[Jx] : 0.0) + lam * s.G[3 * Jx + i] * s.g[k] + m * s.G[3 * Jx + k] * s.g[i];
-}
-
-// A_iJkL for one Neo-Hookean phase
-__device__ __forceinline__ double Aent(const Phase& s, double mu, double lam, int i, int Jx, int k, int L)
-{
-    const double m = mu - lam * s.lnJ;
-    return ((i == k && Jx == L) ? mu : 0.0) + lam * s.G[3 * Jx + i] * s.G[3 * L + k] + m * s.G[3 * Jx + k] * s.G[3 * L + i];
-}
+// One Neo-Hookean phase's tangent data in precision S:
+//   A_iJkL     = mu d_ik d_JL + lam G_Ji G_Lk + m G_Jk G_Li,   m = mu - lam ln J
+//   (A D)_(iJ),k = mu d_ik N_J + lam G_Ji g_k + m G_Jk g_i,     g = G^T N
+template <typename S> struct TanPhase {
+    S G[9], g[3], mu, lam, m;
+    __device__ __forceinline__ void load(const Phase& s, double mu_, double lam_)
+    {
+#pragma unroll
+        for (int q = 0; q < 9; q++) G[q] = (S)s.G[q];
+#pragma unroll
+        for (int q = 0; q < 3; q++) g[q] = (S)s.g[q];
+        mu = (S)mu_;
+        lam = (S)lam_;
+        m = (S)(mu_ - lam_ * s.lnJ);
+    }
+    __device__ __forceinline__ S AD(const S N[3], int i, int Jx, int k) const
+    {
+        return (i == k ? mu * N[Jx] : (S)0) + lam * G[3 * Jx + i] * g[k] + m * G[3 * Jx + k] * g[i];
+    }
+    __device__ __forceinline__ S A(int i, int Jx, int k, int L) const
+    {
+        return ((i == k && Jx == L) ? mu : (S)0) + lam * G[3 * Jx + i] * G[3 * L + k] + m * G[3 * Jx + k] * G[3 * L + i];
+    }
+};
 
 template <typename Tc>
 __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
@@ -216,24 +227,34 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
                 if (!inv3(Dl, Di)) {
                     raise_status(A.sc, COMBO_E_LAMINATE);
                 } else {
+                    // The boxel tangent only feeds the Krylov iterations: it is
+                    // formed in their precision Tc from the converged FP64 state.
+                    TanPhase<Tc> tp, tm;
+                    tp.load(e.p, mu[1], lam[1]);
+                    tm.load(e.m, mu[0], lam[0]);
+                    Tc Nt[3] = {(Tc)N[0], (Tc)N[1], (Tc)N[2]};
+                    Tc Dt[9];
+#pragma unroll
+                    for (int q = 0; q < 9; q++) Dt[q] = (Tc)Di[q];
+                    const Tc cpt = (Tc)cp, cmt = (Tc)cm;
                     // B = dA D (9x3), W = B Delta^{-1}
-                    double B[27], W[27];
+                    Tc B[27], W[27];
+#pragma unroll
+                    for (int r = 0; r < 9; r++)
+#pragma unroll
+                        for (int k = 0; k < 3; k++) B[3 * r + k] = tp.AD(Nt, r / 3, r % 3, k) - tm.AD(Nt, r / 3, r % 3, k);
 #pragma unroll
                     for (int r = 0; r < 9; r++)
 #pragma unroll
                         for (int k = 0; k < 3; k++)
-                            B[3 * r + k] = AD(e.p, mu[1], lam[1], N, r / 3, r % 3, k) - AD(e.m, mu[0], lam[0], N, r / 3, r % 3, k);
+                            W[3 * r + k] = B[3 * r] * Dt[k] + B[3 * r + 1] * Dt[3 + k] + B[3 * r + 2] * Dt[6 + k];
 #pragma unroll
                     for (int r = 0; r < 9; r++)
 #pragma unroll
-                        for (int k = 0; k < 3; k++)
-                            W[3 * r + k] = B[3 * r] * Di[k] + B[3 * r + 1] * Di[3 + k] + B[3 * r + 2] * Di[6 + k];
-                    for (int r = 0; r < 9; r++)
                         for (int s = 0; s < 9; s++) {
-                            const double avg = cp * Aent(e.p, mu[1], lam[1], r / 3, r % 3, s / 3, s % 3) +
-                                               cm * Aent(e.m, mu[0], lam[0], r / 3, r % 3, s / 3, s % 3);
-                            const double corr = W[3 * r] * B[3 * s] + W[3 * r + 1] * B[3 * s + 1] + W[3 * r + 2] * B[3 * s + 2];
-                            A.bA[(int64_t)(r * 9 + s) * A.nb + b] = (Tc)(avg - corr);
+                            const Tc avg = cpt * tp.A(r / 3, r % 3, s / 3, s % 3) + cmt * tm.A(r / 3, r % 3, s / 3, s % 3);
+                            const Tc corr = W[3 * r] * B[3 * s] + W[3 * r + 1] * B[3 * s + 1] + W[3 * r + 2] * B[3 * s + 2];
+                            A.bA[(int64_t)(r * 9 + s) * A.nb + b] = avg - corr;
                         }
                 }
             }
