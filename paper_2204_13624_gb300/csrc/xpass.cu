@@ -1,0 +1,473 @@
+// xpass.cu -- x-axis passes of one operator application.
+//
+//   x-forward : per-voxel constitutive law (paper Sec. 6.1; boxel stresses
+//               come from the laminate kernel) or tangent application, then
+//               a real-to-complex FFT along x (packed half-length complex
+//               transform + Hermitian split), written to the half spectrum.
+//   x-inverse : complex-to-real FFT along x and the solver update fused in
+//               (fixed point F -= G[P]/mu0, or the CG updates x += a p,
+//               r -= a q with (r, r)).
+//
+// Real fields are [9][n3][n2][n1] (x fastest).  A block strides over groups
+// of LB x-lines; each thread owns voxel pairs (x, x+1) and issues all of a
+// pair's loads (vectorised) before any arithmetic, so several DRAM round
+// trips overlap instead of following each other.
+#include "combo_internal.cuh"
+#include "fft_fast.cuh"
+#include "../../include/combo.h"
+
+namespace combo {
+
+size_t xpass_smem(const GridDims& g, int lines, size_t cxbytes)
+{
+    return 2 * (size_t)9 * lines * (g.M + 1) * cxbytes + 256 * sizeof(double) + 16;
+}
+
+int xpass_lines(const GridDims& g, size_t cxbytes)
+{
+    // keep the two ping-pong buffers under ~48 KB while covering >= 512 voxels
+    int lines = 1;
+    while (lines * g.n1 < 512 && xpass_smem(g, lines * 2, cxbytes) <= 48 * 1024 &&
+           (g.n2 * g.n3) % (lines * 2) == 0)
+        lines *= 2;
+    return lines;
+}
+
+// x-pass grid: a few resident blocks per SM stride over the line groups, so
+// that the fused reductions see few partials and few tickets.
+int xpass_grid(const GridDims& g, int lines)
+{
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
+    }
+    const int groups = (g.n2 * g.n3 + lines - 1) / lines;
+    return groups < 4 * nsm ? groups : 4 * nsm;
+}
+
+template <typename K> static void allow_smem(K kernel, bool& done)
+{
+    if (!done) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        done = true;
+    }
+}
+
+// x-pass FFT of the nl lines held in shared memory: compile-time plan when MF > 0
+template <typename T, int MF, bool INV>
+__device__ __forceinline__ cx<T>* xpass_fft(cx<T>* b0, cx<T>* b1, const Plan& plan, int nl, int ls, const cx<T>* tw)
+{
+    if constexpr (MF > 0)
+        return fft_lines_fast<T, MF, INV>(b0, b1, nl, ls, tw);
+    else
+        return fft_lines<T, INV>(b0, b1, plan, nl, ls, 1, tw);
+}
+
+template <typename S> struct Pair;
+template <> struct Pair<float> { typedef float2 type; };
+template <> struct Pair<double> { typedef double2 type; };
+template <typename S> using pair_t = typename Pair<S>::type;
+
+template <typename S> __device__ __forceinline__ pair_t<S> ld2(const S* __restrict__ p)
+{
+    return *reinterpret_cast<const pair_t<S>*>(p);
+}
+template <typename S> __device__ __forceinline__ void st2(S* __restrict__ p, S a, S b)
+{
+    *reinterpret_cast<pair_t<S>*>(p) = pair_t<S>{a, b};
+}
+
+// Neo-Hookean stress (Sec. 6.1) in FP64: P = mu F + (lam ln J - mu) F^{-T};
+// G = F^{-1} and m = mu - lam ln J for the tangent cache.  False if J <= 0.
+__device__ __forceinline__ bool nh_stress(const double F[9], double mu, double lam, double P[9], double G[9], double& m)
+{
+    const double c0 = F[4] * F[8] - F[5] * F[7];
+    const double c1 = F[5] * F[6] - F[3] * F[8];
+    const double c2 = F[3] * F[7] - F[4] * F[6];
+    const double J = F[0] * c0 + F[1] * c1 + F[2] * c2;
+    if (!(J > 0.0)) return false;
+    const double iJ = 1.0 / J;
+    G[0] = c0 * iJ;
+    G[1] = (F[2] * F[7] - F[1] * F[8]) * iJ;
+    G[2] = (F[1] * F[5] - F[2] * F[4]) * iJ;
+    G[3] = c1 * iJ;
+    G[4] = (F[0] * F[8] - F[2] * F[6]) * iJ;
+    G[5] = (F[2] * F[3] - F[0] * F[5]) * iJ;
+    G[6] = c2 * iJ;
+    G[7] = (F[1] * F[6] - F[0] * F[7]) * iJ;
+    G[8] = (F[0] * F[4] - F[1] * F[3]) * iJ;
+    const double lnJ = log(J);
+    const double k = lam * lnJ - mu;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) P[3 * i + j] = mu * F[3 * i + j] + k * G[3 * j + i];
+    m = mu - lam * lnJ;
+    return true;
+}
+
+// y = A : p for a pure Neo-Hookean voxel from its cache (G = F^{-1}, m):
+//   y_iJ = mu p_iJ + lam tr(G p) G_Ji + m (G p G)_Ji
+template <typename S>
+__device__ __forceinline__ void nh_tangent(const S G[9], S m, S mu, S lam, const S p[9], S y[9])
+{
+    S Gp[9], GpG[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) Gp[3 * i + j] = G[3 * i] * p[j] + G[3 * i + 1] * p[3 + j] + G[3 * i + 2] * p[6 + j];
+    const S tr = Gp[0] + Gp[4] + Gp[8];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) GpG[3 * i + j] = Gp[3 * i] * G[j] + Gp[3 * i + 1] * G[3 + j] + Gp[3 * i + 2] * G[6 + j];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) y[3 * i + j] = mu * p[3 * i + j] + lam * tr * G[3 * j + i] + m * GpG[3 * j + i];
+}
+
+// ------------------------------------------------------------- x forward
+template <typename T, typename Tc, int MF>
+__global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
+{
+    if (guard == 1 && a.sc->cg_done) return;
+    if (guard == 2 && a.sc->outer_done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const GridDims g = a.g;
+    const int LB = a.lines_per_block;
+    const int ls = g.M + 1;
+    cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
+    cx<T>* buf1 = buf0 + (size_t)9 * LB * ls;
+    double* red = reinterpret_cast<double*>(buf1 + (size_t)9 * LB * ls);
+    int* flag = reinterpret_cast<int*>(red + 256);
+    T* rb = reinterpret_cast<T*>(buf0);
+    const int nlines = g.n2 * g.n3;
+    const int ngroups = (nlines + LB - 1) / LB;
+    const int64_t V = g.V;
+    const int hn = g.n1 >> 1;
+    double acc = 0.0;
+
+    const bool first = (a.mode == XF_TANGENT) ? (a.sc->cg_iter == 0) : false;
+    const Tc beta = (a.mode == XF_TANGENT && !first) ? (Tc)a.sc->beta : (Tc)0;
+    const uint8_t* __restrict__ phase = a.phase;
+
+    // grid-stride over groups of LB x-lines (a few blocks per SM)
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int L0 = grp * LB;
+        for (int e = threadIdx.x; e < LB * hn; e += blockDim.x) {
+            const int l = e / hn, x = 2 * (e - l * hn);
+            const int L = L0 + l;
+            if (L >= nlines) continue;
+            const int64_t v = (int64_t)L * g.n1 + x;
+            T o0[9], o1[9];
+            if (a.X) {
+#pragma unroll
+                for (int c = 0; c < 9; c++) {
+                    const double2 q = ld2(a.X + c * V + v);
+                    o0[c] = (T)q.x;
+                    o1[c] = (T)q.y;
+                }
+            } else if (a.mode == XF_RESID) {
+                const uchar2 ph = *reinterpret_cast<const uchar2*>(phase + v);
+                double F0[9], F1[9];
+#pragma unroll
+                for (int c = 0; c < 9; c++) {
+                    const double2 q = ld2(a.F + c * V + v);
+                    F0[c] = q.x;
+                    F1[c] = q.y;
+                }
+                Tc G0[10], G1[10];
+#pragma unroll
+                for (int k = 0; k < 2; k++) {
+                    const int pk = k ? ph.y : ph.x;
+                    const double* F = k ? F1 : F0;
+                    T* o = k ? o1 : o0;
+                    Tc* Gc = k ? G1 : G0;
+                    if (pk == 2) {
+                        const int b = a.vox2box[v + k];
+#pragma unroll
+                        for (int c = 0; c < 9; c++) o[c] = (T)a.bP[(int64_t)b * 9 + c];
+#pragma unroll
+                        for (int c = 0; c < 10; c++) Gc[c] = (Tc)0;
+                    } else {
+                        double P[9], G[9], m;
+                        if (!nh_stress(F, a.mu[pk], a.lam[pk], P, G, m)) {
+                            raise_status(a.sc, COMBO_E_INADMISSIBLE);
+#pragma unroll
+                            for (int c = 0; c < 9; c++) P[c] = G[c] = 0.0;
+                            m = 0.0;
+                        }
+#pragma unroll
+                        for (int c = 0; c < 9; c++) {
+                            o[c] = (T)P[c];
+                            Gc[c] = (Tc)G[c];
+                        }
+                        Gc[9] = (Tc)m;
+                    }
+                }
+                if (a.tc) {
+#pragma unroll
+                    for (int c = 0; c < 10; c++) st2<Tc>(a.tc + c * V + v, G0[c], G1[c]);
+                }
+            } else {  // XF_TANGENT: p = r + beta p, y = A : p
+                const uchar2 ph = *reinterpret_cast<const uchar2*>(phase + v);
+                pair_t<Tc> r2[9], p2[9], t2[10];
+#pragma unroll
+                for (int c = 0; c < 9; c++) r2[c] = ld2(a.r + c * V + v);
+                if (!first) {
+#pragma unroll
+                    for (int c = 0; c < 9; c++) p2[c] = ld2(a.p + c * V + v);
+                }
+#pragma unroll
+                for (int c = 0; c < 10; c++) t2[c] = ld2(a.tc + c * V + v);
+                Tc p0[9], p1[9];
+#pragma unroll
+                for (int c = 0; c < 9; c++) {
+                    p0[c] = first ? r2[c].x : r2[c].x + beta * p2[c].x;
+                    p1[c] = first ? r2[c].y : r2[c].y + beta * p2[c].y;
+                    st2<Tc>(a.p + c * V + v, p0[c], p1[c]);
+                }
+#pragma unroll
+                for (int k = 0; k < 2; k++) {
+                    const int pk = k ? ph.y : ph.x;
+                    const Tc* p = k ? p1 : p0;
+                    T* o = k ? o1 : o0;
+                    Tc y[9];
+                    if (pk == 2) {
+                        const int64_t b = a.vox2box[v + k];
+#pragma unroll
+                        for (int r = 0; r < 9; r++) {
+                            Tc s = 0;
+#pragma unroll
+                            for (int c = 0; c < 9; c++) s += a.bA[(int64_t)(r * 9 + c) * a.nb + b] * p[c];
+                            y[r] = s;
+                        }
+                    } else {
+                        Tc G[9];
+#pragma unroll
+                        for (int c = 0; c < 9; c++) G[c] = k ? t2[c].y : t2[c].x;
+                        const Tc m = k ? t2[9].y : t2[9].x;
+                        nh_tangent<Tc>(G, m, (Tc)a.mu[pk], (Tc)a.lam[pk], p, y);
+                    }
+                    double s = 0.0;
+#pragma unroll
+                    for (int c = 0; c < 9; c++) {
+                        s += (double)p[c] * (double)y[c];
+                        o[c] = (T)y[c];
+                    }
+                    acc += s;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 9; c++) st2<T>(rb + (size_t)2 * (c * LB + l) * ls + x, o0[c], o1[c]);
+        }
+        __syncthreads();
+
+        const int nl = 9 * LB;
+        cx<T>* Z = xpass_fft<T, MF, false>(buf0, buf1, a.plan, nl, ls, a.tw);
+
+        // Hermitian split of the packed transform: X[k] = Ze + W^k Zo, k = 0..M
+        const int M = g.M;
+        const int half = M / 2;
+        for (int e = threadIdx.x; e < nl * (half + 1); e += blockDim.x) {
+            const int q = e / (half + 1), k = e - q * (half + 1);  // k fastest: coalesced stores
+            const int c = q / LB, l = q - c * LB;
+            const int L = L0 + l;
+            if (L >= nlines) continue;
+            const cx<T>* z = Z + (size_t)q * ls;
+            cx<T>* o = a.spec + c * g.Vs + (int64_t)L * g.nhp;
+            if (k == 0) {
+                const cx<T> z0 = z[0];
+                o[0] = cx<T>{z0.x + z0.y, (T)0};
+                o[M] = cx<T>{z0.x - z0.y, (T)0};
+                continue;
+            }
+            const int k2 = M - k;
+            const cx<T> A = z[k], B = z[k2];
+            {
+                const cx<T> Bc = c_conj(B);
+                const cx<T> Ze = c_scale(c_add(A, Bc), (T)0.5);
+                const cx<T> D = c_sub(A, Bc);
+                const cx<T> Zo = cx<T>{(T)0.5 * D.y, (T)-0.5 * D.x};
+                o[k] = c_add(Ze, c_mul(a.tw2[k], Zo));
+            }
+            if (k2 != k) {
+                const cx<T> Ac = c_conj(A);
+                const cx<T> Ze = c_scale(c_add(B, Ac), (T)0.5);
+                const cx<T> D = c_sub(B, Ac);
+                const cx<T> Zo = cx<T>{(T)0.5 * D.y, (T)-0.5 * D.x};
+                o[k2] = c_add(Ze, c_mul(a.tw2[k2], Zo));
+            }
+        }
+        __syncthreads();  // the next group reuses the shared buffers
+    }
+    if (a.mode == XF_TANGENT && a.partial) {
+        const double s = block_sum(acc, red);
+        if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
+        if (a.fuse && last_block(&a.sc->ticket[0], flag)) {
+            const double tot = sum_partials_fixed(a.partial, gridDim.x, red);
+            if (threadIdx.x == 0) cg_alpha(a.sc, tot);
+        }
+    }
+}
+
+// ------------------------------------------------------------- x inverse
+template <typename T, typename Tc, int MF>
+__global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
+{
+    if (guard == 1 && a.sc->cg_done) return;
+    if (guard == 2 && a.sc->outer_done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const GridDims g = a.g;
+    const int LB = a.lines_per_block;
+    const int ls = g.M + 1;
+    const int M = g.M;
+    cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
+    cx<T>* buf1 = buf0 + (size_t)9 * LB * ls;
+    double* red = reinterpret_cast<double*>(buf1 + (size_t)9 * LB * ls);
+    int* flag = reinterpret_cast<int*>(red + 256);
+    const int nlines = g.n2 * g.n3;
+    const int ngroups = (nlines + LB - 1) / LB;
+    const int nl = 9 * LB;
+    const int64_t V = g.V;
+    const int hn = g.n1 >> 1;
+    double acc = 0.0;
+    const bool skip_update = (a.mode == XI_FIXEDPOINT) && a.sc->outer_done;
+    const Tc alpha = (a.mode == XI_CG) ? (Tc)a.sc->alpha : (Tc)0;
+
+    // grid-stride over groups of LB x-lines (a few blocks per SM)
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int L0 = grp * LB;
+        for (int e = threadIdx.x; e < nl * (M + 1); e += blockDim.x) {
+            const int q = e / (M + 1), k = e - q * (M + 1);
+            const int c = q / LB, l = q - c * LB;
+            const int L = L0 + l;
+            buf0[(size_t)q * ls + k] =
+                (L < nlines) ? a.spec[c * g.Vs + (int64_t)L * g.nhp + k] : cx<T>{(T)0, (T)0};
+        }
+        __syncthreads();
+        // Z[k] = Ze + i Zo,  Ze = (X[k] + conj X[M-k]) / 2,  Zo = (X[k] - conj X[M-k]) W^{-k} / 2
+        for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
+            const int q = e / M, k = e - q * M;
+            const cx<T> A = buf0[(size_t)q * ls + k];
+            const cx<T> Bc = c_conj(buf0[(size_t)q * ls + (M - k)]);
+            const cx<T> Ze = c_scale(c_add(A, Bc), (T)0.5);
+            const cx<T> Zo = c_mul(c_scale(c_sub(A, Bc), (T)0.5), c_conj(a.tw2[k]));
+            buf1[(size_t)q * ls + k] = cx<T>{Ze.x - Zo.y, Ze.y + Zo.x};
+        }
+        __syncthreads();
+        cx<T>* Zr = xpass_fft<T, MF, true>(buf1, buf0, a.plan, nl, ls, a.tw);
+        const T* rb = reinterpret_cast<const T*>(Zr);
+
+        for (int e = threadIdx.x; e < LB * hn; e += blockDim.x) {
+            const int l = e / hn, x = 2 * (e - l * hn);
+            const int L = L0 + l;
+            if (L >= nlines) continue;
+            const int64_t v = (int64_t)L * g.n1 + x;
+            if (a.mode == XI_CG) {
+                pair_t<Tc> x2[9], r2[9], p2[9];
+#pragma unroll
+                for (int c = 0; c < 9; c++) {
+                    x2[c] = ld2(a.x + c * V + v);
+                    r2[c] = ld2(a.r + c * V + v);
+                    p2[c] = ld2(a.p + c * V + v);
+                }
+#pragma unroll
+                for (int c = 0; c < 9; c++) {
+                    const pair_t<T> gv = *reinterpret_cast<const pair_t<T>*>(rb + (size_t)2 * (c * LB + l) * ls + x);
+                    const Tc ra = r2[c].x - alpha * (Tc)gv.x, rbv = r2[c].y - alpha * (Tc)gv.y;
+                    st2<Tc>(a.x + c * V + v, x2[c].x + alpha * p2[c].x, x2[c].y + alpha * p2[c].y);
+                    st2<Tc>(a.r + c * V + v, ra, rbv);
+                    acc += (double)ra * (double)ra + (double)rbv * (double)rbv;
+                }
+            } else if (a.mode == XI_FIXEDPOINT) {
+                if (skip_update) continue;
+                double2 F2[9];
+#pragma unroll
+                for (int c = 0; c < 9; c++) F2[c] = ld2(a.F + c * V + v);
+#pragma unroll
+                for (int c = 0; c < 9; c++) {
+                    const pair_t<T> gv = *reinterpret_cast<const pair_t<T>*>(rb + (size_t)2 * (c * LB + l) * ls + x);
+                    st2<double>(a.F + c * V + v, F2[c].x - (double)gv.x * a.inv_mu0, F2[c].y - (double)gv.y * a.inv_mu0);
+                }
+            } else if (a.mode == XI_RHS) {
+#pragma unroll
+                for (int c = 0; c < 9; c++) {
+                    const pair_t<T> gv = *reinterpret_cast<const pair_t<T>*>(rb + (size_t)2 * (c * LB + l) * ls + x);
+                    const Tc ra = (Tc)(-gv.x), rbv = (Tc)(-gv.y);
+                    st2<Tc>(a.r + c * V + v, ra, rbv);
+                    st2<Tc>(a.x + c * V + v, (Tc)0, (Tc)0);
+                    acc += (double)ra * (double)ra + (double)rbv * (double)rbv;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 9; c++) {
+                    const pair_t<T> gv = *reinterpret_cast<const pair_t<T>*>(rb + (size_t)2 * (c * LB + l) * ls + x);
+                    st2<double>(a.Y + c * V + v, (double)gv.x, (double)gv.y);
+                }
+            }
+        }
+        __syncthreads();  // the next group reuses the shared buffers
+    }
+    if ((a.mode == XI_RHS || a.mode == XI_CG) && a.partial) {
+        const double s = block_sum(acc, red);
+        if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
+        if (a.mode == XI_CG && a.fuse && last_block(&a.sc->ticket[1], flag)) {
+            const double tot = sum_partials_fixed(a.partial, gridDim.x, red);
+            if (threadIdx.x == 0) cg_beta(a.sc, tot, a.cg_tol, a.cg_max, a.cg_fixed);
+        }
+    }
+}
+
+// ------------------------------------------------------------- launchers
+template <typename T, typename Tc, int MF> static void xfwd_launch(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st)
+{
+    const int grid = xpass_grid(a.g, a.lines_per_block);
+    const size_t sm = xpass_smem(a.g, a.lines_per_block, sizeof(cx<T>));
+    static bool attr = false;
+    allow_smem(k_xfwd<T, Tc, MF>, attr);
+    k_xfwd<T, Tc, MF><<<grid, 256, sm, st>>>(a, guard);
+}
+
+template <typename T, typename Tc> void launch_xfwd(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st)
+{
+    switch (a.g.M) {
+        case 32: xfwd_launch<T, Tc, 32>(a, guard, st); break;
+        case 64: xfwd_launch<T, Tc, 64>(a, guard, st); break;
+        case 128: xfwd_launch<T, Tc, 128>(a, guard, st); break;
+        case 256: xfwd_launch<T, Tc, 256>(a, guard, st); break;
+        default: xfwd_launch<T, Tc, 0>(a, guard, st); break;
+    }
+}
+
+template <typename T, typename Tc, int MF> static void xinv_launch(const XinvArgs<T, Tc>& a, int guard, cudaStream_t st)
+{
+    const int grid = xpass_grid(a.g, a.lines_per_block);
+    const size_t sm = xpass_smem(a.g, a.lines_per_block, sizeof(cx<T>));
+    static bool attr = false;
+    allow_smem(k_xinv<T, Tc, MF>, attr);
+    k_xinv<T, Tc, MF><<<grid, 256, sm, st>>>(a, guard);
+}
+
+template <typename T, typename Tc> void launch_xinv(const XinvArgs<T, Tc>& a, int guard, cudaStream_t st)
+{
+    switch (a.g.M) {
+        case 32: xinv_launch<T, Tc, 32>(a, guard, st); break;
+        case 64: xinv_launch<T, Tc, 64>(a, guard, st); break;
+        case 128: xinv_launch<T, Tc, 128>(a, guard, st); break;
+        case 256: xinv_launch<T, Tc, 256>(a, guard, st); break;
+        default: xinv_launch<T, Tc, 0>(a, guard, st); break;
+    }
+}
+
+template void launch_xfwd<double, double>(const XfwdArgs<double, double>&, int, cudaStream_t);
+template void launch_xfwd<double, float>(const XfwdArgs<double, float>&, int, cudaStream_t);
+template void launch_xfwd<float, float>(const XfwdArgs<float, float>&, int, cudaStream_t);
+template void launch_xinv<double, double>(const XinvArgs<double, double>&, int, cudaStream_t);
+template void launch_xinv<double, float>(const XinvArgs<double, float>&, int, cudaStream_t);
+template void launch_xinv<float, float>(const XinvArgs<float, float>&, int, cudaStream_t);
+
+}  // namespace combo
