@@ -9,9 +9,10 @@
 //               r -= a q with (r, r)).
 //
 // Real fields are [9][n3][n2][n1] (x fastest).  A block strides over groups
-// of LB x-lines; each thread owns voxel pairs (x, x+1) and issues all of a
-// pair's loads (vectorised) before any arithmetic, so several DRAM round
-// trips overlap instead of following each other.
+// of LB x-lines; each thread issues all of a voxel's loads before any
+// arithmetic, so the DRAM round trips overlap.  Dot products are summed in
+// FP32 within a thread's share of a group and in FP64 across groups: FP64
+// arithmetic runs at a small fraction of the FP32 rate on this GPU.
 #include "combo_internal.cuh"
 #include "fft_fast.cuh"
 #include "../../include/combo.h"
@@ -157,113 +158,86 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
     // grid-stride over groups of LB x-lines (a few blocks per SM)
     for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
         const int L0 = grp * LB;
-        for (int e = threadIdx.x; e < LB * hn; e += blockDim.x) {
-            const int l = e / hn, x = 2 * (e - l * hn);
+        // dot products: FP32 within a thread's share of a group, FP64 across
+        // groups (FP64 arithmetic runs at a small fraction of the FP32 rate)
+        Tc accp = 0;
+        for (int e = threadIdx.x; e < LB * g.n1; e += blockDim.x) {
+            const int l = e / g.n1, x = e - l * g.n1;
             const int L = L0 + l;
             if (L >= nlines) continue;
             const int64_t v = (int64_t)L * g.n1 + x;
-            T o0[9], o1[9];
+            T o[9];
             if (a.X) {
 #pragma unroll
-                for (int c = 0; c < 9; c++) {
-                    const double2 q = ld2(a.X + c * V + v);
-                    o0[c] = (T)q.x;
-                    o1[c] = (T)q.y;
-                }
+                for (int c = 0; c < 9; c++) o[c] = (T)a.X[c * V + v];
             } else if (a.mode == XF_RESID) {
-                const uchar2 ph = *reinterpret_cast<const uchar2*>(phase + v);
-                double F0[9], F1[9];
+                const int ph = phase[v];
+                double F[9];
 #pragma unroll
-                for (int c = 0; c < 9; c++) {
-                    const double2 q = ld2(a.F + c * V + v);
-                    F0[c] = q.x;
-                    F1[c] = q.y;
-                }
-                Tc G0[10], G1[10];
+                for (int c = 0; c < 9; c++) F[c] = a.F[c * V + v];
+                if (ph == 2) {
+                    const int b = a.vox2box[v];
 #pragma unroll
-                for (int k = 0; k < 2; k++) {
-                    const int pk = k ? ph.y : ph.x;
-                    const double* F = k ? F1 : F0;
-                    T* o = k ? o1 : o0;
-                    Tc* Gc = k ? G1 : G0;
-                    if (pk == 2) {
-                        const int b = a.vox2box[v + k];
+                    for (int c = 0; c < 9; c++) o[c] = (T)a.bP[(int64_t)b * 9 + c];
+                    if (a.tc) {
 #pragma unroll
-                        for (int c = 0; c < 9; c++) o[c] = (T)a.bP[(int64_t)b * 9 + c];
-#pragma unroll
-                        for (int c = 0; c < 10; c++) Gc[c] = (Tc)0;
-                    } else {
-                        double P[9], G[9], m;
-                        if (!nh_stress(F, a.mu[pk], a.lam[pk], P, G, m)) {
-                            raise_status(a.sc, COMBO_E_INADMISSIBLE);
-#pragma unroll
-                            for (int c = 0; c < 9; c++) P[c] = G[c] = 0.0;
-                            m = 0.0;
-                        }
-#pragma unroll
-                        for (int c = 0; c < 9; c++) {
-                            o[c] = (T)P[c];
-                            Gc[c] = (Tc)G[c];
-                        }
-                        Gc[9] = (Tc)m;
+                        for (int c = 0; c < 10; c++) a.tc[c * V + v] = (Tc)0;
                     }
-                }
-                if (a.tc) {
+                } else {
+                    double P[9], G[9], m;
+                    if (!nh_stress(F, a.mu[ph], a.lam[ph], P, G, m)) {
+                        raise_status(a.sc, COMBO_E_INADMISSIBLE);
 #pragma unroll
-                    for (int c = 0; c < 10; c++) st2<Tc>(a.tc + c * V + v, G0[c], G1[c]);
+                        for (int c = 0; c < 9; c++) P[c] = G[c] = 0.0;
+                        m = 0.0;
+                    }
+#pragma unroll
+                    for (int c = 0; c < 9; c++) o[c] = (T)P[c];
+                    if (a.tc) {
+#pragma unroll
+                        for (int c = 0; c < 9; c++) a.tc[c * V + v] = (Tc)G[c];
+                        a.tc[9 * V + v] = (Tc)m;
+                    }
                 }
             } else {  // XF_TANGENT: p = r + beta p, y = A : p
-                const uchar2 ph = *reinterpret_cast<const uchar2*>(phase + v);
-                pair_t<Tc> r2[9], p2[9], t2[10];
+                // every load is issued before the phase branch
+                const int ph = phase[v];
+                Tc p[9], t[10];
 #pragma unroll
-                for (int c = 0; c < 9; c++) r2[c] = ld2(a.r + c * V + v);
+                for (int c = 0; c < 9; c++) p[c] = a.r[c * V + v];
                 if (!first) {
 #pragma unroll
-                    for (int c = 0; c < 9; c++) p2[c] = ld2(a.p + c * V + v);
+                    for (int c = 0; c < 9; c++) p[c] += beta * a.p[c * V + v];
                 }
 #pragma unroll
-                for (int c = 0; c < 10; c++) t2[c] = ld2(a.tc + c * V + v);
-                Tc p0[9], p1[9];
+                for (int c = 0; c < 10; c++) t[c] = a.tc[c * V + v];
+#pragma unroll
+                for (int c = 0; c < 9; c++) a.p[c * V + v] = p[c];
+                Tc y[9];
+                if (ph == 2) {
+                    const int64_t b = a.vox2box[v];
+#pragma unroll
+                    for (int r = 0; r < 9; r++) {
+                        Tc s = 0;
+#pragma unroll
+                        for (int c = 0; c < 9; c++) s += a.bA[(int64_t)(r * 9 + c) * a.nb + b] * p[c];
+                        y[r] = s;
+                    }
+                } else {
+                    nh_tangent<Tc>(t, t[9], (Tc)a.mu[ph], (Tc)a.lam[ph], p, y);
+                }
+                Tc s = 0;
 #pragma unroll
                 for (int c = 0; c < 9; c++) {
-                    p0[c] = first ? r2[c].x : r2[c].x + beta * p2[c].x;
-                    p1[c] = first ? r2[c].y : r2[c].y + beta * p2[c].y;
-                    st2<Tc>(a.p + c * V + v, p0[c], p1[c]);
+                    s += p[c] * y[c];
+                    o[c] = (T)y[c];
                 }
-#pragma unroll
-                for (int k = 0; k < 2; k++) {
-                    const int pk = k ? ph.y : ph.x;
-                    const Tc* p = k ? p1 : p0;
-                    T* o = k ? o1 : o0;
-                    Tc y[9];
-                    if (pk == 2) {
-                        const int64_t b = a.vox2box[v + k];
-#pragma unroll
-                        for (int r = 0; r < 9; r++) {
-                            Tc s = 0;
-#pragma unroll
-                            for (int c = 0; c < 9; c++) s += a.bA[(int64_t)(r * 9 + c) * a.nb + b] * p[c];
-                            y[r] = s;
-                        }
-                    } else {
-                        Tc G[9];
-#pragma unroll
-                        for (int c = 0; c < 9; c++) G[c] = k ? t2[c].y : t2[c].x;
-                        const Tc m = k ? t2[9].y : t2[9].x;
-                        nh_tangent<Tc>(G, m, (Tc)a.mu[pk], (Tc)a.lam[pk], p, y);
-                    }
-                    double s = 0.0;
-#pragma unroll
-                    for (int c = 0; c < 9; c++) {
-                        s += (double)p[c] * (double)y[c];
-                        o[c] = (T)y[c];
-                    }
-                    acc += s;
-                }
+                accp += s;
             }
 #pragma unroll
-            for (int c = 0; c < 9; c++) st2<T>(rb + (size_t)2 * (c * LB + l) * ls + x, o0[c], o1[c]);
+            for (int c = 0; c < 9; c++) rb[(size_t)2 * (c * LB + l) * ls + x] = o[c];
         }
+        acc += (double)accp;
         __syncthreads();
 
         const int nl = 9 * LB;
@@ -361,55 +335,48 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
         __syncthreads();
         cx<T>* Zr = xpass_fft<T, MF, true>(buf1, buf0, a.plan, nl, ls, a.tw);
         const T* rb = reinterpret_cast<const T*>(Zr);
+        Tc accp = 0;  // FP32 within the group, FP64 across groups
 
-        for (int e = threadIdx.x; e < LB * hn; e += blockDim.x) {
-            const int l = e / hn, x = 2 * (e - l * hn);
+        for (int e = threadIdx.x; e < LB * g.n1; e += blockDim.x) {
+            const int l = e / g.n1, x = e - l * g.n1;
             const int L = L0 + l;
             if (L >= nlines) continue;
             const int64_t v = (int64_t)L * g.n1 + x;
             if (a.mode == XI_CG) {
-                pair_t<Tc> x2[9], r2[9], p2[9];
+                Tc xv[9], rv[9], pv[9];
 #pragma unroll
                 for (int c = 0; c < 9; c++) {
-                    x2[c] = ld2(a.x + c * V + v);
-                    r2[c] = ld2(a.r + c * V + v);
-                    p2[c] = ld2(a.p + c * V + v);
+                    xv[c] = a.x[c * V + v];
+                    rv[c] = a.r[c * V + v];
+                    pv[c] = a.p[c * V + v];
                 }
 #pragma unroll
                 for (int c = 0; c < 9; c++) {
-                    const pair_t<T> gv = *reinterpret_cast<const pair_t<T>*>(rb + (size_t)2 * (c * LB + l) * ls + x);
-                    const Tc ra = r2[c].x - alpha * (Tc)gv.x, rbv = r2[c].y - alpha * (Tc)gv.y;
-                    st2<Tc>(a.x + c * V + v, x2[c].x + alpha * p2[c].x, x2[c].y + alpha * p2[c].y);
-                    st2<Tc>(a.r + c * V + v, ra, rbv);
-                    acc += (double)ra * (double)ra + (double)rbv * (double)rbv;
+                    const Tc gv = (Tc)rb[(size_t)2 * (c * LB + l) * ls + x];
+                    const Tc rn = rv[c] - alpha * gv;
+                    a.x[c * V + v] = xv[c] + alpha * pv[c];
+                    a.r[c * V + v] = rn;
+                    accp += rn * rn;
                 }
             } else if (a.mode == XI_FIXEDPOINT) {
                 if (skip_update) continue;
-                double2 F2[9];
 #pragma unroll
-                for (int c = 0; c < 9; c++) F2[c] = ld2(a.F + c * V + v);
-#pragma unroll
-                for (int c = 0; c < 9; c++) {
-                    const pair_t<T> gv = *reinterpret_cast<const pair_t<T>*>(rb + (size_t)2 * (c * LB + l) * ls + x);
-                    st2<double>(a.F + c * V + v, F2[c].x - (double)gv.x * a.inv_mu0, F2[c].y - (double)gv.y * a.inv_mu0);
-                }
+                for (int c = 0; c < 9; c++)
+                    a.F[c * V + v] -= (double)rb[(size_t)2 * (c * LB + l) * ls + x] * a.inv_mu0;
             } else if (a.mode == XI_RHS) {
 #pragma unroll
                 for (int c = 0; c < 9; c++) {
-                    const pair_t<T> gv = *reinterpret_cast<const pair_t<T>*>(rb + (size_t)2 * (c * LB + l) * ls + x);
-                    const Tc ra = (Tc)(-gv.x), rbv = (Tc)(-gv.y);
-                    st2<Tc>(a.r + c * V + v, ra, rbv);
-                    st2<Tc>(a.x + c * V + v, (Tc)0, (Tc)0);
-                    acc += (double)ra * (double)ra + (double)rbv * (double)rbv;
+                    const Tc rn = (Tc)(-rb[(size_t)2 * (c * LB + l) * ls + x]);
+                    a.r[c * V + v] = rn;
+                    a.x[c * V + v] = (Tc)0;
+                    accp += rn * rn;
                 }
             } else {
 #pragma unroll
-                for (int c = 0; c < 9; c++) {
-                    const pair_t<T> gv = *reinterpret_cast<const pair_t<T>*>(rb + (size_t)2 * (c * LB + l) * ls + x);
-                    st2<double>(a.Y + c * V + v, (double)gv.x, (double)gv.y);
-                }
+                for (int c = 0; c < 9; c++) a.Y[c * V + v] = (double)rb[(size_t)2 * (c * LB + l) * ls + x];
             }
         }
+        acc += (double)accp;
         __syncthreads();  // the next group reuses the shared buffers
     }
     if ((a.mode == XI_RHS || a.mode == XI_CG) && a.partial) {

@@ -125,8 +125,9 @@ __global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
         cx<T> o0{(T)0, (T)0}, o1{(T)0, (T)0}, o2{(T)0, (T)0};
         if (kk > (T)0) {
             // row i of G X: k (k . X_i) / |k|^2
-            const T sr = (k0 * X0.x + k1 * X1.x + k2 * X2.x) / kk;
-            const T si = (k0 * X0.y + k1 * X1.y + k2 * X2.y) / kk;
+            const T ik = (T)1 / kk;
+            const T sr = (k0 * X0.x + k1 * X1.x + k2 * X2.x) * ik;
+            const T si = (k0 * X0.y + k1 * X1.y + k2 * X2.y) * ik;
             o0 = cx<T>{k0 * sr, k0 * si};
             o1 = cx<T>{k1 * sr, k1 * si};
             o2 = cx<T>{k2 * sr, k2 * si};
@@ -213,8 +214,9 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<
         }
         cx<T> o0{(T)0, (T)0}, o1{(T)0, (T)0}, o2{(T)0, (T)0};
         if (kk > (T)0) {
-            const T sr = (k0 * X0.x + k1 * X1.x + k2 * X2.x) / kk;
-            const T si = (k0 * X0.y + k1 * X1.y + k2 * X2.y) / kk;
+            const T ik = (T)1 / kk;
+            const T sr = (k0 * X0.x + k1 * X1.x + k2 * X2.x) * ik;
+            const T si = (k0 * X0.y + k1 * X1.y + k2 * X2.y) * ik;
             o0 = cx<T>{k0 * sr, k0 * si};
             o1 = cx<T>{k1 * sr, k1 * si};
             o2 = cx<T>{k2 * sr, k2 * si};
