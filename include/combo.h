@@ -231,6 +231,34 @@ int combo_apply_G(combo_ctx* ctx, const int32_t n[3], const double l[3], int32_t
 int combo_constitutive(combo_ctx* ctx, const combo_problem* p, const combo_options* o, const double* F,
                        double* a_io, double* P, int32_t mem);
 
+/*
+ * combo_apply_G_noalloc: the same Green operator as combo_apply_G (FP64),
+ * for callers that cannot allocate device memory -- code that runs inside a
+ * memory arena or pool it does not own, a loop that must not allocate, or a
+ * host framework that owns all device memory.  It has no counterpart in the
+ * paper; it is a deployment variant of the Green-operator entry point.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The caller
+ * passes X and Y, [9][V] FP64 in device memory (they may be the same buffer).  The
+ * half spectrum, the reduction partials, the solver scalars and the
+ * twiddle / symbol tables live in one library-owned device array of 4 MiB,
+ * which every GPU that loads libcombo.so holds until the process exits.
+ * Limits: each side 2^a 3^b in [2, 64], n1 even, and
+ * 9 n3 n2 (n1/2 + 1 rounded up to 4) <= 259504 (every grid up to 32^3 fits);
+ * larger grids return COMBO_E_INVALID_ARG with a message.
+ *   device  CUDA device ordinal to run on (made current for the call).
+ *   stream  cudaStream_t (NULL = the default stream).
+ *   sumsq   optional host pointer: receives sum_x |Y(x)|^2; when given, the
+ *           call synchronises the stream before it returns.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Every call on a device shares the
+ * array and finds the previous call's contents there (it clears what must
+ * start at zero): calls that overlap on the GPU -- on different streams, or
+ * from several threads -- race and must be serialised by the caller.
+ */
+int combo_apply_G_noalloc(int32_t device, void* stream, const int32_t n[3], const double l[3], int32_t kspace,
+                          const double* X, double* Y, double* sumsq);
+
 #ifdef __cplusplus
 }
 #endif

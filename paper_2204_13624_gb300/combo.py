@@ -58,7 +58,7 @@ class ResultS(C.Structure):
 EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_options_default",
            "combo_solve_footprint", "combo_solve", "combo_solve_begin", "combo_solve_advance", "combo_solve_finish",
            "combo_solve_end", "combo_solve_profile", "combo_solve_profile_read", "combo_apply_G",
-           "combo_constitutive"]
+           "combo_constitutive", "combo_apply_G_noalloc"]
 
 _lib = None
 
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH):
     L.combo_apply_G.restype = C.c_int
     L.combo_constitutive.argtypes = [vp, vp, vp, vp, vp, vp, i32]
     L.combo_constitutive.restype = C.c_int
+    L.combo_apply_G_noalloc.argtypes = [i32, vp, vp, vp, i32, vp, vp, vp]
+    L.combo_apply_G_noalloc.restype = C.c_int
     _lib = L
     return L
 
@@ -340,3 +342,19 @@ def constitutive(prob: dict, F, a=None, ctx: Context | None = None, **opts):
     P = np.zeros_like(F)
     _check(load().combo_constitutive(ctx.h, C.byref(pb.s), C.byref(o), _ptr(F), _ptr(a), _ptr(P), MEM_HOST))
     return P, a[:nb]
+
+
+def apply_G_noalloc(X, Y, n, l=(1.0, 1.0, 1.0), kspace=ROTATED, device=0, stream=None, want_sumsq=True):
+    """combo_apply_G_noalloc: Y = G[X] in FP64 for callers that cannot
+    allocate device memory.  X and Y are CUDA tensors [9][V] of float64
+    owned by the caller (they may be the same tensor); the library's
+    scratch is a fixed 4 MiB device array (grids up to 32^3).  Returns
+    sum |Y|^2 (synchronising the stream) or None."""
+    if not (_is_dev(X) and _is_dev(Y)):
+        raise ComboError(-1, "apply_G_noalloc takes CUDA tensors")
+    nn = (C.c_int32 * 3)(*[int(v) for v in n])
+    ll = (C.c_double * 3)(*[float(v) for v in l])
+    ss = C.c_double(0.0)
+    _check(load().combo_apply_G_noalloc(int(device), stream, nn, ll, int(kspace), _ptr(X), _ptr(Y),
+                                        C.byref(ss) if want_sumsq else None))
+    return ss.value if want_sumsq else None

@@ -356,6 +356,9 @@ int xpass_grid(const GridDims& g, int lines);  // x-pass blocks (= partial count
 int ypass_tx(int n, size_t cxbytes);  // columns per y-pass block (must match the launcher)
 int zpass_tx(int n, size_t cxbytes);  // columns per z-pass block (sets the partial count)
 
+// Record msg as the calling thread's last error; returns code.
+int set_error(int code, const char* msg);
+
 // boxel laminate Newton solve
 template <typename Tc> struct BoxelArgs {
     int64_t nb;

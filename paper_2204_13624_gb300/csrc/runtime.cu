@@ -38,6 +38,13 @@ static int fail(int code, const std::string& msg)
 
 extern "C" const char* combo_last_error(void) { return g_err.c_str(); }
 
+// Lets other translation units of the library report an error message.
+int combo::set_error(int code, const char* msg)
+{
+    g_err = msg;
+    return code;
+}
+
 // ------------------------------------------------------------------ context
 struct combo_ctx {
     int device;
