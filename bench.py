@@ -131,12 +131,13 @@ def algorithmic_bytes(kernel, p, krylov_bytes):
     if kernel in ("yfwd_fp64", "zgamma_fp64", "yinv_fp64"):
         return 2 * spec_c * 16
     if kernel == "xfwd_tangent":
-        # r, p read; p written; tangent cache (9 + 1 words) at pure voxels; phase byte;
-        # boxel index and 81-entry tangent at boxels; spectrum written
-        return V * (27 * w + 1) + (V - nb) * 10 * w + nb * (4 + 81 * w) + spec_c * 2 * w
+        # r, p, x read; p, x written (x += alpha p of the previous iteration);
+        # tangent cache (9 + 1 words) at pure voxels; phase byte; boxel index and
+        # 81-entry tangent at boxels; spectrum written
+        return V * (45 * w + 1) + (V - nb) * 10 * w + nb * (4 + 81 * w) + spec_c * 2 * w
     if kernel == "xinv_cg":
-        # spectrum read; x, r read + written; p read
-        return spec_c * 2 * w + V * 45 * w
+        # spectrum read; r read + written
+        return spec_c * 2 * w + V * 18 * w
     if kernel == "xfwd_resid_fp64":
         # F read (FP64), phase, P_box at boxels, tangent cache written, spectrum written
         return V * (72 + 1) + nb * (4 + 72) + (V - nb) * 10 * w + spec_c * 16

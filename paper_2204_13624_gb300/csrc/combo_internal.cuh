@@ -58,6 +58,7 @@ struct Scalars {
     unsigned long long nr_iters, n_backproj, n_lam;
     unsigned long long n_operator, n_operator64;
     unsigned int ticket[4];  // last-block counters of fused reductions
+    double alpha_pending;    // x += alpha_pending p still owed by the last CG update
 };
 
 // ---------------------------------------------------------------- FFT core
@@ -244,9 +245,13 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket, int* flag_smem)
 
 // CG scalars (called by one thread).  Loss of positive curvature stops CG
 // with the current iterate.
+// The x update of iteration k (x += alpha_k p_k) is applied by the tangent
+// x-pass of iteration k+1, which reads p_k anyway; alpha_pending records the
+// update still owed (the F update applies it when CG stops).
 __device__ __forceinline__ void cg_alpha(Scalars* sc, double pAp)
 {
     sc->pAp = pAp;
+    sc->alpha_pending = 0.0;  // the owed update was applied by this pass
     if (!(pAp > 0.0)) {
         sc->cg_done = 1;
         return;
@@ -256,6 +261,7 @@ __device__ __forceinline__ void cg_alpha(Scalars* sc, double pAp)
 
 __device__ __forceinline__ void cg_beta(Scalars* sc, double rr_new, double cg_tol, int cg_max, int cg_fixed)
 {
+    sc->alpha_pending = sc->alpha;
     sc->beta = rr_new / sc->rr;
     sc->rr = rr_new;
     const int j = sc->cg_iter + 1;
@@ -291,6 +297,7 @@ template <typename T, typename Tc> struct XfwdArgs {
     // XF_TANGENT
     const Tc* r;
     Tc* p;
+    Tc* x;               // receives the previous iteration's x += alpha p
     const Tc* bA;        // [81][nb]
     int64_t nb;
     // plain operand (no constitutive law): X [9][V] real

@@ -497,18 +497,23 @@ __global__ void k_fin_rhs(Scalars* sc, const double* part, int n, int cg_fixed, 
     sc->rr0 = s;
     sc->cg_iter = 0;
     sc->beta = 0.0;
+    sc->alpha_pending = 0.0;
     const bool stop = (cg_fixed <= 0) && (cg_max <= 0);
     sc->cg_done = (s == 0.0 || stop) ? 1 : 0;
 }
 
-// F += d * x, then admissibility (det F > 0) of every voxel
-template <typename Tc> __global__ void k_update_F(double* F, const Tc* x, double d, int64_t V, Scalars* sc)
+// F += d * (x + alpha_pending p) -- the CG solution including the update the
+// last CG iteration still owes -- then admissibility (det F > 0) of every voxel
+template <typename Tc>
+__global__ void k_update_F(double* F, const Tc* x, const Tc* p, double d, int64_t V, Scalars* sc)
 {
+    const Tc ap = (Tc)sc->alpha_pending;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
         double f[9];
 #pragma unroll
         for (int c = 0; c < 9; c++) {
-            f[c] = F[c * V + v] + d * (double)x[c * V + v];
+            const Tc xv = (ap != (Tc)0) ? x[c * V + v] + ap * p[c * V + v] : x[c * V + v];
+            f[c] = F[c * V + v] + d * (double)xv;
             F[c * V + v] = f[c];
         }
         const double J = f[0] * (f[4] * f[8] - f[5] * f[7]) - f[1] * (f[3] * f[8] - f[5] * f[6]) +
@@ -879,6 +884,7 @@ template <typename Tc> struct Solve : SolveBase {
         xf.tc = d_tc;
         xf.r = d_r;
         xf.p = d_p;
+        xf.x = d_x;
         xf.bA = d_bA;
         xf.nb = std::max<int64_t>(nb, 1);
         xf.partial = d_part;
@@ -1022,7 +1028,7 @@ template <typename Tc> struct Solve : SolveBase {
                     for (int h = 0; h <= 10; h++) {
                         if ((rc = set_flag(offsetof(Scalars, admissible), 1))) return error = rc;
                         prof.begin(K_UPDATE);
-                        k_update_F<Tc><<<grid_for(g.V), 256, 0, st>>>(d_F, d_x, d, g.V, d_sc);
+                        k_update_F<Tc><<<grid_for(g.V), 256, 0, st>>>(d_F, d_x, d_p, d, g.V, d_sc);
                         prof.end();
                         if ((rc = read_scalars(s))) return error = rc;
                         if (s.admissible) {

@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
 
     const bool first = (a.mode == XF_TANGENT) ? (a.sc->cg_iter == 0) : false;
     const Tc beta = (a.mode == XF_TANGENT && !first) ? (Tc)a.sc->beta : (Tc)0;
+    const Tc apend = (a.mode == XF_TANGENT && !first) ? (Tc)a.sc->alpha_pending : (Tc)0;
     const uint8_t* __restrict__ phase = a.phase;
 
     // grid-stride over groups of LB x-lines (a few blocks per SM)
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
                         a.tc[9 * V + v] = (Tc)m;
                     }
                 }
-            } else {  // XF_TANGENT: p = r + beta p, y = A : p
+            } else {  // XF_TANGENT: x += alpha_prev p, p = r + beta p, y = A : p
                 // every load is issued before the phase branch
                 const int ph = phase[v];
                 Tc p[9], t[10];
@@ -207,7 +208,11 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
                 for (int c = 0; c < 9; c++) p[c] = a.r[c * V + v];
                 if (!first) {
 #pragma unroll
-                    for (int c = 0; c < 9; c++) p[c] += beta * a.p[c * V + v];
+                    for (int c = 0; c < 9; c++) {
+                        const Tc po = a.p[c * V + v];
+                        if (apend != (Tc)0) a.x[c * V + v] += apend * po;
+                        p[c] += beta * po;
+                    }
                 }
 #pragma unroll
                 for (int c = 0; c < 10; c++) t[c] = a.tc[c * V + v];
@@ -343,18 +348,15 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
             if (L >= nlines) continue;
             const int64_t v = (int64_t)L * g.n1 + x;
             if (a.mode == XI_CG) {
-                Tc xv[9], rv[9], pv[9];
+                // r -= alpha q; the matching x += alpha p is done by the next
+                // tangent x-pass (or the F update when CG stops)
+                Tc rv[9];
 #pragma unroll
-                for (int c = 0; c < 9; c++) {
-                    xv[c] = a.x[c * V + v];
-                    rv[c] = a.r[c * V + v];
-                    pv[c] = a.p[c * V + v];
-                }
+                for (int c = 0; c < 9; c++) rv[c] = a.r[c * V + v];
 #pragma unroll
                 for (int c = 0; c < 9; c++) {
                     const Tc gv = (Tc)rb[(size_t)2 * (c * LB + l) * ls + x];
                     const Tc rn = rv[c] - alpha * gv;
-                    a.x[c * V + v] = xv[c] + alpha * pv[c];
                     a.r[c * V + v] = rn;
                     accp += rn * rn;
                 }
