@@ -53,6 +53,7 @@ extern "C" {
 #define COMBO_E_NAN (-6)
 #define COMBO_E_TIMEOUT (-7)
 #define COMBO_E_CUDA (-8)
+#define COMBO_E_CANCELLED (-9)
 
 /* Where the pointers of a problem / result live. */
 #define COMBO_MEM_HOST 0
@@ -202,6 +203,56 @@ int combo_solve_begin(combo_ctx* ctx, const combo_problem* p, const combo_option
 int combo_solve_advance(combo_solve_state* s, int64_t max_operator);
 int combo_solve_finish(combo_solve_state* s, combo_result* r);
 void combo_solve_end(combo_solve_state* s);
+
+/*
+ * Serving: a request loop for many solves of different grid sizes,
+ * microstructures and load paths (no counterpart in the paper, which solves
+ * one RVE at a time; each request is the problem of Sec. 2).
+ *   combo_server_create  starts max_slots worker slots on ctx's device, each
+ *                        with its own CUDA stream.  hbm_budget_bytes (<= 0:
+ *                        85 % of the free device memory) bounds the sum of
+ *                        the footprints (combo_solve_footprint) of the
+ *                        running solves.  keep_fields: also keep F and P of
+ *                        every finished request for combo_poll / combo_wait.
+ *   combo_submit         validates and copies the problem (the caller may
+ *                        free it on return) and queues it; returns a ticket.
+ *                        A solve larger than the whole budget: COMBO_E_OOM.
+ *   scheduling           a free slot admits the oldest queued request that
+ *                        fits the memory left; each admitted solve keeps its
+ *                        fields and iteration state on the device until it
+ *                        finishes; requests arriving while others run are
+ *                        admitted as slots and memory free up, and the running
+ *                        solves' kernels overlap on the device.
+ *   combo_poll           COMBO_PENDING while running, else writes the result
+ *                        (host pointers; the mem field is ignored) and
+ *                        releases the ticket, returning the solve's status.
+ *   combo_wait           same, blocking up to timeout_ms (< 0: forever);
+ *                        COMBO_E_TIMEOUT if not finished in time (the ticket
+ *                        stays valid).
+ *   combo_cancel         a queued request finishes with COMBO_E_CANCELLED; a
+ *                        running one stops at its next host round trip.
+ *   combo_server_stats   counts and submit-to-completion latency percentiles
+ *                        of the completed requests.
+ *   combo_server_destroy cancels what is queued or running and joins the slots.
+ */
+typedef struct combo_server combo_server;
+typedef struct {
+    int32_t max_slots;
+    int64_t hbm_budget_bytes;
+    int32_t keep_fields;
+} combo_server_opts;
+typedef struct {
+    int64_t submitted, completed, failed, queued, running, peak_running;
+    int64_t in_use_bytes, budget_bytes;
+    double p50_seconds, p99_seconds, mean_seconds;
+} combo_serving_stats;
+int combo_server_create(combo_ctx* ctx, const combo_server_opts* opts, combo_server** out);
+void combo_server_destroy(combo_server* s);
+int combo_submit(combo_server* s, const combo_problem* p, const combo_options* o, int64_t* ticket);
+int combo_poll(combo_server* s, int64_t ticket, combo_result* r);
+int combo_wait(combo_server* s, int64_t ticket, int64_t timeout_ms, combo_result* r);
+int combo_cancel(combo_server* s, int64_t ticket);
+int combo_server_stats(combo_server* s, combo_serving_stats* st);
 
 /*
  * Per-kernel timing of a solve (instrumentation, no effect on results).

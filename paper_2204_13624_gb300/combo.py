@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libcombo.so")
 
 OK, PENDING = 0, 1
 E_NAMES = {-1: "invalid argument", -2: "out of memory", -3: "not converged", -4: "laminate Newton failed",
-           -5: "inadmissible (det F <= 0)", -6: "NaN", -7: "timeout", -8: "CUDA error"}
+           -5: "inadmissible (det F <= 0)", -6: "NaN", -7: "timeout", -8: "CUDA error", -9: "cancelled"}
 FP64, FP32_REFINED = 0, 1
 ROTATED, SPECTRAL = 0, 1
 FIXED_POINT, NEWTON_CG = 0, 1
@@ -58,7 +58,8 @@ class ResultS(C.Structure):
 EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_options_default",
            "combo_solve_footprint", "combo_solve", "combo_solve_begin", "combo_solve_advance", "combo_solve_finish",
            "combo_solve_end", "combo_solve_profile", "combo_solve_profile_read", "combo_apply_G",
-           "combo_constitutive", "combo_apply_G_noalloc"]
+           "combo_constitutive", "combo_apply_G_noalloc", "combo_server_create", "combo_server_destroy",
+           "combo_submit", "combo_poll", "combo_wait", "combo_cancel", "combo_server_stats"]
 
 _lib = None
 
@@ -358,3 +359,117 @@ def apply_G_noalloc(X, Y, n, l=(1.0, 1.0, 1.0), kspace=ROTATED, device=0, stream
     _check(load().combo_apply_G_noalloc(int(device), stream, nn, ll, int(kspace), _ptr(X), _ptr(Y),
                                         C.byref(ss) if want_sumsq else None))
     return ss.value if want_sumsq else None
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("keep_fields", C.c_int32)]
+
+
+class ServingStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("queued", C.c_int64),
+                ("running", C.c_int64), ("peak_running", C.c_int64), ("in_use_bytes", C.c_int64),
+                ("budget_bytes", C.c_int64), ("p50_seconds", C.c_double), ("p99_seconds", C.c_double),
+                ("mean_seconds", C.c_double)]
+
+
+def _server_lib():
+    L = load()
+    if not getattr(L, "_server_bound", False):
+        vp, i64 = C.c_void_p, C.c_int64
+        L.combo_server_create.argtypes = [vp, vp, C.POINTER(vp)]
+        L.combo_server_create.restype = C.c_int
+        L.combo_server_destroy.argtypes = [vp]
+        L.combo_submit.argtypes = [vp, vp, vp, C.POINTER(i64)]
+        L.combo_submit.restype = C.c_int
+        L.combo_poll.argtypes = [vp, i64, vp]
+        L.combo_poll.restype = C.c_int
+        L.combo_wait.argtypes = [vp, i64, i64, vp]
+        L.combo_wait.restype = C.c_int
+        L.combo_cancel.argtypes = [vp, i64]
+        L.combo_cancel.restype = C.c_int
+        L.combo_server_stats.argtypes = [vp, vp]
+        L.combo_server_stats.restype = C.c_int
+        L._server_bound = True
+    return L
+
+
+class Server:
+    """Request loop over many solves (combo_server_*): submit problems as they
+    arrive, poll or wait for results; admitted solves run concurrently in
+    worker slots on their own streams, admission bounded by device memory."""
+
+    def __init__(self, ctx: Context | None = None, max_slots: int = 4, hbm_budget_bytes: int = 0,
+                 keep_fields: bool = False):
+        L = _server_lib()
+        self.ctx = ctx or default_context()
+        o = ServerOpts(max_slots, hbm_budget_bytes, 1 if keep_fields else 0)
+        h = C.c_void_p()
+        _check(L.combo_server_create(self.ctx.h, C.byref(o), C.byref(h)))
+        self.h = h
+        self.keep_fields = keep_fields
+        self._meta = {}
+
+    def submit(self, prob: dict, **opts) -> int:
+        pb = Problem(prob)
+        o = options(**opts)
+        t = C.c_int64(0)
+        _check(_server_lib().combo_submit(self.h, C.byref(pb.s), C.byref(o), C.byref(t)))
+        self._meta[t.value] = (pb.n_steps, pb.V)
+        return t.value
+
+    def _buffers(self, ticket):
+        S, V = self._meta[ticket]
+        out = dict(Pbar=np.zeros((S, 9)), iters=np.zeros(S, np.int32), cg_iters=np.zeros(S, np.int32),
+                   resid=np.zeros(S))
+        r = ResultS()
+        r.Pbar, r.iters, r.cg_iters, r.resid = (_ptr(out[k]) for k in ("Pbar", "iters", "cg_iters", "resid"))
+        if self.keep_fields:
+            out["F"] = np.zeros((9, V))
+            out["P"] = np.zeros((9, V))
+            r.F_out, r.P_out = _ptr(out["F"]), _ptr(out["P"])
+        return out, r
+
+    def _finish(self, ticket, out, r):
+        del self._meta[ticket]
+        out.update(steps_done=r.steps_done, nr_iters=r.nr_iters, n_backproj=r.n_backproj, n_operator=r.n_operator,
+                   n_operator_fp64=r.n_operator_fp64)
+        return out
+
+    def poll(self, ticket: int):
+        """None while the request runs, else its result dict (raises on failure)."""
+        out, r = self._buffers(ticket)
+        rc = _server_lib().combo_poll(self.h, ticket, C.byref(r))
+        if rc == PENDING:
+            return None
+        if rc < 0:
+            self._meta.pop(ticket, None)
+            _check(rc)
+        return self._finish(ticket, out, r)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        out, r = self._buffers(ticket)
+        rc = _server_lib().combo_wait(self.h, ticket, int(timeout_ms), C.byref(r))
+        if rc < 0:
+            if rc != -7:
+                self._meta.pop(ticket, None)
+            _check(rc)
+        return self._finish(ticket, out, r)
+
+    def cancel(self, ticket: int):
+        _check(_server_lib().combo_cancel(self.h, ticket))
+
+    def stats(self) -> dict:
+        st = ServingStats()
+        _check(_server_lib().combo_server_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServingStats._fields_}
+
+    def close(self):
+        if self.h:
+            _server_lib().combo_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

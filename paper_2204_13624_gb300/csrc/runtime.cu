@@ -677,6 +677,7 @@ struct SolveBase {
     virtual int advance(int64_t max_ops) = 0;
     virtual int finish(combo_result* r) = 0;
     virtual Profiler& profiler() = 0;
+    virtual void request_cancel() = 0;
 };
 
 struct combo_solve_state {
@@ -705,6 +706,10 @@ template <typename Tc> struct Solve : SolveBase {
     Scalars* d_sc = nullptr;
     double mu0 = 0.0;
     Profiler prof;
+    static constexpr int kCgChunk = 8;
+    cudaGraphExec_t cg_exec = nullptr;
+    int64_t cg_chunks_run = 0;
+    volatile int cancel_requested = 0;  // set by the server; checked between chunks
     // host state machine
     enum { ST_STEP, ST_RESID, ST_CG, ST_UPDATE, ST_FP, ST_DONE } state = ST_STEP;
     int step = 0;  // completed load steps
@@ -734,6 +739,7 @@ template <typename Tc> struct Solve : SolveBase {
         cudaFree(d_p);
         cudaFree(d_part);
         cudaFree(d_sc);
+        if (cg_exec) cudaGraphExecDestroy(cg_exec);
         e64.release();
         ec.release();
     }
@@ -910,6 +916,24 @@ template <typename Tc> struct Solve : SolveBase {
         prof.end();
     }
 
+    // capture one chunk of kCgChunk CG iterations (kernel arguments are fixed
+    // for the life of the solve; control flow is on device flags)
+    int capture_cg_chunk()
+    {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < kCgChunk; k++) cg_iteration();
+        const cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (e != cudaSuccess) return fail(COMBO_E_CUDA, std::string("CG graph capture: ") + cudaGetErrorString(e));
+        const cudaError_t e2 = cudaGraphInstantiate(&cg_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e2 != cudaSuccess) {
+            cg_exec = nullptr;
+            return fail(COMBO_E_CUDA, std::string("CG graph instantiate: ") + cudaGetErrorString(e2));
+        }
+        return COMBO_OK;
+    }
+
     int read_scalars(Scalars& s)
     {
         CK(cudaMemcpyAsync(&s, d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
@@ -966,6 +990,7 @@ template <typename Tc> struct Solve : SolveBase {
         while (true) {
             if (state == ST_DONE) return COMBO_OK;
             if (ops_done >= limit) return COMBO_PENDING;
+            if (cancel_requested) return error = fail(COMBO_E_CANCELLED, "solve cancelled");
             switch (state) {
                 case ST_STEP:
                     if (step >= hp.n_steps) {
@@ -1010,8 +1035,16 @@ template <typename Tc> struct Solve : SolveBase {
                     break;
                 }
                 case ST_CG: {
-                    const int chunk = 8;
-                    for (int k = 0; k < chunk; k++) cg_iteration();
+                    // 8 CG iterations per host round trip; iterations after the
+                    // device-side stop test are no-ops.  Without per-kernel
+                    // timing the chunk is replayed from a captured CUDA graph.
+                    if (prof.on || cg_chunks_run == 0) {
+                        for (int k = 0; k < kCgChunk; k++) cg_iteration();
+                    } else {
+                        if (!cg_exec && (rc = capture_cg_chunk())) return error = rc;
+                        CK(cudaGraphLaunch(cg_exec, st));
+                    }
+                    cg_chunks_run++;
                     CK(cudaGetLastError());
                     if ((rc = read_scalars(s))) return error = rc;
                     ops_done = (int64_t)s.n_operator;
@@ -1049,6 +1082,7 @@ template <typename Tc> struct Solve : SolveBase {
     }
 
     Profiler& profiler() override { return prof; }
+    void request_cancel() override { cancel_requested = 1; }
 
     int finish(combo_result* r) override
     {
@@ -1342,6 +1376,372 @@ extern "C" int combo_constitutive(combo_ctx* ctx, const combo_problem* p, const 
         for (int64_t k = 0; k < s.nb; k++)
             for (int i = 0; i < 3; i++) a_all[3 * pos[k] + i] = a_kept[3 * k + i];
         CK(cudaMemcpy(a_io, a_all.data(), 24 * nb_in, dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    }
+    return COMBO_OK;
+}
+
+// ------------------------------------------------------------------ serving
+// A request loop for many solves of different sizes.  submit() validates and
+// copies a problem and queues it; a slot (worker thread with its own CUDA
+// stream) admits the oldest queued request whose device footprint fits the
+// memory left in the budget, keeps that solve's fields and state resident,
+// and runs it to completion; a request that arrives while others run is
+// admitted as soon as a slot and memory are free, and the admitted solves'
+// kernels overlap on the device through their streams.  Latencies (submit to
+// completion) give p50 / p99.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+
+namespace {
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int64_t footprint_of(const HostProblem& h, const combo_options& o)
+{
+    const GridDims g = make_dims(h.n);
+    const int64_t V = g.V;
+    const int64_t nb = std::max<int64_t>((int64_t)h.bidx.size(), 1);
+    const int64_t tc = (o.precision == COMBO_FP32_REFINED) ? 4 : 8;
+    int64_t b = V * (1 + 4 + 72) + 16 * 9 * g.Vs + nb * (4 + 24 + 8 + 24 + 72) + (1 << 20);
+    if (o.solver == COMBO_NEWTON_CG) b += tc * (81 * nb + 37 * V);
+    return b;
+}
+
+struct ServeReq {
+    int64_t id = 0;
+    HostProblem hp;
+    combo_options opt;
+    int64_t footprint = 0;
+    enum { QUEUED, RUNNING, DONE } st = QUEUED;
+    int rc = 0;
+    std::string err;
+    std::vector<double> Pbar, resid, F, P;
+    std::vector<int32_t> iters, cg;
+    combo_result res{};
+    double t_submit = 0, t_start = 0, t_done = 0;
+    SolveBase* live = nullptr;
+    bool cancel = false;
+};
+
+}  // namespace
+
+struct combo_server {
+    int device = 0;
+    int slots = 1;
+    int64_t budget = 0;
+    int keep_fields = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<ServeReq*> queue;
+    std::map<int64_t, ServeReq*> reqs;
+    int64_t next_id = 1, in_use = 0, submitted = 0, completed = 0, failed = 0;
+    int running = 0, peak_running = 0;
+    bool stopping = false;
+    std::vector<double> latency;
+    std::vector<std::thread> workers;
+};
+
+static ServeReq* pick_request(combo_server* S)
+{
+    for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+        ServeReq* r = *it;
+        if (S->in_use + r->footprint <= S->budget || S->running == 0) {
+            S->queue.erase(it);
+            return r;
+        }
+    }
+    return nullptr;
+}
+
+static void run_request(ServeReq* r, combo_ctx* wctx, combo_server* S)
+{
+    SolveBase* impl = nullptr;
+    int rc;
+    const int32_t n_steps = r->hp.n_steps;
+    const int64_t V = (int64_t)r->hp.n[0] * r->hp.n[1] * r->hp.n[2];
+    if (r->opt.precision == COMBO_FP64) {
+        auto* s = new Solve<double>();
+        rc = s->init(wctx, std::move(r->hp), r->opt);
+        impl = s;
+    } else {
+        auto* s = new Solve<float>();
+        rc = s->init(wctx, std::move(r->hp), r->opt);
+        impl = s;
+    }
+    const bool inited = (rc == 0);
+    if (inited) {
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            r->live = impl;
+            if (r->cancel) impl->request_cancel();
+        }
+        rc = impl->advance(0);
+    }
+    const std::string msg = g_err;
+    r->Pbar.assign(9 * (size_t)n_steps, 0.0);
+    r->resid.assign(n_steps, 0.0);
+    r->iters.assign(n_steps, 0);
+    r->cg.assign(n_steps, 0);
+    combo_result res{};
+    res.Pbar = r->Pbar.data();
+    res.resid = r->resid.data();
+    res.iters = r->iters.data();
+    res.cg_iters = r->cg.data();
+    res.mem = COMBO_MEM_HOST;
+    if (S->keep_fields && !rc) {
+        r->F.assign(9 * (size_t)V, 0.0);
+        r->P.assign(9 * (size_t)V, 0.0);
+        res.F_out = r->F.data();
+        res.P_out = r->P.data();
+    }
+    const int rc2 = inited ? impl->finish(&res) : rc;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        r->live = nullptr;
+    }
+    delete impl;
+    r->res = res;
+    r->res.Pbar = nullptr;
+    r->res.F_out = r->res.P_out = nullptr;
+    r->res.resid = nullptr;
+    r->res.iters = r->res.cg_iters = nullptr;
+    r->rc = rc ? rc : (rc2 < 0 ? rc2 : 0);
+    r->err = rc ? msg : g_err;
+    if (rc == COMBO_E_CUDA && msg.find("memory") != std::string::npos) r->rc = COMBO_E_OOM;
+}
+
+static void server_worker(combo_server* S)
+{
+    cudaSetDevice(S->device);
+    combo_ctx wctx;
+    wctx.device = S->device;
+    wctx.own_stream = true;
+    if (cudaStreamCreateWithFlags(&wctx.stream, cudaStreamNonBlocking) != cudaSuccess) wctx.stream = nullptr;
+    for (;;) {
+        ServeReq* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] {
+                if (S->stopping) return true;
+                r = pick_request(S);
+                return r != nullptr;
+            });
+            if (!r) break;  // stopping
+            r->st = ServeReq::RUNNING;
+            r->t_start = now_s();
+            S->in_use += r->footprint;
+            S->running++;
+            S->peak_running = std::max(S->peak_running, S->running);
+        }
+        run_request(r, &wctx, S);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            r->st = ServeReq::DONE;
+            r->t_done = now_s();
+            S->in_use -= r->footprint;
+            S->running--;
+            if (r->rc == 0) {
+                S->completed++;
+                S->latency.push_back(r->t_done - r->t_submit);
+            } else {
+                S->failed++;
+            }
+        }
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+    if (wctx.stream) cudaStreamDestroy(wctx.stream);
+}
+
+extern "C" int combo_server_create(combo_ctx* ctx, const combo_server_opts* o, combo_server** out)
+{
+    if (!ctx || !out) return fail(COMBO_E_INVALID_ARG, "null context or output");
+    CK(cudaSetDevice(ctx->device));
+    combo_server* S = new combo_server();
+    S->device = ctx->device;
+    S->slots = (o && o->max_slots > 0) ? o->max_slots : 4;
+    S->keep_fields = o ? o->keep_fields : 0;
+    if (o && o->hbm_budget_bytes > 0) {
+        S->budget = o->hbm_budget_bytes;
+    } else {
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        S->budget = (int64_t)(0.85 * (double)fr);
+    }
+    for (int i = 0; i < S->slots; i++) S->workers.emplace_back(server_worker, S);
+    *out = S;
+    return COMBO_OK;
+}
+
+extern "C" void combo_server_destroy(combo_server* S)
+{
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stopping = true;
+        for (ServeReq* r : S->queue) {
+            r->st = ServeReq::DONE;
+            r->rc = COMBO_E_CANCELLED;
+        }
+        S->queue.clear();
+        for (auto& kv : S->reqs)
+            if (kv.second->live) kv.second->live->request_cancel();
+    }
+    S->cv_work.notify_all();
+    for (auto& t : S->workers) t.join();
+    for (auto& kv : S->reqs) delete kv.second;
+    delete S;
+}
+
+extern "C" int combo_submit(combo_server* S, const combo_problem* p, const combo_options* o_in, int64_t* ticket)
+{
+    if (!S || !ticket) return fail(COMBO_E_INVALID_ARG, "null server or ticket");
+    combo_options o;
+    if (o_in)
+        o = *o_in;
+    else
+        combo_options_default(&o);
+    int rc = check_options(o);
+    if (rc) return rc;
+    ServeReq* r = new ServeReq();
+    if ((rc = load_problem(p, &o, r->hp))) {
+        delete r;
+        return rc;
+    }
+    r->opt = o;
+    r->footprint = footprint_of(r->hp, o);
+    if (r->footprint > S->budget) {
+        delete r;
+        return fail(COMBO_E_OOM, "the solve does not fit the server's device-memory budget");
+    }
+    r->t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stopping) {
+            delete r;
+            return fail(COMBO_E_INVALID_ARG, "server is stopping");
+        }
+        r->id = S->next_id++;
+        S->reqs[r->id] = r;
+        S->queue.push_back(r);
+        S->submitted++;
+        *ticket = r->id;
+    }
+    S->cv_work.notify_one();
+    return COMBO_OK;
+}
+
+// copy a finished request into the caller's result (host memory) and release it
+static int collect(combo_server* S, ServeReq* r, combo_result* out)
+{
+    int rc = r->rc;
+    if (out) {
+        const int32_t ns = (int32_t)r->iters.size();
+        if (out->Pbar && !r->Pbar.empty()) std::memcpy(out->Pbar, r->Pbar.data(), 8 * r->Pbar.size());
+        if (out->iters && ns) std::memcpy(out->iters, r->iters.data(), 4 * (size_t)ns);
+        if (out->cg_iters && ns) std::memcpy(out->cg_iters, r->cg.data(), 4 * (size_t)ns);
+        if (out->resid && ns) std::memcpy(out->resid, r->resid.data(), 8 * (size_t)ns);
+        if (out->F_out && !r->F.empty()) std::memcpy(out->F_out, r->F.data(), 8 * r->F.size());
+        if (out->P_out && !r->P.empty()) std::memcpy(out->P_out, r->P.data(), 8 * r->P.size());
+        out->steps_done = r->res.steps_done;
+        out->nr_iters = r->res.nr_iters;
+        out->n_backproj = r->res.n_backproj;
+        out->n_laminate_evals = r->res.n_laminate_evals;
+        out->n_operator = r->res.n_operator;
+        out->n_operator_fp64 = r->res.n_operator_fp64;
+    }
+    if (rc) g_err = r->err.empty() ? "request failed" : r->err;
+    S->reqs.erase(r->id);
+    delete r;
+    return rc;
+}
+
+extern "C" int combo_poll(combo_server* S, int64_t ticket, combo_result* out)
+{
+    if (!S) return fail(COMBO_E_INVALID_ARG, "null server");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(COMBO_E_INVALID_ARG, "unknown ticket");
+    if (it->second->st != ServeReq::DONE) return COMBO_PENDING;
+    return collect(S, it->second, out);
+}
+
+extern "C" int combo_wait(combo_server* S, int64_t ticket, int64_t timeout_ms, combo_result* out)
+{
+    if (!S) return fail(COMBO_E_INVALID_ARG, "null server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(COMBO_E_INVALID_ARG, "unknown ticket");
+    ServeReq* r = it->second;
+    auto done = [&] { return r->st == ServeReq::DONE; };
+    if (timeout_ms < 0)
+        S->cv_done.wait(lk, done);
+    else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done))
+        return fail(COMBO_E_TIMEOUT, "request not finished within the timeout");
+    return collect(S, r, out);
+}
+
+extern "C" int combo_cancel(combo_server* S, int64_t ticket)
+{
+    if (!S) return fail(COMBO_E_INVALID_ARG, "null server");
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(ticket);
+        if (it == S->reqs.end()) return fail(COMBO_E_INVALID_ARG, "unknown ticket");
+        ServeReq* r = it->second;
+        if (r->st == ServeReq::QUEUED) {
+            for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
+                if (*q == r) {
+                    S->queue.erase(q);
+                    break;
+                }
+            r->st = ServeReq::DONE;
+            r->rc = COMBO_E_CANCELLED;
+            r->err = "cancelled before it started";
+            S->failed++;
+        } else if (r->st == ServeReq::RUNNING) {
+            r->cancel = true;
+            if (r->live) r->live->request_cancel();
+        }
+    }
+    S->cv_done.notify_all();
+    return COMBO_OK;
+}
+
+extern "C" int combo_server_stats(combo_server* S, combo_serving_stats* st)
+{
+    if (!S || !st) return fail(COMBO_E_INVALID_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    std::memset(st, 0, sizeof(*st));
+    st->submitted = S->submitted;
+    st->completed = S->completed;
+    st->failed = S->failed;
+    st->queued = (int64_t)S->queue.size();
+    st->running = S->running;
+    st->peak_running = S->peak_running;
+    st->in_use_bytes = S->in_use;
+    st->budget_bytes = S->budget;
+    if (!S->latency.empty()) {
+        std::vector<double> l = S->latency;
+        std::sort(l.begin(), l.end());
+        auto pct = [&](double q) {
+            const double pos = q * (double)(l.size() - 1);
+            const size_t i = (size_t)pos;
+            const double f = pos - (double)i;
+            return (i + 1 < l.size()) ? l[i] * (1 - f) + l[i + 1] * f : l[i];
+        };
+        st->p50_seconds = pct(0.5);
+        st->p99_seconds = pct(0.99);
+        double s = 0;
+        for (double v : l) s += v;
+        st->mean_seconds = s / (double)l.size();
     }
     return COMBO_OK;
 }
