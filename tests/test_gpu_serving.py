@@ -28,7 +28,7 @@ def mix_problems():
         Fb = np.eye(3) + np.diag(rng.uniform(-0.05, 0.05, 3))
         Fb[0, 1] += rng.uniform(-0.05, 0.05)
         if i % 2 == 0:
-            p = ms.random_spheres(n, max(2.5, min(n) / 6), 0.15, 100 + i, 10.0, Fb, 1 + i % 3)
+            p = ms.random_spheres(n, max(3.0, min(n) / 6), 0.08, 100 + i, 10.0, Fb, 1 + i % 3)
         else:
             p = ms.random_boxels(n, seed=200 + i, contrast=10.0, Fbar=Fb, n_steps=1 + i % 3)
         out.append(p)
