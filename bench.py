@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--shape", default=None, help="n1,n2,n3 of a smaller ball grid (profiling captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="serving stream of sides 64..256 and 1..10 load steps (takes minutes)")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel table here")
     return ap.parse_args()
 
@@ -292,6 +295,13 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(p)
+    serving = None
+    if not args.no_serving and rank == 0:
+        if args.serve_full:
+            serving = serving_bench(combo, ctx, count=24, sides=(64, 72, 96, 108, 128, 144, 192, 216, 256),
+                                    max_steps=10)
+        else:
+            serving = serving_bench(combo, ctx)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -310,7 +320,7 @@ def main():
                            "operator_applications": int(ops), "solve_finished_in_timed_region": bool(done),
                            "l2": "inputs larger than L2 (each 9-field >= 604 MB)",
                            "parallelism": f"replicas x{world}"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "gpu_launches": launches,
                 "clocks": clocks, "kernels": table}
         if args.profile_json:
             json.dump(line, open(args.profile_json, "w"), indent=1)
@@ -339,6 +349,76 @@ def run_e2e(p, prec, combo, ctx, V):
             "newton_iterations": [int(v) for v in r["iters"]], "cg_iterations": [int(v) for v in r["cg_iters"]],
             "Pbar_final": [float(v) for v in r["Pbar"][-1]],
             "note": "one full combo_solve from host buffers; per-step bytes = totals / operator applications"}
+
+
+def serving_problems(count, seed, sides, max_steps):
+    """A stream of solve requests: grid side from ``sides`` (log-uniform),
+    random balls or z-fibres, vf U(0.1, 0.3), contrast 10, random Fbar
+    (stretch <= 8 %, shear <= 10 %), 1..max_steps load steps."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    rng = np.random.default_rng(seed)
+    logs = np.log(np.asarray(sides, float))
+    out = []
+    for i in range(count):
+        side = int(sides[int(np.argmin(np.abs(logs - rng.uniform(logs[0], logs[-1]))))])
+        Fb = np.eye(3) + np.diag(rng.uniform(-0.08, 0.08, 3))
+        off = rng.uniform(-0.10, 0.10, (3, 3))
+        np.fill_diagonal(off, 0.0)
+        Fb = Fb + off
+        steps = int(rng.integers(1, max_steps + 1))
+        vf = float(rng.uniform(0.1, 0.3))
+        sd = int(rng.integers(1 << 30))
+        if rng.random() < 0.5:
+            p = ms.random_spheres((side,) * 3, max(4.0, side / 10), min(vf, 0.25), sd, 10.0, Fb, steps)
+        else:
+            p = ms.random_fibres((side,) * 3, max(3.0, side / 12), vf, sd, 10.0, Fb, steps)
+        out.append(p)
+    return out
+
+
+def serving_bench(combo, ctx, count=12, sides=(48, 64, 72, 96), max_steps=4, slots=4, seed=2204_13624 + 4):
+    """Saturated throughput of the request stream (all submitted at once),
+    then Poisson arrivals at 0.7 x that rate for latency percentiles; the
+    FP32-refined form against the plain FP64 form on the same requests."""
+    probs = serving_problems(count, seed, sides, max_steps)
+    out = {"requests": count, "sides": list(sides), "load_steps": f"1..{max_steps}", "slots": slots}
+    pbar = {}
+    for form, prec in (("refined", combo.FP32_REFINED), ("fp64", combo.FP64)):
+        srv = combo.Server(ctx, max_slots=slots)
+        t0 = time.perf_counter()
+        tk = [srv.submit(p, precision=prec, tol=1e-8) for p in probs]
+        res = [srv.wait(t) for t in tk]
+        dt = time.perf_counter() - t0
+        srv.close()
+        pbar[form] = [r["Pbar"][-1] for r in res]
+        rate = count / dt
+        entry = {"saturated_solves_per_s": rate, "saturated_seconds": dt}
+        if form == "refined":
+            rng = np.random.default_rng(seed + 1)
+            lam = 0.7 * rate
+            srv = combo.Server(ctx, max_slots=slots)
+            t0 = time.perf_counter()
+            next_t = 0.0
+            tk = []
+            for p in probs:
+                next_t += rng.exponential(1.0 / lam)
+                wait = next_t - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+                tk.append(srv.submit(p, precision=prec, tol=1e-8))
+            for t in tk:
+                srv.wait(t)
+            dt2 = time.perf_counter() - t0
+            st = srv.stats()
+            srv.close()
+            entry.update(arrival_rate_per_s=lam, solves_per_s=count / dt2, p50_seconds=st["p50_seconds"],
+                         p99_seconds=st["p99_seconds"], peak_concurrent=st["peak_running"])
+        out[form] = entry
+    errs = [float(np.max(np.abs(a - b)) / np.max(np.abs(b))) for a, b in zip(pbar["refined"], pbar["fp64"])]
+    out["Pbar_rel_err_refined_vs_fp64_max"] = max(errs)
+    out["speedup_refined_vs_fp64"] = out["refined"]["saturated_solves_per_s"] / out["fp64"]["saturated_solves_per_s"]
+    return out
 
 
 def run_reference(args, rank, world):
