@@ -353,7 +353,8 @@ def run_e2e(p, prec, combo, ctx, V):
 
 def serving_problems(count, seed, sides, max_steps):
     """A stream of solve requests: grid side from ``sides`` (log-uniform),
-    random balls or z-fibres, vf U(0.1, 0.3), contrast 10, random Fbar
+    random balls (vf <= 0.18) or z-fibres (vf <= 0.25), vf drawn U(0.1, 0.3)
+    then capped, contrast 10, random Fbar
     (stretch <= 8 %, shear <= 10 %), 1..max_steps load steps."""
     from paper_2204_13624_gb300 import microstructure as ms
 
@@ -369,10 +370,12 @@ def serving_problems(count, seed, sides, max_steps):
         steps = int(rng.integers(1, max_steps + 1))
         vf = float(rng.uniform(0.1, 0.3))
         sd = int(rng.integers(1 << 30))
+        # centre gap 1.75 voxels (> a voxel diagonal: no voxel is cut twice);
+        # volume fractions capped where random sequential addition jams
         if rng.random() < 0.5:
-            p = ms.random_spheres((side,) * 3, max(4.0, side / 10), min(vf, 0.25), sd, 10.0, Fb, steps)
+            p = ms.random_spheres((side,) * 3, max(4.0, side / 10), min(vf, 0.18), sd, 10.0, Fb, steps, gap_vox=1.75)
         else:
-            p = ms.random_fibres((side,) * 3, max(3.0, side / 12), vf, sd, 10.0, Fb, steps)
+            p = ms.random_fibres((side,) * 3, max(3.0, side / 12), min(vf, 0.25), sd, 10.0, Fb, steps, gap_vox=1.75)
         out.append(p)
     return out
 
