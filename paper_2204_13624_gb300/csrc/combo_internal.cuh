@@ -275,6 +275,27 @@ __device__ __forceinline__ void cg_beta(Scalars* sc, double rr_new, double cg_to
     if (stop || rr_new == 0.0) sc->cg_done = 1;
 }
 
+// y = A : p for a pure Neo-Hookean voxel from its cache (G = F^{-1}, m):
+//   y_iJ = mu p_iJ + lam tr(G p) G_Ji + m (G p G)_Ji
+template <typename S>
+__device__ __forceinline__ void nh_tangent(const S G[9], S m, S mu, S lam, const S p[9], S y[9])
+{
+    S Gp[9], GpG[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) Gp[3 * i + j] = G[3 * i] * p[j] + G[3 * i + 1] * p[3 + j] + G[3 * i + 2] * p[6 + j];
+    const S tr = Gp[0] + Gp[4] + Gp[8];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) GpG[3 * i + j] = Gp[3 * i] * G[j] + Gp[3 * i + 1] * G[3 + j] + Gp[3 * i + 2] * G[6 + j];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) y[3 * i + j] = mu * p[3 * i + j] + lam * tr * G[3 * j + i] + m * GpG[3 * j + i];
+}
+
 // ---------------------------------------------------------------- launchers
 enum XfwdMode { XF_RESID = 0, XF_TANGENT = 1 };
 enum XinvMode { XI_FIXEDPOINT = 0, XI_RHS = 1, XI_CG = 2, XI_PLAIN = 3 };
@@ -362,6 +383,12 @@ int xpass_lines(const GridDims& g, size_t cxbytes);
 int xpass_grid(const GridDims& g, int lines);  // x-pass blocks (= partial count)
 int ypass_tx(int n, size_t cxbytes);  // columns per y-pass block (must match the launcher)
 int zpass_tx(int n, size_t cxbytes);  // columns per z-pass block (sets the partial count)
+
+// FP32 tangent x-forward and CG x-inverse with streamed (bulk asynchronous,
+// double-buffered) inputs, for n1 = 128, 256, 512 (xpass_stream.cu)
+bool stream_xpass_ok(const GridDims& g);
+void launch_xfwd_stream(const XfwdArgs<float, float>& a, cudaStream_t st);
+void launch_xinv_stream(const XinvArgs<float, float>& a, cudaStream_t st);
 
 // Record msg as the calling thread's last error; returns code.
 int set_error(int code, const char* msg);

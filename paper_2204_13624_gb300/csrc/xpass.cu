@@ -13,6 +13,8 @@
 // arithmetic, so the DRAM round trips overlap.  Dot products are summed in
 // FP32 within a thread's share of a group and in FP64 across groups: FP64
 // arithmetic runs at a small fraction of the FP32 rate on this GPU.
+#include <type_traits>
+
 #include "combo_internal.cuh"
 #include "fft_fast.cuh"
 #include "../../include/combo.h"
@@ -107,27 +109,6 @@ __device__ __forceinline__ bool nh_stress(const double F[9], double mu, double l
         for (int j = 0; j < 3; j++) P[3 * i + j] = mu * F[3 * i + j] + k * G[3 * j + i];
     m = mu - lam * lnJ;
     return true;
-}
-
-// y = A : p for a pure Neo-Hookean voxel from its cache (G = F^{-1}, m):
-//   y_iJ = mu p_iJ + lam tr(G p) G_Ji + m (G p G)_Ji
-template <typename S>
-__device__ __forceinline__ void nh_tangent(const S G[9], S m, S mu, S lam, const S p[9], S y[9])
-{
-    S Gp[9], GpG[9];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) Gp[3 * i + j] = G[3 * i] * p[j] + G[3 * i + 1] * p[3 + j] + G[3 * i + 2] * p[6 + j];
-    const S tr = Gp[0] + Gp[4] + Gp[8];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) GpG[3 * i + j] = Gp[3 * i] * G[j] + Gp[3 * i + 1] * G[3 + j] + Gp[3 * i + 2] * G[6 + j];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) y[3 * i + j] = mu * p[3 * i + j] + lam * tr * G[3 * j + i] + m * GpG[3 * j + i];
 }
 
 // ------------------------------------------------------------- x forward
@@ -403,6 +384,12 @@ template <typename T, typename Tc, int MF> static void xfwd_launch(const XfwdArg
 
 template <typename T, typename Tc> void launch_xfwd(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st)
 {
+    if constexpr (std::is_same<T, float>::value && std::is_same<Tc, float>::value) {
+        if (a.mode == XF_TANGENT && !a.X && guard == 1 && stream_xpass_ok(a.g)) {
+            launch_xfwd_stream(a, st);
+            return;
+        }
+    }
     switch (a.g.M) {
         case 32: xfwd_launch<T, Tc, 32>(a, guard, st); break;
         case 64: xfwd_launch<T, Tc, 64>(a, guard, st); break;
@@ -423,6 +410,12 @@ template <typename T, typename Tc, int MF> static void xinv_launch(const XinvArg
 
 template <typename T, typename Tc> void launch_xinv(const XinvArgs<T, Tc>& a, int guard, cudaStream_t st)
 {
+    if constexpr (std::is_same<T, float>::value && std::is_same<Tc, float>::value) {
+        if (a.mode == XI_CG && guard == 1 && stream_xpass_ok(a.g)) {
+            launch_xinv_stream(a, st);
+            return;
+        }
+    }
     switch (a.g.M) {
         case 32: xinv_launch<T, Tc, 32>(a, guard, st); break;
         case 64: xinv_launch<T, Tc, 64>(a, guard, st); break;
