@@ -384,10 +384,9 @@ int xpass_grid(const GridDims& g, int lines);  // x-pass blocks (= partial count
 int ypass_tx(int n, size_t cxbytes);  // columns per y-pass block (must match the launcher)
 int zpass_tx(int n, size_t cxbytes);  // columns per z-pass block (sets the partial count)
 
-// FP32 tangent x-forward and CG x-inverse with streamed (bulk asynchronous,
-// double-buffered) inputs, for n1 = 128, 256, 512 (xpass_stream.cu)
+// FP32 CG x-inverse with streamed (bulk asynchronous, double-buffered)
+// inputs, for n1 = 128, 256, 512 (xpass_stream.cu)
 bool stream_xpass_ok(const GridDims& g);
-void launch_xfwd_stream(const XfwdArgs<float, float>& a, cudaStream_t st);
 void launch_xinv_stream(const XinvArgs<float, float>& a, cudaStream_t st);
 
 // Record msg as the calling thread's last error; returns code.

@@ -384,12 +384,6 @@ template <typename T, typename Tc, int MF> static void xfwd_launch(const XfwdArg
 
 template <typename T, typename Tc> void launch_xfwd(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st)
 {
-    if constexpr (std::is_same<T, float>::value && std::is_same<Tc, float>::value) {
-        if (a.mode == XF_TANGENT && !a.X && guard == 1 && stream_xpass_ok(a.g)) {
-            launch_xfwd_stream(a, st);
-            return;
-        }
-    }
     switch (a.g.M) {
         case 32: xfwd_launch<T, Tc, 32>(a, guard, st); break;
         case 64: xfwd_launch<T, Tc, 64>(a, guard, st); break;

@@ -1,7 +1,7 @@
-// xpass_stream.cu -- the two FP32 Krylov x-passes with streamed inputs.
+// xpass_stream.cu -- the FP32 CG x-inverse with streamed inputs.
 //
-// Same arithmetic as the tangent x-forward and CG x-inverse of xpass.cu,
-// restructured so that memory and arithmetic overlap inside a block: a
+// Same arithmetic as the CG x-inverse of xpass.cu (r -= alpha G[A:p] with the
+// fused beta reduction), restructured so that memory and arithmetic overlap inside a block: a
 // persistent block walks its groups of x-lines, and while it transforms
 // group i the input rows of group i+1 arrive in the other of two shared-
 // memory stage buffers through bulk asynchronous copies (cp.async.bulk,
@@ -16,8 +16,6 @@
 namespace combo {
 
 namespace {
-
-constexpr int kRowsFwd = 37;  // r 9, p 9, x 9, tangent cache 10
 
 template <typename K> void allow_smem_stream(K kernel, bool& done)
 {
@@ -39,178 +37,6 @@ int num_sms()
 }
 
 }  // namespace
-
-// stage layout of the tangent pass: rows [37][LB][n1] floats, then phase [LB][n1]
-__host__ __device__ inline size_t fwd_stage_bytes(int LB, int n1)
-{
-    return ((size_t)kRowsFwd * LB * n1 * 4 + (size_t)LB * n1 + 15) / 16 * 16;
-}
-
-// ------------------------------------------------------------- tangent x-forward
-template <int M>
-__global__ void __launch_bounds__(256) k_xfwd_stream(XfwdArgs<float, float> a, int LB)
-{
-    if (a.sc->cg_done) return;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    constexpr int n1 = 2 * M;
-    constexpr int ls = M + 1;
-    const GridDims g = a.g;
-    const size_t sb = fwd_stage_bytes(LB, n1);
-    unsigned char* stage[2] = {smem_raw, smem_raw + sb};
-    float2* buf0 = reinterpret_cast<float2*>(smem_raw + 2 * sb);
-    float2* buf1 = buf0 + (size_t)9 * LB * ls;
-    double* red = reinterpret_cast<double*>(buf1 + (size_t)9 * LB * ls);
-    int* flag = reinterpret_cast<int*>(red + 256);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(flag + 4);
-    float* rb = reinterpret_cast<float*>(buf0);
-
-    const int nlines = g.n2 * g.n3;
-    const int ngroups = nlines / LB;  // the launcher guarantees nlines % LB == 0
-    const int64_t V = g.V;
-    const bool first = (a.sc->cg_iter == 0);
-    const float beta = first ? 0.f : (float)a.sc->beta;
-    const float apend = first ? 0.f : (float)a.sc->alpha_pending;
-    const int nrows = first ? 19 : kRowsFwd;  // r, tangent cache (+ p, x)
-    const uint32_t row_bytes = n1 * 4;
-    const uint32_t tx_bytes = (uint32_t)nrows * LB * row_bytes + (uint32_t)LB * n1;
-
-    auto issue = [&](int grp, int s) {
-        float* rows = reinterpret_cast<float*>(stage[s]);
-        unsigned char* ph = stage[s] + (size_t)kRowsFwd * LB * n1 * 4;
-        mbar_arrive_expect_tx(&bar[s], tx_bytes);
-        for (int l = 0; l < LB; l++) {
-            const int64_t off = (int64_t)(grp * LB + l) * n1;
-            for (int c = 0; c < 9; c++)
-                bulk_g2s(rows + ((size_t)c * LB + l) * n1, a.r + c * V + off, row_bytes, &bar[s]);
-            if (!first)
-                for (int c = 0; c < 9; c++) {
-                    bulk_g2s(rows + ((size_t)(9 + c) * LB + l) * n1, a.p + c * V + off, row_bytes, &bar[s]);
-                    bulk_g2s(rows + ((size_t)(18 + c) * LB + l) * n1, a.x + c * V + off, row_bytes, &bar[s]);
-                }
-            for (int c = 0; c < 10; c++)
-                bulk_g2s(rows + ((size_t)(27 + c) * LB + l) * n1, a.tc + c * V + off, row_bytes, &bar[s]);
-            bulk_g2s(ph + (size_t)l * n1, a.phase + off, n1, &bar[s]);
-        }
-    };
-
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_proxy_async();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && (int)blockIdx.x < ngroups) issue(blockIdx.x, 0);
-
-    double acc = 0.0;
-    int it = 0;
-    bool timed_out = false;
-    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, it++) {
-        const int s = it & 1;
-        const int nxt = grp + gridDim.x;
-        if (threadIdx.x == 0 && nxt < ngroups) {
-            fence_proxy_async();  // this block's reads of stage s^1 (previous group) precede the copy
-            issue(nxt, s ^ 1);
-        }
-        const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1));
-        if (__syncthreads_or(!ok)) {
-            timed_out = true;
-            break;
-        }
-        const float* rows = reinterpret_cast<const float*>(stage[s]);
-        const unsigned char* phs = stage[s] + (size_t)kRowsFwd * LB * n1 * 4;
-        const int L0 = grp * LB;
-        float accp = 0.f;
-        for (int e = threadIdx.x; e < LB * n1; e += blockDim.x) {
-            const int l = e / n1, x = e - l * n1;
-            const int64_t v = (int64_t)(L0 + l) * n1 + x;
-            const int ph = phs[l * n1 + x];
-            float p[9], t[10];
-#pragma unroll
-            for (int c = 0; c < 9; c++) p[c] = rows[((size_t)c * LB + l) * n1 + x];
-            if (!first) {
-#pragma unroll
-                for (int c = 0; c < 9; c++) {
-                    const float po = rows[((size_t)(9 + c) * LB + l) * n1 + x];
-                    if (apend != 0.f) a.x[c * V + v] = rows[((size_t)(18 + c) * LB + l) * n1 + x] + apend * po;
-                    p[c] += beta * po;
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < 10; c++) t[c] = rows[((size_t)(27 + c) * LB + l) * n1 + x];
-#pragma unroll
-            for (int c = 0; c < 9; c++) a.p[c * V + v] = p[c];
-            float y[9];
-            if (ph == 2) {
-                const int64_t b = a.vox2box[v];
-#pragma unroll
-                for (int r = 0; r < 9; r++) {
-                    float sacc = 0.f;
-#pragma unroll
-                    for (int c = 0; c < 9; c++) sacc += a.bA[(int64_t)(r * 9 + c) * a.nb + b] * p[c];
-                    y[r] = sacc;
-                }
-            } else {
-                nh_tangent<float>(t, t[9], (float)a.mu[ph], (float)a.lam[ph], p, y);
-            }
-            float sd = 0.f;
-#pragma unroll
-            for (int c = 0; c < 9; c++) {
-                sd += p[c] * y[c];
-                rb[(size_t)2 * (c * LB + l) * ls + x] = y[c];
-            }
-            accp += sd;
-        }
-        acc += (double)accp;
-        __syncthreads();
-
-        const int nl = 9 * LB;
-        float2* Z = fft_lines_fast<float, M, false>(buf0, buf1, nl, ls, a.tw);
-        constexpr int half = M / 2;
-        for (int e = threadIdx.x; e < nl * (half + 1); e += blockDim.x) {
-            const int q = e / (half + 1), k = e - q * (half + 1);
-            const int c = q / LB, l = q - c * LB;
-            const float2* z = Z + (size_t)q * ls;
-            float2* o = a.spec + c * g.Vs + (int64_t)(L0 + l) * g.nhp;
-            if (k == 0) {
-                const float2 z0 = z[0];
-                o[0] = float2{z0.x + z0.y, 0.f};
-                o[M] = float2{z0.x - z0.y, 0.f};
-                continue;
-            }
-            const int k2 = M - k;
-            const float2 A = z[k], B = z[k2];
-            {
-                const float2 Bc = c_conj(B);
-                const float2 Ze = c_scale(c_add(A, Bc), 0.5f);
-                const float2 D = c_sub(A, Bc);
-                o[k] = c_add(Ze, c_mul(a.tw2[k], float2{0.5f * D.y, -0.5f * D.x}));
-            }
-            if (k2 != k) {
-                const float2 Ac = c_conj(A);
-                const float2 Ze = c_scale(c_add(B, Ac), 0.5f);
-                const float2 D = c_sub(B, Ac);
-                o[k2] = c_add(Ze, c_mul(a.tw2[k2], float2{0.5f * D.y, -0.5f * D.x}));
-            }
-        }
-        __syncthreads();
-    }
-    if (timed_out) {
-        if (threadIdx.x == 0) {
-            raise_status(a.sc, COMBO_E_TIMEOUT);
-            // the copy issued for the next group may still be in flight
-            mbar_wait_bounded(&bar[it & 1 ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
-        }
-        return;
-    }
-    if (a.partial) {
-        const double sacc = block_sum(acc, red);
-        if (threadIdx.x == 0) a.partial[blockIdx.x] = sacc;
-        if (a.fuse && last_block(&a.sc->ticket[0], flag)) {
-            const double tot = sum_partials_fixed(a.partial, gridDim.x, red);
-            if (threadIdx.x == 0) cg_alpha(a.sc, tot);
-        }
-    }
-}
 
 // ------------------------------------------------------------- CG x-inverse
 // stage layout: spectrum rows [9][LB][lsx] complex, then r rows [9][LB][n1]
@@ -329,18 +155,6 @@ bool stream_xpass_ok(const GridDims& g)
     return (M == 64 || M == 128 || M == 256) && (g.n1 % 16) == 0 && (g.n2 * g.n3) % stream_lines(g) == 0;
 }
 
-template <int M> static void xfwd_stream_launch(const XfwdArgs<float, float>& a, cudaStream_t st)
-{
-    const int LB = stream_lines(a.g);
-    const size_t sm = 2 * fwd_stage_bytes(LB, 2 * M) + (size_t)2 * 9 * LB * (M + 1) * 8 + 256 * 8 + 16 + 16;
-    const int per_sm = sm > 110 * 1024 ? 1 : 2;
-    const int groups = a.g.n2 * a.g.n3 / LB;
-    const int grid = groups < per_sm * num_sms() ? groups : per_sm * num_sms();
-    static bool attr = false;
-    allow_smem_stream(k_xfwd_stream<M>, attr);
-    k_xfwd_stream<M><<<grid, 256, sm, st>>>(a, LB);
-}
-
 template <int M> static void xinv_stream_launch(const XinvArgs<float, float>& a, cudaStream_t st)
 {
     const int LB = stream_lines(a.g);
@@ -353,15 +167,6 @@ template <int M> static void xinv_stream_launch(const XinvArgs<float, float>& a,
     static bool attr = false;
     allow_smem_stream(k_xinv_stream<M>, attr);
     k_xinv_stream<M><<<grid, 256, sm, st>>>(a, LB);
-}
-
-void launch_xfwd_stream(const XfwdArgs<float, float>& a, cudaStream_t st)
-{
-    switch (a.g.M) {
-        case 64: xfwd_stream_launch<64>(a, st); break;
-        case 128: xfwd_stream_launch<128>(a, st); break;
-        default: xfwd_stream_launch<256>(a, st); break;
-    }
 }
 
 void launch_xinv_stream(const XinvArgs<float, float>& a, cudaStream_t st)
