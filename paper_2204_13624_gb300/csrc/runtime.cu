@@ -505,15 +505,26 @@ __global__ void k_fin_rhs(Scalars* sc, const double* part, int n, int cg_fixed, 
 // F += d * (x + alpha_pending p) -- the CG solution including the update the
 // last CG iteration still owes -- then admissibility (det F > 0) of every voxel
 template <typename Tc>
-__global__ void k_update_F(double* F, const Tc* x, const Tc* p, double d, int64_t V, Scalars* sc)
+__global__ void k_update_F(double* __restrict__ F, const Tc* __restrict__ x, const Tc* __restrict__ p, double d,
+                           int64_t V, Scalars* sc)
 {
     const Tc ap = (Tc)sc->alpha_pending;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
         double f[9];
+        Tc xv[9];
+        // all loads before the first store
 #pragma unroll
         for (int c = 0; c < 9; c++) {
-            const Tc xv = (ap != (Tc)0) ? x[c * V + v] + ap * p[c * V + v] : x[c * V + v];
-            f[c] = F[c * V + v] + d * (double)xv;
+            f[c] = F[c * V + v];
+            xv[c] = x[c * V + v];
+        }
+        if (ap != (Tc)0) {
+#pragma unroll
+            for (int c = 0; c < 9; c++) xv[c] += ap * p[c * V + v];
+        }
+#pragma unroll
+        for (int c = 0; c < 9; c++) {
+            f[c] += d * (double)xv[c];
             F[c * V + v] = f[c];
         }
         const double J = f[0] * (f[4] * f[8] - f[5] * f[7]) - f[1] * (f[3] * f[8] - f[5] * f[6]) +

@@ -13,6 +13,7 @@
 // arithmetic, so the DRAM round trips overlap.  Dot products are summed in
 // FP32 within a thread's share of a group and in FP64 across groups: FP64
 // arithmetic runs at a small fraction of the FP32 rate on this GPU.
+#include <algorithm>
 #include <type_traits>
 
 #include "combo_internal.cuh"
@@ -38,7 +39,7 @@ int xpass_lines(const GridDims& g, size_t cxbytes)
 
 // x-pass grid: a few resident blocks per SM stride over the line groups, so
 // that the fused reductions see few partials and few tickets.
-int xpass_grid(const GridDims& g, int lines)
+static int grid_cap(const GridDims&)
 {
     static int nsm = 0;
     if (nsm == 0) {
@@ -46,8 +47,13 @@ int xpass_grid(const GridDims& g, int lines)
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
     }
+    return 4 * nsm;
+}
+
+int xpass_grid(const GridDims& g, int lines)
+{
     const int groups = (g.n2 * g.n3 + lines - 1) / lines;
-    return groups < 4 * nsm ? groups : 4 * nsm;
+    return std::min(groups, grid_cap(g));
 }
 
 template <typename K> static void allow_smem(K kernel, bool& done)
@@ -112,8 +118,10 @@ __device__ __forceinline__ bool nh_stress(const double F[9], double mu, double l
 }
 
 // ------------------------------------------------------------- x forward
-template <typename T, typename Tc, int MF>
-__global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
+// TAN: the Krylov tangent pass (a.mode == XF_TANGENT, no external X), whose
+// FP32 instance is register-capped for three resident blocks per SM
+template <typename T, typename Tc, int MF, bool TAN>
+__global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 3 : 1) k_xfwd(XfwdArgs<T, Tc> a, int guard)
 {
     if (guard == 1 && a.sc->cg_done) return;
     if (guard == 2 && a.sc->outer_done) return;
@@ -129,7 +137,6 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
     const int nlines = g.n2 * g.n3;
     const int ngroups = (nlines + LB - 1) / LB;
     const int64_t V = g.V;
-    const int hn = g.n1 >> 1;
     double acc = 0.0;
 
     const bool first = (a.mode == XF_TANGENT) ? (a.sc->cg_iter == 0) : false;
@@ -149,10 +156,11 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
             if (L >= nlines) continue;
             const int64_t v = (int64_t)L * g.n1 + x;
             T o[9];
-            if (a.X) {
+            if constexpr (!TAN) {
+              if (a.X) {
 #pragma unroll
                 for (int c = 0; c < 9; c++) o[c] = (T)a.X[c * V + v];
-            } else if (a.mode == XF_RESID) {
+              } else {  // XF_RESID
                 const int ph = phase[v];
                 double F[9];
 #pragma unroll
@@ -181,24 +189,34 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
                         a.tc[9 * V + v] = (Tc)m;
                     }
                 }
+              }
             } else {  // XF_TANGENT: x += alpha_prev p, p = r + beta p, y = A : p
-                // every load is issued before the phase branch
+                // every load is issued before the first store and before the
+                // phase branch, so that one memory latency covers all of them
+                const Tc* __restrict__ rg = a.r;
+                Tc* __restrict__ pg = a.p;
+                Tc* __restrict__ xg = a.x;
+                const Tc* __restrict__ tg = a.tc;
                 const int ph = phase[v];
-                Tc p[9], t[10];
+                Tc p[9], po[9], xo[9], t[10];
 #pragma unroll
-                for (int c = 0; c < 9; c++) p[c] = a.r[c * V + v];
+                for (int c = 0; c < 9; c++) p[c] = rg[c * V + v];
+#pragma unroll
+                for (int c = 0; c < 10; c++) t[c] = tg[c * V + v];
                 if (!first) {
 #pragma unroll
-                    for (int c = 0; c < 9; c++) {
-                        const Tc po = a.p[c * V + v];
-                        if (apend != (Tc)0) a.x[c * V + v] += apend * po;
-                        p[c] += beta * po;
+                    for (int c = 0; c < 9; c++) po[c] = pg[c * V + v];
+                    if (apend != (Tc)0) {
+#pragma unroll
+                        for (int c = 0; c < 9; c++) xo[c] = xg[c * V + v];
+#pragma unroll
+                        for (int c = 0; c < 9; c++) xg[c * V + v] = xo[c] + apend * po[c];
                     }
+#pragma unroll
+                    for (int c = 0; c < 9; c++) p[c] += beta * po[c];
                 }
 #pragma unroll
-                for (int c = 0; c < 10; c++) t[c] = a.tc[c * V + v];
-#pragma unroll
-                for (int c = 0; c < 9; c++) a.p[c * V + v] = p[c];
+                for (int c = 0; c < 9; c++) pg[c * V + v] = p[c];
                 Tc y[9];
                 if (ph == 2) {
                     const int64_t b = a.vox2box[v];
@@ -264,7 +282,7 @@ __global__ void __launch_bounds__(256) k_xfwd(XfwdArgs<T, Tc> a, int guard)
         }
         __syncthreads();  // the next group reuses the shared buffers
     }
-    if (a.mode == XF_TANGENT && a.partial) {
+    if (TAN && a.partial) {
         const double s = block_sum(acc, red);
         if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
         if (a.fuse && last_block(&a.sc->ticket[0], flag)) {
@@ -293,7 +311,6 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
     const int ngroups = (nlines + LB - 1) / LB;
     const int nl = 9 * LB;
     const int64_t V = g.V;
-    const int hn = g.n1 >> 1;
     double acc = 0.0;
     const bool skip_update = (a.mode == XI_FIXEDPOINT) && a.sc->outer_done;
     const Tc alpha = (a.mode == XI_CG) ? (Tc)a.sc->alpha : (Tc)0;
@@ -343,9 +360,12 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
                 }
             } else if (a.mode == XI_FIXEDPOINT) {
                 if (skip_update) continue;
+                double* __restrict__ Fg = a.F;
+                double Fo[9];
 #pragma unroll
-                for (int c = 0; c < 9; c++)
-                    a.F[c * V + v] -= (double)rb[(size_t)2 * (c * LB + l) * ls + x] * a.inv_mu0;
+                for (int c = 0; c < 9; c++) Fo[c] = Fg[c * V + v];
+#pragma unroll
+                for (int c = 0; c < 9; c++) Fg[c * V + v] = Fo[c] - (double)rb[(size_t)2 * (c * LB + l) * ls + x] * a.inv_mu0;
             } else if (a.mode == XI_RHS) {
 #pragma unroll
                 for (int c = 0; c < 9; c++) {
@@ -377,9 +397,17 @@ template <typename T, typename Tc, int MF> static void xfwd_launch(const XfwdArg
 {
     const int grid = xpass_grid(a.g, a.lines_per_block);
     const size_t sm = xpass_smem(a.g, a.lines_per_block, sizeof(cx<T>));
-    static bool attr = false;
-    allow_smem(k_xfwd<T, Tc, MF>, attr);
-    k_xfwd<T, Tc, MF><<<grid, 256, sm, st>>>(a, guard);
+    if (a.mode == XF_TANGENT && !a.X) {
+        // one wave: the FP32 instance is register-capped to three blocks per SM
+        const int tgrid = sizeof(T) == 4 ? std::min(grid, 3 * (grid_cap(a.g) / 4)) : grid;
+        static bool attr = false;
+        allow_smem(k_xfwd<T, Tc, MF, true>, attr);
+        k_xfwd<T, Tc, MF, true><<<tgrid, 256, sm, st>>>(a, guard);
+    } else {
+        static bool attr = false;
+        allow_smem(k_xfwd<T, Tc, MF, false>, attr);
+        k_xfwd<T, Tc, MF, false><<<grid, 256, sm, st>>>(a, guard);
+    }
 }
 
 template <typename T, typename Tc> void launch_xfwd(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st)
