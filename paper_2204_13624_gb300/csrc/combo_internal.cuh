@@ -372,6 +372,7 @@ template <typename T> struct ZArgs {
     double* partial; // [gridDim.x * gridDim.y * gridDim.z]
     Scalars* sc;
     int guard;
+    const void* tmap;  // CUtensorMap of spec for the TMA z-pass (FP32), or null
 };
 
 template <typename T, typename Tc> void launch_xfwd(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st);
@@ -387,6 +388,10 @@ int zpass_tx(int n, size_t cxbytes);  // columns per z-pass block (sets the part
 // FP32 CG x-inverse with streamed (bulk asynchronous, double-buffered)
 // inputs, for n1 = 128, 256, 512 (xpass_stream.cu)
 bool stream_xpass_ok(const GridDims& g);
+// FP32 Krylov z-pass with TMA tiles, n3 = 64, 128, 256 (zpass_tma.cu)
+bool zpass_tma_size(int n3);
+bool zpass_tma_encode(void* map, const GridDims& g, const void* spec);
+void launch_zpass_tma(const ZArgs<float>& a, const void* map, cudaStream_t st);
 void launch_xinv_stream(const XinvArgs<float, float>& a, cudaStream_t st);
 
 // Record msg as the calling thread's last error; returns code.

@@ -5,6 +5,7 @@
 // Paper: arXiv 2204.13624.  Sec. 2 (HOM, Pbar = <P>), Sec. 3 (Lippmann-
 // Schwinger equation, Green operator, fixed point / Newton with a fast linear
 // solver), Sec. 4 (composite boxels), Sec. 6.1 (Neo-Hookean phases).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -347,6 +348,13 @@ template <typename T> struct Engine {
     Plan pM, py, pz;
     int lines, txy, txz;
     cx<T>* spec = nullptr;  // not owned
+    CUtensorMap zmap;       // TMA view of spec for the FP32 z-pass
+    bool zmap_ok = false;
+    void bind_spec(void* s)
+    {
+        spec = (cx<T>*)s;
+        zmap_ok = (sizeof(T) == 4) && zpass_tma_encode(&zmap, g, s);
+    }
     int init(const GridDims& gd, const double l[3], int kspace)
     {
         g = gd;
@@ -412,6 +420,7 @@ template <typename T> struct Engine {
         z.partial = partial;
         z.sc = sc;
         z.guard = guard;
+        z.tmap = zmap_ok ? &zmap : nullptr;
         if (pr) pr->begin(kbase + 1);
         launch_zpass<T>(z, st);
         if (pr) pr->end();
@@ -792,8 +801,8 @@ template <typename Tc> struct Solve : SolveBase {
             CK(cudaMalloc(&d_r, sizeof(Tc) * 9 * V));
             CK(cudaMalloc(&d_p, sizeof(Tc) * 9 * V));
         }
-        e64.spec = (cx<double>*)d_spec;
-        ec.spec = (cx<Tc>*)d_spec;
+        e64.bind_spec(d_spec);
+        ec.bind_spec(d_spec);
         CK(cudaMemcpyAsync(d_phase, hp.phase.data(), V, cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(d_v2b, 0xff, 4 * V, st));
         if (nb > 0) {
@@ -1295,7 +1304,7 @@ template <typename T> static int apply_G_impl(combo_ctx* ctx, const int32_t n[3]
     CKC(cudaMalloc(&part, 8 * (size_t)std::max(e.xblocks(), e.zblocks())));
     CKC(cudaMalloc(&sc, sizeof(Scalars)));
     CKC(cudaMemsetAsync(sc, 0, sizeof(Scalars), st));
-    e.spec = (cx<T>*)spec;
+    e.bind_spec(spec);
     auto xf = e.template xf<T>();
     xf.X = dX;
     xf.sc = sc;

@@ -309,6 +309,12 @@ template <typename T, int N> static void zpass_fast_launch(const ZArgs<T>& a, cu
 
 template <typename T> void launch_zpass(const ZArgs<T>& a, cudaStream_t st)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (a.tmap && !a.want_norm && zpass_tma_size(a.g.n3)) {
+            launch_zpass_tma(a, a.tmap, st);
+            return;
+        }
+    }
     switch (a.g.n3) {
         case 64: zpass_fast_launch<T, 64>(a, st); return;
         case 128: zpass_fast_launch<T, 128>(a, st); return;

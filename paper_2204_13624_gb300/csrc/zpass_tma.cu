@@ -1,0 +1,223 @@
+// zpass_tma.cu -- FP32 z-pass (forward z FFT, Green operator, inverse z FFT)
+// with tensor-memory-accelerator (TMA) tile movement.
+//
+// Same arithmetic as k_zpass_fast of yzpass.cu for the Krylov operator (no
+// norm accumulation).  A persistent block walks tiles of the half spectrum;
+// a tile is the three components of one tensor row i, all N z-planes, one y
+// and TX consecutive x frequencies: a 4-D box {TX, 1, N, 3} of the tensor
+// [9][n3][n2][nhp] of complex FP32 (8-byte elements).  One TMA load brings a
+// whole tile into shared memory (completion counted on an mbarrier) while the
+// previous tile is transformed in the other buffer; the result leaves by one
+// TMA store, so no thread waits on global memory.  The column stride of the
+// z direction (n2 * nhp complex) makes this pass the one with the least
+// contiguous rows; the copy engine issues them without occupying warps.
+//
+// Waits on the mbarrier are bounded: a block that exhausts the cap raises
+// COMBO_E_TIMEOUT, waits (bounded) for its own copies in flight and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "async_copy.cuh"
+#include "combo_internal.cuh"
+#include "fft_fast.cuh"
+#include "../../include/combo.h"
+
+namespace combo {
+
+namespace {
+
+template <int N> __host__ __device__ constexpr int tma_tx() { return N == 256 ? 8 : 16; }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+}  // namespace
+
+bool zpass_tma_size(int n3) { return n3 == 64 || n3 == 128 || n3 == 256; }
+
+// Tensor map of a complex FP32 half spectrum [9][n3][n2][nhp] for the z-pass
+// tile box {TX, 1, n3, 3}.  False (map unusable) for other sizes or when the
+// driver entry point is missing.
+bool zpass_tma_encode(void* map, const GridDims& g, const void* spec)
+{
+    if (!zpass_tma_size(g.n3) || !spec) return false;
+    const int tx = g.n3 == 256 ? tma_tx<256>() : tma_tx<128>();
+    if ((g.nhp * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(spec) & 15) != 0) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dim[4] = {(cuuint64_t)g.nhp, (cuuint64_t)g.n2, (cuuint64_t)g.n3, 9};
+    const cuuint64_t stride[3] = {(cuuint64_t)g.nhp * 8, (cuuint64_t)g.n2 * g.nhp * 8,
+                                  (cuuint64_t)g.n3 * g.n2 * g.nhp * 8};
+    const cuuint32_t box[4] = {(cuuint32_t)tx, 1, (cuuint32_t)g.n3, 3};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, 4,
+                          const_cast<void*>(spec), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int N>
+__global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
+    k_zpass_tma(const __grid_constant__ CUtensorMap tm, ZArgs<float> a)
+{
+    if (a.guard == 1 && a.sc->cg_done) return;
+    if (a.guard == 2 && a.sc->outer_done) return;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    constexpr int TX = tma_tx<N>();
+    constexpr int TPL = FastPlan<N>::TPL;
+    constexpr int GS = TX * TPL;  // threads per component group
+    constexpr int TILE = 3 * N * TX;
+    constexpr uint32_t TILE_BYTES = TILE * 8;
+    typedef cx<float> C;
+    C* tiles = reinterpret_cast<C*>(smem_raw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * TILE_BYTES);
+    const GridDims g = a.g;
+    const int c = threadIdx.x / GS;
+    const int r = threadIdx.x - c * GS;
+    const int line = r % TX, tau = r / TX;
+    const int nxt = (g.nh + TX - 1) / TX;
+    const int ntiles = nxt * g.n2 * 3;
+
+    // tile t = (row * n2 + y) * nxt + xt: consecutive blocks take neighbouring
+    // x tiles of the same rows of DRAM
+    auto issue = [&](int t, int s) {
+        const int xt = t % nxt, rest = t / nxt;
+        const int y = rest % g.n2, row = rest / g.n2;
+        mbar_arrive_expect_tx(&bar[s], TILE_BYTES);
+        tma_load_4d(tiles + s * TILE, &tm, xt * TX, y, 0, 3 * row, &bar[s]);
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_proxy_async();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+
+    int it = 0;
+    bool timed_out = false;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+        const int s = it & 1;
+        const int tn = t + gridDim.x;
+        if (threadIdx.x == 0 && tn < ntiles) {
+            bulk_wait_read_all();  // the store of the previous tile has left buffer s ^ 1
+            issue(tn, s ^ 1);
+        }
+        const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        const int xt = t % nxt, rest = t / nxt;
+        const int y = rest % g.n2, row = rest / g.n2;
+        const int x0 = xt * TX;
+        C* park = tiles + s * TILE;
+        C* pc = park + c * N * TX + line;
+        auto lp = [&](int e) { return pc[e * TX]; };
+        auto sp = [&](int e, C v) { pc[e * TX] = v; };
+
+        // forward along z, in place in the tile
+        fft_fast<float, N, false, true, true>(lp, sp, lp, sp, tau, a.tw);
+        __syncthreads();
+
+        // projection: row i of G X at every (xi3, column) = k (k . X_i) / |k|^2
+        const float ay = a.sa[1][y], by = a.sb[1][y];
+        for (int f = threadIdx.x; f < N * TX; f += blockDim.x) {
+            const int z = f / TX, ln = f - z * TX;
+            const int xi1 = x0 + ln;
+            C* p = park + f;
+            if (xi1 >= g.nh) {
+                p[0] = p[N * TX] = p[2 * N * TX] = C{0.f, 0.f};
+                continue;
+            }
+            const C X0 = p[0], X1 = p[N * TX], X2 = p[2 * N * TX];
+            const float ax = a.sa[0][xi1], bx = a.sb[0][xi1];
+            const float az = a.sa[2][z], bz = a.sb[2][z];
+            const float k0 = ax * by * bz, k1 = ay * bx * bz, k2 = az * bx * by;
+            const float kk = k0 * k0 + k1 * k1 + k2 * k2;
+            C o0{0.f, 0.f}, o1{0.f, 0.f}, o2{0.f, 0.f};
+            if (kk > 0.f) {
+                const float ik = 1.f / kk;
+                const float sr = (k0 * X0.x + k1 * X1.x + k2 * X2.x) * ik;
+                const float si = (k0 * X0.y + k1 * X1.y + k2 * X2.y) * ik;
+                o0 = C{k0 * sr, k0 * si};
+                o1 = C{k1 * sr, k1 * si};
+                o2 = C{k2 * sr, k2 * si};
+            }
+            p[0] = c_scale(o0, a.scale);
+            p[N * TX] = c_scale(o1, a.scale);
+            p[2 * N * TX] = c_scale(o2, a.scale);
+        }
+        __syncthreads();
+
+        // inverse along z, in place; then the whole tile leaves by one store
+        fft_fast<float, N, true, true, true>(lp, sp, lp, sp, tau, a.tw);
+        fence_proxy_async();  // this thread's tile writes, before the copy engine reads them
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tma_store_4d(&tm, x0, y, 0, 3 * row, park);
+            bulk_commit();
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (timed_out) {
+            raise_status(a.sc, COMBO_E_TIMEOUT);
+            // loads possibly in flight: this iteration's and the prefetch
+            const int s = it & 1;
+            mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1));
+            if ((int)blockIdx.x + (it + 1) * (int)gridDim.x < ntiles)
+                mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+        }
+        bulk_wait_all();  // the stores are complete before the block's shared memory goes away
+    }
+}
+
+template <int N> static void zpass_tma_launch(const ZArgs<float>& a, const void* map, cudaStream_t st)
+{
+    constexpr int TX = tma_tx<N>();
+    constexpr int threads = 3 * TX * FastPlan<N>::TPL;
+    const size_t sm = (size_t)2 * 3 * N * TX * 8 + 16;
+    static int grid_per_sm = 0;
+    static int nsm = 0;
+    if (grid_per_sm == 0) {
+        cudaFuncSetAttribute(k_zpass_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zpass_tma<N>, threads, sm) != cudaSuccess || per < 1)
+            per = 1;
+        grid_per_sm = per;
+    }
+    const int ntiles = ((a.g.nh + TX - 1) / TX) * a.g.n2 * 3;
+    const int grid = std::min(ntiles, grid_per_sm * nsm);
+    k_zpass_tma<N><<<grid, threads, sm, st>>>(*reinterpret_cast<const CUtensorMap*>(map), a);
+}
+
+void launch_zpass_tma(const ZArgs<float>& a, const void* map, cudaStream_t st)
+{
+    switch (a.g.n3) {
+        case 64: zpass_tma_launch<64>(a, map, st); break;
+        case 128: zpass_tma_launch<128>(a, map, st); break;
+        default: zpass_tma_launch<256>(a, map, st); break;
+    }
+}
+
+}  // namespace combo
