@@ -248,13 +248,16 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
 #pragma unroll
                         for (int k = 0; k < 3; k++)
                             W[3 * r + k] = B[3 * r] * Dt[k] + B[3 * r + 1] * Dt[3 + k] + B[3 * r + 2] * Dt[6 + k];
+                    // A_box is major-symmetric (the second derivative of the
+                    // condensed energy): its upper triangle is stored
+                    const int64_t kb = A.rank ? (int64_t)A.rank[b] : b;
 #pragma unroll
                     for (int r = 0; r < 9; r++)
 #pragma unroll
-                        for (int s = 0; s < 9; s++) {
+                        for (int s = r; s < 9; s++) {
                             const Tc avg = cpt * tp.A(r / 3, r % 3, s / 3, s % 3) + cmt * tm.A(r / 3, r % 3, s / 3, s % 3);
                             const Tc corr = W[3 * r] * B[3 * s] + W[3 * r + 1] * B[3 * s + 1] + W[3 * r + 2] * B[3 * s + 2];
-                            A.bA[(int64_t)(r * 9 + s) * A.nb + b] = avg - corr;
+                            A.bA[(int64_t)sym_idx(r, s) * A.nb + kb] = avg - corr;
                         }
                 }
             }

@@ -298,6 +298,13 @@ __device__ __forceinline__ void nh_tangent(const S G[9], S m, S mu, S lam, const
 
 // ---------------------------------------------------------------- launchers
 enum XfwdMode { XF_RESID = 0, XF_TANGENT = 1 };
+
+// Position of entry (r, s) of a symmetric 9x9 matrix in its packed upper
+// triangle (45 entries, row-major over r <= s).
+__host__ __device__ constexpr int sym_idx(int r, int s)
+{
+    return r <= s ? 9 * r - r * (r - 1) / 2 + (s - r) : 9 * s - s * (s - 1) / 2 + (r - s);
+}
 enum XinvMode { XI_FIXEDPOINT = 0, XI_RHS = 1, XI_CG = 2, XI_PLAIN = 3 };
 
 template <typename T, typename Tc> struct XfwdArgs {
@@ -319,7 +326,9 @@ template <typename T, typename Tc> struct XfwdArgs {
     const Tc* r;
     Tc* p;
     Tc* x;               // receives the previous iteration's x += alpha p
-    const Tc* bA;        // [81][nb]
+    const Tc* bA;        // [45][nb] packed symmetric boxel tangent, boxels in voxel order
+    const int32_t* bvox; // [nb] voxel of the k-th boxel in voxel order
+    const int32_t* lofs; // [n2 n3 + 1] first boxel (voxel order) of each x-line
     int64_t nb;
     // plain operand (no constitutive law): X [9][V] real
     const double* X;
@@ -406,7 +415,8 @@ template <typename Tc> struct BoxelArgs {
     const double* bc;
     double* ba;    // [nb][3] jump vectors (warm start in, converged out)
     double* bP;    // [nb][9]
-    Tc* bA;        // [81][nb] or null
+    Tc* bA;        // [45][nb] packed symmetric tangent (sym_idx), column rank[b]; or null
+    const int32_t* rank;  // position of boxel b in voxel order
     const double* F;
     double mu[2], lam[2];
     double tol_rel, tol_abs;

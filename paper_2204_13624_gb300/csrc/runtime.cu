@@ -717,6 +717,7 @@ template <typename Tc> struct Solve : SolveBase {
     uint8_t* d_phase = nullptr;
     int32_t* d_v2b = nullptr;
     int32_t* d_bidx = nullptr;
+    int32_t *d_rank = nullptr, *d_bvox = nullptr, *d_lofs = nullptr;  // boxels in voxel order
     double *d_bN = nullptr, *d_bc = nullptr, *d_ba = nullptr, *d_bP = nullptr;
     Tc* d_bA = nullptr;
     double* d_F = nullptr;
@@ -746,6 +747,9 @@ template <typename Tc> struct Solve : SolveBase {
         cudaFree(d_phase);
         cudaFree(d_v2b);
         cudaFree(d_bidx);
+        cudaFree(d_rank);
+        cudaFree(d_bvox);
+        cudaFree(d_lofs);
         cudaFree(d_bN);
         cudaFree(d_bc);
         cudaFree(d_ba);
@@ -795,7 +799,10 @@ template <typename Tc> struct Solve : SolveBase {
         CK(cudaMalloc(&d_ba, 24 * nbs));
         CK(cudaMalloc(&d_bP, 72 * nbs));
         if (newton()) {
-            CK(cudaMalloc(&d_bA, sizeof(Tc) * 81 * nbs));
+            CK(cudaMalloc(&d_bA, sizeof(Tc) * 45 * nbs));
+            CK(cudaMalloc(&d_rank, 4 * nbs));
+            CK(cudaMalloc(&d_bvox, 4 * nbs));
+            CK(cudaMalloc(&d_lofs, 4 * ((size_t)g.n2 * g.n3 + 1)));
             CK(cudaMalloc(&d_tc, sizeof(Tc) * 10 * V));
             CK(cudaMalloc(&d_x, sizeof(Tc) * 9 * V));
             CK(cudaMalloc(&d_r, sizeof(Tc) * 9 * V));
@@ -811,6 +818,26 @@ template <typename Tc> struct Solve : SolveBase {
             CK(cudaMemcpyAsync(d_bc, hp.bc.data(), 8 * nb, cudaMemcpyHostToDevice, st));
             CK(cudaMemsetAsync(d_ba, 0, 24 * nb, st));
             k_vox2box<<<(int)((nb + 255) / 256), 256, 0, st>>>(d_v2b, d_bidx, nb);
+        }
+        if (newton()) {
+            // the tangent x-pass visits each x-line's boxels in voxel order
+            const int64_t nlines = (int64_t)g.n2 * g.n3;
+            std::vector<int32_t> order(nb), rank(std::max<int64_t>(nb, 1)), bvox(std::max<int64_t>(nb, 1)), lofs(nlines + 1);
+            for (int64_t b = 0; b < nb; b++) order[b] = (int32_t)b;
+            std::stable_sort(order.begin(), order.end(), [&](int32_t u, int32_t w) { return hp.bidx[u] < hp.bidx[w]; });
+            for (int64_t k = 0; k < nb; k++) {
+                rank[order[k]] = (int32_t)k;
+                bvox[k] = hp.bidx[order[k]];
+            }
+            int64_t k = 0;
+            for (int64_t L = 0; L <= nlines; L++) {
+                while (k < nb && bvox[k] < L * g.n1) k++;
+                lofs[L] = (int32_t)k;
+            }
+            CK(cudaMemcpyAsync(d_rank, rank.data(), 4 * rank.size(), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(d_bvox, bvox.data(), 4 * bvox.size(), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(d_lofs, lofs.data(), 4 * lofs.size(), cudaMemcpyHostToDevice, st));
+            CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
         }
         k_fill_identity<<<grid_for(9 * V), 256, 0, st>>>(d_F, V);
         CK(cudaGetLastError());
@@ -839,6 +866,7 @@ template <typename Tc> struct Solve : SolveBase {
         a.ba = d_ba;
         a.bP = d_bP;
         a.bA = tangent ? d_bA : nullptr;
+        a.rank = d_rank;
         a.F = d_F;
         a.mu[0] = hp.mu[0];
         a.mu[1] = hp.mu[1];
@@ -912,6 +940,8 @@ template <typename Tc> struct Solve : SolveBase {
         xf.p = d_p;
         xf.x = d_x;
         xf.bA = d_bA;
+        xf.bvox = d_bvox;
+        xf.lofs = d_lofs;
         xf.nb = std::max<int64_t>(nb, 1);
         xf.partial = d_part;
         xf.sc = d_sc;

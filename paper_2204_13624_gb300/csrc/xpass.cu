@@ -217,29 +217,50 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 3 : 1) k_xfwd(X
                 }
 #pragma unroll
                 for (int c = 0; c < 9; c++) pg[c * V + v] = p[c];
-                Tc y[9];
                 if (ph == 2) {
-                    const int64_t b = a.vox2box[v];
+                    // boxel: p parks in the transform buffer; the boxel phase
+                    // below replaces it by A_box : p
 #pragma unroll
-                    for (int r = 0; r < 9; r++) {
-                        Tc s = 0;
-#pragma unroll
-                        for (int c = 0; c < 9; c++) s += a.bA[(int64_t)(r * 9 + c) * a.nb + b] * p[c];
-                        y[r] = s;
-                    }
+                    for (int c = 0; c < 9; c++) o[c] = (T)p[c];
                 } else {
+                    Tc y[9];
                     nh_tangent<Tc>(t, t[9], (Tc)a.mu[ph], (Tc)a.lam[ph], p, y);
-                }
-                Tc s = 0;
+                    Tc s = 0;
 #pragma unroll
-                for (int c = 0; c < 9; c++) {
-                    s += p[c] * y[c];
-                    o[c] = (T)y[c];
+                    for (int c = 0; c < 9; c++) {
+                        s += p[c] * y[c];
+                        o[c] = (T)y[c];
+                    }
+                    accp += s;
                 }
-                accp += s;
             }
 #pragma unroll
             for (int c = 0; c < 9; c++) rb[(size_t)2 * (c * LB + l) * ls + x] = o[c];
+        }
+        if constexpr (TAN) {
+            // boxels of the group, in voxel order: consecutive threads read
+            // consecutive columns of the packed tangents (coalesced, no divergence)
+            __syncthreads();
+            const int k0 = a.lofs[L0], k1 = a.lofs[min(L0 + LB, nlines)];
+            for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+                const int64_t v = a.bvox[k];
+                const int l = (int)(v / g.n1) - L0, x = (int)(v % g.n1);
+                Tc Ak[45], p[9];
+#pragma unroll
+                for (int j = 0; j < 45; j++) Ak[j] = a.bA[(int64_t)j * a.nb + k];
+#pragma unroll
+                for (int c = 0; c < 9; c++) p[c] = (Tc)rb[(size_t)2 * (c * LB + l) * ls + x];
+                Tc s = 0;
+#pragma unroll
+                for (int r = 0; r < 9; r++) {
+                    Tc yr = 0;
+#pragma unroll
+                    for (int c = 0; c < 9; c++) yr += Ak[sym_idx(r, c)] * p[c];
+                    s += p[r] * yr;
+                    rb[(size_t)2 * (r * LB + l) * ls + x] = (T)yr;
+                }
+                accp += s;
+            }
         }
         acc += (double)accp;
         __syncthreads();
