@@ -135,9 +135,9 @@ def algorithmic_bytes(kernel, p, krylov_bytes):
         return 2 * spec_c * 16
     if kernel == "xfwd_tangent":
         # r, p, x read; p, x written (x += alpha p of the previous iteration);
-        # tangent cache (9 + 1 words) at pure voxels; phase byte; boxel index and
-        # 81-entry tangent at boxels; spectrum written
-        return V * (45 * w + 1) + (V - nb) * 10 * w + nb * (4 + 81 * w) + spec_c * 2 * w
+        # tangent cache (9 + 1 words) at pure voxels; phase byte; boxel voxel
+        # index and packed symmetric 45-entry tangent at boxels; spectrum written
+        return V * (45 * w + 1) + (V - nb) * 10 * w + nb * (4 + 45 * w) + spec_c * 2 * w
     if kernel == "xinv_cg":
         # spectrum read; r read + written
         return spec_c * 2 * w + V * 18 * w
@@ -147,7 +147,7 @@ def algorithmic_bytes(kernel, p, krylov_bytes):
     if kernel == "xinv_fp64":
         return spec_c * 16 + V * 18 * w
     if kernel == "boxel_laminate":
-        return nb * (4 + 72 + 24 + 8 + 24 * 2 + 72 + 81 * w)
+        return nb * (4 + 72 + 24 + 8 + 24 * 2 + 72 + 4 + 45 * w)
     return None
 
 
