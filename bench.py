@@ -160,29 +160,34 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    with the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    try:
-        d = json.load(open(path))
-    except Exception:
-        return None
-    if d.get("csrc_hash") != csrc_hash():
-        return None
-    v = d.get("per_launch_bytes_full_size", {}).get(kernel)
-    return float(v) if v is not None else None
-
-
-def csrc_hash():
+def ncu_traffic(kernel, alg_bytes):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/ncu_traffic_<kernel>_*.txt): the captured traffic / algorithmic
+    ratio times this workload's algorithmic bytes, or None when the kernel's
+    sources changed after the capture."""
+    import glob
     import hashlib
 
-    h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2204_13624_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
-    return h.hexdigest()[:16]
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"ncu_traffic_{kernel}_*.txt"))):
+        kv = {}
+        for line in open(path):
+            if line.startswith("#") or ":" not in line:
+                continue
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+        if kv.get("kernel") != kernel or not alg_bytes:
+            continue
+        h = hashlib.sha256()
+        d = os.path.join(ROOT, "paper_2204_13624_gb300", "csrc")
+        try:
+            for f in kv["sources"].split():
+                h.update(open(os.path.join(d, f), "rb").read())
+        except OSError:
+            return None
+        if h.hexdigest()[:16] != kv.get("sources_sha256_16"):
+            return None
+        return float(kv["traffic_over_algorithmic"]) * alg_bytes
+    return None
 
 
 # ---------------------------------------------------------------- CPU baseline
@@ -287,7 +292,8 @@ def main():
         ach = table[dom]["GBps"]
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_kind": peak_kind,
-                "traffic": ncu_traffic(dom), "alg_bytes_per_launch": table[dom]["alg_bytes_per_launch"]}
+                "traffic": ncu_traffic(dom, table[dom]["alg_bytes_per_launch"]),
+                "alg_bytes_per_launch": table[dom]["alg_bytes_per_launch"]}
 
     e2e = None
     if not args.no_e2e and rank == 0:
