@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=24)
     ap.add_argument("--impl", default="combo", choices=["combo", "reference"])
-    ap.add_argument("--precision", default="refined", choices=["refined", "fp64"])
+    ap.add_argument("--precision", default="refined", choices=["refined", "refined-df", "fp64"])
     ap.add_argument("--n", type=int, default=256, help="grid side (256 = the benchmark workload)")
     ap.add_argument("--shape", default=None, help="n1,n2,n3 of a smaller ball grid (profiling captures)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -236,7 +236,7 @@ def main():
     V = p["n"][0] * p["n"][1] * p["n"][2]
     stream = torch.cuda.current_stream()
     ctx = combo.Context(local, stream.cuda_stream)
-    prec = combo.FP32_REFINED if args.precision == "refined" else combo.FP64
+    prec = {"refined": combo.FP32_REFINED, "refined-df": combo.FP32_REFINED_DF, "fp64": combo.FP64}[args.precision]
     s = combo.Solve(p, ctx=ctx, solver=combo.NEWTON_CG, precision=prec, tol=1e-8)
     s.advance(max(args.warmup, 3))
     torch.cuda.synchronize()
@@ -274,7 +274,7 @@ def main():
     value = ops_all * V / (t_max / 1e3)
 
     # per-kernel table and the dominant kernel's roofline
-    kb = 4 if prec == combo.FP32_REFINED else 8
+    kb = 8 if prec == combo.FP64 else 4
     peak, peak_kind = peaks()
     table = {}
     for k, (kms, cnt) in prof.items():
@@ -313,7 +313,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / max(ops, 1), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if prec == combo.FP32_REFINED else "f64",
+                "dtype": "f64" if prec == combo.FP64 else "f32",
                 "data": "synthetic",
                 "config": {"workload": (f"spheres_{args.shape.replace(',', 'x')}" if args.shape else
                                         (WORKLOAD if args.n == 256 else f"spheres_{args.n}")),
@@ -321,7 +321,10 @@ def main():
                            "microstructure": "seeded RSA balls r=12 vox, vf 0.25, contrast 100",
                            "load": "Fbar11 = 1.10 in 10 steps",
                            "solver": "Newton-CG, tol 1e-8, cg_tol 1e-3",
-                           "precision": "FP32 Krylov + FP64 residual/laminates/norms" if prec else "FP64",
+                           "precision": {combo.FP32_REFINED: "FP32 Krylov + FP64 residual/laminates/norms",
+                                         combo.FP32_REFINED_DF: "FP32 Krylov + double-float residual transforms, "
+                                                                "FP64 P(F)/laminates/norms",
+                                         combo.FP64: "FP64"}[prec],
                            "kspace": "rotated (HEX8R)",
                            "operator_applications": int(ops), "solve_finished_in_timed_region": bool(done),
                            "l2": "inputs larger than L2 (each 9-field >= 604 MB)",

@@ -62,6 +62,11 @@ extern "C" {
 /* precision */
 #define COMBO_FP64 0          /* every field and operator in FP64 */
 #define COMBO_FP32_REFINED 1  /* FP32 Krylov iterations, FP64 residual, F, laminates, norms */
+/* as COMBO_FP32_REFINED, but the transforms of the residual G[P(F)] run in
+   double-float arithmetic (pairs of FP32, 48-bit significand); P(F), the
+   laminates, F and the norms stay FP64.  No counterpart in the paper: an
+   arithmetic choice for GPUs whose FP64 rate is a small fraction of FP32. */
+#define COMBO_FP32_REFINED_DF 2
 /* kspace: discrete derivative of the Green operator */
 #define COMBO_ROTATED 0  /* Willot's rotated scheme (HEX8R), Sec. 3 and Sec. 6.3 */
 #define COMBO_SPECTRAL 1 /* Moulinec-Suquet trigonometric polynomials, Sec. 3 */
@@ -112,7 +117,7 @@ typedef struct {
 
 /*
  * Solver options; combo_options_default() fills the defaults given here.
- *   precision        COMBO_FP64 (default) or COMBO_FP32_REFINED
+ *   precision        COMBO_FP64 (default), COMBO_FP32_REFINED or COMBO_FP32_REFINED_DF
  *   kspace           COMBO_ROTATED (default) or COMBO_SPECTRAL
  *   solver           COMBO_NEWTON_CG (default) or COMBO_FIXED_POINT
  *   tol              equilibrium tolerance on ||G[P]||_rms / |<P>|  (1e-8)
@@ -271,7 +276,8 @@ int combo_solve_profile_read(combo_solve_state* s, int32_t max_classes, char* na
  * Unit-level entry points (same kernels as the solve).
  *
  * combo_apply_G: Y = G[X] = mu0 Gamma0[X] (Eq. Gamma0 with C0 = mu0 I),
- *   X, Y [9][V] FP64 in `mem`; precision selects the FFT precision;
+ *   X, Y [9][V] FP64 in `mem`; precision selects the FFT arithmetic (FP64,
+ *   FP32, double-float);
  *   *sumsq receives sum_x |Y(x)|^2.
  * combo_constitutive: P[9][V] (FP64) of the field F[9][V] (FP64): pure
  *   voxels Neo-Hookean (Sec. 6.1), boxels the laminate (Algorithms 1-2)

@@ -4,11 +4,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
+
 namespace combo {
 
 template <typename T> struct CxT;
 template <> struct CxT<float> { typedef float2 type; };
 template <> struct CxT<double> { typedef double2 type; };
+template <> struct CxT<df32> { typedef df2 type; };
 template <typename T> using cx = typename CxT<T>::type;
 
 template <typename V> __device__ __forceinline__ V c_add(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
@@ -24,6 +27,21 @@ template <bool INV, typename V> __device__ __forceinline__ V c_rot(V a)
     return INV ? V{-a.y, a.x} : V{a.y, -a.x};
 }
 template <typename V, typename S> __device__ __forceinline__ V c_scale(V a, S s) { return V{a.x * s, a.y * s}; }
+
+// |a|^2 + |b|^2 + |c|^2 for a residual norm: in FP64 from FP32 / FP64 values;
+// from the leading FP32 parts of double-float values (a norm used for a
+// stopping test needs no more than FP32 accuracy)
+template <typename V> __device__ __forceinline__ double sq3(V a, V b, V c)
+{
+    return (double)a.x * (double)a.x + (double)a.y * (double)a.y + (double)b.x * (double)b.x +
+           (double)b.y * (double)b.y + (double)c.x * (double)c.x + (double)c.y * (double)c.y;
+}
+__device__ __forceinline__ double sq3(df2 a, df2 b, df2 c)
+{
+    const float s = a.x.hi * a.x.hi + a.y.hi * a.y.hi + b.x.hi * b.x.hi + b.y.hi * b.y.hi + c.x.hi * c.x.hi +
+                    c.y.hi * c.y.hi;
+    return (double)s;
+}
 
 constexpr int kMaxStages = 12;
 

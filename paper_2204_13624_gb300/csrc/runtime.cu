@@ -679,7 +679,8 @@ static int load_problem(const combo_problem* p, const combo_options* o, HostProb
 
 static int check_options(combo_options& o)
 {
-    if (o.precision != COMBO_FP64 && o.precision != COMBO_FP32_REFINED) return fail(COMBO_E_INVALID_ARG, "bad precision");
+    if (o.precision != COMBO_FP64 && o.precision != COMBO_FP32_REFINED && o.precision != COMBO_FP32_REFINED_DF)
+        return fail(COMBO_E_INVALID_ARG, "bad precision");
     if (o.kspace != COMBO_ROTATED && o.kspace != COMBO_SPECTRAL) return fail(COMBO_E_INVALID_ARG, "bad kspace");
     if (o.solver != COMBO_FIXED_POINT && o.solver != COMBO_NEWTON_CG) return fail(COMBO_E_INVALID_ARG, "bad solver");
     if (o.solver == COMBO_FIXED_POINT && o.precision != COMBO_FP64)
@@ -704,15 +705,17 @@ struct combo_solve_state {
     SolveBase* impl;
 };
 
-template <typename Tc> struct Solve : SolveBase {
+// Tc: Krylov precision (float or double); Rt: arithmetic of the residual
+// transforms (double, or df32 double-float for the refined form)
+template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     combo_ctx* ctx;
     combo_options opt;
     HostProblem hp;
     GridDims g;
     int64_t nb = 0;
     cudaStream_t st;
-    Engine<double> e64;
-    Engine<Tc> ec;  // Krylov precision (same as e64 when Tc = double)
+    Engine<Rt> e64;  // residual operator G[P(F)] (P in FP64)
+    Engine<Tc> ec;   // Krylov operator
     // device memory
     uint8_t* d_phase = nullptr;
     int32_t* d_v2b = nullptr;
@@ -899,7 +902,7 @@ template <typename Tc> struct Solve : SolveBase {
         xf.nb = nb;
         xf.sc = d_sc;
         prof.begin(K_XFWD_RESID);
-        launch_xfwd<double, Tc>(xf, guard, st);
+        launch_xfwd<Rt, Tc>(xf, guard, st);
         prof.end();
         e64.yz(d_sc, guard, true, d_part, st, &prof, K_YFWD_64);
         prof.begin(K_FINALIZE);
@@ -915,7 +918,7 @@ template <typename Tc> struct Solve : SolveBase {
         xi.partial = d_part;
         xi.sc = d_sc;
         prof.begin(K_XINV_64);
-        launch_xinv<double, Tc>(xi, guard, st);
+        launch_xinv<Rt, Tc>(xi, guard, st);
         prof.end();
         if (xi_mode == XI_RHS) {
             prof.begin(K_FINALIZE);
@@ -1177,6 +1180,27 @@ template <typename Tc> struct Solve : SolveBase {
     }
 };
 
+// A solve of the requested precision form: plain FP64; FP32 Krylov with FP64
+// residual transforms; FP32 Krylov with double-float residual transforms.
+static int make_solve(combo_ctx* ctx, HostProblem&& h, const combo_options& o, SolveBase** out)
+{
+    int rc;
+    if (o.precision == COMBO_FP64) {
+        auto* s = new Solve<double, double>();
+        rc = s->init(ctx, std::move(h), o);
+        *out = s;
+    } else if (o.precision == COMBO_FP32_REFINED) {
+        auto* s = new Solve<float, double>();
+        rc = s->init(ctx, std::move(h), o);
+        *out = s;
+    } else {
+        auto* s = new Solve<float, df32>();
+        rc = s->init(ctx, std::move(h), o);
+        *out = s;
+    }
+    return rc;
+}
+
 // ------------------------------------------------------------------ C ABI: solves
 extern "C" int64_t combo_solve_footprint(const combo_problem* p, const combo_options* o)
 {
@@ -1184,7 +1208,7 @@ extern "C" int64_t combo_solve_footprint(const combo_problem* p, const combo_opt
     const int64_t V = (int64_t)p->n[0] * p->n[1] * p->n[2];
     const GridDims g = make_dims(p->n);
     const int64_t nb = std::max<int64_t>(p->n_boxels, 1);
-    const int64_t tc = (o->precision == COMBO_FP32_REFINED) ? 4 : 8;
+    const int64_t tc = (o->precision == COMBO_FP64) ? 8 : 4;
     int64_t b = V * (1 + 4 + 72) + 16 * 9 * g.Vs + nb * (4 + 24 + 8 + 24 + 72);
     if (o->solver == COMBO_NEWTON_CG) b += tc * (81 * nb + 37 * V);
     return b;
@@ -1205,15 +1229,7 @@ extern "C" int combo_solve_begin(combo_ctx* ctx, const combo_problem* p, const c
     HostProblem h;
     if ((rc = load_problem(p, &o, h))) return rc;
     SolveBase* impl = nullptr;
-    if (o.precision == COMBO_FP64) {
-        auto* s = new Solve<double>();
-        rc = s->init(ctx, std::move(h), o);
-        impl = s;
-    } else {
-        auto* s = new Solve<float>();
-        rc = s->init(ctx, std::move(h), o);
-        impl = s;
-    }
+    rc = make_solve(ctx, std::move(h), o, &impl);
     if (rc) {
         std::string msg = g_err;
         delete impl;
@@ -1335,17 +1351,19 @@ template <typename T> static int apply_G_impl(combo_ctx* ctx, const int32_t n[3]
     CKC(cudaMalloc(&sc, sizeof(Scalars)));
     CKC(cudaMemsetAsync(sc, 0, sizeof(Scalars), st));
     e.bind_spec(spec);
-    auto xf = e.template xf<T>();
+    // (the Krylov word type only matters for the solver modes of the x-passes)
+    typedef typename std::conditional<std::is_same<T, df32>::value, float, T>::type Tk;
+    auto xf = e.template xf<Tk>();
     xf.X = dX;
     xf.sc = sc;
-    launch_xfwd<T, T>(xf, 0, st);
+    launch_xfwd<T, Tk>(xf, 0, st);
     e.yz(sc, 0, true, part, st);
     k_fin_resid<<<1, 256, 0, st>>>(sc, part, e.zblocks(), (double)V, 0.0, 0, 0, 0);
-    auto xi = e.template xi<T>();
+    auto xi = e.template xi<Tk>();
     xi.mode = XI_PLAIN;
     xi.Y = dY;
     xi.sc = sc;
-    launch_xinv<T, T>(xi, 0, st);
+    launch_xinv<T, Tk>(xi, 0, st);
     CKC(cudaGetLastError());
     Scalars s;
     CKC(cudaMemcpyAsync(&s, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
@@ -1367,6 +1385,7 @@ extern "C" int combo_apply_G(combo_ctx* ctx, const int32_t n[3], const double l[
     CK(cudaSetDevice(ctx->device));
     if (precision == COMBO_FP64) return apply_G_impl<double>(ctx, n, l, kspace, X, Y, sumsq, mem);
     if (precision == COMBO_FP32_REFINED) return apply_G_impl<float>(ctx, n, l, kspace, X, Y, sumsq, mem);
+    if (precision == COMBO_FP32_REFINED_DF) return apply_G_impl<df32>(ctx, n, l, kspace, X, Y, sumsq, mem);
     return fail(COMBO_E_INVALID_ARG, "bad precision");
 }
 
@@ -1458,7 +1477,7 @@ int64_t footprint_of(const HostProblem& h, const combo_options& o)
     const GridDims g = make_dims(h.n);
     const int64_t V = g.V;
     const int64_t nb = std::max<int64_t>((int64_t)h.bidx.size(), 1);
-    const int64_t tc = (o.precision == COMBO_FP32_REFINED) ? 4 : 8;
+    const int64_t tc = (o.precision == COMBO_FP64) ? 8 : 4;
     int64_t b = V * (1 + 4 + 72) + 16 * 9 * g.Vs + nb * (4 + 24 + 8 + 24 + 72) + (1 << 20);
     if (o.solver == COMBO_NEWTON_CG) b += tc * (81 * nb + 37 * V);
     return b;
@@ -1516,15 +1535,7 @@ static void run_request(ServeReq* r, combo_ctx* wctx, combo_server* S)
     int rc;
     const int32_t n_steps = r->hp.n_steps;
     const int64_t V = (int64_t)r->hp.n[0] * r->hp.n[1] * r->hp.n[2];
-    if (r->opt.precision == COMBO_FP64) {
-        auto* s = new Solve<double>();
-        rc = s->init(wctx, std::move(r->hp), r->opt);
-        impl = s;
-    } else {
-        auto* s = new Solve<float>();
-        rc = s->init(wctx, std::move(r->hp), r->opt);
-        impl = s;
-    }
+    rc = make_solve(wctx, std::move(r->hp), r->opt, &impl);
     const bool inited = (rc == 0);
     if (inited) {
         {

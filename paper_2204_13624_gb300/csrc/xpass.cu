@@ -418,13 +418,17 @@ template <typename T, typename Tc, int MF> static void xfwd_launch(const XfwdArg
 {
     const int grid = xpass_grid(a.g, a.lines_per_block);
     const size_t sm = xpass_smem(a.g, a.lines_per_block, sizeof(cx<T>));
-    if (a.mode == XF_TANGENT && !a.X) {
-        // one wave: the FP32 instance is register-capped to three blocks per SM
-        const int tgrid = sizeof(T) == 4 ? std::min(grid, 3 * (grid_cap(a.g) / 4)) : grid;
-        static bool attr = false;
-        allow_smem(k_xfwd<T, Tc, MF, true>, attr);
-        k_xfwd<T, Tc, MF, true><<<tgrid, 256, sm, st>>>(a, guard);
-    } else {
+    if constexpr (std::is_same<T, Tc>::value) {  // the tangent pass runs in the Krylov precision
+        if (a.mode == XF_TANGENT && !a.X) {
+            // one wave: the FP32 instance is register-capped to three blocks per SM
+            const int tgrid = sizeof(T) == 4 ? std::min(grid, 3 * (grid_cap(a.g) / 4)) : grid;
+            static bool attr = false;
+            allow_smem(k_xfwd<T, Tc, MF, true>, attr);
+            k_xfwd<T, Tc, MF, true><<<tgrid, 256, sm, st>>>(a, guard);
+            return;
+        }
+    }
+    {
         static bool attr = false;
         allow_smem(k_xfwd<T, Tc, MF, false>, attr);
         k_xfwd<T, Tc, MF, false><<<grid, 256, sm, st>>>(a, guard);
@@ -474,5 +478,7 @@ template void launch_xfwd<float, float>(const XfwdArgs<float, float>&, int, cuda
 template void launch_xinv<double, double>(const XinvArgs<double, double>&, int, cudaStream_t);
 template void launch_xinv<double, float>(const XinvArgs<double, float>&, int, cudaStream_t);
 template void launch_xinv<float, float>(const XinvArgs<float, float>&, int, cudaStream_t);
+template void launch_xfwd<df32, float>(const XfwdArgs<df32, float>&, int, cudaStream_t);
+template void launch_xinv<df32, float>(const XinvArgs<df32, float>&, int, cudaStream_t);
 
 }  // namespace combo

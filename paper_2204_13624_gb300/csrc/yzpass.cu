@@ -133,8 +133,7 @@ __global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
             o2 = cx<T>{k2 * sr, k2 * si};
             if (a.want_norm) {
                 const double wgt = (xi1 == 0 || xi1 == g.M) ? 1.0 : 2.0;
-                acc += wgt * ((double)o0.x * o0.x + (double)o0.y * o0.y + (double)o1.x * o1.x + (double)o1.y * o1.y +
-                              (double)o2.x * o2.x + (double)o2.y * o2.y);
+                acc += wgt * sq3(o0, o1, o2);
             }
         }
         p[0] = c_scale(o0, a.scale);
@@ -222,8 +221,7 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<
             o2 = cx<T>{k2 * sr, k2 * si};
             if (a.want_norm) {
                 const double wgt = (xi1 == 0 || xi1 == g.M) ? 1.0 : 2.0;
-                acc += wgt * ((double)o0.x * o0.x + (double)o0.y * o0.y + (double)o1.x * o1.x + (double)o1.y * o1.y +
-                              (double)o2.x * o2.x + (double)o2.y * o2.y);
+                acc += wgt * sq3(o0, o1, o2);
             }
         }
         p[0] = c_scale(o0, a.scale);
@@ -335,5 +333,8 @@ template void launch_ypass<float, false>(const YArgs<float>&, cudaStream_t);
 template void launch_ypass<float, true>(const YArgs<float>&, cudaStream_t);
 template void launch_zpass<double>(const ZArgs<double>&, cudaStream_t);
 template void launch_zpass<float>(const ZArgs<float>&, cudaStream_t);
+template void launch_ypass<df32, false>(const YArgs<df32>&, cudaStream_t);
+template void launch_ypass<df32, true>(const YArgs<df32>&, cudaStream_t);
+template void launch_zpass<df32>(const ZArgs<df32>&, cudaStream_t);
 
 }  // namespace combo

@@ -54,6 +54,20 @@ def test_green_operator_fp32(cb, orc, n):
     assert abs(ssg - sso) <= 1e-5 * sso
 
 
+@pytest.mark.parametrize("n", SHAPES)
+def test_green_operator_double_float(cb, orc, n):
+    """The double-float transforms of the refined residual: 48-bit significand,
+    so G[X] agrees with the FP64 oracle far below the FP32 error."""
+    rng = np.random.default_rng(sum(n) + 7)
+    V = n[0] * n[1] * n[2]
+    l = (1.0, 0.8, 1.3)
+    X = rng.normal(size=(9, V))
+    Yo, sso = orc.apply_G(X, n, l, 0)
+    Yg, ssg = cb.apply_G(X, n, l, 0, cb.FP32_REFINED_DF)
+    assert rel(Yg, Yo) < 1e-11
+    assert abs(ssg - sso) <= 1e-5 * sso  # the norm is summed from the leading FP32 parts
+
+
 def test_constitutive_matches_oracle(cb, orc):
     from paper_2204_13624_gb300 import microstructure as ms
 
@@ -113,7 +127,7 @@ def test_newton_cg_parity(cb, orc, k, kspace):
     assert abs(g["n_backproj"] - r["n_backproj"]) <= max(2, 1e-3 * r["n_backproj"])
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_newton_cg_parity_fast_sizes(cb, orc, prec):
     """64^3, 64 x 32 x 128 and 128 x 64 x 256 grids run the compile-time FFT plans in every
     pass (and the TMA-tiled FP32 z-pass at n3 = 64, 128, 256)."""
@@ -141,12 +155,14 @@ def test_sphere_32_converged_fp64(cb, orc):
     assert rel(g["F"], r["F"]) < 1e-9
 
 
-def test_sphere_32_refined_fp32(cb, orc):
-    """FP32 Krylov iterations with FP64 residual refinement against the FP64 oracle."""
+@pytest.mark.parametrize("prec", [1, 2])
+def test_sphere_32_refined_fp32(cb, orc, prec):
+    """FP32 Krylov iterations with FP64 (1) or double-float (2) residual
+    refinement against the FP64 oracle."""
     from paper_2204_13624_gb300 import microstructure as ms
 
     p = ms.sphere_32()
-    g = cb.solve(p, solver=1, precision=cb.FP32_REFINED, tol=1e-8)
+    g = cb.solve(p, solver=1, precision=prec, tol=1e-8)
     r = orc.solve(p, dict(solver=1, tol=1e-10, cg_tol=1e-4))
     assert g["steps_done"] == 5 and np.all(g["resid"] <= 1e-8)
     assert rel(g["Pbar"], r["Pbar"]) < 1e-5
