@@ -3,8 +3,9 @@
 Workload (default): 256^3 periodic grid of seeded random non-overlapping
 balls of radius 12 voxels at volume fraction 0.25, Neo-Hookean contrast 100,
 uniaxial stretch to Fbar11 = 1.10 in 10 load steps; Newton-CG with FP32
-Krylov iterations, FP64 laminate solves, FP64 residuals and norms
-(``--precision fp64`` runs every operator in FP64).
+Krylov iterations, FP64 laminate solves, FP64 constitutive law and norms,
+residual transforms in double-float arithmetic (``--precision refined``
+keeps them in FP64, ``--precision fp64`` runs every operator in FP64).
 
 A step is one operator application of the solve -- one voxel-iteration per
 voxel: tangent (or constitutive law + boxel laminates), forward FFT, Green
@@ -44,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=24)
     ap.add_argument("--impl", default="combo", choices=["combo", "reference"])
-    ap.add_argument("--precision", default="refined", choices=["refined", "refined-df", "fp64"])
+    ap.add_argument("--precision", default="refined-df", choices=["refined-df", "refined", "fp64"])
     ap.add_argument("--n", type=int, default=256, help="grid side (256 = the benchmark workload)")
     ap.add_argument("--shape", default=None, help="n1,n2,n3 of a smaller ball grid (profiling captures)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -396,7 +397,7 @@ def serving_bench(combo, ctx, count=12, sides=(48, 64, 72, 96), max_steps=4, slo
     probs = serving_problems(count, seed, sides, max_steps)
     out = {"requests": count, "sides": list(sides), "load_steps": f"1..{max_steps}", "slots": slots}
     pbar = {}
-    for form, prec in (("refined", combo.FP32_REFINED), ("fp64", combo.FP64)):
+    for form, prec in (("refined", combo.FP32_REFINED_DF), ("fp64", combo.FP64)):
         srv = combo.Server(ctx, max_slots=slots)
         t0 = time.perf_counter()
         tk = [srv.submit(p, precision=prec, tol=1e-8) for p in probs]
