@@ -409,6 +409,7 @@ template <typename T> void launch_zpass(const ZArgs<T>& a, cudaStream_t st);
 size_t xpass_smem(const GridDims& g, int lines, size_t cxbytes);
 int xpass_lines(const GridDims& g, size_t cxbytes);
 int xpass_grid(const GridDims& g, int lines);  // x-pass blocks (= partial count)
+int xpass_partials_max(const GridDims& g);     // upper bound of any x-pass grid
 int ypass_tx(int n, size_t cxbytes);  // columns per y-pass block (must match the launcher)
 int zpass_tx(int n, size_t cxbytes);  // columns per z-pass block (sets the partial count)
 

@@ -430,6 +430,7 @@ template <typename T> struct Engine {
     }
     int zblocks() const { return ((g.nh + txz - 1) / txz) * g.n2 * 3; }
     int xblocks() const { return xpass_grid(g, lines); }
+    int xpartials() const { return std::max(xpass_grid(g, lines), xpass_partials_max(g)); }
 };
 
 // ------------------------------------------------------------------ small kernels
@@ -791,7 +792,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         CK(cudaMalloc(&d_F, 8 * 9 * V));
         CK(cudaMalloc(&d_spec, sizeof(double2) * 9 * g.Vs));
         CK(cudaMemsetAsync(d_spec, 0, sizeof(double2) * 9 * g.Vs, st));
-        const int nbuf = std::max(std::max(e64.xblocks(), e64.zblocks()), std::max(ec.xblocks(), ec.zblocks()));
+        const int nbuf = std::max(std::max(e64.xpartials(), e64.zblocks()), std::max(ec.xpartials(), ec.zblocks()));
         CK(cudaMalloc(&d_part, 8 * (size_t)nbuf));
         CK(cudaMalloc(&d_sc, sizeof(Scalars)));
         CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars), st));

@@ -50,6 +50,8 @@ static int grid_cap(const GridDims&)
     return 4 * nsm;
 }
 
+int xpass_partials_max(const GridDims& g) { return 2 * grid_cap(g); }
+
 int xpass_grid(const GridDims& g, int lines)
 {
     const int groups = (g.n2 * g.n3 + lines - 1) / lines;
@@ -117,6 +119,43 @@ __device__ __forceinline__ bool nh_stress(const double F[9], double mu, double l
     return true;
 }
 
+// The same stress with the cofactors, J, F^{-1} and P in double-float and
+// ln J in FP64 (one log per voxel); G and m, the tangent cache of the FP32
+// Krylov iterations, are rounded to FP32.  False if J <= 0.
+__device__ __forceinline__ bool nh_stress_df(const double Fd[9], double mu, double lam, df32 P[9], float G[9],
+                                             float& m)
+{
+    df32 F[9];
+#pragma unroll
+    for (int c = 0; c < 9; c++) F[c] = df32(Fd[c]);
+    const df32 c0 = F[4] * F[8] - F[5] * F[7];
+    const df32 c1 = F[5] * F[6] - F[3] * F[8];
+    const df32 c2 = F[3] * F[7] - F[4] * F[6];
+    const df32 J = F[0] * c0 + F[1] * c1 + F[2] * c2;
+    if (!(J.hi > 0.f)) return false;
+    const df32 iJ = df32(1.f, 0.f) / J;
+    df32 Gi[9];
+    Gi[0] = c0 * iJ;
+    Gi[1] = (F[2] * F[7] - F[1] * F[8]) * iJ;
+    Gi[2] = (F[1] * F[5] - F[2] * F[4]) * iJ;
+    Gi[3] = c1 * iJ;
+    Gi[4] = (F[0] * F[8] - F[2] * F[6]) * iJ;
+    Gi[5] = (F[2] * F[3] - F[0] * F[5]) * iJ;
+    Gi[6] = c2 * iJ;
+    Gi[7] = (F[1] * F[6] - F[0] * F[7]) * iJ;
+    Gi[8] = (F[0] * F[4] - F[1] * F[3]) * iJ;
+    const double lnJ = log((double)J);
+    const df32 k = df32(lam * lnJ - mu), mud = df32(mu);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) P[3 * i + j] = mud * F[3 * i + j] + k * Gi[3 * j + i];
+#pragma unroll
+    for (int c = 0; c < 9; c++) G[c] = (float)Gi[c];
+    m = (float)(mu - lam * lnJ);
+    return true;
+}
+
 // ------------------------------------------------------------- x forward
 // TAN: the Krylov tangent pass (a.mode == XF_TANGENT, no external X), whose
 // FP32 instance is register-capped for three resident blocks per SM
@@ -172,6 +211,22 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 3 : 1) k_xfwd(X
                     if (a.tc) {
 #pragma unroll
                         for (int c = 0; c < 10; c++) a.tc[c * V + v] = (Tc)0;
+                    }
+                } else if constexpr (std::is_same<T, df32>::value) {
+                    float G[9], m;
+                    if (!nh_stress_df(F, a.mu[ph], a.lam[ph], o, G, m)) {
+                        raise_status(a.sc, COMBO_E_INADMISSIBLE);
+#pragma unroll
+                        for (int c = 0; c < 9; c++) {
+                            o[c] = df32(0.f, 0.f);
+                            G[c] = 0.f;
+                        }
+                        m = 0.f;
+                    }
+                    if (a.tc) {
+#pragma unroll
+                        for (int c = 0; c < 9; c++) a.tc[c * V + v] = (Tc)G[c];
+                        a.tc[9 * V + v] = (Tc)m;
                     }
                 } else {
                     double P[9], G[9], m;
@@ -420,11 +475,31 @@ template <typename T, typename Tc, int MF> static void xfwd_launch(const XfwdArg
     const size_t sm = xpass_smem(a.g, a.lines_per_block, sizeof(cx<T>));
     if constexpr (std::is_same<T, Tc>::value) {  // the tangent pass runs in the Krylov precision
         if (a.mode == XF_TANGENT && !a.X) {
-            // one wave: the FP32 instance is register-capped to three blocks per SM
-            const int tgrid = sizeof(T) == 4 ? std::min(grid, 3 * (grid_cap(a.g) / 4)) : grid;
             static bool attr = false;
             allow_smem(k_xfwd<T, Tc, MF, true>, attr);
-            k_xfwd<T, Tc, MF, true><<<tgrid, 256, sm, st>>>(a, guard);
+            if constexpr (sizeof(T) == 4 && MF > 0) {
+                // FP32: small blocks of 128 threads whose FFT phase keeps most
+                // of them busy (9 lines x TPL threads per x-line), as many
+                // resident per SM as registers allow, one wave
+                constexpr int TPL = FastPlan<MF>::TPL;
+                int lb = a.lines_per_block;
+                while (lb > 1 && 9 * lb * TPL > 128) lb >>= 1;
+                const int threads = (9 * lb * TPL <= 128) ? 128 : 256;
+                XfwdArgs<T, Tc> b = a;
+                b.lines_per_block = lb;
+                const size_t smb = xpass_smem(a.g, lb, sizeof(cx<T>));
+                static int per_sm = 0;
+                if (per_sm == 0 &&
+                    (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xfwd<T, Tc, MF, true>, threads, smb) !=
+                         cudaSuccess ||
+                     per_sm < 1))
+                    per_sm = 1;
+                const int groups = (a.g.n2 * a.g.n3 + lb - 1) / lb;
+                const int tgrid = std::min(groups, std::min(per_sm * (grid_cap(a.g) / 4), xpass_partials_max(a.g)));
+                k_xfwd<T, Tc, MF, true><<<tgrid, threads, smb, st>>>(b, guard);
+            } else {
+                k_xfwd<T, Tc, MF, true><<<grid, 256, sm, st>>>(a, guard);
+            }
             return;
         }
     }
