@@ -217,7 +217,8 @@ __device__ __forceinline__ void raise_status(Scalars* sc, int code)
 }
 
 // Deterministic sum of n partials by one block: fixed strided accumulation
-// (4 independent chains) then a fixed tree.  red: >= blockDim.x doubles.
+// (4 independent chains) then a fixed tree.  red: >= blockDim.x rounded up to
+// a power of two doubles (blockDim.x <= 256 with the 256-entry buffers).
 // All threads call it; every thread gets the total.
 __device__ __forceinline__ double sum_partials_fixed(const double* p, int n, double* red)
 {
@@ -231,10 +232,13 @@ __device__ __forceinline__ double sum_partials_fixed(const double* p, int n, dou
         a3 += __ldcg(p + i + 3 * bd);
     }
     for (; i < n; i += bd) a0 += __ldcg(p + i);
+    int pw = 1;  // tree over the next power of two, zero-padded
+    while (pw < bd) pw <<= 1;
     __syncthreads();
     red[tid] = (a0 + a1) + (a2 + a3);
+    if (tid + bd < pw) red[tid + bd] = 0.0;
     __syncthreads();
-    for (int o = bd / 2; o > 0; o >>= 1) {
+    for (int o = pw / 2; o > 0; o >>= 1) {
         if (tid < o) red[tid] += red[tid + o];
         __syncthreads();
     }

@@ -8,6 +8,8 @@
 // completion counted on an mbarrier).  Outputs are written with ordinary
 // coalesced stores.  Waits are bounded: a block that exhausts the cap
 // raises COMBO_E_TIMEOUT, waits (bounded) for its own copies and returns.
+#include <algorithm>
+
 #include "async_copy.cuh"
 #include "combo_internal.cuh"
 #include "fft_fast.cuh"
@@ -39,33 +41,45 @@ int num_sms()
 }  // namespace
 
 // ------------------------------------------------------------- CG x-inverse
-// stage layout: spectrum rows [9][LB][lsx] complex, then r rows [9][LB][n1]
-template <int M>
-__global__ void __launch_bounds__(256) k_xinv_stream(XinvArgs<float, float> a, int LB)
+// Thread q * TPL + tau transforms line q = c * LB + l of the group with the
+// TPL threads of its compile-time plan; the block has just enough warps.
+template <int M, int LB> __host__ __device__ constexpr int xinv_threads()
+{
+    return (9 * LB * FastPlan<M>::TPL + 31) / 32 * 32;
+}
+
+// stage layout: spectrum rows [9][LB][lsx] complex, then r rows [9][LB][n1].
+// Per group: the first FFT stage reads the spectrum rows and forms the packed
+// half-length input (Hermitian combine) on the fly; the last stage hands each
+// output pair straight to the CG update r -= alpha G[A:p] and (r, r).
+template <int M, int LB>
+__global__ void __launch_bounds__(xinv_threads<M, LB>()) k_xinv_stream(XinvArgs<float, float> a)
 {
     if (a.sc->cg_done) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int n1 = 2 * M;
     constexpr int lsx = (M + 2) / 2 * 2;  // M + 1 rounded up to even: 16-byte rows
+    constexpr int TPL = FastPlan<M>::TPL;
+    constexpr int NL = 9 * LB;
+    constexpr size_t SPEC = (size_t)NL * lsx * 8;
+    constexpr size_t SB = SPEC + (size_t)NL * n1 * 4;
     const GridDims g = a.g;
-    const size_t spec_bytes = (size_t)9 * LB * lsx * 8;
-    const size_t sb = spec_bytes + (size_t)9 * LB * n1 * 4;
-    unsigned char* stage[2] = {smem_raw, smem_raw + sb};
-    float2* buf1 = reinterpret_cast<float2*>(smem_raw + 2 * sb);
-    float2* buf2 = buf1 + (size_t)9 * LB * lsx;
-    double* red = reinterpret_cast<double*>(buf2 + (size_t)9 * LB * lsx);
+    unsigned char* stage[2] = {smem_raw, smem_raw + SB};
+    float2* xb = reinterpret_cast<float2*>(smem_raw + 2 * SB);  // exchange rows [NL][lsx]
+    float2* w2 = xb + (size_t)NL * lsx;                          // exp(-2 pi i k / n1), k < M
+    double* red = reinterpret_cast<double*>(w2 + M);
     int* flag = reinterpret_cast<int*>(red + 256);
     uint64_t* bar = reinterpret_cast<uint64_t*>(flag + 4);
 
     const int nlines = g.n2 * g.n3;
-    const int ngroups = nlines / LB;
+    const int ngroups = nlines / LB;  // the launcher guarantees nlines % LB == 0
     const int64_t V = g.V;
     const float alpha = (float)a.sc->alpha;
-    const uint32_t tx_bytes = (uint32_t)(9 * LB * lsx * 8 + 9 * LB * n1 * 4);
+    constexpr uint32_t tx_bytes = (uint32_t)SB;
 
     auto issue = [&](int grp, int s) {
         float2* sp = reinterpret_cast<float2*>(stage[s]);
-        float* rr = reinterpret_cast<float*>(stage[s] + spec_bytes);
+        float* rr = reinterpret_cast<float*>(stage[s] + SPEC);
         mbar_arrive_expect_tx(&bar[s], tx_bytes);
         for (int l = 0; l < LB; l++) {
             const int L = grp * LB + l;
@@ -76,6 +90,7 @@ __global__ void __launch_bounds__(256) k_xinv_stream(XinvArgs<float, float> a, i
         }
     };
 
+    for (int k = threadIdx.x; k < M; k += blockDim.x) w2[k] = a.tw2[k];
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -84,10 +99,13 @@ __global__ void __launch_bounds__(256) k_xinv_stream(XinvArgs<float, float> a, i
     __syncthreads();
     if (threadIdx.x == 0 && (int)blockIdx.x < ngroups) issue(blockIdx.x, 0);
 
+    const int q = threadIdx.x / TPL, tau = threadIdx.x - (threadIdx.x / TPL) * TPL;
+    const bool act = q < NL;
+    const int c = act ? q / LB : 0, l = act ? q - (q / LB) * LB : 0;
+    float2* xq = xb + (size_t)(act ? q : 0) * lsx;
     double acc = 0.0;
     int it = 0;
     bool timed_out = false;
-    const int nl = 9 * LB;
     for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, it++) {
         const int s = it & 1;
         const int nxt = grp + gridDim.x;
@@ -100,34 +118,34 @@ __global__ void __launch_bounds__(256) k_xinv_stream(XinvArgs<float, float> a, i
             timed_out = true;
             break;
         }
-        const float2* X = reinterpret_cast<const float2*>(stage[s]);
-        const float* rr = reinterpret_cast<const float*>(stage[s] + spec_bytes);
-        // Z[k] = Ze + i Zo,  Ze = (X[k] + conj X[M-k]) / 2,  Zo = (X[k] - conj X[M-k]) W^{-k} / 2
-        for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
-            const int q = e / M, k = e - q * M;
-            const float2 A = X[(size_t)q * lsx + k];
-            const float2 Bc = c_conj(X[(size_t)q * lsx + (M - k)]);
-            const float2 Ze = c_scale(c_add(A, Bc), 0.5f);
-            const float2 Zo = c_mul(c_scale(c_sub(A, Bc), 0.5f), c_conj(a.tw2[k]));
-            buf1[(size_t)q * lsx + k] = float2{Ze.x - Zo.y, Ze.y + Zo.x};
-        }
-        __syncthreads();
-        float2* Zr = fft_lines_fast<float, M, true>(buf1, buf2, nl, lsx, a.tw);
-        const float* gq = reinterpret_cast<const float*>(Zr);
-        const int L0 = grp * LB;
+        const float2* X = reinterpret_cast<const float2*>(stage[s]) + (size_t)(act ? q : 0) * lsx;
+        const float* rr = reinterpret_cast<const float*>(stage[s] + SPEC) + (size_t)(act ? q : 0) * n1;
+        float* rg = a.r + (int64_t)c * V + (int64_t)(grp * LB + l) * n1;
         float accp = 0.f;
-        for (int e = threadIdx.x; e < LB * n1; e += blockDim.x) {
-            const int l = e / n1, x = e - l * n1;
-            const int64_t v = (int64_t)(L0 + l) * n1 + x;
-#pragma unroll
-            for (int c = 0; c < 9; c++) {
-                const float rn = rr[((size_t)c * LB + l) * n1 + x] - alpha * gq[(size_t)2 * (c * LB + l) * lsx + x];
-                a.r[c * V + v] = rn;
-                accp += rn * rn;
-            }
-        }
+        // Z[k] = Ze + i Zo,  Ze = (X[k] + conj X[M-k]) / 2,  Zo = (X[k] - conj X[M-k]) W^{-k} / 2
+        auto lg = [&](int k) -> float2 {
+            if (!act) return float2{0.f, 0.f};
+            const float2 A = X[k];
+            const float2 Bc = c_conj(X[M - k]);
+            const float2 Ze = c_scale(c_add(A, Bc), 0.5f);
+            const float2 Zo = c_mul(c_scale(c_sub(A, Bc), 0.5f), c_conj(w2[k]));
+            return float2{Ze.x - Zo.y, Ze.y + Zo.x};
+        };
+        auto lx = [&](int e) -> float2 { return act ? xq[e] : float2{0.f, 0.f}; };
+        auto sx = [&](int e, float2 v) {
+            if (act) xq[e] = v;
+        };
+        // output e of the packed inverse holds the reals 2e, 2e + 1
+        auto sg = [&](int e, float2 v) {
+            if (!act) return;
+            const float2 r0 = *reinterpret_cast<const float2*>(rr + 2 * e);
+            const float2 rn = float2{r0.x - alpha * v.x, r0.y - alpha * v.y};
+            *reinterpret_cast<float2*>(rg + 2 * e) = rn;
+            accp += rn.x * rn.x + rn.y * rn.y;
+        };
+        fft_fast<float, M, true, false, false>(lg, sg, lx, sx, tau, a.tw);
         acc += (double)accp;
-        __syncthreads();
+        __syncthreads();  // stage s and the exchange rows are reused
     }
     if (timed_out) {
         if (threadIdx.x == 0) {
@@ -155,26 +173,36 @@ bool stream_xpass_ok(const GridDims& g)
     return (M == 64 || M == 128 || M == 256) && (g.n1 % 16) == 0 && (g.n2 * g.n3) % stream_lines(g) == 0;
 }
 
-template <int M> static void xinv_stream_launch(const XinvArgs<float, float>& a, cudaStream_t st)
+template <int M, int LB> static void xinv_stream_launch(const XinvArgs<float, float>& a, cudaStream_t st)
 {
-    const int LB = stream_lines(a.g);
     constexpr int lsx = (M + 2) / 2 * 2;
-    const size_t sb = (size_t)9 * LB * lsx * 8 + (size_t)9 * LB * 2 * M * 4;
-    const size_t sm = 2 * sb + (size_t)2 * 9 * LB * lsx * 8 + 256 * 8 + 16 + 16;
-    const int per_sm = sm > 72 * 1024 ? 2 : 3;
+    constexpr int threads = xinv_threads<M, LB>();
+    constexpr size_t sb = (size_t)9 * LB * lsx * 8 + (size_t)9 * LB * 2 * M * 4;
+    constexpr size_t sm = 2 * sb + (size_t)9 * LB * lsx * 8 + (size_t)M * 8 + 256 * 8 + 16 + 16;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(k_xinv_stream<M, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xinv_stream<M, LB>, threads, sm) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+    }
     const int groups = a.g.n2 * a.g.n3 / LB;
-    const int grid = groups < per_sm * num_sms() ? groups : per_sm * num_sms();
-    static bool attr = false;
-    allow_smem_stream(k_xinv_stream<M>, attr);
-    k_xinv_stream<M><<<grid, 256, sm, st>>>(a, LB);
+    const int grid = std::min(groups, std::min(per_sm * num_sms(), xpass_partials_max(a.g)));
+    k_xinv_stream<M, LB><<<grid, threads, sm, st>>>(a);
 }
 
 void launch_xinv_stream(const XinvArgs<float, float>& a, cudaStream_t st)
 {
+    const int LB = stream_lines(a.g);
     switch (a.g.M) {
-        case 64: xinv_stream_launch<64>(a, st); break;
-        case 128: xinv_stream_launch<128>(a, st); break;
-        default: xinv_stream_launch<256>(a, st); break;
+        case 64:
+            if (LB == 2)
+                xinv_stream_launch<64, 2>(a, st);
+            else
+                xinv_stream_launch<64, 1>(a, st);
+            break;
+        case 128: xinv_stream_launch<128, 1>(a, st); break;
+        default: xinv_stream_launch<256, 1>(a, st); break;
     }
 }
 
