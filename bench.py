@@ -278,12 +278,17 @@ def main():
     kb = 8 if prec == combo.FP64 else 4
     peak, peak_kind = peaks()
     table = {}
+    krylov = ("xfwd_tangent", "yfwd_krylov", "zgamma_krylov", "yinv_krylov", "xinv_cg")
     for k, (kms, cnt) in prof.items():
         if cnt == 0:
             continue
         b = algorithmic_bytes(k, p, kb)
-        per = kms / cnt if cnt else 0.0
-        table[k] = {"ms_total": kms, "launches": cnt, "ms_per_launch": per,
+        # CG kernels are launched in graph chunks of 8 iterations; launches
+        # past the converged iteration return at once and do no work, so the
+        # per-launch time divides by the iterations that ran (ops)
+        work = min(cnt, ops) if k in krylov else cnt
+        per = kms / work if work else 0.0
+        table[k] = {"ms_total": kms, "launches": cnt, "launches_with_work": work, "ms_per_launch": per,
                     "alg_bytes_per_launch": b, "GBps": (b / (per / 1e3) / 1e9) if (b and per > 0) else None}
     hot = {k: v for k, v in table.items() if v["alg_bytes_per_launch"] and k not in ("boxel_laminate",)}
     dom = max(hot, key=lambda k: hot[k]["ms_total"]) if hot else None

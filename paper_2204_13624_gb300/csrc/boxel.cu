@@ -14,6 +14,8 @@
 //   N.A.N      = mu |N|^2 I + (lam + m) g (x) g
 //   (A D)_(iJ),k = mu d_ik N_J + lam G_Ji g_k + m G_Jk g_i
 // so the Hessian and the tangent correction need no 9x9 products.
+#include <type_traits>
+
 #include "combo_internal.cuh"
 #include "../../include/combo.h"
 
@@ -122,6 +124,118 @@ __device__ __forceinline__ bool inv3(const double A[9], double B[9])
     return true;
 }
 
+// ---- double-float form of the laminate solve (refined precision form with
+// double-float residuals): the phase states F, F^{-1}, J and P and the
+// traction residual f in df32, ln J in FP64, the Hessian and its inverse in
+// FP32 (a Newton direction needs no more: the iteration converges on the
+// residual f, which keeps ~48 bits), the jump a and the back-projection in FP64.
+struct PhaseD {
+    df32 F[9], G[9], P[9], J;
+    float g[3];  // G^T N
+    double lnJ;
+};
+
+__device__ __forceinline__ bool nh_phase_df(PhaseD& s, double mu, double lam, const df32 N[3], double* gd = nullptr)
+{
+    const df32* F = s.F;
+    const df32 c0 = F[4] * F[8] - F[5] * F[7];
+    const df32 c1 = F[5] * F[6] - F[3] * F[8];
+    const df32 c2 = F[3] * F[7] - F[4] * F[6];
+    const df32 J = F[0] * c0 + F[1] * c1 + F[2] * c2;
+    s.J = J;
+    if (!(J.hi > 0.f)) return false;
+    const df32 iJ = df32(1.f, 0.f) / J;
+    s.G[0] = c0 * iJ;
+    s.G[1] = (F[2] * F[7] - F[1] * F[8]) * iJ;
+    s.G[2] = (F[1] * F[5] - F[2] * F[4]) * iJ;
+    s.G[3] = c1 * iJ;
+    s.G[4] = (F[0] * F[8] - F[2] * F[6]) * iJ;
+    s.G[5] = (F[2] * F[3] - F[0] * F[5]) * iJ;
+    s.G[6] = c2 * iJ;
+    s.G[7] = (F[1] * F[6] - F[0] * F[7]) * iJ;
+    s.G[8] = (F[0] * F[4] - F[1] * F[3]) * iJ;
+    s.lnJ = log((double)J);
+    const df32 k = df32(lam * s.lnJ - mu), mud = df32(mu);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+#pragma unroll
+        for (int j = 0; j < 3; j++) s.P[3 * i + j] = mud * F[3 * i + j] + k * s.G[3 * j + i];
+        const df32 gi = s.G[i] * N[0] + s.G[3 + i] * N[1] + s.G[6 + i] * N[2];
+        s.g[i] = (float)gi;
+        if (gd) gd[i] = (double)gi;
+    }
+    return true;
+}
+
+struct LamEvalD {
+    PhaseD p, m;
+    double f[3];
+    double err, eps;
+};
+
+__device__ __forceinline__ bool lam_eval(LamEvalD& e, const df32 Fb[9], const df32 N[3], df32 icp, df32 icm,
+                                         const double a[3], const double mu[2], const double lam[2], double tol_rel,
+                                         double tol_abs)
+{
+    const df32 ad[3] = {df32(a[0]), df32(a[1]), df32(a[2])};
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const df32 t = ad[i] * N[j];
+            e.p.F[3 * i + j] = Fb[3 * i + j] + t * icp;
+            e.m.F[3 * i + j] = Fb[3 * i + j] - t * icm;
+        }
+    if (!nh_phase_df(e.p, mu[1], lam[1], N)) return false;
+    if (!nh_phase_df(e.m, mu[0], lam[0], N)) return false;
+    float tp = 0.f, tm = 0.f, ff = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const df32 a1 = e.p.P[3 * i] * N[0] + e.p.P[3 * i + 1] * N[1] + e.p.P[3 * i + 2] * N[2];
+        const df32 a2 = e.m.P[3 * i] * N[0] + e.m.P[3 * i + 1] * N[1] + e.m.P[3 * i + 2] * N[2];
+        const df32 fi = a1 - a2;
+        e.f[i] = (double)fi;
+        tp += a1.hi * a1.hi;
+        tm += a2.hi * a2.hi;
+        ff += fi.hi * fi.hi;
+    }
+    e.err = (double)sqrtf(ff);
+    e.eps = tol_rel * ((double)sqrtf(tp) + (double)sqrtf(tm)) + tol_abs * fmax(mu[0], mu[1]);
+    return true;
+}
+
+// Delta (as in the FP64 form) and its inverse, in FP32
+__device__ __forceinline__ bool hessian_inv(const LamEvalD& e, double cp, double cm, const double mu[2],
+                                            const double lam[2], double Di[9])
+{
+    const float wp = (float)(1.0 / cp), wm = (float)(1.0 / cm);
+    const float sp = (float)(lam[1] + mu[1] - lam[1] * e.p.lnJ) * wp;
+    const float sm = (float)(lam[0] + mu[0] - lam[0] * e.m.lnJ) * wm;
+    const float d = (float)mu[1] * wp + (float)mu[0] * wm;
+    float A[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            A[3 * i + k] = (i == k ? d : 0.f) + sp * e.p.g[i] * e.p.g[k] + sm * e.m.g[i] * e.m.g[k];
+    const float c0 = A[4] * A[8] - A[5] * A[7];
+    const float c1 = A[5] * A[6] - A[3] * A[8];
+    const float c2 = A[3] * A[7] - A[4] * A[6];
+    const float det = A[0] * c0 + A[1] * c1 + A[2] * c2;
+    if (det == 0.f || !isfinite(det)) return false;
+    const float id = 1.f / det;
+    Di[0] = c0 * id;
+    Di[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    Di[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    Di[3] = c1 * id;
+    Di[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    Di[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    Di[6] = c2 * id;
+    Di[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    Di[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    return true;
+}
+
 // One Neo-Hookean phase's tangent data in precision S:
 //   A_iJkL     = mu d_ik d_JL + lam G_Ji G_Lk + m G_Jk G_Li,   m = mu - lam ln J
 //   (A D)_(iJ),k = mu d_ik N_J + lam G_Ji g_k + m G_Jk g_i,     g = G^T N
@@ -131,6 +245,16 @@ template <typename S> struct TanPhase {
     {
 #pragma unroll
         for (int q = 0; q < 9; q++) G[q] = (S)s.G[q];
+#pragma unroll
+        for (int q = 0; q < 3; q++) g[q] = (S)s.g[q];
+        mu = (S)mu_;
+        lam = (S)lam_;
+        m = (S)(mu_ - lam_ * s.lnJ);
+    }
+    __device__ __forceinline__ void load(const PhaseD& s, double mu_, double lam_)
+    {
+#pragma unroll
+        for (int q = 0; q < 9; q++) G[q] = (S)(float)s.G[q];
 #pragma unroll
         for (int q = 0; q < 3; q++) g[q] = (S)s.g[q];
         mu = (S)mu_;
@@ -147,13 +271,15 @@ template <typename S> struct TanPhase {
     }
 };
 
-template <typename Tc>
+// DFM: the double-float form (phase states and residual in df32)
+template <typename Tc, bool DFM>
 __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
 {
     if (A.guard == 2 && A.sc->outer_done) return;
     __shared__ double red[64];
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double its = 0.0, nbp = 0.0, nev = 0.0;
+    typedef typename std::conditional<DFM, LamEvalD, LamEval>::type LE;
     if (b < A.nb) {
         nev = 1.0;
         const int64_t v = A.bidx[b];
@@ -169,27 +295,58 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
         const double mu[2] = {A.mu[0], A.mu[1]}, lam[2] = {A.lam[0], A.lam[1]};
         int status = 0;
         // m_beta = F^{-T} N / |F^{-T} N|, beta_c(+/-) = -/+ c(+/-) / |F^{-T} N|  (Sec. 4.2)
-        Phase box;
+        double gbox[3];
+        df32 Fd[9], Nd[3], icp, icm;
+        if constexpr (DFM) {
 #pragma unroll
-        for (int c = 0; c < 9; c++) box.F[c] = Fb[c];
-        if (!nh_phase(box, mu[0], lam[0], N)) status = COMBO_E_INADMISSIBLE;
-        LamEval e;
-        double Dl[9], Di[9];
+            for (int c = 0; c < 9; c++) Fd[c] = df32(Fb[c]);
+#pragma unroll
+            for (int i = 0; i < 3; i++) Nd[i] = df32(N[i]);
+            icp = df32(1.0 / cp);
+            icm = df32(1.0 / cm);
+            PhaseD box;
+#pragma unroll
+            for (int c = 0; c < 9; c++) box.F[c] = Fd[c];
+            if (!nh_phase_df(box, mu[0], lam[0], Nd, gbox)) status = COMBO_E_INADMISSIBLE;
+        } else {
+            Phase box;
+#pragma unroll
+            for (int c = 0; c < 9; c++) box.F[c] = Fb[c];
+            if (!nh_phase(box, mu[0], lam[0], N)) status = COMBO_E_INADMISSIBLE;
+#pragma unroll
+            for (int i = 0; i < 3; i++) gbox[i] = box.g[i];
+        }
+        LE e;
+        auto evaluate = [&]() -> bool {
+            if constexpr (DFM)
+                return lam_eval(e, Fd, Nd, icp, icm, a, mu, lam, A.tol_rel, A.tol_abs);
+            else
+                return lam_eval(e, Fb, N, cp, cm, a, mu, lam, A.tol_rel, A.tol_abs);
+        };
+        auto newton_inverse = [&](double Di[9]) -> bool {
+            if constexpr (DFM) {
+                return hessian_inv(e, cp, cm, mu, lam, Di);
+            } else {
+                double Dl[9];
+                hessian(e, cp, cm, mu, lam, Dl);
+                return inv3(Dl, Di);
+            }
+        };
+        double Di[9];
         if (!status) {
-            const double ng = sqrt(box.g[0] * box.g[0] + box.g[1] * box.g[1] + box.g[2] * box.g[2]);
-            const double m[3] = {box.g[0] / ng, box.g[1] / ng, box.g[2] / ng};
+            const double ng = sqrt(gbox[0] * gbox[0] + gbox[1] * gbox[1] + gbox[2] * gbox[2]);
+            const double m[3] = {gbox[0] / ng, gbox[1] / ng, gbox[2] / ng};
             const double bcp = -cp / ng, bcm = cm / ng;
             double beta = a[0] * m[0] + a[1] * m[1] + a[2] * m[2];
             if (!(beta > bcp && beta < bcm)) a[0] = a[1] = a[2] = 0.0;
-            if (!lam_eval(e, Fb, N, cp, cm, a, mu, lam, A.tol_rel, A.tol_abs)) status = COMBO_E_LAMINATE;
+            if (!evaluate()) status = COMBO_E_LAMINATE;
             int it = 0;
             while (!status && e.err > e.eps) {
                 if (it >= A.max_iter) {
                     status = COMBO_E_LAMINATE;
                     break;
                 }
-                hessian(e, cp, cm, mu, lam, Dl);
-                if (!inv3(Dl, Di)) {
+                if (!newton_inverse(Di)) {
                     status = COMBO_E_LAMINATE;
                     break;
                 }
@@ -211,24 +368,29 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
                 a[1] = a1[1];
                 a[2] = a1[2];
                 it++;
-                if (!lam_eval(e, Fb, N, cp, cm, a, mu, lam, A.tol_rel, A.tol_abs)) status = COMBO_E_LAMINATE;
+                if (!evaluate()) status = COMBO_E_LAMINATE;
             }
             its = it;
         }
         if (status) {
             raise_status(A.sc, status);
         } else {
+            if constexpr (DFM) {
+                const df32 cpd = df32(cp), cmd = df32(cm);
 #pragma unroll
-            for (int c = 0; c < 9; c++) A.bP[9 * b + c] = cp * e.p.P[c] + cm * e.m.P[c];
+                for (int c = 0; c < 9; c++) A.bP[9 * b + c] = (double)(cpd * e.p.P[c] + cmd * e.m.P[c]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 9; c++) A.bP[9 * b + c] = cp * e.p.P[c] + cm * e.m.P[c];
+            }
 #pragma unroll
             for (int i = 0; i < 3; i++) A.ba[3 * b + i] = a[i];
             if (A.bA) {
-                hessian(e, cp, cm, mu, lam, Dl);
-                if (!inv3(Dl, Di)) {
+                if (!newton_inverse(Di)) {
                     raise_status(A.sc, COMBO_E_LAMINATE);
                 } else {
                     // The boxel tangent only feeds the Krylov iterations: it is
-                    // formed in their precision Tc from the converged FP64 state.
+                    // formed in their precision Tc from the converged state.
                     TanPhase<Tc> tp, tm;
                     tp.load(e.p, mu[1], lam[1]);
                     tm.load(e.m, mu[0], lam[0]);
@@ -278,7 +440,13 @@ template <typename Tc> void launch_boxel(const BoxelArgs<Tc>& a, cudaStream_t st
 {
     if (a.nb <= 0) return;
     const int grid = (int)((a.nb + 127) / 128);
-    k_boxel<Tc><<<grid, 128, 0, st>>>(a);
+    if constexpr (std::is_same<Tc, float>::value) {
+        if (a.dfloat) {
+            k_boxel<Tc, true><<<grid, 128, 0, st>>>(a);
+            return;
+        }
+    }
+    k_boxel<Tc, false><<<grid, 128, 0, st>>>(a);
 }
 
 template void launch_boxel<double>(const BoxelArgs<double>&, cudaStream_t);

@@ -446,6 +446,7 @@ template <typename Tc> struct BoxelArgs {
     int max_iter;
     Scalars* sc;
     int guard;
+    int dfloat;  // phase states and residual in double-float (refined double-float form)
 };
 template <typename Tc> void launch_boxel(const BoxelArgs<Tc>& a, cudaStream_t st);
 

@@ -871,6 +871,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         a.bP = d_bP;
         a.bA = tangent ? d_bA : nullptr;
         a.rank = d_rank;
+        a.dfloat = std::is_same<Rt, df32>::value ? 1 : 0;
         a.F = d_F;
         a.mu[0] = hp.mu[0];
         a.mu[1] = hp.mu[1];
