@@ -127,8 +127,9 @@ __device__ __forceinline__ bool inv3(const double A[9], double B[9])
 // ---- double-float form of the laminate solve (refined precision form with
 // double-float residuals): the phase states F, F^{-1}, J and P and the
 // traction residual f in df32, ln J in FP64, the Hessian and its inverse in
-// FP32 (a Newton direction needs no more: the iteration converges on the
-// residual f, which keeps ~48 bits), the jump a and the back-projection in FP64.
+// FP32 (a Newton direction needs no more), the jump a and the back-projection
+// in FP64.  These iterations stop at the rounding level of the df32 residual;
+// the FP64 residual then decides convergence.
 struct PhaseD {
     df32 F[9], G[9], P[9], J;
     float g[3];  // G^T N
@@ -171,6 +172,7 @@ struct LamEvalD {
     PhaseD p, m;
     double f[3];
     double err, eps;
+    double floor;  // rounding level of f in double-float: below it only FP64 can decide
 };
 
 __device__ __forceinline__ bool lam_eval(LamEvalD& e, const df32 Fb[9], const df32 N[3], df32 icp, df32 icm,
@@ -201,6 +203,8 @@ __device__ __forceinline__ bool lam_eval(LamEvalD& e, const df32 Fb[9], const df
     }
     e.err = (double)sqrtf(ff);
     e.eps = tol_rel * ((double)sqrtf(tp) + (double)sqrtf(tm)) + tol_abs * fmax(mu[0], mu[1]);
+    // P = mu F + k F^{-T} is formed from terms of size ~(mu + lam) |F|: 2^-44 of that
+    e.floor = 0x1p-44 * (fmax(mu[0], mu[1]) + fmax(lam[0], lam[1])) * (1.0 + (double)sqrtf(tp) + (double)sqrtf(tm));
     return true;
 }
 
@@ -251,16 +255,7 @@ template <typename S> struct TanPhase {
         lam = (S)lam_;
         m = (S)(mu_ - lam_ * s.lnJ);
     }
-    __device__ __forceinline__ void load(const PhaseD& s, double mu_, double lam_)
-    {
-#pragma unroll
-        for (int q = 0; q < 9; q++) G[q] = (S)(float)s.G[q];
-#pragma unroll
-        for (int q = 0; q < 3; q++) g[q] = (S)s.g[q];
-        mu = (S)mu_;
-        lam = (S)lam_;
-        m = (S)(mu_ - lam_ * s.lnJ);
-    }
+
     __device__ __forceinline__ S AD(const S N[3], int i, int Jx, int k) const
     {
         return (i == k ? mu * N[Jx] : (S)0) + lam * G[3 * Jx + i] * g[k] + m * G[3 * Jx + k] * g[i];
@@ -271,7 +266,45 @@ template <typename S> struct TanPhase {
     }
 };
 
-// DFM: the double-float form (phase states and residual in df32)
+// Newton-Raphson on the jump a (Algorithm 1) with selective back-projection
+// (Algorithm 2) from the current a, until e.err <= max(e.eps, floor); it counts
+// the iterations of every call against max_iter.  Returns a COMBO_E_* code or 0.
+template <class LE, class EV, class INV>
+__device__ __forceinline__ int nr_loop(LE& e, double a[3], const double m[3], double bcp, double bcm, double floor,
+                                       int& it, int max_iter, double& nbp, const EV& evaluate, const INV& inverse)
+{
+    if (!evaluate(e)) return COMBO_E_LAMINATE;
+    while (e.err > fmax(e.eps, floor)) {
+        if (it >= max_iter) return COMBO_E_LAMINATE;
+        double Di[9];
+        if (!inverse(e, Di)) return COMBO_E_LAMINATE;
+        double a1[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) a1[i] = a[i] - (Di[3 * i] * e.f[0] + Di[3 * i + 1] * e.f[1] + Di[3 * i + 2] * e.f[2]);
+        const double b1 = a1[0] * m[0] + a1[1] * m[1] + a1[2] * m[2];
+        if (!(b1 > bcp && b1 < bcm)) {
+            // Algorithm 2: keep M_perp a1, move the m_beta coordinate to the
+            // midpoint between the admissible beta0 and the crossed bound
+            const double b0 = a[0] * m[0] + a[1] * m[1] + a[2] * m[2];
+            const double bc = (b1 <= bcp) ? bcp : bcm;
+            const double bs = 0.5 * (b0 + bc);
+#pragma unroll
+            for (int i = 0; i < 3; i++) a1[i] = (a1[i] - b1 * m[i]) + bs * m[i];
+            nbp += 1.0;
+        }
+        a[0] = a1[0];
+        a[1] = a1[1];
+        a[2] = a1[2];
+        it++;
+        if (!evaluate(e)) return COMBO_E_LAMINATE;
+    }
+    return 0;
+}
+
+// DFM: the double-float form: the Newton iterations run on the double-float
+// residual down to its rounding level, then the FP64 residual decides
+// convergence (and takes the last step if needed), so the stopping test and
+// the returned state are those of the FP64 form.
 template <typename Tc, bool DFM>
 __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
 {
@@ -279,7 +312,6 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
     __shared__ double red[64];
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double its = 0.0, nbp = 0.0, nev = 0.0;
-    typedef typename std::conditional<DFM, LamEvalD, LamEval>::type LE;
     if (b < A.nb) {
         nev = 1.0;
         const int64_t v = A.bidx[b];
@@ -316,21 +348,12 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
 #pragma unroll
             for (int i = 0; i < 3; i++) gbox[i] = box.g[i];
         }
-        LE e;
-        auto evaluate = [&]() -> bool {
-            if constexpr (DFM)
-                return lam_eval(e, Fd, Nd, icp, icm, a, mu, lam, A.tol_rel, A.tol_abs);
-            else
-                return lam_eval(e, Fb, N, cp, cm, a, mu, lam, A.tol_rel, A.tol_abs);
-        };
-        auto newton_inverse = [&](double Di[9]) -> bool {
-            if constexpr (DFM) {
-                return hessian_inv(e, cp, cm, mu, lam, Di);
-            } else {
-                double Dl[9];
-                hessian(e, cp, cm, mu, lam, Dl);
-                return inv3(Dl, Di);
-            }
+        LamEval e;
+        auto eval64 = [&](LamEval& x) { return lam_eval(x, Fb, N, cp, cm, a, mu, lam, A.tol_rel, A.tol_abs); };
+        auto inv64 = [&](const LamEval& x, double Di[9]) {
+            double Dl[9];
+            hessian(x, cp, cm, mu, lam, Dl);
+            return inv3(Dl, Di);
         };
         double Di[9];
         if (!status) {
@@ -339,54 +362,30 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
             const double bcp = -cp / ng, bcm = cm / ng;
             double beta = a[0] * m[0] + a[1] * m[1] + a[2] * m[2];
             if (!(beta > bcp && beta < bcm)) a[0] = a[1] = a[2] = 0.0;
-            if (!evaluate()) status = COMBO_E_LAMINATE;
             int it = 0;
-            while (!status && e.err > e.eps) {
-                if (it >= A.max_iter) {
-                    status = COMBO_E_LAMINATE;
-                    break;
-                }
-                if (!newton_inverse(Di)) {
-                    status = COMBO_E_LAMINATE;
-                    break;
-                }
-                double a1[3];
-#pragma unroll
-                for (int i = 0; i < 3; i++) a1[i] = a[i] - (Di[3 * i] * e.f[0] + Di[3 * i + 1] * e.f[1] + Di[3 * i + 2] * e.f[2]);
-                const double b1 = a1[0] * m[0] + a1[1] * m[1] + a1[2] * m[2];
-                if (!(b1 > bcp && b1 < bcm)) {
-                    // Algorithm 2: keep M_perp a1, move the m_beta coordinate to the
-                    // midpoint between the admissible beta0 and the crossed bound
-                    const double b0 = a[0] * m[0] + a[1] * m[1] + a[2] * m[2];
-                    const double bc = (b1 <= bcp) ? bcp : bcm;
-                    const double bs = 0.5 * (b0 + bc);
-#pragma unroll
-                    for (int i = 0; i < 3; i++) a1[i] = (a1[i] - b1 * m[i]) + bs * m[i];
-                    nbp += 1.0;
-                }
-                a[0] = a1[0];
-                a[1] = a1[1];
-                a[2] = a1[2];
-                it++;
-                if (!evaluate()) status = COMBO_E_LAMINATE;
+            if constexpr (DFM) {
+                LamEvalD ed;
+                status = nr_loop(
+                    ed, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp,
+                    [&](LamEvalD& x) {
+                        if (!lam_eval(x, Fd, Nd, icp, icm, a, mu, lam, A.tol_rel, A.tol_abs)) return false;
+                        x.eps = fmax(x.eps, x.floor);
+                        return true;
+                    },
+                    [&](const LamEvalD& x, double Dv[9]) { return hessian_inv(x, cp, cm, mu, lam, Dv); });
             }
+            if (!status) status = nr_loop(e, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp, eval64, inv64);
             its = it;
         }
         if (status) {
             raise_status(A.sc, status);
         } else {
-            if constexpr (DFM) {
-                const df32 cpd = df32(cp), cmd = df32(cm);
 #pragma unroll
-                for (int c = 0; c < 9; c++) A.bP[9 * b + c] = (double)(cpd * e.p.P[c] + cmd * e.m.P[c]);
-            } else {
-#pragma unroll
-                for (int c = 0; c < 9; c++) A.bP[9 * b + c] = cp * e.p.P[c] + cm * e.m.P[c];
-            }
+            for (int c = 0; c < 9; c++) A.bP[9 * b + c] = cp * e.p.P[c] + cm * e.m.P[c];
 #pragma unroll
             for (int i = 0; i < 3; i++) A.ba[3 * b + i] = a[i];
             if (A.bA) {
-                if (!newton_inverse(Di)) {
+                if (!inv64(e, Di)) {
                     raise_status(A.sc, COMBO_E_LAMINATE);
                 } else {
                     // The boxel tangent only feeds the Krylov iterations: it is
