@@ -208,26 +208,33 @@ __device__ __forceinline__ bool lam_eval(LamEvalD& e, const df32 Fb[9], const df
     return true;
 }
 
-// Delta (as in the FP64 form) and its inverse, in FP32
+// Delta (as in the FP64 form) and its inverse, in FP32, scaled by 1/d.  False
+// when the rank-one parts outweigh the isotropic part d I by more than 1e4
+// (a phase close to collapse, J -> 0): an FP32 inverse would not give a
+// Newton direction there, and the caller continues in FP64.
 __device__ __forceinline__ bool hessian_inv(const LamEvalD& e, double cp, double cm, const double mu[2],
                                             const double lam[2], double Di[9])
 {
     const float wp = (float)(1.0 / cp), wm = (float)(1.0 / cm);
-    const float sp = (float)(lam[1] + mu[1] - lam[1] * e.p.lnJ) * wp;
-    const float sm = (float)(lam[0] + mu[0] - lam[0] * e.m.lnJ) * wm;
     const float d = (float)mu[1] * wp + (float)mu[0] * wm;
+    const float id0 = 1.f / d;
+    const float sp = (float)(lam[1] + mu[1] - lam[1] * e.p.lnJ) * wp * id0;
+    const float sm = (float)(lam[0] + mu[0] - lam[0] * e.m.lnJ) * wm * id0;
+    const float gp2 = e.p.g[0] * e.p.g[0] + e.p.g[1] * e.p.g[1] + e.p.g[2] * e.p.g[2];
+    const float gm2 = e.m.g[0] * e.m.g[0] + e.m.g[1] * e.m.g[1] + e.m.g[2] * e.m.g[2];
+    if (!(fabsf(sp) * gp2 <= 1e4f && fabsf(sm) * gm2 <= 1e4f)) return false;
     float A[9];
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int k = 0; k < 3; k++)
-            A[3 * i + k] = (i == k ? d : 0.f) + sp * e.p.g[i] * e.p.g[k] + sm * e.m.g[i] * e.m.g[k];
+            A[3 * i + k] = (i == k ? 1.f : 0.f) + sp * e.p.g[i] * e.p.g[k] + sm * e.m.g[i] * e.m.g[k];
     const float c0 = A[4] * A[8] - A[5] * A[7];
     const float c1 = A[5] * A[6] - A[3] * A[8];
     const float c2 = A[3] * A[7] - A[4] * A[6];
     const float det = A[0] * c0 + A[1] * c1 + A[2] * c2;
     if (det == 0.f || !isfinite(det)) return false;
-    const float id = 1.f / det;
+    const float id = id0 / det;  // Delta^{-1} = (Delta / d)^{-1} / d
     Di[0] = c0 * id;
     Di[1] = (A[2] * A[7] - A[1] * A[8]) * id;
     Di[2] = (A[1] * A[5] - A[2] * A[4]) * id;
@@ -268,16 +275,17 @@ template <typename S> struct TanPhase {
 
 // Newton-Raphson on the jump a (Algorithm 1) with selective back-projection
 // (Algorithm 2) from the current a, until e.err <= max(e.eps, floor); it counts
-// the iterations of every call against max_iter.  Returns a COMBO_E_* code or 0.
+// the iterations of every call against max_iter.  Returns 0, or the failure
+// reason: 2 a phase inadmissible, 3 singular Hessian, 4 iteration cap.
 template <class LE, class EV, class INV>
 __device__ __forceinline__ int nr_loop(LE& e, double a[3], const double m[3], double bcp, double bcm, double floor,
                                        int& it, int max_iter, double& nbp, const EV& evaluate, const INV& inverse)
 {
-    if (!evaluate(e)) return COMBO_E_LAMINATE;
+    if (!evaluate(e)) return 2;
     while (e.err > fmax(e.eps, floor)) {
-        if (it >= max_iter) return COMBO_E_LAMINATE;
+        if (it >= max_iter) return 4;
         double Di[9];
-        if (!inverse(e, Di)) return COMBO_E_LAMINATE;
+        if (!inverse(e, Di)) return 3;
         double a1[3];
 #pragma unroll
         for (int i = 0; i < 3; i++) a1[i] = a[i] - (Di[3 * i] * e.f[0] + Di[3 * i + 1] * e.f[1] + Di[3 * i + 2] * e.f[2]);
@@ -296,7 +304,7 @@ __device__ __forceinline__ int nr_loop(LE& e, double a[3], const double m[3], do
         a[1] = a1[1];
         a[2] = a1[2];
         it++;
-        if (!evaluate(e)) return COMBO_E_LAMINATE;
+        if (!evaluate(e)) return 2;
     }
     return 0;
 }
@@ -325,7 +333,7 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
         }
         const double cp = A.bc[b], cm = 1.0 - cp;
         const double mu[2] = {A.mu[0], A.mu[1]}, lam[2] = {A.lam[0], A.lam[1]};
-        int status = 0;
+        int status = 0, reason = 0;
         // m_beta = F^{-T} N / |F^{-T} N|, beta_c(+/-) = -/+ c(+/-) / |F^{-T} N|  (Sec. 4.2)
         double gbox[3];
         df32 Fd[9], Nd[3], icp, icm;
@@ -362,23 +370,46 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
             const double bcp = -cp / ng, bcm = cm / ng;
             double beta = a[0] * m[0] + a[1] * m[1] + a[2] * m[2];
             if (!(beta > bcp && beta < bcm)) a[0] = a[1] = a[2] = 0.0;
-            int it = 0;
+            int it = 0, it_df = 0;
             if constexpr (DFM) {
+                // double-float iterations from a copy of the start; if they
+                // stop early (a phase near collapse, an ill-conditioned
+                // Hessian), the FP64 iterations start over from a
                 LamEvalD ed;
-                status = nr_loop(
-                    ed, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp,
+                double ad[3] = {a[0], a[1], a[2]};
+                const int rdf = nr_loop(
+                    ed, ad, m, bcp, bcm, 0.0, it_df, A.max_iter, nbp,
                     [&](LamEvalD& x) {
-                        if (!lam_eval(x, Fd, Nd, icp, icm, a, mu, lam, A.tol_rel, A.tol_abs)) return false;
+                        if (!lam_eval(x, Fd, Nd, icp, icm, ad, mu, lam, A.tol_rel, A.tol_abs)) return false;
                         x.eps = fmax(x.eps, x.floor);
                         return true;
                     },
                     [&](const LamEvalD& x, double Dv[9]) { return hessian_inv(x, cp, cm, mu, lam, Dv); });
+                if (rdf == 0) {
+                    a[0] = ad[0];
+                    a[1] = ad[1];
+                    a[2] = ad[2];
+                }
             }
-            if (!status) status = nr_loop(e, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp, eval64, inv64);
-            its = it;
+            reason = nr_loop(e, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp, eval64, inv64);
+            if (reason) status = COMBO_E_LAMINATE;
+            its = it + it_df;
+        } else {
+            reason = 1;
         }
         if (status) {
             raise_status(A.sc, status);
+            if (atomicCAS(&A.sc->fail_boxel, 0, (int32_t)(b + 1)) == 0) {
+                A.sc->fail_reason = reason;
+#pragma unroll
+                for (int c = 0; c < 9; c++) A.sc->fail_state[c] = Fb[c];
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    A.sc->fail_state[9 + i] = N[i];
+                    A.sc->fail_state[13 + i] = a[i];
+                }
+                A.sc->fail_state[12] = cp;
+            }
         } else {
 #pragma unroll
             for (int c = 0; c < 9; c++) A.bP[9 * b + c] = cp * e.p.P[c] + cm * e.m.P[c];

@@ -77,6 +77,11 @@ struct Scalars {
     unsigned long long n_operator, n_operator64;
     unsigned int ticket[4];  // last-block counters of fused reductions
     double alpha_pending;    // x += alpha_pending p still owed by the last CG update
+    // first failed laminate solve: 1 + boxel index (0: none), reason (1 F_box
+    // inadmissible, 2 a phase inadmissible, 3 singular Hessian, 4 iteration
+    // cap) and its state: F_box (9), N (3), c+ (1), a (3)
+    int32_t fail_boxel, fail_reason;
+    double fail_state[16];
 };
 
 // ---------------------------------------------------------------- FFT core

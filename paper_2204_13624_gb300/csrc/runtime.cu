@@ -989,6 +989,23 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         return COMBO_OK;
     }
 
+    // description of the first failed laminate solve, if any
+    std::string boxel_failure(const Scalars& s) const
+    {
+        if (s.fail_boxel <= 0) return "";
+        static const char* why[5] = {"", "F_box inadmissible", "a phase inadmissible", "singular Hessian",
+                                     "iteration cap"};
+        const int r = (s.fail_reason >= 1 && s.fail_reason <= 4) ? s.fail_reason : 0;
+        char buf[512];
+        const double* q = s.fail_state;
+        snprintf(buf, sizeof buf,
+                 "; boxel %d (voxel %d): %s; F_box = [%.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g], "
+                 "N = [%.17g %.17g %.17g], c+ = %.17g, a = [%.17g %.17g %.17g]",
+                 s.fail_boxel - 1, hp.bidx[s.fail_boxel - 1], why[r], q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7],
+                 q[8], q[9], q[10], q[11], q[12], q[13], q[14], q[15]);
+        return buf;
+    }
+
     int read_scalars(Scalars& s)
     {
         CK(cudaMemcpyAsync(&s, d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
@@ -1065,7 +1082,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                     CK(cudaGetLastError());
                     if ((rc = read_scalars(s))) return error = rc;
                     ops_done = (int64_t)s.n_operator;
-                    if (s.status) return error = fail(s.status, "fixed point failed");
+                    if (s.status) return error = fail(s.status, "fixed point failed" + boxel_failure(s));
                     if (s.outer_done) {
                         record_step(s);
                         state = ST_STEP;
@@ -1077,7 +1094,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                     resid_operator(XI_RHS, 0);
                     CK(cudaGetLastError());
                     if ((rc = read_scalars(s))) return error = rc;
-                    if (s.status) return error = fail(s.status, "residual evaluation failed");
+                    if (s.status) return error = fail(s.status, "residual evaluation failed" + boxel_failure(s));
                     const bool conv = (opt.fixed_iterations > 0) ? (outer >= opt.fixed_iterations) : (s.eps <= opt.tol);
                     if (conv) {
                         record_step(s);

@@ -169,6 +169,20 @@ def test_sphere_32_refined_fp32(cb, orc, prec):
     assert rel(g["F"], r["F"]) < 1e-4
 
 
+def test_double_float_form_high_contrast(cb):
+    """Contrast 100 under a 10 % stretch (thin, strongly compressed boxel
+    phases): the double-float form converges to the state of the plain FP64
+    form, which the parity tests above pin to the oracle."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.random_spheres((64, 64, 64), 6.0, 0.2, 5, 100.0, np.diag([1.10, 1.0, 1.0]), 2)
+    g64 = cb.solve(p, solver=1, precision=cb.FP64, tol=1e-8)
+    gdf = cb.solve(p, solver=1, precision=cb.FP32_REFINED_DF, tol=1e-8)
+    assert gdf["steps_done"] == 2 and np.all(gdf["resid"] <= 1e-8)
+    assert rel(gdf["Pbar"], g64["Pbar"]) < 1e-6
+    assert rel(gdf["F"], g64["F"]) < 1e-4
+
+
 def test_layered_laminate_exact_on_gpu(cb, orc):
     from paper_2204_13624_gb300 import microstructure as ms
     import test_oracle_solve as tos
