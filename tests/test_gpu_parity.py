@@ -275,3 +275,52 @@ def test_full_size_256_sampled(cb, orc):
         err = (Z - Y).abs().max().item() / Y.abs().max().item()
         assert err < tol
         assert Y.mean(dim=1).abs().max().item() < tol
+
+
+def test_full_size_512_fibres_sampled(cb, orc):
+    """The 512^3 z-fibre workload (134 M voxels, 10 M boxels) in the double-float
+    refined form: after the first Newton step, the stress at sampled voxels
+    equals the oracle's per-voxel constitutive law at the GPU's F, and the
+    fluctuation F - <F> is compatible (G leaves it unchanged)."""
+    import torch
+
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.fibres_512()
+    s = cb.Solve(p, solver=1, precision=cb.FP32_REFINED_DF, tol=1e-8)
+    s.advance(24)
+    out = s.finish(fields=True, device_results=True)
+    s.close()
+    F, P, a = out["F"], out["P"], out["a"].cpu().numpy()
+    V = 512 ** 3
+    rng = np.random.default_rng(1)
+    vox = rng.integers(0, V, 1500)
+    bvox = rng.choice(p["boxel_idx"], 500)  # boxels in particular
+    vox = np.concatenate([vox, bvox])
+    idx = torch.as_tensor(vox, device=F.device)
+    Fs = F[:, idx].cpu().numpy()
+    Ps = P[:, idx].cpu().numpy()
+    # a is returned for the boxels kept after the c_min snap, in input order
+    c = p["boxel_c"]
+    cmin = cb.options().c_min
+    kept = (c >= cmin) & (c <= 1.0 - cmin)
+    kpos = np.cumsum(kept) - 1
+    vb = {int(v): i for i, v in enumerate(p["boxel_idx"])}
+    mat = (p["mu"][0], p["lam"][0], p["mu"][1], p["lam"][1])
+    for j, v in enumerate(vox):
+        ph = int(p["phase"][v])
+        if ph == 2 and not kept[vb[int(v)]]:
+            ph = 0 if c[vb[int(v)]] < cmin else 1
+        if ph == 2:
+            b = vb[int(v)]
+            Po = orc.laminate(Fs[:, j], p["boxel_N"][b], c[b], mat, a0=a[kpos[b]])["P"]
+        else:
+            Po = orc.neohooke(Fs[:, j], p["mu"][ph], p["lam"][ph], False)
+        assert np.allclose(Ps[:, j], Po, rtol=1e-12, atol=1e-12 * max(1.0, np.abs(Po).max()))
+    del P
+    # compatibility of the solved fluctuation
+    Fm = F - F.mean(dim=1, keepdim=True)
+    del F
+    GF, _ = cb.apply_G(Fm, (512, 512, 512), precision=cb.FP32_REFINED_DF)
+    err = (GF - Fm).abs().max().item() / Fm.abs().max().item()
+    assert err < 1e-5
