@@ -152,7 +152,9 @@ typedef struct {
 /*
  * Results, caller-allocated.  Pbar [n_steps][9] is required; every other
  * pointer may be NULL.
- *   F_out, P_out  [9][V] FP64 fields of the last completed step, in `mem`.
+ *   F_out, P_out  [9][V] FP64 fields F and P(F), in `mem`: the converged
+ *                 fields of the last step once the solve has finished, the
+ *                 current iterate if combo_solve_finish ends it earlier.
  *   a_out         [n_boxels][3] laminate jump vectors, in `mem`.
  *   iters         [n_steps] outer (Newton / fixed-point) iterations.
  *   cg_iters      [n_steps] CG iterations.

@@ -1173,6 +1173,12 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         const int64_t V = g.V;
         if (r->F_out) CK(cudaMemcpyAsync(r->F_out, d_F, 8 * 9 * V, d2x, st));
         if (r->P_out) {
+            // F changed since the last laminate solve (a solve stopped between
+            // an F update and the next residual): solve the boxels at this F
+            if (state == ST_RESID && nb > 0) {
+                boxels(false, 0);
+                CK(cudaGetLastError());
+            }
             double* P = dev ? r->P_out : nullptr;
             if (!dev) CK(cudaMalloc(&P, 8 * 9 * V));
             Mat9 m{};
