@@ -393,6 +393,7 @@ template <typename T> struct YArgs {
     int tx;
     const Scalars* sc;
     int guard;  // 0 none, 1 skip if cg_done, 2 skip if outer_done
+    const void* tmap;  // CUtensorMap of spec for the TMA y-pass (FP32), or null
 };
 
 template <typename T> struct ZArgs {
@@ -425,10 +426,12 @@ int zpass_tx(int n, size_t cxbytes);  // columns per z-pass block (sets the part
 // FP32 CG x-inverse with streamed (bulk asynchronous, double-buffered)
 // inputs, for n1 = 128, 256, 512 (xpass_stream.cu)
 bool stream_xpass_ok(const GridDims& g);
-// FP32 Krylov z-pass with TMA tiles, n3 = 64, 128, 256 (zpass_tma.cu)
+// FP32 Krylov z- and y-passes with TMA tiles, n = 64, 128, 256 (zpass_tma.cu)
 bool zpass_tma_size(int n3);
 bool zpass_tma_encode(void* map, const GridDims& g, const void* spec);
 void launch_zpass_tma(const ZArgs<float>& a, const void* map, cudaStream_t st);
+bool ypass_tma_encode(void* map, const GridDims& g, const void* spec);
+template <bool INV> void launch_ypass_tma(const YArgs<float>& a, const void* map, cudaStream_t st);
 void launch_xinv_stream(const XinvArgs<float, float>& a, cudaStream_t st);
 
 // Record msg as the calling thread's last error; returns code.

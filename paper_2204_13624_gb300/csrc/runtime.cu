@@ -348,12 +348,13 @@ template <typename T> struct Engine {
     Plan pM, py, pz;
     int lines, txy, txz;
     cx<T>* spec = nullptr;  // not owned
-    CUtensorMap zmap;       // TMA view of spec for the FP32 z-pass
-    bool zmap_ok = false;
+    CUtensorMap zmap, ymap;  // TMA views of spec for the FP32 z- and y-passes
+    bool zmap_ok = false, ymap_ok = false;
     void bind_spec(void* s)
     {
         spec = (cx<T>*)s;
         zmap_ok = (sizeof(T) == 4) && zpass_tma_encode(&zmap, g, s);
+        ymap_ok = (sizeof(T) == 4) && ypass_tma_encode(&ymap, g, s);
     }
     int init(const GridDims& gd, const double l[3], int kspace)
     {
@@ -402,6 +403,7 @@ template <typename T> struct Engine {
         y.tx = txy;
         y.sc = sc;
         y.guard = guard;
+        y.tmap = ymap_ok ? &ymap : nullptr;
         if (pr) pr->begin(kbase);
         launch_ypass<T, false>(y, st);
         if (pr) pr->end();

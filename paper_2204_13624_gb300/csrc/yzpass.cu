@@ -281,6 +281,12 @@ template <typename T, int N, bool INV> static void ypass_fast_launch(const YArgs
 
 template <typename T, bool INV> void launch_ypass(const YArgs<T>& a, cudaStream_t st)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (a.tmap && zpass_tma_size(a.g.n2)) {
+            launch_ypass_tma<INV>(a, a.tmap, st);
+            return;
+        }
+    }
     switch (a.g.n2) {
         case 64: ypass_fast_launch<T, 64, INV>(a, st); return;
         case 128: ypass_fast_launch<T, 128, INV>(a, st); return;

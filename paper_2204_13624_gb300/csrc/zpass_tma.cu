@@ -1,5 +1,5 @@
 // zpass_tma.cu -- FP32 z-pass (forward z FFT, Green operator, inverse z FFT)
-// with tensor-memory-accelerator (TMA) tile movement.
+// and y-passes with tensor-memory-accelerator (TMA) tile movement.
 //
 // Same arithmetic as k_zpass_fast of yzpass.cu for the Krylov operator (no
 // norm accumulation).  A persistent block walks tiles of the half spectrum;
@@ -189,6 +189,137 @@ __global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
     }
 }
 
+// ------------------------------------------------------------- y-pass
+// Tile: one component, one z plane, all n2 y rows, TYX consecutive x
+// frequencies: box {TYX, n2, 1, 1}; the transform runs in place in the tile.
+constexpr int TYX = 16;
+
+bool ypass_tma_encode(void* map, const GridDims& g, const void* spec)
+{
+    if (!zpass_tma_size(g.n2) || !spec) return false;
+    if ((g.nhp * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(spec) & 15) != 0) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dim[4] = {(cuuint64_t)g.nhp, (cuuint64_t)g.n2, (cuuint64_t)g.n3, 9};
+    const cuuint64_t stride[3] = {(cuuint64_t)g.nhp * 8, (cuuint64_t)g.n2 * g.nhp * 8,
+                                  (cuuint64_t)g.n3 * g.n2 * g.nhp * 8};
+    const cuuint32_t box[4] = {(cuuint32_t)TYX, (cuuint32_t)g.n2, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, 4,
+                          const_cast<void*>(spec), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int N, bool INV>
+__global__ void __launch_bounds__(TYX * FastPlan<N>::TPL)
+    k_ypass_tma(const __grid_constant__ CUtensorMap tm, YArgs<float> a)
+{
+    if (a.guard == 1 && a.sc->cg_done) return;
+    if (a.guard == 2 && a.sc->outer_done) return;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    constexpr int TX = TYX;
+    constexpr int TILE = N * TX;
+    constexpr uint32_t TILE_BYTES = TILE * 8;
+    typedef cx<float> C;
+    C* tiles = reinterpret_cast<C*>(smem_raw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * TILE_BYTES);
+    const GridDims g = a.g;
+    const int line = threadIdx.x % TX, tau = threadIdx.x / TX;
+    const int nxt = (g.nh + TX - 1) / TX;
+    const int ntiles = nxt * g.n3 * 9;
+
+    // tile t = (c * n3 + z) * nxt + xt
+    auto issue = [&](int t, int s) {
+        const int xt = t % nxt, rest = t / nxt;
+        const int z = rest % g.n3, c = rest / g.n3;
+        mbar_arrive_expect_tx(&bar[s], TILE_BYTES);
+        tma_load_4d(tiles + s * TILE, &tm, xt * TX, 0, z, c, &bar[s]);
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_proxy_async();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+
+    int it = 0;
+    bool timed_out = false;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+        const int s = it & 1;
+        const int tn = t + gridDim.x;
+        if (threadIdx.x == 0 && tn < ntiles) {
+            bulk_wait_read_all();  // the store of the previous tile has left buffer s ^ 1
+            issue(tn, s ^ 1);
+        }
+        const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        const int xt = t % nxt, rest = t / nxt;
+        const int z = rest % g.n3, c = rest / g.n3;
+        C* park = tiles + s * TILE;
+        C* pc = park + line;
+        auto lp = [&](int e) { return pc[e * TX]; };
+        auto sp = [&](int e, C v) { pc[e * TX] = v; };
+        fft_fast<float, N, INV, true, true>(lp, sp, lp, sp, tau, a.tw);
+        fence_proxy_async();  // this thread's tile writes, before the copy engine reads them
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tma_store_4d(&tm, xt * TX, 0, z, c, park);
+            bulk_commit();
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (timed_out) {
+            raise_status(const_cast<Scalars*>(a.sc), COMBO_E_TIMEOUT);
+            const int s = it & 1;
+            mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1));
+            if ((int)blockIdx.x + (it + 1) * (int)gridDim.x < ntiles)
+                mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+        }
+        bulk_wait_all();
+    }
+}
+
+template <int N, bool INV> static void ypass_tma_launch(const YArgs<float>& a, const void* map, cudaStream_t st)
+{
+    constexpr int threads = TYX * FastPlan<N>::TPL;
+    const size_t sm = (size_t)2 * N * TYX * 8 + 16;
+    static int grid_per_sm = 0;
+    static int nsm = 0;
+    if (grid_per_sm == 0) {
+        cudaFuncSetAttribute(k_ypass_tma<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ypass_tma<N, INV>, threads, sm) != cudaSuccess ||
+            per < 1)
+            per = 1;
+        grid_per_sm = per;
+    }
+    const int ntiles = ((a.g.nh + TYX - 1) / TYX) * a.g.n3 * 9;
+    const int grid = std::min(ntiles, grid_per_sm * nsm);
+    k_ypass_tma<N, INV><<<grid, threads, sm, st>>>(*reinterpret_cast<const CUtensorMap*>(map), a);
+}
+
+template <bool INV> void launch_ypass_tma(const YArgs<float>& a, const void* map, cudaStream_t st)
+{
+    switch (a.g.n2) {
+        case 64: ypass_tma_launch<64, INV>(a, map, st); break;
+        case 128: ypass_tma_launch<128, INV>(a, map, st); break;
+        default: ypass_tma_launch<256, INV>(a, map, st); break;
+    }
+}
+template void launch_ypass_tma<false>(const YArgs<float>&, const void*, cudaStream_t);
+template void launch_ypass_tma<true>(const YArgs<float>&, const void*, cudaStream_t);
+
+// ------------------------------------------------------------- z-pass launch
 template <int N> static void zpass_tma_launch(const ZArgs<float>& a, const void* map, cudaStream_t st)
 {
     constexpr int TX = tma_tx<N>();

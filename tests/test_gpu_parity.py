@@ -129,11 +129,11 @@ def test_newton_cg_parity(cb, orc, k, kspace):
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_newton_cg_parity_fast_sizes(cb, orc, prec):
-    """64^3, 64 x 32 x 128 and 128 x 64 x 256 grids run the compile-time FFT plans in every
-    pass (and the TMA-tiled FP32 z-pass at n3 = 64, 128, 256)."""
+    """Grids whose sides run the compile-time FFT plans in every pass, and the
+    TMA-tiled FP32 y- and z-passes at n2, n3 = 64, 128, 256."""
     from paper_2204_13624_gb300 import microstructure as ms
 
-    for n in [(64, 64, 64), (64, 32, 128), (128, 64, 256)]:
+    for n in [(64, 64, 64), (64, 32, 128), (128, 64, 256), (32, 128, 32), (16, 256, 16)]:
         p = ms.random_spheres(n, 5.0, 0.15, 11, 10.0, np.diag([1.03, 1.0, 1.0]) + 0.01, 1)
         g, r = solve_both(cb, orc, p, solver=1, precision=prec, fixed_iterations=1, cg_fixed_iterations=10)
         tol = 1e-10 if prec == 0 else 2e-5
