@@ -22,9 +22,10 @@
 
 namespace combo {
 
+// ping-pong line buffers, reduction scratch and flag, twiddle table
 size_t xpass_smem(const GridDims& g, int lines, size_t cxbytes)
 {
-    return 2 * (size_t)9 * lines * (g.M + 1) * cxbytes + 256 * sizeof(double) + 16;
+    return 2 * (size_t)9 * lines * (g.M + 1) * cxbytes + 256 * sizeof(double) + 16 + (size_t)g.M * cxbytes;
 }
 
 int xpass_lines(const GridDims& g, size_t cxbytes)
@@ -172,6 +173,8 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 3 : 1) k_xfwd(X
     cx<T>* buf1 = buf0 + (size_t)9 * LB * ls;
     double* red = reinterpret_cast<double*>(buf1 + (size_t)9 * LB * ls);
     int* flag = reinterpret_cast<int*>(red + 256);
+    cx<T>* tws = reinterpret_cast<cx<T>*>(flag + 4);  // twiddles exp(-2 pi i t / M)
+    for (int i = threadIdx.x; i < g.M; i += blockDim.x) tws[i] = a.tw[i];
     T* rb = reinterpret_cast<T*>(buf0);
     const int nlines = g.n2 * g.n3;
     const int ngroups = (nlines + LB - 1) / LB;
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 3 : 1) k_xfwd(X
         __syncthreads();
 
         const int nl = 9 * LB;
-        cx<T>* Z = xpass_fft<T, MF, false>(buf0, buf1, a.plan, nl, ls, a.tw);
+        cx<T>* Z = xpass_fft<T, MF, false>(buf0, buf1, a.plan, nl, ls, tws);
 
         // Hermitian split of the packed transform: X[k] = Ze + W^k Zo, k = 0..M
         const int M = g.M;
@@ -383,6 +386,8 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
     cx<T>* buf1 = buf0 + (size_t)9 * LB * ls;
     double* red = reinterpret_cast<double*>(buf1 + (size_t)9 * LB * ls);
     int* flag = reinterpret_cast<int*>(red + 256);
+    cx<T>* tws = reinterpret_cast<cx<T>*>(flag + 4);  // twiddles exp(-2 pi i t / M)
+    for (int i = threadIdx.x; i < g.M; i += blockDim.x) tws[i] = a.tw[i];
     const int nlines = g.n2 * g.n3;
     const int ngroups = (nlines + LB - 1) / LB;
     const int nl = 9 * LB;
@@ -412,7 +417,7 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
             buf1[(size_t)q * ls + k] = cx<T>{Ze.x - Zo.y, Ze.y + Zo.x};
         }
         __syncthreads();
-        cx<T>* Zr = xpass_fft<T, MF, true>(buf1, buf0, a.plan, nl, ls, a.tw);
+        cx<T>* Zr = xpass_fft<T, MF, true>(buf1, buf0, a.plan, nl, ls, tws);
         const T* rb = reinterpret_cast<const T*>(Zr);
         Tc accp = 0;  // FP32 within the group, FP64 across groups
 

@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(xinv_threads<M, LB>()) k_xinv_stream(XinvArgs<
     unsigned char* stage[2] = {smem_raw, smem_raw + SB};
     float2* xb = reinterpret_cast<float2*>(smem_raw + 2 * SB);  // exchange rows [NL][lsx]
     float2* w2 = xb + (size_t)NL * lsx;                          // exp(-2 pi i k / n1), k < M
-    double* red = reinterpret_cast<double*>(w2 + M);
+    float2* tws = w2 + M;                                        // exp(-2 pi i t / M)
+    double* red = reinterpret_cast<double*>(tws + M);
     int* flag = reinterpret_cast<int*>(red + 256);
     uint64_t* bar = reinterpret_cast<uint64_t*>(flag + 4);
 
@@ -90,7 +91,10 @@ __global__ void __launch_bounds__(xinv_threads<M, LB>()) k_xinv_stream(XinvArgs<
         }
     };
 
-    for (int k = threadIdx.x; k < M; k += blockDim.x) w2[k] = a.tw2[k];
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        w2[k] = a.tw2[k];
+        tws[k] = a.tw[k];
+    }
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(xinv_threads<M, LB>()) k_xinv_stream(XinvArgs<
             *reinterpret_cast<float2*>(rg + 2 * e) = rn;
             accp += rn.x * rn.x + rn.y * rn.y;
         };
-        fft_fast<float, M, true, false, false>(lg, sg, lx, sx, tau, a.tw);
+        fft_fast<float, M, true, false, false>(lg, sg, lx, sx, tau, tws);
         acc += (double)accp;
         __syncthreads();  // stage s and the exchange rows are reused
     }
@@ -178,7 +182,7 @@ template <int M, int LB> static void xinv_stream_launch(const XinvArgs<float, fl
     constexpr int lsx = (M + 2) / 2 * 2;
     constexpr int threads = xinv_threads<M, LB>();
     constexpr size_t sb = (size_t)9 * LB * lsx * 8 + (size_t)9 * LB * 2 * M * 4;
-    constexpr size_t sm = 2 * sb + (size_t)9 * LB * lsx * 8 + (size_t)M * 8 + 256 * 8 + 16 + 16;
+    constexpr size_t sm = 2 * sb + (size_t)9 * LB * lsx * 8 + (size_t)2 * M * 8 + 256 * 8 + 16 + 16;
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaFuncSetAttribute(k_xinv_stream<M, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

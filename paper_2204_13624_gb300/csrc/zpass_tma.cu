@@ -87,7 +87,9 @@ __global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
     typedef cx<float> C;
     C* tiles = reinterpret_cast<C*>(smem_raw);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * TILE_BYTES);
+    C* tws = reinterpret_cast<C*>(bar + 2);  // twiddles exp(-2 pi i t / N) in shared memory
     const GridDims g = a.g;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = a.tw[i];
     const int c = threadIdx.x / GS;
     const int r = threadIdx.x - c * GS;
     const int line = r % TX, tau = r / TX;
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
         auto sp = [&](int e, C v) { pc[e * TX] = v; };
 
         // forward along z, in place in the tile
-        fft_fast<float, N, false, true, true>(lp, sp, lp, sp, tau, a.tw);
+        fft_fast<float, N, false, true, true>(lp, sp, lp, sp, tau, tws);
         __syncthreads();
 
         // projection: row i of G X at every (xi3, column) = k (k . X_i) / |k|^2
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
         __syncthreads();
 
         // inverse along z, in place; then the whole tile leaves by one store
-        fft_fast<float, N, true, true, true>(lp, sp, lp, sp, tau, a.tw);
+        fft_fast<float, N, true, true, true>(lp, sp, lp, sp, tau, tws);
         fence_proxy_async();  // this thread's tile writes, before the copy engine reads them
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -225,7 +227,9 @@ __global__ void __launch_bounds__(TYX * FastPlan<N>::TPL)
     typedef cx<float> C;
     C* tiles = reinterpret_cast<C*>(smem_raw);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * TILE_BYTES);
+    C* tws = reinterpret_cast<C*>(bar + 2);  // twiddles in shared memory
     const GridDims g = a.g;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = a.tw[i];
     const int line = threadIdx.x % TX, tau = threadIdx.x / TX;
     const int nxt = (g.nh + TX - 1) / TX;
     const int ntiles = nxt * g.n3 * 9;
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(TYX * FastPlan<N>::TPL)
         C* pc = park + line;
         auto lp = [&](int e) { return pc[e * TX]; };
         auto sp = [&](int e, C v) { pc[e * TX] = v; };
-        fft_fast<float, N, INV, true, true>(lp, sp, lp, sp, tau, a.tw);
+        fft_fast<float, N, INV, true, true>(lp, sp, lp, sp, tau, tws);
         fence_proxy_async();  // this thread's tile writes, before the copy engine reads them
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -289,7 +293,7 @@ __global__ void __launch_bounds__(TYX * FastPlan<N>::TPL)
 template <int N, bool INV> static void ypass_tma_launch(const YArgs<float>& a, const void* map, cudaStream_t st)
 {
     constexpr int threads = TYX * FastPlan<N>::TPL;
-    const size_t sm = (size_t)2 * N * TYX * 8 + 16;
+    const size_t sm = (size_t)2 * N * TYX * 8 + 16 + (size_t)N * 8;
     static int grid_per_sm = 0;
     static int nsm = 0;
     if (grid_per_sm == 0) {
@@ -324,7 +328,7 @@ template <int N> static void zpass_tma_launch(const ZArgs<float>& a, const void*
 {
     constexpr int TX = tma_tx<N>();
     constexpr int threads = 3 * TX * FastPlan<N>::TPL;
-    const size_t sm = (size_t)2 * 3 * N * TX * 8 + 16;
+    const size_t sm = (size_t)2 * 3 * N * TX * 8 + 16 + (size_t)N * 8;
     static int grid_per_sm = 0;
     static int nsm = 0;
     if (grid_per_sm == 0) {
