@@ -161,7 +161,7 @@ __device__ __forceinline__ bool nh_stress_df(const double Fd[9], double mu, doub
 // TAN: the Krylov tangent pass (a.mode == XF_TANGENT, no external X), whose
 // FP32 instance is register-capped for three resident blocks per SM
 template <typename T, typename Tc, int MF, bool TAN>
-__global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 3 : 1) k_xfwd(XfwdArgs<T, Tc> a, int guard)
+__global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(XfwdArgs<T, Tc> a, int guard)
 {
     if (guard == 1 && a.sc->cg_done) return;
     if (guard == 2 && a.sc->outer_done) return;
