@@ -398,11 +398,13 @@ def serving_problems(count, seed, sides, max_steps):
 def serving_bench(combo, ctx, count=12, sides=(48, 64, 72, 96), max_steps=4, slots=4, seed=2204_13624 + 4):
     """Saturated throughput of the request stream (all submitted at once),
     then Poisson arrivals at 0.7 x that rate for latency percentiles; the
-    FP32-refined form against the plain FP64 form on the same requests."""
+    refined forms (double-float and FP64 residual transforms) against the
+    plain FP64 form on the same requests."""
     probs = serving_problems(count, seed, sides, max_steps)
     out = {"requests": count, "sides": list(sides), "load_steps": f"1..{max_steps}", "slots": slots}
     pbar = {}
-    for form, prec in (("refined", combo.FP32_REFINED_DF), ("fp64", combo.FP64)):
+    for form, prec in (("refined", combo.FP32_REFINED_DF), ("refined_fp64_residual", combo.FP32_REFINED),
+                       ("fp64", combo.FP64)):
         srv = combo.Server(ctx, max_slots=slots)
         t0 = time.perf_counter()
         tk = [srv.submit(p, precision=prec, tol=1e-8) for p in probs]
@@ -433,9 +435,10 @@ def serving_bench(combo, ctx, count=12, sides=(48, 64, 72, 96), max_steps=4, slo
             entry.update(arrival_rate_per_s=lam, solves_per_s=count / dt2, p50_seconds=st["p50_seconds"],
                          p99_seconds=st["p99_seconds"], peak_concurrent=st["peak_running"])
         out[form] = entry
-    errs = [float(np.max(np.abs(a - b)) / np.max(np.abs(b))) for a, b in zip(pbar["refined"], pbar["fp64"])]
-    out["Pbar_rel_err_refined_vs_fp64_max"] = max(errs)
-    out["speedup_refined_vs_fp64"] = out["refined"]["saturated_solves_per_s"] / out["fp64"]["saturated_solves_per_s"]
+    for form in ("refined", "refined_fp64_residual"):
+        errs = [float(np.max(np.abs(a - b)) / np.max(np.abs(b))) for a, b in zip(pbar[form], pbar["fp64"])]
+        out[f"Pbar_rel_err_{form}_vs_fp64_max"] = max(errs)
+        out[f"speedup_{form}_vs_fp64"] = out[form]["saturated_solves_per_s"] / out["fp64"]["saturated_solves_per_s"]
     return out
 
 

@@ -35,7 +35,7 @@ def mix_problems():
     return out
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_results_alone_equal_results_in_the_mix(cb, prec):
     probs = mix_problems()
     alone = [cb.solve(p, fields=True, precision=prec, tol=1e-8) for p in probs]
