@@ -316,11 +316,14 @@ __device__ __forceinline__ int nr_loop(LE& e, double a[3], const double m[3], do
 template <typename Tc, bool DFM>
 __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
 {
-    if (A.guard == 2 && A.sc->outer_done) return;
     __shared__ double red[64];
+    __shared__ int same_problem;
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // the problem of this boxel (stacked problems: boxels in problem order)
+    const int pb = (A.bprob && b < A.nb) ? A.bprob[b] : 0;
+    Scalars* sc = A.sc + pb;
     double its = 0.0, nbp = 0.0, nev = 0.0;
-    if (b < A.nb) {
+    if (b < A.nb && !(A.guard == 2 && sc->outer_done)) {
         nev = 1.0;
         const int64_t v = A.bidx[b];
         double Fb[9], N[3], a[3];
@@ -332,7 +335,9 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
             a[i] = A.ba[3 * b + i];
         }
         const double cp = A.bc[b], cm = 1.0 - cp;
-        const double mu[2] = {A.mu[0], A.mu[1]}, lam[2] = {A.lam[0], A.lam[1]};
+        const double* mp = A.matp ? A.matp + 4 * pb : nullptr;
+        const double mu[2] = {mp ? mp[0] : A.mu[0], mp ? mp[1] : A.mu[1]};
+        const double lam[2] = {mp ? mp[2] : A.lam[0], mp ? mp[3] : A.lam[1]};
         int status = 0, reason = 0;
         // m_beta = F^{-T} N / |F^{-T} N|, beta_c(+/-) = -/+ c(+/-) / |F^{-T} N|  (Sec. 4.2)
         double gbox[3];
@@ -398,17 +403,17 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
             reason = 1;
         }
         if (status) {
-            raise_status(A.sc, status);
-            if (atomicCAS(&A.sc->fail_boxel, 0, (int32_t)(b + 1)) == 0) {
-                A.sc->fail_reason = reason;
+            raise_status(sc, status);
+            if (atomicCAS(&sc->fail_boxel, 0, (int32_t)(b + 1)) == 0) {
+                sc->fail_reason = reason;
 #pragma unroll
-                for (int c = 0; c < 9; c++) A.sc->fail_state[c] = Fb[c];
+                for (int c = 0; c < 9; c++) sc->fail_state[c] = Fb[c];
 #pragma unroll
                 for (int i = 0; i < 3; i++) {
-                    A.sc->fail_state[9 + i] = N[i];
-                    A.sc->fail_state[13 + i] = a[i];
+                    sc->fail_state[9 + i] = N[i];
+                    sc->fail_state[13 + i] = a[i];
                 }
-                A.sc->fail_state[12] = cp;
+                sc->fail_state[12] = cp;
             }
         } else {
 #pragma unroll
@@ -417,7 +422,7 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
             for (int i = 0; i < 3; i++) A.ba[3 * b + i] = a[i];
             if (A.bA) {
                 if (!inv64(e, Di)) {
-                    raise_status(A.sc, COMBO_E_LAMINATE);
+                    raise_status(sc, COMBO_E_LAMINATE);
                 } else {
                     // The boxel tangent only feeds the Krylov iterations: it is
                     // formed in their precision Tc from the converged state.
@@ -455,14 +460,28 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
             }
         }
     }
-    const double s1 = block_sum(its, red);
-    const double s2 = block_sum(nbp, red + 32);
-    __syncthreads();
-    const double s3 = block_sum(nev, red);
+    // counters: one atomic per block when its boxels share a problem
     if (threadIdx.x == 0) {
-        atomicAdd(&A.sc->nr_iters, (unsigned long long)s1);
-        atomicAdd(&A.sc->n_backproj, (unsigned long long)s2);
-        atomicAdd(&A.sc->n_lam, (unsigned long long)s3);
+        const int64_t first = (int64_t)blockIdx.x * blockDim.x;
+        const int64_t last = min(first + (int64_t)blockDim.x, A.nb) - 1;
+        same_problem = (!A.bprob || A.bprob[first] == A.bprob[last]) ? 1 : 0;
+    }
+    __syncthreads();
+    if (same_problem) {
+        const double s1 = block_sum(its, red);
+        const double s2 = block_sum(nbp, red + 32);
+        __syncthreads();
+        const double s3 = block_sum(nev, red);
+        if (threadIdx.x == 0) {
+            Scalars* s0 = A.sc + (A.bprob ? A.bprob[(int64_t)blockIdx.x * blockDim.x] : 0);
+            atomicAdd(&s0->nr_iters, (unsigned long long)s1);
+            atomicAdd(&s0->n_backproj, (unsigned long long)s2);
+            atomicAdd(&s0->n_lam, (unsigned long long)s3);
+        }
+    } else if (nev > 0.0) {
+        atomicAdd(&sc->nr_iters, (unsigned long long)its);
+        atomicAdd(&sc->n_backproj, (unsigned long long)nbp);
+        atomicAdd(&sc->n_lam, (unsigned long long)nev);
     }
 }
 

@@ -53,14 +53,31 @@ struct Plan {
     int Ns[kMaxStages];  // product of the radices of the stages before this one
 };
 
+// A batch of nprob independent problems on equal grids n1 x n2 x n3p is laid
+// out as one grid whose z axis holds the problems one after another
+// (n3 = nprob * n3p): every x-line, y-column and z-column then belongs to one
+// problem, the x- and y-passes need no change, the z-passes transform
+// segments of length n3p, and solver scalars are kept per problem.  A single
+// solve is the batch of one (nprob = 1, n3p = n3).
 struct GridDims {
     int n1, n2, n3;
     int M;     // n1 / 2: complex length of the packed x transform
     int nh;    // M + 1 stored x frequencies (Hermitian half)
     int nhp;   // pitch of the x-frequency axis in the spectrum (>= nh)
-    int64_t V;   // voxels
+    int64_t V;   // voxels (all problems)
     int64_t Vs;  // complex entries per spectrum component: n3 * n2 * nhp
+    int nprob;   // stacked problems
+    int n3p;     // z planes of one problem
 };
+
+// x-pass grids give every problem the same number of blocks gp: block ->
+// (problem b, index j within the problem's blocks)
+__device__ __forceinline__ void prob_block(const GridDims& g, int& b, int& j, int& gp)
+{
+    gp = (int)gridDim.x / g.nprob;
+    b = (int)blockIdx.x / gp;
+    j = (int)blockIdx.x - b * gp;
+}
 
 // Solver scalars that live on the device between kernels.
 struct Scalars {
@@ -252,15 +269,15 @@ __device__ __forceinline__ double sum_partials_fixed(const double* p, int n, dou
     return s;
 }
 
-// True in every thread of the block that finishes last (after its partial
-// was written by thread 0).  ticket is reset by that block.
-__device__ __forceinline__ bool last_block(unsigned int* ticket, int* flag_smem)
+// True in every thread of the block that finishes last of nblocks blocks
+// sharing ticket (after its partial was written by thread 0).  ticket is reset
+// by that block.
+__device__ __forceinline__ bool last_block(unsigned int* ticket, int* flag_smem, unsigned int nblocks)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned int t = atomicAdd(ticket, 1u);
-        const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
         *flag_smem = (t == nblocks - 1) ? 1 : 0;
         if (*flag_smem) *ticket = 0u;
     }
@@ -353,6 +370,7 @@ template <typename T, typename Tc> struct XfwdArgs {
     const Tc* r;
     Tc* p;
     Tc* x;               // receives the previous iteration's x += alpha p
+    const double* matp;  // [nprob][4] (mu-, mu+, lam-, lam+) per problem, or null: mu, lam
     const Tc* bA;        // [45][nb] packed symmetric boxel tangent, boxels in voxel order
     const int32_t* bvox; // [nb] voxel of the k-th boxel in voxel order
     const int32_t* lofs; // [n2 n3 + 1] first boxel (voxel order) of each x-line
@@ -420,6 +438,7 @@ size_t xpass_smem(const GridDims& g, int lines, size_t cxbytes);
 int xpass_lines(const GridDims& g, size_t cxbytes);
 int xpass_grid(const GridDims& g, int lines);  // x-pass blocks (= partial count)
 int xpass_partials_max(const GridDims& g);     // upper bound of any x-pass grid
+int xpass_gp(const GridDims& g, int lines, int cap);  // x-pass blocks per problem (grid = nprob * gp)
 int ypass_tx(int n, size_t cxbytes);  // columns per y-pass block (must match the launcher)
 int zpass_tx(int n, size_t cxbytes);  // columns per z-pass block (sets the partial count)
 
@@ -448,6 +467,8 @@ template <typename Tc> struct BoxelArgs {
     double* bP;    // [nb][9]
     Tc* bA;        // [45][nb] packed symmetric tangent (sym_idx), column rank[b]; or null
     const int32_t* rank;  // position of boxel b in voxel order
+    const int32_t* bprob; // problem of boxel b (stacked problems), or null
+    const double* matp;   // [nprob][4] (mu-, mu+, lam-, lam+), or null: mu, lam
     const double* F;
     double mu[2], lam[2];
     double tol_rel, tol_abs;

@@ -119,6 +119,8 @@ extern "C" int combo_apply_G_noalloc(int32_t device, void* stream, const int32_t
     g.n1 = n[0];
     g.n2 = n[1];
     g.n3 = n[2];
+    g.n3p = n[2];
+    g.nprob = 1;
     g.M = n[0] / 2;
     g.nh = g.M + 1;
     g.nhp = (g.nh + 3) / 4 * 4;

@@ -208,8 +208,8 @@ template <typename T> static int make_tables(DevTables<T>& t, const GridDims& g,
     if ((rc = upload_tw<T>(&t.twM, g.M, g.M))) return rc;
     if ((rc = upload_tw<T>(&t.tw2, g.M + 1, g.n1))) return rc;
     if ((rc = upload_tw<T>(&t.twy, g.n2, g.n2))) return rc;
-    if ((rc = upload_tw<T>(&t.twz, g.n3, g.n3))) return rc;
-    const int n[3] = {g.n1, g.n2, g.n3};
+    if ((rc = upload_tw<T>(&t.twz, g.n3p, g.n3p))) return rc;
+    const int n[3] = {g.n1, g.n2, g.n3p};
     return upload_symbols<T>(t, n, l, kspace);
 }
 
@@ -232,17 +232,20 @@ static int tx_for(int n, size_t cxbytes, size_t budget, int comps)
     return tx;
 }
 
-static GridDims make_dims(const int32_t n[3])
+// grid of nprob stacked problems of n1 x n2 x n3 each (z axis: problem-major)
+static GridDims make_dims(const int32_t n[3], int nprob = 1)
 {
     GridDims g{};
     g.n1 = n[0];
     g.n2 = n[1];
-    g.n3 = n[2];
+    g.n3 = n[2] * nprob;
+    g.n3p = n[2];
+    g.nprob = nprob;
     g.M = n[0] / 2;
     g.nh = g.M + 1;
     g.nhp = (g.nh + 3) / 4 * 4;
-    g.V = (int64_t)n[0] * n[1] * n[2];
-    g.Vs = (int64_t)n[2] * n[1] * g.nhp;
+    g.V = (int64_t)n[0] * n[1] * g.n3;
+    g.Vs = (int64_t)g.n3 * n[1] * g.nhp;
     return g;
 }
 
@@ -361,10 +364,10 @@ template <typename T> struct Engine {
         g = gd;
         pM = make_plan(g.M);
         py = make_plan(g.n2);
-        pz = make_plan(g.n3);
+        pz = make_plan(g.n3p);
         lines = xpass_lines(g, sizeof(cx<T>));
         txy = ypass_tx(g.n2, sizeof(cx<T>));
-        txz = zpass_tx(g.n3, sizeof(cx<T>));
+        txz = zpass_tx(g.n3p, sizeof(cx<T>));
         return make_tables<T>(tab, g, l, kspace);
     }
     void release() { free_tables<T>(tab); }
@@ -430,7 +433,8 @@ template <typename T> struct Engine {
         launch_ypass<T, true>(y, st);
         if (pr) pr->end();
     }
-    int zblocks() const { return ((g.nh + txz - 1) / txz) * g.n2 * 3; }
+    int zblocks_p() const { return ((g.nh + txz - 1) / txz) * g.n2 * 3; }  // z-pass blocks (partials) per problem
+    int zblocks() const { return zblocks_p() * g.nprob; }
     int xblocks() const { return xpass_grid(g, lines); }
     int xpartials() const { return std::max(xpass_grid(g, lines), xpass_partials_max(g)); }
 };
@@ -448,10 +452,13 @@ struct Mat9 {
     double v[9];
 };
 
-__global__ void k_add_uniform(double* F, int64_t V, Mat9 d)
+// F += d (uniform); stacked problems: dF [nprob][9] per problem of Vp voxels
+__global__ void k_add_uniform(double* F, int64_t V, Mat9 d, const double* dF, int64_t Vp)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 9 * V; i += (int64_t)gridDim.x * blockDim.x)
-        F[i] += d.v[i / V];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 9 * V; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / V;
+        F[i] += dF ? dF[9 * ((i - c * V) / Vp) + c] : d.v[c];
+    }
 }
 
 __global__ void k_vox2box(int32_t* map, const int32_t* bidx, int64_t nb)
@@ -463,12 +470,16 @@ __global__ void k_vox2box(int32_t* map, const int32_t* bidx, int64_t nb)
 // deterministic fixed-order sum of n partials by one block
 __device__ double sum_partials(const double* p, int n, double* red) { return sum_partials_fixed(p, n, red); }
 
-// residual of the current evaluation; fixed-point bookkeeping (mode 1)
-__global__ void k_fin_resid(Scalars* sc, const double* part, int n, double V, double tol, int fixed, int max_iter,
-                            int fixed_point)
+// residual of the current evaluation; fixed-point bookkeeping (mode 1).
+// Block b: problem b, partials part[b n .. b n + n); V voxels per problem.
+// skip_done: problems whose outer_done is set were not evaluated.
+__global__ void k_fin_resid(Scalars* scs, const double* part_all, int n, double V, double tol, int fixed, int max_iter,
+                            int fixed_point, int skip_done = 0)
 {
     __shared__ double red[256];
-    if (fixed_point && sc->outer_done) return;
+    Scalars* sc = scs + blockIdx.x;
+    const double* part = part_all + (size_t)blockIdx.x * n;
+    if ((fixed_point || skip_done) && sc->outer_done) return;
     const double s = sum_partials(part, n, red);
     if (threadIdx.x != 0) return;
     sc->resid2 = s;
@@ -500,10 +511,17 @@ __global__ void k_fin_resid(Scalars* sc, const double* part, int n, double V, do
     }
 }
 
-__global__ void k_fin_rhs(Scalars* sc, const double* part, int n, int cg_fixed, int cg_max)
+// CG start of problem b = block b (partials part[b n ..]); a problem whose
+// outer_done is set takes no CG iterations in this round
+__global__ void k_fin_rhs(Scalars* scs, const double* part_all, int n, int cg_fixed, int cg_max)
 {
     __shared__ double red[256];
-    const double s = sum_partials(part, n, red);
+    Scalars* sc = scs + blockIdx.x;
+    if (sc->outer_done) {
+        if (threadIdx.x == 0) sc->cg_done = 1;
+        return;
+    }
+    const double s = sum_partials(part_all + (size_t)blockIdx.x * n, n, red);
     if (threadIdx.x != 0) return;
     sc->rr = s;
     sc->rr0 = s;
@@ -516,12 +534,18 @@ __global__ void k_fin_rhs(Scalars* sc, const double* part, int n, int cg_fixed, 
 
 // F += d * (x + alpha_pending p) -- the CG solution including the update the
 // last CG iteration still owes -- then admissibility (det F > 0) of every voxel
+// Stacked problems: dv[b] per problem of Vp voxels (0: F of that problem is
+// left unchanged), the pending alpha and the admissibility flag per problem.
 template <typename Tc>
-__global__ void k_update_F(double* __restrict__ F, const Tc* __restrict__ x, const Tc* __restrict__ p, double d,
-                           int64_t V, Scalars* sc)
+__global__ void k_update_F(double* __restrict__ F, const Tc* __restrict__ x, const Tc* __restrict__ p, double d0,
+                           int64_t V, Scalars* scs, const double* dv, int64_t Vp)
 {
-    const Tc ap = (Tc)sc->alpha_pending;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = dv ? v / Vp : 0;
+        const double d = dv ? dv[b] : d0;
+        if (d == 0.0) continue;
+        Scalars* sc = scs + b;
+        const Tc ap = (Tc)sc->alpha_pending;
         double f[9];
         Tc xv[9];
         // all loads before the first store
@@ -546,8 +570,9 @@ __global__ void k_update_F(double* __restrict__ F, const Tc* __restrict__ x, con
 }
 
 // P field of F (pure voxels Neo-Hookean, boxels from the laminate stresses)
+// matp [nprob][4] per problem of Vp voxels, or null: mat
 __global__ void k_eval_P(const double* F, const uint8_t* phase, const int32_t* vox2box, const double* bP, Mat9 mat,
-                         double* P, int64_t V, Scalars* sc)
+                         double* P, int64_t V, Scalars* sc, const double* matp, int64_t Vp)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
         const int ph = phase[v];
@@ -558,7 +583,8 @@ __global__ void k_eval_P(const double* F, const uint8_t* phase, const int32_t* v
         }
         double f[9];
         for (int c = 0; c < 9; c++) f[c] = F[c * V + v];
-        const double mu = mat.v[ph], lam = mat.v[2 + ph];
+        const double* mp = matp ? matp + 4 * (v / Vp) : mat.v;
+        const double mu = mp[ph], lam = mp[2 + ph];
         const double c0 = f[4] * f[8] - f[5] * f[7], c1 = f[5] * f[6] - f[3] * f[8], c2 = f[3] * f[7] - f[4] * f[6];
         const double J = f[0] * c0 + f[1] * c1 + f[2] * c2;
         if (!(J > 0.0)) {
@@ -1034,7 +1060,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         }
         std::memcpy(Fprev, Fn, sizeof(Fn));
         prof.begin(K_UPDATE);
-        k_add_uniform<<<grid_for(9 * g.V), 256, 0, st>>>(d_F, g.V, d);
+        k_add_uniform<<<grid_for(9 * g.V), 256, 0, st>>>(d_F, g.V, d, nullptr, g.V);
         prof.end();
         CK(cudaGetLastError());
         outer = 0;
@@ -1135,7 +1161,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                     for (int h = 0; h <= 10; h++) {
                         if ((rc = set_flag(offsetof(Scalars, admissible), 1))) return error = rc;
                         prof.begin(K_UPDATE);
-                        k_update_F<Tc><<<grid_for(g.V), 256, 0, st>>>(d_F, d_x, d_p, d, g.V, d_sc);
+                        k_update_F<Tc><<<grid_for(g.V), 256, 0, st>>>(d_F, d_x, d_p, d, g.V, d_sc, nullptr, g.V);
                         prof.end();
                         if ((rc = read_scalars(s))) return error = rc;
                         if (s.admissible) {
@@ -1188,7 +1214,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             m.v[1] = hp.mu[1];
             m.v[2] = hp.lam[0];
             m.v[3] = hp.lam[1];
-            k_eval_P<<<grid_for(V), 256, 0, st>>>(d_F, d_phase, d_v2b, d_bP, m, P, V, d_sc);
+            k_eval_P<<<grid_for(V), 256, 0, st>>>(d_F, d_phase, d_v2b, d_bP, m, P, V, d_sc, nullptr, V);
             if (!dev) {
                 CK(cudaMemcpyAsync(r->P_out, P, 8 * 9 * V, cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));

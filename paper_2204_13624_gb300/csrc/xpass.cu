@@ -33,7 +33,7 @@ int xpass_lines(const GridDims& g, size_t cxbytes)
     // keep the two ping-pong buffers under ~48 KB while covering >= 512 voxels
     int lines = 1;
     while (lines * g.n1 < 512 && xpass_smem(g, lines * 2, cxbytes) <= 48 * 1024 &&
-           (g.n2 * g.n3) % (lines * 2) == 0)
+           (g.n2 * g.n3p) % (lines * 2) == 0)
         lines *= 2;
     return lines;
 }
@@ -51,13 +51,16 @@ static int grid_cap(const GridDims&)
     return 4 * nsm;
 }
 
-int xpass_partials_max(const GridDims& g) { return 2 * grid_cap(g); }
+int xpass_partials_max(const GridDims& g) { return 2 * grid_cap(g) + g.nprob; }
 
-int xpass_grid(const GridDims& g, int lines)
+// blocks per problem: the problem's line groups, at most cap / nprob
+int xpass_gp(const GridDims& g, int lines, int cap)
 {
-    const int groups = (g.n2 * g.n3 + lines - 1) / lines;
-    return std::min(groups, grid_cap(g));
+    const int groups = (g.n2 * g.n3p + lines - 1) / lines;
+    return std::max(1, std::min(groups, cap / g.nprob));
 }
+
+int xpass_grid(const GridDims& g, int lines) { return g.nprob * xpass_gp(g, lines, grid_cap(g)); }
 
 template <typename K> static void allow_smem(K kernel, bool& done)
 {
@@ -163,10 +166,13 @@ __device__ __forceinline__ bool nh_stress_df(const double Fd[9], double mu, doub
 template <typename T, typename Tc, int MF, bool TAN>
 __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(XfwdArgs<T, Tc> a, int guard)
 {
-    if (guard == 1 && a.sc->cg_done) return;
-    if (guard == 2 && a.sc->outer_done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const GridDims g = a.g;
+    int pb, pj, gp;  // problem of this block, index among its gp blocks
+    prob_block(g, pb, pj, gp);
+    Scalars* sc = a.sc + pb;
+    if (guard == 1 && sc->cg_done) return;
+    if (guard == 2 && sc->outer_done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int LB = a.lines_per_block;
     const int ls = g.M + 1;
     cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
@@ -176,26 +182,32 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
     cx<T>* tws = reinterpret_cast<cx<T>*>(flag + 4);  // twiddles exp(-2 pi i t / M)
     for (int i = threadIdx.x; i < g.M; i += blockDim.x) tws[i] = a.tw[i];
     T* rb = reinterpret_cast<T*>(buf0);
-    const int nlines = g.n2 * g.n3;
-    const int ngroups = (nlines + LB - 1) / LB;
+    const int nlp = g.n2 * g.n3p;  // x-lines of one problem
+    const int Lbase = pb * nlp, Lend = Lbase + nlp;
+    const int ngroups = (nlp + LB - 1) / LB;
     const int64_t V = g.V;
     double acc = 0.0;
+    double mu[2], lam[2];
+    for (int i = 0; i < 2; i++) {
+        mu[i] = a.matp ? a.matp[4 * pb + i] : a.mu[i];
+        lam[i] = a.matp ? a.matp[4 * pb + 2 + i] : a.lam[i];
+    }
 
-    const bool first = (a.mode == XF_TANGENT) ? (a.sc->cg_iter == 0) : false;
-    const Tc beta = (a.mode == XF_TANGENT && !first) ? (Tc)a.sc->beta : (Tc)0;
-    const Tc apend = (a.mode == XF_TANGENT && !first) ? (Tc)a.sc->alpha_pending : (Tc)0;
+    const bool first = (a.mode == XF_TANGENT) ? (sc->cg_iter == 0) : false;
+    const Tc beta = (a.mode == XF_TANGENT && !first) ? (Tc)sc->beta : (Tc)0;
+    const Tc apend = (a.mode == XF_TANGENT && !first) ? (Tc)sc->alpha_pending : (Tc)0;
     const uint8_t* __restrict__ phase = a.phase;
 
-    // grid-stride over groups of LB x-lines (a few blocks per SM)
-    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-        const int L0 = grp * LB;
+    // grid-stride over the problem's groups of LB x-lines
+    for (int grp = pj; grp < ngroups; grp += gp) {
+        const int L0 = Lbase + grp * LB;
         // dot products: FP32 within a thread's share of a group, FP64 across
         // groups (FP64 arithmetic runs at a small fraction of the FP32 rate)
         Tc accp = 0;
         for (int e = threadIdx.x; e < LB * g.n1; e += blockDim.x) {
             const int l = e / g.n1, x = e - l * g.n1;
             const int L = L0 + l;
-            if (L >= nlines) continue;
+            if (L >= Lend) continue;
             const int64_t v = (int64_t)L * g.n1 + x;
             T o[9];
             if constexpr (!TAN) {
@@ -217,8 +229,8 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
                     }
                 } else if constexpr (std::is_same<T, df32>::value) {
                     float G[9], m;
-                    if (!nh_stress_df(F, a.mu[ph], a.lam[ph], o, G, m)) {
-                        raise_status(a.sc, COMBO_E_INADMISSIBLE);
+                    if (!nh_stress_df(F, mu[ph], lam[ph], o, G, m)) {
+                        raise_status(sc, COMBO_E_INADMISSIBLE);
 #pragma unroll
                         for (int c = 0; c < 9; c++) {
                             o[c] = df32(0.f, 0.f);
@@ -233,8 +245,8 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
                     }
                 } else {
                     double P[9], G[9], m;
-                    if (!nh_stress(F, a.mu[ph], a.lam[ph], P, G, m)) {
-                        raise_status(a.sc, COMBO_E_INADMISSIBLE);
+                    if (!nh_stress(F, mu[ph], lam[ph], P, G, m)) {
+                        raise_status(sc, COMBO_E_INADMISSIBLE);
 #pragma unroll
                         for (int c = 0; c < 9; c++) P[c] = G[c] = 0.0;
                         m = 0.0;
@@ -282,7 +294,7 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
                     for (int c = 0; c < 9; c++) o[c] = (T)p[c];
                 } else {
                     Tc y[9];
-                    nh_tangent<Tc>(t, t[9], (Tc)a.mu[ph], (Tc)a.lam[ph], p, y);
+                    nh_tangent<Tc>(t, t[9], (Tc)mu[ph], (Tc)lam[ph], p, y);
                     Tc s = 0;
 #pragma unroll
                     for (int c = 0; c < 9; c++) {
@@ -299,7 +311,7 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
             // boxels of the group, in voxel order: consecutive threads read
             // consecutive columns of the packed tangents (coalesced, no divergence)
             __syncthreads();
-            const int k0 = a.lofs[L0], k1 = a.lofs[min(L0 + LB, nlines)];
+            const int k0 = a.lofs[L0], k1 = a.lofs[min(L0 + LB, Lend)];
             for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
                 const int64_t v = a.bvox[k];
                 const int l = (int)(v / g.n1) - L0, x = (int)(v % g.n1);
@@ -333,7 +345,7 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
             const int q = e / (half + 1), k = e - q * (half + 1);  // k fastest: coalesced stores
             const int c = q / LB, l = q - c * LB;
             const int L = L0 + l;
-            if (L >= nlines) continue;
+            if (L >= Lend) continue;
             const cx<T>* z = Z + (size_t)q * ls;
             cx<T>* o = a.spec + c * g.Vs + (int64_t)L * g.nhp;
             if (k == 0) {
@@ -364,9 +376,9 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
     if (TAN && a.partial) {
         const double s = block_sum(acc, red);
         if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
-        if (a.fuse && last_block(&a.sc->ticket[0], flag)) {
-            const double tot = sum_partials_fixed(a.partial, gridDim.x, red);
-            if (threadIdx.x == 0) cg_alpha(a.sc, tot);
+        if (a.fuse && last_block(&sc->ticket[0], flag, gp)) {
+            const double tot = sum_partials_fixed(a.partial + (size_t)pb * gp, gp, red);
+            if (threadIdx.x == 0) cg_alpha(sc, tot);
         }
     }
 }
@@ -375,10 +387,13 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
 template <typename T, typename Tc, int MF>
 __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
 {
-    if (guard == 1 && a.sc->cg_done) return;
-    if (guard == 2 && a.sc->outer_done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const GridDims g = a.g;
+    int pb, pj, gp;  // problem of this block, index among its gp blocks
+    prob_block(g, pb, pj, gp);
+    Scalars* sc = a.sc + pb;
+    if (guard == 1 && sc->cg_done) return;
+    if (guard == 2 && sc->outer_done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int LB = a.lines_per_block;
     const int ls = g.M + 1;
     const int M = g.M;
@@ -388,23 +403,24 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
     int* flag = reinterpret_cast<int*>(red + 256);
     cx<T>* tws = reinterpret_cast<cx<T>*>(flag + 4);  // twiddles exp(-2 pi i t / M)
     for (int i = threadIdx.x; i < g.M; i += blockDim.x) tws[i] = a.tw[i];
-    const int nlines = g.n2 * g.n3;
-    const int ngroups = (nlines + LB - 1) / LB;
+    const int nlp = g.n2 * g.n3p;  // x-lines of one problem
+    const int Lbase = pb * nlp, Lend = Lbase + nlp;
+    const int ngroups = (nlp + LB - 1) / LB;
     const int nl = 9 * LB;
     const int64_t V = g.V;
     double acc = 0.0;
-    const bool skip_update = (a.mode == XI_FIXEDPOINT) && a.sc->outer_done;
-    const Tc alpha = (a.mode == XI_CG) ? (Tc)a.sc->alpha : (Tc)0;
+    const bool skip_update = (a.mode == XI_FIXEDPOINT) && sc->outer_done;
+    const Tc alpha = (a.mode == XI_CG) ? (Tc)sc->alpha : (Tc)0;
 
-    // grid-stride over groups of LB x-lines (a few blocks per SM)
-    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-        const int L0 = grp * LB;
+    // grid-stride over the problem's groups of LB x-lines
+    for (int grp = pj; grp < ngroups; grp += gp) {
+        const int L0 = Lbase + grp * LB;
         for (int e = threadIdx.x; e < nl * (M + 1); e += blockDim.x) {
             const int q = e / (M + 1), k = e - q * (M + 1);
             const int c = q / LB, l = q - c * LB;
             const int L = L0 + l;
             buf0[(size_t)q * ls + k] =
-                (L < nlines) ? a.spec[c * g.Vs + (int64_t)L * g.nhp + k] : cx<T>{(T)0, (T)0};
+                (L < Lend) ? a.spec[c * g.Vs + (int64_t)L * g.nhp + k] : cx<T>{(T)0, (T)0};
         }
         __syncthreads();
         // Z[k] = Ze + i Zo,  Ze = (X[k] + conj X[M-k]) / 2,  Zo = (X[k] - conj X[M-k]) W^{-k} / 2
@@ -424,7 +440,7 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
         for (int e = threadIdx.x; e < LB * g.n1; e += blockDim.x) {
             const int l = e / g.n1, x = e - l * g.n1;
             const int L = L0 + l;
-            if (L >= nlines) continue;
+            if (L >= Lend) continue;
             const int64_t v = (int64_t)L * g.n1 + x;
             if (a.mode == XI_CG) {
                 // r -= alpha q; the matching x += alpha p is done by the next
@@ -466,9 +482,9 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
     if ((a.mode == XI_RHS || a.mode == XI_CG) && a.partial) {
         const double s = block_sum(acc, red);
         if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
-        if (a.mode == XI_CG && a.fuse && last_block(&a.sc->ticket[1], flag)) {
-            const double tot = sum_partials_fixed(a.partial, gridDim.x, red);
-            if (threadIdx.x == 0) cg_beta(a.sc, tot, a.cg_tol, a.cg_max, a.cg_fixed);
+        if (a.mode == XI_CG && a.fuse && last_block(&sc->ticket[1], flag, gp)) {
+            const double tot = sum_partials_fixed(a.partial + (size_t)pb * gp, gp, red);
+            if (threadIdx.x == 0) cg_beta(sc, tot, a.cg_tol, a.cg_max, a.cg_fixed);
         }
     }
 }
@@ -499,8 +515,7 @@ template <typename T, typename Tc, int MF> static void xfwd_launch(const XfwdArg
                          cudaSuccess ||
                      per_sm < 1))
                     per_sm = 1;
-                const int groups = (a.g.n2 * a.g.n3 + lb - 1) / lb;
-                const int tgrid = std::min(groups, std::min(per_sm * (grid_cap(a.g) / 4), xpass_partials_max(a.g)));
+                const int tgrid = a.g.nprob * xpass_gp(a.g, lb, per_sm * (grid_cap(a.g) / 4));
                 k_xfwd<T, Tc, MF, true><<<tgrid, threads, smb, st>>>(b, guard);
             } else {
                 k_xfwd<T, Tc, MF, true><<<grid, 256, sm, st>>>(a, guard);

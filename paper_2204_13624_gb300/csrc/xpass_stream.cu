@@ -55,7 +55,10 @@ template <int M, int LB> __host__ __device__ constexpr int xinv_threads()
 template <int M, int LB>
 __global__ void __launch_bounds__(xinv_threads<M, LB>()) k_xinv_stream(XinvArgs<float, float> a)
 {
-    if (a.sc->cg_done) return;
+    int pb, pj, gp;  // problem of this block, index among its gp blocks
+    prob_block(a.g, pb, pj, gp);
+    Scalars* scp = a.sc + pb;
+    if (scp->cg_done) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int n1 = 2 * M;
     constexpr int lsx = (M + 2) / 2 * 2;  // M + 1 rounded up to even: 16-byte rows
@@ -72,10 +75,11 @@ __global__ void __launch_bounds__(xinv_threads<M, LB>()) k_xinv_stream(XinvArgs<
     int* flag = reinterpret_cast<int*>(red + 256);
     uint64_t* bar = reinterpret_cast<uint64_t*>(flag + 4);
 
-    const int nlines = g.n2 * g.n3;
-    const int ngroups = nlines / LB;  // the launcher guarantees nlines % LB == 0
+    const int nlp = g.n2 * g.n3p;  // x-lines of one problem
+    const int ngroups = nlp / LB;  // the launcher guarantees nlp % LB == 0
+    const int gbase = pb * ngroups;
     const int64_t V = g.V;
-    const float alpha = (float)a.sc->alpha;
+    const float alpha = (float)scp->alpha;
     constexpr uint32_t tx_bytes = (uint32_t)SB;
 
     auto issue = [&](int grp, int s) {
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(xinv_threads<M, LB>()) k_xinv_stream(XinvArgs<
         fence_proxy_async();
     }
     __syncthreads();
-    if (threadIdx.x == 0 && (int)blockIdx.x < ngroups) issue(blockIdx.x, 0);
+    if (threadIdx.x == 0 && pj < ngroups) issue(gbase + pj, 0);
 
     const int q = threadIdx.x / TPL, tau = threadIdx.x - (threadIdx.x / TPL) * TPL;
     const bool act = q < NL;
@@ -110,12 +114,12 @@ __global__ void __launch_bounds__(xinv_threads<M, LB>()) k_xinv_stream(XinvArgs<
     double acc = 0.0;
     int it = 0;
     bool timed_out = false;
-    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, it++) {
+    for (int lgrp = pj; lgrp < ngroups; lgrp += gp, it++) {
+        const int grp = gbase + lgrp;
         const int s = it & 1;
-        const int nxt = grp + gridDim.x;
-        if (threadIdx.x == 0 && nxt < ngroups) {
+        if (threadIdx.x == 0 && lgrp + gp < ngroups) {
             fence_proxy_async();
-            issue(nxt, s ^ 1);
+            issue(grp + gp, s ^ 1);
         }
         const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1));
         if (__syncthreads_or(!ok)) {
@@ -153,7 +157,7 @@ __global__ void __launch_bounds__(xinv_threads<M, LB>()) k_xinv_stream(XinvArgs<
     }
     if (timed_out) {
         if (threadIdx.x == 0) {
-            raise_status(a.sc, COMBO_E_TIMEOUT);
+            raise_status(scp, COMBO_E_TIMEOUT);
             mbar_wait_bounded(&bar[it & 1 ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
         }
         return;
@@ -161,20 +165,20 @@ __global__ void __launch_bounds__(xinv_threads<M, LB>()) k_xinv_stream(XinvArgs<
     if (a.partial) {
         const double sacc = block_sum(acc, red);
         if (threadIdx.x == 0) a.partial[blockIdx.x] = sacc;
-        if (a.fuse && last_block(&a.sc->ticket[1], flag)) {
-            const double tot = sum_partials_fixed(a.partial, gridDim.x, red);
-            if (threadIdx.x == 0) cg_beta(a.sc, tot, a.cg_tol, a.cg_max, a.cg_fixed);
+        if (a.fuse && last_block(&scp->ticket[1], flag, gp)) {
+            const double tot = sum_partials_fixed(a.partial + (size_t)pb * gp, gp, red);
+            if (threadIdx.x == 0) cg_beta(scp, tot, a.cg_tol, a.cg_max, a.cg_fixed);
         }
     }
 }
 
 // ------------------------------------------------------------- launchers
-static int stream_lines(const GridDims& g) { return (g.n1 <= 128 && (g.n2 * g.n3) % 2 == 0) ? 2 : 1; }
+static int stream_lines(const GridDims& g) { return (g.n1 <= 128 && (g.n2 * g.n3p) % 2 == 0) ? 2 : 1; }
 
 bool stream_xpass_ok(const GridDims& g)
 {
     const int M = g.M;
-    return (M == 64 || M == 128 || M == 256) && (g.n1 % 16) == 0 && (g.n2 * g.n3) % stream_lines(g) == 0;
+    return (M == 64 || M == 128 || M == 256) && (g.n1 % 16) == 0 && (g.n2 * g.n3p) % stream_lines(g) == 0;
 }
 
 template <int M, int LB> static void xinv_stream_launch(const XinvArgs<float, float>& a, cudaStream_t st)
@@ -190,8 +194,7 @@ template <int M, int LB> static void xinv_stream_launch(const XinvArgs<float, fl
             per_sm < 1)
             per_sm = 1;
     }
-    const int groups = a.g.n2 * a.g.n3 / LB;
-    const int grid = std::min(groups, std::min(per_sm * num_sms(), xpass_partials_max(a.g)));
+    const int grid = a.g.nprob * xpass_gp(a.g, LB, per_sm * num_sms());
     k_xinv_stream<M, LB><<<grid, threads, sm, st>>>(a);
 }
 

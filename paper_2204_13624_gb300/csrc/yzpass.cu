@@ -27,8 +27,9 @@ template <typename K> static void allow_smem(K kernel, bool& done)
 template <typename T, bool INV>
 __global__ void __launch_bounds__(256) k_ypass(YArgs<T> a)
 {
-    if (a.guard == 1 && a.sc->cg_done) return;
-    if (a.guard == 2 && a.sc->outer_done) return;
+    const Scalars* sc = a.sc + blockIdx.y / a.g.n3p;  // this z plane's problem
+    if (a.guard == 1 && sc->cg_done) return;
+    if (a.guard == 2 && sc->outer_done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const GridDims g = a.g;
     const int TX = a.tx;
@@ -56,8 +57,9 @@ __global__ void __launch_bounds__(256) k_ypass(YArgs<T> a)
 template <typename T, int N, int TX, bool INV>
 __global__ void __launch_bounds__(TX * FastPlan<N>::TPL) k_ypass_fast(YArgs<T> a)
 {
-    if (a.guard == 1 && a.sc->cg_done) return;
-    if (a.guard == 2 && a.sc->outer_done) return;
+    const Scalars* sc = a.sc + blockIdx.y / a.g.n3p;  // this z plane's problem
+    if (a.guard == 1 && sc->cg_done) return;
+    if (a.guard == 2 && sc->outer_done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* ex = reinterpret_cast<cx<T>*>(smem_raw);
     const GridDims g = a.g;
@@ -78,21 +80,23 @@ __global__ void __launch_bounds__(TX * FastPlan<N>::TPL) k_ypass_fast(YArgs<T> a
 template <typename T>
 __global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
 {
-    if (a.guard == 1 && a.sc->cg_done) return;
-    if (a.guard == 2 && a.sc->outer_done) return;
+    const int pb = blockIdx.z / 3;  // problem; gridDim.z = 3 nprob
+    Scalars* sc = a.sc + pb;
+    if (a.guard == 1 && sc->cg_done) return;
+    if (a.guard == 2 && sc->outer_done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const GridDims g = a.g;
     const int TX = a.tx;
-    const int n3 = g.n3;
+    const int n3 = g.n3p;
     const int W = 3 * TX;  // elements per z row of the tile
     cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
     cx<T>* buf1 = buf0 + (size_t)n3 * W;
     double* red = reinterpret_cast<double*>(buf1 + (size_t)n3 * W);
     const int x0 = blockIdx.x * TX;
     const int y = blockIdx.y;
-    const int row = blockIdx.z;  // tensor row i: components 3i, 3i+1, 3i+2
+    const int row = blockIdx.z - 3 * pb;  // tensor row i: components 3i, 3i+1, 3i+2
     const int64_t zstride = (int64_t)g.n2 * g.nhp;
-    cx<T>* base = a.spec + (int64_t)(3 * row) * g.Vs + (int64_t)y * g.nhp + x0;
+    cx<T>* base = a.spec + (int64_t)(3 * row) * g.Vs + (int64_t)pb * g.n3p * zstride + (int64_t)y * g.nhp + x0;
 
     for (int e = threadIdx.x; e < n3 * W; e += blockDim.x) {
         const int z = e / W, r = e - z * W;
@@ -118,9 +122,9 @@ __global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
         const T kk = k0 * k0 + k1 * k1 + k2 * k2;
         const cx<T> X0 = p[0], X1 = p[TX], X2 = p[2 * TX];
         if (a.want_norm && xi1 == 0 && y == 0 && z == 0) {
-            a.sc->dc[3 * row + 0] = (double)X0.x;
-            a.sc->dc[3 * row + 1] = (double)X1.x;
-            a.sc->dc[3 * row + 2] = (double)X2.x;
+            sc->dc[3 * row + 0] = (double)X0.x;
+            sc->dc[3 * row + 1] = (double)X1.x;
+            sc->dc[3 * row + 2] = (double)X2.x;
         }
         cx<T> o0{(T)0, (T)0}, o1{(T)0, (T)0}, o2{(T)0, (T)0};
         if (kk > (T)0) {
@@ -164,8 +168,10 @@ __global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
 template <typename T, int N, int TX>
 __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<T> a)
 {
-    if (a.guard == 1 && a.sc->cg_done) return;
-    if (a.guard == 2 && a.sc->outer_done) return;
+    const int pb = blockIdx.z / 3;  // problem; gridDim.z = 3 nprob
+    Scalars* sc = a.sc + pb;
+    if (a.guard == 1 && sc->cg_done) return;
+    if (a.guard == 2 && sc->outer_done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TPL = FastPlan<N>::TPL;
     constexpr int GS = TX * TPL;  // threads per component group
@@ -178,9 +184,9 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<
     const int x0 = blockIdx.x * TX;
     const bool valid = x0 + line < g.nh;
     const int y = blockIdx.y;
-    const int row = blockIdx.z;
+    const int row = blockIdx.z - 3 * pb;
     const int64_t zst = (int64_t)g.n2 * g.nhp;
-    cx<T>* bc = a.spec + (int64_t)(3 * row + c) * g.Vs + (int64_t)y * g.nhp + x0 + line;
+    cx<T>* bc = a.spec + (int64_t)(3 * row + c) * g.Vs + (int64_t)pb * N * zst + (int64_t)y * g.nhp + x0 + line;
     cx<T>* pc = park + c * N * TX + line;
     auto lp = [&](int e) { return pc[e * TX]; };
     auto sp = [&](int e, cx<T> v) { pc[e * TX] = v; };
@@ -207,9 +213,9 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<
         const T k0 = ax * by * bz, k1 = ay * bx * bz, k2 = az * bx * by;
         const T kk = k0 * k0 + k1 * k1 + k2 * k2;
         if (a.want_norm && xi1 == 0 && y == 0 && z == 0) {
-            a.sc->dc[3 * row + 0] = (double)X0.x;
-            a.sc->dc[3 * row + 1] = (double)X1.x;
-            a.sc->dc[3 * row + 2] = (double)X2.x;
+            sc->dc[3 * row + 0] = (double)X0.x;
+            sc->dc[3 * row + 1] = (double)X1.x;
+            sc->dc[3 * row + 2] = (double)X2.x;
         }
         cx<T> o0{(T)0, (T)0}, o1{(T)0, (T)0}, o2{(T)0, (T)0};
         if (kk > (T)0) {
@@ -304,7 +310,7 @@ template <typename T, bool INV> void launch_ypass(const YArgs<T>& a, cudaStream_
 template <typename T, int N> static void zpass_fast_launch(const ZArgs<T>& a, cudaStream_t st)
 {
     constexpr int TX = ztx_const<T>(N);
-    dim3 grid((a.g.nh + TX - 1) / TX, a.g.n2, 3);
+    dim3 grid((a.g.nh + TX - 1) / TX, a.g.n2, 3 * a.g.nprob);
     const size_t sm = (size_t)3 * N * TX * sizeof(cx<T>) + 64 * sizeof(double);
     static bool attr = false;
     allow_smem(k_zpass_fast<T, N, TX>, attr);
@@ -314,20 +320,20 @@ template <typename T, int N> static void zpass_fast_launch(const ZArgs<T>& a, cu
 template <typename T> void launch_zpass(const ZArgs<T>& a, cudaStream_t st)
 {
     if constexpr (sizeof(T) == 4) {
-        if (a.tmap && !a.want_norm && zpass_tma_size(a.g.n3)) {
+        if (a.tmap && !a.want_norm && zpass_tma_size(a.g.n3p)) {
             launch_zpass_tma(a, a.tmap, st);
             return;
         }
     }
-    switch (a.g.n3) {
+    switch (a.g.n3p) {
         case 64: zpass_fast_launch<T, 64>(a, st); return;
         case 128: zpass_fast_launch<T, 128>(a, st); return;
         case 256: zpass_fast_launch<T, 256>(a, st); return;
         case 512: zpass_fast_launch<T, 512>(a, st); return;
         default: break;
     }
-    dim3 grid((a.g.nh + a.tx - 1) / a.tx, a.g.n2, 3);
-    const size_t sm = 2 * (size_t)a.g.n3 * 3 * a.tx * sizeof(cx<T>) + 64 * sizeof(double);
+    dim3 grid((a.g.nh + a.tx - 1) / a.tx, a.g.n2, 3 * a.g.nprob);
+    const size_t sm = 2 * (size_t)a.g.n3p * 3 * a.tx * sizeof(cx<T>) + 64 * sizeof(double);
     static bool attr = false;
     allow_smem(k_zpass<T>, attr);
     k_zpass<T><<<grid, 256, sm, st>>>(a);

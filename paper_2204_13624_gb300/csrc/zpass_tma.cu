@@ -55,15 +55,15 @@ bool zpass_tma_size(int n3) { return n3 == 64 || n3 == 128 || n3 == 256; }
 // driver entry point is missing.
 bool zpass_tma_encode(void* map, const GridDims& g, const void* spec)
 {
-    if (!zpass_tma_size(g.n3) || !spec) return false;
-    const int tx = g.n3 == 256 ? tma_tx<256>() : tma_tx<128>();
+    if (!zpass_tma_size(g.n3p) || !spec) return false;
+    const int tx = g.n3p == 256 ? tma_tx<256>() : tma_tx<128>();
     if ((g.nhp * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(spec) & 15) != 0) return false;
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dim[4] = {(cuuint64_t)g.nhp, (cuuint64_t)g.n2, (cuuint64_t)g.n3, 9};
     const cuuint64_t stride[3] = {(cuuint64_t)g.nhp * 8, (cuuint64_t)g.n2 * g.nhp * 8,
                                   (cuuint64_t)g.n3 * g.n2 * g.nhp * 8};
-    const cuuint32_t box[4] = {(cuuint32_t)tx, 1, (cuuint32_t)g.n3, 3};
+    const cuuint32_t box[4] = {(cuuint32_t)tx, 1, (cuuint32_t)g.n3p, 3};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, 4,
                           const_cast<void*>(spec), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -76,8 +76,6 @@ template <int N>
 __global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
     k_zpass_tma(const __grid_constant__ CUtensorMap tm, ZArgs<float> a)
 {
-    if (a.guard == 1 && a.sc->cg_done) return;
-    if (a.guard == 2 && a.sc->outer_done) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr int TX = tma_tx<N>();
     constexpr int TPL = FastPlan<N>::TPL;
@@ -94,15 +92,26 @@ __global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
     const int r = threadIdx.x - c * GS;
     const int line = r % TX, tau = r / TX;
     const int nxt = (g.nh + TX - 1) / TX;
-    const int ntiles = nxt * g.n2 * 3;
+    const int tpp = nxt * g.n2 * 3;  // tiles per problem
+    const int ntiles = tpp * g.nprob;
+    // a tile of a finished problem is skipped (guard 1: CG done, 2: outer done)
+    auto active = [&](int t) {
+        const Scalars* q = a.sc + t / tpp;
+        return !((a.guard == 1 && q->cg_done) || (a.guard == 2 && q->outer_done));
+    };
+    auto next_tile = [&](int t) {
+        while (t < ntiles && !active(t)) t += gridDim.x;
+        return t;
+    };
 
-    // tile t = (row * n2 + y) * nxt + xt: consecutive blocks take neighbouring
-    // x tiles of the same rows of DRAM
+    // tile t = ((b * 3 + row) * n2 + y) * nxt + xt: consecutive blocks take
+    // neighbouring x tiles of the same rows of DRAM
     auto issue = [&](int t, int s) {
         const int xt = t % nxt, rest = t / nxt;
-        const int y = rest % g.n2, row = rest / g.n2;
+        const int y = rest % g.n2, rb = rest / g.n2;
+        const int b = rb / 3, row = rb - 3 * b;
         mbar_arrive_expect_tx(&bar[s], TILE_BYTES);
-        tma_load_4d(tiles + s * TILE, &tm, xt * TX, y, 0, 3 * row, &bar[s]);
+        tma_load_4d(tiles + s * TILE, &tm, xt * TX, y, b * N, 3 * row, &bar[s]);
     };
 
     if (threadIdx.x == 0) {
@@ -111,13 +120,14 @@ __global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
         fence_proxy_async();
     }
     __syncthreads();
-    if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    const int t0 = next_tile(blockIdx.x);
+    if (threadIdx.x == 0 && t0 < ntiles) issue(t0, 0);
 
-    int it = 0;
+    int it = 0, tn = ntiles;
     bool timed_out = false;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+    for (int t = t0; t < ntiles; t = tn, it++) {
         const int s = it & 1;
-        const int tn = t + gridDim.x;
+        tn = next_tile(t + gridDim.x);
         if (threadIdx.x == 0 && tn < ntiles) {
             bulk_wait_read_all();  // the store of the previous tile has left buffer s ^ 1
             issue(tn, s ^ 1);
@@ -128,7 +138,8 @@ __global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
             break;
         }
         const int xt = t % nxt, rest = t / nxt;
-        const int y = rest % g.n2, row = rest / g.n2;
+        const int y = rest % g.n2, rb = rest / g.n2;
+        const int pb = rb / 3, row = rb - 3 * pb;
         const int x0 = xt * TX;
         C* park = tiles + s * TILE;
         C* pc = park + c * N * TX + line;
@@ -174,7 +185,7 @@ __global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
         fence_proxy_async();  // this thread's tile writes, before the copy engine reads them
         __syncthreads();
         if (threadIdx.x == 0) {
-            tma_store_4d(&tm, x0, y, 0, 3 * row, park);
+            tma_store_4d(&tm, x0, y, pb * N, 3 * row, park);
             bulk_commit();
         }
     }
@@ -184,8 +195,7 @@ __global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
             // loads possibly in flight: this iteration's and the prefetch
             const int s = it & 1;
             mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1));
-            if ((int)blockIdx.x + (it + 1) * (int)gridDim.x < ntiles)
-                mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            if (tn < ntiles) mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
         }
         bulk_wait_all();  // the stores are complete before the block's shared memory goes away
     }
@@ -218,8 +228,6 @@ template <int N, bool INV>
 __global__ void __launch_bounds__(TYX * FastPlan<N>::TPL)
     k_ypass_tma(const __grid_constant__ CUtensorMap tm, YArgs<float> a)
 {
-    if (a.guard == 1 && a.sc->cg_done) return;
-    if (a.guard == 2 && a.sc->outer_done) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr int TX = TYX;
     constexpr int TILE = N * TX;
@@ -233,6 +241,16 @@ __global__ void __launch_bounds__(TYX * FastPlan<N>::TPL)
     const int line = threadIdx.x % TX, tau = threadIdx.x / TX;
     const int nxt = (g.nh + TX - 1) / TX;
     const int ntiles = nxt * g.n3 * 9;
+    // a tile of a finished problem (the problem of its z plane) is skipped
+    auto active = [&](int t) {
+        const int z = (t / nxt) % g.n3;
+        const Scalars* q = a.sc + z / g.n3p;
+        return !((a.guard == 1 && q->cg_done) || (a.guard == 2 && q->outer_done));
+    };
+    auto next_tile = [&](int t) {
+        while (t < ntiles && !active(t)) t += gridDim.x;
+        return t;
+    };
 
     // tile t = (c * n3 + z) * nxt + xt
     auto issue = [&](int t, int s) {
@@ -248,13 +266,14 @@ __global__ void __launch_bounds__(TYX * FastPlan<N>::TPL)
         fence_proxy_async();
     }
     __syncthreads();
-    if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    const int t0 = next_tile(blockIdx.x);
+    if (threadIdx.x == 0 && t0 < ntiles) issue(t0, 0);
 
-    int it = 0;
+    int it = 0, tn = ntiles;
     bool timed_out = false;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+    for (int t = t0; t < ntiles; t = tn, it++) {
         const int s = it & 1;
-        const int tn = t + gridDim.x;
+        tn = next_tile(t + gridDim.x);
         if (threadIdx.x == 0 && tn < ntiles) {
             bulk_wait_read_all();  // the store of the previous tile has left buffer s ^ 1
             issue(tn, s ^ 1);
@@ -283,8 +302,7 @@ __global__ void __launch_bounds__(TYX * FastPlan<N>::TPL)
             raise_status(const_cast<Scalars*>(a.sc), COMBO_E_TIMEOUT);
             const int s = it & 1;
             mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1));
-            if ((int)blockIdx.x + (it + 1) * (int)gridDim.x < ntiles)
-                mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            if (tn < ntiles) mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
         }
         bulk_wait_all();
     }
@@ -341,14 +359,14 @@ template <int N> static void zpass_tma_launch(const ZArgs<float>& a, const void*
             per = 1;
         grid_per_sm = per;
     }
-    const int ntiles = ((a.g.nh + TX - 1) / TX) * a.g.n2 * 3;
+    const int ntiles = ((a.g.nh + TX - 1) / TX) * a.g.n2 * 3 * a.g.nprob;
     const int grid = std::min(ntiles, grid_per_sm * nsm);
     k_zpass_tma<N><<<grid, threads, sm, st>>>(*reinterpret_cast<const CUtensorMap*>(map), a);
 }
 
 void launch_zpass_tma(const ZArgs<float>& a, const void* map, cudaStream_t st)
 {
-    switch (a.g.n3) {
+    switch (a.g.n3p) {
         case 64: zpass_tma_launch<64>(a, map, st); break;
         case 128: zpass_tma_launch<128>(a, map, st); break;
         default: zpass_tma_launch<256>(a, map, st); break;
