@@ -197,6 +197,26 @@ int64_t combo_solve_footprint(const combo_problem* p, const combo_options* o);
 int combo_solve(combo_ctx* ctx, const combo_problem* p, const combo_options* o, combo_result* r);
 
 /*
+ * Batched solve (no counterpart in the paper, which solves one RVE at a time;
+ * each problem is the problem of Sec. 2): n_problems independent problems
+ * on the same grid n and cell size l, each with its own phase field, boxels,
+ * materials, Fbar and number of load steps, solved together with the
+ * Newton-CG solver (Sec. 3).  The problems are stacked along z into one grid,
+ * so every kernel launch works on the pencils of all of them (the x-passes
+ * give each problem its own blocks and reductions, the z-passes transform
+ * each problem's segment); CG scalars, stopping tests, step halving and
+ * results are per problem, and a problem that has converged is masked out
+ * of the launches until the others finish the load step.
+ *   problems[n_problems], results[n_problems]: as for combo_solve (each
+ *   result's mem, pointers and sizes refer to its own problem).
+ *   Errors: COMBO_E_INVALID_ARG for unequal grids or the fixed-point solver
+ *   with n_problems > 1; a failing problem fails the batch and the message
+ *   names it.  n_problems == 1 is combo_solve.
+ */
+int combo_solve_batch(combo_ctx* ctx, int32_t n_problems, const combo_problem* problems, const combo_options* o,
+                      combo_result* results);
+
+/*
  * Incremental interface (used for timing and by the serving loop):
  *   begin    validates and copies the problem to the device, allocates the
  *            solve's fields; nothing runs yet.

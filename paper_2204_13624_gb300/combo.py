@@ -57,7 +57,7 @@ class ResultS(C.Structure):
 
 EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_options_default",
            "combo_solve_footprint", "combo_solve", "combo_solve_begin", "combo_solve_advance", "combo_solve_finish",
-           "combo_solve_end", "combo_solve_profile", "combo_solve_profile_read", "combo_apply_G",
+           "combo_solve_end", "combo_solve_batch", "combo_solve_profile", "combo_solve_profile_read", "combo_apply_G",
            "combo_constitutive", "combo_apply_G_noalloc", "combo_server_create", "combo_server_destroy",
            "combo_submit", "combo_poll", "combo_wait", "combo_cancel", "combo_server_stats"]
 
@@ -82,6 +82,8 @@ def load(path: str = LIB_PATH):
     L.combo_solve_footprint.restype = i64
     L.combo_solve.argtypes = [vp, vp, vp, vp]
     L.combo_solve.restype = C.c_int
+    L.combo_solve_batch.argtypes = [vp, i32, vp, vp, vp]
+    L.combo_solve_batch.restype = C.c_int
     L.combo_solve_begin.argtypes = [vp, vp, vp, C.POINTER(vp)]
     L.combo_solve_begin.restype = C.c_int
     L.combo_solve_advance.argtypes = [vp, i64]
@@ -253,6 +255,20 @@ def solve(prob: dict, ctx: Context | None = None, fields: bool = True, device_re
     out, r = _result_buffers(pb, fields, device_results)
     _check(load().combo_solve(ctx.h, C.byref(pb.s), C.byref(o), C.byref(r)))
     return _collect(out, r, pb.n_boxels)
+
+
+def solve_batch(probs: list, ctx: Context | None = None, fields: bool = True, device_results: bool = False, **opts):
+    """combo_solve_batch: independent problems on one grid solved together
+    (stacked, one launch per pass for all of them); a list of results as
+    from solve()."""
+    ctx = ctx or default_context()
+    pbs = [Problem(p) for p in probs]
+    o = options(**opts)
+    bufs = [_result_buffers(pb, fields, device_results) for pb in pbs]
+    parr = (ProblemS * len(pbs))(*[pb.s for pb in pbs])
+    rarr = (ResultS * len(pbs))(*[r for _, r in bufs])
+    _check(load().combo_solve_batch(ctx.h, len(pbs), C.byref(parr), C.byref(o), C.byref(rarr)))
+    return [_collect(out, rarr[i], pbs[i].n_boxels) for i, (out, _) in enumerate(bufs)]
 
 
 class Solve:

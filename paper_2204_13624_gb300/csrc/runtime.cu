@@ -726,6 +726,8 @@ struct SolveBase {
     virtual ~SolveBase() {}
     virtual int advance(int64_t max_ops) = 0;
     virtual int finish(combo_result* r) = 0;
+    virtual int run_batch() = 0;
+    virtual int batch_results(combo_result* rs) = 0;
     virtual Profiler& profiler() = 0;
     virtual void request_cancel() = 0;
 };
@@ -756,8 +758,17 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     void* d_spec = nullptr;
     Tc *d_tc = nullptr, *d_x = nullptr, *d_r = nullptr, *d_p = nullptr;
     double* d_part = nullptr;
-    Scalars* d_sc = nullptr;
+    Scalars* d_sc = nullptr;  // [B]
     double mu0 = 0.0;
+    // stacked problems (a batch of B equal grids along z; B = 1 for one solve)
+    int B = 1;
+    int64_t Vp = 0;                    // voxels of one problem
+    std::vector<HostProblem> hps;      // the problems of a batch (empty for one solve)
+    std::vector<int64_t> boff;         // boxels of problem b: [boff[b], boff[b + 1])
+    double* d_mat = nullptr;           // [B][4] materials (batch only)
+    double* d_dF = nullptr;            // [B][9] load-step increments (batch only)
+    double* d_dv = nullptr;            // [B] F-update factors (batch only)
+    int32_t* d_bprob = nullptr;        // problem of each boxel (batch only)
     Profiler prof;
     static constexpr int kCgChunk = 8;
     cudaGraphExec_t cg_exec = nullptr;
@@ -795,6 +806,10 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         cudaFree(d_p);
         cudaFree(d_part);
         cudaFree(d_sc);
+        cudaFree(d_mat);
+        cudaFree(d_dF);
+        cudaFree(d_dv);
+        cudaFree(d_bprob);
         if (cg_exec) cudaGraphExecDestroy(cg_exec);
         e64.release();
         ec.release();
@@ -804,12 +819,43 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
 
     int init(combo_ctx* c, HostProblem&& h, const combo_options& o)
     {
+        std::vector<HostProblem> one;
+        one.push_back(std::move(h));
+        return init(c, std::move(one), o);
+    }
+
+    // B >= 1 problems of equal grid n and cell size l: stacked along z; the
+    // phase fields, boxel lists and materials are concatenated per problem
+    int init(combo_ctx* c, std::vector<HostProblem>&& hs, const combo_options& o)
+    {
         ctx = c;
         st = c->stream;
         prof.st = st;
         opt = o;
-        hp = std::move(h);
-        g = make_dims(hp.n);
+        B = (int)hs.size();
+        if (B == 1) {
+            hp = std::move(hs[0]);
+        } else {
+            hps = std::move(hs);
+            hp.n[0] = hps[0].n[0], hp.n[1] = hps[0].n[1], hp.n[2] = hps[0].n[2];
+            for (int j = 0; j < 3; j++) hp.l[j] = hps[0].l[j];
+            for (int i = 0; i < 2; i++) hp.mu[i] = hps[0].mu[i], hp.lam[i] = hps[0].lam[i];
+            std::memcpy(hp.Fbar, hps[0].Fbar, sizeof hp.Fbar);
+            hp.n_steps = hps[0].n_steps;
+            Vp = (int64_t)hp.n[0] * hp.n[1] * hp.n[2];
+            hp.phase.resize((size_t)B * Vp);
+            boff.assign(B + 1, 0);
+            for (int b = 0; b < B; b++) {
+                std::memcpy(hp.phase.data() + (size_t)b * Vp, hps[b].phase.data(), Vp);
+                boff[b + 1] = boff[b] + (int64_t)hps[b].bidx.size();
+                for (size_t k = 0; k < hps[b].bidx.size(); k++) hp.bidx.push_back((int32_t)(b * Vp + hps[b].bidx[k]));
+                hp.bN.insert(hp.bN.end(), hps[b].bN.begin(), hps[b].bN.end());
+                hp.bc.insert(hp.bc.end(), hps[b].bc.begin(), hps[b].bc.end());
+                std::vector<uint8_t>().swap(hps[b].phase);  // uploaded with the batch
+            }
+        }
+        g = make_dims(hp.n, B);
+        if (B == 1) Vp = g.V;
         nb = (int64_t)hp.bidx.size();
         const int64_t V = g.V;
         int rc;
@@ -822,8 +868,25 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         CK(cudaMemsetAsync(d_spec, 0, sizeof(double2) * 9 * g.Vs, st));
         const int nbuf = std::max(std::max(e64.xpartials(), e64.zblocks()), std::max(ec.xpartials(), ec.zblocks()));
         CK(cudaMalloc(&d_part, 8 * (size_t)nbuf));
-        CK(cudaMalloc(&d_sc, sizeof(Scalars)));
-        CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars), st));
+        CK(cudaMalloc(&d_sc, sizeof(Scalars) * B));
+        CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars) * B, st));
+        if (B > 1) {
+            std::vector<double> mat(4 * B);
+            std::vector<int32_t> bprob(std::max<int64_t>(nb, 1), 0);
+            for (int b = 0; b < B; b++) {
+                mat[4 * b + 0] = hps[b].mu[0];
+                mat[4 * b + 1] = hps[b].mu[1];
+                mat[4 * b + 2] = hps[b].lam[0];
+                mat[4 * b + 3] = hps[b].lam[1];
+                for (int64_t k = boff[b]; k < boff[b + 1]; k++) bprob[k] = b;
+            }
+            CK(cudaMalloc(&d_mat, 8 * mat.size()));
+            CK(cudaMalloc(&d_dF, 8 * 9 * (size_t)B));
+            CK(cudaMalloc(&d_dv, 8 * (size_t)B));
+            CK(cudaMalloc(&d_bprob, 4 * bprob.size()));
+            CK(cudaMemcpy(d_mat, mat.data(), 8 * mat.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(d_bprob, bprob.data(), 4 * bprob.size(), cudaMemcpyHostToDevice));
+        }
         const size_t nbs = std::max<int64_t>(nb, 1);
         CK(cudaMalloc(&d_bidx, 4 * nbs));
         CK(cudaMalloc(&d_bN, 24 * nbs));
@@ -899,6 +962,8 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         a.bP = d_bP;
         a.bA = tangent ? d_bA : nullptr;
         a.rank = d_rank;
+        a.bprob = d_bprob;
+        a.matp = d_mat;
         a.dfloat = std::is_same<Rt, df32>::value ? 1 : 0;
         a.F = d_F;
         a.mu[0] = hp.mu[0];
@@ -929,6 +994,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         xf.F = d_F;
         xf.bP = d_bP;
         xf.tc = (xi_mode == XI_RHS) ? d_tc : nullptr;
+        xf.matp = d_mat;
         xf.nb = nb;
         xf.sc = d_sc;
         prof.begin(K_XFWD_RESID);
@@ -936,8 +1002,8 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         prof.end();
         e64.yz(d_sc, guard, true, d_part, st, &prof, K_YFWD_64);
         prof.begin(K_FINALIZE);
-        k_fin_resid<<<1, 256, 0, st>>>(d_sc, d_part, e64.zblocks(), (double)g.V, opt.tol, opt.fixed_iterations,
-                                       opt.max_iter, xi_mode == XI_FIXEDPOINT ? 1 : 0);
+        k_fin_resid<<<B, 256, 0, st>>>(d_sc, d_part, e64.zblocks_p(), (double)Vp, opt.tol, opt.fixed_iterations,
+                                       opt.max_iter, xi_mode == XI_FIXEDPOINT ? 1 : 0, B > 1 ? 1 : 0);
         prof.end();
         auto xi = e64.template xi<Tc>();
         xi.mode = xi_mode;
@@ -952,7 +1018,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         prof.end();
         if (xi_mode == XI_RHS) {
             prof.begin(K_FINALIZE);
-            k_fin_rhs<<<1, 256, 0, st>>>(d_sc, d_part, e64.xblocks(), opt.cg_fixed_iterations, opt.cg_max_iter);
+            k_fin_rhs<<<B, 256, 0, st>>>(d_sc, d_part, e64.xblocks() / B, opt.cg_fixed_iterations, opt.cg_max_iter);
             prof.end();
         }
     }
@@ -972,6 +1038,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         xf.r = d_r;
         xf.p = d_p;
         xf.x = d_x;
+        xf.matp = d_mat;
         xf.bA = d_bA;
         xf.bvox = d_bvox;
         xf.lofs = d_lofs;
@@ -1181,6 +1248,225 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         }
     }
 
+    // ---- batch of B > 1 problems: Newton-CG in lockstep rounds.  Each round
+    // starts the next load step of every problem that has one; its Newton
+    // iterations evaluate the residual of the problems still iterating (the
+    // others are masked by outer_done), run CG on them until each meets its
+    // own stopping test (masked by cg_done), and update their F.
+    struct PState {
+        int step = 0, outer = 0, cg_total = 0;
+        bool active = false;
+        double Fprev[9];
+        std::vector<double> Pbar, resid;
+        std::vector<int32_t> iters, cg_iters;
+    };
+    std::vector<PState> ps;
+    std::vector<Scalars> hsc;
+
+    int read_all()
+    {
+        CK(cudaMemcpyAsync(hsc.data(), d_sc, sizeof(Scalars) * B, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        prof.collect();
+        return COMBO_OK;
+    }
+
+    int set_flag_of(int b, size_t offset, int32_t value)
+    {
+        CK(cudaMemcpyAsync((char*)(d_sc + b) + offset, &value, 4, cudaMemcpyHostToDevice, st));
+        return COMBO_OK;
+    }
+
+    int batch_status(const char* what)
+    {
+        for (int b = 0; b < B; b++)
+            if (hsc[b].status)
+                return error = fail(hsc[b].status, std::string(what) + " (problem " + std::to_string(b) + ")" +
+                                                       boxel_failure(hsc[b]));
+        return COMBO_OK;
+    }
+
+    int run_batch() override
+    {
+        CK(cudaSetDevice(ctx->device));
+        if (!newton()) return error = fail(COMBO_E_INVALID_ARG, "a batch runs the Newton-CG solver");
+        ps.assign(B, PState{});
+        hsc.resize(B);
+        for (int b = 0; b < B; b++) {
+            for (int c = 0; c < 9; c++) ps[b].Fprev[c] = (c == 0 || c == 4 || c == 8) ? 1.0 : 0.0;
+            const int S = hps[b].n_steps;
+            ps[b].Pbar.assign(9 * (size_t)S, 0.0);
+            ps[b].resid.assign(S, 0.0);
+            ps[b].iters.assign(S, 0);
+            ps[b].cg_iters.assign(S, 0);
+        }
+        std::vector<double> dF(9 * (size_t)B), dv(B);
+        int rc;
+        while (true) {
+            // next load step of every problem that has one
+            bool any = false;
+            for (int b = 0; b < B; b++) {
+                PState& q = ps[b];
+                q.active = q.step < hps[b].n_steps;
+                for (int c = 0; c < 9; c++) dF[9 * b + c] = 0.0;
+                if (q.active) {
+                    any = true;
+                    const double f = (double)(q.step + 1) / hps[b].n_steps;
+                    for (int c = 0; c < 9; c++) {
+                        const double I = (c == 0 || c == 4 || c == 8) ? 1.0 : 0.0;
+                        const double Fn = I + f * (hps[b].Fbar[c] - I);
+                        dF[9 * b + c] = Fn - q.Fprev[c];
+                        q.Fprev[c] = Fn;
+                    }
+                    q.outer = 0;
+                    q.cg_total = 0;
+                }
+                if ((rc = set_flag_of(b, offsetof(Scalars, outer_done), q.active ? 0 : 1))) return error = rc;
+                if ((rc = set_flag_of(b, offsetof(Scalars, outer_iter), 0))) return error = rc;
+            }
+            if (!any) break;
+            CK(cudaMemcpyAsync(d_dF, dF.data(), 8 * dF.size(), cudaMemcpyHostToDevice, st));
+            Mat9 zero{};
+            prof.begin(K_UPDATE);
+            k_add_uniform<<<grid_for(9 * g.V), 256, 0, st>>>(d_F, g.V, zero, d_dF, Vp);
+            prof.end();
+            CK(cudaGetLastError());
+            // Newton iterations of this round
+            while (true) {
+                if (cancel_requested) return error = fail(COMBO_E_CANCELLED, "solve cancelled");
+                boxels(true, 2);
+                resid_operator(XI_RHS, 2);
+                CK(cudaGetLastError());
+                if ((rc = read_all())) return error = rc;
+                if ((rc = batch_status("residual evaluation failed"))) return rc;
+                bool any_cg = false;
+                for (int b = 0; b < B; b++) {
+                    PState& q = ps[b];
+                    if (!q.active) continue;
+                    const Scalars& sb = hsc[b];
+                    const bool conv = (opt.fixed_iterations > 0) ? (q.outer >= opt.fixed_iterations) : (sb.eps <= opt.tol);
+                    if (conv) {
+                        for (int c = 0; c < 9; c++) q.Pbar[9 * q.step + c] = sb.Pbar[c];
+                        q.resid[q.step] = sb.eps;
+                        q.iters[q.step] = q.outer;
+                        q.cg_iters[q.step] = q.cg_total;
+                        q.step++;
+                        q.active = false;
+                        if ((rc = set_flag_of(b, offsetof(Scalars, outer_done), 1))) return error = rc;
+                        if ((rc = set_flag_of(b, offsetof(Scalars, cg_done), 1))) return error = rc;
+                    } else if (q.outer >= opt.max_iter) {
+                        return error = fail(COMBO_E_NOT_CONVERGED,
+                                            "Newton did not converge (problem " + std::to_string(b) + ")");
+                    } else {
+                        any_cg = true;
+                    }
+                }
+                if (!any_cg) break;
+                // CG on the problems still iterating, 8 iterations per host round trip
+                while (true) {
+                    if (prof.on || cg_chunks_run == 0) {
+                        for (int k = 0; k < kCgChunk; k++) cg_iteration();
+                    } else {
+                        if (!cg_exec && (rc = capture_cg_chunk())) return error = rc;
+                        CK(cudaGraphLaunch(cg_exec, st));
+                    }
+                    cg_chunks_run++;
+                    CK(cudaGetLastError());
+                    if ((rc = read_all())) return error = rc;
+                    if ((rc = batch_status("CG failed"))) return rc;
+                    bool all = true;
+                    for (int b = 0; b < B; b++) all = all && hsc[b].cg_done;
+                    if (all) break;
+                }
+                // F += x with per-problem step halving until every det F > 0
+                for (int b = 0; b < B; b++) {
+                    dv[b] = ps[b].active ? 1.0 : 0.0;
+                    if (ps[b].active) ps[b].cg_total += hsc[b].cg_iter;
+                }
+                bool ok = false;
+                for (int h = 0; h <= 10; h++) {
+                    for (int b = 0; b < B; b++)
+                        if ((rc = set_flag_of(b, offsetof(Scalars, admissible), 1))) return error = rc;
+                    CK(cudaMemcpyAsync(d_dv, dv.data(), 8 * B, cudaMemcpyHostToDevice, st));
+                    prof.begin(K_UPDATE);
+                    k_update_F<Tc><<<grid_for(g.V), 256, 0, st>>>(d_F, d_x, d_p, 0.0, g.V, d_sc, d_dv, Vp);
+                    prof.end();
+                    if ((rc = read_all())) return error = rc;
+                    bool bad = false;
+                    for (int b = 0; b < B; b++) {
+                        if (dv[b] != 0.0 && !hsc[b].admissible) {
+                            dv[b] = -std::ldexp(1.0, -(h + 1));  // F_old + 2^-(h+1) x
+                            bad = true;
+                        } else {
+                            dv[b] = 0.0;
+                        }
+                    }
+                    if (!bad) {
+                        ok = true;
+                        break;
+                    }
+                }
+                if (!ok) return error = fail(COMBO_E_INADMISSIBLE, "det F <= 0 after 10 step halvings");
+                for (int b = 0; b < B; b++)
+                    if (ps[b].active) ps[b].outer++;
+            }
+        }
+        int64_t ops = 0;
+        for (int b = 0; b < B; b++) ops += (int64_t)hsc[b].n_operator;
+        ops_done = ops;
+        state = ST_DONE;
+        return COMBO_OK;
+    }
+
+    // per-problem results of a finished batch (fields sliced out of the stacked grid)
+    int batch_results(combo_result* rs) override
+    {
+        CK(cudaSetDevice(ctx->device));
+        double* P = nullptr;
+        bool needP = false;
+        for (int b = 0; b < B; b++) needP = needP || rs[b].P_out;
+        if (needP) {
+            CK(cudaMalloc(&P, 8 * 9 * (size_t)g.V));
+            Mat9 m{};
+            k_eval_P<<<grid_for(g.V), 256, 0, st>>>(d_F, d_phase, d_v2b, d_bP, m, P, g.V, d_sc, d_mat, Vp);
+            CK(cudaGetLastError());
+        }
+        int rc = COMBO_OK;
+        for (int b = 0; b < B && !rc; b++) {
+            combo_result* r = rs + b;
+            if (!r->Pbar) {
+                rc = fail(COMBO_E_INVALID_ARG, "result needs Pbar");
+                break;
+            }
+            const bool dev = (r->mem == COMBO_MEM_DEVICE);
+            const cudaMemcpyKind h2x = dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+            const cudaMemcpyKind d2x = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+            const PState& q = ps[b];
+            CK(cudaMemcpy(r->Pbar, q.Pbar.data(), 8 * q.Pbar.size(), h2x));
+            if (r->iters) CK(cudaMemcpy(r->iters, q.iters.data(), 4 * q.iters.size(), h2x));
+            if (r->cg_iters) CK(cudaMemcpy(r->cg_iters, q.cg_iters.data(), 4 * q.cg_iters.size(), h2x));
+            if (r->resid) CK(cudaMemcpy(r->resid, q.resid.data(), 8 * q.resid.size(), h2x));
+            for (int c = 0; c < 9; c++) {
+                if (r->F_out)
+                    CK(cudaMemcpyAsync(r->F_out + (size_t)c * Vp, d_F + (size_t)c * g.V + (size_t)b * Vp, 8 * Vp, d2x,
+                                       st));
+                if (r->P_out)
+                    CK(cudaMemcpyAsync(r->P_out + (size_t)c * Vp, P + (size_t)c * g.V + (size_t)b * Vp, 8 * Vp, d2x, st));
+            }
+            const int64_t nbb = boff[b + 1] - boff[b];
+            if (r->a_out && nbb > 0) CK(cudaMemcpyAsync(r->a_out, d_ba + 3 * boff[b], 24 * nbb, d2x, st));
+            CK(cudaStreamSynchronize(st));
+            r->steps_done = q.step;
+            r->nr_iters = (int64_t)hsc[b].nr_iters;
+            r->n_backproj = (int64_t)hsc[b].n_backproj;
+            r->n_laminate_evals = (int64_t)hsc[b].n_lam;
+            r->n_operator = (int64_t)hsc[b].n_operator;
+            r->n_operator_fp64 = (int64_t)hsc[b].n_operator64;
+        }
+        cudaFree(P);
+        return rc;
+    }
+
     Profiler& profiler() override { return prof; }
     void request_cancel() override { cancel_requested = 1; }
 
@@ -1235,7 +1521,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
 
 // A solve of the requested precision form: plain FP64; FP32 Krylov with FP64
 // residual transforms; FP32 Krylov with double-float residual transforms.
-static int make_solve(combo_ctx* ctx, HostProblem&& h, const combo_options& o, SolveBase** out)
+template <class H> static int make_solve(combo_ctx* ctx, H&& h, const combo_options& o, SolveBase** out)
 {
     int rc;
     if (o.precision == COMBO_FP64) {
@@ -1356,6 +1642,57 @@ extern "C" int combo_solve(combo_ctx* ctx, const combo_problem* p, const combo_o
         return rc;
     }
     return rc2;
+}
+
+extern "C" int combo_solve_batch(combo_ctx* ctx, int32_t n_problems, const combo_problem* problems,
+                                 const combo_options* o_in, combo_result* results)
+{
+    if (!ctx || !problems || !results || n_problems <= 0) return fail(COMBO_E_INVALID_ARG, "bad batch arguments");
+    combo_options o;
+    if (o_in)
+        o = *o_in;
+    else
+        combo_options_default(&o);
+    int rc = check_options(o);
+    if (rc) return rc;
+    if (n_problems > 1 && o.solver != COMBO_NEWTON_CG)
+        return fail(COMBO_E_INVALID_ARG, "a batch runs the Newton-CG solver");
+    CK(cudaSetDevice(ctx->device));
+    std::vector<HostProblem> hs(n_problems);
+    for (int b = 0; b < n_problems; b++) {
+        if ((rc = load_problem(problems + b, &o, hs[b]))) return rc;
+        for (int j = 0; j < 3; j++)
+            if (hs[b].n[j] != hs[0].n[j] || hs[b].l[j] != hs[0].l[j])
+                return fail(COMBO_E_INVALID_ARG, "the problems of a batch need equal grids n and cell sizes l");
+    }
+    const int64_t V = (int64_t)hs[0].n[0] * hs[0].n[1] * hs[0].n[2];
+    if (V * n_problems >= (int64_t)1 << 31) return fail(COMBO_E_INVALID_ARG, "batch too large");
+    if (n_problems == 1) {
+        // a batch of one is a plain solve
+        SolveBase* impl = nullptr;
+        rc = make_solve(ctx, std::move(hs[0]), o, &impl);
+        if (!rc) rc = impl->advance(0);
+        const std::string msg = g_err;
+        const int rc2 = impl ? impl->finish(results) : rc;
+        delete impl;
+        if (rc) {
+            g_err = msg;
+            return rc;
+        }
+        return rc2;
+    }
+    SolveBase* impl = nullptr;
+    rc = make_solve(ctx, std::move(hs), o, &impl);
+    if (!rc) rc = impl->run_batch();
+    const std::string msg = g_err;
+    if (!rc) rc = impl->batch_results(results);
+    delete impl;
+    if (rc) {
+        cudaGetLastError();
+        g_err = msg.empty() ? g_err : msg;
+        return (rc == COMBO_E_CUDA && g_err.find("memory") != std::string::npos) ? COMBO_E_OOM : rc;
+    }
+    return COMBO_OK;
 }
 
 // ------------------------------------------------------------------ C ABI: unit entry points

@@ -95,10 +95,9 @@ __global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
     const int tpp = nxt * g.n2 * 3;  // tiles per problem
     const int ntiles = tpp * g.nprob;
     // a tile of a finished problem is skipped (guard 1: CG done, 2: outer done)
-    auto active = [&](int t) {
-        const Scalars* q = a.sc + t / tpp;
-        return !((a.guard == 1 && q->cg_done) || (a.guard == 2 && q->outer_done));
-    };
+    auto done_of = [&](const Scalars* q) { return (a.guard == 1 && q->cg_done) || (a.guard == 2 && q->outer_done); };
+    const bool done0 = done_of(a.sc);
+    auto active = [&](int t) { return g.nprob == 1 ? !done0 : !done_of(a.sc + t / tpp); };
     auto next_tile = [&](int t) {
         while (t < ntiles && !active(t)) t += gridDim.x;
         return t;
@@ -242,11 +241,9 @@ __global__ void __launch_bounds__(TYX * FastPlan<N>::TPL)
     const int nxt = (g.nh + TX - 1) / TX;
     const int ntiles = nxt * g.n3 * 9;
     // a tile of a finished problem (the problem of its z plane) is skipped
-    auto active = [&](int t) {
-        const int z = (t / nxt) % g.n3;
-        const Scalars* q = a.sc + z / g.n3p;
-        return !((a.guard == 1 && q->cg_done) || (a.guard == 2 && q->outer_done));
-    };
+    auto done_of = [&](const Scalars* q) { return (a.guard == 1 && q->cg_done) || (a.guard == 2 && q->outer_done); };
+    const bool done0 = done_of(a.sc);
+    auto active = [&](int t) { return g.nprob == 1 ? !done0 : !done_of(a.sc + ((t / nxt) % g.n3) / g.n3p); };
     auto next_tile = [&](int t) {
         while (t < ntiles && !active(t)) t += gridDim.x;
         return t;
