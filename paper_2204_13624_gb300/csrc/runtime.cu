@@ -420,7 +420,7 @@ template <typename T> struct Engine {
             z.sa[j] = tab.sa[j];
             z.sb[j] = tab.sb[j];
         }
-        z.scale = (T)(2.0 / (double)g.V);
+        z.scale = (T)(2.0 * g.nprob / (double)g.V);  // 2 / (voxels of one problem)
         z.want_norm = want_norm ? 1 : 0;
         z.partial = partial;
         z.sc = sc;
