@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--serve-full", action="store_true",
                     help="serving stream of sides 64..256 and 1..10 load steps (takes minutes)")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel table here")
@@ -314,6 +315,9 @@ def main():
                                     max_steps=10)
         else:
             serving = serving_bench(combo, ctx)
+    batch = None
+    if not args.no_batch and rank == 0:
+        batch = batch_bench(combo, ctx)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -335,7 +339,7 @@ def main():
                            "operator_applications": int(ops), "solve_finished_in_timed_region": bool(done),
                            "l2": "inputs larger than L2 (each 9-field >= 604 MB)",
                            "parallelism": f"replicas x{world}"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "batch": batch, "gpu_launches": launches,
                 "clocks": clocks, "kernels": table}
         if args.profile_json:
             json.dump(line, open(args.profile_json, "w"), indent=1)
@@ -440,6 +444,43 @@ def serving_bench(combo, ctx, count=12, sides=(48, 64, 72, 96), max_steps=4, slo
         out[f"Pbar_rel_err_{form}_vs_fp64_max"] = max(errs)
         out[f"speedup_{form}_vs_fp64"] = out[form]["saturated_solves_per_s"] / out["fp64"]["saturated_solves_per_s"]
     return out
+
+
+def batch_bench(combo, ctx, prec=None):
+    """64 independent random-ball solves, sides from {32, 48, 64, 96, 128}, 5
+    load steps each: batched (one combo_solve_batch per grid size: all solves
+    of a size stacked, every launch working on all of them) against the same
+    solves one after another; wall clock around all of them."""
+    import torch
+
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    prec = combo.FP32_REFINED_DF if prec is None else prec
+    probs = ms.batch_mix()
+    groups = {}
+    for i, p in enumerate(probs):
+        groups.setdefault(tuple(p["n"]), []).append(i)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res_b = [None] * len(probs)
+    for n, idx in sorted(groups.items()):
+        out = combo.solve_batch([probs[i] for i in idx], ctx=ctx, fields=False, precision=prec, tol=1e-8)
+        for i, r in zip(idx, out):
+            res_b[i] = r
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res_s = [combo.solve(p, ctx=ctx, fields=False, precision=prec, tol=1e-8) for p in probs]
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    vit = sum(int(r["n_operator"]) * int(np.prod(p["n"])) for r, p in zip(res_b, probs))
+    err = max(float(np.max(np.abs(a["Pbar"] - b["Pbar"])) / np.max(np.abs(b["Pbar"]))) for a, b in zip(res_b, res_s))
+    return {"solves": len(probs), "sides": sorted({int(p["n"][0]) for p in probs}), "load_steps": 5,
+            "groups": {f"{k[0]}^3": len(v) for k, v in sorted(groups.items())},
+            "batched_seconds": tb, "batched_solves_per_s": len(probs) / tb, "batched_voxel_iterations_per_s": vit / tb,
+            "one_by_one_seconds": ts, "one_by_one_solves_per_s": len(probs) / ts,
+            "speedup_batched": ts / tb, "Pbar_rel_diff_batched_vs_one_by_one_max": err,
+            "precision": "FP32 Krylov + double-float residual"}
 
 
 def run_reference(args, rank, world):

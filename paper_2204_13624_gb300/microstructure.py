@@ -386,21 +386,25 @@ def fibres_512(n=512, n_steps=15, seed=SEED_BASE + 2, vf=0.3):
     return random_fibres((n, n, n), r, vf, seed, 50.0, Fb, n_steps, gap_vox=2.0)
 
 
-def batch_mix(count=64, seed=SEED_BASE + 3, sides=(32, 48, 64, 96, 128), n_steps=5):
+def batch_mix(count=64, seed=SEED_BASE + 3, sides=(32, 48, 64, 96, 128), n_steps=5, gap_vox=1.75):
     """``count`` independent random-sphere solves: side uniform from ``sides``,
     vf ~ U(0.1, 0.35), radius max(4, side/10) voxels, contrast 10, Fbar =
-    I + diag(U(-.08,.08)^3) + off-diagonal U(-.10,.10)."""
+    I + diag(U(-.08,.08)^3) + off-diagonal U(-.10,.10).  The drawn vf is
+    capped where random sequential addition with the gap that keeps every
+    voxel cut by at most one ball would jam: (r + gap/2)^3 / r^3 * vf <= 0.3."""
     rng = np.random.default_rng(seed)
     out = []
     for s in range(count):
         side = int(rng.choice(sides))
         vf = float(rng.uniform(0.1, 0.35))
+        r = max(4.0, side / 10.0)
+        vf = min(vf, 0.3 * (r / (r + 0.5 * gap_vox)) ** 3)
         Fb = np.eye(3) + np.diag(rng.uniform(-0.08, 0.08, 3))
         off = rng.uniform(-0.10, 0.10, (3, 3))
         np.fill_diagonal(off, 0.0)
         Fb = Fb + off
-        out.append(random_spheres((side,) * 3, max(4.0, side / 10.0), vf, int(rng.integers(1 << 31)), 10.0, Fb,
-                                  n_steps))
+        out.append(random_spheres((side,) * 3, r, vf, int(rng.integers(1 << 31)), 10.0, Fb, n_steps,
+                                  gap_vox=gap_vox))
     return out
 
 
