@@ -250,6 +250,14 @@ void combo_solve_end(combo_solve_state* s);
  *                        finishes; requests arriving while others run are
  *                        admitted as slots and memory free up, and the running
  *                        solves' kernels overlap on the device.
+ *   batching             with batch_max >= 2, a slot that admits a Newton-CG
+ *                        request of at most batch_max_voxels voxels (<= 0:
+ *                        96^3) also admits the queued requests with the same
+ *                        grid, cell size and options, up to batch_max and the
+ *                        memory left, and solves them together as one
+ *                        combo_solve_batch (each request's result is the
+ *                        result of its own solve); cancelling one request of a
+ *                        running batch discards its result when the batch ends.
  *   combo_poll           COMBO_PENDING while running, else writes the result
  *                        (host pointers; the mem field is ignored) and
  *                        releases the ticket, returning the solve's status.
@@ -267,11 +275,14 @@ typedef struct {
     int32_t max_slots;
     int64_t hbm_budget_bytes;
     int32_t keep_fields;
+    int32_t batch_max;         /* <= 1: no batching; else up to this many requests per batch */
+    int64_t batch_max_voxels;  /* requests of at most this many voxels may be batched */
 } combo_server_opts;
 typedef struct {
     int64_t submitted, completed, failed, queued, running, peak_running;
     int64_t in_use_bytes, budget_bytes;
     double p50_seconds, p99_seconds, mean_seconds;
+    int64_t batches, batched_requests; /* batches of >= 2 requests run, and their requests */
 } combo_serving_stats;
 int combo_server_create(combo_ctx* ctx, const combo_server_opts* opts, combo_server** out);
 void combo_server_destroy(combo_server* s);

@@ -378,14 +378,15 @@ def apply_G_noalloc(X, Y, n, l=(1.0, 1.0, 1.0), kspace=ROTATED, device=0, stream
 
 
 class ServerOpts(C.Structure):
-    _fields_ = [("max_slots", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("keep_fields", C.c_int32)]
+    _fields_ = [("max_slots", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("keep_fields", C.c_int32),
+                ("batch_max", C.c_int32), ("batch_max_voxels", C.c_int64)]
 
 
 class ServingStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("queued", C.c_int64),
                 ("running", C.c_int64), ("peak_running", C.c_int64), ("in_use_bytes", C.c_int64),
                 ("budget_bytes", C.c_int64), ("p50_seconds", C.c_double), ("p99_seconds", C.c_double),
-                ("mean_seconds", C.c_double)]
+                ("mean_seconds", C.c_double), ("batches", C.c_int64), ("batched_requests", C.c_int64)]
 
 
 def _server_lib():
@@ -415,10 +416,10 @@ class Server:
     worker slots on their own streams, admission bounded by device memory."""
 
     def __init__(self, ctx: Context | None = None, max_slots: int = 4, hbm_budget_bytes: int = 0,
-                 keep_fields: bool = False):
+                 keep_fields: bool = False, batch_max: int = 8, batch_max_voxels: int = 0):
         L = _server_lib()
         self.ctx = ctx or default_context()
-        o = ServerOpts(max_slots, hbm_budget_bytes, 1 if keep_fields else 0)
+        o = ServerOpts(max_slots, hbm_budget_bytes, 1 if keep_fields else 0, batch_max, batch_max_voxels)
         h = C.c_void_p()
         _check(L.combo_server_create(self.ctx.h, C.byref(o), C.byref(h)))
         self.h = h

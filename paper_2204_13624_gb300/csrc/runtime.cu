@@ -1869,7 +1869,7 @@ int64_t footprint_of(const HostProblem& h, const combo_options& o)
     const int64_t nb = std::max<int64_t>((int64_t)h.bidx.size(), 1);
     const int64_t tc = (o.precision == COMBO_FP64) ? 8 : 4;
     int64_t b = V * (1 + 4 + 72) + 16 * 9 * g.Vs + nb * (4 + 24 + 8 + 24 + 72) + (1 << 20);
-    if (o.solver == COMBO_NEWTON_CG) b += tc * (81 * nb + 37 * V);
+    if (o.solver == COMBO_NEWTON_CG) b += tc * (45 * nb + 37 * V) + 8 * nb + 4 * ((int64_t)g.n2 * g.n3 + 1);
     return b;
 }
 
@@ -1887,6 +1887,7 @@ struct ServeReq {
     double t_submit = 0, t_start = 0, t_done = 0;
     SolveBase* live = nullptr;
     bool cancel = false;
+    bool batched = false;  // running in a batch with other requests
 };
 
 }  // namespace
@@ -1896,6 +1897,9 @@ struct combo_server {
     int slots = 1;
     int64_t budget = 0;
     int keep_fields = 0;
+    int batch_max = 1;
+    int64_t batch_max_voxels = 0;
+    int64_t batches = 0, batched_requests = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<ServeReq*> queue;
@@ -1919,6 +1923,70 @@ static ServeReq* pick_request(combo_server* S)
     return nullptr;
 }
 
+static bool batchable(const combo_server* S, const ServeReq* r)
+{
+    const int64_t V = (int64_t)r->hp.n[0] * r->hp.n[1] * r->hp.n[2];
+    return S->batch_max >= 2 && r->opt.solver == COMBO_NEWTON_CG && !r->cancel && V <= S->batch_max_voxels;
+}
+
+// a request that may share a batch with `first`: same grid, cell size and options
+static bool compatible(const ServeReq* first, const ServeReq* r)
+{
+    for (int j = 0; j < 3; j++)
+        if (r->hp.n[j] != first->hp.n[j] || r->hp.l[j] != first->hp.l[j]) return false;
+    return std::memcmp(&r->opt, &first->opt, sizeof(combo_options)) == 0;
+}
+
+// the admitted request plus the queued requests it can be batched with
+// (called with S->mu held; r already left the queue, its footprint is not yet counted)
+static void gather_batch(combo_server* S, ServeReq* r, std::vector<ServeReq*>& batch)
+{
+    batch.assign(1, r);
+    if (!batchable(S, r)) return;
+    int64_t mem = S->in_use + r->footprint;
+    for (auto it = S->queue.begin(); it != S->queue.end() && (int)batch.size() < S->batch_max;) {
+        ServeReq* q = *it;
+        if (batchable(S, q) && compatible(r, q) && mem + q->footprint <= S->budget) {
+            mem += q->footprint;
+            batch.push_back(q);
+            it = S->queue.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+// result buffers of a request and its combo_result pointing at them
+static combo_result request_buffers(ServeReq* r, int32_t n_steps, int64_t V, bool fields)
+{
+    r->Pbar.assign(9 * (size_t)n_steps, 0.0);
+    r->resid.assign(n_steps, 0.0);
+    r->iters.assign(n_steps, 0);
+    r->cg.assign(n_steps, 0);
+    combo_result res{};
+    res.Pbar = r->Pbar.data();
+    res.resid = r->resid.data();
+    res.iters = r->iters.data();
+    res.cg_iters = r->cg.data();
+    res.mem = COMBO_MEM_HOST;
+    if (fields) {
+        r->F.assign(9 * (size_t)V, 0.0);
+        r->P.assign(9 * (size_t)V, 0.0);
+        res.F_out = r->F.data();
+        res.P_out = r->P.data();
+    }
+    return res;
+}
+
+static void keep_result(ServeReq* r, const combo_result& res)
+{
+    r->res = res;
+    r->res.Pbar = nullptr;
+    r->res.F_out = r->res.P_out = nullptr;
+    r->res.resid = nullptr;
+    r->res.iters = r->res.cg_iters = nullptr;
+}
+
 static void run_request(ServeReq* r, combo_ctx* wctx, combo_server* S)
 {
     SolveBase* impl = nullptr;
@@ -1936,36 +2004,62 @@ static void run_request(ServeReq* r, combo_ctx* wctx, combo_server* S)
         rc = impl->advance(0);
     }
     const std::string msg = g_err;
-    r->Pbar.assign(9 * (size_t)n_steps, 0.0);
-    r->resid.assign(n_steps, 0.0);
-    r->iters.assign(n_steps, 0);
-    r->cg.assign(n_steps, 0);
-    combo_result res{};
-    res.Pbar = r->Pbar.data();
-    res.resid = r->resid.data();
-    res.iters = r->iters.data();
-    res.cg_iters = r->cg.data();
-    res.mem = COMBO_MEM_HOST;
-    if (S->keep_fields && !rc) {
-        r->F.assign(9 * (size_t)V, 0.0);
-        r->P.assign(9 * (size_t)V, 0.0);
-        res.F_out = r->F.data();
-        res.P_out = r->P.data();
-    }
+    combo_result res = request_buffers(r, n_steps, V, S->keep_fields && !rc);
     const int rc2 = inited ? impl->finish(&res) : rc;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         r->live = nullptr;
     }
     delete impl;
-    r->res = res;
-    r->res.Pbar = nullptr;
-    r->res.F_out = r->res.P_out = nullptr;
-    r->res.resid = nullptr;
-    r->res.iters = r->res.cg_iters = nullptr;
+    keep_result(r, res);
     r->rc = rc ? rc : (rc2 < 0 ? rc2 : 0);
     r->err = rc ? msg : g_err;
     if (rc == COMBO_E_CUDA && msg.find("memory") != std::string::npos) r->rc = COMBO_E_OOM;
+}
+
+// requests of one batch (>= 2) solved together by one combo_solve_batch
+static void run_batch_requests(std::vector<ServeReq*>& batch, combo_ctx* wctx, combo_server* S)
+{
+    const int B = (int)batch.size();
+    std::vector<HostProblem> hs(B);
+    std::vector<int32_t> steps(B);
+    const int64_t V = (int64_t)batch[0]->hp.n[0] * batch[0]->hp.n[1] * batch[0]->hp.n[2];
+    for (int b = 0; b < B; b++) {
+        steps[b] = batch[b]->hp.n_steps;
+        hs[b] = std::move(batch[b]->hp);
+    }
+    SolveBase* impl = nullptr;
+    int rc = make_solve(wctx, std::move(hs), batch[0]->opt, &impl);
+    if (!rc) {
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (ServeReq* r : batch) r->live = impl;
+        }
+        rc = impl->run_batch();
+    }
+    std::string msg = g_err;
+    std::vector<combo_result> res(B);
+    for (int b = 0; b < B; b++) res[b] = request_buffers(batch[b], steps[b], V, S->keep_fields && !rc);
+    if (!rc) {
+        rc = impl->batch_results(res.data());
+        if (rc) msg = g_err;
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (ServeReq* r : batch) r->live = nullptr;
+    }
+    delete impl;
+    for (int b = 0; b < B; b++) {
+        ServeReq* r = batch[b];
+        keep_result(r, res[b]);
+        r->rc = rc;
+        r->err = rc ? msg : "";
+        if (rc == COMBO_E_CUDA && msg.find("memory") != std::string::npos) r->rc = COMBO_E_OOM;
+        if (!rc && r->cancel) {
+            r->rc = COMBO_E_CANCELLED;
+            r->err = "request cancelled";
+        }
+    }
 }
 
 static void server_worker(combo_server* S)
@@ -1975,6 +2069,7 @@ static void server_worker(combo_server* S)
     wctx.device = S->device;
     wctx.own_stream = true;
     if (cudaStreamCreateWithFlags(&wctx.stream, cudaStreamNonBlocking) != cudaSuccess) wctx.stream = nullptr;
+    std::vector<ServeReq*> batch;
     for (;;) {
         ServeReq* r = nullptr;
         {
@@ -1985,24 +2080,37 @@ static void server_worker(combo_server* S)
                 return r != nullptr;
             });
             if (!r) break;  // stopping
-            r->st = ServeReq::RUNNING;
-            r->t_start = now_s();
-            S->in_use += r->footprint;
-            S->running++;
+            gather_batch(S, r, batch);
+            for (ServeReq* q : batch) {
+                q->st = ServeReq::RUNNING;
+                q->batched = batch.size() > 1;
+                q->t_start = now_s();
+                S->in_use += q->footprint;
+                S->running++;
+            }
             S->peak_running = std::max(S->peak_running, S->running);
+            if (batch.size() > 1) {
+                S->batches++;
+                S->batched_requests += (int64_t)batch.size();
+            }
         }
-        run_request(r, &wctx, S);
+        if (batch.size() > 1)
+            run_batch_requests(batch, &wctx, S);
+        else
+            run_request(r, &wctx, S);
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            r->st = ServeReq::DONE;
-            r->t_done = now_s();
-            S->in_use -= r->footprint;
-            S->running--;
-            if (r->rc == 0) {
-                S->completed++;
-                S->latency.push_back(r->t_done - r->t_submit);
-            } else {
-                S->failed++;
+            for (ServeReq* q : batch) {
+                q->st = ServeReq::DONE;
+                q->t_done = now_s();
+                S->in_use -= q->footprint;
+                S->running--;
+                if (q->rc == 0) {
+                    S->completed++;
+                    S->latency.push_back(q->t_done - q->t_submit);
+                } else {
+                    S->failed++;
+                }
             }
         }
         S->cv_done.notify_all();
@@ -2019,6 +2127,8 @@ extern "C" int combo_server_create(combo_ctx* ctx, const combo_server_opts* o, c
     S->device = ctx->device;
     S->slots = (o && o->max_slots > 0) ? o->max_slots : 4;
     S->keep_fields = o ? o->keep_fields : 0;
+    S->batch_max = (o && o->batch_max > 1) ? o->batch_max : 1;
+    S->batch_max_voxels = (o && o->batch_max_voxels > 0) ? o->batch_max_voxels : (int64_t)96 * 96 * 96;
     if (o && o->hbm_budget_bytes > 0) {
         S->budget = o->hbm_budget_bytes;
     } else {
@@ -2159,7 +2269,9 @@ extern "C" int combo_cancel(combo_server* S, int64_t ticket)
             S->failed++;
         } else if (r->st == ServeReq::RUNNING) {
             r->cancel = true;
-            if (r->live) r->live->request_cancel();
+            // a batch is not stopped for one of its requests: that request's
+            // result is discarded when the batch ends
+            if (r->live && !r->batched) r->live->request_cancel();
         }
     }
     S->cv_done.notify_all();
@@ -2179,6 +2291,8 @@ extern "C" int combo_server_stats(combo_server* S, combo_serving_stats* st)
     st->peak_running = S->peak_running;
     st->in_use_bytes = S->in_use;
     st->budget_bytes = S->budget;
+    st->batches = S->batches;
+    st->batched_requests = S->batched_requests;
     if (!S->latency.empty()) {
         std::vector<double> l = S->latency;
         std::sort(l.begin(), l.end());

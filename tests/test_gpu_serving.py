@@ -123,3 +123,34 @@ def test_requests_arriving_while_others_run_are_admitted(cb):
         srv.close()
     assert all(r["steps_done"] == p["n_steps"] for r, p in zip(res, probs))
     assert st["peak_running"] == 2 and st["completed"] == len(probs)
+
+
+def test_small_compatible_requests_are_batched(cb):
+    """Queued requests on the same small grid with the same options are solved
+    as one batch; each result equals the same solve run alone."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    rng = np.random.default_rng(11)
+    probs = []
+    for i in range(6):
+        Fb = np.eye(3) + np.diag(rng.uniform(-0.04, 0.04, 3))
+        probs.append(ms.random_spheres((16, 16, 16), 3.0, 0.06 + 0.02 * (i % 3), 500 + i, 5.0 + i, Fb, 1 + i % 2))
+    other = mix_problems()[1]  # another grid: never in the same batch
+    alone = [cb.solve(p, precision=0, tol=1e-8) for p in probs]
+    srv = cb.Server(max_slots=1, batch_max=4)
+    try:
+        blocker = srv.submit(ms.spheres_256(n=128, vf=0.1, n_steps=1), precision=1)  # keeps the slot busy
+        tickets = [srv.submit(p, precision=0, tol=1e-8) for p in probs]
+        t_other = srv.submit(other, precision=0, tol=1e-8)
+        srv.wait(blocker, timeout_ms=120000)
+        res = [srv.wait(t, timeout_ms=120000) for t in tickets]
+        r_other = srv.wait(t_other, timeout_ms=120000)
+        st = srv.stats()
+    finally:
+        srv.close()
+    assert st["batches"] >= 2 and st["batched_requests"] >= 4
+    assert st["completed"] == len(probs) + 2 and st["failed"] == 0
+    for a, r in zip(alone, res):
+        assert np.array_equal(a["iters"], r["iters"]) and np.array_equal(a["cg_iters"], r["cg_iters"])
+        assert np.max(np.abs(a["Pbar"] - r["Pbar"])) <= 1e-12 * np.max(np.abs(a["Pbar"]))
+    assert r_other["steps_done"] == other["n_steps"]
