@@ -293,6 +293,26 @@ int combo_cancel(combo_server* s, int64_t ticket);
 int combo_server_stats(combo_server* s, combo_serving_stats* st);
 
 /*
+ * Launch-shape autotuner (no counterpart in the paper).  The first Newton-CG
+ * solve (or batch) of a grid -- sides, batch size, Krylov precision -- in
+ * the process times the candidate launch shapes of each FP32 Krylov pass
+ * (pass 0 tangent x-forward: 128- or 256-thread blocks; 1 y-pass and 2
+ * z-pass: two TMA tile widths; 3 CG x-inverse: one or two x-lines per group)
+ * on the solve's own buffers before its first iteration, and every later
+ * solve of that grid uses the fastest.  Shapes change no result beyond
+ * floating-point summation order.
+ *   combo_autotune_enable(0) keeps the default shapes for grids not yet tuned.
+ *   combo_autotune_force(pass, cand) makes solves set up afterwards use
+ *     candidate cand (0, 1) of pass (0..3), or the tuned one (cand = -1).
+ *   combo_autotune_report writes one line per tuned grid (decisions and the
+ *     time of 3 launches of each candidate) into buf (NUL-terminated, at most
+ *     len bytes) and returns the full length.
+ */
+void combo_autotune_enable(int32_t enable);
+int combo_autotune_force(int32_t pass, int32_t cand);
+int64_t combo_autotune_report(char* buf, int64_t len);
+
+/*
  * Per-kernel timing of a solve (instrumentation, no effect on results).
  *   combo_solve_profile(s, 1) resets the counters and records a CUDA event
  *   pair around every kernel launch of the solve on its stream; 0 stops.

@@ -59,7 +59,8 @@ EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_o
            "combo_solve_footprint", "combo_solve", "combo_solve_begin", "combo_solve_advance", "combo_solve_finish",
            "combo_solve_end", "combo_solve_batch", "combo_solve_profile", "combo_solve_profile_read", "combo_apply_G",
            "combo_constitutive", "combo_apply_G_noalloc", "combo_server_create", "combo_server_destroy",
-           "combo_submit", "combo_poll", "combo_wait", "combo_cancel", "combo_server_stats"]
+           "combo_submit", "combo_poll", "combo_wait", "combo_cancel", "combo_server_stats",
+           "combo_autotune_enable", "combo_autotune_force", "combo_autotune_report"]
 
 _lib = None
 
@@ -101,6 +102,12 @@ def load(path: str = LIB_PATH):
     L.combo_constitutive.restype = C.c_int
     L.combo_apply_G_noalloc.argtypes = [i32, vp, vp, vp, i32, vp, vp, vp]
     L.combo_apply_G_noalloc.restype = C.c_int
+    L.combo_autotune_enable.argtypes = [i32]
+    L.combo_autotune_enable.restype = None
+    L.combo_autotune_force.argtypes = [i32, i32]
+    L.combo_autotune_force.restype = C.c_int
+    L.combo_autotune_report.argtypes = [C.c_char_p, i64]
+    L.combo_autotune_report.restype = i64
     _lib = L
     return L
 
@@ -255,6 +262,23 @@ def solve(prob: dict, ctx: Context | None = None, fields: bool = True, device_re
     out, r = _result_buffers(pb, fields, device_results)
     _check(load().combo_solve(ctx.h, C.byref(pb.s), C.byref(o), C.byref(r)))
     return _collect(out, r, pb.n_boxels)
+
+
+def autotune_enable(enable: bool = True):
+    load().combo_autotune_enable(1 if enable else 0)
+
+
+def autotune_force(pass_index: int, candidate: int):
+    """Force launch-shape candidate (0, 1) of pass 0..3 for solves set up
+    afterwards; -1 returns to the tuned choice."""
+    _check(load().combo_autotune_force(pass_index, candidate))
+
+
+def autotune_report() -> str:
+    n = load().combo_autotune_report(None, 0)
+    buf = C.create_string_buffer(int(n) + 1)
+    load().combo_autotune_report(buf, n + 1)
+    return buf.value.decode()
 
 
 def solve_batch(probs: list, ctx: Context | None = None, fields: bool = True, device_results: bool = False, **opts):

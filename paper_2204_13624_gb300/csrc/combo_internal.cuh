@@ -380,6 +380,7 @@ template <typename T, typename Tc> struct XfwdArgs {
     double* partial;     // [gridDim.x] pAp partials
     Scalars* sc;
     int fuse;            // last block turns the pAp partials into alpha
+    int cfg;             // launch-shape candidate (autotuner; 0 = default)
 };
 
 template <typename T, typename Tc> struct XinvArgs {
@@ -401,6 +402,7 @@ template <typename T, typename Tc> struct XinvArgs {
     int fuse;        // last block turns the (r, r) partials into beta / stop (XI_CG)
     double cg_tol;
     int cg_max, cg_fixed;
+    int cfg;         // launch-shape candidate (autotuner; 0 = default)
 };
 
 template <typename T> struct YArgs {
@@ -412,6 +414,7 @@ template <typename T> struct YArgs {
     const Scalars* sc;
     int guard;  // 0 none, 1 skip if cg_done, 2 skip if outer_done
     const void* tmap;  // CUtensorMap of spec for the TMA y-pass (FP32), or null
+    int cfg;           // launch-shape candidate (autotuner; 0 = default)
 };
 
 template <typename T> struct ZArgs {
@@ -428,6 +431,7 @@ template <typename T> struct ZArgs {
     Scalars* sc;
     int guard;
     const void* tmap;  // CUtensorMap of spec for the TMA z-pass (FP32), or null
+    int cfg;           // launch-shape candidate (autotuner; 0 = default)
 };
 
 template <typename T, typename Tc> void launch_xfwd(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st);
@@ -447,9 +451,11 @@ int zpass_tx(int n, size_t cxbytes);  // columns per z-pass block (sets the part
 bool stream_xpass_ok(const GridDims& g);
 // FP32 Krylov z- and y-passes with TMA tiles, n = 64, 128, 256 (zpass_tma.cu)
 bool zpass_tma_size(int n3);
-bool zpass_tma_encode(void* map, const GridDims& g, const void* spec);
+// (cand: tile-width candidate; the tensor map must be encoded for the
+// candidate the launch's cfg selects)
+bool zpass_tma_encode(void* map, const GridDims& g, const void* spec, int cand);
 void launch_zpass_tma(const ZArgs<float>& a, const void* map, cudaStream_t st);
-bool ypass_tma_encode(void* map, const GridDims& g, const void* spec);
+bool ypass_tma_encode(void* map, const GridDims& g, const void* spec, int cand);
 template <bool INV> void launch_ypass_tma(const YArgs<float>& a, const void* map, cudaStream_t st);
 void launch_xinv_stream(const XinvArgs<float, float>& a, cudaStream_t st);
 

@@ -9,6 +9,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <condition_variable>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <atomic>
 #include <cmath>
 #include <cstddef>
 #include <type_traits>
@@ -351,13 +356,20 @@ template <typename T> struct Engine {
     Plan pM, py, pz;
     int lines, txy, txz;
     cx<T>* spec = nullptr;  // not owned
-    CUtensorMap zmap, ymap;  // TMA views of spec for the FP32 z- and y-passes
-    bool zmap_ok = false, ymap_ok = false;
+    // TMA views of spec for the FP32 z- and y-passes, one per tile-width candidate
+    CUtensorMap zmap[2], ymap[2];
+    bool zmap_ok[2] = {false, false}, ymap_ok[2] = {false, false};
+    // launch-shape candidates chosen by the autotuner: x-forward, y, z, x-inverse
+    int cfg_xf = 0, cfg_y = 0, cfg_z = 0, cfg_xi = 0;
     void bind_spec(void* s)
     {
         spec = (cx<T>*)s;
-        zmap_ok = (sizeof(T) == 4) && zpass_tma_encode(&zmap, g, s);
-        ymap_ok = (sizeof(T) == 4) && ypass_tma_encode(&ymap, g, s);
+        for (int c = 0; c < 2; c++) {
+            zmap_ok[c] = (sizeof(T) == 4) && zpass_tma_encode(&zmap[c], g, s, c);
+            ymap_ok[c] = (sizeof(T) == 4) && ypass_tma_encode(&ymap[c], g, s, c);
+        }
+        if (!zmap_ok[cfg_z]) cfg_z = 0;
+        if (!ymap_ok[cfg_y]) cfg_y = 0;
     }
     int init(const GridDims& gd, const double l[3], int kspace)
     {
@@ -381,6 +393,7 @@ template <typename T> struct Engine {
         a.tw2 = tab.tw2;
         a.spec = spec;
         a.lines_per_block = lines;
+        a.cfg = cfg_xf;
         return a;
     }
     template <typename Tc> XinvArgs<T, Tc> xi() const
@@ -392,6 +405,7 @@ template <typename T> struct Engine {
         a.tw2 = tab.tw2;
         a.spec = spec;
         a.lines_per_block = lines;
+        a.cfg = cfg_xi;
         return a;
     }
     // y forward, z forward + projection + z inverse, y inverse
@@ -406,7 +420,8 @@ template <typename T> struct Engine {
         y.tx = txy;
         y.sc = sc;
         y.guard = guard;
-        y.tmap = ymap_ok ? &ymap : nullptr;
+        y.cfg = cfg_y;
+        y.tmap = ymap_ok[cfg_y] ? &ymap[cfg_y] : nullptr;
         if (pr) pr->begin(kbase);
         launch_ypass<T, false>(y, st);
         if (pr) pr->end();
@@ -425,7 +440,8 @@ template <typename T> struct Engine {
         z.partial = partial;
         z.sc = sc;
         z.guard = guard;
-        z.tmap = zmap_ok ? &zmap : nullptr;
+        z.cfg = cfg_z;
+        z.tmap = zmap_ok[cfg_z] ? &zmap[cfg_z] : nullptr;
         if (pr) pr->begin(kbase + 1);
         launch_zpass<T>(z, st);
         if (pr) pr->end();
@@ -721,6 +737,52 @@ static int check_options(combo_options& o)
     return COMBO_OK;
 }
 
+// ------------------------------------------------------------------ autotuner store
+struct TuneKey {
+    int word, n1, n2, n3p, nprob;
+    bool operator<(const TuneKey& o) const
+    {
+        return std::tie(word, n1, n2, n3p, nprob) < std::tie(o.word, o.n1, o.n2, o.n3p, o.nprob);
+    }
+};
+struct TuneRec {
+    int cfg[4] = {0, 0, 0, 0};  // x-forward, y, z, x-inverse
+    float ms[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};  // 3 launches of each candidate
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneRec> g_tune;
+static std::atomic<int> g_tune_enabled{1};
+static std::atomic<int> g_tune_force[4] = {{-1}, {-1}, {-1}, {-1}};  // per pass: forced candidate or -1
+
+static void tune_store(const TuneKey& k, const TuneRec& r)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[k] = r;
+}
+
+// the decisions for this grid into an engine; false if none yet
+template <typename T> static bool tune_lookup(const TuneKey& k, Engine<T>& e)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(k);
+    if (it == g_tune.end()) return false;
+    e.cfg_xf = it->second.cfg[0];
+    e.cfg_y = e.ymap_ok[it->second.cfg[1]] ? it->second.cfg[1] : 0;
+    e.cfg_z = e.zmap_ok[it->second.cfg[2]] ? it->second.cfg[2] : 0;
+    e.cfg_xi = it->second.cfg[3];
+    return true;
+}
+
+// forced candidates (tests of every launch shape) override the decisions
+template <typename T> static void tune_force(Engine<T>& e)
+{
+    int f;
+    if ((f = g_tune_force[0].load()) >= 0) e.cfg_xf = f;
+    if ((f = g_tune_force[1].load()) >= 0) e.cfg_y = e.ymap_ok[f] ? f : 0;
+    if ((f = g_tune_force[2].load()) >= 0) e.cfg_z = e.zmap_ok[f] ? f : 0;
+    if ((f = g_tune_force[3].load()) >= 0) e.cfg_xi = f;
+}
+
 // ------------------------------------------------------------------ solve state
 struct SolveBase {
     virtual ~SolveBase() {}
@@ -945,7 +1007,114 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         iters.assign(hp.n_steps, 0);
         cg_iters.assign(hp.n_steps, 0);
         CK(cudaStreamSynchronize(st));
+        if (newton()) {
+            if ((rc = autotune())) return rc;
+            tune_force(ec);
+        }
         return COMBO_OK;
+    }
+
+    // ---- launch-shape autotuner: the first solve of a grid (sides, batch
+    // size, Krylov precision) times every candidate shape of each Krylov pass
+    // on its own, still empty, buffers (3 launches each after one warm-up, no
+    // solver scalars touched) and keeps the fastest for every later solve
+    // of that grid in the process.
+    int autotune()
+    {
+        if constexpr (sizeof(Tc) != 4) {
+            return COMBO_OK;  // the candidates are shapes of the FP32 passes
+        } else {
+            const TuneKey key{sizeof(Tc), g.n1, g.n2, g.n3p, g.nprob};
+            if (tune_lookup(key, ec)) return COMBO_OK;
+            if (!g_tune_enabled.load()) return COMBO_OK;
+            CK(cudaMemsetAsync(d_r, 0, sizeof(Tc) * 9 * g.V, st));
+            CK(cudaMemsetAsync(d_p, 0, sizeof(Tc) * 9 * g.V, st));
+            CK(cudaMemsetAsync(d_x, 0, sizeof(Tc) * 9 * g.V, st));
+            CK(cudaMemsetAsync(d_tc, 0, sizeof(Tc) * 10 * g.V, st));
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            auto time_of = [&](auto&& launch) -> float {
+                launch();
+                cudaEventRecord(e0, st);
+                for (int k = 0; k < 3; k++) launch();
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                return (cudaGetLastError() == cudaSuccess) ? ms : 1e30f;
+            };
+            TuneRec rec;
+            // tangent x-forward
+            for (int c = 0; c < 2; c++) {
+                auto xf = ec.template xf<Tc>();
+                xf.mode = XF_TANGENT;
+                xf.phase = d_phase;
+                xf.vox2box = d_v2b;
+                for (int i = 0; i < 2; i++) xf.mu[i] = hp.mu[i], xf.lam[i] = hp.lam[i];
+                xf.tc = d_tc;
+                xf.r = d_r;
+                xf.p = d_p;
+                xf.x = d_x;
+                xf.matp = d_mat;
+                xf.bA = d_bA;
+                xf.bvox = d_bvox;
+                xf.lofs = d_lofs;
+                xf.nb = std::max<int64_t>(nb, 1);
+                xf.partial = d_part;
+                xf.sc = d_sc;
+                xf.fuse = 0;
+                xf.cfg = c;
+                rec.ms[0][c] = time_of([&] { launch_xfwd<Tc, Tc>(xf, 0, st); });
+            }
+            // y forward and z (+ projection): tile widths with a valid tensor map
+            for (int c = 0; c < 2; c++) {
+                YArgs<Tc> y{};
+                y.g = g;
+                y.plan = ec.py;
+                y.tw = ec.tab.twy;
+                y.spec = ec.spec;
+                y.tx = ec.txy;
+                y.sc = d_sc;
+                y.cfg = c;
+                y.tmap = ec.ymap_ok[c] ? &ec.ymap[c] : nullptr;
+                rec.ms[1][c] = (c == 0 || y.tmap) ? time_of([&] { launch_ypass<Tc, false>(y, st); }) : 1e30f;
+                ZArgs<Tc> z{};
+                z.g = g;
+                z.plan = ec.pz;
+                z.tw = ec.tab.twz;
+                z.spec = ec.spec;
+                z.tx = ec.txz;
+                for (int j = 0; j < 3; j++) z.sa[j] = ec.tab.sa[j], z.sb[j] = ec.tab.sb[j];
+                z.scale = (Tc)(2.0 * g.nprob / (double)g.V);
+                z.sc = d_sc;
+                z.cfg = c;
+                z.tmap = ec.zmap_ok[c] ? &ec.zmap[c] : nullptr;
+                rec.ms[2][c] = (c == 0 || z.tmap) ? time_of([&] { launch_zpass<Tc>(z, st); }) : 1e30f;
+            }
+            // CG x-inverse
+            for (int c = 0; c < 2; c++) {
+                auto xi = ec.template xi<Tc>();
+                xi.mode = XI_CG;
+                xi.x = d_x;
+                xi.r = d_r;
+                xi.p = d_p;
+                xi.partial = d_part;
+                xi.sc = d_sc;
+                xi.fuse = 0;
+                xi.cfg = c;
+                rec.ms[3][c] = time_of([&] { launch_xinv<Tc, Tc>(xi, 0, st); });
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars) * B, st));
+            CK(cudaStreamSynchronize(st));
+            CK(cudaGetLastError());
+            for (int k = 0; k < 4; k++) rec.cfg[k] = rec.ms[k][1] < rec.ms[k][0] ? 1 : 0;
+            tune_store(key, rec);
+            tune_lookup(key, ec);
+            return COMBO_OK;
+        }
     }
 
     // --- kernel sequences
@@ -1642,6 +1811,40 @@ extern "C" int combo_solve(combo_ctx* ctx, const combo_problem* p, const combo_o
         return rc;
     }
     return rc2;
+}
+
+extern "C" void combo_autotune_enable(int32_t enable) { g_tune_enabled.store(enable ? 1 : 0); }
+
+extern "C" int combo_autotune_force(int32_t pass, int32_t cand)
+{
+    if (pass < 0 || pass > 3 || cand < -1 || cand > 1) return fail(COMBO_E_INVALID_ARG, "bad pass or candidate");
+    g_tune_force[pass].store(cand);
+    return COMBO_OK;
+}
+
+extern "C" int64_t combo_autotune_report(char* buf, int64_t len)
+{
+    std::string out;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        static const char* pass[4] = {"x-forward", "y", "z", "x-inverse"};
+        for (const auto& kv : g_tune) {
+            char line[512];
+            int n = snprintf(line, sizeof line, "%dx%dx%d x%d FP%d:", kv.first.n1, kv.first.n2, kv.first.n3p,
+                             kv.first.nprob, kv.first.word * 8);
+            for (int k = 0; k < 4; k++)
+                n += snprintf(line + n, sizeof line - n, " %s=%d (%.3f/%.3f ms)", pass[k], kv.second.cfg[k],
+                              kv.second.ms[k][0] / 3.0, kv.second.ms[k][1] >= 1e29f ? -1.0 : kv.second.ms[k][1] / 3.0);
+            out += line;
+            out += "\n";
+        }
+    }
+    if (buf && len > 0) {
+        const size_t m = std::min<size_t>((size_t)len - 1, out.size());
+        std::memcpy(buf, out.data(), m);
+        buf[m] = 0;
+    }
+    return (int64_t)out.size();
 }
 
 extern "C" int combo_solve_batch(combo_ctx* ctx, int32_t n_problems, const combo_problem* problems,

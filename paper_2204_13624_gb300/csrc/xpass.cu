@@ -502,14 +502,17 @@ template <typename T, typename Tc, int MF> static void xfwd_launch(const XfwdArg
                 // FP32: small blocks of 128 threads whose FFT phase keeps most
                 // of them busy (9 lines x TPL threads per x-line), as many
                 // resident per SM as registers allow, one wave
+                // candidate 1 (autotuner): the engine's group of lines in 256 threads
                 constexpr int TPL = FastPlan<MF>::TPL;
                 int lb = a.lines_per_block;
-                while (lb > 1 && 9 * lb * TPL > 128) lb >>= 1;
-                const int threads = (9 * lb * TPL <= 128) ? 128 : 256;
+                if (a.cfg != 1)
+                    while (lb > 1 && 9 * lb * TPL > 128) lb >>= 1;
+                const int threads = (a.cfg != 1 && 9 * lb * TPL <= 128) ? 128 : 256;
                 XfwdArgs<T, Tc> b = a;
                 b.lines_per_block = lb;
                 const size_t smb = xpass_smem(a.g, lb, sizeof(cx<T>));
-                static int per_sm = 0;
+                static int per_sm_c[2] = {0, 0};
+                int& per_sm = per_sm_c[threads == 256 ? 1 : 0];
                 if (per_sm == 0 &&
                     (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xfwd<T, Tc, MF, true>, threads, smb) !=
                          cudaSuccess ||

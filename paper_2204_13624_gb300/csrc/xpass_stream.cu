@@ -198,17 +198,23 @@ template <int M, int LB> static void xinv_stream_launch(const XinvArgs<float, fl
     k_xinv_stream<M, LB><<<grid, threads, sm, st>>>(a);
 }
 
+// lines per group: candidate 0 (default) and candidate 1 (autotuner)
 void launch_xinv_stream(const XinvArgs<float, float>& a, cudaStream_t st)
 {
-    const int LB = stream_lines(a.g);
+    const bool even = (a.g.n2 * a.g.n3p) % 2 == 0;
     switch (a.g.M) {
         case 64:
-            if (LB == 2)
+            if (stream_lines(a.g) == 2 && a.cfg != 1)
                 xinv_stream_launch<64, 2>(a, st);
             else
                 xinv_stream_launch<64, 1>(a, st);
             break;
-        case 128: xinv_stream_launch<128, 1>(a, st); break;
+        case 128:
+            if (a.cfg == 1 && even)
+                xinv_stream_launch<128, 2>(a, st);
+            else
+                xinv_stream_launch<128, 1>(a, st);
+            break;
         default: xinv_stream_launch<256, 1>(a, st); break;
     }
 }

@@ -29,7 +29,14 @@ namespace combo {
 
 namespace {
 
-template <int N> __host__ __device__ constexpr int tma_tx() { return N == 256 ? 8 : 16; }
+// x-frequency widths of a z-pass tile: two candidates per size (the
+// autotuner picks one per grid; candidate 0 is the default)
+template <int N, int C> __host__ __device__ constexpr int tma_tx()
+{
+    return (N == 256 ? 8 : 16) >> C;
+}
+// x-frequency widths of a y-pass tile
+template <int C> __host__ __device__ constexpr int tma_tyx() { return 16 >> C; }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
@@ -53,10 +60,10 @@ bool zpass_tma_size(int n3) { return n3 == 64 || n3 == 128 || n3 == 256; }
 // Tensor map of a complex FP32 half spectrum [9][n3][n2][nhp] for the z-pass
 // tile box {TX, 1, n3, 3}.  False (map unusable) for other sizes or when the
 // driver entry point is missing.
-bool zpass_tma_encode(void* map, const GridDims& g, const void* spec)
+bool zpass_tma_encode(void* map, const GridDims& g, const void* spec, int cand)
 {
     if (!zpass_tma_size(g.n3p) || !spec) return false;
-    const int tx = g.n3p == 256 ? tma_tx<256>() : tma_tx<128>();
+    const int tx = (g.n3p == 256 ? 8 : 16) >> cand;
     if ((g.nhp * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(spec) & 15) != 0) return false;
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn) return false;
@@ -72,12 +79,11 @@ bool zpass_tma_encode(void* map, const GridDims& g, const void* spec)
     return r == CUDA_SUCCESS;
 }
 
-template <int N>
-__global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
+template <int N, int TX>
+__global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL)
     k_zpass_tma(const __grid_constant__ CUtensorMap tm, ZArgs<float> a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    constexpr int TX = tma_tx<N>();
     constexpr int TPL = FastPlan<N>::TPL;
     constexpr int GS = TX * TPL;  // threads per component group
     constexpr int TILE = 3 * N * TX;
@@ -201,12 +207,11 @@ __global__ void __launch_bounds__(3 * tma_tx<N>() * FastPlan<N>::TPL)
 }
 
 // ------------------------------------------------------------- y-pass
-// Tile: one component, one z plane, all n2 y rows, TYX consecutive x
-// frequencies: box {TYX, n2, 1, 1}; the transform runs in place in the tile.
-constexpr int TYX = 16;
-
-bool ypass_tma_encode(void* map, const GridDims& g, const void* spec)
+// Tile: one component, one z plane, all n2 y rows, TX consecutive x
+// frequencies: box {TX, n2, 1, 1}; the transform runs in place in the tile.
+bool ypass_tma_encode(void* map, const GridDims& g, const void* spec, int cand)
 {
+    const int TYX = 16 >> cand;
     if (!zpass_tma_size(g.n2) || !spec) return false;
     if ((g.nhp * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(spec) & 15) != 0) return false;
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
@@ -223,12 +228,11 @@ bool ypass_tma_encode(void* map, const GridDims& g, const void* spec)
     return r == CUDA_SUCCESS;
 }
 
-template <int N, bool INV>
-__global__ void __launch_bounds__(TYX * FastPlan<N>::TPL)
+template <int N, int TX, bool INV>
+__global__ void __launch_bounds__(TX * FastPlan<N>::TPL)
     k_ypass_tma(const __grid_constant__ CUtensorMap tm, YArgs<float> a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    constexpr int TX = TYX;
     constexpr int TILE = N * TX;
     constexpr uint32_t TILE_BYTES = TILE * 8;
     typedef cx<float> C;
@@ -305,68 +309,85 @@ __global__ void __launch_bounds__(TYX * FastPlan<N>::TPL)
     }
 }
 
-template <int N, bool INV> static void ypass_tma_launch(const YArgs<float>& a, const void* map, cudaStream_t st)
+template <int N, int TX, bool INV>
+static void ypass_tma_launch(const YArgs<float>& a, const void* map, cudaStream_t st)
 {
-    constexpr int threads = TYX * FastPlan<N>::TPL;
-    const size_t sm = (size_t)2 * N * TYX * 8 + 16 + (size_t)N * 8;
+    constexpr int threads = TX * FastPlan<N>::TPL;
+    const size_t sm = (size_t)2 * N * TX * 8 + 16 + (size_t)N * 8;
     static int grid_per_sm = 0;
     static int nsm = 0;
     if (grid_per_sm == 0) {
-        cudaFuncSetAttribute(k_ypass_tma<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_ypass_tma<N, TX, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         int dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
         int per = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ypass_tma<N, INV>, threads, sm) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ypass_tma<N, TX, INV>, threads, sm) != cudaSuccess ||
             per < 1)
             per = 1;
         grid_per_sm = per;
     }
-    const int ntiles = ((a.g.nh + TYX - 1) / TYX) * a.g.n3 * 9;
+    const int ntiles = ((a.g.nh + TX - 1) / TX) * a.g.n3 * 9;
     const int grid = std::min(ntiles, grid_per_sm * nsm);
-    k_ypass_tma<N, INV><<<grid, threads, sm, st>>>(*reinterpret_cast<const CUtensorMap*>(map), a);
+    k_ypass_tma<N, TX, INV><<<grid, threads, sm, st>>>(*reinterpret_cast<const CUtensorMap*>(map), a);
+}
+
+template <int N, bool INV> static void ypass_tma_pick(const YArgs<float>& a, const void* map, cudaStream_t st)
+{
+    if (a.cfg == 1)
+        ypass_tma_launch<N, tma_tyx<1>(), INV>(a, map, st);
+    else
+        ypass_tma_launch<N, tma_tyx<0>(), INV>(a, map, st);
 }
 
 template <bool INV> void launch_ypass_tma(const YArgs<float>& a, const void* map, cudaStream_t st)
 {
     switch (a.g.n2) {
-        case 64: ypass_tma_launch<64, INV>(a, map, st); break;
-        case 128: ypass_tma_launch<128, INV>(a, map, st); break;
-        default: ypass_tma_launch<256, INV>(a, map, st); break;
+        case 64: ypass_tma_pick<64, INV>(a, map, st); break;
+        case 128: ypass_tma_pick<128, INV>(a, map, st); break;
+        default: ypass_tma_pick<256, INV>(a, map, st); break;
     }
 }
 template void launch_ypass_tma<false>(const YArgs<float>&, const void*, cudaStream_t);
 template void launch_ypass_tma<true>(const YArgs<float>&, const void*, cudaStream_t);
 
 // ------------------------------------------------------------- z-pass launch
-template <int N> static void zpass_tma_launch(const ZArgs<float>& a, const void* map, cudaStream_t st)
+template <int N, int TX> static void zpass_tma_launch(const ZArgs<float>& a, const void* map, cudaStream_t st)
 {
-    constexpr int TX = tma_tx<N>();
     constexpr int threads = 3 * TX * FastPlan<N>::TPL;
     const size_t sm = (size_t)2 * 3 * N * TX * 8 + 16 + (size_t)N * 8;
     static int grid_per_sm = 0;
     static int nsm = 0;
     if (grid_per_sm == 0) {
-        cudaFuncSetAttribute(k_zpass_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_zpass_tma<N, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         int dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
         int per = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zpass_tma<N>, threads, sm) != cudaSuccess || per < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zpass_tma<N, TX>, threads, sm) != cudaSuccess ||
+            per < 1)
             per = 1;
         grid_per_sm = per;
     }
     const int ntiles = ((a.g.nh + TX - 1) / TX) * a.g.n2 * 3 * a.g.nprob;
     const int grid = std::min(ntiles, grid_per_sm * nsm);
-    k_zpass_tma<N><<<grid, threads, sm, st>>>(*reinterpret_cast<const CUtensorMap*>(map), a);
+    k_zpass_tma<N, TX><<<grid, threads, sm, st>>>(*reinterpret_cast<const CUtensorMap*>(map), a);
+}
+
+template <int N> static void zpass_tma_pick(const ZArgs<float>& a, const void* map, cudaStream_t st)
+{
+    if (a.cfg == 1)
+        zpass_tma_launch<N, tma_tx<N, 1>()>(a, map, st);
+    else
+        zpass_tma_launch<N, tma_tx<N, 0>()>(a, map, st);
 }
 
 void launch_zpass_tma(const ZArgs<float>& a, const void* map, cudaStream_t st)
 {
     switch (a.g.n3p) {
-        case 64: zpass_tma_launch<64>(a, map, st); break;
-        case 128: zpass_tma_launch<128>(a, map, st); break;
-        default: zpass_tma_launch<256>(a, map, st); break;
+        case 64: zpass_tma_pick<64>(a, map, st); break;
+        case 128: zpass_tma_pick<128>(a, map, st); break;
+        default: zpass_tma_pick<256>(a, map, st); break;
     }
 }
 
