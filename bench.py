@@ -338,6 +338,7 @@ def main():
                            "kspace": "rotated (HEX8R)",
                            "operator_applications": int(ops), "solve_finished_in_timed_region": bool(done),
                            "l2": "inputs larger than L2 (each 9-field >= 604 MB)",
+                           "autotune": combo.autotune_report().strip().splitlines(),
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "batch": batch, "gpu_launches": launches,
                 "clocks": clocks, "kernels": table}

@@ -1034,8 +1034,10 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             cudaEvent_t e0, e1;
             CK(cudaEventCreate(&e0));
             CK(cudaEventCreate(&e1));
-            auto time_of = [&](auto&& launch) -> float {
-                launch();
+            // best of 3 timings of 3 launches (after a warm-up launch); the
+            // candidates of a pass are timed alternately so that clock and
+            // cache drift affect both alike
+            auto time_once = [&](auto&& launch) -> float {
                 cudaEventRecord(e0, st);
                 for (int k = 0; k < 3; k++) launch();
                 cudaEventRecord(e1, st);
@@ -1044,73 +1046,90 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                 cudaEventElapsedTime(&ms, e0, e1);
                 return (cudaGetLastError() == cudaSuccess) ? ms : 1e30f;
             };
+            auto time_pair = [&](auto&& l0, auto&& l1, bool has1, float* out) {
+                l0();
+                if (has1) l1();
+                out[0] = out[1] = 1e30f;
+                for (int rep = 0; rep < 3; rep++) {
+                    out[0] = std::min(out[0], time_once(l0));
+                    if (has1) out[1] = std::min(out[1], time_once(l1));
+                }
+            };
             TuneRec rec;
             // tangent x-forward
-            for (int c = 0; c < 2; c++) {
-                auto xf = ec.template xf<Tc>();
-                xf.mode = XF_TANGENT;
-                xf.phase = d_phase;
-                xf.vox2box = d_v2b;
-                for (int i = 0; i < 2; i++) xf.mu[i] = hp.mu[i], xf.lam[i] = hp.lam[i];
-                xf.tc = d_tc;
-                xf.r = d_r;
-                xf.p = d_p;
-                xf.x = d_x;
-                xf.matp = d_mat;
-                xf.bA = d_bA;
-                xf.bvox = d_bvox;
-                xf.lofs = d_lofs;
-                xf.nb = std::max<int64_t>(nb, 1);
-                xf.partial = d_part;
-                xf.sc = d_sc;
-                xf.fuse = 0;
-                xf.cfg = c;
-                rec.ms[0][c] = time_of([&] { launch_xfwd<Tc, Tc>(xf, 0, st); });
-            }
+            auto xf = ec.template xf<Tc>();
+            xf.mode = XF_TANGENT;
+            xf.phase = d_phase;
+            xf.vox2box = d_v2b;
+            for (int i = 0; i < 2; i++) xf.mu[i] = hp.mu[i], xf.lam[i] = hp.lam[i];
+            xf.tc = d_tc;
+            xf.r = d_r;
+            xf.p = d_p;
+            xf.x = d_x;
+            xf.matp = d_mat;
+            xf.bA = d_bA;
+            xf.bvox = d_bvox;
+            xf.lofs = d_lofs;
+            xf.nb = std::max<int64_t>(nb, 1);
+            xf.partial = d_part;
+            xf.sc = d_sc;
+            xf.fuse = 0;
+            auto xf1 = xf;
+            xf.cfg = 0;
+            xf1.cfg = 1;
+            time_pair([&] { launch_xfwd<Tc, Tc>(xf, 0, st); }, [&] { launch_xfwd<Tc, Tc>(xf1, 0, st); }, true,
+                      rec.ms[0]);
             // y forward and z (+ projection): tile widths with a valid tensor map
-            for (int c = 0; c < 2; c++) {
-                YArgs<Tc> y{};
-                y.g = g;
-                y.plan = ec.py;
-                y.tw = ec.tab.twy;
-                y.spec = ec.spec;
-                y.tx = ec.txy;
-                y.sc = d_sc;
-                y.cfg = c;
-                y.tmap = ec.ymap_ok[c] ? &ec.ymap[c] : nullptr;
-                rec.ms[1][c] = (c == 0 || y.tmap) ? time_of([&] { launch_ypass<Tc, false>(y, st); }) : 1e30f;
-                ZArgs<Tc> z{};
-                z.g = g;
-                z.plan = ec.pz;
-                z.tw = ec.tab.twz;
-                z.spec = ec.spec;
-                z.tx = ec.txz;
-                for (int j = 0; j < 3; j++) z.sa[j] = ec.tab.sa[j], z.sb[j] = ec.tab.sb[j];
-                z.scale = (Tc)(2.0 * g.nprob / (double)g.V);
-                z.sc = d_sc;
-                z.cfg = c;
-                z.tmap = ec.zmap_ok[c] ? &ec.zmap[c] : nullptr;
-                rec.ms[2][c] = (c == 0 || z.tmap) ? time_of([&] { launch_zpass<Tc>(z, st); }) : 1e30f;
-            }
+            YArgs<Tc> y0{};
+            y0.g = g;
+            y0.plan = ec.py;
+            y0.tw = ec.tab.twy;
+            y0.spec = ec.spec;
+            y0.tx = ec.txy;
+            y0.sc = d_sc;
+            YArgs<Tc> y1 = y0;
+            y0.cfg = 0;
+            y0.tmap = ec.ymap_ok[0] ? &ec.ymap[0] : nullptr;
+            y1.cfg = 1;
+            y1.tmap = ec.ymap_ok[1] ? &ec.ymap[1] : nullptr;
+            time_pair([&] { launch_ypass<Tc, false>(y0, st); }, [&] { launch_ypass<Tc, false>(y1, st); },
+                      y1.tmap != nullptr, rec.ms[1]);
+            ZArgs<Tc> z0{};
+            z0.g = g;
+            z0.plan = ec.pz;
+            z0.tw = ec.tab.twz;
+            z0.spec = ec.spec;
+            z0.tx = ec.txz;
+            for (int j = 0; j < 3; j++) z0.sa[j] = ec.tab.sa[j], z0.sb[j] = ec.tab.sb[j];
+            z0.scale = (Tc)(2.0 * g.nprob / (double)g.V);
+            z0.sc = d_sc;
+            ZArgs<Tc> z1 = z0;
+            z0.cfg = 0;
+            z0.tmap = ec.zmap_ok[0] ? &ec.zmap[0] : nullptr;
+            z1.cfg = 1;
+            z1.tmap = ec.zmap_ok[1] ? &ec.zmap[1] : nullptr;
+            time_pair([&] { launch_zpass<Tc>(z0, st); }, [&] { launch_zpass<Tc>(z1, st); }, z1.tmap != nullptr,
+                      rec.ms[2]);
             // CG x-inverse
-            for (int c = 0; c < 2; c++) {
-                auto xi = ec.template xi<Tc>();
-                xi.mode = XI_CG;
-                xi.x = d_x;
-                xi.r = d_r;
-                xi.p = d_p;
-                xi.partial = d_part;
-                xi.sc = d_sc;
-                xi.fuse = 0;
-                xi.cfg = c;
-                rec.ms[3][c] = time_of([&] { launch_xinv<Tc, Tc>(xi, 0, st); });
-            }
+            auto xi = ec.template xi<Tc>();
+            xi.mode = XI_CG;
+            xi.x = d_x;
+            xi.r = d_r;
+            xi.p = d_p;
+            xi.partial = d_part;
+            xi.sc = d_sc;
+            xi.fuse = 0;
+            auto xi1 = xi;
+            xi.cfg = 0;
+            xi1.cfg = 1;
+            time_pair([&] { launch_xinv<Tc, Tc>(xi, 0, st); }, [&] { launch_xinv<Tc, Tc>(xi1, 0, st); }, true,
+                      rec.ms[3]);
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars) * B, st));
             CK(cudaStreamSynchronize(st));
             CK(cudaGetLastError());
-            for (int k = 0; k < 4; k++) rec.cfg[k] = rec.ms[k][1] < rec.ms[k][0] ? 1 : 0;
+            for (int k = 0; k < 4; k++) rec.cfg[k] = rec.ms[k][1] < 0.98f * rec.ms[k][0] ? 1 : 0;  // 2 % margin
             tune_store(key, rec);
             tune_lookup(key, ec);
             return COMBO_OK;
