@@ -1122,7 +1122,8 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             auto xi1 = xi;
             xi.cfg = 0;
             xi1.cfg = 1;
-            time_pair([&] { launch_xinv<Tc, Tc>(xi, 0, st); }, [&] { launch_xinv<Tc, Tc>(xi1, 0, st); }, true,
+            // (guard 1 selects the streamed kernel; cg_done is 0 here)
+            time_pair([&] { launch_xinv<Tc, Tc>(xi, 1, st); }, [&] { launch_xinv<Tc, Tc>(xi1, 1, st); }, true,
                       rec.ms[3]);
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
