@@ -408,6 +408,29 @@ def batch_mix(count=64, seed=SEED_BASE + 3, sides=(32, 48, 64, 96, 128), n_steps
     return out
 
 
+def fine_ball_image(fine=256, R=0.4):
+    """Binary fine image chi[k, j, i] (uint8, x fastest) of the ball |x| < R of
+    the unit RVE [-0.5, 0.5]^3 sampled at the fine voxel centres (the paper's
+    Sec. 6.2 sphere before coarse-graining)."""
+    x = (np.arange(fine) + 0.5) / fine - 0.5
+    r2 = x[None, None, :] ** 2 + x[None, :, None] ** 2 + x[:, None, None] ** 2
+    return (r2 < R * R).astype(np.uint8)
+
+
+def fine_plane_image(n, normal, offset=0.0, h=(1.0, 1.0, 1.0)):
+    """Binary fine image of the half space (x - c) . normal < offset (the
+    inclusion), c the centre of the periodic box of n voxels of edges h,
+    sampled at voxel centres; normal is normalised here."""
+    n1, n2, n3 = (int(v) for v in n)
+    nv = np.asarray(normal, float)
+    nv = nv / np.linalg.norm(nv)
+    x = (np.arange(n1) + 0.5 - 0.5 * n1) * h[0]
+    y = (np.arange(n2) + 0.5 - 0.5 * n2) * h[1]
+    z = (np.arange(n3) + 0.5 - 0.5 * n3) * h[2]
+    d = nv[0] * x[None, None, :] + nv[1] * y[None, :, None] + nv[2] * z[:, None, None]
+    return (d < offset).astype(np.uint8)
+
+
 def fine_sphere_block_count(fine=256, coarse=32, R=0.4):
     """Number of coarse blocks that hold both phases when a ball of radius R
     (RVE [-0.5, 0.5]^3) is sampled at the fine voxel centres and the fine

@@ -1,0 +1,111 @@
+"""Pins of the coarse-graining oracle (normal detection, paper Sec. 5)."""
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def nrm():
+    from oracle import normals
+
+    return normals
+
+
+@pytest.fixture(scope="module")
+def ball():
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    return ms.fine_ball_image(256, 0.4)
+
+
+def test_paper_composite_voxel_count(nrm, ball):
+    # Sec. 6.2: the 256^3 ball coarse-grained to 32^3 has 2624 composite voxels
+    phase, idx, c, N = nrm.block_normals(ball, (8, 8, 8), (1, 1, 1))
+    assert int((phase == 2).sum()) == 2624 == idx.size
+
+
+def test_volume_fractions_are_voxel_counts(nrm):
+    rng = np.random.default_rng(0)
+    chi = (rng.random((12, 16, 20)) < 0.3).astype(np.uint8)
+    phase, idx, c, N = nrm.block_normals(chi, (4, 4, 3), (1, 1, 1))
+    cnt = chi.reshape(4, 3, 4, 4, 5, 4).sum(axis=(1, 3, 5))  # [K, J, I] inclusion voxels per block
+    frac = cnt / 48.0
+    mixed = (cnt > 0) & (cnt < 48)
+    assert np.array_equal(np.flatnonzero(mixed.ravel()), idx)
+    assert np.allclose(c, frac.ravel()[idx], rtol=0, atol=1e-15)
+    assert np.array_equal(phase.ravel() == 1, (cnt == 48).ravel())
+
+
+def test_stencil_weights_equal_the_direct_periodic_stencil(nrm):
+    rng = np.random.default_rng(1)
+    chi = (rng.random((6, 8, 10)) < 0.5).astype(np.float64)
+    h = (0.7, 1.3, 2.1)
+    r = (h[1] * h[2] / h[0], h[0] * h[2] / h[1], h[0] * h[1] / h[2])
+    direct = np.zeros_like(chi)
+    for axis, ri in zip((2, 1, 0), r):
+        direct += ri * (np.roll(chi, 1, axis) - 2 * chi + np.roll(chi, -1, axis))
+    assert np.allclose(nrm.stencil_weights(chi, h), np.abs(direct), atol=1e-12)
+
+
+@pytest.mark.parametrize("b,h", [((8, 8, 8), (1, 1, 1)), ((16, 8, 4), (1, 1, 1)), ((8, 8, 4), (1.0, 1.0, 2.0))])
+def test_planar_interface_normal_is_recovered(nrm, b, h):
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    nt = np.array([0.48, 0.6, 0.64])
+    chi = ms.fine_plane_image((64, 64, 64), nt, 3.3, h)
+    phase, idx, c, N = nrm.block_normals(chi, b, h)
+    assert idx.size > 10
+    # The half space is not periodic: its wrap at the faces of the box makes
+    # further interfaces there, so only boxels off the box faces are checked.
+    nc = (64 // b[0], 64 // b[1], 64 // b[2])
+    I, J, K = idx % nc[0], (idx // nc[0]) % nc[1], idx // (nc[0] * nc[1])
+    inner = (I > 0) & (I < nc[0] - 1) & (J > 0) & (J < nc[1] - 1) & (K > 0) & (K < nc[2] - 1)
+    dots = N[inner] @ nt
+    assert inner.sum() > 40
+    assert np.all(dots > 0.75)  # out of the inclusion (the negative side)
+    # Boxels the plane cuts across (not only at a corner, where a few staircase
+    # voxels carry the weights) recover the normal to the staircase's accuracy.
+    cut = inner & (c > 0.1) & (c < 0.9)
+    assert cut.sum() > 20
+    assert np.all(N[cut] @ nt > 0.998)
+    assert np.mean(N[cut] @ nt) > 0.999
+    if b == (16, 8, 4):
+        # non-equiaxed boxels: the barycentre normal is far off (Fig. normal:kabel2)
+        _, _, _, Nk = nrm.block_normals(chi, b, h, "kabel")
+        assert np.mean(Nk[cut] @ nt) < 0.9
+
+
+def test_ball_normals_point_out_and_beat_the_barycentre_normals(nrm, ball):
+    """Sec. 5.2 / Sec. 6.2: the Laplacian normals are closer to the radial
+    direction than the barycentre normals, for equiaxed voxels and more so for
+    non-equiaxed boxels."""
+    for b in [(8, 8, 8), (32, 16, 8)]:
+        errs = {}
+        for method in ("laplace", "kabel"):
+            phase, idx, c, N = nrm.block_normals(ball, b, (1, 1, 1), method)
+            nc = (256 // b[0], 256 // b[1], 256 // b[2])
+            I, J, K = idx % nc[0], (idx // nc[0]) % nc[1], idx // (nc[0] * nc[1])
+            cen = np.stack([(I + 0.5) * b[0], (J + 0.5) * b[1], (K + 0.5) * b[2]], 1) - 128.0
+            radial = cen / np.linalg.norm(cen, axis=1)[:, None]
+            cosang = np.clip(np.sum(N * radial, 1), -1, 1)
+            assert np.all(cosang > 0)  # out of the ball
+            errs[method] = float(np.mean(np.arccos(cosang)))
+        assert errs["laplace"] < errs["kabel"]
+        if b == (32, 16, 8):
+            assert errs["laplace"] < 0.5 * errs["kabel"]
+
+
+def test_normal_minimises_the_weighted_squared_distance(nrm, ball):
+    """Brute force over directions: N minimises sum_w (N . x)^2 over unit
+    vectors (the weighted least-squares plane of Sec. 5.2)."""
+    b = (32, 16, 8)
+    phase, idx, c, N = nrm.block_normals(ball, b, (1, 1, 1))
+    w = nrm.stencil_weights(ball, (1, 1, 1))
+    rng = np.random.default_rng(3)
+    d = rng.normal(size=(20000, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    for t in rng.choice(idx.size, 6, replace=False):
+        M = nrm.moment_tensor(ball, b, (1, 1, 1), int(idx[t]), w)
+        q = np.einsum("ni,ij,nj->n", d, M, d)
+        qn = float(N[t] @ M @ N[t])
+        assert abs(np.linalg.norm(N[t]) - 1.0) < 1e-12
+        assert qn <= q.min() * (1 + 1e-12)
