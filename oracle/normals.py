@@ -59,20 +59,32 @@ def block_normals(chi, b, h, method="laplace"):
     """Coarse-grain chi into boxels of b fine voxels.
 
     Returns (phase_c [nc3, nc2, nc1] uint8: 0 matrix, 1 inclusion, 2 boxel;
-    boxel_idx (linear coarse index, increasing); c_plus; N [nb, 3])."""
+    boxel_idx (linear coarse index, increasing); c_plus; N [nb, 3]).
+
+    Readings where the paper is silent (degenerate boxels):
+      - Ntilde is undefined (taken as 0) when the two barycentres coincide;
+        the sign rule keeps N only for Ntilde . N > 0, so N's sign is then
+        the eigen-solver's;
+      - the "kabel" method falls back to the Laplacian normal there;
+      - the weights of a boxel holding both phases never all vanish: a fine
+        voxel with a neighbour of the other phase has w > 0 (all its second
+        differences share the sign of -chi), so M is well defined."""
     chi = np.asarray(chi, dtype=np.uint8)
     n3, n2, n1 = chi.shape
     b1, b2, b3 = (int(v) for v in b)
     if n1 % b1 or n2 % b2 or n3 % b3:
         raise ValueError("block sizes must divide the fine grid")
-    hx, hy, hz = (float(v) for v in h)
+    hv = np.array([float(v) for v in h])
     nc1, nc2, nc3 = n1 // b1, n2 // b2, n3 // b3
-    w = stencil_weights(chi, h) if method == "laplace" else None
-    # fine-voxel centre offsets from the boxel centre, per axis
-    ox = (np.arange(b1) + 0.5 - 0.5 * b1) * hx
-    oy = (np.arange(b2) + 0.5 - 0.5 * b2) * hy
-    oz = (np.arange(b3) + 0.5 - 0.5 * b3) * hz
-    Z, Y, X = np.meshgrid(oz, oy, ox, indexing="ij")
+    w = stencil_weights(chi, h)
+    # fine-voxel centre offsets from the boxel centre: x = q h / 2 with the
+    # integer q = 2 i' + 1 - b (i' the position in the boxel)
+    qx = 2 * np.arange(b1) + 1 - b1
+    qy = 2 * np.arange(b2) + 1 - b2
+    qz = 2 * np.arange(b3) + 1 - b3
+    QZ, QY, QX = np.meshgrid(qz, qy, qx, indexing="ij")
+    Q = np.stack([QX.ravel(), QY.ravel(), QZ.ravel()], 1)  # int64 [b1 b2 b3, 3]
+    P_all = Q * (0.5 * hv)[None, :]
     phase = np.zeros((nc3, nc2, nc1), np.uint8)
     idx, cs, Ns = [], [], []
     nblock = b1 * b2 * b3
@@ -80,23 +92,27 @@ def block_normals(chi, b, h, method="laplace"):
         for J in range(nc2):
             for I in range(nc1):
                 blk = chi[K * b3:(K + 1) * b3, J * b2:(J + 1) * b2, I * b1:(I + 1) * b1]
-                npl = int(blk.sum())
+                inc = blk.ravel().astype(bool)
+                npl = int(inc.sum())
                 if npl == 0:
                     continue
                 if npl == nblock:
                     phase[K, J, I] = 1
                     continue
                 phase[K, J, I] = 2
-                inc = blk.astype(bool)
-                cp = np.array([X[inc].mean(), Y[inc].mean(), Z[inc].mean()])
-                cm = np.array([X[~inc].mean(), Y[~inc].mean(), Z[~inc].mean()])
-                Nt = (cm - cp) / np.linalg.norm(cm - cp)  # Eq. normal:kabel
-                if method == "kabel":
+                # barycentres (Eq. normal:kabel) from the exact integer sums
+                Qp = Q[inc].sum(0)
+                Qm = Q[~inc].sum(0)
+                cp = 0.5 * hv * Qp / npl
+                cm = 0.5 * hv * Qm / (nblock - npl)
+                dc = cm - cp
+                Nt = dc / np.linalg.norm(dc) if np.any(dc != 0.0) else np.zeros(3)
+                if method == "kabel" and np.any(Nt != 0.0):
                     N = Nt
                 else:
                     wb = w[K * b3:(K + 1) * b3, J * b2:(J + 1) * b2, I * b1:(I + 1) * b1].ravel()
-                    P = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
-                    P = P - (wb @ P) / wb.sum()  # relative to the weighted barycentre c_S
+                    assert wb.sum() > 0.0
+                    P = P_all - (wb @ P_all) / wb.sum()  # relative to the weighted barycentre c_S
                     M = (P * wb[:, None]).T @ P  # sum w x (x) x
                     lam, vec = np.linalg.eigh(M)
                     N = vec[:, 0]
@@ -106,6 +122,26 @@ def block_normals(chi, b, h, method="laplace"):
                 Ns.append(N)
     return (phase, np.asarray(idx, np.int64), np.asarray(cs, np.float64),
             np.asarray(Ns, np.float64).reshape(-1, 3))
+
+
+def barycentre_normal(chi, b, h, coarse_index):
+    """Ntilde of one boxel (Eq. normal:kabel), zeros when undefined."""
+    chi = np.asarray(chi, dtype=np.uint8)
+    n3, n2, n1 = chi.shape
+    b1, b2, b3 = (int(v) for v in b)
+    nc1, nc2 = n1 // b1, n2 // b2
+    I = coarse_index % nc1
+    J = (coarse_index // nc1) % nc2
+    K = coarse_index // (nc1 * nc2)
+    blk = chi[K * b3:(K + 1) * b3, J * b2:(J + 1) * b2, I * b1:(I + 1) * b1].astype(bool)
+    hv = np.array([float(v) for v in h])
+    Z, Y, X = np.meshgrid(*(0.5 * hv[a] * (2 * np.arange(bb) + 1 - bb) for a, bb in ((2, b3), (1, b2), (0, b1))),
+                          indexing="ij")
+    cp = np.array([X[blk].mean(), Y[blk].mean(), Z[blk].mean()])
+    cm = np.array([X[~blk].mean(), Y[~blk].mean(), Z[~blk].mean()])
+    d = cm - cp
+    nd = np.linalg.norm(d)
+    return d / nd if nd > 0 else np.zeros(3)
 
 
 def moment_tensor(chi, b, h, coarse_index, w=None):

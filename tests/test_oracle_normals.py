@@ -109,3 +109,43 @@ def test_normal_minimises_the_weighted_squared_distance(nrm, ball):
         qn = float(N[t] @ M @ N[t])
         assert abs(np.linalg.norm(N[t]) - 1.0) < 1e-12
         assert qn <= q.min() * (1 + 1e-12)
+
+
+def test_weights_count_the_neighbours_of_the_other_phase(nrm):
+    """For a binary image every second difference of a voxel has the sign of
+    -chi (or vanishes), so |S * chi| = sum_i r_i (number of the two
+    neighbours along e_i in the other phase)."""
+    rng = np.random.default_rng(4)
+    chi = (rng.random((10, 12, 14)) < 0.4).astype(np.uint8)
+    h = (0.9, 1.7, 0.6)
+    r = (h[1] * h[2] / h[0], h[0] * h[2] / h[1], h[0] * h[1] / h[2])
+    cnt = np.zeros(chi.shape)
+    for axis, ri in zip((2, 1, 0), r):
+        for sh in (1, -1):
+            cnt += ri * (np.roll(chi, sh, axis) != chi)
+    assert np.allclose(nrm.stencil_weights(chi, h), cnt, rtol=1e-13, atol=1e-12)
+
+
+def test_barycentre_normal_and_its_degenerate_case(nrm):
+    rng = np.random.default_rng(5)
+    h = (1.0, 0.5, 2.0)
+    chi = (rng.random((8, 16, 12)) < 0.5).astype(np.uint8)
+    # coarse voxel 0 holds a centred 2x2x2 inclusion: the barycentres coincide
+    chi[0:4, 0:4, 0:4] = 0
+    chi[1:3, 1:3, 1:3] = 1
+    b = (4, 4, 4)
+    _, idx, _, Nk = nrm.block_normals(chi, b, h, "kabel")
+    _, idx2, _, Nl = nrm.block_normals(chi, b, h, "laplace")
+    assert np.array_equal(idx, idx2) and idx[0] == 0
+    for t, ci in enumerate(idx):
+        Nt = nrm.barycentre_normal(chi, b, h, int(ci))
+        if np.any(Nt != 0):
+            assert np.allclose(Nk[t], Nt, atol=1e-14)
+    assert np.all(nrm.barycentre_normal(chi, b, h, 0) == 0)
+    # undefined Ntilde: both methods give the Laplacian normal (up to sign),
+    # an eigenvector of the smallest eigenvalue of M; for the centred cube M
+    # is a multiple of the identity only when h is isotropic, not here
+    M = nrm.moment_tensor(chi, b, h, 0)
+    lam = np.linalg.eigvalsh(M)
+    assert abs(abs(Nk[0] @ Nl[0]) - 1) < 1e-12
+    assert Nl[0] @ M @ Nl[0] <= lam[0] * (1 + 1e-12)
