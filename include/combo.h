@@ -342,6 +342,51 @@ int combo_constitutive(combo_ctx* ctx, const combo_problem* p, const combo_optio
                        double* a_io, double* P, int32_t mem);
 
 /*
+ * combo_coarse_grain: composite boxels from a binary fine image (Sec. 5).
+ *
+ * The fine image of n1 x n2 x n3 voxels (edges h) is cut into coarse voxels
+ * of b1 x b2 x b3 fine voxels (b_j divides n_j), nc_j = n_j / b_j.  A coarse
+ * voxel whose fine voxels are all matrix gets phase 0, all inclusion phase 1,
+ * both phases phase 2: a composite boxel with c+ = (its inclusion voxels) /
+ * (b1 b2 b3) and an interface normal N.
+ *
+ * method COMBO_NORMAL_LAPLACE (Sec. 5.1-5.2): weights w = |S * chi| of the
+ *   periodic discrete Laplacian whose axis-i second difference is scaled by
+ *   r_i = h_j h_k / h_i; N is the eigenvector of the smallest eigenvalue of
+ *   the boxel's second moment M = sum w x (x) x, x taken from the w-weighted
+ *   barycentre of the boxel's fine voxels (the least-squares plane through the
+ *   interface voxels), its sign set by Eq. normal:flip so that N points out of
+ *   the inclusion.
+ * method COMBO_NORMAL_KABEL: N = Ntilde of Eq. normal:kabel (the direction
+ *   from the inclusion's barycentre to the matrix's), the comparison method
+ *   of Sec. 5; where the two barycentres coincide, the Laplacian normal.
+ * In both, where the barycentres coincide the sign of the Laplacian normal is
+ * the eigen-solver's (Eq. normal:flip cannot decide it).
+ *
+ * The outputs feed combo_problem directly (phase, boxel_idx, boxel_N,
+ * boxel_c).
+ *   n[3], b[3]  fine grid and boxel sizes in fine voxels (host).
+ *   h[3]        fine voxel edges, > 0 (host).
+ *   chi         [n3][n2][n1] bytes, x fastest; nonzero = inclusion.  In `mem`.
+ *   phase_out   [nc1 nc2 nc3] phase codes, coarse index I + nc1 (J + nc2 K).
+ *   idx_out     [cap] coarse indices of the boxels, increasing.
+ *   N_out       [cap][3] unit normals; c_out [cap] c+ (FP64).
+ *   n_boxels    host: receives the number of boxels; only the first
+ *               min(cap, *n_boxels) are written (cap = 0 counts only; the
+ *               boxel pointers may then be NULL).
+ *   mem         COMBO_MEM_HOST or COMBO_MEM_DEVICE for chi and the outputs.
+ * Limits (else COMBO_E_INVALID_ARG): 2 b1 b2 b3 max(b_j)^2 < 2^31 (the
+ * moments are exact integer sums) and (b2 + 2)(b3 + 2)(ceil(n1 / 32) + 1)
+ * 4 bytes + 8 nc1 bytes <= 200 KiB (one slab of boxel rows in shared memory).
+ * Runs on the context's stream and synchronises it before returning.
+ */
+#define COMBO_NORMAL_LAPLACE 0
+#define COMBO_NORMAL_KABEL 1
+int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int32_t b[3], const double h[3], int32_t method,
+                       const uint8_t* chi, uint8_t* phase_out, int64_t cap, int64_t* idx_out, double* N_out,
+                       double* c_out, int64_t* n_boxels, int32_t mem);
+
+/*
  * combo_apply_G_noalloc: the same Green operator as combo_apply_G (FP64),
  * for callers that cannot allocate device memory -- code that runs inside a
  * memory arena or pool it does not own, a loop that must not allocate, or a

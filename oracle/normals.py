@@ -47,7 +47,7 @@ def stencil_weights(chi, h):
         idx_m = [0, 0, 0]
         idx_p = [0, 0, 0]
         idx_m[axis] = -1
-        idx_p[axis] = 1
+        idx_p[axis] = 1 % chi.shape[axis]  # one voxel along the axis: its own neighbour
         S[tuple(idx_m)] += ri
         S[tuple(idx_p)] += ri
         S[0, 0, 0] -= 2.0 * ri
@@ -69,7 +69,7 @@ def block_normals(chi, b, h, method="laplace"):
       - the weights of a boxel holding both phases never all vanish: a fine
         voxel with a neighbour of the other phase has w > 0 (all its second
         differences share the sign of -chi), so M is well defined."""
-    chi = np.asarray(chi, dtype=np.uint8)
+    chi = (np.asarray(chi) != 0).astype(np.uint8)  # nonzero = inclusion
     n3, n2, n1 = chi.shape
     b1, b2, b3 = (int(v) for v in b)
     if n1 % b1 or n2 % b2 or n3 % b3:
@@ -79,12 +79,7 @@ def block_normals(chi, b, h, method="laplace"):
     w = stencil_weights(chi, h)
     # fine-voxel centre offsets from the boxel centre: x = q h / 2 with the
     # integer q = 2 i' + 1 - b (i' the position in the boxel)
-    qx = 2 * np.arange(b1) + 1 - b1
-    qy = 2 * np.arange(b2) + 1 - b2
-    qz = 2 * np.arange(b3) + 1 - b3
-    QZ, QY, QX = np.meshgrid(qz, qy, qx, indexing="ij")
-    Q = np.stack([QX.ravel(), QY.ravel(), QZ.ravel()], 1)  # int64 [b1 b2 b3, 3]
-    P_all = Q * (0.5 * hv)[None, :]
+    Q, P_all = _offsets((b1, b2, b3), hv)
     phase = np.zeros((nc3, nc2, nc1), np.uint8)
     idx, cs, Ns = [], [], []
     nblock = b1 * b2 * b3
@@ -100,33 +95,90 @@ def block_normals(chi, b, h, method="laplace"):
                     phase[K, J, I] = 1
                     continue
                 phase[K, J, I] = 2
-                # barycentres (Eq. normal:kabel) from the exact integer sums
-                Qp = Q[inc].sum(0)
-                Qm = Q[~inc].sum(0)
-                cp = 0.5 * hv * Qp / npl
-                cm = 0.5 * hv * Qm / (nblock - npl)
-                dc = cm - cp
-                Nt = dc / np.linalg.norm(dc) if np.any(dc != 0.0) else np.zeros(3)
-                if method == "kabel" and np.any(Nt != 0.0):
-                    N = Nt
-                else:
-                    wb = w[K * b3:(K + 1) * b3, J * b2:(J + 1) * b2, I * b1:(I + 1) * b1].ravel()
-                    assert wb.sum() > 0.0
-                    P = P_all - (wb @ P_all) / wb.sum()  # relative to the weighted barycentre c_S
-                    M = (P * wb[:, None]).T @ P  # sum w x (x) x
-                    lam, vec = np.linalg.eigh(M)
-                    N = vec[:, 0]
-                    N = N if float(Nt @ N) > 0.0 else -N  # Eq. normal:flip
+                wb = w[K * b3:(K + 1) * b3, J * b2:(J + 1) * b2, I * b1:(I + 1) * b1].ravel()
                 idx.append(I + nc1 * (J + nc2 * K))
                 cs.append(npl / nblock)
-                Ns.append(N)
+                Ns.append(_boxel_normal(inc, wb, Q, P_all, hv, method))
     return (phase, np.asarray(idx, np.int64), np.asarray(cs, np.float64),
             np.asarray(Ns, np.float64).reshape(-1, 3))
 
 
+def _offsets(b, hv):
+    """Integer offsets q = 2 i' + 1 - b of a boxel's fine voxels ([nblock, 3],
+    x fastest) and their positions q h / 2 from the boxel centre."""
+    b1, b2, b3 = b
+    qx = 2 * np.arange(b1) + 1 - b1
+    qy = 2 * np.arange(b2) + 1 - b2
+    qz = 2 * np.arange(b3) + 1 - b3
+    QZ, QY, QX = np.meshgrid(qz, qy, qx, indexing="ij")
+    Q = np.stack([QX.ravel(), QY.ravel(), QZ.ravel()], 1)
+    return Q, Q * (0.5 * hv)[None, :]
+
+
+def _boxel_normal(inc, wb, Q, P_all, hv, method):
+    """N of one boxel holding both phases: inc its inclusion flags, wb its
+    Laplacian weights (both [nblock], x fastest)."""
+    npl = int(inc.sum())
+    nblock = inc.size
+    # barycentres (Eq. normal:kabel) from the exact integer sums
+    Qp = Q[inc].sum(0)
+    Qm = Q[~inc].sum(0)
+    cp = 0.5 * hv * Qp / npl
+    cm = 0.5 * hv * Qm / (nblock - npl)
+    dc = cm - cp
+    Nt = dc / np.linalg.norm(dc) if np.any(dc != 0.0) else np.zeros(3)
+    if method == "kabel" and np.any(Nt != 0.0):
+        return Nt
+    assert wb.sum() > 0.0
+    P = P_all - (wb @ P_all) / wb.sum()  # relative to the weighted barycentre c_S
+    M = (P * wb[:, None]).T @ P  # sum w x (x) x
+    lam, vec = np.linalg.eigh(M)
+    N = vec[:, 0]
+    return N if float(Nt @ N) > 0.0 else -N  # Eq. normal:flip
+
+
+def block_normals_at(chi, b, h, coarse_index, method="laplace"):
+    """The boxels among the listed coarse voxels, for images too large for
+    block_normals: the same steps, with the weights of each boxel from the
+    periodic Laplacian stencil applied directly on its one-voxel halo (the
+    direct evaluation Sec. 5.1 names as an alternative to the Fourier one;
+    the two agree to rounding, pinned by the tests).  Returns (phase of each
+    listed coarse voxel, c_plus, N) with c_plus = nan, N = nan for the pure
+    ones."""
+    chi = np.asarray(chi)
+    n3, n2, n1 = chi.shape
+    b1, b2, b3 = (int(v) for v in b)
+    hv = np.array([float(v) for v in h])
+    r = (hv[1] * hv[2] / hv[0], hv[0] * hv[2] / hv[1], hv[0] * hv[1] / hv[2])
+    nc1, nc2 = n1 // b1, n2 // b2
+    Q, P_all = _offsets((b1, b2, b3), hv)
+    nblock = b1 * b2 * b3
+    out_ph, out_c, out_N = [], [], []
+    for ci in np.asarray(coarse_index, np.int64).ravel():
+        I, J, K = int(ci % nc1), int((ci // nc1) % nc2), int(ci // (nc1 * nc2))
+        xs = np.arange(I * b1 - 1, (I + 1) * b1 + 1) % n1
+        ys = np.arange(J * b2 - 1, (J + 1) * b2 + 1) % n2
+        zs = np.arange(K * b3 - 1, (K + 1) * b3 + 1) % n3
+        win = (chi[np.ix_(zs, ys, xs)] != 0).astype(np.float64)
+        c0 = win[1:-1, 1:-1, 1:-1]
+        npl = int(c0.sum())
+        if npl == 0 or npl == nblock:
+            out_ph.append(0 if npl == 0 else 1)
+            out_c.append(np.nan)
+            out_N.append(np.full(3, np.nan))
+            continue
+        s = (r[0] * (win[1:-1, 1:-1, :-2] + win[1:-1, 1:-1, 2:] - 2 * c0)
+             + r[1] * (win[1:-1, :-2, 1:-1] + win[1:-1, 2:, 1:-1] - 2 * c0)
+             + r[2] * (win[:-2, 1:-1, 1:-1] + win[2:, 1:-1, 1:-1] - 2 * c0))
+        out_ph.append(2)
+        out_c.append(npl / nblock)
+        out_N.append(_boxel_normal(c0.ravel().astype(bool), np.abs(s).ravel(), Q, P_all, hv, method))
+    return np.asarray(out_ph, np.uint8), np.asarray(out_c), np.asarray(out_N).reshape(-1, 3)
+
+
 def barycentre_normal(chi, b, h, coarse_index):
     """Ntilde of one boxel (Eq. normal:kabel), zeros when undefined."""
-    chi = np.asarray(chi, dtype=np.uint8)
+    chi = (np.asarray(chi) != 0).astype(np.uint8)  # nonzero = inclusion
     n3, n2, n1 = chi.shape
     b1, b2, b3 = (int(v) for v in b)
     nc1, nc2 = n1 // b1, n2 // b2
@@ -147,7 +199,7 @@ def barycentre_normal(chi, b, h, coarse_index):
 def moment_tensor(chi, b, h, coarse_index, w=None):
     """M of one boxel (for the property checks of degenerate eigenvalues);
     w = stencil_weights(chi, h) when the caller has it already."""
-    chi = np.asarray(chi, dtype=np.uint8)
+    chi = (np.asarray(chi) != 0).astype(np.uint8)  # nonzero = inclusion
     n3, n2, n1 = chi.shape
     b1, b2, b3 = (int(v) for v in b)
     nc1, nc2 = n1 // b1, n2 // b2

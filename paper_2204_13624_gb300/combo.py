@@ -60,7 +60,7 @@ EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_o
            "combo_solve_end", "combo_solve_batch", "combo_solve_profile", "combo_solve_profile_read", "combo_apply_G",
            "combo_constitutive", "combo_apply_G_noalloc", "combo_server_create", "combo_server_destroy",
            "combo_submit", "combo_poll", "combo_wait", "combo_cancel", "combo_server_stats",
-           "combo_autotune_enable", "combo_autotune_force", "combo_autotune_report"]
+           "combo_autotune_enable", "combo_autotune_force", "combo_autotune_report", "combo_coarse_grain"]
 
 _lib = None
 
@@ -108,6 +108,8 @@ def load(path: str = LIB_PATH):
     L.combo_autotune_force.restype = C.c_int
     L.combo_autotune_report.argtypes = [C.c_char_p, i64]
     L.combo_autotune_report.restype = i64
+    L.combo_coarse_grain.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp, vp, C.POINTER(i64), i32]
+    L.combo_coarse_grain.restype = C.c_int
     _lib = L
     return L
 
@@ -383,6 +385,55 @@ def constitutive(prob: dict, F, a=None, ctx: Context | None = None, **opts):
     P = np.zeros_like(F)
     _check(load().combo_constitutive(ctx.h, C.byref(pb.s), C.byref(o), _ptr(F), _ptr(a), _ptr(P), MEM_HOST))
     return P, a[:nb]
+
+
+NORMAL_LAPLACE = 0
+NORMAL_KABEL = 1
+
+
+def coarse_grain(chi, b, h=(1.0, 1.0, 1.0), method="laplace", ctx: Context | None = None, cap=None):
+    """combo_coarse_grain: composite boxels of a binary fine image (Sec. 5).
+
+    chi is [n3][n2][n1] (x fastest), nonzero = inclusion: a numpy array (the
+    call copies it to the device and returns numpy arrays) or a CUDA uint8
+    tensor (the outputs are then CUDA tensors).  b = (b1, b2, b3) fine voxels
+    per coarse voxel, h the fine voxel edges, method "laplace" (Sec. 5) or
+    "kabel" (Eq. normal:kabel).  Returns (phase [nc3, nc2, nc1] uint8,
+    boxel_idx int64 [k] increasing, c_plus [k], N [k, 3], n_boxels) with
+    k = min(n_boxels, cap); cap limits the boxels written (default: every
+    coarse voxel, so k = n_boxels)."""
+    ctx = ctx or default_context()
+    m = {"laplace": NORMAL_LAPLACE, "kabel": NORMAL_KABEL}[method]
+    dev = _is_dev(chi)
+    n3, n2, n1 = (int(v) for v in chi.shape)
+    b1, b2, b3 = (int(v) for v in b)
+    nc = (n3 // b3, n2 // b2, n1 // b1) if (n1 % b1 == 0 and n2 % b2 == 0 and n3 % b3 == 0) else (0, 0, 0)
+    ncv = max(nc[0] * nc[1] * nc[2], 1)
+    cap = ncv if cap is None else int(cap)
+    if dev:
+        import torch
+
+        if chi.dtype != torch.uint8 or not chi.is_contiguous():
+            chi = chi.contiguous().to(torch.uint8)
+        kw = dict(device=chi.device)
+        phase = torch.empty(ncv, dtype=torch.uint8, **kw)
+        idx = torch.empty(max(cap, 1), dtype=torch.int64, **kw)
+        N = torch.empty((max(cap, 1), 3), dtype=torch.float64, **kw)
+        c = torch.empty(max(cap, 1), dtype=torch.float64, **kw)
+    else:
+        chi = np.ascontiguousarray(chi, dtype=np.uint8)
+        phase = np.empty(ncv, np.uint8)
+        idx = np.empty(max(cap, 1), np.int64)
+        N = np.empty((max(cap, 1), 3), np.float64)
+        c = np.empty(max(cap, 1), np.float64)
+    nn = (C.c_int32 * 3)(n1, n2, n3)
+    bb = (C.c_int32 * 3)(b1, b2, b3)
+    hh = (C.c_double * 3)(*[float(v) for v in h])
+    nb = C.c_int64(0)
+    _check(load().combo_coarse_grain(ctx.h, nn, bb, hh, m, _ptr(chi), _ptr(phase), cap, _ptr(idx), _ptr(N),
+                                     _ptr(c), C.byref(nb), MEM_DEVICE if dev else MEM_HOST))
+    k = min(nb.value, cap)
+    return phase.reshape(nc), idx[:k], c[:k], N[:k], nb.value
 
 
 def apply_G_noalloc(X, Y, n, l=(1.0, 1.0, 1.0), kspace=ROTATED, device=0, stream=None, want_sumsq=True):

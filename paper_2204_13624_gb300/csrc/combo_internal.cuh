@@ -486,3 +486,14 @@ template <typename Tc> struct BoxelArgs {
 template <typename Tc> void launch_boxel(const BoxelArgs<Tc>& a, cudaStream_t st);
 
 }  // namespace combo
+
+// Library context: a device and the stream every call on it runs on, plus a
+// device scratch array grown on demand by the calls that need one (freed
+// with the context).
+struct combo_ctx {
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+};

@@ -52,12 +52,6 @@ int combo::set_error(int code, const char* msg)
 }
 
 // ------------------------------------------------------------------ context
-struct combo_ctx {
-    int device;
-    cudaStream_t stream;
-    bool own_stream;
-};
-
 extern "C" int combo_ctx_create(const combo_ctx_opts* o, combo_ctx** out)
 {
     if (!out) return fail(COMBO_E_INVALID_ARG, "null output pointer");
@@ -87,6 +81,10 @@ extern "C" void combo_ctx_destroy(combo_ctx* c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
+    if (c->scratch) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->scratch);
+    }
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -431,6 +431,32 @@ def fine_plane_image(n, normal, offset=0.0, h=(1.0, 1.0, 1.0)):
     return (d < offset).astype(np.uint8)
 
 
+def fine_spheres_image(n, radius_vox, count, seed=SEED_BASE + 4, h=(1.0, 1.0, 1.0)):
+    """Binary fine image chi[k, j, i] (uint8, x fastest) of `count` balls of
+    radius radius_vox (in units of h[0]) at uniform random centres of the
+    periodic box of n = (n1, n2, n3) voxels with edges h (balls may overlap;
+    voxels are classified by their centres)."""
+    n1, n2, n3 = (int(v) for v in n)
+    hx, hy, hz = (float(v) for v in h)
+    rng = np.random.default_rng(seed)
+    L = np.array([n1 * hx, n2 * hy, n3 * hz])
+    chi = np.zeros((n3, n2, n1), np.uint8)
+    R = float(radius_vox) * hx
+    for c in rng.random((int(count), 3)) * L:
+        lo = np.floor((c - R) / [hx, hy, hz]).astype(int) - 1
+        hi = np.ceil((c + R) / [hx, hy, hz]).astype(int) + 1
+        ix = np.arange(lo[0], hi[0] + 1)
+        iy = np.arange(lo[1], hi[1] + 1)
+        iz = np.arange(lo[2], hi[2] + 1)
+        dx = (ix + 0.5) * hx - c[0]
+        dy = (iy + 0.5) * hy - c[1]
+        dz = (iz + 0.5) * hz - c[2]
+        inside = dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2 < R * R
+        sub = np.ix_(iz % n3, iy % n2, ix % n1)
+        chi[sub] |= inside.astype(np.uint8)
+    return chi
+
+
 def fine_sphere_block_count(fine=256, coarse=32, R=0.4):
     """Number of coarse blocks that hold both phases when a ball of radius R
     (RVE [-0.5, 0.5]^3) is sampled at the fine voxel centres and the fine

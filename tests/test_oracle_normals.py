@@ -149,3 +149,18 @@ def test_barycentre_normal_and_its_degenerate_case(nrm):
     lam = np.linalg.eigvalsh(M)
     assert abs(abs(Nk[0] @ Nl[0]) - 1) < 1e-12
     assert Nl[0] @ M @ Nl[0] <= lam[0] * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("method", ["laplace", "kabel"])
+def test_windowed_boxels_equal_the_whole_image_pass(nrm, method):
+    """block_normals_at (direct stencil on each boxel's periodic halo) agrees
+    with block_normals (Fourier-domain stencil over the image)."""
+    rng = np.random.default_rng(6)
+    chi = (rng.random((9, 12, 20)) < 0.45).astype(np.uint8) * 7  # any nonzero byte is inclusion
+    b, h = (5, 4, 3), (1.2, 0.8, 1.0)
+    phase, idx, c, N = nrm.block_normals(chi, b, h, method)
+    allc = np.arange(phase.size)
+    ph2, c2, N2 = nrm.block_normals_at(chi, b, h, allc, method)
+    assert np.array_equal(ph2, phase.ravel())
+    assert np.array_equal(c2[idx], c)
+    assert np.allclose(N2[idx], N, atol=1e-12)
