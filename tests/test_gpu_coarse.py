@@ -4,7 +4,9 @@
 Phase codes, boxel indices and c+ are exact.  The normals are compared with a
 tolerance from the eigenvalue gap of each boxel's M (Davis-Kahan: the angle
 between computed and exact eigenvectors is at most the perturbation of M over
-the gap, and both sides perturb M by a few ulps of sum w |x|^2); where the gap
+the gap).  The GPU forms M from exact integer sums; the oracle sums
+nblock FP64 products, so its M is off by at most about nblock ulps of
+sum w |x|^2 (the gamma_n bound of recursive summation); where the gap
 is too small for that bound to mean anything, N is checked to be a unit
 eigenvector of the smallest eigenvalue.  Where the barycentre normal is
 undefined (coincident barycentres) the sign of the Laplacian normal is the
@@ -80,7 +82,7 @@ def check_normals(chi, b, h, idx, N_gpu, N_or, method):
         gap = lam[1] - lam[0]
         # N is a unit eigenvector of the smallest eigenvalue (always)
         assert N_gpu[t] @ M @ N_gpu[t] - lam[0] <= 1e-12 * scale, ci
-        tol = 1e-12 + 64 * EPS * scale / max(gap, 1e-300)
+        tol = 1e-12 + (w.size + 64) * EPS * scale / max(gap, 1e-300)
         nt = dc / np.linalg.norm(dc) if nt_defined else np.zeros(3)
         undecided = (not nt_defined) or abs(nt @ N_or[t]) < 1e-9
         d = np.abs(N_gpu[t] - N_or[t]).max()
