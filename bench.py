@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-normals", action="store_true")
+    ap.add_argument("--normals-only", default=None, metavar="N1,N2,N3",
+                    help="only coarse-grain a seeded spheres image of this size (8^3 boxels), three calls "
+                         "(profiling captures of the coarse-graining kernels)")
     ap.add_argument("--serve-full", action="store_true",
                     help="serving stream of sides 64..256 and 1..10 load steps (takes minutes)")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel table here")
@@ -234,10 +238,21 @@ def main():
     if dist:
         dist.barrier()
     combo.load()
-    p = workload(args.n, args.shape)
-    V = p["n"][0] * p["n"][1] * p["n"][2]
     stream = torch.cuda.current_stream()
     ctx = combo.Context(local, stream.cuda_stream)
+    if args.normals_only:
+        from paper_2204_13624_gb300 import microstructure as ms
+
+        n = tuple(int(v) for v in args.normals_only.split(","))
+        d = torch.from_numpy(ms.fine_spheres_image(n, 24, max(1, int(4000 * np.prod(n) / 1024**3)),
+                                                   seed=ms.SEED_BASE + 5)).cuda()
+        for _ in range(3):
+            nb = combo.coarse_grain(d, (8, 8, 8), ctx=ctx)[4]
+        torch.cuda.synchronize()
+        print(json.dumps({"normals_only": list(n), "boxels": int(nb)}))
+        return
+    p = workload(args.n, args.shape)
+    V = p["n"][0] * p["n"][1] * p["n"][2]
     prec = {"refined": combo.FP32_REFINED, "refined-df": combo.FP32_REFINED_DF, "fp64": combo.FP64}[args.precision]
     s = combo.Solve(p, ctx=ctx, solver=combo.NEWTON_CG, precision=prec, tol=1e-8)
     s.advance(max(args.warmup, 3))
@@ -318,6 +333,9 @@ def main():
     batch = None
     if not args.no_batch and rank == 0:
         batch = batch_bench(combo, ctx)
+    normals = None
+    if not args.no_normals and rank == 0:
+        normals = normals_bench(combo, ctx, stream, peak, peak_kind, cpu=not args.no_cpu_baseline and world == 1)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -340,7 +358,8 @@ def main():
                            "l2": "inputs larger than L2 (each 9-field >= 604 MB)",
                            "autotune": combo.autotune_report().strip().splitlines(),
                            "parallelism": f"replicas x{world}"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "batch": batch, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "batch": batch,
+                "normal_detection": normals, "gpu_launches": launches,
                 "clocks": clocks, "kernels": table}
         if args.profile_json:
             json.dump(line, open(args.profile_json, "w"), indent=1)
@@ -482,6 +501,90 @@ def batch_bench(combo, ctx, prec=None):
             "one_by_one_seconds": ts, "one_by_one_solves_per_s": len(probs) / ts,
             "speedup_batched": ts / tb, "Pbar_rel_diff_batched_vs_one_by_one_max": err,
             "precision": "FP32 Krylov + double-float residual"}
+
+
+def normals_bench(combo, ctx, stream, peak, peak_kind, cpu=True, reps=20):
+    """Coarse-graining with the Sec. 5 normal detection (combo_coarse_grain):
+    the paper's 256^3 ball (radius 0.4 L) to 32^3 composite voxels and to
+    8 x 16 x 32 boxels, and a 1 GiB image of seeded random balls (radius 24
+    voxels, about 20 % inclusion) to 128^3.  Device-resident image, L2
+    flushed (256 MiB write) before each call, CUDA events on the call's
+    stream around the call and (library events) around each launch; median
+    of `reps` calls.  The coarse-graining's speed of light is one read of the
+    image plus the writes of the phase codes and boxel lists."""
+    import torch
+
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ball = ms.fine_ball_image(256, 0.4)
+    work = [("ball_256_to_32^3", ball, (8, 8, 8)), ("ball_256_to_8x16x32", ball, (32, 16, 8)),
+            ("spheres_1024_to_128^3", ms.fine_spheres_image((1024, 1024, 1024), 24, 4000, seed=ms.SEED_BASE + 5),
+             (8, 8, 8))]
+    out = {}
+    combo.coarse_grain_profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches = 0
+    for name, chi, b in work:
+        d = torch.from_numpy(chi).cuda()
+        for _ in range(3):
+            res = combo.coarse_grain(d, b, ctx=ctx)
+        calls, kern = [], []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0.record(stream)
+            res = combo.coarse_grain(d, b, ctx=ctx)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            calls.append(e0.elapsed_time(e1))
+            kern.append(combo.coarse_grain_profile_read())
+            launches += 5
+        V = int(chi.size)
+        nb = int(res[4])
+        nc = V // (b[0] * b[1] * b[2])
+        ms_call = statistics.median(calls)
+        ms_k = [statistics.median(k[i] for k in kern) for i in range(5)]
+        ms_kernels = sum(ms_k)
+        # speed of light of the whole coarse-graining: the image read once, the
+        # phase codes and the boxel lists (index, normal, c+) written once
+        alg_all = V + nc + 40 * nb
+        # the packing pass reads the image and writes one bit per voxel
+        alg_pack = V + V // 8
+        gbps_all = alg_all / (ms_kernels / 1e3) / 1e9
+        gbps_pack = alg_pack / (ms_k[0] / 1e3) / 1e9
+        # end to end from a host image: H2D of the image, D2H of phases and boxels
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        combo.coarse_grain(chi, b, ctx=ctx)
+        t_e2e = time.perf_counter() - t0
+        out[name] = {"fine": list(chi.shape[::-1]), "boxel": list(b), "coarse_voxels": nc, "boxels": nb,
+                     "ms_call": ms_call, "ms_kernels": ms_kernels, "ms_pack": ms_k[0], "ms_slab": ms_k[1],
+                     "ms_scan": ms_k[2], "ms_scatter": ms_k[3], "ms_finish": ms_k[4],
+                     "fine_voxels_per_s": V / (ms_kernels / 1e3),
+                     "fine_voxels_per_s_call": V / (ms_call / 1e3),
+                     "roofline": {"bound": "hbm", "achieved": gbps_all, "peak": peak, "unit": "GB/s",
+                                  "frac": gbps_all / peak, "peak_kind": peak_kind, "alg_bytes": alg_all,
+                                  "what": "all five kernels against one read of the image"},
+                     "roofline_pack": {"bound": "hbm", "achieved": gbps_pack, "peak": peak, "unit": "GB/s",
+                                       "frac": gbps_pack / peak, "peak_kind": peak_kind, "alg_bytes": alg_pack},
+                     "e2e": {"value": V / t_e2e, "unit": "fine voxels/s", "h2d_bytes": V,
+                             "d2h_bytes": nc + 40 * nb, "seconds": t_e2e}}
+        del d
+        if cpu and name == "ball_256_to_32^3":
+            from oracle import normals as nrm
+
+            t0 = time.perf_counter()
+            nrm.block_normals(chi, b, (1.0, 1.0, 1.0))
+            dt = time.perf_counter() - t0
+            out[name]["cpu_baseline"] = {"value": V / dt, "unit": "fine voxels/s", "cores": 1, "kind": "oracle",
+                                         "sample": "the whole 256^3 image, one pass"}
+    combo.coarse_grain_profile(False)
+    out["note"] = ("ms_call: events around the whole call (five launches, the count's copy back and the "
+                   "call's host synchronisation); ms_pack/slab/scan/scatter/finish: library events around each "
+                   "launch; fine_voxels_per_s from their sum")
+    out["gpu_launches"] = launches
+    return out
 
 
 def run_reference(args, rank, world):

@@ -377,7 +377,8 @@ int combo_constitutive(combo_ctx* ctx, const combo_problem* p, const combo_optio
  *   mem         COMBO_MEM_HOST or COMBO_MEM_DEVICE for chi and the outputs.
  * Limits (else COMBO_E_INVALID_ARG): 2 b1 b2 b3 max(b_j)^2 < 2^31 (the
  * moments are exact integer sums) and (b2 + 2)(b3 + 2)(ceil(n1 / 32) + 1)
- * 4 bytes + 8 nc1 bytes <= 200 KiB (one slab of boxel rows in shared memory).
+ * 4 bytes + 8 nc1 bytes <= 200 KiB (one slab of fine rows with its halo in
+ * shared memory).
  * Runs on the context's stream and synchronises it before returning.
  */
 #define COMBO_NORMAL_LAPLACE 0
@@ -385,6 +386,19 @@ int combo_constitutive(combo_ctx* ctx, const combo_problem* p, const combo_optio
 int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int32_t b[3], const double h[3], int32_t method,
                        const uint8_t* chi, uint8_t* phase_out, int64_t cap, int64_t* idx_out, double* N_out,
                        double* c_out, int64_t* n_boxels, int32_t mem);
+
+/*
+ * Event timing of combo_coarse_grain's kernels, for benchmarks (no
+ * counterpart in the paper).  While enabled (per process), each call records
+ * CUDA events on its stream around its five launches -- the packing of the
+ * image to bits, the slab pass (counts, integer moments), the scan of the
+ * per-slab counts, the scatter of the boxel indices and the per-boxel finish
+ * (normal, c+) -- and combo_coarse_grain_profile_read gives the last call's
+ * durations in ms (ms[0..4]).  Returns COMBO_OK, or COMBO_E_INVALID_ARG when
+ * nothing was recorded yet.
+ */
+int combo_coarse_grain_profile(int32_t enable);
+int combo_coarse_grain_profile_read(double ms[5]);
 
 /*
  * combo_apply_G_noalloc: the same Green operator as combo_apply_G (FP64),

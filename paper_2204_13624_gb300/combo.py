@@ -60,7 +60,8 @@ EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_o
            "combo_solve_end", "combo_solve_batch", "combo_solve_profile", "combo_solve_profile_read", "combo_apply_G",
            "combo_constitutive", "combo_apply_G_noalloc", "combo_server_create", "combo_server_destroy",
            "combo_submit", "combo_poll", "combo_wait", "combo_cancel", "combo_server_stats",
-           "combo_autotune_enable", "combo_autotune_force", "combo_autotune_report", "combo_coarse_grain"]
+           "combo_autotune_enable", "combo_autotune_force", "combo_autotune_report", "combo_coarse_grain",
+           "combo_coarse_grain_profile", "combo_coarse_grain_profile_read"]
 
 _lib = None
 
@@ -110,6 +111,10 @@ def load(path: str = LIB_PATH):
     L.combo_autotune_report.restype = i64
     L.combo_coarse_grain.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp, vp, C.POINTER(i64), i32]
     L.combo_coarse_grain.restype = C.c_int
+    L.combo_coarse_grain_profile.argtypes = [i32]
+    L.combo_coarse_grain_profile.restype = C.c_int
+    L.combo_coarse_grain_profile_read.argtypes = [vp]
+    L.combo_coarse_grain_profile_read.restype = C.c_int
     _lib = L
     return L
 
@@ -434,6 +439,18 @@ def coarse_grain(chi, b, h=(1.0, 1.0, 1.0), method="laplace", ctx: Context | Non
                                      _ptr(c), C.byref(nb), MEM_DEVICE if dev else MEM_HOST))
     k = min(nb.value, cap)
     return phase.reshape(nc), idx[:k], c[:k], N[:k], nb.value
+
+
+def coarse_grain_profile(enable: bool = True):
+    """Record CUDA events around the coarse-graining launches (benchmarks)."""
+    _check(load().combo_coarse_grain_profile(1 if enable else 0))
+
+
+def coarse_grain_profile_read():
+    """(pack, slab pass, scan, scatter, finish) durations in ms of the last coarse_grain call."""
+    ms = (C.c_double * 5)()
+    _check(load().combo_coarse_grain_profile_read(ms))
+    return tuple(ms)
 
 
 def apply_G_noalloc(X, Y, n, l=(1.0, 1.0, 1.0), kspace=ROTATED, device=0, stream=None, want_sumsq=True):

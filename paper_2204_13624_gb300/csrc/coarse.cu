@@ -14,25 +14,29 @@
 //     sum w x_c     = h_c / 2       sum_i r_i T1_ic,
 //     sum w x_c x_d = h_c h_d / 4   sum_i r_i T2_icd,
 // where T are integer sums of m_i, m_i q_c and m_i q_c q_d over the boxel.
-// The kernel gets them from XOR masks of neighbouring bit rows; M about the
+// The kernel gets them from XOR masks of neighbouring bit rows and byte tables
+// of bit-position sums (branch-free, so a warp never waits on its densest
+// lane); M about the
 // weighted barycentre is S2 - S1 S1^T / S0 in FP64 and its smallest
 // eigenvector comes from cyclic Jacobi rotations.  The barycentre normal is
 // -(h o Q) / |h o Q| with Q the integer sum of q over the inclusion voxels
 // (the offsets of all voxels of a boxel sum to zero).
 //
-// Work layout.  One CTA per slab (J, K) of coarse voxels (all I along x): the
-// b2 b3 fine rows of the slab are read once from HBM with 16-byte loads and
-// packed to bit rows in shared memory (one bit per fine voxel).  Coarse
-// voxels are counted with popcounts; only a slab that holds a composite boxel
-// loads the one-voxel halo rows (periodic in y and z; x wraps inside a row)
-// and accumulates the moments, a group of G lanes per boxel.  The boxels are
-// written to a dense per-coarse-voxel scratch; a one-CTA scan of the per-slab
-// counts and a scatter kernel compact them in increasing coarse index.
+// Work layout.  A streaming pass packs the image to one bit per fine voxel
+// (16-byte loads, the image read from HBM once).  Then one CTA per slab (J, K)
+// of coarse voxels (all I along x) copies the bit rows of the slab and its
+// one-voxel halo (periodic in y and z; x wraps inside a row) to shared
+// memory.  Coarse voxels are counted with popcounts, and each composite boxel's integer sums are
+// accumulated by a group of G lanes and written to a dense per-coarse-voxel
+// scratch.  A one-CTA scan of the per-slab counts and a scatter kernel list
+// the boxels in increasing coarse index; a last kernel finishes one boxel per
+// thread (eigenvector, sign, c+), so the scarce FP64 pipe runs full warps.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 
 #include "combo.h"
@@ -45,44 +49,40 @@ constexpr int CG_THREADS = 256;
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCATTER_THREADS = 256;
 constexpr size_t CG_SMEM_MAX = 200 * 1024;
+constexpr int FIN_THREADS = 256;
+// Per-boxel integer sums: [0..2] Q (sum of q over the inclusion voxels), then
+// per axis i the ten moments T0, T1x, T1y, T1z, T2xx, T2xy, T2xz, T2yy, T2yz,
+// T2zz of m_i, then the inclusion-voxel count; NSUM pads the record to 16 bytes.
+constexpr int NACC = 33;
+constexpr int NSUM = 36;
 
 struct CgArgs {
-    const uint8_t* chi;  // [n3][n2][n1]
+    const uint32_t* bitimg;  // [n3][n2][nw - 1] bit rows of the image
     int n1, n2, n3;
     int b1, b2, b3;
     int nc1, nc2, nc3;
-    int nw;      // words per shared-memory bit row: ceil(n1 / 32) + 1 (zero pad)
-    int vec;     // 16-byte loads (n1 % 32 == 0 and chi 16-byte aligned)
-    int G;       // lanes per composite boxel (power of two, <= 32)
+    int nwr;     // words per fine row: ceil(n1 / 32)
+    int nw;      // words per shared-memory bit row: nwr + 3 (pads)
+    int G;       // lanes per composite boxel (power of two, <= 32): G = Gq b2 + Gr
+    int Gq, Gr;
+    int R;       // lanes per coarse voxel in the count (power of two, <= 32): R = Rq b2 + Rr
+    int Rq, Rr;
+    float inv_b2, inv_pl, inv_nw;  // reciprocals for the divisions in the loops
     int method;  // COMBO_NORMAL_LAPLACE / COMBO_NORMAL_KABEL
+    int iso;     // h1 == h2 == h3: the moments combine exactly in int64
+    int nblock_pow2;  // b1 b2 b3 a power of two: c+ = count * inv_nblock exactly
+    double inv_nblock;
     double h[3], r[3];
     uint8_t* phase;  // [nc]
     int* slab_cnt;   // [nc2 nc3] boxels per slab
-    double* sN;      // [nc][3] dense scratch (boxels only)
-    double* sc;      // [nc]
+    int* sums;       // [nc][NSUM] dense scratch: the integer sums of each boxel
 };
 
 __device__ __forceinline__ int lrow(int jj, int kk, int b2) { return (kk + 1) * (b2 + 2) + (jj + 1); }
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// bits [x, x + L) of a bit row, L in [0, 32]
-__device__ __forceinline__ uint32_t ext(const uint32_t* row, int x, int L)
-{
-    if (L <= 0) return 0u;
-    const int w = x >> 5, s = x & 31;
-    const uint64_t v = (((uint64_t)row[w + 1] << 32) | row[w]) >> s;
-    return (uint32_t)v & (L == 32 ? 0xFFFFFFFFu : ((1u << L) - 1u));
-}
-
 __device__ __forceinline__ uint32_t bit_at(const uint32_t* row, int x) { return (row[x >> 5] >> (x & 31)) & 1u; }
-
-// sum of the positions of the set bits of m
-__device__ __forceinline__ int pos_sum(uint32_t m)
-{
-    return __popc(m & 0xAAAAAAAAu) + (__popc(m & 0xCCCCCCCCu) << 1) + (__popc(m & 0xF0F0F0F0u) << 2) +
-           (__popc(m & 0xFF00FF00u) << 3) + (__popc(m & 0xFFFF0000u) << 4);
-}
 
 // 16 fine voxels (bytes, nonzero = inclusion) -> 16 bits, voxel x0 + k at bit k
 __device__ __forceinline__ uint32_t pack16(uint4 v)
@@ -98,122 +98,213 @@ __device__ __forceinline__ uint32_t pack16(uint4 v)
     return m;
 }
 
-// Map t in [0, nrows) to the slab-local row (jj, kk): the interior rows, or the
-// halo rows (planes kk = -1 and kk = b3, then the y edges jj = -1, b2 of the
-// interior planes).
-template <bool HALO> __device__ __forceinline__ void row_of(int t, int b2, int& jj, int& kk)
+// q = v / d for 0 <= v < 2^22, d >= 1, inv = 1.0f / d: the float quotient is
+// within one of the exact one, so one correction either way makes it exact.
+__device__ __forceinline__ int fdiv(int v, int d, float inv)
 {
-    if (!HALO) {
-        jj = t % b2;
-        kk = t / b2;
-        return;
-    }
-    const int pl = b2 + 2;
-    if (t < pl) {
-        kk = -1;
-        jj = t - 1;
-    } else if (t < 2 * pl) {
-        kk = -2;  // placeholder, fixed by the caller (b3)
-        jj = t - pl - 1;
-    } else {
-        const int u = t - 2 * pl;
-        kk = u >> 1;
-        jj = (u & 1) ? b2 : -1;
+    int q = __float2int_rz((float)v * inv);
+    const int r = v - q * d;
+    return q + (r >= d) - (r < 0);
+}
+
+// Pass 1: the binary image packed to bit rows, bitimg[(z n2 + y) nwr + w]
+// bit j = voxel (32 w + j, y, z), zero past n1.  With n1 % 32 == 0 the bit
+// rows are the flattened image packed 32 voxels a word: each thread reads
+// 2 x 16 bytes per word (four words in flight) and writes the word.
+constexpr int PACK_THREADS = 256;
+constexpr int PACK_UNROLL = 4;
+
+__global__ void __launch_bounds__(PACK_THREADS) k_cg_pack_vec(const uint8_t* chi, int64_t nwords, uint32_t* bitimg)
+{
+    const int64_t stride = (int64_t)gridDim.x * PACK_THREADS * PACK_UNROLL;
+    for (int64_t base = (int64_t)blockIdx.x * PACK_THREADS * PACK_UNROLL + threadIdx.x; base < nwords;
+         base += stride) {
+        uint4 v[2 * PACK_UNROLL];
+#pragma unroll
+        for (int k = 0; k < PACK_UNROLL; k++) {
+            const int64_t gw = base + (int64_t)k * PACK_THREADS;
+            const uint4* src = reinterpret_cast<const uint4*>(chi + 32 * gw);
+            v[2 * k] = gw < nwords ? __ldcs(src) : make_uint4(0u, 0u, 0u, 0u);
+            v[2 * k + 1] = gw < nwords ? __ldcs(src + 1) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int k = 0; k < PACK_UNROLL; k++) {
+            const int64_t gw = base + (int64_t)k * PACK_THREADS;
+            if (gw < nwords) bitimg[gw] = pack16(v[2 * k]) | (pack16(v[2 * k + 1]) << 16);
+        }
     }
 }
 
-template <bool HALO> __device__ void load_rows(const CgArgs& a, uint32_t* bits, int J, int K)
+// the same for any n1 and alignment: a warp per word, one byte a lane
+__global__ void __launch_bounds__(PACK_THREADS) k_cg_pack_bytes(const uint8_t* chi, int n1, int nwr, int64_t nrows,
+                                                                uint32_t* bitimg)
 {
-    const int nrows = HALO ? 2 * (a.b2 + 2) + 2 * a.b3 : a.b2 * a.b3;
-    const int nwr = a.nw - 1;
-    if (a.vec) {
-        const int ipr = a.n1 >> 4;  // 16-byte items per row (even)
-        const int total = nrows * ipr;
-        constexpr int U = 4;
-        for (int base = 0; base < total; base += U * CG_THREADS) {
-            uint4 v[U];
-            int lr[U], u[U];
+    const int lane = threadIdx.x & 31;
+    const int64_t nwords = nrows * nwr;
+    const int64_t wstride = (int64_t)gridDim.x * (PACK_THREADS / 32);
+    for (int64_t gw = (int64_t)blockIdx.x * (PACK_THREADS / 32) + (threadIdx.x >> 5); gw < nwords; gw += wstride) {
+        const int64_t row = gw / nwr;
+        const int w = (int)(gw - row * nwr);
+        const int x = 32 * w + lane;
+        const uint8_t c = x < n1 ? __ldcs(chi + row * n1 + x) : (uint8_t)0;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, c != 0);
+        if (lane == 0) bitimg[gw] = m;
+    }
+}
+
+// Pass 2 input: the slab's (b2 + 2)(b3 + 2) bit rows -- its own b2 b3 rows and
+// the one-voxel halo around them, periodic in y and z -- copied from the bit
+// image.  Slab-local row t holds (jj, kk) = (t mod (b2 + 2), t div (b2 + 2)) - 1
+// and takes nw = nwr + 3 words: word 1 + w is word w of the fine row; where
+// n1 % 32 == 0, word 0 and word nwr + 1 repeat the row's last and first words,
+// so the periodic x neighbours of the row's ends sit next to them; the other
+// pad words are zero.
+__device__ void load_rows(const CgArgs& a, uint32_t* bits, int J, int K)
+{
+    const int pl = a.b2 + 2;
+    const int nrows = pl * (a.b3 + 2);
+    const int nwr = a.nwr, nw = a.nw;
+    const bool aligned = (a.n1 & 31) == 0;
+    const int total = nrows * nw;
+    constexpr int U = 4;
+    for (int base = 0; base < total; base += U * CG_THREADS) {
+        uint32_t v[U];
+        int dst[U];
 #pragma unroll
-            for (int k = 0; k < U; k++) {
-                const int it = base + k * CG_THREADS + (int)threadIdx.x;
-                v[k] = make_uint4(0u, 0u, 0u, 0u);
-                lr[k] = -1;
-                if (it < total) {
-                    const int t = it / ipr;
-                    u[k] = it - t * ipr;
-                    int jj, kk;
-                    row_of<HALO>(t, a.b2, jj, kk);
-                    if (kk == -2) kk = a.b3;
-                    const int y = wrap(J * a.b2 + jj, a.n2), z = wrap(K * a.b3 + kk, a.n3);
-                    const uint4* src =
-                        reinterpret_cast<const uint4*>(a.chi + ((size_t)z * a.n2 + y) * (size_t)a.n1) + u[k];
-                    v[k] = __ldg(src);
-                    lr[k] = lrow(jj, kk, a.b2);
+        for (int k = 0; k < U; k++) {
+            const int it = base + k * CG_THREADS + (int)threadIdx.x;
+            dst[k] = -1;
+            v[k] = 0u;
+            if (it < total) {
+                const int t = fdiv(it, nw, a.inv_nw), u = it - t * nw;
+                const int gw = u == 0 ? (aligned ? nwr - 1 : -1)
+                                      : (u <= nwr ? u - 1 : (u == nwr + 1 && aligned ? 0 : -1));
+                if (gw >= 0) {
+                    const int k1 = fdiv(t, pl, a.inv_pl);
+                    const int y = wrap(J * a.b2 + (t - k1 * pl) - 1, a.n2), z = wrap(K * a.b3 + k1 - 1, a.n3);
+                    v[k] = __ldg(a.bitimg + ((size_t)z * a.n2 + y) * nwr + gw);
                 }
+                dst[k] = it;
             }
+        }
 #pragma unroll
-            for (int k = 0; k < U; k++) {
-                const uint32_t m = pack16(v[k]);
-                const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, m, 1);
-                // lanes 2m and 2m+1 hold the two halves of one 32-bit word
-                if (lr[k] >= 0 && !(u[k] & 1)) bits[lr[k] * a.nw + (u[k] >> 1)] = m | (o << 16);
-            }
-        }
-    } else {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int total = nrows * nwr;
-        for (int it = warp; it < total; it += CG_THREADS / 32) {
-            const int t = it / nwr, wd = it - t * nwr;
-            int jj, kk;
-            row_of<HALO>(t, a.b2, jj, kk);
-            if (kk == -2) kk = a.b3;
-            const int y = wrap(J * a.b2 + jj, a.n2), z = wrap(K * a.b3 + kk, a.n3);
-            const int x = 32 * wd + lane;
-            const uint8_t c = x < a.n1 ? __ldg(a.chi + ((size_t)z * a.n2 + y) * (size_t)a.n1 + x) : (uint8_t)0;
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, c != 0);
-            if (lane == 0) bits[lrow(jj, kk, a.b2) * a.nw + wd] = m;
-        }
-    }
-    for (int t = threadIdx.x; t < nrows; t += CG_THREADS) {
-        int jj, kk;
-        row_of<HALO>(t, a.b2, jj, kk);
-        if (kk == -2) kk = a.b3;
-        bits[lrow(jj, kk, a.b2) * a.nw + nwr] = 0u;
+        for (int k = 0; k < U; k++)
+            if (dst[k] >= 0) bits[dst[k]] = v[k];
     }
 }
 
-// Smallest-eigenvalue eigenvector of the symmetric 3x3 matrix
-// m = (xx, xy, xz, yy, yz, zz) by cyclic Jacobi rotations: each rotation in
-// the (p, q) plane annihilates a_pq with tan(phi) the smaller root of
-// t^2 + 2 theta t - 1 = 0, theta = (a_qq - a_pp) / (2 a_pq) (the stable form
-// of the classical method, Golub & Van Loan, Matrix Computations, Sec. 8.5).
-__device__ void sym3_min_eigvec(const double m[6], double v[3])
+// The part of a fine row that one boxel covers: bits [x, x + L) of the
+// slab's bit row, x = I b1 + x0, L <= 32.
+struct Span {
+    int w, s, L;    // word, shift and width
+    uint32_t msk;   // L low bits
+    int o;          // offset q = 2 i + o of bit i (q = 2 i' + 1 - b1)
+    int nbytes;     // bytes of the L-bit masks (table lookups)
+    bool one;       // s + L <= 32: the span lies in one word
+    bool left_in;   // x > 0: bit x - 1 is in the row (else it wraps to n1 - 1)
+    bool right_in;  // x + L < n1: bit x + L is in the row (else it wraps to 0)
+};
+
+__device__ __forceinline__ Span make_span(const CgArgs& a, int I, int x0)
 {
-    double a[3][3] = {{m[0], m[1], m[2]}, {m[1], m[3], m[4]}, {m[2], m[4], m[5]}};
-    double V[3][3] = {{1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
-    for (int sweep = 0; sweep < 32; sweep++) {
+    Span c;
+    const int x = I * a.b1 + x0;
+    c.L = min(32, a.b1 - x0);
+    c.w = x >> 5;
+    c.s = x & 31;
+    c.msk = c.L == 32 ? 0xFFFFFFFFu : ((1u << c.L) - 1u);
+    c.o = 2 * x0 + 1 - a.b1;
+    c.nbytes = (c.L + 7) >> 3;
+    c.one = c.s + c.L <= 32;
+    c.left_in = x > 0;
+    c.right_in = x + c.L < a.n1;
+    return c;
+}
+
+__device__ __forceinline__ uint32_t take(const uint32_t* row, const Span& c)
+{
+    if (c.one) return (row[c.w] >> c.s) & c.msk;
+    return (uint32_t)((((uint64_t)row[c.w + 1] << 32) | row[c.w]) >> c.s) & c.msk;
+}
+
+// Byte tables of bit-position sums.  lut[k][v] packs, for the set bits j of
+// the byte v taken as positions i = 8 k + j of a 32-bit mask, the count (bits
+// 0-6), sum i (bits 7-16) and sum i^2 (bits 17-31).  The fields of two
+// masks' sums still fit (count <= 64, sum i <= 992, sum i^2 <= 20832), so the
+// packed words of two masks add with one integer add.
+constexpr int LUT_N = 4 * 256;
+
+__device__ void build_lut(uint32_t* lut)
+{
+    for (int e = threadIdx.x; e < LUT_N; e += CG_THREADS) {
+        const uint32_t k = e >> 8, v = e & 255;
+        // positions j of the set bits from the bit planes of j (0..7)
+        const uint32_t p0 = v & 0xAAu, p1 = v & 0xCCu, p2 = v & 0xF0u;
+        const uint32_t n = __popc(v);
+        const uint32_t sj = __popc(p0) + 2 * __popc(p1) + 4 * __popc(p2);
+        const uint32_t sjj = __popc(p0) + 4 * __popc(p1) + 16 * __popc(p2) + 4 * __popc(p0 & p1) +
+                             8 * __popc(p0 & p2) + 16 * __popc(p1 & p2);
+        // i = 8 k + j
+        const uint32_t si = 8 * k * n + sj, sii = 64 * k * k * n + 16 * k * sj + sjj;
+        lut[e] = n | (si << 7) | (sii << 17);
+    }
+}
+
+template <int NB> __device__ __forceinline__ uint32_t look(const uint32_t* lut, uint32_t m)
+{
+    uint32_t v = lut[m & 255u];
+    if (NB > 1) v += lut[256 + (m >> 8 & 255u)];
+    if (NB > 2) v += lut[512 + (m >> 16 & 255u)];
+    if (NB > 3) v += lut[768 + (m >> 24)];
+    return v;
+}
+
+// Smallest-eigenvalue eigenvector of a symmetric positive semidefinite 3x3
+// matrix K = (xx, xy, xz, yy, yz, zz).
+//
+// A start vector comes from cyclic Jacobi rotations in FP32 on K / tr K: each
+// rotation in the (p, q) plane annihilates a_pq, tan(phi) being the smaller
+// root of t^2 + 2 theta t - 1 = 0 with theta = (a_qq - a_pp) / (2 a_pq) (the
+// classical method in its stable form, Golub & Van Loan, Matrix
+// Computations, Sec. 8.5).  It is refined in FP64 by Rayleigh-quotient
+// iteration written with the adjugate: for sigma the Rayleigh quotient of v,
+// adj(K - sigma I) = sum_i prod_{j != i} (lambda_j - sigma) u_i u_i^T, so
+// adj(K - sigma I) v keeps v's component along the sought eigenvector u_0
+// and damps the others by (lambda_0 - sigma) / (lambda_i - sigma) -- cubic
+// convergence, one step from an FP32 start except where the two smallest
+// eigenvalues are close (then two).  FP64 is the scarce pipe on this GPU,
+// so the FP64 part is a few dozen operations.
+__device__ void min_eigvec(const double K[6], double N[3])
+{
+    const double tr = K[0] + K[3] + K[5];
+    const double sc = tr > 0.0 ? 1.0 / tr : 1.0;
+    float a[3][3] = {{(float)(K[0] * sc), (float)(K[1] * sc), (float)(K[2] * sc)},
+                     {(float)(K[1] * sc), (float)(K[3] * sc), (float)(K[4] * sc)},
+                     {(float)(K[2] * sc), (float)(K[4] * sc), (float)(K[5] * sc)}};
+    float V[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+    for (int sweep = 0; sweep < 8; sweep++) {
         bool rotated = false;
 #pragma unroll
         for (int pq = 0; pq < 3; pq++) {
             const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2, r = 3 - p - q;
-            const double apq = a[p][q];
-            if (fabs(apq) <= 0x1p-60 * (fabs(a[p][p]) + fabs(a[q][q])) || fabs(apq) < 1e-300) {
-                a[p][q] = a[q][p] = 0.0;
+            const float apq = a[p][q];
+            if (fabsf(apq) <= 1e-9f * (fabsf(a[p][p]) + fabsf(a[q][q])) || fabsf(apq) < 1e-30f) {
+                a[p][q] = a[q][p] = 0.f;
                 continue;
             }
-            const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
-            const double t = fabs(theta) > 1e150 ? 0.5 / theta
-                                                 : (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+            const float theta = (a[q][q] - a[p][p]) / (2.f * apq);
+            const float t = fabsf(theta) > 1e9f ? 0.5f / theta
+                                                : copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+            const float c = rsqrtf(t * t + 1.f), s = t * c;
             a[p][p] -= t * apq;
             a[q][q] += t * apq;
-            a[p][q] = a[q][p] = 0.0;
-            const double arp = a[r][p], arq = a[r][q];
+            a[p][q] = a[q][p] = 0.f;
+            const float arp = a[r][p], arq = a[r][q];
             a[r][p] = a[p][r] = c * arp - s * arq;
             a[r][q] = a[q][r] = s * arp + c * arq;
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                const double vp = V[k][p], vq = V[k][q];
+                const float vp = V[k][p], vq = V[k][q];
                 V[k][p] = c * vp - s * vq;
                 V[k][q] = s * vp + c * vq;
             }
@@ -221,82 +312,286 @@ __device__ void sym3_min_eigvec(const double m[6], double v[3])
         }
         if (!rotated) break;
     }
-    // the column of the smallest diagonal entry (selected without a dynamic
-    // index so the matrices stay in registers)
-    const bool k1 = a[1][1] < a[0][0];
-    const double d01 = k1 ? a[1][1] : a[0][0];
-    const bool k2 = a[2][2] < d01;
+    // smallest and middle diagonal entries (no dynamic index: registers only)
+    const float d0 = a[0][0], d1 = a[1][1], d2 = a[2][2];
+    const int k = (d0 <= d1 && d0 <= d2) ? 0 : (d1 <= d2 ? 1 : 2);
+    const float lo = k == 0 ? d0 : (k == 1 ? d1 : d2);
+    const float mid = k == 0 ? fminf(d1, d2) : (k == 1 ? fminf(d0, d2) : fminf(d0, d1));
+    double v[3];
 #pragma unroll
-    for (int i = 0; i < 3; i++) v[i] = k2 ? V[i][2] : (k1 ? V[i][1] : V[i][0]);
-    const double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int i = 0; i < 3; i++) v[i] = (double)(k == 0 ? V[i][0] : (k == 1 ? V[i][1] : V[i][2]));
+    double nv = rsqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
 #pragma unroll
-    for (int i = 0; i < 3; i++) v[i] /= nv;
+    for (int i = 0; i < 3; i++) v[i] *= nv;
+    const int steps = (mid - lo) < 1e-3f ? 2 : 1;
+    for (int it = 0; it < steps; it++) {
+        const double kv0 = K[0] * v[0] + K[1] * v[1] + K[2] * v[2];
+        const double kv1 = K[1] * v[0] + K[3] * v[1] + K[4] * v[2];
+        const double kv2 = K[2] * v[0] + K[4] * v[1] + K[5] * v[2];
+        const double sg = v[0] * kv0 + v[1] * kv1 + v[2] * kv2;  // Rayleigh quotient (|v| = 1)
+        const double A00 = K[0] - sg, A11 = K[3] - sg, A22 = K[5] - sg, A01 = K[1], A02 = K[2], A12 = K[4];
+        const double C00 = A11 * A22 - A12 * A12, C11 = A00 * A22 - A02 * A02, C22 = A00 * A11 - A01 * A01;
+        const double C01 = A02 * A12 - A01 * A22, C02 = A01 * A12 - A02 * A11, C12 = A01 * A02 - A00 * A12;
+        const double y0 = C00 * v[0] + C01 * v[1] + C02 * v[2];
+        const double y1 = C01 * v[0] + C11 * v[1] + C12 * v[2];
+        const double y2 = C02 * v[0] + C12 * v[1] + C22 * v[2];
+        const double ny = y0 * y0 + y1 * y1 + y2 * y2;
+        if (!(ny > 0.0) || !isfinite(ny)) break;  // v already spans a multiple eigenvalue
+        nv = rsqrt(ny);
+        v[0] = y0 * nv;
+        v[1] = y1 * nv;
+        v[2] = y2 * nv;
+    }
+    N[0] = v[0];
+    N[1] = v[1];
+    N[2] = v[2];
 }
 
-// acc: [0..2] Q (sum of q over the inclusion voxels), then per axis i the ten
-// integer moments T0, T1x, T1y, T1z, T2xx, T2xy, T2xz, T2yy, T2yz, T2zz of m_i.
-constexpr int NACC = 33;
 
-__device__ __forceinline__ void boxel_result(const CgArgs& a, const int* acc, double* N)
+__device__ void boxel_finish(const CgArgs& a, const int* acc, double* N)
 {
-    const bool has_nt = acc[0] != 0 || acc[1] != 0 || acc[2] != 0;
-    double nt[3] = {0.0, 0.0, 0.0};
-    if (has_nt) {
-        const double d[3] = {-a.h[0] * acc[0], -a.h[1] * acc[1], -a.h[2] * acc[2]};
-        const double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-#pragma unroll
-        for (int c = 0; c < 3; c++) nt[c] = d[c] / nd;
-    }
+    const int Qx = acc[0], Qy = acc[1], Qz = acc[2];
+    // the barycentre normal's direction, unnormalised: -(h o Q)
+    const double d0 = -a.h[0] * Qx, d1 = -a.h[1] * Qy, d2 = -a.h[2] * Qz;
+    const bool has_nt = (Qx | Qy | Qz) != 0;
     if (a.method == COMBO_NORMAL_KABEL && has_nt) {
-        for (int c = 0; c < 3; c++) N[c] = nt[c];
+        const double s = rsqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        N[0] = d0 * s;
+        N[1] = d1 * s;
+        N[2] = d2 * s;
         return;
     }
-    double S0 = 0.0, S1[3] = {0.0, 0.0, 0.0}, S2[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        const int* T = acc + 3 + 10 * i;
-        const double ri = a.r[i];
-        S0 += ri * T[0];
-#pragma unroll
-        for (int c = 0; c < 3; c++) S1[c] += ri * T[1 + c];
-#pragma unroll
-        for (int c = 0; c < 6; c++) S2[c] += ri * T[4 + c];
-    }
-    for (int c = 0; c < 3; c++) S1[c] *= 0.5 * a.h[c];
+    // K = 4 S0 M = (h_c h_d) (S0 U2_cd - U1_c U1_d), U = sum_i r_i T_i, a
+    // positive multiple of M with the same eigenvectors
+    double K[6];
     const int ci[6] = {0, 0, 0, 1, 1, 2}, di[6] = {0, 1, 2, 1, 2, 2};
-    double M[6];
+    if (a.iso) {
+        // equal r_i and h_c: K is h^4 r^2 (T0 T2 - T1 T1^T), exact in int64
+        int64_t T0 = 0, T1[3] = {0, 0, 0}, T2[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
-    for (int c = 0; c < 6; c++) M[c] = S2[c] * (0.25 * a.h[ci[c]] * a.h[di[c]]) - S1[ci[c]] * S1[di[c]] / S0;
-    sym3_min_eigvec(M, N);
+        for (int i = 0; i < 3; i++) {
+            const int* T = acc + 3 + 10 * i;
+            T0 += T[0];
+#pragma unroll
+            for (int c = 0; c < 3; c++) T1[c] += T[1 + c];
+#pragma unroll
+            for (int c = 0; c < 6; c++) T2[c] += T[4 + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 6; c++) K[c] = (double)(T0 * T2[c] - T1[ci[c]] * T1[di[c]]);
+    } else {
+        double S0 = 0.0, U1[3] = {0.0, 0.0, 0.0}, U2[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const int* T = acc + 3 + 10 * i;
+            const double ri = a.r[i];
+            S0 += ri * T[0];
+#pragma unroll
+            for (int c = 0; c < 3; c++) U1[c] += ri * T[1 + c];
+#pragma unroll
+            for (int c = 0; c < 6; c++) U2[c] += ri * T[4 + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 6; c++) K[c] = (a.h[ci[c]] * a.h[di[c]]) * (S0 * U2[c] - U1[ci[c]] * U1[di[c]]);
+    }
+    min_eigvec(K, N);
     // Eq. normal:flip: keep N only where it agrees with the barycentre normal
-    if (!(nt[0] * N[0] + nt[1] * N[1] + nt[2] * N[2] > 0.0))
-        for (int c = 0; c < 3; c++) N[c] = -N[c];
+    if (!(d0 * N[0] + d1 * N[1] + d2 * N[2] > 0.0)) {
+        N[0] = -N[0];
+        N[1] = -N[1];
+        N[2] = -N[2];
+    }
 }
 
-__global__ void __launch_bounds__(CG_THREADS) k_cg_slab(CgArgs a)
+// Accumulate the integer moments of one boxel row span into acc, given its
+// bits W, its x neighbours Wm (bits x - 1 ..) and Wp (bits x + 1 ..), and the
+// same span of the four y / z neighbour rows; q = 2 i + o for bit i.
+template <int NB>
+__device__ __forceinline__ void span_moments(const uint32_t* lut, uint32_t W, uint32_t Wm, uint32_t Wp,
+                                             uint32_t Ym, uint32_t Yp, uint32_t Zm, uint32_t Zp, int o, int qy,
+                                             int qz, int* acc)
+{
+    const uint32_t vw = look<NB>(lut, W);
+    const int np = vw & 127, sw = vw >> 7 & 1023;
+    acc[0] += 2 * sw + o * np;
+    acc[1] += qy * np;
+    acc[2] += qz * np;
+    const uint32_t e[6] = {W ^ Wm, W ^ Wp, W ^ Ym, W ^ Yp, W ^ Zm, W ^ Zp};
+    const int qyy = qy * qy, qyz = qy * qz, qzz = qz * qz;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        // m_i over the span: its two neighbours' XOR masks
+        const uint32_t v = look<NB>(lut, e[2 * i]) + look<NB>(lut, e[2 * i + 1]);
+        const int n = v & 127, si = v >> 7 & 1023, sii = v >> 17;
+        const int s1 = 2 * si + o * n;                       // sum of q
+        const int s2 = 4 * sii + 4 * o * si + o * o * n;     // sum of q^2
+        int* T = acc + 3 + 10 * i;
+        T[0] += n;
+        T[1] += s1;
+        T[2] += qy * n;
+        T[3] += qz * n;
+        T[4] += s2;
+        T[5] += qy * s1;
+        T[6] += qz * s1;
+        T[7] += qyy * n;
+        T[8] += qyz * n;
+        T[9] += qzz * n;
+    }
+}
+
+// General spans (any n1, any b1): bits [x, x + L) of the row whose global
+// word w is C[w]; the row's ends wrap explicitly.
+__device__ __forceinline__ void row_moments(const CgArgs& a, const uint32_t* lut, const Span& c, const uint32_t* C,
+                                            int rstride, int qy, int qz, int* acc)
+{
+    const uint64_t win = ((uint64_t)C[c.w + 1] << 32) | C[c.w];
+    const uint32_t W = (uint32_t)(win >> c.s) & c.msk;
+    const uint32_t Wp = c.right_in ? ((uint32_t)(win >> (c.s + 1)) & c.msk)
+                                   : ((W >> 1) | ((C[0] & 1u) << (c.L - 1)));
+    uint32_t Wm;
+    if (c.s > 0)
+        Wm = (uint32_t)(win >> (c.s - 1)) & c.msk;
+    else
+        Wm = ((W << 1) | (c.left_in ? (C[c.w - 1] >> 31) : bit_at(C, a.n1 - 1))) & c.msk;
+    span_moments<4>(lut, W, Wm, Wp, take(C - a.nw, c), take(C + a.nw, c), take(C - rstride, c),
+                    take(C + rstride, c), c.o, qy, qz, acc);
+}
+
+// Fast spans: n1 % 32 == 0 and b1 <= 32, so x = I b1 and every neighbour bit
+// lies in the three padded words around the span (the wrap words included).
+struct FastSpan {
+    int w;         // padded index of the word before the span's first word
+    int s, o;
+    uint32_t msk;
+};
+
+__device__ __forceinline__ FastSpan make_fast_span(const CgArgs& a, int I)
+{
+    FastSpan c;
+    const int x = I * a.b1;
+    c.w = x >> 5;
+    c.s = x & 31;
+    c.o = 1 - a.b1;
+    c.msk = a.b1 == 32 ? 0xFFFFFFFFu : ((1u << a.b1) - 1u);
+    return c;
+}
+
+template <bool ONE> __device__ __forceinline__ uint32_t take_fast(const uint32_t* R, const FastSpan& c)
+{
+    if (ONE) return (R[c.w + 1] >> c.s) & c.msk;
+    return __funnelshift_r(R[c.w + 1], R[c.w + 2], c.s) & c.msk;
+}
+
+// The fast path's lanes keep one y row offset qy (the group size is a
+// multiple of b2), so a lane sums only what varies with its rows: per axis
+// i, n, sum q, sum q^2, sum qz n, sum qz q, sum qz^2 n (f[6 i ..]), then
+// sum q over the inclusion bits, their count and sum qz count (f[18 ..]).
+constexpr int NFAST = 21;
+
+template <int NB, bool ONE>
+__device__ __forceinline__ void row_moments_fast(const uint32_t* lut, const FastSpan& c, const uint32_t* R, int nw,
+                                                 int rstride, int qz, int* f)
+{
+    const uint32_t lo = R[c.w], mid = R[c.w + 1], hi = R[c.w + 2];
+    const uint32_t W = (ONE ? (mid >> c.s) : __funnelshift_r(mid, hi, c.s)) & c.msk;
+    const uint32_t Wm = (c.s == 0 ? __funnelshift_r(lo, mid, 31) : __funnelshift_r(mid, hi, c.s - 1)) & c.msk;
+    const uint32_t Wp = (c.s == 31 ? hi : __funnelshift_r(mid, hi, c.s + 1)) & c.msk;
+    const uint32_t e[6] = {W ^ Wm, W ^ Wp, W ^ take_fast<ONE>(R - nw, c), W ^ take_fast<ONE>(R + nw, c),
+                           W ^ take_fast<ONE>(R - rstride, c), W ^ take_fast<ONE>(R + rstride, c)};
+    const int o = c.o, qzz = qz * qz;
+    const uint32_t vw = look<NB>(lut, W);
+    const int np = vw & 127, sw = vw >> 7 & 1023;
+    f[18] += 2 * sw + o * np;
+    f[19] += np;
+    f[20] += qz * np;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const uint32_t v = look<NB>(lut, e[2 * i]) + look<NB>(lut, e[2 * i + 1]);
+        const int n = v & 127, si = v >> 7 & 1023, sii = v >> 17;
+        const int s1 = 2 * si + o * n;                    // sum of q
+        const int s2 = 4 * sii + 4 * o * si + o * o * n;  // sum of q^2
+        int* F = f + 6 * i;
+        F[0] += n;
+        F[1] += s1;
+        F[2] += s2;
+        F[3] += qz * n;
+        F[4] += qz * s1;
+        F[5] += qzz * n;
+    }
+}
+
+// the lane's sums with its qy folded in, in the layout of the per-boxel record
+__device__ __forceinline__ void expand_fast(const int* f, int qy, int* acc)
+{
+    acc[0] = f[18];
+    acc[1] = qy * f[19];
+    acc[2] = f[20];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const int* F = f + 6 * i;
+        int* T = acc + 3 + 10 * i;
+        T[0] = F[0];
+        T[1] = F[1];
+        T[2] = qy * F[0];
+        T[3] = F[3];
+        T[4] = F[2];
+        T[5] = qy * F[1];
+        T[6] = F[4];
+        T[7] = qy * qy * F[0];
+        T[8] = qy * F[3];
+        T[9] = F[5];
+    }
+}
+
+template <int NB, bool ONE, bool FAST>
+__global__ void __launch_bounds__(CG_THREADS, 4) k_cg_slab(CgArgs a)
 {
     extern __shared__ __align__(16) uint32_t bits[];
-    const int nrow_all = (a.b2 + 2) * (a.b3 + 2);
-    int* cnt = reinterpret_cast<int*>(bits + (size_t)nrow_all * a.nw);
+    const int pl = a.b2 + 2;  // bit rows per slab plane
+    int* cnt = reinterpret_cast<int*>(bits + (size_t)pl * (a.b3 + 2) * a.nw);
     int* mixed = cnt + a.nc1;
     __shared__ int nmixed;
+    __shared__ uint32_t lut[LUT_N];
     const int slab = blockIdx.x;
     const int J = slab % a.nc2, K = slab / a.nc2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NWARP = CG_THREADS / 32;
-    if (threadIdx.x == 0) nmixed = 0;
-    load_rows<false>(a, bits, J, K);
-    __syncthreads();
-    // inclusion voxels per coarse voxel
     const int rows = a.b2 * a.b3;
-    for (int I = warp; I < a.nc1; I += NWARP) {
-        int s = 0;
-        for (int t = lane; t < rows; t += 32) {
-            const uint32_t* row = bits + lrow(t % a.b2, t / a.b2, a.b2) * a.nw;
-            for (int c0 = 0; c0 < a.b1; c0 += 32) s += __popc(ext(row, I * a.b1 + c0, min(32, a.b1 - c0)));
+    if (threadIdx.x == 0) nmixed = 0;
+    build_lut(lut);
+    load_rows(a, bits, J, K);
+    __syncthreads();
+
+    // inclusion voxels per coarse voxel: R consecutive lanes per coarse voxel,
+    // each summing the popcounts of every R-th fine row
+    {
+        const int R = a.R;
+        const int per = CG_THREADS / R;
+        for (int I0 = 0; I0 < a.nc1; I0 += per) {
+            const int I = I0 + (int)threadIdx.x / R, rg = threadIdx.x & (R - 1);
+            int s = 0;
+            if (I < a.nc1) {
+                int kk = fdiv(rg, a.b2, a.inv_b2), jj = rg - kk * a.b2;
+                const FastSpan fc = make_fast_span(a, I);
+                const Span c = make_span(a, I, 0);
+                for (int t = rg; t < rows; t += R) {
+                    const uint32_t* row = bits + lrow(jj, kk, a.b2) * a.nw;
+                    if (FAST)
+                        s += __popc(take_fast<ONE>(row, fc));
+                    else
+                        for (int x0 = 0; x0 < a.b1; x0 += 32)
+                            s += __popc(take(row + 1, x0 == 0 ? c : make_span(a, I, x0)));
+                    jj += a.Rr;
+                    kk += a.Rq;
+                    if (jj >= a.b2) {
+                        jj -= a.b2;
+                        kk++;
+                    }
+                }
+            }
+            for (int off = R >> 1; off >= 1; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+            if (I < a.nc1 && rg == 0) cnt[I] = s;
         }
-        s = __reduce_add_sync(0xFFFFFFFFu, s);
-        if (lane == 0) cnt[I] = s;
     }
     __syncthreads();
     const int nblock = a.b1 * a.b2 * a.b3;
@@ -311,66 +606,44 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_slab(CgArgs a)
     const int nm = nmixed;
     if (threadIdx.x == 0) a.slab_cnt[slab] = nm;
     if (nm == 0) return;
-    load_rows<true>(a, bits, J, K);
-    __syncthreads();
 
+    // integer moments: G lanes per boxel, every G-th fine row a lane
     const int G = a.G, gpw = 32 / G, g = lane / G, lg = lane & (G - 1);
+    const int rstride = pl * a.nw;  // one plane of bit rows
+    const int kk0 = fdiv(lg, a.b2, a.inv_b2), jj0 = lg - kk0 * a.b2;
     for (int mb = warp * gpw; mb < nm; mb += NWARP * gpw) {
         const int m = mb + g;
         const bool act = m < nm;
         const int I = act ? mixed[m] : 0;
         int acc[NACC];
+        if (FAST) {
+            // rows t = lg + G k: jj = jj0 for all of them (G % b2 == 0)
+            int f[NFAST];
 #pragma unroll
-        for (int k = 0; k < NACC; k++) acc[k] = 0;
-        if (act) {
-            for (int t = lg; t < rows; t += G) {
-                const int jj = t % a.b2, kk = t / a.b2;
-                const uint32_t* C = bits + lrow(jj, kk, a.b2) * a.nw;
-                const uint32_t* YM = bits + lrow(jj - 1, kk, a.b2) * a.nw;
-                const uint32_t* YP = bits + lrow(jj + 1, kk, a.b2) * a.nw;
-                const uint32_t* ZM = bits + lrow(jj, kk - 1, a.b2) * a.nw;
-                const uint32_t* ZP = bits + lrow(jj, kk + 1, a.b2) * a.nw;
-                const int qy = 2 * jj + 1 - a.b2, qz = 2 * kk + 1 - a.b3;
-                for (int c0 = 0; c0 < a.b1; c0 += 32) {
-                    const int L = min(32, a.b1 - c0), x = I * a.b1 + c0;
-                    const uint32_t W = ext(C, x, L);
-                    const uint32_t Wm = x > 0 ? ext(C, x - 1, L) : ((ext(C, 0, L - 1) << 1) | bit_at(C, a.n1 - 1));
-                    const uint32_t Wp =
-                        x + L < a.n1 ? ext(C, x + 1, L) : (ext(C, x + 1, L - 1) | (bit_at(C, 0) << (L - 1)));
-                    const uint32_t msk = L == 32 ? 0xFFFFFFFFu : ((1u << L) - 1u);
-                    const int o = 2 * c0 + 1 - a.b1;  // q = 2 i + o for bit i
-                    const int np = __popc(W);
-                    acc[0] += 2 * pos_sum(W) + o * np;
-                    acc[1] += qy * np;
-                    acc[2] += qz * np;
-                    const uint32_t e[6] = {(W ^ Wm) & msk, (W ^ Wp) & msk, W ^ ext(YM, x, L),
-                                           W ^ ext(YP, x, L),  W ^ ext(ZM, x, L), W ^ ext(ZP, x, L)};
+            for (int k = 0; k < NFAST; k++) f[k] = 0;
+            if (act) {
+                const FastSpan c = make_fast_span(a, I);
+                const uint32_t* R = bits + lrow(jj0, kk0, a.b2) * a.nw;
+                const int rstep = a.Gq * pl * a.nw;
+                for (int kk = kk0; kk < a.b3; kk += a.Gq, R += rstep)
+                    row_moments_fast<NB, ONE>(lut, c, R, a.nw, rstride, 2 * kk + 1 - a.b3, f);
+            }
+            expand_fast(f, 2 * jj0 + 1 - a.b2, acc);
+        } else {
 #pragma unroll
-                    for (int i = 0; i < 3; i++) {
-                        const int n = __popc(e[2 * i]) + __popc(e[2 * i + 1]);
-                        if (n == 0) continue;
-                        int s1 = 0, s2 = 0;
-#pragma unroll
-                        for (int h = 0; h < 2; h++) {
-                            uint32_t mm = e[2 * i + h];
-                            while (mm) {
-                                const int q = 2 * (__ffs(mm) - 1) + o;
-                                mm &= mm - 1u;
-                                s1 += q;
-                                s2 += q * q;
-                            }
-                        }
-                        int* T = acc + 3 + 10 * i;
-                        T[0] += n;
-                        T[1] += s1;
-                        T[2] += qy * n;
-                        T[3] += qz * n;
-                        T[4] += s2;
-                        T[5] += qy * s1;
-                        T[6] += qz * s1;
-                        T[7] += qy * qy * n;
-                        T[8] += qy * qz * n;
-                        T[9] += qz * qz * n;
+            for (int k = 0; k < NACC; k++) acc[k] = 0;
+            if (act) {
+                int jj = jj0, kk = kk0;
+                for (int t = lg; t < rows; t += G) {
+                    const uint32_t* C = bits + lrow(jj, kk, a.b2) * a.nw + 1;
+                    for (int x0 = 0; x0 < a.b1; x0 += 32)
+                        row_moments(a, lut, make_span(a, I, x0), C, rstride, 2 * jj + 1 - a.b2, 2 * kk + 1 - a.b3,
+                                    acc);
+                    jj += a.Gr;
+                    kk += a.Gq;
+                    if (jj >= a.b2) {
+                        jj -= a.b2;
+                        kk++;
                     }
                 }
             }
@@ -379,14 +652,50 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_slab(CgArgs a)
 #pragma unroll
             for (int k = 0; k < NACC; k++) acc[k] += __shfl_xor_sync(0xFFFFFFFFu, acc[k], off);
         if (act && lg == 0) {
-            double N[3];
-            boxel_result(a, acc, N);
-            const size_t ci = cbase + I;
-            a.sN[3 * ci + 0] = N[0];
-            a.sN[3 * ci + 1] = N[1];
-            a.sN[3 * ci + 2] = N[2];
-            a.sc[ci] = (double)cnt[I] / (double)nblock;
+            int4* dst = reinterpret_cast<int4*>(a.sums + (cbase + I) * NSUM);
+#pragma unroll
+            for (int k = 0; k < 8; k++) dst[k] = make_int4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+            dst[8] = make_int4(acc[32], cnt[I], 0, 0);
         }
+    }
+}
+
+using SlabKernel = void (*)(CgArgs);
+
+SlabKernel pick_slab_kernel(int n1, int b1, bool fast)
+{
+    if (!fast) return k_cg_slab<4, false, false>;
+    const bool one = 32 % b1 == 0;
+    if (b1 <= 8) return one ? k_cg_slab<1, true, true> : k_cg_slab<1, false, true>;
+    if (b1 <= 16) return one ? k_cg_slab<2, true, true> : k_cg_slab<2, false, true>;
+    return one ? k_cg_slab<4, true, true> : k_cg_slab<4, false, true>;
+}
+
+// the normals and c+ of the listed boxels, one boxel per thread
+__global__ void __launch_bounds__(FIN_THREADS) k_cg_finish(CgArgs a, const int64_t* total, int64_t cap,
+                                                           const int64_t* idx_out, double* N_out, double* c_out)
+{
+    const int64_t nb = min(*total, cap);
+    const int nblock = a.b1 * a.b2 * a.b3;
+    for (int64_t pos = blockIdx.x * (int64_t)FIN_THREADS + threadIdx.x; pos < nb;
+         pos += (int64_t)gridDim.x * FIN_THREADS) {
+        const int4* src = reinterpret_cast<const int4*>(a.sums + idx_out[pos] * NSUM);
+        int acc[NACC + 3];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const int4 v = src[k];
+            acc[4 * k] = v.x;
+            acc[4 * k + 1] = v.y;
+            acc[4 * k + 2] = v.z;
+            acc[4 * k + 3] = v.w;
+        }
+        double N[3];
+        boxel_finish(a, acc, N);
+        N_out[3 * pos + 0] = N[0];
+        N_out[3 * pos + 1] = N[1];
+        N_out[3 * pos + 2] = N[2];
+        const int npl = acc[NACC];
+        c_out[pos] = a.nblock_pow2 ? npl * a.inv_nblock : (double)npl / (double)nblock;
     }
 }
 
@@ -423,10 +732,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_cg_scan(const int* cnt, int ns
     if (threadIdx.x == SCAN_THREADS - 1) *total = run;
 }
 
-// compact the boxels of one slab into the output lists (increasing index)
+// the coarse indices of one slab's boxels into the output list (increasing)
 __global__ void __launch_bounds__(SCATTER_THREADS)
-    k_cg_scatter(const uint8_t* phase, const int* cnt, const int64_t* off, const double* sN, const double* sc,
-                 int nc1, int64_t cap, int64_t* idx_out, double* N_out, double* c_out)
+    k_cg_scatter(const uint8_t* phase, const int* cnt, const int64_t* off, int nc1, int64_t cap, int64_t* idx_out)
 {
     __shared__ int wtot[SCATTER_THREADS / 32];
     const int slab = blockIdx.x;
@@ -446,20 +754,21 @@ __global__ void __launch_bounds__(SCATTER_THREADS)
             all += wtot[w];
         }
         const int64_t pos = run + before + __popc(bal & ((1u << lane) - 1u));
-        if (f && pos < cap) {
-            const size_t ci = base + I;
-            idx_out[pos] = (int64_t)ci;
-            N_out[3 * pos + 0] = sN[3 * ci + 0];
-            N_out[3 * pos + 1] = sN[3 * ci + 1];
-            N_out[3 * pos + 2] = sN[3 * ci + 2];
-            c_out[pos] = sc[ci];
-        }
+        if (f && pos < cap) idx_out[pos] = (int64_t)(base + I);
         run += all;
         __syncthreads();
     }
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// event timing of the launches (combo_coarse_grain_profile)
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+int g_prof_dev = -1;
+cudaEvent_t g_prof_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+bool g_prof_have = false;
+double g_prof_ms[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 
 }  // namespace
 }  // namespace combo
@@ -504,16 +813,37 @@ extern "C" int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int3
     a.nc1 = n[0] / b[0];
     a.nc2 = n[1] / b[1];
     a.nc3 = n[2] / b[2];
-    a.nw = (a.n1 + 31) / 32 + 1;
+    a.nwr = (a.n1 + 31) / 32;
+    a.nw = a.nwr + 3;
     a.method = method;
     for (int j = 0; j < 3; j++) a.h[j] = h[j];
     a.r[0] = h[1] * h[2] / h[0];  // r_i = h_j h_k / h_i
     a.r[1] = h[0] * h[2] / h[1];
     a.r[2] = h[0] * h[1] / h[2];
     const int rows = a.b2 * a.b3;
+    // lanes per boxel: about eight fine rows a lane (fewer reduction levels);
+    // the fast path (n1 % 32 == 0, b1 <= 32, b2 a power of two <= 32) takes a
+    // multiple of b2 so that each lane keeps one y row offset
     int G = 1;
-    while (G < 32 && 4 * G < rows) G <<= 1;  // about four rows per lane
+    while (G < 32 && 16 * G <= rows) G <<= 1;
+    const bool b2pow2 = (a.b2 & (a.b2 - 1)) == 0 && a.b2 <= 32;
+    const bool fast = a.n1 % 32 == 0 && a.b1 <= 32 && b2pow2;
+    if (fast) G = std::max(G, a.b2);
     a.G = G;
+    a.Gq = G / a.b2;
+    a.Gr = G % a.b2;
+    // lanes per coarse voxel in the count
+    int R = 1;
+    while (R < 32 && 2 * R * a.nc1 <= CG_THREADS && 2 * R <= rows) R <<= 1;
+    a.R = R;
+    a.Rq = R / a.b2;
+    a.Rr = R % a.b2;
+    a.inv_b2 = 1.0f / (float)a.b2;
+    a.inv_nw = 1.0f / (float)a.nw;
+    a.inv_pl = 1.0f / (float)(a.b2 + 2);
+    a.iso = h[0] == h[1] && h[1] == h[2];
+    a.nblock_pow2 = (nblock & (nblock - 1)) == 0;
+    a.inv_nblock = 1.0 / (double)nblock;
     const size_t smem = (size_t)(a.b2 + 2) * (a.b3 + 2) * a.nw * 4 + (size_t)8 * a.nc1;
     if (smem > CG_SMEM_MAX)
         return set_error(COMBO_E_INVALID_ARG, "combo_coarse_grain: slab rows exceed the shared-memory limit");
@@ -524,7 +854,7 @@ extern "C" int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int3
     CGK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
 
-    // scratch: [chi copy] [phase] slab_cnt slab_off total sN sc [idx N c]
+    // scratch: [chi copy] [phase] slab_cnt slab_off total sums [idx N c]
     size_t o_chi = 0, sz = 0;
     if (!dev) sz += align256(V);
     const size_t o_phase = sz;
@@ -535,10 +865,11 @@ extern "C" int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int3
     sz += align256(8 * (size_t)nslab);
     const size_t o_tot = sz;
     sz += 256;
-    const size_t o_sN = sz;
-    sz += align256(24 * nc);
-    const size_t o_sc = sz;
-    sz += align256(8 * nc);
+    const size_t o_sums = sz;
+    sz += align256(4 * NSUM * nc);
+    const size_t nwr = (size_t)a.nwr;
+    const size_t o_bits = sz;
+    sz += align256(4 * nwr * (size_t)n[1] * n[2]);
     const int64_t ncap = std::min<int64_t>(cap, (int64_t)nc);
     const size_t o_out = sz;
     if (!dev) sz += align256(40 * (size_t)std::max<int64_t>(ncap, 1));
@@ -555,20 +886,21 @@ extern "C" int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int3
         ctx->scratch_bytes = sz;
     }
     char* S = static_cast<char*>(ctx->scratch);
+    const uint8_t* d_chi = chi;
     if (!dev) {
         CGK(cudaMemcpyAsync(S + o_chi, chi, V, cudaMemcpyHostToDevice, st));
-        a.chi = reinterpret_cast<const uint8_t*>(S + o_chi);
+        d_chi = reinterpret_cast<const uint8_t*>(S + o_chi);
         a.phase = reinterpret_cast<uint8_t*>(S + o_phase);
     } else {
-        a.chi = chi;
         a.phase = phase_out;
     }
-    a.vec = (a.n1 % 32 == 0) && ((reinterpret_cast<uintptr_t>(a.chi) & 15) == 0);
+    uint32_t* d_bits = reinterpret_cast<uint32_t*>(S + o_bits);
+    a.bitimg = d_bits;
+    const bool vec = (a.n1 % 32 == 0) && ((reinterpret_cast<uintptr_t>(d_chi) & 15) == 0);
     a.slab_cnt = reinterpret_cast<int*>(S + o_cnt);
     int64_t* d_off = reinterpret_cast<int64_t*>(S + o_off);
     int64_t* d_tot = reinterpret_cast<int64_t*>(S + o_tot);
-    a.sN = reinterpret_cast<double*>(S + o_sN);
-    a.sc = reinterpret_cast<double*>(S + o_sc);
+    a.sums = reinterpret_cast<int*>(S + o_sums);
     int64_t* oi = idx_out;
     double* oN = N_out;
     double* oc = c_out;
@@ -577,17 +909,60 @@ extern "C" int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int3
         oN = reinterpret_cast<double*>(S + o_out + 8 * (size_t)std::max<int64_t>(ncap, 1));
         oc = reinterpret_cast<double*>(S + o_out + 32 * (size_t)std::max<int64_t>(ncap, 1));
     }
-    CGK(cudaFuncSetAttribute(k_cg_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
-    k_cg_slab<<<nslab, CG_THREADS, smem, st>>>(a);
+    const SlabKernel slab_kernel = pick_slab_kernel(a.n1, a.b1, fast);
+    CGK(cudaFuncSetAttribute(slab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
+    std::unique_lock<std::mutex> plock(g_prof_mu);
+    const bool prof = g_prof_on;
+    if (prof && g_prof_dev != ctx->device) {
+        for (auto& e : g_prof_ev)
+            if (e) cudaEventDestroy(e), e = nullptr;
+        for (auto& e : g_prof_ev) CGK(cudaEventCreate(&e));
+        g_prof_dev = ctx->device;
+    }
+    if (!prof) plock.unlock();
+    if (prof) CGK(cudaEventRecord(g_prof_ev[0], st));
+    {
+        const int64_t nrows = (int64_t)n[1] * n[2];
+        if (vec) {
+            const int64_t nwords = nrows * (int64_t)nwr;
+            const int64_t per = (int64_t)PACK_THREADS * PACK_UNROLL;
+            const int grid = (int)std::min<int64_t>((nwords + per - 1) / per, 152 * 32);
+            k_cg_pack_vec<<<grid, PACK_THREADS, 0, st>>>(d_chi, nwords, d_bits);
+        } else {
+            const int64_t nwords = nrows * (int64_t)nwr;
+            const int grid = (int)std::min<int64_t>((nwords + 7) / 8, 152 * 32);
+            k_cg_pack_bytes<<<grid, PACK_THREADS, 0, st>>>(d_chi, a.n1, (int)nwr, nrows, d_bits);
+        }
+        CGK(cudaGetLastError());
+    }
+    if (prof) CGK(cudaEventRecord(g_prof_ev[1], st));
+    slab_kernel<<<nslab, CG_THREADS, smem, st>>>(a);
     CGK(cudaGetLastError());
+    if (prof) CGK(cudaEventRecord(g_prof_ev[2], st));
     k_cg_scan<<<1, SCAN_THREADS, 0, st>>>(a.slab_cnt, nslab, d_off, d_tot);
     CGK(cudaGetLastError());
-    k_cg_scatter<<<nslab, SCATTER_THREADS, 0, st>>>(a.phase, a.slab_cnt, d_off, a.sN, a.sc, a.nc1, ncap, oi, oN,
-                                                    oc);
+    if (prof) CGK(cudaEventRecord(g_prof_ev[3], st));
+    k_cg_scatter<<<nslab, SCATTER_THREADS, 0, st>>>(a.phase, a.slab_cnt, d_off, a.nc1, ncap, oi);
     CGK(cudaGetLastError());
+    if (prof) CGK(cudaEventRecord(g_prof_ev[4], st));
+    if (ncap > 0) {
+        const int fin_grid = (int)std::min<int64_t>((ncap + FIN_THREADS - 1) / FIN_THREADS, 152 * 8);
+        k_cg_finish<<<fin_grid, FIN_THREADS, 0, st>>>(a, d_tot, ncap, oi, oN, oc);
+        CGK(cudaGetLastError());
+    }
+    if (prof) CGK(cudaEventRecord(g_prof_ev[5], st));
     int64_t total = 0;
     CGK(cudaMemcpyAsync(&total, d_tot, 8, cudaMemcpyDeviceToHost, st));
     CGK(cudaStreamSynchronize(st));
+    if (prof) {
+        float t = 0.f;
+        for (int k = 0; k < 5; k++) {
+            CGK(cudaEventElapsedTime(&t, g_prof_ev[k], g_prof_ev[k + 1]));
+            g_prof_ms[k] = t;
+        }
+        g_prof_have = true;
+        plock.unlock();
+    }
     *n_boxels = total;
     if (!dev) {
         const int64_t k = std::min<int64_t>(total, ncap);
@@ -599,5 +974,20 @@ extern "C" int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int3
         }
         CGK(cudaStreamSynchronize(st));
     }
+    return COMBO_OK;
+}
+
+extern "C" int combo_coarse_grain_profile(int32_t enable)
+{
+    std::lock_guard<std::mutex> l(g_prof_mu);
+    g_prof_on = enable != 0;
+    return COMBO_OK;
+}
+
+extern "C" int combo_coarse_grain_profile_read(double ms[5])
+{
+    std::lock_guard<std::mutex> l(g_prof_mu);
+    if (!ms || !g_prof_have) return set_error(COMBO_E_INVALID_ARG, "combo_coarse_grain_profile_read: nothing recorded");
+    for (int k = 0; k < 5; k++) ms[k] = g_prof_ms[k];
     return COMBO_OK;
 }

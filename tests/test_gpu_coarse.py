@@ -127,6 +127,10 @@ CASES = [
     ((2, 2, 2), (2, 1, 1), (1.0, 1.0, 1.0), "noise"),         # 2-voxel axes
     ((1, 4, 4), (1, 2, 2), (1.0, 1.0, 1.0), "noise"),         # 1-voxel axis
     ((64, 64, 64), (4, 4, 4), (1.0, 1.0, 1.0), "noise"),      # every coarse voxel a boxel
+    ((96, 64, 48), (12, 8, 6), (1.0, 1.0, 1.0), "spheres"),   # fast path, spans across words
+    ((128, 32, 24), (16, 16, 3), (1.0, 0.5, 2.0), "spheres"), # fast path, two table bytes
+    ((96, 16, 16), (24, 2, 4), (1.0, 1.0, 1.0), "noise"),     # fast path, four bytes across words
+    ((64, 8, 8), (1, 1, 1), (1.0, 1.0, 1.0), "noise"),        # one fine voxel per coarse voxel
 ]
 
 
