@@ -57,17 +57,19 @@ constexpr int NACC = 33;
 constexpr int NSUM = 36;
 
 struct CgArgs {
-    const uint32_t* bitimg;  // [n3][n2][nw - 1] bit rows of the image
+    const uint32_t* bitimg;  // [n3][n2][nw] bit rows of the image (padded rows)
+    const uint32_t* glut;    // byte tables of bit-position sums
     int n1, n2, n3;
     int b1, b2, b3;
     int nc1, nc2, nc3;
     int nwr;     // words per fine row: ceil(n1 / 32)
-    int nw;      // words per shared-memory bit row: nwr + 3 (pads)
+    int nw;      // words per padded bit row: nwr + 3 rounded up to a multiple of 4
     int G;       // lanes per composite boxel (power of two, <= 32): G = Gq b2 + Gr
     int Gq, Gr;
     int R;       // lanes per coarse voxel in the count (power of two, <= 32): R = Rq b2 + Rr
     int Rq, Rr;
-    float inv_b2, inv_pl, inv_nw;  // reciprocals for the divisions in the loops
+    int NGq, NGr;  // column count: row groups NG = NGq b2 + NGr
+    float inv_b2, inv_per, inv_nw4, inv_nwr;  // reciprocals for the divisions in the loops
     int method;  // COMBO_NORMAL_LAPLACE / COMBO_NORMAL_KABEL
     int iso;     // h1 == h2 == h3: the moments combine exactly in int64
     int nblock_pow2;  // b1 b2 b3 a power of two: c+ = count * inv_nblock exactly
@@ -107,89 +109,121 @@ __device__ __forceinline__ int fdiv(int v, int d, float inv)
     return q + (r >= d) - (r < 0);
 }
 
-// Pass 1: the binary image packed to bit rows, bitimg[(z n2 + y) nwr + w]
-// bit j = voxel (32 w + j, y, z), zero past n1.  With n1 % 32 == 0 the bit
-// rows are the flattened image packed 32 voxels a word: each thread reads
-// 2 x 16 bytes per word (four words in flight) and writes the word.
-constexpr int PACK_THREADS = 256;
-constexpr int PACK_UNROLL = 4;
+// Byte tables of bit-position sums.  lut[k][v] packs, for the set bits j of
+// the byte v taken as positions i = 8 k + j of a 32-bit mask, the count (bits
+// 0-6), sum i (bits 7-16) and sum i^2 (bits 17-31).  The fields of two
+// masks' sums still fit (count <= 64, sum i <= 992, sum i^2 <= 20832), so the
+// packed words of two masks add with one integer add.
+constexpr int LUT_N = 4 * 256;
 
-__global__ void __launch_bounds__(PACK_THREADS) k_cg_pack_vec(const uint8_t* chi, int64_t nwords, uint32_t* bitimg)
+__device__ void build_lut(uint32_t* lut)
 {
-    const int64_t stride = (int64_t)gridDim.x * PACK_THREADS * PACK_UNROLL;
-    for (int64_t base = (int64_t)blockIdx.x * PACK_THREADS * PACK_UNROLL + threadIdx.x; base < nwords;
-         base += stride) {
-        uint4 v[2 * PACK_UNROLL];
-#pragma unroll
-        for (int k = 0; k < PACK_UNROLL; k++) {
-            const int64_t gw = base + (int64_t)k * PACK_THREADS;
-            const uint4* src = reinterpret_cast<const uint4*>(chi + 32 * gw);
-            v[2 * k] = gw < nwords ? __ldcs(src) : make_uint4(0u, 0u, 0u, 0u);
-            v[2 * k + 1] = gw < nwords ? __ldcs(src + 1) : make_uint4(0u, 0u, 0u, 0u);
-        }
-#pragma unroll
-        for (int k = 0; k < PACK_UNROLL; k++) {
-            const int64_t gw = base + (int64_t)k * PACK_THREADS;
-            if (gw < nwords) bitimg[gw] = pack16(v[2 * k]) | (pack16(v[2 * k + 1]) << 16);
+    for (int e = threadIdx.x; e < LUT_N; e += blockDim.x) {
+        const uint32_t k = e >> 8, v = e & 255;
+        // positions j of the set bits from the bit planes of j (0..7)
+        const uint32_t p0 = v & 0xAAu, p1 = v & 0xCCu, p2 = v & 0xF0u;
+        const uint32_t n = __popc(v);
+        const uint32_t sj = __popc(p0) + 2 * __popc(p1) + 4 * __popc(p2);
+        const uint32_t sjj = __popc(p0) + 4 * __popc(p1) + 16 * __popc(p2) + 4 * __popc(p0 & p1) +
+                             8 * __popc(p0 & p2) + 16 * __popc(p1 & p2);
+        // i = 8 k + j
+        const uint32_t si = 8 * k * n + sj, sii = 64 * k * k * n + 16 * k * sj + sjj;
+        lut[e] = n | (si << 7) | (sii << 17);
+    }
+}
+
+// Pass 1: the binary image packed to bit rows of nw words (nw a multiple of
+// four, >= nwr + 3, nwr = ceil(n1 / 32)): word 1 + w of row (y, z) holds bit
+// j = voxel (32 w + j, y, z), zero past n1; where n1 % 32 == 0, word 0 and
+// word nwr + 1 repeat the row's last and first words (the periodic x
+// neighbours of its two ends); the other words are zero.  Block 0 also
+// writes the byte tables.
+constexpr int PACK_THREADS = 256;
+
+__device__ __forceinline__ void put_word(uint32_t* dst, int w, int nwr, int nw, uint32_t m, bool wrapx)
+{
+    dst[1 + w] = m;
+    if (w == nwr - 1) dst[0] = wrapx ? m : 0u;
+    if (w == 0) {
+        dst[nwr + 1] = wrapx ? m : 0u;
+        for (int p = nwr + 2; p < nw; p++) dst[p] = 0u;
+    }
+}
+
+// n1 % 32 == 0, chi 16-byte aligned: a lane per word (two 16-byte loads),
+// 32 / nwr rows a warp step where a row has fewer than 32 words
+__global__ void __launch_bounds__(PACK_THREADS) k_cg_pack_vec(const uint8_t* chi, int n1, int nwr, int nw,
+                                                              int64_t nrows, uint32_t* bitimg, uint32_t* lut)
+{
+    if (blockIdx.x == 0) build_lut(lut);
+    const int lane = threadIdx.x & 31;
+    const int rpw = nwr <= 32 ? 32 / nwr : 1;
+    const int rs = nwr <= 32 ? lane / nwr : 0, w0 = nwr <= 32 ? lane - rs * nwr : lane;
+    const bool on = rs < rpw;
+    const int64_t nwarps = (int64_t)gridDim.x * (PACK_THREADS / 32);
+    for (int64_t r0 = ((int64_t)blockIdx.x * (PACK_THREADS / 32) + (threadIdx.x >> 5)) * rpw; r0 < nrows;
+         r0 += nwarps * rpw) {
+        const int64_t row = r0 + rs;
+        if (!on || row >= nrows) continue;
+        for (int w = w0; w < nwr; w += 32) {
+            const uint4* src = reinterpret_cast<const uint4*>(chi + row * n1 + 32 * w);
+            const uint4 a = __ldcs(src), b = __ldcs(src + 1);
+            put_word(bitimg + row * nw, w, nwr, nw, pack16(a) | (pack16(b) << 16), true);
         }
     }
 }
 
-// the same for any n1 and alignment: a warp per word, one byte a lane
-__global__ void __launch_bounds__(PACK_THREADS) k_cg_pack_bytes(const uint8_t* chi, int n1, int nwr, int64_t nrows,
-                                                                uint32_t* bitimg)
+// any n1 and alignment: a warp per row, one byte a lane
+__global__ void __launch_bounds__(PACK_THREADS) k_cg_pack_bytes(const uint8_t* chi, int n1, int nwr, int nw,
+                                                                int64_t nrows, uint32_t* bitimg, uint32_t* lut)
 {
+    if (blockIdx.x == 0) build_lut(lut);
     const int lane = threadIdx.x & 31;
-    const int64_t nwords = nrows * nwr;
-    const int64_t wstride = (int64_t)gridDim.x * (PACK_THREADS / 32);
-    for (int64_t gw = (int64_t)blockIdx.x * (PACK_THREADS / 32) + (threadIdx.x >> 5); gw < nwords; gw += wstride) {
-        const int64_t row = gw / nwr;
-        const int w = (int)(gw - row * nwr);
-        const int x = 32 * w + lane;
-        const uint8_t c = x < n1 ? __ldcs(chi + row * n1 + x) : (uint8_t)0;
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, c != 0);
-        if (lane == 0) bitimg[gw] = m;
+    const bool wrapx = (n1 & 31) == 0;
+    const int64_t nwarps = (int64_t)gridDim.x * (PACK_THREADS / 32);
+    for (int64_t row = (int64_t)blockIdx.x * (PACK_THREADS / 32) + (threadIdx.x >> 5); row < nrows; row += nwarps) {
+        for (int w = 0; w < nwr; w++) {
+            const int x = 32 * w + lane;
+            const uint8_t c = x < n1 ? __ldcs(chi + row * n1 + x) : (uint8_t)0;
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, c != 0);
+            if (lane == 0) put_word(bitimg + row * nw, w, nwr, nw, m, wrapx);
+        }
     }
 }
 
 // Pass 2 input: the slab's (b2 + 2)(b3 + 2) bit rows -- its own b2 b3 rows and
 // the one-voxel halo around them, periodic in y and z -- copied from the bit
-// image.  Slab-local row t holds (jj, kk) = (t mod (b2 + 2), t div (b2 + 2)) - 1
-// and takes nw = nwr + 3 words: word 1 + w is word w of the fine row; where
-// n1 % 32 == 0, word 0 and word nwr + 1 repeat the row's last and first words,
-// so the periodic x neighbours of the row's ends sit next to them; the other
-// pad words are zero.
-__device__ void load_rows(const CgArgs& a, uint32_t* bits, int J, int K)
+// image with 16-byte loads (row layout as in the bit image).  Slab-local row t
+// holds (jj, kk) = (t mod (b2 + 2), t div (b2 + 2)) - 1.  Also copies the byte
+// tables.
+__device__ void load_rows(const CgArgs& a, uint32_t* bits, uint32_t* lut, int J, int K)
 {
-    const int pl = a.b2 + 2;
-    const int nrows = pl * (a.b3 + 2);
-    const int nwr = a.nwr, nw = a.nw;
-    const bool aligned = (a.n1 & 31) == 0;
-    const int total = nrows * nw;
+    if (threadIdx.x < LUT_N / 4)
+        reinterpret_cast<uint4*>(lut)[threadIdx.x] = __ldg(reinterpret_cast<const uint4*>(a.glut) + threadIdx.x);
+    const int pl = a.b2 + 2, nw4 = a.nw >> 2;
+    const int per = pl * nw4;  // 16-byte words per plane of rows
+    const int total = (a.b3 + 2) * per;
+    const uint4* src = reinterpret_cast<const uint4*>(a.bitimg);
+    uint4* dst = reinterpret_cast<uint4*>(bits);
     constexpr int U = 4;
     for (int base = 0; base < total; base += U * CG_THREADS) {
-        uint32_t v[U];
-        int dst[U];
+        uint4 v[U];
+        int d[U];
 #pragma unroll
         for (int k = 0; k < U; k++) {
             const int it = base + k * CG_THREADS + (int)threadIdx.x;
-            dst[k] = -1;
-            v[k] = 0u;
+            d[k] = -1;
             if (it < total) {
-                const int t = fdiv(it, nw, a.inv_nw), u = it - t * nw;
-                const int gw = u == 0 ? (aligned ? nwr - 1 : -1)
-                                      : (u <= nwr ? u - 1 : (u == nwr + 1 && aligned ? 0 : -1));
-                if (gw >= 0) {
-                    const int k1 = fdiv(t, pl, a.inv_pl);
-                    const int y = wrap(J * a.b2 + (t - k1 * pl) - 1, a.n2), z = wrap(K * a.b3 + k1 - 1, a.n3);
-                    v[k] = __ldg(a.bitimg + ((size_t)z * a.n2 + y) * nwr + gw);
-                }
-                dst[k] = it;
+                const int pk = fdiv(it, per, a.inv_per), u = it - pk * per;
+                const int jr = fdiv(u, nw4, a.inv_nw4), q = u - jr * nw4;
+                const int y = wrap(J * a.b2 + jr - 1, a.n2), z = wrap(K * a.b3 + pk - 1, a.n3);
+                v[k] = __ldg(src + ((size_t)z * a.n2 + y) * nw4 + q);
+                d[k] = it;
             }
         }
 #pragma unroll
         for (int k = 0; k < U; k++)
-            if (dst[k] >= 0) bits[dst[k]] = v[k];
+            if (d[k] >= 0) dst[d[k]] = v[k];
     }
 }
 
@@ -225,29 +259,6 @@ __device__ __forceinline__ uint32_t take(const uint32_t* row, const Span& c)
 {
     if (c.one) return (row[c.w] >> c.s) & c.msk;
     return (uint32_t)((((uint64_t)row[c.w + 1] << 32) | row[c.w]) >> c.s) & c.msk;
-}
-
-// Byte tables of bit-position sums.  lut[k][v] packs, for the set bits j of
-// the byte v taken as positions i = 8 k + j of a 32-bit mask, the count (bits
-// 0-6), sum i (bits 7-16) and sum i^2 (bits 17-31).  The fields of two
-// masks' sums still fit (count <= 64, sum i <= 992, sum i^2 <= 20832), so the
-// packed words of two masks add with one integer add.
-constexpr int LUT_N = 4 * 256;
-
-__device__ void build_lut(uint32_t* lut)
-{
-    for (int e = threadIdx.x; e < LUT_N; e += CG_THREADS) {
-        const uint32_t k = e >> 8, v = e & 255;
-        // positions j of the set bits from the bit planes of j (0..7)
-        const uint32_t p0 = v & 0xAAu, p1 = v & 0xCCu, p2 = v & 0xF0u;
-        const uint32_t n = __popc(v);
-        const uint32_t sj = __popc(p0) + 2 * __popc(p1) + 4 * __popc(p2);
-        const uint32_t sjj = __popc(p0) + 4 * __popc(p1) + 16 * __popc(p2) + 4 * __popc(p0 & p1) +
-                             8 * __popc(p0 & p2) + 16 * __popc(p1 & p2);
-        // i = 8 k + j
-        const uint32_t si = 8 * k * n + sj, sii = 64 * k * k * n + 16 * k * sj + sjj;
-        lut[e] = n | (si << 7) | (sii << 17);
-    }
 }
 
 template <int NB> __device__ __forceinline__ uint32_t look(const uint32_t* lut, uint32_t m)
@@ -551,20 +562,70 @@ __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_slab(CgArgs a)
     int* cnt = reinterpret_cast<int*>(bits + (size_t)pl * (a.b3 + 2) * a.nw);
     int* mixed = cnt + a.nc1;
     __shared__ int nmixed;
-    __shared__ uint32_t lut[LUT_N];
+    __shared__ __align__(16) uint32_t lut[LUT_N];
     const int slab = blockIdx.x;
     const int J = slab % a.nc2, K = slab / a.nc2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NWARP = CG_THREADS / 32;
     const int rows = a.b2 * a.b3;
     if (threadIdx.x == 0) nmixed = 0;
-    build_lut(lut);
-    load_rows(a, bits, J, K);
+    // column counts (b1 = 8, 16, 32 on the fast path) accumulate with atomics
+    const bool colcount = FAST && ONE && a.b1 >= 8;
+    if (colcount)
+        for (int I = threadIdx.x; I < a.nc1; I += CG_THREADS) cnt[I] = 0;
+    load_rows(a, bits, lut, J, K);
     __syncthreads();
 
-    // inclusion voxels per coarse voxel: R consecutive lanes per coarse voxel,
-    // each summing the popcounts of every R-th fine row
-    {
+    // inclusion voxels per coarse voxel
+    if (colcount) {
+        // a thread per (word column w, row group g): byte-wise popcounts of the
+        // words, summed over every NG-th row in packed bytes (flushed before a
+        // byte can overflow), then added to the word's 32 / b1 coarse voxels
+        const int NG = a.NGq * a.b2 + a.NGr;
+        for (int it = threadIdx.x; it < a.nwr * NG; it += CG_THREADS) {
+            const int g = fdiv(it, a.nwr, a.inv_nwr), w = it - g * a.nwr;
+            int kk = fdiv(g, a.b2, a.inv_b2), jj = g - kk * a.b2;
+            uint32_t packed = 0;
+            int c0 = 0, c1 = 0, c2 = 0, c3 = 0, nrow = 0;
+            for (int r = g; r < rows; r += NG) {
+                uint32_t x = bits[lrow(jj, kk, a.b2) * a.nw + 1 + w];
+                x = x - ((x >> 1) & 0x55555555u);
+                x = (x & 0x33333333u) + ((x >> 2) & 0x33333333u);
+                packed += (x + (x >> 4)) & 0x0F0F0F0Fu;
+                if (++nrow == 31) {
+                    c0 += packed & 255u;
+                    c1 += packed >> 8 & 255u;
+                    c2 += packed >> 16 & 255u;
+                    c3 += packed >> 24;
+                    packed = 0;
+                    nrow = 0;
+                }
+                jj += a.NGr;
+                kk += a.NGq;
+                if (jj >= a.b2) {
+                    jj -= a.b2;
+                    kk++;
+                }
+            }
+            c0 += packed & 255u;
+            c1 += packed >> 8 & 255u;
+            c2 += packed >> 16 & 255u;
+            c3 += packed >> 24;
+            if (a.b1 == 8) {
+                if (c0) atomicAdd(&cnt[4 * w], c0);
+                if (c1) atomicAdd(&cnt[4 * w + 1], c1);
+                if (c2) atomicAdd(&cnt[4 * w + 2], c2);
+                if (c3) atomicAdd(&cnt[4 * w + 3], c3);
+            } else if (a.b1 == 16) {
+                if (c0 + c1) atomicAdd(&cnt[2 * w], c0 + c1);
+                if (c2 + c3) atomicAdd(&cnt[2 * w + 1], c2 + c3);
+            } else if (c0 + c1 + c2 + c3) {
+                atomicAdd(&cnt[w], c0 + c1 + c2 + c3);
+            }
+        }
+    } else {
+        // R consecutive lanes per coarse voxel, each summing the popcounts of
+        // every R-th fine row
         const int R = a.R;
         const int per = CG_THREADS / R;
         for (int I0 = 0; I0 < a.nc1; I0 += per) {
@@ -814,7 +875,7 @@ extern "C" int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int3
     a.nc2 = n[1] / b[1];
     a.nc3 = n[2] / b[2];
     a.nwr = (a.n1 + 31) / 32;
-    a.nw = a.nwr + 3;
+    a.nw = (a.nwr + 3 + 3) & ~3;
     a.method = method;
     for (int j = 0; j < 3; j++) a.h[j] = h[j];
     a.r[0] = h[1] * h[2] / h[0];  // r_i = h_j h_k / h_i
@@ -839,8 +900,14 @@ extern "C" int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int3
     a.Rq = R / a.b2;
     a.Rr = R % a.b2;
     a.inv_b2 = 1.0f / (float)a.b2;
-    a.inv_nw = 1.0f / (float)a.nw;
-    a.inv_pl = 1.0f / (float)(a.b2 + 2);
+    a.inv_per = 1.0f / (float)((a.b2 + 2) * (a.nw / 4));
+    a.inv_nw4 = 1.0f / (float)(a.nw / 4);
+    a.inv_nwr = 1.0f / (float)a.nwr;
+    {
+        const int NG = std::max(1, CG_THREADS / a.nwr);
+        a.NGq = NG / a.b2;
+        a.NGr = NG % a.b2;
+    }
     a.iso = h[0] == h[1] && h[1] == h[2];
     a.nblock_pow2 = (nblock & (nblock - 1)) == 0;
     a.inv_nblock = 1.0 / (double)nblock;
@@ -869,7 +936,9 @@ extern "C" int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int3
     sz += align256(4 * NSUM * nc);
     const size_t nwr = (size_t)a.nwr;
     const size_t o_bits = sz;
-    sz += align256(4 * nwr * (size_t)n[1] * n[2]);
+    sz += align256(4 * (size_t)a.nw * (size_t)n[1] * n[2]);
+    const size_t o_lut = sz;
+    sz += align256(4 * LUT_N);
     const int64_t ncap = std::min<int64_t>(cap, (int64_t)nc);
     const size_t o_out = sz;
     if (!dev) sz += align256(40 * (size_t)std::max<int64_t>(ncap, 1));
@@ -895,7 +964,9 @@ extern "C" int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int3
         a.phase = phase_out;
     }
     uint32_t* d_bits = reinterpret_cast<uint32_t*>(S + o_bits);
+    uint32_t* d_lut = reinterpret_cast<uint32_t*>(S + o_lut);
     a.bitimg = d_bits;
+    a.glut = d_lut;
     const bool vec = (a.n1 % 32 == 0) && ((reinterpret_cast<uintptr_t>(d_chi) & 15) == 0);
     a.slab_cnt = reinterpret_cast<int*>(S + o_cnt);
     int64_t* d_off = reinterpret_cast<int64_t*>(S + o_off);
@@ -923,16 +994,13 @@ extern "C" int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int3
     if (prof) CGK(cudaEventRecord(g_prof_ev[0], st));
     {
         const int64_t nrows = (int64_t)n[1] * n[2];
-        if (vec) {
-            const int64_t nwords = nrows * (int64_t)nwr;
-            const int64_t per = (int64_t)PACK_THREADS * PACK_UNROLL;
-            const int grid = (int)std::min<int64_t>((nwords + per - 1) / per, 152 * 32);
-            k_cg_pack_vec<<<grid, PACK_THREADS, 0, st>>>(d_chi, nwords, d_bits);
-        } else {
-            const int64_t nwords = nrows * (int64_t)nwr;
-            const int grid = (int)std::min<int64_t>((nwords + 7) / 8, 152 * 32);
-            k_cg_pack_bytes<<<grid, PACK_THREADS, 0, st>>>(d_chi, a.n1, (int)nwr, nrows, d_bits);
-        }
+        const int rpw = a.nwr <= 32 ? 32 / a.nwr : 1;
+        const int64_t warps = vec ? (nrows + rpw - 1) / rpw : nrows;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 152 * 16));
+        if (vec)
+            k_cg_pack_vec<<<grid, PACK_THREADS, 0, st>>>(d_chi, a.n1, a.nwr, a.nw, nrows, d_bits, d_lut);
+        else
+            k_cg_pack_bytes<<<grid, PACK_THREADS, 0, st>>>(d_chi, a.n1, a.nwr, a.nw, nrows, d_bits, d_lut);
         CGK(cudaGetLastError());
     }
     if (prof) CGK(cudaEventRecord(g_prof_ev[1], st));
