@@ -580,11 +580,40 @@ def normals_bench(combo, ctx, stream, peak, peak_kind, cpu=True, reps=20):
             out[name]["cpu_baseline"] = {"value": V / dt, "unit": "fine voxels/s", "cores": 1, "kind": "oracle",
                                          "sample": "the whole 256^3 image, one pass"}
     combo.coarse_grain_profile(False)
+    out["sphere_table1"] = sphere_table1(combo, ctx)
     out["note"] = ("ms_call: events around the whole call (five launches, the count's copy back and the "
                    "call's host synchronisation); ms_pack/slab/scan/scatter/finish: library events around each "
                    "launch; fine_voxels_per_s from their sum")
     out["gpu_launches"] = launches
     return out
+
+
+def sphere_table1(combo, ctx):
+    """Sec. 6.2: Pbar errors (%) of ComBo discretisations of the 256^3 ball
+    (Sec. 5 normals and barycentre normals) against the 256^3 rotated-scheme
+    reference, beside the paper's printed Table tab:ex:sphere:P1."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "sphere_table1.json")))
+    t0 = time.perf_counter()
+    ref = combo.solve(ms.sphere_e1_fine(256, 5), ctx=ctx, fields=False, precision=combo.FP32_REFINED_DF, tol=1e-9)
+    t_ref = time.perf_counter() - t0
+    Pref = ref["Pbar"][-1]
+    chi = ms.fine_ball_image(256, 0.4)
+    rows = {}
+    for key, (pk, pl) in gold["rows"].items():
+        b = tuple(256 // int(v) for v in key.split("x"))
+        row = {"paper_kabel": pk, "paper_sec5": pl}
+        for meth, name in (("kabel", "kabel"), ("laplace", "sec5")):
+            ph, idx, c, N, nb = combo.coarse_grain(chi, b, method=meth, ctx=ctx)
+            r = combo.solve(ms.sphere_e1_coarse(ph, idx, c, N, 5), ctx=ctx, fields=False, precision=combo.FP64,
+                            tol=1e-10)
+            row[name] = 100.0 * float(np.linalg.norm(r["Pbar"][-1] - Pref) / np.linalg.norm(Pref))
+            row["boxels"] = int(nb)
+        rows[key] = row
+    return {"rows": rows, "unit": "% Pbar error", "reference_seconds": t_ref,
+            "reference": "256^3 ball, rotated scheme, 5 load steps, refined double-float, tol 1e-9",
+            "coarse": "combo_coarse_grain + FP64 ComBo solve, 5 load steps, tol 1e-10"}
 
 
 def run_reference(args, rank, world):

@@ -161,14 +161,30 @@ __global__ void __launch_bounds__(PACK_THREADS) k_cg_pack_vec(const uint8_t* chi
     const int rs = nwr <= 32 ? lane / nwr : 0, w0 = nwr <= 32 ? lane - rs * nwr : lane;
     const bool on = rs < rpw;
     const int64_t nwarps = (int64_t)gridDim.x * (PACK_THREADS / 32);
+    const int64_t step = nwarps * rpw;
+    // four rows a lane per step: eight 16-byte loads in flight
+    constexpr int RU = 4;
     for (int64_t r0 = ((int64_t)blockIdx.x * (PACK_THREADS / 32) + (threadIdx.x >> 5)) * rpw; r0 < nrows;
-         r0 += nwarps * rpw) {
-        const int64_t row = r0 + rs;
-        if (!on || row >= nrows) continue;
+         r0 += RU * step) {
         for (int w = w0; w < nwr; w += 32) {
-            const uint4* src = reinterpret_cast<const uint4*>(chi + row * n1 + 32 * w);
-            const uint4 a = __ldcs(src), b = __ldcs(src + 1);
-            put_word(bitimg + row * nw, w, nwr, nw, pack16(a) | (pack16(b) << 16), true);
+            uint4 v[2 * RU];
+#pragma unroll
+            for (int k = 0; k < RU; k++) {
+                const int64_t row = r0 + k * step + rs;
+                v[2 * k] = make_uint4(0u, 0u, 0u, 0u);
+                v[2 * k + 1] = v[2 * k];
+                if (on && row < nrows) {
+                    const uint4* src = reinterpret_cast<const uint4*>(chi + row * n1 + 32 * w);
+                    v[2 * k] = __ldcs(src);
+                    v[2 * k + 1] = __ldcs(src + 1);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RU; k++) {
+                const int64_t row = r0 + k * step + rs;
+                if (on && row < nrows)
+                    put_word(bitimg + row * nw, w, nwr, nw, pack16(v[2 * k]) | (pack16(v[2 * k + 1]) << 16), true);
+            }
         }
     }
 }
@@ -285,13 +301,14 @@ template <int NB> __device__ __forceinline__ uint32_t look(const uint32_t* lut, 
 // convergence, one step from an FP32 start except where the two smallest
 // eigenvalues are close (then two).  FP64 is the scarce pipe on this GPU,
 // so the FP64 part is a few dozen operations.
-__device__ void min_eigvec(const double K[6], double N[3])
+__device__ void min_eigvec(const double K[6], const float Kf[6], double N[3])
 {
-    const double tr = K[0] + K[3] + K[5];
-    const double sc = tr > 0.0 ? 1.0 / tr : 1.0;
-    float a[3][3] = {{(float)(K[0] * sc), (float)(K[1] * sc), (float)(K[2] * sc)},
-                     {(float)(K[1] * sc), (float)(K[3] * sc), (float)(K[4] * sc)},
-                     {(float)(K[2] * sc), (float)(K[4] * sc), (float)(K[5] * sc)}};
+    // Kf: K rounded to FP32 (any positive multiple), scaled to unit trace
+    const float trf = Kf[0] + Kf[3] + Kf[5];
+    const float sc = trf > 0.f ? 1.f / trf : 1.f;
+    float a[3][3] = {{Kf[0] * sc, Kf[1] * sc, Kf[2] * sc},
+                     {Kf[1] * sc, Kf[3] * sc, Kf[4] * sc},
+                     {Kf[2] * sc, Kf[4] * sc, Kf[5] * sc}};
     float V[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
     for (int sweep = 0; sweep < 8; sweep++) {
         bool rotated = false;
@@ -328,18 +345,20 @@ __device__ void min_eigvec(const double K[6], double N[3])
     const int k = (d0 <= d1 && d0 <= d2) ? 0 : (d1 <= d2 ? 1 : 2);
     const float lo = k == 0 ? d0 : (k == 1 ? d1 : d2);
     const float mid = k == 0 ? fminf(d1, d2) : (k == 1 ? fminf(d0, d2) : fminf(d0, d1));
+    // the FP32 start: a unit vector to FP32 rounding
     double v[3];
 #pragma unroll
     for (int i = 0; i < 3; i++) v[i] = (double)(k == 0 ? V[i][0] : (k == 1 ? V[i][1] : V[i][2]));
-    double nv = rsqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-#pragma unroll
-    for (int i = 0; i < 3; i++) v[i] *= nv;
+    double nv;
     const int steps = (mid - lo) < 1e-3f ? 2 : 1;
     for (int it = 0; it < steps; it++) {
         const double kv0 = K[0] * v[0] + K[1] * v[1] + K[2] * v[2];
         const double kv1 = K[1] * v[0] + K[3] * v[1] + K[4] * v[2];
         const double kv2 = K[2] * v[0] + K[4] * v[1] + K[5] * v[2];
-        const double sg = v[0] * kv0 + v[1] * kv1 + v[2] * kv2;  // Rayleigh quotient (|v| = 1)
+        // Rayleigh quotient v^T K v / v^T v, with 1 / (1 + d) ~ 1 - d for the
+        // FP32-sized d = v^T v - 1 (second-order error ~ 1e-15)
+        const double vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        const double sg = (v[0] * kv0 + v[1] * kv1 + v[2] * kv2) * (2.0 - vv);
         const double A00 = K[0] - sg, A11 = K[3] - sg, A22 = K[5] - sg, A01 = K[1], A02 = K[2], A12 = K[4];
         const double C00 = A11 * A22 - A12 * A12, C11 = A00 * A22 - A02 * A02, C22 = A00 * A11 - A01 * A01;
         const double C01 = A02 * A12 - A01 * A22, C02 = A01 * A12 - A02 * A11, C12 = A01 * A02 - A00 * A12;
@@ -347,7 +366,13 @@ __device__ void min_eigvec(const double K[6], double N[3])
         const double y1 = C01 * v[0] + C11 * v[1] + C12 * v[2];
         const double y2 = C02 * v[0] + C12 * v[1] + C22 * v[2];
         const double ny = y0 * y0 + y1 * y1 + y2 * y2;
-        if (!(ny > 0.0) || !isfinite(ny)) break;  // v already spans a multiple eigenvalue
+        if (!(ny > 0.0) || !isfinite(ny)) {  // v already spans a multiple eigenvalue
+            nv = rsqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            v[0] *= nv;
+            v[1] *= nv;
+            v[2] *= nv;
+            break;
+        }
         nv = rsqrt(ny);
         v[0] = y0 * nv;
         v[1] = y1 * nv;
@@ -375,6 +400,7 @@ __device__ void boxel_finish(const CgArgs& a, const int* acc, double* N)
     // K = 4 S0 M = (h_c h_d) (S0 U2_cd - U1_c U1_d), U = sum_i r_i T_i, a
     // positive multiple of M with the same eigenvectors
     double K[6];
+    float Kf[6];
     const int ci[6] = {0, 0, 0, 1, 1, 2}, di[6] = {0, 1, 2, 1, 2, 2};
     if (a.iso) {
         // equal r_i and h_c: K is h^4 r^2 (T0 T2 - T1 T1^T), exact in int64
@@ -389,7 +415,11 @@ __device__ void boxel_finish(const CgArgs& a, const int* acc, double* N)
             for (int c = 0; c < 6; c++) T2[c] += T[4 + c];
         }
 #pragma unroll
-        for (int c = 0; c < 6; c++) K[c] = (double)(T0 * T2[c] - T1[ci[c]] * T1[di[c]]);
+        for (int c = 0; c < 6; c++) {
+            const int64_t D = T0 * T2[c] - T1[ci[c]] * T1[di[c]];
+            K[c] = (double)D;
+            Kf[c] = (float)D;
+        }
     } else {
         double S0 = 0.0, U1[3] = {0.0, 0.0, 0.0}, U2[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
@@ -403,9 +433,12 @@ __device__ void boxel_finish(const CgArgs& a, const int* acc, double* N)
             for (int c = 0; c < 6; c++) U2[c] += ri * T[4 + c];
         }
 #pragma unroll
-        for (int c = 0; c < 6; c++) K[c] = (a.h[ci[c]] * a.h[di[c]]) * (S0 * U2[c] - U1[ci[c]] * U1[di[c]]);
+        for (int c = 0; c < 6; c++) {
+            K[c] = (a.h[ci[c]] * a.h[di[c]]) * (S0 * U2[c] - U1[ci[c]] * U1[di[c]]);
+            Kf[c] = (float)K[c];
+        }
     }
-    min_eigvec(K, N);
+    min_eigvec(K, Kf, N);
     // Eq. normal:flip: keep N only where it agrees with the barycentre normal
     if (!(d0 * N[0] + d1 * N[1] + d2 * N[2] > 0.0)) {
         N[0] = -N[0];
@@ -760,64 +793,60 @@ __global__ void __launch_bounds__(FIN_THREADS) k_cg_finish(CgArgs a, const int64
     }
 }
 
-// exclusive scan of the per-slab boxel counts (one CTA)
+// exclusive scan of the per-slab boxel counts (one CTA, coalesced chunks)
 __global__ void __launch_bounds__(SCAN_THREADS) k_cg_scan(const int* cnt, int nslab, int64_t* off, int64_t* total)
 {
     __shared__ int64_t wsum[SCAN_THREADS / 32];
-    const int per = (nslab + SCAN_THREADS - 1) / SCAN_THREADS;
-    const int s0 = threadIdx.x * per, s1 = min(nslab, s0 + per);
-    int64_t mine = 0;
-    for (int s = s0; s < s1; s++) mine += cnt[s];
+    __shared__ int64_t carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int64_t incl = mine;
-    for (int d = 1; d < 32; d <<= 1) {
-        const int64_t v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if (lane >= d) incl += v;
-    }
-    if (lane == 31) wsum[warp] = incl;
+    if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    if (warp == 0) {
-        int64_t w = wsum[lane];
+    for (int base = 0; base < nslab; base += SCAN_THREADS) {
+        const int s = base + threadIdx.x;
+        const int64_t v = s < nslab ? cnt[s] : 0;
+        int64_t incl = v;
         for (int d = 1; d < 32; d <<= 1) {
-            const int64_t v = __shfl_up_sync(0xFFFFFFFFu, w, d);
-            if (lane >= d) w += v;
+            const int64_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (lane >= d) incl += t;
         }
-        wsum[lane] = w;  // inclusive over warps
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = wsum[lane];
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t t = __shfl_up_sync(0xFFFFFFFFu, w, d);
+                if (lane >= d) w += t;
+            }
+            wsum[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        const int64_t excl = carry + incl - v + (warp > 0 ? wsum[warp - 1] : 0);
+        if (s < nslab) off[s] = excl;
+        __syncthreads();  // every thread has read carry
+        if (threadIdx.x == SCAN_THREADS - 1) carry = excl + v;
+        __syncthreads();
     }
-    __syncthreads();
-    int64_t run = incl - mine + (warp > 0 ? wsum[warp - 1] : 0);
-    for (int s = s0; s < s1; s++) {
-        off[s] = run;
-        run += cnt[s];
-    }
-    if (threadIdx.x == SCAN_THREADS - 1) *total = run;
+    if (threadIdx.x == 0) *total = carry;
 }
 
-// the coarse indices of one slab's boxels into the output list (increasing)
+// the coarse indices of each slab's boxels into the output list (increasing):
+// a warp per slab
 __global__ void __launch_bounds__(SCATTER_THREADS)
-    k_cg_scatter(const uint8_t* phase, const int* cnt, const int64_t* off, int nc1, int64_t cap, int64_t* idx_out)
+    k_cg_scatter(const uint8_t* phase, const int* cnt, const int64_t* off, int nc1, int nslab, int64_t cap,
+                 int64_t* idx_out)
 {
-    __shared__ int wtot[SCATTER_THREADS / 32];
-    const int slab = blockIdx.x;
-    if (cnt[slab] == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int slab = blockIdx.x * (SCATTER_THREADS / 32) + (threadIdx.x >> 5);
+    if (slab >= nslab || cnt[slab] == 0) return;
     const size_t base = (size_t)slab * nc1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int64_t run = off[slab];
-    for (int I0 = 0; I0 < nc1; I0 += SCATTER_THREADS) {
-        const int I = I0 + threadIdx.x;
+    for (int I0 = 0; I0 < nc1; I0 += 32) {
+        const int I = I0 + lane;
         const bool f = I < nc1 && phase[base + I] == 2;
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, f);
-        if (lane == 0) wtot[warp] = __popc(bal);
-        __syncthreads();
-        int before = 0, all = 0;
-        for (int w = 0; w < SCATTER_THREADS / 32; w++) {
-            before += w < warp ? wtot[w] : 0;
-            all += wtot[w];
-        }
-        const int64_t pos = run + before + __popc(bal & ((1u << lane) - 1u));
+        const int64_t pos = run + __popc(bal & ((1u << lane) - 1u));
         if (f && pos < cap) idx_out[pos] = (int64_t)(base + I);
-        run += all;
-        __syncthreads();
+        run += __popc(bal);
     }
 }
 
@@ -934,7 +963,6 @@ extern "C" int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int3
     sz += 256;
     const size_t o_sums = sz;
     sz += align256(4 * NSUM * nc);
-    const size_t nwr = (size_t)a.nwr;
     const size_t o_bits = sz;
     sz += align256(4 * (size_t)a.nw * (size_t)n[1] * n[2]);
     const size_t o_lut = sz;
@@ -1010,7 +1038,8 @@ extern "C" int combo_coarse_grain(combo_ctx* ctx, const int32_t n[3], const int3
     k_cg_scan<<<1, SCAN_THREADS, 0, st>>>(a.slab_cnt, nslab, d_off, d_tot);
     CGK(cudaGetLastError());
     if (prof) CGK(cudaEventRecord(g_prof_ev[3], st));
-    k_cg_scatter<<<nslab, SCATTER_THREADS, 0, st>>>(a.phase, a.slab_cnt, d_off, a.nc1, ncap, oi);
+    k_cg_scatter<<<(nslab + SCATTER_THREADS / 32 - 1) / (SCATTER_THREADS / 32), SCATTER_THREADS, 0, st>>>(
+        a.phase, a.slab_cnt, d_off, a.nc1, nslab, ncap, oi);
     CGK(cudaGetLastError());
     if (prof) CGK(cudaEventRecord(g_prof_ev[4], st));
     if (ncap > 0) {

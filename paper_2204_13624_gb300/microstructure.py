@@ -408,6 +408,34 @@ def batch_mix(count=64, seed=SEED_BASE + 3, sides=(32, 48, 64, 96, 128), n_steps
     return out
 
 
+def lame(E, nu):
+    """(mu, lambda) of Young's modulus E and Poisson ratio nu."""
+    return E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+
+
+# Sec. 6.1: inclusion E = 10, nu = 0.3; matrix E = 1, nu = 0 (GPa); 50 % shear F_xy
+E1_MU = (lame(1.0, 0.0)[0], lame(10.0, 0.3)[0])
+E1_LAM = (lame(1.0, 0.0)[1], lame(10.0, 0.3)[1])
+E1_FBAR = np.array([[1.0, 0.5, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+
+
+def sphere_e1_fine(fine=256, n_steps=5):
+    """Sec. 6.2: the fine reference problem, the ball R = 0.4 of the unit RVE
+    sampled at fine voxel centres, no composite voxels."""
+    chi = fine_ball_image(fine, 0.4)
+    n = (fine, fine, fine)
+    return make_problem(n, (1.0, 1.0, 1.0), chi.ravel(), np.zeros(0, np.int64), np.zeros(0), np.zeros((0, 3)),
+                        E1_MU, E1_LAM, E1_FBAR, n_steps)
+
+
+def sphere_e1_coarse(phase, idx, c, N, n_steps=5):
+    """Sec. 6.2: a coarse-grained problem from combo_coarse_grain's outputs
+    (phase [nc3, nc2, nc1], boxel indices, c+, normals) on the unit RVE."""
+    nc3, nc2, nc1 = phase.shape
+    return make_problem((nc1, nc2, nc3), (1.0, 1.0, 1.0), np.ascontiguousarray(phase).ravel(), idx, c, N, E1_MU,
+                        E1_LAM, E1_FBAR, n_steps)
+
+
 def fine_ball_image(fine=256, R=0.4):
     """Binary fine image chi[k, j, i] (uint8, x fastest) of the ball |x| < R of
     the unit RVE [-0.5, 0.5]^3 sampled at the fine voxel centres (the paper's
