@@ -508,7 +508,7 @@ def normals_bench(combo, ctx, stream, peak, peak_kind, cpu=True, reps=20):
     the paper's 256^3 ball (radius 0.4 L) to 32^3 composite voxels and to
     8 x 16 x 32 boxels, and a 1 GiB image of seeded random balls (radius 24
     voxels, about 20 % inclusion) to 128^3.  Device-resident image, L2
-    flushed (256 MiB write) before each call, CUDA events on the call's
+    flushed (a 256 MiB read) before each call, CUDA events on the call's
     stream around the call and (library events) around each launch; median
     of `reps` calls.  The coarse-graining's speed of light is one read of the
     image plus the writes of the phase codes and boxel lists."""
@@ -532,7 +532,9 @@ def normals_bench(combo, ctx, stream, peak, peak_kind, cpu=True, reps=20):
             res = combo.coarse_grain(d, b, ctx=ctx)
         calls, kern = [], []
         for _ in range(reps):
-            flush.fill_(1)
+            # evict L2 by reading (a written flush buffer would leave dirty
+            # lines whose write-back lands in the timed kernels)
+            flush.sum()
             e0.record(stream)
             res = combo.coarse_grain(d, b, ctx=ctx)
             e1.record(stream)

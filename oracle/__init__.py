@@ -8,7 +8,7 @@ The oracle is plain C (``combo_oracle.c``) compiled with gcc and reached
 through ctypes.  It shares no code with the CUDA library.  See the C file's
 header for what each function computes and which part of the paper it
 follows (Sec. 3 Lippmann-Schwinger / Green operator, Sec. 4 laminate
-Algorithms 1 and 2, Sec. 6.1 Neo-Hookean material).  ``normals.py`` (plain
+Algorithms 1 and 2, Sec. 6.1 Neo-Hookean material, App. A staggered grid).  ``normals.py`` (plain
 numpy) is the oracle of the coarse-graining with the Sec. 5 normal detection.
 
 Parity pins: every function here is pinned by ``tests/test_oracle_*.py``
@@ -27,7 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "combo_oracle.c")
 _LIB = os.path.join(_HERE, "libcombo_oracle.so")
 
-ROTATED, SPECTRAL = 0, 1
+ROTATED, SPECTRAL, STAGGERED = 0, 1, 2
 FIXED_POINT, NEWTON_CG = 0, 1
 
 STATUS = {0: "ok", -1: "invalid", -3: "not converged", -4: "laminate NR failed",
@@ -65,6 +65,7 @@ def lib():
         L.orc_fft1.argtypes = [C.c_int, C.c_int, dp, dp]
         L.orc_fft3.argtypes = [ip, C.c_int, dp]
         L.orc_kvec.argtypes = [C.c_int, ip, dp, ip, dp]
+        L.orc_kvec_row.argtypes = [C.c_int, ip, dp, ip, C.c_int, dp]
         L.orc_gamma_matrix.argtypes = [C.c_int, ip, dp, ip, dp]
         L.orc_gamma_matrix.restype = C.c_int
         L.orc_apply_G.argtypes = [C.c_int, ip, dp, dp, dp]
@@ -159,6 +160,16 @@ def kvec(kspace, n, l, xi):
     xi = np.asarray(xi, dtype=np.int32)
     out = np.zeros(6)
     lib().orc_kvec(kspace, _i(n), _d(l), _i(xi), _d(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+def kvec_row(kspace, n, l, xi, a):
+    """The derivative vector of row a of F (the staggered grid has one per row)."""
+    n = np.asarray(n, dtype=np.int32)
+    l = _f64(l)
+    xi = np.asarray(xi, dtype=np.int32)
+    out = np.zeros(6)
+    lib().orc_kvec_row(kspace, _i(n), _d(l), _i(xi), int(a), _d(out))
     return out[0::2] + 1j * out[1::2]
 
 

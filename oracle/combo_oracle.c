@@ -414,6 +414,7 @@ void orc_fft3(const int n[3], int sign, double* data_ri)
 /* ------------------------------------------------------------------ */
 #define ORC_ROTATED 0
 #define ORC_SPECTRAL 1
+#define ORC_STAGGERED 2
 
 /*
  * ROTATED (Willot's rotated / HEX8R scheme, Sec. 3 and Sec. 6.3): the
@@ -426,6 +427,15 @@ void orc_fft3(const int n[3], int sign, double* data_ri)
  * SPECTRAL (Moulinec-Suquet trigonometric polynomials, Sec. 3):
  *   k_j = 2 pi i xit_j / l_j,  xit the signed frequency;
  * READING: k_j = 0 at the Nyquist index of an even n_j.
+ *
+ * STAGGERED (App. A, Eqs. forward_backward_difference, gradient_operator):
+ * F_aB = D_B^+ U_a on the diagonal (B = a) and D_B^- U_a off it, with
+ * D^+ phi[I] = (phi[I + e_B] - phi[I]) / h_B and D^- phi[I] = (phi[I] -
+ * phi[I - e_B]) / h_B; their Fourier symbols (x[I + e] <-> e^{i theta} x-hat
+ * under the inverse transform's + sign) are (e^{i theta} - 1) / h and
+ * (1 - e^{-i theta}) / h.  Each row a of F has its own vector k_a (the
+ * diagonal entry forward, the others backward).  The rotated and spectral
+ * schemes use the same k for every row.
  */
 void orc_kvec(int kspace, const int n[3], const double l[3], const int xi[3], double* k_ri)
 {
@@ -463,30 +473,61 @@ void orc_kvec(int kspace, const int n[3], const double l[3], const int xi[3], do
     }
 }
 
+/* the derivative vector of row a of F: k_a[B], B = 0..2 */
+static void row_kvecs(int kspace, const int n[3], const double l[3], const int xi[3], cplx kr[3][3])
+{
+    if (kspace == ORC_STAGGERED) {
+        for (int B = 0; B < 3; B++) {
+            const double t = 2.0 * M_PI * (double)xi[B] / (double)n[B];
+            const double h = l[B] / (double)n[B];
+            const cplx fwd = ((cos(t) + I * sin(t)) - 1.0) / h;
+            const cplx bwd = (1.0 - (cos(t) - I * sin(t))) / h;
+            for (int a = 0; a < 3; a++) kr[a][B] = (a == B) ? fwd : bwd;
+        }
+        return;
+    }
+    double k6[6];
+    orc_kvec(kspace, n, l, xi, k6);
+    for (int a = 0; a < 3; a++)
+        for (int B = 0; B < 3; B++) kr[a][B] = k6[2 * B] + I * k6[2 * B + 1];
+}
+
+/* the derivative vector of row a (test entry point), 3 complex values */
+void orc_kvec_row(int kspace, const int n[3], const double l[3], const int xi[3], int a, double* k_ri)
+{
+    cplx kr[3][3];
+    row_kvecs(kspace, n, l, xi, kr);
+    for (int B = 0; B < 3; B++) {
+        k_ri[2 * B] = creal(kr[a][B]);
+        k_ri[2 * B + 1] = cimag(kr[a][B]);
+    }
+}
+
 /*
  * Gamma-hat for the reference medium C0 = mu0 * I4 (I4_iJkL = d_ik d_JL):
- *   Gamma0_hat_(iJ),(kL) = d_ik k_J conj(k_L) / (mu0 |k|^2),  Gamma0_hat = 0 where k = 0
- * (Eq. (Gamma0): Grad G0 Div, with Div the adjoint of Grad).  The oracle
- * works with G = mu0 Gamma0, the orthogonal projection onto compatible
- * zero-mean fields.  READING: C0 = mu0 I4 (the paper does not fix C0).
+ *   Gamma0_hat_(iJ),(kL) = d_ik k_iJ conj(k_iL) / (mu0 |k_i|^2),  Gamma0_hat = 0 where k_i = 0
+ * (Eq. (Gamma0): Grad G0 Div, with Div the adjoint of Grad; k_i the
+ * derivative vector of row i, the same for all rows except on the staggered
+ * grid).  The oracle works with G = mu0 Gamma0, the orthogonal projection
+ * onto compatible zero-mean fields.  READING: C0 = mu0 I4 (the paper does not
+ * fix C0); on the staggered grid Div is the adjoint of the printed Grad,
+ * Div P_a = sum_B D_B^{-+} P_aB (the printed Div lists P_Ba).
  * Builds the explicit 9x9 complex matrix at one frequency; returns 0 if k=0.
  */
 static int gamma_matrix(int kspace, const int n[3], const double l[3], const int xi[3], cplx Gm[81])
 {
-    double kr[6];
-    orc_kvec(kspace, n, l, xi, kr);
-    cplx k[3] = {kr[0] + I * kr[1], kr[2] + I * kr[3], kr[4] + I * kr[5]};
-    double k2 = creal(k[0] * conj(k[0]) + k[1] * conj(k[1]) + k[2] * conj(k[2]));
-    if (k2 == 0.0) {
-        for (int q = 0; q < 81; q++) Gm[q] = 0.0;
-        return 0;
-    }
-    for (int i = 0; i < 3; i++)
+    cplx k[3][3];
+    row_kvecs(kspace, n, l, xi, k);
+    int any = 0;
+    for (int q = 0; q < 81; q++) Gm[q] = 0.0;
+    for (int i = 0; i < 3; i++) {
+        double k2 = creal(k[i][0] * conj(k[i][0]) + k[i][1] * conj(k[i][1]) + k[i][2] * conj(k[i][2]));
+        if (k2 == 0.0) continue;
+        any = 1;
         for (int Jx = 0; Jx < 3; Jx++)
-            for (int kk = 0; kk < 3; kk++)
-                for (int L = 0; L < 3; L++)
-                    Gm[(3 * i + Jx) * 9 + 3 * kk + L] = (i == kk) ? k[Jx] * conj(k[L]) / k2 : 0.0;
-    return 1;
+            for (int L = 0; L < 3; L++) Gm[(3 * i + Jx) * 9 + 3 * i + L] = k[i][Jx] * conj(k[i][L]) / k2;
+    }
+    return any;
 }
 
 /* Y = G[X] for a real 9-component field (forward FFT, 9x9 complex matrix per
@@ -560,7 +601,7 @@ typedef struct {
 
 typedef struct {
     int32_t solver; /* 0 fixed point (basic scheme), 1 Newton-CG */
-    int32_t kspace; /* 0 rotated, 1 spectral */
+    int32_t kspace; /* 0 rotated, 1 spectral, 2 staggered */
     double tol;
     int32_t max_iter;
     int32_t fixed_iter; /* > 0: exactly this many outer iterations per load step */

@@ -69,6 +69,22 @@ def spectral_gradient(U, l):
     return H.reshape(9, -1)
 
 
+def staggered_gradient(U, h):
+    """App. A, Eq. gradient_operator: F_aa = D_a^+ U_a, F_aB = D_B^- U_a (B != a),
+    D^+ phi[I] = (phi[I + e] - phi[I]) / h, D^- phi[I] = (phi[I] - phi[I - e]) / h,
+    periodic; U[a][n3][n2][n1]."""
+    ax_of = {0: 3, 1: 2, 2: 1}
+    H = np.zeros((3, 3) + U.shape[1:])
+    for a in range(3):
+        for B in range(3):
+            ax = ax_of[B] - 1  # axis of U[a]
+            if a == B:
+                H[a, B] = (np.roll(U[a], -1, axis=ax) - U[a]) / h[B]
+            else:
+                H[a, B] = (U[a] - np.roll(U[a], 1, axis=ax)) / h[B]
+    return H.reshape(9, -1)
+
+
 def band_limit(U):
     Uh = np.fft.fftn(U, axes=(1, 2, 3))
     for ax in (1, 2, 3):
@@ -103,7 +119,28 @@ def test_spectral_G_keeps_spectral_gradients(orc, n, l):
     assert np.allclose(Y, X, atol=1e-12 * np.abs(X).max())
 
 
-@pytest.mark.parametrize("kspace", [0, 1])
+@pytest.mark.parametrize("n,l", SHAPES)
+def test_staggered_G_keeps_staggered_gradients(orc, n, l):
+    rng = np.random.default_rng(11)
+    U = rng.normal(size=(3, n[2], n[1], n[0]))
+    h = [l[j] / n[j] for j in range(3)]
+    X = staggered_gradient(U, h)
+    Y, ss = orc.apply_G(X, n, l, orc.STAGGERED)
+    assert np.allclose(Y, X, atol=1e-12 * np.abs(X).max())
+    # and removes what is orthogonal to every staggered gradient: a field
+    # whose rows have zero staggered divergence (adjoint of Grad) is mapped to 0
+    Z = rng.normal(size=(9, n[0] * n[1] * n[2]))
+    GZ, _ = orc.apply_G(Z, n, l, orc.STAGGERED)
+    R = Z - GZ
+    # R is orthogonal to all gradients: <R, Grad e_q> = 0 for unit displacements
+    for q in rng.choice(3 * n[0] * n[1] * n[2], 12, replace=False):
+        e = np.zeros(3 * n[0] * n[1] * n[2])
+        e[q] = 1.0
+        g = staggered_gradient(e.reshape(3, n[2], n[1], n[0]), h)
+        assert abs(np.sum(R * g)) < 1e-10 * np.abs(Z).max()
+
+
+@pytest.mark.parametrize("kspace", [0, 1, 2])
 @pytest.mark.parametrize("n,l", SHAPES)
 def test_G_is_zero_mean_projector(orc, kspace, n, l):
     rng = np.random.default_rng(9)
@@ -129,7 +166,7 @@ def test_G_is_zero_mean_projector(orc, kspace, n, l):
     assert np.allclose(y.real.reshape(9, V), Y, atol=1e-13)
 
 
-@pytest.mark.parametrize("kspace", [0, 1])
+@pytest.mark.parametrize("kspace", [0, 1, 2])
 def test_gamma_matrix_properties(orc, kspace):
     rng = np.random.default_rng(10)
     n, l = (6, 4, 8), (1.0, 0.7, 1.3)
@@ -137,16 +174,19 @@ def test_gamma_matrix_properties(orc, kspace):
     for _ in range(20):
         xi = tuple(int(rng.integers(0, m)) for m in n)
         Gm = orc.gamma_matrix(kspace, n, l, xi)
-        k = orc.kvec(kspace, n, l, xi)
-        if np.all(k == 0):
+        ks = [orc.kvec_row(kspace, n, l, xi, a) for a in range(3)]
+        if kspace != 2:
+            assert all(np.array_equal(ks[a], orc.kvec(kspace, n, l, xi)) for a in range(3))
+        if np.all(ks[0] == 0):
             assert np.all(Gm == 0)
             continue
         assert np.allclose(Gm, Gm.conj().T, atol=1e-14)
         assert np.allclose(Gm @ Gm, Gm, atol=1e-13)
         x = rng.normal(size=9) + 1j * rng.normal(size=9)
         y = (Gm @ x).reshape(3, 3)
-        # compatibility: y_iJ k_K = y_iK k_J
-        assert np.allclose(np.einsum("ij,k->ijk", y, k), np.einsum("ik,j->ijk", y, k), atol=1e-12)
+        # compatibility: y_iJ k_iK = y_iK k_iJ (row i is a multiple of k_i)
+        for i in range(3):
+            assert np.allclose(y[i][:, None] * ks[i][None, :], ks[i][:, None] * y[i][None, :], atol=1e-12)
         # Hermitian symmetry of the symbol: G(-xi) = conj G(xi)
         xm = tuple((-xi[j]) % n[j] for j in range(3))
         assert np.allclose(orc.gamma_matrix(kspace, n, l, xm), np.conj(Gm), atol=1e-14)

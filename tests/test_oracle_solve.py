@@ -16,7 +16,7 @@ import pytest
 from scipy.optimize import fsolve
 
 from paper_2204_13624_gb300 import microstructure as ms
-from test_oracle_fft_gamma import band_limit, hex8r_gradient, spectral_gradient
+from test_oracle_fft_gamma import band_limit, hex8r_gradient, spectral_gradient, staggered_gradient
 
 TIGHT = dict(tol=1e-12, cg_tol=1e-8, max_iter=60)
 
@@ -128,7 +128,7 @@ def brute_force(orc, p, grad):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("kspace", [0, 1])
+@pytest.mark.parametrize("kspace", [0, 1, 2])
 def test_brute_force_4cubed(orc, kspace):
     p = ms.random_boxels((4, 4, 4), seed=21, boxel_frac=0.3, incl_frac=0.3, contrast=10.0)
     l = p["l"]
@@ -136,8 +136,10 @@ def test_brute_force_4cubed(orc, kspace):
     h = [l[j] / n[j] for j in range(3)]
     if kspace == 0:
         grad = lambda U: hex8r_gradient(U, h)
-    else:
+    elif kspace == 1:
         grad = lambda U: spectral_gradient(U, l)
+    else:
+        grad = lambda U: staggered_gradient(U, h)
     F_bf, P_bf = brute_force(orc, p, grad)
     r = orc.solve(p, dict(solver=1, kspace=kspace, **TIGHT))
     assert np.allclose(r["F"], F_bf, atol=1e-10)
