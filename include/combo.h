@@ -70,6 +70,13 @@ extern "C" {
 /* kspace: discrete derivative of the Green operator */
 #define COMBO_ROTATED 0  /* Willot's rotated scheme (HEX8R), Sec. 3 and Sec. 6.3 */
 #define COMBO_SPECTRAL 1 /* Moulinec-Suquet trigonometric polynomials, Sec. 3 */
+/* staggered grid (App. A, Eqs. forward_backward_difference, gradient_operator):
+   F_aa = D_a^+ U_a, F_aB = D_B^- U_a (B != a), Div the adjoint of Grad; the
+   nine components of a voxel's F sit at its centre (diagonal) and edge
+   midpoints (off-diagonal), and the material law is applied to them as
+   stored (the plain staggered scheme; no doubly-fine material grid).  Not
+   available to combo_apply_G_noalloc. */
+#define COMBO_STAGGERED 2
 /* solver */
 #define COMBO_FIXED_POINT 0 /* basic scheme on the nonlinear LSE, Sec. 3 */
 #define COMBO_NEWTON_CG 1   /* Newton with conjugate gradients on the linearised LSE, Sec. 3 */

@@ -28,6 +28,17 @@ template <bool INV, typename V> __device__ __forceinline__ V c_rot(V a)
 }
 template <typename V, typename S> __device__ __forceinline__ V c_scale(V a, S s) { return V{a.x * s, a.y * s}; }
 
+// Staggered grid (App. A): row i of F uses k_iB = i rho_B e^{+i theta_B/2}
+// (forward difference) for B = i and i rho_B e^{-i theta_B/2} (backward) for
+// B != i, rho_B = (2/h_B) sin(theta_B/2).  Row i of the projection
+// k_i (k_i^H X_i) / |k|^2 is then the real projection with k = rho between
+// the rotations X_B -> u_B X_B and o_B -> conj(u_B) o_B, u_B = e^{-i theta_B/2}
+// for B = i and e^{+i theta_B/2} otherwise.
+template <typename V> __device__ __forceinline__ V stag_u(int row, int B, V ph)
+{
+    return row == B ? c_conj(ph) : ph;
+}
+
 // |a|^2 + |b|^2 + |c|^2 for a residual norm: in FP64 from FP32 / FP64 values;
 // from the leading FP32 parts of double-float values (a norm used for a
 // stopping test needs no more than FP32 accuracy)
@@ -425,6 +436,7 @@ template <typename T> struct ZArgs {
     int tx;
     const T* sa[3];  // symbol tables: k_j(xi) = sa[j][xi_j] * prod_{m != j} sb[m][xi_m]
     const T* sb[3];
+    const cx<T>* ph[3];  // staggered grid: e^{i theta_j / 2} per index (else null)
     T scale;         // 2 / V
     int want_norm;   // accumulate sum w |G X|^2 and the zero frequency
     double* partial; // [gridDim.x * gridDim.y * gridDim.z]

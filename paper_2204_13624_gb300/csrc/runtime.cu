@@ -161,6 +161,7 @@ template <typename T> struct DevTables {
     cx<T>* twz = nullptr;   // [n3]
     T* sa[3] = {nullptr, nullptr, nullptr};
     T* sb[3] = {nullptr, nullptr, nullptr};
+    cx<T>* ph[3] = {nullptr, nullptr, nullptr};  // staggered grid only
 };
 
 template <typename T> static int upload_tw(cx<T>** d, int n, int denom)
@@ -181,14 +182,23 @@ template <typename T> static int upload_tw(cx<T>** d, int n, int denom)
 //     this is the rotated-scheme symbol up to the common phase i e^{i sum theta/2},
 //     which cancels in k k^H / |k|^2.
 //   spectral (Moulinec-Suquet): sa = 2 pi xi_signed / l (0 at Nyquist), sb = 1.
+//   staggered (App. A): sa = (2/h) sin(pi xi / n), sb = 1, and the phase
+//     table ph = e^{i pi xi / n} = e^{i theta/2} of the forward / backward
+//     difference symbols i sa e^{+-i theta/2} (rows differ: stag_u).
 template <typename T> static int upload_symbols(DevTables<T>& t, const int n[3], const double l[3], int kspace)
 {
     for (int j = 0; j < 3; j++) {
         std::vector<T> a(n[j]), b(n[j]);
+        std::vector<cx<T>> ph(n[j]);
         const double h = l[j] / n[j];
         for (int x = 0; x < n[j]; x++) {
             const bool nyq = (2 * x == n[j]);
-            if (kspace == COMBO_ROTATED) {
+            ph[x].x = (T)std::cos(M_PI * (double)x / n[j]);
+            ph[x].y = (T)std::sin(M_PI * (double)x / n[j]);
+            if (kspace == COMBO_STAGGERED) {
+                a[x] = (T)((2.0 / h) * std::sin(M_PI * (double)x / n[j]));
+                b[x] = (T)1;
+            } else if (kspace == COMBO_ROTATED) {
                 a[x] = (T)((2.0 / h) * std::sin(M_PI * (double)x / n[j]));
                 b[x] = nyq ? (T)0 : (T)std::cos(M_PI * (double)x / n[j]);
             } else {
@@ -201,6 +211,10 @@ template <typename T> static int upload_symbols(DevTables<T>& t, const int n[3],
         CK(cudaMalloc(&t.sb[j], sizeof(T) * n[j]));
         CK(cudaMemcpy(t.sa[j], a.data(), sizeof(T) * n[j], cudaMemcpyHostToDevice));
         CK(cudaMemcpy(t.sb[j], b.data(), sizeof(T) * n[j], cudaMemcpyHostToDevice));
+        if (kspace == COMBO_STAGGERED) {
+            CK(cudaMalloc(&t.ph[j], sizeof(cx<T>) * n[j]));
+            CK(cudaMemcpy(t.ph[j], ph.data(), sizeof(cx<T>) * n[j], cudaMemcpyHostToDevice));
+        }
     }
     return COMBO_OK;
 }
@@ -225,6 +239,7 @@ template <typename T> static void free_tables(DevTables<T>& t)
     for (int j = 0; j < 3; j++) {
         cudaFree(t.sa[j]);
         cudaFree(t.sb[j]);
+        cudaFree(t.ph[j]);
     }
 }
 
@@ -432,6 +447,7 @@ template <typename T> struct Engine {
         for (int j = 0; j < 3; j++) {
             z.sa[j] = tab.sa[j];
             z.sb[j] = tab.sb[j];
+            z.ph[j] = tab.ph[j];
         }
         z.scale = (T)(2.0 * g.nprob / (double)g.V);  // 2 / (voxels of one problem)
         z.want_norm = want_norm ? 1 : 0;
@@ -724,7 +740,7 @@ static int check_options(combo_options& o)
 {
     if (o.precision != COMBO_FP64 && o.precision != COMBO_FP32_REFINED && o.precision != COMBO_FP32_REFINED_DF)
         return fail(COMBO_E_INVALID_ARG, "bad precision");
-    if (o.kspace != COMBO_ROTATED && o.kspace != COMBO_SPECTRAL) return fail(COMBO_E_INVALID_ARG, "bad kspace");
+    if (o.kspace != COMBO_ROTATED && o.kspace != COMBO_SPECTRAL && o.kspace != COMBO_STAGGERED) return fail(COMBO_E_INVALID_ARG, "bad kspace");
     if (o.solver != COMBO_FIXED_POINT && o.solver != COMBO_NEWTON_CG) return fail(COMBO_E_INVALID_ARG, "bad solver");
     if (o.solver == COMBO_FIXED_POINT && o.precision != COMBO_FP64)
         return fail(COMBO_E_INVALID_ARG, "the fixed point runs in FP64 only");
@@ -1098,7 +1114,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             z0.tw = ec.tab.twz;
             z0.spec = ec.spec;
             z0.tx = ec.txz;
-            for (int j = 0; j < 3; j++) z0.sa[j] = ec.tab.sa[j], z0.sb[j] = ec.tab.sb[j];
+            for (int j = 0; j < 3; j++) z0.sa[j] = ec.tab.sa[j], z0.sb[j] = ec.tab.sb[j], z0.ph[j] = ec.tab.ph[j];
             z0.scale = (Tc)(2.0 * g.nprob / (double)g.V);
             z0.sc = d_sc;
             ZArgs<Tc> z1 = z0;
@@ -1992,7 +2008,8 @@ extern "C" int combo_apply_G(combo_ctx* ctx, const int32_t n[3], const double l[
     if (!ctx || !n || !l || !X || !Y) return fail(COMBO_E_INVALID_ARG, "null argument");
     int rc = validate_dims(n);
     if (rc) return rc;
-    if (kspace != COMBO_ROTATED && kspace != COMBO_SPECTRAL) return fail(COMBO_E_INVALID_ARG, "bad kspace");
+    if (kspace != COMBO_ROTATED && kspace != COMBO_SPECTRAL && kspace != COMBO_STAGGERED)
+        return fail(COMBO_E_INVALID_ARG, "bad kspace");
     CK(cudaSetDevice(ctx->device));
     if (precision == COMBO_FP64) return apply_G_impl<double>(ctx, n, l, kspace, X, Y, sumsq, mem);
     if (precision == COMBO_FP32_REFINED) return apply_G_impl<float>(ctx, n, l, kspace, X, Y, sumsq, mem);

@@ -120,11 +120,20 @@ __global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
         const T az = a.sa[2][z], bz = a.sb[2][z];
         const T k0 = ax * by * bz, k1 = ay * bx * bz, k2 = az * bx * by;
         const T kk = k0 * k0 + k1 * k1 + k2 * k2;
-        const cx<T> X0 = p[0], X1 = p[TX], X2 = p[2 * TX];
+        cx<T> X0 = p[0], X1 = p[TX], X2 = p[2 * TX];
         if (a.want_norm && xi1 == 0 && y == 0 && z == 0) {
             sc->dc[3 * row + 0] = (double)X0.x;
             sc->dc[3 * row + 1] = (double)X1.x;
             sc->dc[3 * row + 2] = (double)X2.x;
+        }
+        cx<T> u0, u1, u2;
+        if (a.ph[0]) {
+            u0 = stag_u(row, 0, a.ph[0][xi1]);
+            u1 = stag_u(row, 1, a.ph[1][y]);
+            u2 = stag_u(row, 2, a.ph[2][z]);
+            X0 = c_mul(X0, u0);
+            X1 = c_mul(X1, u1);
+            X2 = c_mul(X2, u2);
         }
         cx<T> o0{(T)0, (T)0}, o1{(T)0, (T)0}, o2{(T)0, (T)0};
         if (kk > (T)0) {
@@ -135,6 +144,11 @@ __global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
             o0 = cx<T>{k0 * sr, k0 * si};
             o1 = cx<T>{k1 * sr, k1 * si};
             o2 = cx<T>{k2 * sr, k2 * si};
+            if (a.ph[0]) {
+                o0 = c_mul(o0, c_conj(u0));
+                o1 = c_mul(o1, c_conj(u1));
+                o2 = c_mul(o2, c_conj(u2));
+            }
             if (a.want_norm) {
                 const double wgt = (xi1 == 0 || xi1 == g.M) ? 1.0 : 2.0;
                 acc += wgt * sq3(o0, o1, o2);
@@ -207,7 +221,7 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<
             p[0] = p[N * TX] = p[2 * N * TX] = cx<T>{(T)0, (T)0};
             continue;
         }
-        const cx<T> X0 = p[0], X1 = p[N * TX], X2 = p[2 * N * TX];
+        cx<T> X0 = p[0], X1 = p[N * TX], X2 = p[2 * N * TX];
         const T ax = a.sa[0][xi1], bx = a.sb[0][xi1];
         const T az = a.sa[2][z], bz = a.sb[2][z];
         const T k0 = ax * by * bz, k1 = ay * bx * bz, k2 = az * bx * by;
@@ -217,6 +231,15 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<
             sc->dc[3 * row + 1] = (double)X1.x;
             sc->dc[3 * row + 2] = (double)X2.x;
         }
+        cx<T> u0, u1, u2;
+        if (a.ph[0]) {
+            u0 = stag_u(row, 0, a.ph[0][xi1]);
+            u1 = stag_u(row, 1, a.ph[1][y]);
+            u2 = stag_u(row, 2, a.ph[2][z]);
+            X0 = c_mul(X0, u0);
+            X1 = c_mul(X1, u1);
+            X2 = c_mul(X2, u2);
+        }
         cx<T> o0{(T)0, (T)0}, o1{(T)0, (T)0}, o2{(T)0, (T)0};
         if (kk > (T)0) {
             const T ik = (T)1 / kk;
@@ -225,6 +248,11 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<
             o0 = cx<T>{k0 * sr, k0 * si};
             o1 = cx<T>{k1 * sr, k1 * si};
             o2 = cx<T>{k2 * sr, k2 * si};
+            if (a.ph[0]) {
+                o0 = c_mul(o0, c_conj(u0));
+                o1 = c_mul(o1, c_conj(u1));
+                o2 = c_mul(o2, c_conj(u2));
+            }
             if (a.want_norm) {
                 const double wgt = (xi1 == 0 || xi1 == g.M) ? 1.0 : 2.0;
                 acc += wgt * sq3(o0, o1, o2);

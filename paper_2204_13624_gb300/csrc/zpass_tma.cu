@@ -165,7 +165,16 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL)
                 p[0] = p[N * TX] = p[2 * N * TX] = C{0.f, 0.f};
                 continue;
             }
-            const C X0 = p[0], X1 = p[N * TX], X2 = p[2 * N * TX];
+            C X0 = p[0], X1 = p[N * TX], X2 = p[2 * N * TX];
+            C u0, u1, u2;
+            if (a.ph[0]) {
+                u0 = stag_u(row, 0, a.ph[0][xi1]);
+                u1 = stag_u(row, 1, a.ph[1][y]);
+                u2 = stag_u(row, 2, a.ph[2][z]);
+                X0 = c_mul(X0, u0);
+                X1 = c_mul(X1, u1);
+                X2 = c_mul(X2, u2);
+            }
             const float ax = a.sa[0][xi1], bx = a.sb[0][xi1];
             const float az = a.sa[2][z], bz = a.sb[2][z];
             const float k0 = ax * by * bz, k1 = ay * bx * bz, k2 = az * bx * by;
@@ -178,6 +187,11 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL)
                 o0 = C{k0 * sr, k0 * si};
                 o1 = C{k1 * sr, k1 * si};
                 o2 = C{k2 * sr, k2 * si};
+                if (a.ph[0]) {
+                    o0 = c_mul(o0, c_conj(u0));
+                    o1 = c_mul(o1, c_conj(u1));
+                    o2 = c_mul(o2, c_conj(u2));
+                }
             }
             p[0] = c_scale(o0, a.scale);
             p[N * TX] = c_scale(o1, a.scale);

@@ -30,7 +30,7 @@ SHAPES = [(4, 4, 4), (2, 3, 4), (6, 9, 8), (8, 12, 18), (32, 16, 24), (24, 27, 6
           (64, 64, 64), (128, 256, 16), (256, 64, 128), (32, 128, 512), (512, 16, 64), (16, 512, 16)]
 
 
-@pytest.mark.parametrize("kspace", [0, 1])
+@pytest.mark.parametrize("kspace", [0, 1, 2])
 @pytest.mark.parametrize("n", SHAPES)
 def test_green_operator_fp64(cb, orc, n, kspace):
     rng = np.random.default_rng(sum(n) + kspace)
@@ -43,27 +43,29 @@ def test_green_operator_fp64(cb, orc, n, kspace):
     assert abs(ssg - sso) <= 1e-11 * sso
 
 
+@pytest.mark.parametrize("kspace", [0, 2])
 @pytest.mark.parametrize("n", SHAPES)
-def test_green_operator_fp32(cb, orc, n):
+def test_green_operator_fp32(cb, orc, n, kspace):
     rng = np.random.default_rng(sum(n))
     V = n[0] * n[1] * n[2]
     X = rng.normal(size=(9, V))
-    Yo, sso = orc.apply_G(X, n, (1.0, 1.0, 1.0), 0)
-    Yg, ssg = cb.apply_G(X, n, (1.0, 1.0, 1.0), 0, cb.FP32_REFINED)
+    Yo, sso = orc.apply_G(X, n, (1.0, 1.0, 1.0), kspace)
+    Yg, ssg = cb.apply_G(X, n, (1.0, 1.0, 1.0), kspace, cb.FP32_REFINED)
     assert rel(Yg, Yo) < 2e-6
     assert abs(ssg - sso) <= 1e-5 * sso
 
 
+@pytest.mark.parametrize("kspace", [0, 2])
 @pytest.mark.parametrize("n", SHAPES)
-def test_green_operator_double_float(cb, orc, n):
+def test_green_operator_double_float(cb, orc, n, kspace):
     """The double-float transforms of the refined residual: 48-bit significand,
     so G[X] agrees with the FP64 oracle far below the FP32 error."""
     rng = np.random.default_rng(sum(n) + 7)
     V = n[0] * n[1] * n[2]
     l = (1.0, 0.8, 1.3)
     X = rng.normal(size=(9, V))
-    Yo, sso = orc.apply_G(X, n, l, 0)
-    Yg, ssg = cb.apply_G(X, n, l, 0, cb.FP32_REFINED_DF)
+    Yo, sso = orc.apply_G(X, n, l, kspace)
+    Yg, ssg = cb.apply_G(X, n, l, kspace, cb.FP32_REFINED_DF)
     assert rel(Yg, Yo) < 1e-11
     assert abs(ssg - sso) <= 1e-5 * sso  # the norm is summed from the leading FP32 parts
 
@@ -112,7 +114,7 @@ def test_fixed_point_parity(cb, orc, k):
     assert g["n_operator"] == r["n_operator"]
 
 
-@pytest.mark.parametrize("kspace", [0, 1])
+@pytest.mark.parametrize("kspace", [0, 1, 2])
 @pytest.mark.parametrize("k", [0, 1, 2])
 def test_newton_cg_parity(cb, orc, k, kspace):
     p = problems()[k]
@@ -139,6 +141,34 @@ def test_newton_cg_parity_fast_sizes(cb, orc, prec):
         tol = 1e-10 if prec == 0 else 2e-5
         assert rel(g["F"], r["F"]) < tol
         assert rel(g["Pbar"], r["Pbar"]) < (1e-9 if prec == 0 else 2e-5)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_staggered_parity_fast_sizes(cb, orc, prec):
+    """The staggered grid (App. A) through every z-pass variant: runtime
+    plans, compile-time plans and the TMA-tiled FP32 pass."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    for n in [(12, 9, 18), (64, 32, 128), (16, 256, 16)]:
+        p = ms.random_spheres(n, 4.0, 0.15, 13, 10.0, np.diag([1.03, 1.0, 1.0]) + 0.01, 1)
+        g, r = solve_both(cb, orc, p, solver=1, kspace=2, precision=prec, fixed_iterations=1,
+                          cg_fixed_iterations=10)
+        tol = 1e-10 if prec == 0 else 2e-5
+        assert rel(g["F"], r["F"]) < tol
+        assert rel(g["Pbar"], r["Pbar"]) < (1e-9 if prec == 0 else 2e-5)
+
+
+def test_staggered_sphere_32_converged(cb, orc):
+    """The 32^3 ball solved to tol 1e-8 on the staggered grid, against the oracle."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.sphere_32()
+    g, r = solve_both(cb, orc, p, solver=1, kspace=2, tol=1e-8)
+    assert g["steps_done"] == 5
+    assert np.all(g["resid"] <= 1e-8)
+    assert list(g["iters"]) == list(r["iters"])
+    assert rel(g["Pbar"], r["Pbar"]) < 1e-9
+    assert rel(g["F"], r["F"]) < 1e-9
 
 
 def test_sphere_32_converged_fp64(cb, orc):
