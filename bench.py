@@ -601,16 +601,20 @@ def sphere_table1(combo, ctx):
     ref = combo.solve(ms.sphere_e1_fine(256, 5), ctx=ctx, fields=False, precision=combo.FP32_REFINED_DF, tol=1e-9)
     t_ref = time.perf_counter() - t0
     Pref = ref["Pbar"][-1]
+    Pph = ref["Pbar_phase"][-1]
     chi = ms.fine_ball_image(256, 0.4)
     rows = {}
-    for key, (pk, pl) in gold["rows"].items():
+    err = lambda x, y: 100.0 * float(np.linalg.norm(x - y) / np.linalg.norm(y))
+    for key, vals in gold["rows"].items():
         b = tuple(256 // int(v) for v in key.split("x"))
-        row = {"paper_kabel": pk, "paper_sec5": pl}
+        row = {"paper": dict(zip(gold["columns"], vals))}
         for meth, name in (("kabel", "kabel"), ("laplace", "sec5")):
             ph, idx, c, N, nb = combo.coarse_grain(chi, b, method=meth, ctx=ctx)
             r = combo.solve(ms.sphere_e1_coarse(ph, idx, c, N, 5), ctx=ctx, fields=False, precision=combo.FP64,
                             tol=1e-10)
-            row[name] = 100.0 * float(np.linalg.norm(r["Pbar"][-1] - Pref) / np.linalg.norm(Pref))
+            row[name + "_Pbar"] = err(r["Pbar"][-1], Pref)
+            row[name + "_Pbar_matrix"] = err(r["Pbar_phase"][-1][0], Pph[0])
+            row[name + "_Pbar_inclusion"] = err(r["Pbar_phase"][-1][1], Pph[1])
             row["boxels"] = int(nb)
         rows[key] = row
     return {"rows": rows, "unit": "% Pbar error", "reference_seconds": t_ref,

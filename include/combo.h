@@ -166,6 +166,11 @@ typedef struct {
  *   iters         [n_steps] outer (Newton / fixed-point) iterations.
  *   cg_iters      [n_steps] CG iterations.
  *   resid         [n_steps] final equilibrium residual.
+ *   Pbar_phase    [n_steps][2][9] phase averages of P at each step's converged
+ *                 state (Sec. 6.2): [0] the matrix, [1] the inclusion; pure
+ *                 voxels add P and their volume to their phase, a composite
+ *                 boxel adds c+- P+- (its laminate phase stresses at F+- =
+ *                 F +- a (x) N / c+-) and c+- to each.  In `mem`.
  * Counters are totals over the solve.  steps_done is the number of load
  * steps completed (partial results are valid up to it on failure).
  */
@@ -184,6 +189,7 @@ typedef struct {
     int64_t n_laminate_evals;
     int64_t n_operator; /* operator applications; voxel-iterations = n_operator * V */
     int64_t n_operator_fp64;
+    double* Pbar_phase;
 } combo_result;
 
 /* Context: owns the device, the stream and the library's device memory.

@@ -299,5 +299,43 @@ def constitutive_field(prob, F, a=None, opts=None, tangent=False):
     return (P, a[:nb], A.reshape(V, 9, 9)) if tangent else (P, a[:nb])
 
 
+def phase_averages(prob, F, a, c_min=1e-6):
+    """Phase averages Pbar_- (matrix) and Pbar_+ (inclusion) of a state (Sec. 6.2):
+    the mean of P over the volume of each phase, where a pure voxel adds its P
+    and its volume to its phase and a composite boxel adds c+- P+- and c+- to
+    each, P+- the Neo-Hookean stresses at the laminate phase deformations
+    F+- = F +- a (x) N / c+- (Sec. 4.1).  Boxels with c+ outside
+    [c_min, 1 - c_min] count as pure voxels, as in the solve.  F [9][V],
+    a [n_boxels][3] (the converged jump vectors).  Returns [2][9]."""
+    phase = np.asarray(prob["phase"]).ravel().copy()
+    F = np.asarray(F, dtype=np.float64).reshape(9, -1)
+    mu, lam = prob["mu"], prob["lam"]
+    sums = np.zeros((2, 9))
+    vol = np.zeros(2)
+    idx = np.asarray(prob["boxel_idx"], np.int64)
+    cs = np.asarray(prob["boxel_c"], float)
+    for k, v in enumerate(idx):
+        if cs[k] < c_min:
+            phase[v] = 0
+        elif cs[k] > 1.0 - c_min:
+            phase[v] = 1
+    for v in np.flatnonzero(phase != 2):
+        ph = int(phase[v])
+        sums[ph] += neohooke(F[:, v], mu[ph], lam[ph], tangent=False)
+        vol[ph] += 1.0
+    for k, v in enumerate(idx):
+        if phase[v] != 2:
+            continue
+        c = float(cs[k])
+        N = np.asarray(prob["boxel_N"][k], float)
+        N = N / np.linalg.norm(N)
+        Fb = F[:, v].reshape(3, 3)
+        aN = np.outer(a[k], N)
+        for ph, cph, Fph in ((1, c, Fb + aN / c), (0, 1.0 - c, Fb - aN / (1.0 - c))):
+            sums[ph] += cph * neohooke(Fph.reshape(9), mu[ph], lam[ph], tangent=False)
+            vol[ph] += cph
+    return np.where(vol[:, None] > 0, sums / np.maximum(vol, 1e-300)[:, None], 0.0)
+
+
 def num_threads():
     return lib().orc_num_threads()

@@ -52,7 +52,8 @@ class ResultS(C.Structure):
     _fields_ = [("Pbar", C.c_void_p), ("F_out", C.c_void_p), ("P_out", C.c_void_p), ("a_out", C.c_void_p),
                 ("iters", C.c_void_p), ("cg_iters", C.c_void_p), ("resid", C.c_void_p), ("mem", C.c_int32),
                 ("steps_done", C.c_int32), ("nr_iters", C.c_int64), ("n_backproj", C.c_int64),
-                ("n_laminate_evals", C.c_int64), ("n_operator", C.c_int64), ("n_operator_fp64", C.c_int64)]
+                ("n_laminate_evals", C.c_int64), ("n_operator", C.c_int64), ("n_operator_fp64", C.c_int64),
+                ("Pbar_phase", C.c_void_p)]
 
 
 EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_options_default",
@@ -222,9 +223,10 @@ class Problem:
 def _result_buffers(pb: Problem, fields: bool, device: bool):
     S, V, nb = pb.n_steps, pb.V, pb.n_boxels
     out = dict(Pbar=np.zeros((S, 9)), iters=np.zeros(S, np.int32), cg_iters=np.zeros(S, np.int32),
-               resid=np.zeros(S))
+               resid=np.zeros(S), Pbar_phase=np.zeros((S, 2, 9)))
     r = ResultS()
     r.Pbar = _ptr(out["Pbar"])
+    r.Pbar_phase = _ptr(out["Pbar_phase"])
     r.iters = _ptr(out["iters"])
     r.cg_iters = _ptr(out["cg_iters"])
     r.resid = _ptr(out["resid"])
@@ -238,9 +240,10 @@ def _result_buffers(pb: Problem, fields: bool, device: bool):
             r.mem = MEM_DEVICE
             # Pbar etc. are host arrays; with mem = device the library expects
             # device pointers for every array, so keep scalars on the device too
-            for k in ("Pbar", "iters", "cg_iters", "resid"):
+            for k in ("Pbar", "iters", "cg_iters", "resid", "Pbar_phase"):
                 out[k] = torch.as_tensor(out[k]).cuda()
-            r.Pbar, r.iters, r.cg_iters, r.resid = (_ptr(out[k]) for k in ("Pbar", "iters", "cg_iters", "resid"))
+            r.Pbar, r.iters, r.cg_iters, r.resid, r.Pbar_phase = (
+                _ptr(out[k]) for k in ("Pbar", "iters", "cg_iters", "resid", "Pbar_phase"))
         else:
             out["F"] = np.zeros((9, V))
             out["P"] = np.zeros((9, V))
@@ -529,9 +532,10 @@ class Server:
     def _buffers(self, ticket):
         S, V = self._meta[ticket]
         out = dict(Pbar=np.zeros((S, 9)), iters=np.zeros(S, np.int32), cg_iters=np.zeros(S, np.int32),
-                   resid=np.zeros(S))
+                   resid=np.zeros(S), Pbar_phase=np.zeros((S, 2, 9)))
         r = ResultS()
-        r.Pbar, r.iters, r.cg_iters, r.resid = (_ptr(out[k]) for k in ("Pbar", "iters", "cg_iters", "resid"))
+        r.Pbar, r.iters, r.cg_iters, r.resid, r.Pbar_phase = (
+            _ptr(out[k]) for k in ("Pbar", "iters", "cg_iters", "resid", "Pbar_phase"))
         if self.keep_fields:
             out["F"] = np.zeros((9, V))
             out["P"] = np.zeros((9, V))

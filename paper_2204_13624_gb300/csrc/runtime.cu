@@ -637,6 +637,97 @@ __global__ void k_eval_P(const double* F, const uint8_t* phase, const int32_t* v
     }
 }
 
+// Neo-Hookean P of F (Sec. 6.1) in FP64; false where det F <= 0
+__device__ __forceinline__ bool nh_P64(const double f[9], double mu, double lam, double P[9])
+{
+    const double c0 = f[4] * f[8] - f[5] * f[7], c1 = f[5] * f[6] - f[3] * f[8], c2 = f[3] * f[7] - f[4] * f[6];
+    const double J = f[0] * c0 + f[1] * c1 + f[2] * c2;
+    if (!(J > 0.0)) return false;
+    const double iJ = 1.0 / J;
+    const double G[9] = {c0 * iJ,
+                         (f[2] * f[7] - f[1] * f[8]) * iJ,
+                         (f[1] * f[5] - f[2] * f[4]) * iJ,
+                         c1 * iJ,
+                         (f[0] * f[8] - f[2] * f[6]) * iJ,
+                         (f[2] * f[3] - f[0] * f[5]) * iJ,
+                         c2 * iJ,
+                         (f[1] * f[6] - f[0] * f[7]) * iJ,
+                         (f[0] * f[4] - f[1] * f[3]) * iJ};
+    const double k = lam * log(J) - mu;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) P[3 * i + j] = mu * f[3 * i + j] + k * G[3 * j + i];
+    return true;
+}
+
+// Phase-wise sums for the phase averages Pbar_- and Pbar_+ of one problem
+// (voxels [v0, v1) of a field with stride V, boxels [b0, b1)): pure voxels add
+// P(F) and 1 to their phase; a boxel adds c+ P+ and c+ to the inclusion and
+// c- P- and c- to the matrix, P+- the laminate phase stresses at
+// F+- = F +- a (x) N / c+- (Sec. 4.1).  Per block: 18 sums, 2 volumes.
+constexpr int PHASE_SUMS = 20;
+constexpr int PHASE_GRID = 152 * 4;
+
+__global__ void __launch_bounds__(256) k_phase_sums(const double* F, int64_t V, const uint8_t* phase, int64_t v0,
+                                                    int64_t v1, const int32_t* bidx, const double* bN,
+                                                    const double* bc, const double* ba, int64_t b0, int64_t b1,
+                                                    Mat9 mat, double* part, Scalars* sc)
+{
+    double s[PHASE_SUMS];
+#pragma unroll
+    for (int k = 0; k < PHASE_SUMS; k++) s[k] = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = v0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < v1; v += stride) {
+        const int ph = phase[v];
+        if (ph == 2) continue;
+        double f[9], P[9];
+        for (int c = 0; c < 9; c++) f[c] = F[c * V + v];
+        if (!nh_P64(f, mat.v[ph], mat.v[2 + ph], P)) {
+            atomicCAS(&sc->status, 0, COMBO_E_INADMISSIBLE);
+            continue;
+        }
+        for (int c = 0; c < 9; c++) s[9 * ph + c] += P[c];
+        s[18 + ph] += 1.0;
+    }
+    for (int64_t b = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < b1; b += stride) {
+        const int64_t v = bidx[b];
+        const double cp = bc[b], cm = 1.0 - cp;
+        const double N[3] = {bN[3 * b], bN[3 * b + 1], bN[3 * b + 2]};
+        const double a[3] = {ba[3 * b], ba[3 * b + 1], ba[3 * b + 2]};
+        double fp[9], fm[9], Pp[9], Pm[9];
+        for (int i = 0; i < 3; i++)
+            for (int J = 0; J < 3; J++) {
+                const double f = F[(3 * i + J) * V + v], aN = a[i] * N[J];
+                fp[3 * i + J] = f + aN / cp;
+                fm[3 * i + J] = f - aN / cm;
+            }
+        if (!nh_P64(fp, mat.v[1], mat.v[3], Pp) || !nh_P64(fm, mat.v[0], mat.v[2], Pm)) {
+            atomicCAS(&sc->status, 0, COMBO_E_INADMISSIBLE);
+            continue;
+        }
+        for (int c = 0; c < 9; c++) {
+            s[c] += cm * Pm[c];
+            s[9 + c] += cp * Pp[c];
+        }
+        s[18] += cm;
+        s[19] += cp;
+    }
+    // block sum (fixed order) -> part[blockIdx.x][PHASE_SUMS]
+    __shared__ double red[8][PHASE_SUMS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < PHASE_SUMS; k++) {
+        double x = s[k];
+        for (int o = 16; o >= 1; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+        if (lane == 0) red[warp][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < PHASE_SUMS) {
+        double x = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) x += red[w][threadIdx.x];
+        part[(int64_t)blockIdx.x * PHASE_SUMS + threadIdx.x] = x;
+    }
+}
+
 static int grid_for(int64_t n, int block = 256)
 {
     int64_t g = (n + block - 1) / block;
@@ -835,6 +926,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     Tc *d_tc = nullptr, *d_x = nullptr, *d_r = nullptr, *d_p = nullptr;
     double* d_part = nullptr;
     Scalars* d_sc = nullptr;  // [B]
+    double* d_phpart = nullptr;  // [PHASE_GRID][PHASE_SUMS] phase-average partials
     double mu0 = 0.0;
     // stacked problems (a batch of B equal grids along z; B = 1 for one solve)
     int B = 1;
@@ -857,6 +949,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     int cg_step_total = 0;
     double Fprev[9];
     std::vector<double> Pbar, resid;
+    std::vector<double> Pphase;  // [n_steps][2][9] phase averages Pbar_-, Pbar_+
     std::vector<int32_t> iters, cg_iters;
     int64_t ops_done = 0;
     int error = 0;
@@ -882,6 +975,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         cudaFree(d_p);
         cudaFree(d_part);
         cudaFree(d_sc);
+        cudaFree(d_phpart);
         cudaFree(d_mat);
         cudaFree(d_dF);
         cudaFree(d_dv);
@@ -945,6 +1039,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         const int nbuf = std::max(std::max(e64.xpartials(), e64.zblocks()), std::max(ec.xpartials(), ec.zblocks()));
         CK(cudaMalloc(&d_part, 8 * (size_t)nbuf));
         CK(cudaMalloc(&d_sc, sizeof(Scalars) * B));
+        CK(cudaMalloc(&d_phpart, sizeof(double) * PHASE_GRID * PHASE_SUMS));
         CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars) * B, st));
         if (B > 1) {
             std::vector<double> mat(4 * B);
@@ -1017,6 +1112,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             mu0 = 0.5 * (std::min(hp.mu[0], hp.mu[1]) + std::max(hp.lam[0] + 2 * hp.mu[0], hp.lam[1] + 2 * hp.mu[1]));
         for (int c = 0; c < 9; c++) Fprev[c] = (c == 0 || c == 4 || c == 8) ? 1.0 : 0.0;
         Pbar.assign(9 * (size_t)hp.n_steps, 0.0);
+        Pphase.assign(18 * (size_t)hp.n_steps, 0.0);
         resid.assign(hp.n_steps, 0.0);
         iters.assign(hp.n_steps, 0);
         cg_iters.assign(hp.n_steps, 0);
@@ -1341,13 +1437,40 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         return COMBO_OK;
     }
 
-    void record_step(const Scalars& s)
+    // Pbar_- and Pbar_+ of the converged state of one problem (Sec. 6.2 phase
+    // averages): out[0..8] the matrix, out[9..17] the inclusion
+    int phase_avg(int64_t v0, int64_t v1, int64_t b0, int64_t b1, const double mu[2], const double lam[2],
+                  double* out)
     {
+        Mat9 m{};
+        m.v[0] = mu[0];
+        m.v[1] = mu[1];
+        m.v[2] = lam[0];
+        m.v[3] = lam[1];
+        k_phase_sums<<<PHASE_GRID, 256, 0, st>>>(d_F, g.V, d_phase, v0, v1, d_bidx, d_bN, d_bc, d_ba, b0, b1, m,
+                                                 d_phpart, d_sc);
+        CK(cudaGetLastError());
+        std::vector<double> part((size_t)PHASE_GRID * PHASE_SUMS);
+        CK(cudaMemcpyAsync(part.data(), d_phpart, 8 * part.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double tot[PHASE_SUMS] = {0.0};
+        for (int blk = 0; blk < PHASE_GRID; blk++)
+            for (int k = 0; k < PHASE_SUMS; k++) tot[k] += part[(size_t)blk * PHASE_SUMS + k];
+        for (int ph = 0; ph < 2; ph++)
+            for (int c = 0; c < 9; c++) out[9 * ph + c] = tot[18 + ph] > 0.0 ? tot[9 * ph + c] / tot[18 + ph] : 0.0;
+        return COMBO_OK;
+    }
+
+    int record_step(const Scalars& s)
+    {
+        int rc = phase_avg(0, g.V, 0, nb, hp.mu, hp.lam, Pphase.data() + 18 * (size_t)step);
+        if (rc) return rc;
         for (int c = 0; c < 9; c++) Pbar[9 * step + c] = s.Pbar[c];
         resid[step] = s.eps;
         iters[step] = newton() ? outer : s.outer_iter;
         cg_iters[step] = cg_step_total;
         step++;
+        return COMBO_OK;
     }
 
     int advance(int64_t max_ops) override
@@ -1382,7 +1505,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                     ops_done = (int64_t)s.n_operator;
                     if (s.status) return error = fail(s.status, "fixed point failed" + boxel_failure(s));
                     if (s.outer_done) {
-                        record_step(s);
+                        if ((rc = record_step(s))) return error = rc;
                         state = ST_STEP;
                     }
                     break;
@@ -1395,7 +1518,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                     if (s.status) return error = fail(s.status, "residual evaluation failed" + boxel_failure(s));
                     const bool conv = (opt.fixed_iterations > 0) ? (outer >= opt.fixed_iterations) : (s.eps <= opt.tol);
                     if (conv) {
-                        record_step(s);
+                        if ((rc = record_step(s))) return error = rc;
                         state = ST_STEP;
                     } else if (outer >= opt.max_iter) {
                         return error = fail(COMBO_E_NOT_CONVERGED, "Newton did not converge");
@@ -1460,7 +1583,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         int step = 0, outer = 0, cg_total = 0;
         bool active = false;
         double Fprev[9];
-        std::vector<double> Pbar, resid;
+        std::vector<double> Pbar, resid, Pphase;
         std::vector<int32_t> iters, cg_iters;
     };
     std::vector<PState> ps;
@@ -1499,6 +1622,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             for (int c = 0; c < 9; c++) ps[b].Fprev[c] = (c == 0 || c == 4 || c == 8) ? 1.0 : 0.0;
             const int S = hps[b].n_steps;
             ps[b].Pbar.assign(9 * (size_t)S, 0.0);
+            ps[b].Pphase.assign(18 * (size_t)S, 0.0);
             ps[b].resid.assign(S, 0.0);
             ps[b].iters.assign(S, 0);
             ps[b].cg_iters.assign(S, 0);
@@ -1549,6 +1673,9 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                     const Scalars& sb = hsc[b];
                     const bool conv = (opt.fixed_iterations > 0) ? (q.outer >= opt.fixed_iterations) : (sb.eps <= opt.tol);
                     if (conv) {
+                        if ((rc = phase_avg((int64_t)b * Vp, (int64_t)(b + 1) * Vp, boff[b], boff[b + 1], hps[b].mu,
+                                            hps[b].lam, q.Pphase.data() + 18 * (size_t)q.step)))
+                            return error = rc;
                         for (int c = 0; c < 9; c++) q.Pbar[9 * q.step + c] = sb.Pbar[c];
                         q.resid[q.step] = sb.eps;
                         q.iters[q.step] = q.outer;
@@ -1646,6 +1773,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             const cudaMemcpyKind d2x = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
             const PState& q = ps[b];
             CK(cudaMemcpy(r->Pbar, q.Pbar.data(), 8 * q.Pbar.size(), h2x));
+            if (r->Pbar_phase) CK(cudaMemcpy(r->Pbar_phase, q.Pphase.data(), 8 * q.Pphase.size(), h2x));
             if (r->iters) CK(cudaMemcpy(r->iters, q.iters.data(), 4 * q.iters.size(), h2x));
             if (r->cg_iters) CK(cudaMemcpy(r->cg_iters, q.cg_iters.data(), 4 * q.cg_iters.size(), h2x));
             if (r->resid) CK(cudaMemcpy(r->resid, q.resid.data(), 8 * q.resid.size(), h2x));
@@ -1684,6 +1812,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         const cudaMemcpyKind h2x = dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
         const cudaMemcpyKind d2x = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         CK(cudaMemcpy(r->Pbar, Pbar.data(), 8 * Pbar.size(), h2x));
+        if (r->Pbar_phase) CK(cudaMemcpy(r->Pbar_phase, Pphase.data(), 8 * Pphase.size(), h2x));
         if (r->iters) CK(cudaMemcpy(r->iters, iters.data(), 4 * iters.size(), h2x));
         if (r->cg_iters) CK(cudaMemcpy(r->cg_iters, cg_iters.data(), 4 * cg_iters.size(), h2x));
         if (r->resid) CK(cudaMemcpy(r->resid, resid.data(), 8 * resid.size(), h2x));
@@ -2119,7 +2248,7 @@ struct ServeReq {
     enum { QUEUED, RUNNING, DONE } st = QUEUED;
     int rc = 0;
     std::string err;
-    std::vector<double> Pbar, resid, F, P;
+    std::vector<double> Pbar, resid, F, P, Pphase;
     std::vector<int32_t> iters, cg;
     combo_result res{};
     double t_submit = 0, t_start = 0, t_done = 0;
@@ -2198,11 +2327,13 @@ static void gather_batch(combo_server* S, ServeReq* r, std::vector<ServeReq*>& b
 static combo_result request_buffers(ServeReq* r, int32_t n_steps, int64_t V, bool fields)
 {
     r->Pbar.assign(9 * (size_t)n_steps, 0.0);
+    r->Pphase.assign(18 * (size_t)n_steps, 0.0);
     r->resid.assign(n_steps, 0.0);
     r->iters.assign(n_steps, 0);
     r->cg.assign(n_steps, 0);
     combo_result res{};
     res.Pbar = r->Pbar.data();
+    res.Pbar_phase = r->Pphase.data();
     res.resid = r->resid.data();
     res.iters = r->iters.data();
     res.cg_iters = r->cg.data();
@@ -2220,6 +2351,7 @@ static void keep_result(ServeReq* r, const combo_result& res)
 {
     r->res = res;
     r->res.Pbar = nullptr;
+    r->res.Pbar_phase = nullptr;
     r->res.F_out = r->res.P_out = nullptr;
     r->res.resid = nullptr;
     r->res.iters = r->res.cg_iters = nullptr;
@@ -2444,6 +2576,8 @@ static int collect(combo_server* S, ServeReq* r, combo_result* out)
     if (out) {
         const int32_t ns = (int32_t)r->iters.size();
         if (out->Pbar && !r->Pbar.empty()) std::memcpy(out->Pbar, r->Pbar.data(), 8 * r->Pbar.size());
+        if (out->Pbar_phase && !r->Pphase.empty())
+            std::memcpy(out->Pbar_phase, r->Pphase.data(), 8 * r->Pphase.size());
         if (out->iters && ns) std::memcpy(out->iters, r->iters.data(), 4 * (size_t)ns);
         if (out->cg_iters && ns) std::memcpy(out->cg_iters, r->cg.data(), 4 * (size_t)ns);
         if (out->resid && ns) std::memcpy(out->resid, r->resid.data(), 8 * (size_t)ns);

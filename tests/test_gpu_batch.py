@@ -54,6 +54,7 @@ def test_batch_equals_individual_solves_fp64(cb, n):
         assert np.array_equal(a["iters"], b["iters"])
         assert np.all(np.abs(a["cg_iters"] - b["cg_iters"]) <= 1)
         assert rel(b["Pbar"], a["Pbar"]) < 1e-9
+        assert rel(b["Pbar_phase"], a["Pbar_phase"]) < 1e-8
         assert rel(b["F"], a["F"]) < 1e-8
         assert rel(b["P"], a["P"]) < 1e-8
         assert np.all(b["resid"] <= 1e-8)
@@ -69,6 +70,7 @@ def test_batch_refined_at_compile_time_sizes(cb, prec):
     for p, a, b in zip(probs, alone, batch):
         assert b["steps_done"] == p["n_steps"] and np.all(b["resid"] <= 1e-8)
         assert rel(b["Pbar"], a["Pbar"]) < 1e-6
+        assert rel(b["Pbar_phase"], a["Pbar_phase"]) < 1e-5
         assert rel(b["F"], a["F"]) < 1e-4
 
 

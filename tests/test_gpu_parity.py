@@ -123,6 +123,9 @@ def test_newton_cg_parity(cb, orc, k, kspace):
     assert rel(g["P"], r["P"]) < 1e-10
     assert rel(g["Pbar"], r["Pbar"]) < 1e-9
     assert list(g["cg_iters"]) == list(r["cg_iters"])
+    # phase averages (Sec. 6.2) of the final state
+    pa = orc.phase_averages(p, r["F"], r["a"])
+    assert rel(g["Pbar_phase"][-1], pa) < 1e-9
     # laminate NR counts may differ where |f| sits on the stopping threshold
     # within rounding (the two sides form Delta and f differently)
     assert abs(g["nr_iters"] - r["nr_iters"]) <= max(2, 1e-3 * r["nr_iters"])
@@ -183,6 +186,7 @@ def test_sphere_32_converged_fp64(cb, orc):
     assert list(g["cg_iters"]) == list(r["cg_iters"])
     assert rel(g["Pbar"], r["Pbar"]) < 1e-9
     assert rel(g["F"], r["F"]) < 1e-9
+    assert rel(g["Pbar_phase"][-1], orc.phase_averages(p, r["F"], r["a"])) < 1e-9
 
 
 @pytest.mark.parametrize("prec", [1, 2])

@@ -155,3 +155,30 @@ def test_hill_mandel_and_solvers_agree(orc):
     assert abs(hm - np.dot(r1["Pbar"][-1], p["Fbar"])) < 1e-11
     assert np.allclose(r0["Pbar"], r1["Pbar"], atol=1e-9)
     assert np.allclose(r0["F"], r1["F"], atol=1e-8)
+
+
+def test_phase_averages_split_the_mean_stress(orc):
+    """Sec. 6.2 phase averages: the volume-weighted sum of Pbar_- and Pbar_+ is
+    Pbar (P_box = c+ P+ + c- P-); a layered laminate has the exact laminate
+    phase stresses as its phase averages; with one phase, Pbar_+- = Pbar."""
+    p = ms.random_boxels((6, 5, 4), seed=31, boxel_frac=0.3, incl_frac=0.3, contrast=10.0)
+    r = orc.solve(p, dict(solver=1, **TIGHT))
+    pa = orc.phase_averages(p, r["F"], r["a"])
+    phase = np.asarray(p["phase"]).ravel()
+    c = np.asarray(p["boxel_c"])
+    vol_p = (phase == 1).sum() + c.sum()
+    vol_m = (phase == 0).sum() + (1 - c).sum()
+    assert np.allclose((vol_m * pa[0] + vol_p * pa[1]) / phase.size, r["Pbar"][-1], atol=1e-12)
+    # layered along x: every inclusion layer carries the same stress, so does every matrix layer
+    q = ms.layered((8, 4, 4), axis=0, m_incl=3, c_boxel=0.4, contrast=10.0, Fbar=np.eye(3) + 0.05, n_steps=1)
+    rq = orc.solve(q, dict(solver=1, **TIGHT))
+    Pq = rq["P"].reshape(9, 4, 4, 8)
+    paq = orc.phase_averages(q, rq["F"], rq["a"])
+    ph = np.asarray(q["phase"]).reshape(4, 4, 8)
+    assert np.allclose(paq[1], Pq[:, ph == 1].mean(1), atol=1e-11)
+    assert np.allclose(paq[0], Pq[:, ph == 0].mean(1), atol=1e-11)
+    h = ms.homogeneous((4, 4, 4), Fbar=np.eye(3) + 0.03)
+    rh = orc.solve(h, dict(solver=1, **TIGHT))
+    pah = orc.phase_averages(h, rh["F"], rh["a"])
+    assert np.allclose(pah[0], rh["Pbar"][-1], atol=1e-13)
+    assert np.all(pah[1] == 0)
