@@ -80,6 +80,11 @@ extern "C" {
 /* solver */
 #define COMBO_FIXED_POINT 0 /* basic scheme on the nonlinear LSE, Sec. 3 */
 #define COMBO_NEWTON_CG 1   /* Newton with conjugate gradients on the linearised LSE, Sec. 3 */
+/* nonlinear conjugate gradients on the nonlinear LSE (cited in Sec. 3; the
+   paper gives no steps): Fletcher-Reeves directions d = -G[P]/mu0 + beta d,
+   beta = ||G[P]||^2 / ||G[P]_prev||^2, and the basic scheme's step F += d.
+   FP64, like the fixed point. */
+#define COMBO_NONLINEAR_CG 2
 
 typedef struct combo_ctx combo_ctx;
 typedef struct combo_solve_state combo_solve_state;

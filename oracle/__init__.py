@@ -28,7 +28,7 @@ _SRC = os.path.join(_HERE, "combo_oracle.c")
 _LIB = os.path.join(_HERE, "libcombo_oracle.so")
 
 ROTATED, SPECTRAL, STAGGERED = 0, 1, 2
-FIXED_POINT, NEWTON_CG = 0, 1
+FIXED_POINT, NEWTON_CG, NONLINEAR_CG = 0, 1, 2
 
 STATUS = {0: "ok", -1: "invalid", -3: "not converged", -4: "laminate NR failed",
           -5: "inadmissible (det F <= 0)", -6: "NaN"}

@@ -600,7 +600,7 @@ typedef struct {
 } orc_problem;
 
 typedef struct {
-    int32_t solver; /* 0 fixed point (basic scheme), 1 Newton-CG */
+    int32_t solver; /* 0 fixed point (basic scheme), 1 Newton-CG, 2 nonlinear CG */
     int32_t kspace; /* 0 rotated, 1 spectral, 2 staggered */
     double tol;
     int32_t max_iter;
@@ -758,6 +758,13 @@ static int all_admissible(const double* F, size_t V)
  * (Sec. 3): F <- F - Gamma0 (P(F)) = F - G[P(F)] / mu0 for compatible F with
  * mean Fbar.  READING: mu0 = (min mu + max(lam + 2 mu)) / 2.
  *
+ * Nonlinear CG (solver 2; Sec. 3 cites it, the paper gives no steps): the
+ * Fletcher-Reeves nonlinear conjugate gradient method on the energy over
+ * compatible fields, with the basic scheme's preconditioned gradient
+ * G[P(F)] / mu0 and its step length: d = -G[P]/mu0 + beta d_prev,
+ * beta = ||G[P]||^2 / ||G[P_prev]||^2 (0 at a load step's first iteration),
+ * F += d.  READING: Fletcher-Reeves, no line search.
+ *
  * Newton-CG (solver 1): Newton on G[P(F)] = 0 with the linearised system
  * G[A : dF] = -G[P] solved by conjugate gradients in the Frobenius inner
  * product on compatible zero-mean fields (Sec. 3, Newton with a fast linear
@@ -784,7 +791,8 @@ int orc_solve(const orc_problem* pb, const orc_options* op, orc_result* res)
     double* P = (double*)malloc(sizeof(double) * N9);
     double* g = (double*)malloc(sizeof(double) * N9);
     double* A = NULL;
-    double *x = NULL, *r = NULL, *p = NULL, *q = NULL, *t = NULL;
+    double *x = NULL, *r = NULL, *p = NULL, *q = NULL, *t = NULL, *dir = NULL;
+    if (op->solver == 2) dir = (double*)calloc(N9, sizeof(double));
     if (op->solver == 1) {
         A = (double*)malloc(sizeof(double) * 81 * V);
         x = (double*)malloc(sizeof(double) * N9);
@@ -816,7 +824,7 @@ int orc_solve(const orc_problem* pb, const orc_options* op, orc_result* res)
         }
         memcpy(Fprev, Fn, sizeof(Fn));
         int it = 0, cg_total = 0;
-        double eps = 0.0, Pbar[9];
+        double eps = 0.0, Pbar[9], gg_prev = 0.0;
         for (;;) {
             int rc = constitutive(&cx, F, P, A, &res->nr_iters, &res->n_backproj, &res->n_lam_evals);
             if (rc) {
@@ -838,6 +846,14 @@ int orc_solve(const orc_problem* pb, const orc_options* op, orc_result* res)
             }
             if (op->solver == 0) {
                 for (size_t w = 0; w < N9; w++) F[w] -= g[w] / mu0;
+                res->n_operator += 1;
+            } else if (op->solver == 2) {
+                const double beta = (it == 0) ? 0.0 : ss / gg_prev;
+                for (size_t w = 0; w < N9; w++) {
+                    dir[w] = -g[w] / mu0 + beta * dir[w];
+                    F[w] += dir[w];
+                }
+                gg_prev = ss;
                 res->n_operator += 1;
             } else {
                 /* CG on G[A : x] = b, b = -G[P] */
@@ -909,6 +925,7 @@ int orc_solve(const orc_problem* pb, const orc_options* op, orc_result* res)
     free(p);
     free(q);
     free(t);
+    free(dir);
     return status;
 }
 

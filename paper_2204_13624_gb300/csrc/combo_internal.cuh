@@ -104,6 +104,7 @@ struct Scalars {
     unsigned long long nr_iters, n_backproj, n_lam;
     unsigned long long n_operator, n_operator64;
     unsigned int ticket[4];  // last-block counters of fused reductions
+    double ncg_gg;           // nonlinear CG: ||G[P]||^2 of the previous iteration
     double alpha_pending;    // x += alpha_pending p still owed by the last CG update
     // first failed laminate solve: 1 + boxel index (0: none), reason (1 F_box
     // inadmissible, 2 a phase inadmissible, 3 singular Hessian, 4 iteration
@@ -360,7 +361,7 @@ __host__ __device__ constexpr int sym_idx(int r, int s)
 {
     return r <= s ? 9 * r - r * (r - 1) / 2 + (s - r) : 9 * s - s * (s - 1) / 2 + (r - s);
 }
-enum XinvMode { XI_FIXEDPOINT = 0, XI_RHS = 1, XI_CG = 2, XI_PLAIN = 3 };
+enum XinvMode { XI_FIXEDPOINT = 0, XI_RHS = 1, XI_CG = 2, XI_PLAIN = 3, XI_NCG = 4 };
 
 template <typename T, typename Tc> struct XfwdArgs {
     GridDims g;
@@ -403,7 +404,8 @@ template <typename T, typename Tc> struct XinvArgs {
     int lines_per_block;
     int mode;
     double inv_mu0;
-    double* F;       // XI_FIXEDPOINT
+    double* F;       // XI_FIXEDPOINT / XI_NCG
+    double* d;       // XI_NCG: the direction [9][V]
     Tc* x;           // XI_RHS / XI_CG
     Tc* r;
     const Tc* p;

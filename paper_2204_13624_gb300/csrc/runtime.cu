@@ -504,7 +504,7 @@ __device__ double sum_partials(const double* p, int n, double* red) { return sum
 // Block b: problem b, partials part[b n .. b n + n); V voxels per problem.
 // skip_done: problems whose outer_done is set were not evaluated.
 __global__ void k_fin_resid(Scalars* scs, const double* part_all, int n, double V, double tol, int fixed, int max_iter,
-                            int fixed_point, int skip_done = 0)
+                            int fixed_point, int skip_done = 0, int ncg = 0)
 {
     __shared__ double red[256];
     Scalars* sc = scs + blockIdx.x;
@@ -537,6 +537,10 @@ __global__ void k_fin_resid(Scalars* scs, const double* part_all, int n, double 
         } else {
             sc->outer_iter = it + 1;
             sc->n_operator += 1;
+            if (ncg) {  // Fletcher-Reeves beta; 0 at a load step's first iteration
+                sc->beta = (it == 0) ? 0.0 : s / sc->ncg_gg;
+                sc->ncg_gg = s;
+            }
         }
     }
 }
@@ -832,10 +836,11 @@ static int check_options(combo_options& o)
     if (o.precision != COMBO_FP64 && o.precision != COMBO_FP32_REFINED && o.precision != COMBO_FP32_REFINED_DF)
         return fail(COMBO_E_INVALID_ARG, "bad precision");
     if (o.kspace != COMBO_ROTATED && o.kspace != COMBO_SPECTRAL && o.kspace != COMBO_STAGGERED) return fail(COMBO_E_INVALID_ARG, "bad kspace");
-    if (o.solver != COMBO_FIXED_POINT && o.solver != COMBO_NEWTON_CG) return fail(COMBO_E_INVALID_ARG, "bad solver");
-    if (o.solver == COMBO_FIXED_POINT && o.precision != COMBO_FP64)
-        return fail(COMBO_E_INVALID_ARG, "the fixed point runs in FP64 only");
-    if (o.max_iter <= 0) o.max_iter = (o.solver == COMBO_FIXED_POINT) ? 100000 : 200;
+    if (o.solver != COMBO_FIXED_POINT && o.solver != COMBO_NEWTON_CG && o.solver != COMBO_NONLINEAR_CG)
+        return fail(COMBO_E_INVALID_ARG, "bad solver");
+    if (o.solver != COMBO_NEWTON_CG && o.precision != COMBO_FP64)
+        return fail(COMBO_E_INVALID_ARG, "the fixed point and nonlinear CG run in FP64 only");
+    if (o.max_iter <= 0) o.max_iter = (o.solver == COMBO_NEWTON_CG) ? 200 : 100000;
     if (!(o.tol >= 0.0) || !(o.cg_tol >= 0.0)) return fail(COMBO_E_INVALID_ARG, "negative tolerance");
     if (o.nr_max_iter <= 0) o.nr_max_iter = 50;
     if (!(o.c_min >= 0.0 && o.c_min < 0.5)) return fail(COMBO_E_INVALID_ARG, "c_min outside [0, 0.5)");
@@ -927,6 +932,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     double* d_part = nullptr;
     Scalars* d_sc = nullptr;  // [B]
     double* d_phpart = nullptr;  // [PHASE_GRID][PHASE_SUMS] phase-average partials
+    double* d_dir = nullptr;     // nonlinear CG direction [9][V]
     double mu0 = 0.0;
     // stacked problems (a batch of B equal grids along z; B = 1 for one solve)
     int B = 1;
@@ -976,6 +982,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         cudaFree(d_part);
         cudaFree(d_sc);
         cudaFree(d_phpart);
+        cudaFree(d_dir);
         cudaFree(d_mat);
         cudaFree(d_dF);
         cudaFree(d_dv);
@@ -1040,6 +1047,10 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         CK(cudaMalloc(&d_part, 8 * (size_t)nbuf));
         CK(cudaMalloc(&d_sc, sizeof(Scalars) * B));
         CK(cudaMalloc(&d_phpart, sizeof(double) * PHASE_GRID * PHASE_SUMS));
+        if (opt.solver == COMBO_NONLINEAR_CG) {
+            CK(cudaMalloc(&d_dir, sizeof(double) * 9 * (size_t)g.V));
+            CK(cudaMemsetAsync(d_dir, 0, sizeof(double) * 9 * (size_t)g.V, st));
+        }
         CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars) * B, st));
         if (B > 1) {
             std::vector<double> mat(4 * B);
@@ -1302,12 +1313,14 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         e64.yz(d_sc, guard, true, d_part, st, &prof, K_YFWD_64);
         prof.begin(K_FINALIZE);
         k_fin_resid<<<B, 256, 0, st>>>(d_sc, d_part, e64.zblocks_p(), (double)Vp, opt.tol, opt.fixed_iterations,
-                                       opt.max_iter, xi_mode == XI_FIXEDPOINT ? 1 : 0, B > 1 ? 1 : 0);
+                                       opt.max_iter, (xi_mode == XI_FIXEDPOINT || xi_mode == XI_NCG) ? 1 : 0,
+                                       B > 1 ? 1 : 0, xi_mode == XI_NCG ? 1 : 0);
         prof.end();
         auto xi = e64.template xi<Tc>();
         xi.mode = xi_mode;
         xi.inv_mu0 = 1.0 / mu0;
         xi.F = d_F;
+        xi.d = d_dir;
         xi.x = d_x;
         xi.r = d_r;
         xi.partial = d_part;
@@ -1498,7 +1511,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                     const int chunk = 16;
                     for (int k = 0; k < chunk; k++) {
                         boxels(false, 2);
-                        resid_operator(XI_FIXEDPOINT, 2);
+                        resid_operator(opt.solver == COMBO_NONLINEAR_CG ? XI_NCG : XI_FIXEDPOINT, 2);
                     }
                     CK(cudaGetLastError());
                     if ((rc = read_scalars(s))) return error = rc;
@@ -1882,6 +1895,7 @@ extern "C" int64_t combo_solve_footprint(const combo_problem* p, const combo_opt
     const int64_t tc = (o->precision == COMBO_FP64) ? 8 : 4;
     int64_t b = V * (1 + 4 + 72) + 16 * 9 * g.Vs + nb * (4 + 24 + 8 + 24 + 72);
     if (o->solver == COMBO_NEWTON_CG) b += tc * (81 * nb + 37 * V);
+    if (o->solver == COMBO_NONLINEAR_CG) b += 72 * V;
     return b;
 }
 

@@ -409,7 +409,8 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
     const int nl = 9 * LB;
     const int64_t V = g.V;
     double acc = 0.0;
-    const bool skip_update = (a.mode == XI_FIXEDPOINT) && sc->outer_done;
+    const bool skip_update = (a.mode == XI_FIXEDPOINT || a.mode == XI_NCG) && sc->outer_done;
+    const double ncg_beta = (a.mode == XI_NCG) ? sc->beta : 0.0;
     const Tc alpha = (a.mode == XI_CG) ? (Tc)sc->alpha : (Tc)0;
 
     // grid-stride over the problem's groups of LB x-lines
@@ -463,6 +464,23 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
                 for (int c = 0; c < 9; c++) Fo[c] = Fg[c * V + v];
 #pragma unroll
                 for (int c = 0; c < 9; c++) Fg[c * V + v] = Fo[c] - (double)rb[(size_t)2 * (c * LB + l) * ls + x] * a.inv_mu0;
+            } else if (a.mode == XI_NCG) {
+                // d = -G[P]/mu0 + beta d, F += d (Fletcher-Reeves, basic-scheme step)
+                if (skip_update) continue;
+                double* __restrict__ Fg = a.F;
+                double* __restrict__ dg = a.d;
+                double Fo[9], dn[9];
+#pragma unroll
+                for (int c = 0; c < 9; c++) {
+                    Fo[c] = Fg[c * V + v];
+                    dn[c] = dg[c * V + v];
+                }
+#pragma unroll
+                for (int c = 0; c < 9; c++) {
+                    const double d = -(double)rb[(size_t)2 * (c * LB + l) * ls + x] * a.inv_mu0 + ncg_beta * dn[c];
+                    dg[c * V + v] = d;
+                    Fg[c * V + v] = Fo[c] + d;
+                }
             } else if (a.mode == XI_RHS) {
 #pragma unroll
                 for (int c = 0; c < 9; c++) {

@@ -114,6 +114,31 @@ def test_fixed_point_parity(cb, orc, k):
     assert g["n_operator"] == r["n_operator"]
 
 
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_nonlinear_cg_parity(cb, orc, k):
+    """Nonlinear CG (Fletcher-Reeves, basic-scheme step): iteration by
+    iteration equal to the oracle."""
+    p = problems()[k]
+    g, r = solve_both(cb, orc, p, solver=2, fixed_iterations=7)
+    assert rel(g["F"], r["F"]) < 1e-10
+    assert rel(g["Pbar"], r["Pbar"]) < 1e-9
+    assert list(g["iters"]) == list(r["iters"])
+
+
+def test_nonlinear_cg_converged(cb, orc):
+    """The 32^3 ball to tol 1e-8 by nonlinear CG: same iteration counts as the
+    oracle, and the state Newton-CG reaches."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.sphere_32()
+    g, r = solve_both(cb, orc, p, solver=2, tol=1e-8)
+    assert g["steps_done"] == 5 and np.all(g["resid"] <= 1e-8)
+    assert np.all(np.abs(np.asarray(g["iters"]) - np.asarray(r["iters"])) <= 1)
+    assert rel(g["Pbar"], r["Pbar"]) < 1e-8
+    gn = cb.solve(p, solver=1, tol=1e-10)
+    assert rel(g["Pbar"][-1], gn["Pbar"][-1]) < 1e-7
+
+
 @pytest.mark.parametrize("kspace", [0, 1, 2])
 @pytest.mark.parametrize("k", [0, 1, 2])
 def test_newton_cg_parity(cb, orc, k, kspace):

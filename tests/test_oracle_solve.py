@@ -182,3 +182,21 @@ def test_phase_averages_split_the_mean_stress(orc):
     pah = orc.phase_averages(h, rh["F"], rh["a"])
     assert np.allclose(pah[0], rh["Pbar"][-1], atol=1e-13)
     assert np.all(pah[1] == 0)
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_nonlinear_cg_reaches_the_newton_solution(orc, k):
+    """Nonlinear CG (Sec. 3): its first iteration of a load step is the basic
+    scheme's; converged, it reaches the state Newton-CG reaches (the discrete
+    equilibrium is unique), in far fewer iterations than the basic scheme."""
+    p = [ms.centred_sphere((12, 12, 12), 0.2, 10.0, np.diag([1.04, 1.0, 0.99]), 2),
+         ms.random_boxels((12, 6, 9), seed=7, contrast=10.0, n_steps=2)][k]
+    r0 = orc.solve(p, dict(solver=0, fixed_iter=1))
+    r2 = orc.solve(p, dict(solver=2, fixed_iter=1))
+    assert np.array_equal(r0["F"], r2["F"])
+    rn = orc.solve(p, dict(solver=2, tol=1e-10, max_iter=5000))
+    rN = orc.solve(p, dict(solver=1, tol=1e-10))
+    rb = orc.solve(p, dict(solver=0, tol=1e-10, max_iter=20000))
+    assert np.allclose(rn["F"], rN["F"], atol=1e-8)
+    assert np.allclose(rn["Pbar"], rN["Pbar"], atol=1e-10)
+    assert 3 * rn["iters"].sum() < rb["iters"].sum()
