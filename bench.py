@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-normals", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--normals-only", default=None, metavar="N1,N2,N3",
                     help="only coarse-grain a seeded spheres image of this size (8^3 boxels), three calls "
                          "(profiling captures of the coarse-graining kernels)")
@@ -238,7 +239,11 @@ def main():
     if dist:
         dist.barrier()
     combo.load()
-    stream = torch.cuda.current_stream()
+    # one explicit stream for torch and the library, so that the CUDA events
+    # bracket the library's launches and torch's allocations are ordered
+    # with them (the default stream's handle would give the library its own)
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
     ctx = combo.Context(local, stream.cuda_stream)
     if args.normals_only:
         from paper_2204_13624_gb300 import microstructure as ms
@@ -333,6 +338,9 @@ def main():
     batch = None
     if not args.no_batch and rank == 0:
         batch = batch_bench(combo, ctx)
+    variants = None
+    if not args.no_variants and rank == 0:
+        variants = variants_bench(combo, ctx)
     normals = None
     if not args.no_normals and rank == 0:
         normals = normals_bench(combo, ctx, stream, peak, peak_kind, cpu=not args.no_cpu_baseline and world == 1)
@@ -359,7 +367,7 @@ def main():
                            "autotune": combo.autotune_report().strip().splitlines(),
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "batch": batch,
-                "normal_detection": normals, "gpu_launches": launches,
+                "normal_detection": normals, "variants": variants, "gpu_launches": launches,
                 "clocks": clocks, "kernels": table}
         if args.profile_json:
             json.dump(line, open(args.profile_json, "w"), indent=1)
@@ -587,6 +595,43 @@ def normals_bench(combo, ctx, stream, peak, peak_kind, cpu=True, reps=20):
                    "call's host synchronisation); ms_pack/slab/scan/scatter/finish: library events around each "
                    "launch; fine_voxels_per_s from their sum")
     out["gpu_launches"] = launches
+    return out
+
+
+def variants_bench(combo, ctx):
+    """Solver and discretisation variants on one 128^3 problem (seeded random
+    balls, radius 8 voxels, vf 0.2, contrast 10, Fbar_11 = 1.05 in 2 steps,
+    tol 1e-8): wall clock of combo_solve from host buffers, operator
+    applications, and Pbar against the rotated Newton-CG result."""
+    import torch
+
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.random_spheres((128, 128, 128), 8.0, 0.2, ms.SEED_BASE + 6, 10.0, np.diag([1.05, 1.0, 1.0]), 2)
+    V = 128 ** 3
+    runs = [("newton_cg_rotated_refined_df", dict(solver=combo.NEWTON_CG, precision=combo.FP32_REFINED_DF)),
+            ("newton_cg_rotated_fp64", dict(solver=combo.NEWTON_CG, precision=combo.FP64)),
+            ("newton_cg_spectral_refined_df", dict(solver=combo.NEWTON_CG, precision=combo.FP32_REFINED_DF,
+                                                   kspace=combo.SPECTRAL)),
+            ("newton_cg_staggered_refined_df", dict(solver=combo.NEWTON_CG, precision=combo.FP32_REFINED_DF,
+                                                    kspace=combo.STAGGERED)),
+            ("nonlinear_cg_rotated_fp64", dict(solver=combo.NONLINEAR_CG, precision=combo.FP64)),
+            ("basic_scheme_rotated_fp64", dict(solver=combo.FIXED_POINT, precision=combo.FP64))]
+    out = {"problem": "128^3 random balls r=8 vox, vf 0.2, contrast 10, Fbar11 = 1.05 in 2 steps, tol 1e-8"}
+    ref = None
+    for name, o in runs:
+        combo.solve(p, ctx=ctx, fields=False, tol=1e-8, **o)  # warm (tables, autotuner)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = combo.solve(p, ctx=ctx, fields=False, tol=1e-8, **o)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if ref is None:
+            ref = r["Pbar"][-1]
+        out[name] = {"seconds": dt, "outer_iterations": [int(v) for v in r["iters"]],
+                     "operator_applications": int(r["n_operator"]),
+                     "voxel_iterations_per_s": int(r["n_operator"]) * V / dt,
+                     "Pbar_rel_diff_vs_rotated_newton": float(np.linalg.norm(r["Pbar"][-1] - ref) / np.linalg.norm(ref))}
     return out
 
 

@@ -138,6 +138,17 @@ def _is_dev(a):
     return hasattr(a, "is_cuda") and a.is_cuda
 
 
+def _torch_quiesce():
+    """Wait for the work pending on torch's current stream before the library
+    touches device memory torch allocated.  The library launches on its
+    context's stream; torch's caching allocator orders reuse on torch's
+    stream only, so a tensor handed out just now may sit in a block that a
+    torch kernel still pending on that stream reads or writes."""
+    import torch
+
+    torch.cuda.current_stream().synchronize()
+
+
 class Context:
     """A device, its stream and the library's memory (combo_ctx)."""
 
@@ -270,6 +281,8 @@ def solve(prob: dict, ctx: Context | None = None, fields: bool = True, device_re
     pb = Problem(prob)
     o = options(**opts)
     out, r = _result_buffers(pb, fields, device_results)
+    if device_results or pb.s.mem == MEM_DEVICE:
+        _torch_quiesce()
     _check(load().combo_solve(ctx.h, C.byref(pb.s), C.byref(o), C.byref(r)))
     return _collect(out, r, pb.n_boxels)
 
@@ -301,6 +314,8 @@ def solve_batch(probs: list, ctx: Context | None = None, fields: bool = True, de
     bufs = [_result_buffers(pb, fields, device_results) for pb in pbs]
     parr = (ProblemS * len(pbs))(*[pb.s for pb in pbs])
     rarr = (ResultS * len(pbs))(*[r for _, r in bufs])
+    if device_results or any(pb.s.mem == MEM_DEVICE for pb in pbs):
+        _torch_quiesce()
     _check(load().combo_solve_batch(ctx.h, len(pbs), C.byref(parr), C.byref(o), C.byref(rarr)))
     return [_collect(out, rarr[i], pbs[i].n_boxels) for i, (out, _) in enumerate(bufs)]
 
@@ -313,6 +328,8 @@ class Solve:
         self.pb = Problem(prob)
         self.o = options(**opts)
         h = C.c_void_p()
+        if self.pb.s.mem == MEM_DEVICE:
+            _torch_quiesce()
         _check(load().combo_solve_begin(self.ctx.h, C.byref(self.pb.s), C.byref(self.o), C.byref(h)))
         self.h = h
 
@@ -322,6 +339,8 @@ class Solve:
 
     def finish(self, fields: bool = True, device_results: bool = False):
         out, r = _result_buffers(self.pb, fields, device_results)
+        if device_results:
+            _torch_quiesce()
         _check(load().combo_solve_finish(self.h, C.byref(r)))
         return _collect(out, r, self.pb.n_boxels)
 
@@ -370,6 +389,7 @@ def apply_G(X, n, l=(1.0, 1.0, 1.0), kspace=ROTATED, precision=FP64, ctx: Contex
 
         X = X.contiguous().to(torch.float64)
         Y = torch.empty_like(X)
+        _torch_quiesce()
     else:
         X = np.ascontiguousarray(X, dtype=np.float64)
         Y = np.zeros_like(X)
@@ -428,6 +448,7 @@ def coarse_grain(chi, b, h=(1.0, 1.0, 1.0), method="laplace", ctx: Context | Non
         idx = torch.empty(max(cap, 1), dtype=torch.int64, **kw)
         N = torch.empty((max(cap, 1), 3), dtype=torch.float64, **kw)
         c = torch.empty(max(cap, 1), dtype=torch.float64, **kw)
+        _torch_quiesce()
     else:
         chi = np.ascontiguousarray(chi, dtype=np.uint8)
         phase = np.empty(ncv, np.uint8)
@@ -464,6 +485,7 @@ def apply_G_noalloc(X, Y, n, l=(1.0, 1.0, 1.0), kspace=ROTATED, device=0, stream
     sum |Y|^2 (synchronising the stream) or None."""
     if not (_is_dev(X) and _is_dev(Y)):
         raise ComboError(-1, "apply_G_noalloc takes CUDA tensors")
+    _torch_quiesce()
     nn = (C.c_int32 * 3)(*[int(v) for v in n])
     ll = (C.c_double * 3)(*[float(v) for v in l])
     ss = C.c_double(0.0)

@@ -93,9 +93,11 @@ __device__ __forceinline__ uint32_t pack16(uint4 v)
     uint32_t m = 0;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        // byte flags at bits 0, 8, 16, 24; the product gathers them at bits 21..24
-        const uint32_t f = __vcmpne4(w[k], 0u) & 0x01010101u;
-        m |= ((f * 0x00204081u) >> 21 & 0xFu) << (4 * k);
+        // bit 7 of each byte: the byte is nonzero (adding 0x7F to its low
+        // seven bits carries into bit 7 unless they are all zero)
+        const uint32_t t = (((w[k] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w[k]) & 0x80808080u;
+        // the product moves bits 7, 15, 23, 31 to bits 28..31 without carries
+        m |= ((t * 0x00204081u) >> 28) << (4 * k);
     }
     return m;
 }
