@@ -27,7 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "combo_oracle.c")
 _LIB = os.path.join(_HERE, "libcombo_oracle.so")
 
-ROTATED, SPECTRAL, STAGGERED = 0, 1, 2
+ROTATED, SPECTRAL, STAGGERED, STAGGERED_DFMG = 0, 1, 2, 3
 FIXED_POINT, NEWTON_CG, NONLINEAR_CG = 0, 1, 2
 
 STATUS = {0: "ok", -1: "invalid", -3: "not converged", -4: "laminate NR failed",

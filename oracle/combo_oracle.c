@@ -415,6 +415,7 @@ void orc_fft3(const int n[3], int sign, double* data_ri)
 #define ORC_ROTATED 0
 #define ORC_SPECTRAL 1
 #define ORC_STAGGERED 2
+#define ORC_STAGGERED_DFMG 3 /* staggered grid with the doubly-fine material grid */
 
 /*
  * ROTATED (Willot's rotated / HEX8R scheme, Sec. 3 and Sec. 6.3): the
@@ -476,7 +477,7 @@ void orc_kvec(int kspace, const int n[3], const double l[3], const int xi[3], do
 /* the derivative vector of row a of F: k_a[B], B = 0..2 */
 static void row_kvecs(int kspace, const int n[3], const double l[3], const int xi[3], cplx kr[3][3])
 {
-    if (kspace == ORC_STAGGERED) {
+    if (kspace == ORC_STAGGERED || kspace == ORC_STAGGERED_DFMG) {
         for (int B = 0; B < 3; B++) {
             const double t = 2.0 * M_PI * (double)xi[B] / (double)n[B];
             const double h = l[B] / (double)n[B];
@@ -601,7 +602,7 @@ typedef struct {
 
 typedef struct {
     int32_t solver; /* 0 fixed point (basic scheme), 1 Newton-CG, 2 nonlinear CG */
-    int32_t kspace; /* 0 rotated, 1 spectral, 2 staggered */
+    int32_t kspace; /* 0 rotated, 1 spectral, 2 staggered, 3 staggered + doubly-fine material grid */
     double tol;
     int32_t max_iter;
     int32_t fixed_iter; /* > 0: exactly this many outer iterations per load step */
@@ -638,13 +639,139 @@ typedef struct {
     const orc_options* op;
     int32_t* vox2box; /* [V] boxel index or -1 */
     double* a;        /* [nb][3] jump vectors (warm start state) */
+    double* a8;       /* doubly-fine material grid: [nb][8][3] jump vectors of the sub-cells */
 } orc_ctx;
+
+/* Material law of cell v at Fs (pure Neo-Hookean, or the laminate of a boxel
+ * cell from the warm start a_ws, updated). */
+static int cell_law(orc_ctx* cx, long v, const double Fs[9], double a_ws[3], double P[9], int64_t* its_o,
+                    int64_t* nbp_o)
+{
+    const orc_problem* pb = cx->pb;
+    int b = cx->vox2box[v];
+    int ph = pb->phase[v];
+    double cpl = 0.0;
+    if (b >= 0) {
+        cpl = pb->bc[b];
+        if (cpl < cx->op->c_min) ph = 0;
+        else if (cpl > 1.0 - cx->op->c_min) ph = 1;
+    }
+    if (ph == 2) {
+        double mat[4] = {pb->mu[0], pb->lam[0], pb->mu[1], pb->lam[1]};
+        int its = 0, nbpv = 0;
+        int rc = orc_laminate(Fs, pb->bN + 3 * (size_t)b, cpl, mat, a_ws, cx->op->nr_tol_rel, cx->op->nr_tol_abs,
+                              cx->op->nr_max_iter, P, NULL, &its, &nbpv, NULL);
+        *its_o += its;
+        *nbp_o += nbpv;
+        return rc;
+    }
+    return orc_neohooke(Fs, pb->mu[ph], pb->lam[ph], P, NULL);
+}
+
+static long wrapi(long i, long n) { return ((i % n) + n) % n; }
+
+/*
+ * Doubly-fine material grid (App. A, Eq. constitutive_law): every cell is cut
+ * into 8 sub-cells l = (l1, l2, l3) in {0,1}^3; sub-cell l of cell c carries the
+ * deformation gradient F_sub(c, l) whose diagonal entries are those of the
+ * cell centre c and whose off-diagonal entries come from the nearest staggered
+ * positions: F_12, F_21 from c + (l1, l2, 0), F_13, F_31 from c + (l1, 0, l3),
+ * F_23, F_32 from c + (0, l2, l3) (the F^{aa}_l of the paper).  The law is
+ *   P_aa[xi] = 1/8 sum_l P_xi(F_sub(xi, l))_aa,
+ *   P_ab[xi] = 1/8 sum_l P_c(F_sub(c, l))_ab, c = xi - l_a e_a - l_b e_b (a != b),
+ * which is the paper's F^{ab}_l[xi] assembly (F_sub(c, l) with that c) with the
+ * material of the cell that holds the sub-cell.  READING: the paper prints the
+ * material P[xi + l^{+a,+b}], whose offsets disagree in sign with those of
+ * F^{ab}_l; with xi - l_a e_a - l_b e_b the law is the gradient of the sub-cell
+ * energy 1/8 sum_c sum_l W_c(F_sub(c, l)) (pinned by finite differences).
+ * Each sub-cell's law is evaluated once (S below) and gathered per the
+ * equation; boxel cells keep one jump-vector warm start per sub-cell.
+ */
+static int constitutive_dfmg(orc_ctx* cx, const double* F, double* P, int64_t* nr_it, int64_t* nbp, int64_t* nevals)
+{
+    const orc_problem* pb = cx->pb;
+    const long n1 = pb->n[0], n2 = pb->n[1], n3 = pb->n[2];
+    size_t V = (size_t)n1 * n2 * n3;
+    double* S = (double*)malloc(sizeof(double) * 72 * V); /* [V][8][9] */
+    int status = ORC_OK;
+    int64_t it_sum = 0, bp_sum = 0, ev_sum = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : it_sum, bp_sum, ev_sum)
+    for (long v = 0; v < (long)V; v++) {
+        const long i = v % n1, j = (v / n1) % n2, k = v / (n1 * n2);
+        const int b = cx->vox2box[v];
+        for (int l = 0; l < 8; l++) {
+            const long l1 = l & 1, l2 = (l >> 1) & 1, l3 = (l >> 2) & 1;
+            const long v12 = wrapi(i + l1, n1) + n1 * (wrapi(j + l2, n2) + n2 * k);
+            const long v13 = wrapi(i + l1, n1) + n1 * (j + n2 * wrapi(k + l3, n3));
+            const long v23 = i + n1 * (wrapi(j + l2, n2) + n2 * wrapi(k + l3, n3));
+            double Fs[9];
+            Fs[0] = F[0 * V + v];
+            Fs[4] = F[4 * V + v];
+            Fs[8] = F[8 * V + v];
+            Fs[1] = F[1 * V + v12];
+            Fs[3] = F[3 * V + v12];
+            Fs[2] = F[2 * V + v13];
+            Fs[6] = F[6 * V + v13];
+            Fs[5] = F[5 * V + v23];
+            Fs[7] = F[7 * V + v23];
+            double aw[3] = {0.0, 0.0, 0.0};
+            if (b >= 0) memcpy(aw, cx->a8 + 24 * (size_t)b + 3 * l, sizeof(aw));
+            int64_t its = 0, nbpv = 0;
+            int rc = cell_law(cx, v, Fs, aw, S + 72 * (size_t)v + 9 * l, &its, &nbpv);
+            if (b >= 0) {
+                memcpy(cx->a8 + 24 * (size_t)b + 3 * l, aw, sizeof(aw));
+                ev_sum += 1;
+            }
+            it_sum += its;
+            bp_sum += nbpv;
+            if (rc) {
+#pragma omp critical
+                {
+                    if (status == ORC_OK) status = rc;
+                }
+            }
+        }
+    }
+    if (status == ORC_OK) {
+#pragma omp parallel for schedule(static)
+        for (long v = 0; v < (long)V; v++) {
+            const long i = v % n1, j = (v / n1) % n2, k = v / (n1 * n2);
+            double out[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            for (int l = 0; l < 8; l++) {
+                const long l1 = l & 1, l2 = (l >> 1) & 1, l3 = (l >> 2) & 1;
+                const double* Sv = S + 72 * (size_t)v + 9 * l;
+                out[0] += Sv[0];
+                out[4] += Sv[4];
+                out[8] += Sv[8];
+                const long c12 = wrapi(i - l1, n1) + n1 * (wrapi(j - l2, n2) + n2 * k);
+                const long c13 = wrapi(i - l1, n1) + n1 * (j + n2 * wrapi(k - l3, n3));
+                const long c23 = i + n1 * (wrapi(j - l2, n2) + n2 * wrapi(k - l3, n3));
+                out[1] += S[72 * (size_t)c12 + 9 * l + 1];
+                out[3] += S[72 * (size_t)c12 + 9 * l + 3];
+                out[2] += S[72 * (size_t)c13 + 9 * l + 2];
+                out[6] += S[72 * (size_t)c13 + 9 * l + 6];
+                out[5] += S[72 * (size_t)c23 + 9 * l + 5];
+                out[7] += S[72 * (size_t)c23 + 9 * l + 7];
+            }
+            for (int c = 0; c < 9; c++) P[(size_t)c * V + v] = 0.125 * out[c];
+        }
+    }
+    free(S);
+    if (nr_it) *nr_it += it_sum;
+    if (nbp) *nbp += bp_sum;
+    if (nevals) *nevals += ev_sum;
+    return status;
+}
 
 /* P (and optionally the 9x9 tangent A) at every voxel.  Returns status. */
 static int constitutive(orc_ctx* cx, const double* F, double* P, double* A, int64_t* nr_it, int64_t* nbp,
                         int64_t* nevals)
 {
     const orc_problem* pb = cx->pb;
+    if (cx->op->kspace == ORC_STAGGERED_DFMG) {
+        if (A) return ORC_E_INVALID; /* no tangent of the doubly-fine material grid */
+        return constitutive_dfmg(cx, F, P, nr_it, nbp, nevals);
+    }
     size_t V = (size_t)pb->n[0] * pb->n[1] * pb->n[2];
     int status = ORC_OK;
     int64_t it_sum = 0, bp_sum = 0, ev_sum = 0;
@@ -692,11 +819,13 @@ int orc_constitutive_field(const orc_problem* pb, const orc_options* op, const d
                            double* A)
 {
     size_t V = (size_t)pb->n[0] * pb->n[1] * pb->n[2];
-    orc_ctx cx = {pb, op, (int32_t*)malloc(sizeof(int32_t) * V), a_io};
+    orc_ctx cx = {pb, op, (int32_t*)malloc(sizeof(int32_t) * V), a_io,
+                  (double*)calloc(24 * (size_t)(pb->nb > 0 ? pb->nb : 1), sizeof(double))};
     for (size_t v = 0; v < V; v++) cx.vox2box[v] = -1;
     for (int64_t b = 0; b < pb->nb; b++) cx.vox2box[pb->bidx[b]] = (int32_t)b;
     int rc = constitutive(&cx, F, P, A, NULL, NULL, NULL);
     free(cx.vox2box);
+    free(cx.a8);
     return rc;
 }
 
@@ -786,6 +915,13 @@ int orc_solve(const orc_problem* pb, const orc_options* op, orc_result* res)
     for (size_t v = 0; v < V; v++) cx.vox2box[v] = -1;
     for (int64_t b = 0; b < pb->nb; b++) cx.vox2box[pb->bidx[b]] = (int32_t)b;
     cx.a = (double*)calloc(3 * (size_t)(pb->nb > 0 ? pb->nb : 1), sizeof(double));
+    cx.a8 = (double*)calloc(24 * (size_t)(pb->nb > 0 ? pb->nb : 1), sizeof(double));
+    if (op->kspace == ORC_STAGGERED_DFMG && op->solver == 1) {
+        free(cx.vox2box);
+        free(cx.a);
+        free(cx.a8);
+        return ORC_E_INVALID; /* Newton needs the tangent, which the DFMG law does not provide here */
+    }
 
     double* F = (double*)malloc(sizeof(double) * N9);
     double* P = (double*)malloc(sizeof(double) * N9);
@@ -916,6 +1052,7 @@ int orc_solve(const orc_problem* pb, const orc_options* op, orc_result* res)
     if (res->a && pb->nb > 0) memcpy(res->a, cx.a, sizeof(double) * 3 * (size_t)pb->nb);
     free(cx.vox2box);
     free(cx.a);
+    free(cx.a8);
     free(F);
     free(P);
     free(g);
