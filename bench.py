@@ -616,6 +616,10 @@ def variants_bench(combo, ctx):
             ("newton_cg_staggered_refined_df", dict(solver=combo.NEWTON_CG, precision=combo.FP32_REFINED_DF,
                                                     kspace=combo.STAGGERED)),
             ("nonlinear_cg_rotated_fp64", dict(solver=combo.NONLINEAR_CG, precision=combo.FP64)),
+            ("nonlinear_cg_staggered_fp64", dict(solver=combo.NONLINEAR_CG, precision=combo.FP64,
+                                                 kspace=combo.STAGGERED)),
+            ("nonlinear_cg_staggered_dfmg_fp64", dict(solver=combo.NONLINEAR_CG, precision=combo.FP64,
+                                                      kspace=combo.STAGGERED_DFMG)),
             ("basic_scheme_rotated_fp64", dict(solver=combo.FIXED_POINT, precision=combo.FP64))]
     out = {"problem": "128^3 random balls r=8 vox, vf 0.2, contrast 10, Fbar11 = 1.05 in 2 steps, tol 1e-8"}
     ref = None
@@ -632,6 +636,41 @@ def variants_bench(combo, ctx):
                      "operator_applications": int(r["n_operator"]),
                      "voxel_iterations_per_s": int(r["n_operator"]) * V / dt,
                      "Pbar_rel_diff_vs_rotated_newton": float(np.linalg.norm(r["Pbar"][-1] - ref) / np.linalg.norm(ref))}
+    out["dfmg_kernels"] = dfmg_kernels(combo, ctx, p)
+    return out
+
+
+def dfmg_kernels(combo, ctx, p):
+    """Per-kernel CUDA-event times of the doubly-fine material grid law inside
+    a nonlinear-CG solve of the same problem (first load step, 40 iterations
+    after 10 untimed).  Algorithmic bytes per cell: dfmg_pure reads F (72 B)
+    and writes the 8 sub-cell stresses (576 B); dfmg_gather reads those
+    (576 B) and writes P (72 B).  dfmg_pure also does 8 FP64 Neo-Hookean
+    evaluations per cell (a logarithm, a division, ~70 FMAs each)."""
+    import torch
+
+    n = p["n"]
+    V = n[0] * n[1] * n[2]
+    s = combo.Solve(p, ctx=ctx, solver=combo.NONLINEAR_CG, precision=combo.FP64, kspace=combo.STAGGERED_DFMG,
+                    tol=1e-12)
+    s.advance(10)
+    torch.cuda.synchronize()
+    s.profile(True)
+    s.advance(40)
+    torch.cuda.synchronize()
+    prof = s.profile_read()
+    s.profile(False)
+    s.close()
+    peak, kind = peaks()
+    out = {"cells": V, "hbm_peak_gbs": peak, "peak_kind": kind}
+    for name, nbytes in (("dfmg_pure", 648), ("dfmg_gather", 648)):
+        ms_tot, cnt = prof.get(name, (0.0, 0))
+        if cnt:
+            per = ms_tot / cnt
+            gbs = nbytes * V / (per * 1e-3) / 1e9
+            out[name] = {"launches": cnt, "ms_per_launch": per, "algorithmic_GB_s": gbs, "frac_hbm": gbs / peak}
+    out["other_kernels_ms_per_iteration"] = {k: v[0] / max(v[1], 1) for k, v in prof.items()
+                                             if k not in ("dfmg_pure", "dfmg_gather")}
     return out
 
 

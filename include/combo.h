@@ -77,6 +77,19 @@ extern "C" {
    stored (the plain staggered scheme; no doubly-fine material grid).  Not
    available to combo_apply_G_noalloc. */
 #define COMBO_STAGGERED 2
+/* staggered grid with the doubly-fine material grid (App. A, Eq.
+   constitutive_law): every voxel is cut into 8 sub-cells l in {0,1}^3; sub-cell
+   l of cell c takes the diagonal of F at c and the off-diagonal pairs F_ab,
+   F_ba at c + l_a e_a + l_b e_b (the edge nearest the sub-cell); the material
+   of c is evaluated at each (a composite boxel: one laminate per sub-cell,
+   each with its own jump vector), and the stress gathers
+   P_aa[xi] = 1/8 sum_l S(xi, l)_aa, P_ab[xi] = 1/8 sum_l S(xi - l_a e_a - l_b e_b, l)_ab,
+   the gradient of the sub-cell energy 1/8 sum_c sum_l W_c(F_sub(c, l)).  The
+   operator is that of COMBO_STAGGERED.  Fixed point and nonlinear CG only
+   (COMBO_E_INVALID_ARG with Newton-CG); combo_solve and combo_solve_begin
+   only (not the batch, not combo_apply_G).  combo_result.a_out holds the mean
+   of a boxel's 8 sub-cell jumps; Pbar_phase averages over sub-cells. */
+#define COMBO_STAGGERED_DFMG 3
 /* solver */
 #define COMBO_FIXED_POINT 0 /* basic scheme on the nonlinear LSE, Sec. 3 */
 #define COMBO_NEWTON_CG 1   /* Newton with conjugate gradients on the linearised LSE, Sec. 3 */

@@ -299,7 +299,22 @@ def constitutive_field(prob, F, a=None, opts=None, tangent=False):
     return (P, a[:nb], A.reshape(V, 9, 9)) if tangent else (P, a[:nb])
 
 
-def phase_averages(prob, F, a, c_min=1e-6):
+def dfmg_subcell_F(F, n, l):
+    """F_sub(c, l) of every cell c under the doubly-fine material grid (App. A,
+    Eq. constitutive_law): the diagonal of F at c, the off-diagonal pairs
+    F_ab, F_ba at c + l_a e_a + l_b e_b.  F [9][V] (x fastest), l in {0,1}^3."""
+    G = np.asarray(F, dtype=np.float64).reshape(9, n[2], n[1], n[0])
+    out = G.copy()
+    npax = {0: 2, 1: 1, 2: 0}
+    for comp, (a_, b_) in ((1, (0, 1)), (3, (0, 1)), (2, (0, 2)), (6, (0, 2)), (5, (1, 2)), (7, (1, 2))):
+        shift = [0, 0, 0]
+        shift[npax[a_]] = -l[a_]
+        shift[npax[b_]] = -l[b_]
+        out[comp] = np.roll(G[comp], shift, axis=(0, 1, 2))
+    return out.reshape(9, -1)
+
+
+def phase_averages(prob, F, a, c_min=1e-6, kspace=None):
     """Phase averages Pbar_- (matrix) and Pbar_+ (inclusion) of a state (Sec. 6.2):
     the mean of P over the volume of each phase, where a pure voxel adds its P
     and its volume to its phase and a composite boxel adds c+- P+- and c+- to
@@ -310,6 +325,8 @@ def phase_averages(prob, F, a, c_min=1e-6):
     phase = np.asarray(prob["phase"]).ravel().copy()
     F = np.asarray(F, dtype=np.float64).reshape(9, -1)
     mu, lam = prob["mu"], prob["lam"]
+    if kspace == STAGGERED_DFMG:
+        return _phase_averages_dfmg(prob, F, c_min)
     sums = np.zeros((2, 9))
     vol = np.zeros(2)
     idx = np.asarray(prob["boxel_idx"], np.int64)
@@ -334,6 +351,47 @@ def phase_averages(prob, F, a, c_min=1e-6):
         for ph, cph, Fph in ((1, c, Fb + aN / c), (0, 1.0 - c, Fb - aN / (1.0 - c))):
             sums[ph] += cph * neohooke(Fph.reshape(9), mu[ph], lam[ph], tangent=False)
             vol[ph] += cph
+    return np.where(vol[:, None] > 0, sums / np.maximum(vol, 1e-300)[:, None], 0.0)
+
+
+def _phase_averages_dfmg(prob, F, c_min):
+    """Phase averages under the doubly-fine material grid: every sub-cell has
+    volume 1/8; a pure sub-cell adds P(F_sub) to its phase, a composite boxel's
+    sub-cell adds c+- P+- at F_sub +- a (x) N / c+-, a the laminate jump at
+    F_sub (Algorithm 1 solved afresh here)."""
+    n = tuple(int(v) for v in prob["n"])
+    phase = np.asarray(prob["phase"]).ravel().copy()
+    mu, lam = prob["mu"], prob["lam"]
+    idx = np.asarray(prob["boxel_idx"], np.int64)
+    cs = np.asarray(prob["boxel_c"], float)
+    box = {}
+    for k, v in enumerate(idx):
+        if cs[k] < c_min:
+            phase[v] = 0
+        elif cs[k] > 1.0 - c_min:
+            phase[v] = 1
+        else:
+            box[int(v)] = k
+    sums = np.zeros((2, 9))
+    vol = np.zeros(2)
+    mat = (mu[0], lam[0], mu[1], lam[1])
+    for li in range(8):
+        Fs = dfmg_subcell_F(F, n, (li & 1, (li >> 1) & 1, (li >> 2) & 1))
+        for v in range(phase.size):
+            if phase[v] != 2:
+                ph = int(phase[v])
+                sums[ph] += 0.125 * neohooke(Fs[:, v], mu[ph], lam[ph], tangent=False)
+                vol[ph] += 0.125
+                continue
+            k = box[v]
+            c = float(cs[k])
+            N = np.asarray(prob["boxel_N"][k], float)
+            N = N / np.linalg.norm(N)
+            aN = np.outer(laminate(Fs[:, v], N, c, mat)["a"], N).ravel()
+            sums[1] += 0.125 * c * neohooke(Fs[:, v] + aN / c, mu[1], lam[1], tangent=False)
+            sums[0] += 0.125 * (1 - c) * neohooke(Fs[:, v] - aN / (1 - c), mu[0], lam[0], tangent=False)
+            vol[1] += 0.125 * c
+            vol[0] += 0.125 * (1 - c)
     return np.where(vol[:, None] > 0, sums / np.maximum(vol, 1e-300)[:, None], 0.0)
 
 

@@ -763,6 +763,19 @@ static int constitutive_dfmg(orc_ctx* cx, const double* F, double* P, int64_t* n
     return status;
 }
 
+/* Reported jump vector of a boxel under the doubly-fine material grid: the
+ * mean of its 8 sub-cell jumps (the sub-cell jumps themselves are internal
+ * warm-start state). */
+static void dfmg_mean_jumps(const double* a8, int64_t nb, double* a)
+{
+    for (int64_t b = 0; b < nb; b++)
+        for (int q = 0; q < 3; q++) {
+            double s = 0.0;
+            for (int l = 0; l < 8; l++) s += a8[24 * b + 3 * l + q];
+            a[3 * b + q] = 0.125 * s;
+        }
+}
+
 /* P (and optionally the 9x9 tangent A) at every voxel.  Returns status. */
 static int constitutive(orc_ctx* cx, const double* F, double* P, double* A, int64_t* nr_it, int64_t* nbp,
                         int64_t* nevals)
@@ -824,6 +837,7 @@ int orc_constitutive_field(const orc_problem* pb, const orc_options* op, const d
     for (size_t v = 0; v < V; v++) cx.vox2box[v] = -1;
     for (int64_t b = 0; b < pb->nb; b++) cx.vox2box[pb->bidx[b]] = (int32_t)b;
     int rc = constitutive(&cx, F, P, A, NULL, NULL, NULL);
+    if (op->kspace == ORC_STAGGERED_DFMG) dfmg_mean_jumps(cx.a8, pb->nb, a_io);
     free(cx.vox2box);
     free(cx.a8);
     return rc;
@@ -1049,6 +1063,7 @@ int orc_solve(const orc_problem* pb, const orc_options* op, orc_result* res)
     }
     if (res->F) memcpy(res->F, F, sizeof(double) * N9);
     if (res->P) memcpy(res->P, P, sizeof(double) * N9);
+    if (op->kspace == ORC_STAGGERED_DFMG) dfmg_mean_jumps(cx.a8, pb->nb, cx.a);
     if (res->a && pb->nb > 0) memcpy(res->a, cx.a, sizeof(double) * 3 * (size_t)pb->nb);
     free(cx.vox2box);
     free(cx.a);

@@ -19,7 +19,7 @@ OK, PENDING = 0, 1
 E_NAMES = {-1: "invalid argument", -2: "out of memory", -3: "not converged", -4: "laminate Newton failed",
            -5: "inadmissible (det F <= 0)", -6: "NaN", -7: "timeout", -8: "CUDA error", -9: "cancelled"}
 FP64, FP32_REFINED, FP32_REFINED_DF = 0, 1, 2
-ROTATED, SPECTRAL, STAGGERED = 0, 1, 2
+ROTATED, SPECTRAL, STAGGERED, STAGGERED_DFMG = 0, 1, 2, 3
 FIXED_POINT, NEWTON_CG, NONLINEAR_CG = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 

@@ -498,6 +498,115 @@ template <typename Tc> void launch_boxel(const BoxelArgs<Tc>& a, cudaStream_t st
     k_boxel<Tc, false><<<grid, 128, 0, st>>>(a);
 }
 
+// Doubly-fine material grid (App. A): the laminate of every sub-cell l of
+// every composite boxel, at F_sub(c, l) (the cell's diagonal, the staggered
+// off-diagonals nearest the sub-cell), from the sub-cell's own warm start
+// a [nb][8][3]; the boxel stress c+ P+ + c- P- goes to S[9 l + comp][v].
+// One thread per (boxel, sub-cell), FP64 (the fixed point and nonlinear CG
+// run in FP64 only).
+__global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArgs<double> A)
+{
+    __shared__ double red[64];
+    __shared__ int same_problem;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nt = 8 * A.nb;
+    const int64_t b = t >> 3;
+    const int l = (int)(t & 7);
+    const int pb = (A.bprob && t < nt) ? A.bprob[b] : 0;
+    Scalars* sc = A.sc + pb;
+    double its = 0.0, nbp = 0.0, nev = 0.0;
+    if (t < nt && !(A.guard == 2 && sc->outer_done)) {
+        nev = 1.0;
+        const int64_t v = A.bidx[b];
+        const int64_t base = (int64_t)pb * A.Vp, lv = v - base;
+        const int i = (int)(lv % A.n1), j = (int)((lv / A.n1) % A.n2), k = (int)(lv / ((int64_t)A.n1 * A.n2));
+        double Fb[9], N[3], a[3];
+        dfmg_fsub(A.F, A.V, base, A.n1, A.n2, A.n3, i, j, k, l, Fb);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            N[q] = A.bN[3 * b + q];
+            a[q] = A.ba[24 * b + 3 * l + q];
+        }
+        const double cp = A.bc[b], cm = 1.0 - cp;
+        const double* mp = A.matp ? A.matp + 4 * pb : nullptr;
+        const double mu[2] = {mp ? mp[0] : A.mu[0], mp ? mp[1] : A.mu[1]};
+        const double lam[2] = {mp ? mp[2] : A.lam[0], mp ? mp[3] : A.lam[1]};
+        int status = 0, reason = 0;
+        Phase box;
+#pragma unroll
+        for (int c = 0; c < 9; c++) box.F[c] = Fb[c];
+        if (!nh_phase(box, mu[0], lam[0], N)) status = COMBO_E_INADMISSIBLE;
+        LamEval e;
+        auto eval64 = [&](LamEval& x) { return lam_eval(x, Fb, N, cp, cm, a, mu, lam, A.tol_rel, A.tol_abs); };
+        auto inv64 = [&](const LamEval& x, double Di[9]) {
+            double Dl[9];
+            hessian(x, cp, cm, mu, lam, Dl);
+            return inv3(Dl, Di);
+        };
+        if (!status) {
+            const double ng = sqrt(box.g[0] * box.g[0] + box.g[1] * box.g[1] + box.g[2] * box.g[2]);
+            const double m[3] = {box.g[0] / ng, box.g[1] / ng, box.g[2] / ng};
+            const double bcp = -cp / ng, bcm = cm / ng;
+            const double beta = a[0] * m[0] + a[1] * m[1] + a[2] * m[2];
+            if (!(beta > bcp && beta < bcm)) a[0] = a[1] = a[2] = 0.0;
+            int it = 0;
+            reason = nr_loop(e, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp, eval64, inv64);
+            if (reason) status = COMBO_E_LAMINATE;
+            its = it;
+        } else {
+            reason = 1;
+        }
+        if (status) {
+            raise_status(sc, status);
+            if (atomicCAS(&sc->fail_boxel, 0, (int32_t)(b + 1)) == 0) {
+                sc->fail_reason = reason;
+#pragma unroll
+                for (int c = 0; c < 9; c++) sc->fail_state[c] = Fb[c];
+#pragma unroll
+                for (int q = 0; q < 3; q++) {
+                    sc->fail_state[9 + q] = N[q];
+                    sc->fail_state[13 + q] = a[q];
+                }
+                sc->fail_state[12] = cp;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 9; c++) A.S[(int64_t)(9 * l + c) * A.V + v] = cp * e.p.P[c] + cm * e.m.P[c];
+#pragma unroll
+            for (int q = 0; q < 3; q++) A.ba[24 * b + 3 * l + q] = a[q];
+        }
+    }
+    if (threadIdx.x == 0) {
+        const int64_t first = ((int64_t)blockIdx.x * blockDim.x) >> 3;
+        const int64_t last = (min((int64_t)(blockIdx.x + 1) * blockDim.x, nt) - 1) >> 3;
+        same_problem = (!A.bprob || A.bprob[first] == A.bprob[last]) ? 1 : 0;
+    }
+    __syncthreads();
+    if (same_problem) {
+        const double s1 = block_sum(its, red);
+        const double s2 = block_sum(nbp, red + 32);
+        __syncthreads();
+        const double s3 = block_sum(nev, red);
+        if (threadIdx.x == 0) {
+            Scalars* s0 = A.sc + (A.bprob ? A.bprob[((int64_t)blockIdx.x * blockDim.x) >> 3] : 0);
+            atomicAdd(&s0->nr_iters, (unsigned long long)s1);
+            atomicAdd(&s0->n_backproj, (unsigned long long)s2);
+            atomicAdd(&s0->n_lam, (unsigned long long)s3);
+        }
+    } else if (nev > 0.0) {
+        atomicAdd(&sc->nr_iters, (unsigned long long)its);
+        atomicAdd(&sc->n_backproj, (unsigned long long)nbp);
+        atomicAdd(&sc->n_lam, (unsigned long long)nev);
+    }
+}
+
+void launch_boxel_dfmg(const BoxelArgs<double>& a, cudaStream_t st)
+{
+    if (a.nb <= 0) return;
+    const int grid = (int)((8 * a.nb + 127) / 128);
+    k_boxel_dfmg<<<grid, 128, 0, st>>>(a);
+}
+
 template void launch_boxel<double>(const BoxelArgs<double>&, cudaStream_t);
 template void launch_boxel<float>(const BoxelArgs<float>&, cudaStream_t);
 

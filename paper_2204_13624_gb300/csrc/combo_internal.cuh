@@ -476,6 +476,78 @@ void launch_xinv_stream(const XinvArgs<float, float>& a, cudaStream_t st);
 // Record msg as the calling thread's last error; returns code.
 int set_error(int code, const char* msg);
 
+// ------------------------------------------------ doubly-fine material grid
+// Sub-cell l = (l1, l2, l3) in {0,1}^3 (bit k of l is l_{k+1}) of the cell
+// (i, j, k) of one problem (voxels base + i + n1 (j + n2 k), field stride V):
+// the diagonal of F at the cell, the off-diagonal pairs at the staggered
+// positions c + (l1, l2, 0) (F12, F21), c + (l1, 0, l3) (F13, F31) and
+// c + (0, l2, l3) (F23, F32), periodic (App. A, Eq. constitutive_law).
+__device__ __forceinline__ void dfmg_fsub(const double* __restrict__ F, int64_t V, int64_t base, int n1, int n2,
+                                          int n3, int i, int j, int k, int l, double f[9])
+{
+    const int ip = (l & 1) ? (i + 1 == n1 ? 0 : i + 1) : i;
+    const int jp = (l & 2) ? (j + 1 == n2 ? 0 : j + 1) : j;
+    const int kp = (l & 4) ? (k + 1 == n3 ? 0 : k + 1) : k;
+    const int64_t vc = base + i + (int64_t)n1 * (j + (int64_t)n2 * k);
+    const int64_t v12 = base + ip + (int64_t)n1 * (jp + (int64_t)n2 * k);
+    const int64_t v13 = base + ip + (int64_t)n1 * (j + (int64_t)n2 * kp);
+    const int64_t v23 = base + i + (int64_t)n1 * (jp + (int64_t)n2 * kp);
+    f[0] = F[0 * V + vc];
+    f[4] = F[4 * V + vc];
+    f[8] = F[8 * V + vc];
+    f[1] = F[1 * V + v12];
+    f[3] = F[3 * V + v12];
+    f[2] = F[2 * V + v13];
+    f[6] = F[6 * V + v13];
+    f[5] = F[5 * V + v23];
+    f[7] = F[7 * V + v23];
+}
+
+// Neo-Hookean P of F (Sec. 6.1) in FP64; false where det F <= 0
+__device__ __forceinline__ bool nh_P64(const double f[9], double mu, double lam, double P[9])
+{
+    const double c0 = f[4] * f[8] - f[5] * f[7], c1 = f[5] * f[6] - f[3] * f[8], c2 = f[3] * f[7] - f[4] * f[6];
+    const double J = f[0] * c0 + f[1] * c1 + f[2] * c2;
+    if (!(J > 0.0)) return false;
+    const double iJ = 1.0 / J;
+    const double G[9] = {c0 * iJ,
+                         (f[2] * f[7] - f[1] * f[8]) * iJ,
+                         (f[1] * f[5] - f[2] * f[4]) * iJ,
+                         c1 * iJ,
+                         (f[0] * f[8] - f[2] * f[6]) * iJ,
+                         (f[2] * f[3] - f[0] * f[5]) * iJ,
+                         c2 * iJ,
+                         (f[1] * f[6] - f[0] * f[7]) * iJ,
+                         (f[0] * f[4] - f[1] * f[3]) * iJ};
+    const double k = lam * log(J) - mu;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) P[3 * i + j] = mu * f[3 * i + j] + k * G[3 * j + i];
+    return true;
+}
+
+// Arguments of the doubly-fine material grid law (dfmg.cu, boxel.cu): the
+// field F [9][V] of nprob problems stacked along z (Vp voxels, n1 x n2 x n3
+// each); S [72][V] receives, at cell c and row 9 l + comp, component comp of
+// the stress of sub-cell l of c; P [9][V] the gathered stress.
+struct DfmgArgs {
+    const double* F;
+    double* S;
+    double* P;
+    const uint8_t* phase;
+    const double* matp;  // [nprob][4] (mu-, mu+, lam-, lam+), or null: mu, lam
+    double mu[2], lam[2];
+    int64_t V, Vp;
+    int n1, n2, n3;
+    Scalars* sc;
+    int guard;           // 2: skip problems whose outer iteration is done
+};
+void launch_dfmg_pure(const DfmgArgs& a, cudaStream_t st);
+void launch_dfmg_gather(const DfmgArgs& a, cudaStream_t st);
+// mean over the 8 sub-cells of the jump vectors ba8 [nb][8][3] -> ba [nb][3]
+void launch_dfmg_amean(const double* ba8, double* ba, int64_t nb, cudaStream_t st);
+
 // boxel laminate Newton solve
 template <typename Tc> struct BoxelArgs {
     int64_t nb;
@@ -496,8 +568,14 @@ template <typename Tc> struct BoxelArgs {
     Scalars* sc;
     int guard;
     int dfloat;  // phase states and residual in double-float (refined double-float form)
+    // doubly-fine material grid (launch_boxel_dfmg): one laminate per boxel
+    // sub-cell, ba holds [nb][8][3], the stress goes to S [72][V]
+    double* S;
+    int64_t Vp;
+    int n1, n2, n3;
 };
 template <typename Tc> void launch_boxel(const BoxelArgs<Tc>& a, cudaStream_t st);
+void launch_boxel_dfmg(const BoxelArgs<double>& a, cudaStream_t st);
 
 }  // namespace combo
 

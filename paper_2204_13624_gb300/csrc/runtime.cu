@@ -284,11 +284,14 @@ enum KClass {
     K_XINV_CG,
     K_FINALIZE,
     K_UPDATE,
+    K_DFMG_PURE,
+    K_DFMG_GATHER,
     K_NCLASS
 };
 static const char* kclass_name[K_NCLASS] = {"boxel_laminate", "xfwd_resid_fp64", "yfwd_fp64", "zgamma_fp64",
                                              "yinv_fp64", "xinv_fp64", "xfwd_tangent", "yfwd_krylov",
-                                             "zgamma_krylov", "yinv_krylov", "xinv_cg", "finalize", "update_F"};
+                                             "zgamma_krylov", "yinv_krylov", "xinv_cg", "finalize", "update_F",
+                                             "dfmg_pure", "dfmg_gather"};
 
 struct Profiler {
     bool on = false;
@@ -641,28 +644,6 @@ __global__ void k_eval_P(const double* F, const uint8_t* phase, const int32_t* v
     }
 }
 
-// Neo-Hookean P of F (Sec. 6.1) in FP64; false where det F <= 0
-__device__ __forceinline__ bool nh_P64(const double f[9], double mu, double lam, double P[9])
-{
-    const double c0 = f[4] * f[8] - f[5] * f[7], c1 = f[5] * f[6] - f[3] * f[8], c2 = f[3] * f[7] - f[4] * f[6];
-    const double J = f[0] * c0 + f[1] * c1 + f[2] * c2;
-    if (!(J > 0.0)) return false;
-    const double iJ = 1.0 / J;
-    const double G[9] = {c0 * iJ,
-                         (f[2] * f[7] - f[1] * f[8]) * iJ,
-                         (f[1] * f[5] - f[2] * f[4]) * iJ,
-                         c1 * iJ,
-                         (f[0] * f[8] - f[2] * f[6]) * iJ,
-                         (f[2] * f[3] - f[0] * f[5]) * iJ,
-                         c2 * iJ,
-                         (f[1] * f[6] - f[0] * f[7]) * iJ,
-                         (f[0] * f[4] - f[1] * f[3]) * iJ};
-    const double k = lam * log(J) - mu;
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++) P[3 * i + j] = mu * f[3 * i + j] + k * G[3 * j + i];
-    return true;
-}
-
 // Phase-wise sums for the phase averages Pbar_- and Pbar_+ of one problem
 // (voxels [v0, v1) of a field with stride V, boxels [b0, b1)): pure voxels add
 // P(F) and 1 to their phase; a boxel adds c+ P+ and c+ to the inclusion and
@@ -716,6 +697,79 @@ __global__ void __launch_bounds__(256) k_phase_sums(const double* F, int64_t V, 
         s[19] += cp;
     }
     // block sum (fixed order) -> part[blockIdx.x][PHASE_SUMS]
+    __shared__ double red[8][PHASE_SUMS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < PHASE_SUMS; k++) {
+        double x = s[k];
+        for (int o = 16; o >= 1; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+        if (lane == 0) red[warp][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < PHASE_SUMS) {
+        double x = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) x += red[w][threadIdx.x];
+        part[(int64_t)blockIdx.x * PHASE_SUMS + threadIdx.x] = x;
+    }
+}
+
+// Phase-wise sums under the doubly-fine material grid: every sub-cell counts
+// with volume 1/8 -- a pure sub-cell adds P(F_sub) to its phase, a boxel
+// sub-cell adds c+ P+ and c- P- at F_sub +- a_l (x) N / c+- with its own jump
+// a_l (Sec. 4.1, App. A).  One problem: voxels [v0, v1) of n1 x n2 x n3.
+__global__ void __launch_bounds__(256) k_phase_sums_dfmg(const double* F, int64_t V, const uint8_t* phase,
+                                                         int64_t v0, int64_t v1, int n1, int n2, int n3,
+                                                         const int32_t* bidx, const double* bN, const double* bc,
+                                                         const double* ba8, int64_t b0, int64_t b1, Mat9 mat,
+                                                         double* part, Scalars* sc)
+{
+    double s[PHASE_SUMS];
+#pragma unroll
+    for (int k = 0; k < PHASE_SUMS; k++) s[k] = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = v0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < v1; v += stride) {
+        const int ph = phase[v];
+        if (ph == 2) continue;
+        const int64_t lv = v - v0;
+        const int i = (int)(lv % n1), j = (int)((lv / n1) % n2), k = (int)(lv / ((int64_t)n1 * n2));
+        for (int l = 0; l < 8; l++) {
+            double f[9], P[9];
+            dfmg_fsub(F, V, v0, n1, n2, n3, i, j, k, l, f);
+            if (!nh_P64(f, mat.v[ph], mat.v[2 + ph], P)) {
+                atomicCAS(&sc->status, 0, COMBO_E_INADMISSIBLE);
+                continue;
+            }
+            for (int c = 0; c < 9; c++) s[9 * ph + c] += 0.125 * P[c];
+            s[18 + ph] += 0.125;
+        }
+    }
+    for (int64_t t = 8 * b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 8 * b1; t += stride) {
+        const int64_t b = t >> 3;
+        const int l = (int)(t & 7);
+        const int64_t v = bidx[b], lv = v - v0;
+        const int i = (int)(lv % n1), j = (int)((lv / n1) % n2), k = (int)(lv / ((int64_t)n1 * n2));
+        const double cp = bc[b], cm = 1.0 - cp;
+        const double N[3] = {bN[3 * b], bN[3 * b + 1], bN[3 * b + 2]};
+        const double* a = ba8 + 24 * b + 3 * l;
+        double fs[9], fp[9], fm[9], Pp[9], Pm[9];
+        dfmg_fsub(F, V, v0, n1, n2, n3, i, j, k, l, fs);
+        for (int r = 0; r < 3; r++)
+            for (int J = 0; J < 3; J++) {
+                const double aN = a[r] * N[J];
+                fp[3 * r + J] = fs[3 * r + J] + aN / cp;
+                fm[3 * r + J] = fs[3 * r + J] - aN / cm;
+            }
+        if (!nh_P64(fp, mat.v[1], mat.v[3], Pp) || !nh_P64(fm, mat.v[0], mat.v[2], Pm)) {
+            atomicCAS(&sc->status, 0, COMBO_E_INADMISSIBLE);
+            continue;
+        }
+        for (int c = 0; c < 9; c++) {
+            s[c] += 0.125 * cm * Pm[c];
+            s[9 + c] += 0.125 * cp * Pp[c];
+        }
+        s[18] += 0.125 * cm;
+        s[19] += 0.125 * cp;
+    }
     __shared__ double red[8][PHASE_SUMS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -835,11 +889,15 @@ static int check_options(combo_options& o)
 {
     if (o.precision != COMBO_FP64 && o.precision != COMBO_FP32_REFINED && o.precision != COMBO_FP32_REFINED_DF)
         return fail(COMBO_E_INVALID_ARG, "bad precision");
-    if (o.kspace != COMBO_ROTATED && o.kspace != COMBO_SPECTRAL && o.kspace != COMBO_STAGGERED) return fail(COMBO_E_INVALID_ARG, "bad kspace");
+    if (o.kspace != COMBO_ROTATED && o.kspace != COMBO_SPECTRAL && o.kspace != COMBO_STAGGERED &&
+        o.kspace != COMBO_STAGGERED_DFMG)
+        return fail(COMBO_E_INVALID_ARG, "bad kspace");
     if (o.solver != COMBO_FIXED_POINT && o.solver != COMBO_NEWTON_CG && o.solver != COMBO_NONLINEAR_CG)
         return fail(COMBO_E_INVALID_ARG, "bad solver");
     if (o.solver != COMBO_NEWTON_CG && o.precision != COMBO_FP64)
         return fail(COMBO_E_INVALID_ARG, "the fixed point and nonlinear CG run in FP64 only");
+    if (o.kspace == COMBO_STAGGERED_DFMG && o.solver == COMBO_NEWTON_CG)
+        return fail(COMBO_E_INVALID_ARG, "the doubly-fine material grid runs with the fixed point or nonlinear CG");
     if (o.max_iter <= 0) o.max_iter = (o.solver == COMBO_NEWTON_CG) ? 200 : 100000;
     if (!(o.tol >= 0.0) || !(o.cg_tol >= 0.0)) return fail(COMBO_E_INVALID_ARG, "negative tolerance");
     if (o.nr_max_iter <= 0) o.nr_max_iter = 50;
@@ -939,6 +997,9 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     int64_t Vp = 0;                    // voxels of one problem
     std::vector<HostProblem> hps;      // the problems of a batch (empty for one solve)
     std::vector<int64_t> boff;         // boxels of problem b: [boff[b], boff[b + 1])
+    double* d_S = nullptr;             // doubly-fine material grid: [72][V] sub-cell stresses
+    double* d_Pd = nullptr;            //   [9][V] gathered stress
+    double* d_ba8 = nullptr;           //   [nb][8][3] sub-cell jump vectors
     double* d_mat = nullptr;           // [B][4] materials (batch only)
     double* d_dF = nullptr;            // [B][9] load-step increments (batch only)
     double* d_dv = nullptr;            // [B] F-update factors (batch only)
@@ -983,6 +1044,9 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         cudaFree(d_sc);
         cudaFree(d_phpart);
         cudaFree(d_dir);
+        cudaFree(d_S);
+        cudaFree(d_Pd);
+        cudaFree(d_ba8);
         cudaFree(d_mat);
         cudaFree(d_dF);
         cudaFree(d_dv);
@@ -993,6 +1057,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     }
 
     bool newton() const { return opt.solver == COMBO_NEWTON_CG; }
+    bool dfmg() const { return opt.kspace == COMBO_STAGGERED_DFMG; }
 
     int init(combo_ctx* c, HostProblem&& h, const combo_options& o)
     {
@@ -1036,8 +1101,10 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         nb = (int64_t)hp.bidx.size();
         const int64_t V = g.V;
         int rc;
-        if ((rc = e64.init(g, hp.l, opt.kspace))) return rc;
-        if ((rc = ec.init(g, hp.l, opt.kspace))) return rc;
+        // the doubly-fine material grid changes the law, not the operator
+        const int kop = dfmg() ? COMBO_STAGGERED : opt.kspace;
+        if ((rc = e64.init(g, hp.l, kop))) return rc;
+        if ((rc = ec.init(g, hp.l, kop))) return rc;
         CK(cudaMalloc(&d_phase, V));
         CK(cudaMalloc(&d_v2b, 4 * V));
         CK(cudaMalloc(&d_F, 8 * 9 * V));
@@ -1050,6 +1117,12 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         if (opt.solver == COMBO_NONLINEAR_CG) {
             CK(cudaMalloc(&d_dir, sizeof(double) * 9 * (size_t)g.V));
             CK(cudaMemsetAsync(d_dir, 0, sizeof(double) * 9 * (size_t)g.V, st));
+        }
+        if (dfmg()) {
+            CK(cudaMalloc(&d_S, sizeof(double) * 72 * (size_t)g.V));
+            CK(cudaMalloc(&d_Pd, sizeof(double) * 9 * (size_t)g.V));
+            CK(cudaMalloc(&d_ba8, sizeof(double) * 24 * (size_t)std::max<int64_t>(nb, 1)));
+            CK(cudaMemsetAsync(d_ba8, 0, sizeof(double) * 24 * (size_t)std::max<int64_t>(nb, 1), st));
         }
         CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars) * B, st));
         if (B > 1) {
@@ -1290,6 +1363,64 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         prof.end();
     }
 
+    // doubly-fine material grid law (App. A): sub-cell stresses of the pure
+    // cells and of the composite boxels into d_S, gathered into d_Pd
+    void dfmg_law(int guard)
+    {
+        DfmgArgs d{};
+        d.F = d_F;
+        d.S = d_S;
+        d.P = d_Pd;
+        d.phase = d_phase;
+        d.matp = d_mat;
+        for (int i = 0; i < 2; i++) {
+            d.mu[i] = hp.mu[i];
+            d.lam[i] = hp.lam[i];
+        }
+        d.V = g.V;
+        d.Vp = (B > 1) ? Vp : g.V;
+        d.n1 = hp.n[0];
+        d.n2 = hp.n[1];
+        d.n3 = hp.n[2];
+        d.sc = d_sc;
+        d.guard = guard;
+        if (nb > 0) {
+            BoxelArgs<double> a{};
+            a.nb = nb;
+            a.V = g.V;
+            a.bidx = d_bidx;
+            a.bN = d_bN;
+            a.bc = d_bc;
+            a.ba = d_ba8;
+            a.bprob = d_bprob;
+            a.matp = d_mat;
+            a.F = d_F;
+            for (int i = 0; i < 2; i++) {
+                a.mu[i] = hp.mu[i];
+                a.lam[i] = hp.lam[i];
+            }
+            a.tol_rel = opt.nr_tol_rel;
+            a.tol_abs = opt.nr_tol_abs;
+            a.max_iter = opt.nr_max_iter;
+            a.sc = d_sc;
+            a.guard = guard;
+            a.S = d_S;
+            a.Vp = d.Vp;
+            a.n1 = d.n1;
+            a.n2 = d.n2;
+            a.n3 = d.n3;
+            prof.begin(K_BOXEL);
+            launch_boxel_dfmg(a, st);
+            prof.end();
+        }
+        prof.begin(K_DFMG_PURE);
+        launch_dfmg_pure(d, st);
+        prof.end();
+        prof.begin(K_DFMG_GATHER);
+        launch_dfmg_gather(d, st);
+        prof.end();
+    }
+
     // FP64 residual operator: G[P(F)]; mode: XI_FIXEDPOINT (update F) or XI_RHS (r = -G[P], x = 0)
     void resid_operator(int xi_mode, int guard)
     {
@@ -1303,6 +1434,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         }
         xf.F = d_F;
         xf.bP = d_bP;
+        xf.X = dfmg() ? d_Pd : nullptr;  // the gathered stress of the doubly-fine material grid
         xf.tc = (xi_mode == XI_RHS) ? d_tc : nullptr;
         xf.matp = d_mat;
         xf.nb = nb;
@@ -1460,8 +1592,12 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         m.v[1] = mu[1];
         m.v[2] = lam[0];
         m.v[3] = lam[1];
-        k_phase_sums<<<PHASE_GRID, 256, 0, st>>>(d_F, g.V, d_phase, v0, v1, d_bidx, d_bN, d_bc, d_ba, b0, b1, m,
-                                                 d_phpart, d_sc);
+        if (dfmg())
+            k_phase_sums_dfmg<<<PHASE_GRID, 256, 0, st>>>(d_F, g.V, d_phase, v0, v1, hp.n[0], hp.n[1], hp.n[2], d_bidx,
+                                                          d_bN, d_bc, d_ba8, b0, b1, m, d_phpart, d_sc);
+        else
+            k_phase_sums<<<PHASE_GRID, 256, 0, st>>>(d_F, g.V, d_phase, v0, v1, d_bidx, d_bN, d_bc, d_ba, b0, b1, m,
+                                                     d_phpart, d_sc);
         CK(cudaGetLastError());
         std::vector<double> part((size_t)PHASE_GRID * PHASE_SUMS);
         CK(cudaMemcpyAsync(part.data(), d_phpart, 8 * part.size(), cudaMemcpyDeviceToHost, st));
@@ -1510,7 +1646,10 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                     // a chunk of fixed-point iterations; kernels skip once converged
                     const int chunk = 16;
                     for (int k = 0; k < chunk; k++) {
-                        boxels(false, 2);
+                        if (dfmg())
+                            dfmg_law(2);
+                        else
+                            boxels(false, 2);
                         resid_operator(opt.solver == COMBO_NONLINEAR_CG ? XI_NCG : XI_FIXEDPOINT, 2);
                     }
                     CK(cudaGetLastError());
@@ -1831,7 +1970,12 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         if (r->resid) CK(cudaMemcpy(r->resid, resid.data(), 8 * resid.size(), h2x));
         const int64_t V = g.V;
         if (r->F_out) CK(cudaMemcpyAsync(r->F_out, d_F, 8 * 9 * V, d2x, st));
-        if (r->P_out) {
+        if (r->P_out && dfmg()) {
+            // the law at the current F (a solve stopped between an F update
+            // and the next residual has a stale gathered stress)
+            dfmg_law(0);
+            CK(cudaMemcpyAsync(r->P_out, d_Pd, 8 * 9 * V, d2x, st));
+        } else if (r->P_out) {
             // F changed since the last laminate solve (a solve stopped between
             // an F update and the next residual): solve the boxels at this F
             if (state == ST_RESID && nb > 0) {
@@ -1852,6 +1996,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                 cudaFree(P);
             }
         }
+        if (dfmg()) launch_dfmg_amean(d_ba8, d_ba, nb, st);  // reported: the mean of the sub-cell jumps
         if (r->a_out && nb > 0) CK(cudaMemcpyAsync(r->a_out, d_ba, 24 * nb, d2x, st));
         CK(cudaStreamSynchronize(st));
         r->steps_done = step;
@@ -1896,6 +2041,7 @@ extern "C" int64_t combo_solve_footprint(const combo_problem* p, const combo_opt
     int64_t b = V * (1 + 4 + 72) + 16 * 9 * g.Vs + nb * (4 + 24 + 8 + 24 + 72);
     if (o->solver == COMBO_NEWTON_CG) b += tc * (81 * nb + 37 * V);
     if (o->solver == COMBO_NONLINEAR_CG) b += 72 * V;
+    if (o->kspace == COMBO_STAGGERED_DFMG) b += 8 * 81 * V + 192 * nb;
     return b;
 }
 
@@ -2201,7 +2347,9 @@ extern "C" int combo_constitutive(combo_ctx* ctx, const combo_problem* p, const 
             k++;
         }
     if (s.nb > 0) CK(cudaMemcpyAsync(s.d_ba, a_kept.data(), 24 * s.nb, cudaMemcpyHostToDevice, s.st));
-    s.boxels(false, 0);
+    // (the doubly-fine material grid evaluates its law in finish, from zero
+    // sub-cell jumps; a_io returns the mean of the converged sub-cell jumps)
+    if (!s.dfmg()) s.boxels(false, 0);
     combo_result r{};
     std::vector<double> pb(9 * (size_t)s.hp.n_steps);
     r.Pbar = pb.data();
@@ -2251,6 +2399,8 @@ int64_t footprint_of(const HostProblem& h, const combo_options& o)
     const int64_t tc = (o.precision == COMBO_FP64) ? 8 : 4;
     int64_t b = V * (1 + 4 + 72) + 16 * 9 * g.Vs + nb * (4 + 24 + 8 + 24 + 72) + (1 << 20);
     if (o.solver == COMBO_NEWTON_CG) b += tc * (45 * nb + 37 * V) + 8 * nb + 4 * ((int64_t)g.n2 * g.n3 + 1);
+    if (o.solver == COMBO_NONLINEAR_CG) b += 72 * V;
+    if (o.kspace == COMBO_STAGGERED_DFMG) b += 8 * 81 * V + 192 * nb;
     return b;
 }
 

@@ -1,0 +1,84 @@
+"""GPU parity of the doubly-fine material grid (App. A, Eq. constitutive_law)
+against the FP64 oracle, through the C ABI (kspace COMBO_STAGGERED_DFMG).
+
+Tolerances (max-abs error relative to the max-abs reference value): the law
+of a field <= 1e-12 (the same FP64 formulas, summed in the same order; the
+laminates converge to the same root within their NR tolerance, which the
+jump vectors show at <= 1e-9); equal iterations of a solve <= 1e-10 in F,
+<= 1e-9 in Pbar, the same iteration counts; converged solves <= 1e-8.
+"""
+import numpy as np
+import pytest
+
+from test_gpu_parity import problems, rel, solve_both
+
+pytestmark = pytest.mark.gpu
+DFMG = 3
+
+
+@pytest.fixture(scope="module")
+def cb():
+    from paper_2204_13624_gb300 import build, combo
+
+    build.build()
+    combo.load()
+    return combo
+
+
+@pytest.mark.parametrize("n", [(12, 9, 18), (16, 16, 16), (64, 32, 8), (8, 64, 6)])
+def test_law_parity(cb, orc, n):
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.random_boxels(n, seed=sum(n), boxel_frac=0.3, incl_frac=0.3, contrast=10.0)
+    V = n[0] * n[1] * n[2]
+    rng = np.random.default_rng(V)
+    F = np.eye(3).reshape(9, 1) + 0.08 * rng.uniform(-1, 1, (9, V))
+    Pg, ag = cb.constitutive(p, F, kspace=DFMG)
+    Po, ao = orc.constitutive_field(p, F, opts=dict(kspace=DFMG))
+    assert rel(Pg, Po) < 1e-12
+    assert rel(ag, ao) < 1e-9
+    # the plain law differs: the gather is not the identity
+    P2, _ = cb.constitutive(p, F, kspace=2)
+    assert rel(P2, Po) > 1e-3
+
+
+@pytest.mark.parametrize("solver", [0, 2])
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_iteration_parity(cb, orc, k, solver):
+    """Fixed point and nonlinear CG, iteration by iteration."""
+    p = problems()[k]
+    g, r = solve_both(cb, orc, p, solver=solver, kspace=DFMG, fixed_iterations=6)
+    assert rel(g["F"], r["F"]) < 1e-10
+    assert rel(g["P"], r["P"]) < 1e-10
+    assert rel(g["Pbar"], r["Pbar"]) < 1e-9
+    if len(r["a"]):
+        assert rel(g["a"], r["a"]) < 1e-8
+    assert list(g["iters"]) == list(r["iters"])
+    assert g["n_operator"] == r["n_operator"]
+    assert g["n_laminate_evals"] == r["n_lam_evals"]
+
+
+def test_converged_sphere(cb, orc):
+    """A 24^3 ball, two load steps, nonlinear CG to tol 1e-8: the oracle's
+    state, its iteration counts within one, and its sub-cell phase averages;
+    the fixed point reaches the same state."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.centred_sphere((24, 24, 24), 0.2, 10.0, np.diag([1.06, 1.0, 0.97]), 2)
+    g, r = solve_both(cb, orc, p, solver=2, kspace=DFMG, tol=1e-8)
+    assert g["steps_done"] == 2 and np.all(g["resid"] <= 1e-8)
+    assert np.all(np.abs(np.asarray(g["iters"]) - np.asarray(r["iters"])) <= 1)
+    assert rel(g["Pbar"], r["Pbar"]) < 1e-8
+    assert rel(g["F"], r["F"]) < 1e-6
+    pa = orc.phase_averages(p, r["F"], r["a"], kspace=DFMG)
+    assert rel(g["Pbar_phase"][-1], pa) < 1e-7
+    g0 = cb.solve(p, solver=0, kspace=DFMG, tol=1e-8)
+    assert rel(g0["Pbar"][-1], g["Pbar"][-1]) < 1e-6
+    assert g0["iters"].sum() > g["iters"].sum()
+
+
+def test_newton_rejected(cb):
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    with pytest.raises(Exception):
+        cb.solve(ms.homogeneous((8, 8, 8)), solver=1, kspace=DFMG)

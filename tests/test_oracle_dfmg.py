@@ -170,3 +170,17 @@ def test_newton_is_rejected(orc):
     p = ms.homogeneous((4, 4, 4))
     r = orc.solve(p, dict(solver=1, kspace=DFMG), raise_on_error=False)
     assert r["status"] != 0
+
+
+def test_phase_averages_split_the_mean_stress(orc):
+    """Sub-cell phase averages: their volume-weighted sum is Pbar, since the
+    gather moves every sub-cell stress component to exactly one cell."""
+    p = ms.random_boxels((6, 5, 4), seed=44, boxel_frac=0.3, incl_frac=0.3, contrast=10.0)
+    r = orc.solve(p, dict(solver=2, kspace=DFMG, tol=1e-11, max_iter=5000))
+    pa = orc.phase_averages(p, r["F"], r["a"], kspace=DFMG)
+    phase = np.asarray(p["phase"]).ravel()
+    c = np.asarray(p["boxel_c"])
+    vol_p = (phase == 1).sum() + c.sum()
+    vol_m = (phase == 0).sum() + (1 - c).sum()
+    assert np.allclose((vol_m * pa[0] + vol_p * pa[1]) / phase.size, r["Pbar"][-1], atol=1e-11)
+    assert np.allclose(r["P"].mean(axis=1), r["Pbar"][-1], atol=1e-13)
