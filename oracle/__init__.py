@@ -62,6 +62,10 @@ def lib():
         L.orc_laminate.argtypes = [dp, dp, C.c_double, dp, dp, C.c_double, C.c_double, C.c_int,
                                    dp, dp, ip, ip, dp]
         L.orc_laminate.restype = C.c_int
+        L.orc_linear.argtypes = [dp, C.c_double, C.c_double, dp, dp]
+        L.orc_linear.restype = C.c_int
+        L.orc_laminate_linear.argtypes = [dp, dp, C.c_double, dp, dp, dp, dp]
+        L.orc_laminate_linear.restype = C.c_int
         L.orc_fft1.argtypes = [C.c_int, C.c_int, dp, dp]
         L.orc_fft3.argtypes = [ip, C.c_int, dp]
         L.orc_kvec.argtypes = [C.c_int, ip, dp, ip, dp]
@@ -135,6 +139,30 @@ def laminate(F, N, c, mat, a0=None, tol_rel=1e-12, tol_abs=1e-14, max_iter=50, t
     return out
 
 
+def linear(F, mu, lam):
+    """Infinitesimal strain: sigma and C of an isotropic linear phase at F = I + H."""
+    F = _f64(F, (9,))
+    S = np.zeros(9)
+    Cm = np.zeros(81)
+    lib().orc_linear(_d(F), mu, lam, _d(S), _d(Cm))
+    return S, Cm.reshape(9, 9)
+
+
+def laminate_linear(F, N, c, mat):
+    """Infinitesimal-strain composite boxel in closed form (cheat sheet):
+    returns dict(S=sigma_box, C=C_box, a)."""
+    F = _f64(F, (9,))
+    N = _f64(N, (3,))
+    m = _f64(mat, (4,))
+    a = np.zeros(3)
+    S = np.zeros(9)
+    Cb = np.zeros(81)
+    rc = lib().orc_laminate_linear(_d(F), _d(N), float(c), _d(m), _d(a), _d(S), _d(Cb))
+    if rc:
+        raise ValueError(STATUS.get(rc, rc))
+    return dict(S=S, C=Cb.reshape(9, 9), a=a)
+
+
 # ---------------------------------------------------------------- FFT / Gamma
 def fft1(x, sign=-1):
     x = np.asarray(x, dtype=np.complex128)
@@ -202,7 +230,8 @@ class _Options(C.Structure):
     _fields_ = [("solver", C.c_int32), ("kspace", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("fixed_iter", C.c_int32), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32),
                 ("cg_fixed_iter", C.c_int32), ("nr_tol_rel", C.c_double), ("nr_tol_abs", C.c_double),
-                ("nr_max_iter", C.c_int32), ("c_min", C.c_double), ("mu0", C.c_double), ("nthreads", C.c_int32)]
+                ("nr_max_iter", C.c_int32), ("c_min", C.c_double), ("mu0", C.c_double), ("nthreads", C.c_int32),
+                ("theory", C.c_int32)]
 
 
 class _Result(C.Structure):
@@ -213,7 +242,7 @@ class _Result(C.Structure):
 
 DEFAULTS = dict(solver=NEWTON_CG, kspace=ROTATED, tol=1e-8, max_iter=200, fixed_iter=0, cg_tol=1e-3,
                 cg_max_iter=2000, cg_fixed_iter=0, nr_tol_rel=1e-12, nr_tol_abs=1e-14, nr_max_iter=50,
-                c_min=1e-6, mu0=0.0, nthreads=0)
+                c_min=1e-6, mu0=0.0, nthreads=0, theory=0)
 
 
 def _problem_struct(prob, keep):
@@ -314,7 +343,7 @@ def dfmg_subcell_F(F, n, l):
     return out.reshape(9, -1)
 
 
-def phase_averages(prob, F, a, c_min=1e-6, kspace=None):
+def phase_averages(prob, F, a, c_min=1e-6, kspace=None, theory=0):
     """Phase averages Pbar_- (matrix) and Pbar_+ (inclusion) of a state (Sec. 6.2):
     the mean of P over the volume of each phase, where a pure voxel adds its P
     and its volume to its phase and a composite boxel adds c+- P+- and c+- to
@@ -327,6 +356,9 @@ def phase_averages(prob, F, a, c_min=1e-6, kspace=None):
     mu, lam = prob["mu"], prob["lam"]
     if kspace == STAGGERED_DFMG:
         return _phase_averages_dfmg(prob, F, c_min)
+    law = (lambda f, m, l: linear(f, m, l)[0]) if theory == 1 else (lambda f, m, l: neohooke(f, m, l, tangent=False))
+    # infinitesimal strain: the jump enters symmetrised, eps+- = eps +- sym(a (x) N) / c+-;
+    # sigma depends on sym(H) only, so a (x) N itself can be added to F
     sums = np.zeros((2, 9))
     vol = np.zeros(2)
     idx = np.asarray(prob["boxel_idx"], np.int64)
@@ -338,7 +370,7 @@ def phase_averages(prob, F, a, c_min=1e-6, kspace=None):
             phase[v] = 1
     for v in np.flatnonzero(phase != 2):
         ph = int(phase[v])
-        sums[ph] += neohooke(F[:, v], mu[ph], lam[ph], tangent=False)
+        sums[ph] += law(F[:, v], mu[ph], lam[ph])
         vol[ph] += 1.0
     for k, v in enumerate(idx):
         if phase[v] != 2:
@@ -349,7 +381,7 @@ def phase_averages(prob, F, a, c_min=1e-6, kspace=None):
         Fb = F[:, v].reshape(3, 3)
         aN = np.outer(a[k], N)
         for ph, cph, Fph in ((1, c, Fb + aN / c), (0, 1.0 - c, Fb - aN / (1.0 - c))):
-            sums[ph] += cph * neohooke(Fph.reshape(9), mu[ph], lam[ph], tangent=False)
+            sums[ph] += cph * law(Fph.reshape(9), mu[ph], lam[ph])
             vol[ph] += cph
     return np.where(vol[:, None] > 0, sums / np.maximum(vol, 1e-300)[:, None], 0.0)
 

@@ -321,6 +321,118 @@ int orc_laminate(const double Fb[9], const double N[3], double c, const double m
 }
 
 /* ------------------------------------------------------------------ */
+/* Infinitesimal-strain theory (cheat sheet, right column).             */
+/* The stored field F is I + H (H the displacement gradient);            */
+/* eps = sym(H), sigma = lam tr(eps) I + 2 mu eps = C : eps with         */
+/*   C_iJkL = lam d_iJ d_kL + mu (d_ik d_JL + d_iL d_Jk).                */
+/* ------------------------------------------------------------------ */
+static void iso_C(double mu, double lam, double C[81])
+{
+    for (int i = 0; i < 3; i++)
+        for (int J = 0; J < 3; J++)
+            for (int k = 0; k < 3; k++)
+                for (int L = 0; L < 3; L++)
+                    C[9 * (3 * i + J) + 3 * k + L] =
+                        lam * (i == J) * (k == L) + mu * ((i == k) * (J == L) + (i == L) * (J == k));
+}
+
+static void strain_of(const double F[9], double eps[9])
+{
+    for (int i = 0; i < 3; i++)
+        for (int J = 0; J < 3; J++) {
+            const double Hij = F[3 * i + J] - (i == J), Hji = F[3 * J + i] - (i == J);
+            eps[3 * i + J] = 0.5 * (Hij + Hji);
+        }
+}
+
+static void apply_C(const double C[81], const double e[9], double s[9])
+{
+    for (int r = 0; r < 9; r++) {
+        double t = 0.0;
+        for (int q = 0; q < 9; q++) t += C[9 * r + q] * e[q];
+        s[r] = t;
+    }
+}
+
+int orc_linear(const double F[9], double mu, double lam, double S[9], double Cout[81])
+{
+    double C[81], eps[9];
+    iso_C(mu, lam, C);
+    strain_of(F, eps);
+    apply_C(C, eps, S);
+    if (Cout) memcpy(Cout, C, sizeof(C));
+    return ORC_OK;
+}
+
+/*
+ * Infinitesimal-strain composite boxel in closed form (cheat sheet, right
+ * column): Delta = N . (C+/c+ + C-/c-) . N, i.e. Delta_ik = N_J (C+/c+ + C-/c-)_iJkL N_L;
+ * a = Delta^{-1} N . (C- - C+) : eps_box, i.e. a = Delta^{-1} f with f_i = ((C- - C+) : eps_box)_iJ N_J;
+ * eps+- = eps_box +- sym(a (x) N) / c+-;  sigma_box = c+ sigma+ + c- sigma-;
+ * C_box = (c+ C+ + c- C-) - dC (N (x) Delta^{-1} (x) N) dC, dC = C+ - C-.
+ * mat = {mu-, lam-, mu+, lam+}; a receives the jump vector.
+ */
+int orc_laminate_linear(const double Fb[9], const double N[3], double c, const double mat[4], double a[3],
+                        double S[9], double Cb[81])
+{
+    const double cp = c, cm = 1.0 - c;
+    if (!(cp > 0.0 && cm > 0.0)) return ORC_E_INVALID;
+    double Cp[81], Cm[81], eps[9];
+    iso_C(mat[2], mat[3], Cp);
+    iso_C(mat[0], mat[1], Cm);
+    strain_of(Fb, eps);
+    double Delta[9], f[3];
+    for (int i = 0; i < 3; i++) {
+        for (int k = 0; k < 3; k++) {
+            double t = 0.0;
+            for (int J = 0; J < 3; J++)
+                for (int L = 0; L < 3; L++) {
+                    const int r = 9 * (3 * i + J) + 3 * k + L;
+                    t += N[J] * (Cp[r] / cp + Cm[r] / cm) * N[L];
+                }
+            Delta[3 * i + k] = t;
+        }
+        double t = 0.0;
+        for (int J = 0; J < 3; J++)
+            for (int q = 0; q < 9; q++) t += (Cm[9 * (3 * i + J) + q] - Cp[9 * (3 * i + J) + q]) * eps[q] * N[J];
+        f[i] = t;
+    }
+    if (solve3(Delta, f, a)) return ORC_E_LAMINATE;
+    double ep[9], em[9], sp[9], sm[9];
+    for (int i = 0; i < 3; i++)
+        for (int J = 0; J < 3; J++) {
+            const double s_aN = 0.5 * (a[i] * N[J] + a[J] * N[i]);
+            ep[3 * i + J] = eps[3 * i + J] + s_aN / cp;
+            em[3 * i + J] = eps[3 * i + J] - s_aN / cm;
+        }
+    apply_C(Cp, ep, sp);
+    apply_C(Cm, em, sm);
+    for (int q = 0; q < 9; q++) S[q] = cp * sp[q] + cm * sm[q];
+    if (Cb) {
+        double Dinv[9];
+        const double dJ = det3(Delta);
+        if (dJ == 0.0) return ORC_E_LAMINATE;
+        inv3(Delta, dJ, Dinv);
+        /* B_(iJ),m = dC_iJmQ N_Q */
+        double B[27];
+        for (int r = 0; r < 9; r++)
+            for (int m = 0; m < 3; m++) {
+                double t = 0.0;
+                for (int Q = 0; Q < 3; Q++) t += (Cp[9 * r + 3 * m + Q] - Cm[9 * r + 3 * m + Q]) * N[Q];
+                B[3 * r + m] = t;
+            }
+        for (int r = 0; r < 9; r++)
+            for (int q = 0; q < 9; q++) {
+                double corr = 0.0;
+                for (int m = 0; m < 3; m++)
+                    for (int n = 0; n < 3; n++) corr += B[3 * r + m] * Dinv[3 * m + n] * B[3 * q + n];
+                Cb[9 * r + q] = cp * Cp[9 * r + q] + cm * Cm[9 * r + q] - corr;
+            }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* FFT: recursive mixed-radix decimation in time, full complex.         */
 /* out[k] = sum_j in[j*stride] exp(sign 2 pi i j k / n).                 */
 /* The twiddle table w holds exp(sign 2 pi i t / n_top) for the top-level */
@@ -614,6 +726,7 @@ typedef struct {
     double c_min;
     double mu0; /* <= 0: default reading */
     int32_t nthreads; /* <= 0: OpenMP default */
+    int32_t theory;   /* 0 finite strain (Neo-Hookean phases), 1 infinitesimal strain (isotropic linear phases) */
 } orc_options;
 
 typedef struct {
@@ -801,7 +914,16 @@ static int constitutive(orc_ctx* cx, const double* F, double* P, double* A, int6
             if (cpl < cx->op->c_min) ph = 0;
             else if (cpl > 1.0 - cx->op->c_min) ph = 1;
         }
-        if (ph == 2) {
+        if (cx->op->theory == 1) {
+            if (ph == 2) {
+                double mat[4] = {pb->mu[0], pb->lam[0], pb->mu[1], pb->lam[1]};
+                rc = orc_laminate_linear(Fv, pb->bN + 3 * (size_t)b, cpl, mat, cx->a + 3 * (size_t)b, Pv,
+                                         A ? Av : NULL);
+                ev_sum += 1;
+            } else {
+                rc = orc_linear(Fv, pb->mu[ph], pb->lam[ph], Pv, A ? Av : NULL);
+            }
+        } else if (ph == 2) {
             double mat[4] = {pb->mu[0], pb->lam[0], pb->mu[1], pb->lam[1]};
             int its = 0, nbpv = 0;
             rc = orc_laminate(Fv, pb->bN + 3 * (size_t)b, cpl, mat, cx->a + 3 * (size_t)b, cx->op->nr_tol_rel,
@@ -930,7 +1052,7 @@ int orc_solve(const orc_problem* pb, const orc_options* op, orc_result* res)
     for (int64_t b = 0; b < pb->nb; b++) cx.vox2box[pb->bidx[b]] = (int32_t)b;
     cx.a = (double*)calloc(3 * (size_t)(pb->nb > 0 ? pb->nb : 1), sizeof(double));
     cx.a8 = (double*)calloc(24 * (size_t)(pb->nb > 0 ? pb->nb : 1), sizeof(double));
-    if (op->kspace == ORC_STAGGERED_DFMG && op->solver == 1) {
+    if (op->kspace == ORC_STAGGERED_DFMG && (op->solver == 1 || op->theory == 1)) {
         free(cx.vox2box);
         free(cx.a);
         free(cx.a8);
@@ -1042,7 +1164,7 @@ int orc_solve(const orc_problem* pb, const orc_options* op, orc_result* res)
                 int ok = 0;
                 for (int h = 0; h <= 10; h++) {
                     for (size_t w = 0; w < N9; w++) t[w] = F[w] + s * x[w];
-                    if (all_admissible(t, V)) {
+                    if (op->theory == 1 || all_admissible(t, V)) { /* (no det F constraint on small strains) */
                         ok = 1;
                         break;
                     }
