@@ -140,11 +140,28 @@ typedef struct {
     int32_t mem;
 } combo_problem;
 
+/* theory: the kinematics and the phases' material law */
+/* finite strain (default): compressible Neo-Hookean phases (Sec. 6.1), the
+   laminate of Algorithm 1 and 2 in composite boxels (Sec. 4) */
+#define COMBO_FINITE_STRAIN 0
+/* infinitesimal strain (cheat sheet of the appendix, right column): the
+   stored field F is I + H, H the displacement gradient; the phases are
+   isotropic linear elastic, sigma = lam tr(eps) I + 2 mu eps, eps = sym(H),
+   with the problem's (mu, lam); a composite boxel takes the closed form
+   a = Delta^{-1} N . (C- - C+) : eps_box, Delta = N . (C+/c+ + C-/c-) . N,
+   sigma_box = c+ sigma+ + c- sigma-, eps+- = eps_box +- sym(a (x) N)/c+-, and
+   the tangent C_box = (c+ C+ + c- C-) - dC (N (x) Delta^{-1} (x) N) dC.  Pbar
+   and P_out then hold sigma; det F is not constrained.  Not with
+   COMBO_STAGGERED_DFMG. */
+#define COMBO_INFINITESIMAL_STRAIN 1
+
 /*
  * Solver options; combo_options_default() fills the defaults given here.
  *   precision        COMBO_FP64 (default), COMBO_FP32_REFINED or COMBO_FP32_REFINED_DF
- *   kspace           COMBO_ROTATED (default) or COMBO_SPECTRAL
- *   solver           COMBO_NEWTON_CG (default) or COMBO_FIXED_POINT
+ *                    (the refined forms with COMBO_NEWTON_CG only)
+ *   kspace           COMBO_ROTATED (default), COMBO_SPECTRAL, COMBO_STAGGERED or
+ *                    COMBO_STAGGERED_DFMG
+ *   solver           COMBO_NEWTON_CG (default), COMBO_FIXED_POINT or COMBO_NONLINEAR_CG
  *   tol              equilibrium tolerance on ||G[P]||_rms / |<P>|  (1e-8)
  *   max_iter         outer iterations per load step (200 Newton / 100000 fixed point)
  *   fixed_iterations > 0: run exactly this many outer iterations per load step
@@ -156,6 +173,7 @@ typedef struct {
  *   c_min            boxel volume-fraction snap (1e-6)
  *   mu0              reference shear modulus of the fixed point; <= 0 picks
  *                    (min mu + max(lambda + 2 mu)) / 2
+ *   theory           COMBO_FINITE_STRAIN (default) or COMBO_INFINITESIMAL_STRAIN
  */
 typedef struct {
     int32_t precision;
@@ -172,6 +190,7 @@ typedef struct {
     int32_t nr_max_iter;
     double c_min;
     double mu0;
+    int32_t theory; /* COMBO_FINITE_STRAIN (default) or COMBO_INFINITESIMAL_STRAIN */
 } combo_options;
 
 /*

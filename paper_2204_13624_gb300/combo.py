@@ -20,6 +20,7 @@ E_NAMES = {-1: "invalid argument", -2: "out of memory", -3: "not converged", -4:
            -5: "inadmissible (det F <= 0)", -6: "NaN", -7: "timeout", -8: "CUDA error", -9: "cancelled"}
 FP64, FP32_REFINED, FP32_REFINED_DF = 0, 1, 2
 ROTATED, SPECTRAL, STAGGERED, STAGGERED_DFMG = 0, 1, 2, 3
+FINITE_STRAIN, INFINITESIMAL_STRAIN = 0, 1
 FIXED_POINT, NEWTON_CG, NONLINEAR_CG = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 
@@ -45,7 +46,8 @@ class OptionsS(C.Structure):
     _fields_ = [("precision", C.c_int32), ("kspace", C.c_int32), ("solver", C.c_int32), ("tol", C.c_double),
                 ("max_iter", C.c_int32), ("fixed_iterations", C.c_int32), ("cg_tol", C.c_double),
                 ("cg_max_iter", C.c_int32), ("cg_fixed_iterations", C.c_int32), ("nr_tol_rel", C.c_double),
-                ("nr_tol_abs", C.c_double), ("nr_max_iter", C.c_int32), ("c_min", C.c_double), ("mu0", C.c_double)]
+                ("nr_tol_abs", C.c_double), ("nr_max_iter", C.c_int32), ("c_min", C.c_double), ("mu0", C.c_double),
+                ("theory", C.c_int32)]
 
 
 class ResultS(C.Structure):

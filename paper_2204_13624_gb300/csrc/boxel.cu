@@ -485,9 +485,127 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
     }
 }
 
+// Infinitesimal-strain composite boxel in closed form (cheat sheet of the
+// appendix, right column), |N| = 1:
+//   Delta = N . (C+/c+ + C-/c-) . N = (mu+/c+ + mu-/c-) I + ((lam+ + mu+)/c+ + (lam- + mu-)/c-) N N^T,
+//   f = N . (C- - C+) : eps = (lam- - lam+) tr(eps) N + 2 (mu- - mu+) eps N,   a = Delta^{-1} f,
+//   eps+- = eps +- sym(a (x) N) / c+-,  sigma_box = c+ sigma+ + c- sigma-,
+//   C_box = (c+ C+ + c- C-) - dC (N (x) Delta^{-1} (x) N) dC  (packed, in Tc).
+// The tangent reuses TanPhase with G = I, g = N, m = mu, which is C.
+template <typename Tc> __global__ void __launch_bounds__(128) k_boxel_linear(BoxelArgs<Tc> A)
+{
+    __shared__ double red[32];
+    __shared__ int same_problem;
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int pb = (A.bprob && b < A.nb) ? A.bprob[b] : 0;
+    Scalars* sc = A.sc + pb;
+    double nev = 0.0;
+    if (b < A.nb && !(A.guard == 2 && sc->outer_done)) {
+        nev = 1.0;
+        const int64_t v = A.bidx[b];
+        double e[9], N[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+                e[3 * i + j] = 0.5 * (A.F[(3 * i + j) * A.V + v] + A.F[(3 * j + i) * A.V + v]) - (i == j ? 1.0 : 0.0);
+#pragma unroll
+        for (int i = 0; i < 3; i++) N[i] = A.bN[3 * b + i];
+        const double cp = A.bc[b], cm = 1.0 - cp;
+        const double* mp = A.matp ? A.matp + 4 * pb : nullptr;
+        const double mu[2] = {mp ? mp[0] : A.mu[0], mp ? mp[1] : A.mu[1]};
+        const double lam[2] = {mp ? mp[2] : A.lam[0], mp ? mp[3] : A.lam[1]};
+        const double d0 = mu[1] / cp + mu[0] / cm;
+        const double d1 = (lam[1] + mu[1]) / cp + (lam[0] + mu[0]) / cm;
+        double Dl[9], Di[9];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) Dl[3 * i + k] = (i == k ? d0 : 0.0) + d1 * N[i] * N[k];
+        const double tr = e[0] + e[4] + e[8];
+        double f[3], a[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+            f[i] = (lam[0] - lam[1]) * tr * N[i] +
+                   2.0 * (mu[0] - mu[1]) * (e[3 * i] * N[0] + e[3 * i + 1] * N[1] + e[3 * i + 2] * N[2]);
+        if (!inv3(Dl, Di)) {
+            raise_status(sc, COMBO_E_LAMINATE);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3; i++) a[i] = Di[3 * i] * f[0] + Di[3 * i + 1] * f[1] + Di[3 * i + 2] * f[2];
+            double trp = tr, trm = tr;
+            const double aN = a[0] * N[0] + a[1] * N[1] + a[2] * N[2];
+            trp += aN / cp;
+            trm -= aN / cm;
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    const double s = 0.5 * (a[i] * N[j] + a[j] * N[i]);
+                    const double ep = e[3 * i + j] + s / cp, em = e[3 * i + j] - s / cm;
+                    const double sp = 2.0 * mu[1] * ep + (i == j ? lam[1] * trp : 0.0);
+                    const double sm = 2.0 * mu[0] * em + (i == j ? lam[0] * trm : 0.0);
+                    A.bP[9 * b + 3 * i + j] = cp * sp + cm * sm;
+                }
+#pragma unroll
+            for (int i = 0; i < 3; i++) A.ba[3 * b + i] = a[i];
+            if (A.bA) {
+                TanPhase<Tc> tp, tm;
+#pragma unroll
+                for (int q = 0; q < 9; q++) tp.G[q] = tm.G[q] = (Tc)((q == 0 || q == 4 || q == 8) ? 1.0 : 0.0);
+#pragma unroll
+                for (int q = 0; q < 3; q++) tp.g[q] = tm.g[q] = (Tc)N[q];
+                tp.mu = (Tc)mu[1], tp.lam = (Tc)lam[1], tp.m = (Tc)mu[1];
+                tm.mu = (Tc)mu[0], tm.lam = (Tc)lam[0], tm.m = (Tc)mu[0];
+                Tc Nt[3] = {(Tc)N[0], (Tc)N[1], (Tc)N[2]};
+                Tc Dt[9];
+#pragma unroll
+                for (int q = 0; q < 9; q++) Dt[q] = (Tc)Di[q];
+                const Tc cpt = (Tc)cp, cmt = (Tc)cm;
+                Tc B[27], W[27];
+#pragma unroll
+                for (int r = 0; r < 9; r++)
+#pragma unroll
+                    for (int k = 0; k < 3; k++) B[3 * r + k] = tp.AD(Nt, r / 3, r % 3, k) - tm.AD(Nt, r / 3, r % 3, k);
+#pragma unroll
+                for (int r = 0; r < 9; r++)
+#pragma unroll
+                    for (int k = 0; k < 3; k++)
+                        W[3 * r + k] = B[3 * r] * Dt[k] + B[3 * r + 1] * Dt[3 + k] + B[3 * r + 2] * Dt[6 + k];
+                const int64_t kb = A.rank ? (int64_t)A.rank[b] : b;
+#pragma unroll
+                for (int r = 0; r < 9; r++)
+#pragma unroll
+                    for (int s2 = r; s2 < 9; s2++) {
+                        const Tc avg = cpt * tp.A(r / 3, r % 3, s2 / 3, s2 % 3) + cmt * tm.A(r / 3, r % 3, s2 / 3, s2 % 3);
+                        const Tc corr = W[3 * r] * B[3 * s2] + W[3 * r + 1] * B[3 * s2 + 1] + W[3 * r + 2] * B[3 * s2 + 2];
+                        A.bA[(int64_t)sym_idx(r, s2) * A.nb + kb] = avg - corr;
+                    }
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        const int64_t first = (int64_t)blockIdx.x * blockDim.x;
+        const int64_t last = min(first + (int64_t)blockDim.x, A.nb) - 1;
+        same_problem = (!A.bprob || A.bprob[first] == A.bprob[last]) ? 1 : 0;
+    }
+    __syncthreads();
+    if (same_problem) {
+        const double s3 = block_sum(nev, red);
+        if (threadIdx.x == 0)
+            atomicAdd(&(A.sc + (A.bprob ? A.bprob[(int64_t)blockIdx.x * blockDim.x] : 0))->n_lam, (unsigned long long)s3);
+    } else if (nev > 0.0) {
+        atomicAdd(&sc->n_lam, (unsigned long long)nev);
+    }
+}
+
 template <typename Tc> void launch_boxel(const BoxelArgs<Tc>& a, cudaStream_t st)
 {
     if (a.nb <= 0) return;
+    if (a.linear) {
+        k_boxel_linear<Tc><<<(int)((a.nb + 127) / 128), 128, 0, st>>>(a);
+        return;
+    }
     const int grid = (int)((a.nb + 127) / 128);
     if constexpr (std::is_same<Tc, float>::value) {
         if (a.dfloat) {

@@ -393,6 +393,7 @@ template <typename T, typename Tc> struct XfwdArgs {
     Scalars* sc;
     int fuse;            // last block turns the pAp partials into alpha
     int cfg;             // launch-shape candidate (autotuner; 0 = default)
+    int linear;          // infinitesimal strain: isotropic linear phases (XF_RESID)
 };
 
 template <typename T, typename Tc> struct XinvArgs {
@@ -527,6 +528,20 @@ __device__ __forceinline__ bool nh_P64(const double f[9], double mu, double lam,
     return true;
 }
 
+// Infinitesimal strain: sigma = lam tr(H) I + mu (H + H^T), H = F - I (an
+// isotropic linear phase; sigma depends on sym(H) only)
+__device__ __forceinline__ void lin_sigma(const double f[9], double mu, double lam, double S[9])
+{
+    const double tr = (f[0] - 1.0) + (f[4] - 1.0) + (f[8] - 1.0);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const double hij = f[3 * i + j] - (i == j ? 1.0 : 0.0), hji = f[3 * j + i] - (i == j ? 1.0 : 0.0);
+            S[3 * i + j] = mu * (hij + hji) + (i == j ? lam * tr : 0.0);
+        }
+}
+
 // Arguments of the doubly-fine material grid law (dfmg.cu, boxel.cu): the
 // field F [9][V] of nprob problems stacked along z (Vp voxels, n1 x n2 x n3
 // each); S [72][V] receives, at cell c and row 9 l + comp, component comp of
@@ -568,6 +583,7 @@ template <typename Tc> struct BoxelArgs {
     Scalars* sc;
     int guard;
     int dfloat;  // phase states and residual in double-float (refined double-float form)
+    int linear;  // infinitesimal strain: the closed-form linear laminate (no Newton)
     // doubly-fine material grid (launch_boxel_dfmg): one laminate per boxel
     // sub-cell, ba holds [nb][8][3], the stress goes to S [72][V]
     double* S;

@@ -609,7 +609,7 @@ __global__ void k_update_F(double* __restrict__ F, const Tc* __restrict__ x, con
 // P field of F (pure voxels Neo-Hookean, boxels from the laminate stresses)
 // matp [nprob][4] per problem of Vp voxels, or null: mat
 __global__ void k_eval_P(const double* F, const uint8_t* phase, const int32_t* vox2box, const double* bP, Mat9 mat,
-                         double* P, int64_t V, Scalars* sc, const double* matp, int64_t Vp)
+                         double* P, int64_t V, Scalars* sc, const double* matp, int64_t Vp, int linear)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
         const int ph = phase[v];
@@ -622,6 +622,12 @@ __global__ void k_eval_P(const double* F, const uint8_t* phase, const int32_t* v
         for (int c = 0; c < 9; c++) f[c] = F[c * V + v];
         const double* mp = matp ? matp + 4 * (v / Vp) : mat.v;
         const double mu = mp[ph], lam = mp[2 + ph];
+        if (linear) {
+            double S[9];
+            lin_sigma(f, mu, lam, S);
+            for (int c = 0; c < 9; c++) P[c * V + v] = S[c];
+            continue;
+        }
         const double c0 = f[4] * f[8] - f[5] * f[7], c1 = f[5] * f[6] - f[3] * f[8], c2 = f[3] * f[7] - f[4] * f[6];
         const double J = f[0] * c0 + f[1] * c1 + f[2] * c2;
         if (!(J > 0.0)) {
@@ -655,7 +661,7 @@ constexpr int PHASE_GRID = 152 * 4;
 __global__ void __launch_bounds__(256) k_phase_sums(const double* F, int64_t V, const uint8_t* phase, int64_t v0,
                                                     int64_t v1, const int32_t* bidx, const double* bN,
                                                     const double* bc, const double* ba, int64_t b0, int64_t b1,
-                                                    Mat9 mat, double* part, Scalars* sc)
+                                                    Mat9 mat, double* part, Scalars* sc, int linear)
 {
     double s[PHASE_SUMS];
 #pragma unroll
@@ -666,7 +672,9 @@ __global__ void __launch_bounds__(256) k_phase_sums(const double* F, int64_t V, 
         if (ph == 2) continue;
         double f[9], P[9];
         for (int c = 0; c < 9; c++) f[c] = F[c * V + v];
-        if (!nh_P64(f, mat.v[ph], mat.v[2 + ph], P)) {
+        if (linear) {
+            lin_sigma(f, mat.v[ph], mat.v[2 + ph], P);
+        } else if (!nh_P64(f, mat.v[ph], mat.v[2 + ph], P)) {
             atomicCAS(&sc->status, 0, COMBO_E_INADMISSIBLE);
             continue;
         }
@@ -685,7 +693,12 @@ __global__ void __launch_bounds__(256) k_phase_sums(const double* F, int64_t V, 
                 fp[3 * i + J] = f + aN / cp;
                 fm[3 * i + J] = f - aN / cm;
             }
-        if (!nh_P64(fp, mat.v[1], mat.v[3], Pp) || !nh_P64(fm, mat.v[0], mat.v[2], Pm)) {
+        // (infinitesimal strain: sigma depends on sym(H) only, so a (x) N
+        // stands for its symmetric part)
+        if (linear) {
+            lin_sigma(fp, mat.v[1], mat.v[3], Pp);
+            lin_sigma(fm, mat.v[0], mat.v[2], Pm);
+        } else if (!nh_P64(fp, mat.v[1], mat.v[3], Pp) || !nh_P64(fm, mat.v[0], mat.v[2], Pm)) {
             atomicCAS(&sc->status, 0, COMBO_E_INADMISSIBLE);
             continue;
         }
@@ -896,6 +909,10 @@ static int check_options(combo_options& o)
         return fail(COMBO_E_INVALID_ARG, "bad solver");
     if (o.solver != COMBO_NEWTON_CG && o.precision != COMBO_FP64)
         return fail(COMBO_E_INVALID_ARG, "the fixed point and nonlinear CG run in FP64 only");
+    if (o.theory != COMBO_FINITE_STRAIN && o.theory != COMBO_INFINITESIMAL_STRAIN)
+        return fail(COMBO_E_INVALID_ARG, "bad theory");
+    if (o.kspace == COMBO_STAGGERED_DFMG && o.theory == COMBO_INFINITESIMAL_STRAIN)
+        return fail(COMBO_E_INVALID_ARG, "the doubly-fine material grid is built for finite strain only");
     if (o.kspace == COMBO_STAGGERED_DFMG && o.solver == COMBO_NEWTON_CG)
         return fail(COMBO_E_INVALID_ARG, "the doubly-fine material grid runs with the fixed point or nonlinear CG");
     if (o.max_iter <= 0) o.max_iter = (o.solver == COMBO_NEWTON_CG) ? 200 : 100000;
@@ -1058,6 +1075,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
 
     bool newton() const { return opt.solver == COMBO_NEWTON_CG; }
     bool dfmg() const { return opt.kspace == COMBO_STAGGERED_DFMG; }
+    bool linear() const { return opt.theory == COMBO_INFINITESIMAL_STRAIN; }
 
     int init(combo_ctx* c, HostProblem&& h, const combo_options& o)
     {
@@ -1348,6 +1366,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         a.bprob = d_bprob;
         a.matp = d_mat;
         a.dfloat = std::is_same<Rt, df32>::value ? 1 : 0;
+        a.linear = linear() ? 1 : 0;
         a.F = d_F;
         a.mu[0] = hp.mu[0];
         a.mu[1] = hp.mu[1];
@@ -1435,6 +1454,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         xf.F = d_F;
         xf.bP = d_bP;
         xf.X = dfmg() ? d_Pd : nullptr;  // the gathered stress of the doubly-fine material grid
+        xf.linear = linear() ? 1 : 0;
         xf.tc = (xi_mode == XI_RHS) ? d_tc : nullptr;
         xf.matp = d_mat;
         xf.nb = nb;
@@ -1597,7 +1617,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                                                           d_bN, d_bc, d_ba8, b0, b1, m, d_phpart, d_sc);
         else
             k_phase_sums<<<PHASE_GRID, 256, 0, st>>>(d_F, g.V, d_phase, v0, v1, d_bidx, d_bN, d_bc, d_ba, b0, b1, m,
-                                                     d_phpart, d_sc);
+                                                     d_phpart, d_sc, linear() ? 1 : 0);
         CK(cudaGetLastError());
         std::vector<double> part((size_t)PHASE_GRID * PHASE_SUMS);
         CK(cudaMemcpyAsync(part.data(), d_phpart, 8 * part.size(), cudaMemcpyDeviceToHost, st));
@@ -1709,7 +1729,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                         k_update_F<Tc><<<grid_for(g.V), 256, 0, st>>>(d_F, d_x, d_p, d, g.V, d_sc, nullptr, g.V);
                         prof.end();
                         if ((rc = read_scalars(s))) return error = rc;
-                        if (s.admissible) {
+                        if (s.admissible || linear()) {  // (det F is not constrained on small strains)
                             ok = true;
                             break;
                         }
@@ -1876,7 +1896,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                     if ((rc = read_all())) return error = rc;
                     bool bad = false;
                     for (int b = 0; b < B; b++) {
-                        if (dv[b] != 0.0 && !hsc[b].admissible) {
+                        if (dv[b] != 0.0 && !hsc[b].admissible && !linear()) {
                             dv[b] = -std::ldexp(1.0, -(h + 1));  // F_old + 2^-(h+1) x
                             bad = true;
                         } else {
@@ -1910,7 +1930,8 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         if (needP) {
             CK(cudaMalloc(&P, 8 * 9 * (size_t)g.V));
             Mat9 m{};
-            k_eval_P<<<grid_for(g.V), 256, 0, st>>>(d_F, d_phase, d_v2b, d_bP, m, P, g.V, d_sc, d_mat, Vp);
+            k_eval_P<<<grid_for(g.V), 256, 0, st>>>(d_F, d_phase, d_v2b, d_bP, m, P, g.V, d_sc, d_mat, Vp,
+                                                    linear() ? 1 : 0);
             CK(cudaGetLastError());
         }
         int rc = COMBO_OK;
@@ -1989,7 +2010,8 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             m.v[1] = hp.mu[1];
             m.v[2] = hp.lam[0];
             m.v[3] = hp.lam[1];
-            k_eval_P<<<grid_for(V), 256, 0, st>>>(d_F, d_phase, d_v2b, d_bP, m, P, V, d_sc, nullptr, V);
+            k_eval_P<<<grid_for(V), 256, 0, st>>>(d_F, d_phase, d_v2b, d_bP, m, P, V, d_sc, nullptr, V,
+                                                  linear() ? 1 : 0);
             if (!dev) {
                 CK(cudaMemcpyAsync(r->P_out, P, 8 * 9 * V, cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));

@@ -227,6 +227,19 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
 #pragma unroll
                         for (int c = 0; c < 10; c++) a.tc[c * V + v] = (Tc)0;
                     }
+                } else if (a.linear) {
+                    // infinitesimal strain: sigma = C : sym(F - I); the tangent
+                    // cache holds G = I, m = mu, for which the Neo-Hookean
+                    // tangent formula is exactly C
+                    double S[9];
+                    lin_sigma(F, mu[ph], lam[ph], S);
+#pragma unroll
+                    for (int c = 0; c < 9; c++) o[c] = (T)S[c];
+                    if (a.tc) {
+#pragma unroll
+                        for (int c = 0; c < 9; c++) a.tc[c * V + v] = (Tc)((c == 0 || c == 4 || c == 8) ? 1.0 : 0.0);
+                        a.tc[9 * V + v] = (Tc)mu[ph];
+                    }
                 } else if constexpr (std::is_same<T, df32>::value) {
                     float G[9], m;
                     if (!nh_stress_df(F, mu[ph], lam[ph], o, G, m)) {
