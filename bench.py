@@ -620,7 +620,11 @@ def variants_bench(combo, ctx):
                                                  kspace=combo.STAGGERED)),
             ("nonlinear_cg_staggered_dfmg_fp64", dict(solver=combo.NONLINEAR_CG, precision=combo.FP64,
                                                       kspace=combo.STAGGERED_DFMG)),
-            ("basic_scheme_rotated_fp64", dict(solver=combo.FIXED_POINT, precision=combo.FP64))]
+            ("basic_scheme_rotated_fp64", dict(solver=combo.FIXED_POINT, precision=combo.FP64)),
+            ("newton_cg_rotated_refined_df_infinitesimal_strain",
+             dict(solver=combo.NEWTON_CG, precision=combo.FP32_REFINED_DF, theory=combo.INFINITESIMAL_STRAIN)),
+            ("newton_cg_rotated_fp64_infinitesimal_strain",
+             dict(solver=combo.NEWTON_CG, precision=combo.FP64, theory=combo.INFINITESIMAL_STRAIN))]
     out = {"problem": "128^3 random balls r=8 vox, vf 0.2, contrast 10, Fbar11 = 1.05 in 2 steps, tol 1e-8"}
     ref = None
     for name, o in runs:
