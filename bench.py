@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--serve-full", action="store_true",
                     help="serving stream of sides 64..256 and 1..10 load steps (takes minutes)")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel table here")
+    ap.add_argument("--dfmg-only", type=int, default=0, metavar="N",
+                    help="only the doubly-fine material grid kernel timings on an N^3 random-ball problem")
     return ap.parse_args()
 
 
@@ -245,6 +247,13 @@ def main():
     stream = torch.cuda.Stream(device=local)
     torch.cuda.set_stream(stream)
     ctx = combo.Context(local, stream.cuda_stream)
+    if args.dfmg_only:
+        from paper_2204_13624_gb300 import microstructure as ms
+
+        n = args.dfmg_only
+        p = ms.random_spheres((n, n, n), 8.0, 0.2, ms.SEED_BASE + 6, 10.0, np.diag([1.05, 1.0, 1.0]), 2)
+        print(json.dumps({"dfmg_only": n, "dfmg_kernels": dfmg_kernels(combo, ctx, p)}))
+        return
     if args.normals_only:
         from paper_2204_13624_gb300 import microstructure as ms
 
