@@ -199,6 +199,22 @@ def ncu_traffic(kernel, alg_bytes):
     return None
 
 
+# ---------------------------------------------------------------- replicas
+def replicas_aggregate(ms, ops, dist, device):
+    """Whole-job figures of N independent replicas (one per rank, no data-path
+    collective): the longest timed region over the ranks and the operator
+    applications of all ranks.  dist None: the rank's own figures."""
+    if dist is None:
+        return ms, ops
+    import torch
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    o = torch.tensor([float(ops)], device=device, dtype=torch.float64)
+    dist.all_reduce(o, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(o.item())
+
+
 # ---------------------------------------------------------------- CPU baseline
 def cpu_baseline(p, iters=1):
     """The oracle as it stands (FP64 fixed point, OpenMP over the host cores)
@@ -293,15 +309,7 @@ def main():
     prof = s.profile_read()
     s.profile(False)
     s.close()
-    t_max = ms
-    ops_all = ops
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        o = torch.tensor([ops], device="cuda", dtype=torch.float64)
-        dist.all_reduce(o, op=dist.ReduceOp.SUM)
-        ops_all = int(o.item())
+    t_max, ops_all = replicas_aggregate(ms, ops, dist, "cuda")
     value = ops_all * V / (t_max / 1e3)
 
     # per-kernel table and the dominant kernel's roofline
