@@ -158,7 +158,10 @@ typedef struct {
 /*
  * Solver options; combo_options_default() fills the defaults given here.
  *   precision        COMBO_FP64 (default), COMBO_FP32_REFINED or COMBO_FP32_REFINED_DF
- *                    (the refined forms with COMBO_NEWTON_CG only)
+ *                    (COMBO_FP32_REFINED with COMBO_NEWTON_CG only; with the fixed
+ *                    point and nonlinear CG, COMBO_FP32_REFINED_DF evaluates every
+ *                    residual -- law, doubly-fine sub-cell laws and gather, transforms --
+ *                    in double-float arithmetic and keeps F in FP64)
  *   kspace           COMBO_ROTATED (default), COMBO_SPECTRAL, COMBO_STAGGERED or
  *                    COMBO_STAGGERED_DFMG
  *   solver           COMBO_NEWTON_CG (default), COMBO_FIXED_POINT or COMBO_NONLINEAR_CG

@@ -688,8 +688,17 @@ __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArgs<double> A)
                 sc->fail_state[12] = cp;
             }
         } else {
+            if (A.dfloat) {  // S in (hi, lo) pairs: the double-float residual form
+                float2* S2 = reinterpret_cast<float2*>(A.S);
 #pragma unroll
-            for (int c = 0; c < 9; c++) A.S[(int64_t)(9 * l + c) * A.V + v] = cp * e.p.P[c] + cm * e.m.P[c];
+                for (int c = 0; c < 9; c++) {
+                    const df32 t(cp * e.p.P[c] + cm * e.m.P[c]);
+                    S2[(int64_t)(9 * l + c) * A.V + v] = make_float2(t.hi, t.lo);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 9; c++) A.S[(int64_t)(9 * l + c) * A.V + v] = cp * e.p.P[c] + cm * e.m.P[c];
+            }
 #pragma unroll
             for (int q = 0; q < 3; q++) A.ba[24 * b + 3 * l + q] = a[q];
         }

@@ -557,6 +557,8 @@ struct DfmgArgs {
     int n1, n2, n3;
     Scalars* sc;
     int guard;           // 2: skip problems whose outer iteration is done
+    int dfloat;          // double-float residual form: the pure-cell laws and the gather in double-float,
+                         // S holds (hi, lo) float pairs in place of doubles
 };
 void launch_dfmg_pure(const DfmgArgs& a, cudaStream_t st);
 void launch_dfmg_gather(const DfmgArgs& a, cudaStream_t st);

@@ -30,6 +30,140 @@ static int dfmg_grid(int64_t n)
     return (int)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
 }
 
+// Neo-Hookean P of F_sub in double-float: cofactors, J, 1/J and P in df32,
+// ln J in FP64 (one logarithm per sub-cell).  False if J <= 0.
+__device__ __forceinline__ bool nh_P_df(const df32 F[9], double mu, double lam, df32 P[9])
+{
+    const df32 c0 = F[4] * F[8] - F[5] * F[7];
+    const df32 c1 = F[5] * F[6] - F[3] * F[8];
+    const df32 c2 = F[3] * F[7] - F[4] * F[6];
+    const df32 J = F[0] * c0 + F[1] * c1 + F[2] * c2;
+    if (!(J.hi > 0.f)) return false;
+    const df32 iJ = df32(1.f, 0.f) / J;
+    df32 G[9];
+    G[0] = c0 * iJ;
+    G[1] = (F[2] * F[7] - F[1] * F[8]) * iJ;
+    G[2] = (F[1] * F[5] - F[2] * F[4]) * iJ;
+    G[3] = c1 * iJ;
+    G[4] = (F[0] * F[8] - F[2] * F[6]) * iJ;
+    G[5] = (F[2] * F[3] - F[0] * F[5]) * iJ;
+    G[6] = c2 * iJ;
+    G[7] = (F[1] * F[6] - F[0] * F[7]) * iJ;
+    G[8] = (F[0] * F[4] - F[1] * F[3]) * iJ;
+    const df32 k = df32(lam * log((double)J) - mu), mud = df32(mu);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) P[3 * i + j] = mud * F[3 * i + j] + k * G[3 * j + i];
+    return true;
+}
+
+// Double-float form of k_dfmg_pure: the 27 distinct entries a cell's
+// sub-cells draw from F (the diagonal, each off-diagonal pair at its four
+// staggered positions) are converted once; S receives (hi, lo) pairs.
+__global__ void __launch_bounds__(256) k_dfmg_pure_df(DfmgArgs a)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t V = a.V;
+    float2* __restrict__ S = reinterpret_cast<float2*>(a.S);
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += stride) {
+        const int ph = a.phase[v];
+        if (ph == 2) continue;  // composite boxel: k_boxel_dfmg
+        const int pb = (int)(v / a.Vp);
+        Scalars* sc = a.sc + pb;
+        if (a.guard == 2 && sc->outer_done) continue;
+        const int64_t base = (int64_t)pb * a.Vp, lv = v - base;
+        const int i = (int)(lv % a.n1), j = (int)((lv / a.n1) % a.n2), k = (int)(lv / ((int64_t)a.n1 * a.n2));
+        const int ip = (i + 1 == a.n1) ? 0 : i + 1, jp = (j + 1 == a.n2) ? 0 : j + 1, kp = (k + 1 == a.n3) ? 0 : k + 1;
+        const double mu = a.matp ? a.matp[4 * pb + ph] : a.mu[ph];
+        const double lam = a.matp ? a.matp[4 * pb + 2 + ph] : a.lam[ph];
+        auto at = [&](int c, int x, int y, int z) {
+            return df32(a.F[(int64_t)c * V + base + x + (int64_t)a.n1 * (y + (int64_t)a.n2 * z)]);
+        };
+        const df32 d0 = at(0, i, j, k), d4 = at(4, i, j, k), d8 = at(8, i, j, k);
+        df32 o12[4][2], o13[4][2], o23[4][2];  // [la + 2 lb][first, second component of the pair]
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int x1 = (q & 1) ? ip : i, y1 = (q & 2) ? jp : j;  // (l1, l2) for the 12 pair
+            o12[q][0] = at(1, x1, y1, k);
+            o12[q][1] = at(3, x1, y1, k);
+            const int z1 = (q & 2) ? kp : k;  // (l1, l3) for the 13 pair
+            o13[q][0] = at(2, x1, j, z1);
+            o13[q][1] = at(6, x1, j, z1);
+            const int y2 = (q & 1) ? jp : j;  // (l2, l3) for the 23 pair
+            o23[q][0] = at(5, i, y2, z1);
+            o23[q][1] = at(7, i, y2, z1);
+        }
+        bool ok = true;
+#pragma unroll
+        for (int l = 0; l < 8; l++) {
+            const int l1 = l & 1, l2 = (l >> 1) & 1, l3 = (l >> 2) & 1;
+            const int q12 = l1 + 2 * l2, q13 = l1 + 2 * l3, q23 = l2 + 2 * l3;
+            df32 f[9], P[9];
+            f[0] = d0;
+            f[4] = d4;
+            f[8] = d8;
+            f[1] = o12[q12][0];
+            f[3] = o12[q12][1];
+            f[2] = o13[q13][0];
+            f[6] = o13[q13][1];
+            f[5] = o23[q23][0];
+            f[7] = o23[q23][1];
+            if (!nh_P_df(f, mu, lam, P)) {
+                ok = false;
+#pragma unroll
+                for (int c = 0; c < 9; c++) P[c] = df32(0.f, 0.f);
+            }
+#pragma unroll
+            for (int c = 0; c < 9; c++) S[(int64_t)(9 * l + c) * V + v] = make_float2(P[c].hi, P[c].lo);
+        }
+        if (!ok) raise_status(sc, COMBO_E_INADMISSIBLE);
+    }
+}
+
+// Double-float form of k_dfmg_gather: sums of (hi, lo) pairs in df32, P in FP64.
+__global__ void __launch_bounds__(256) k_dfmg_gather_df(DfmgArgs a)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t V = a.V;
+    const float2* __restrict__ S = reinterpret_cast<const float2*>(a.S);
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += stride) {
+        const int pb = (int)(v / a.Vp);
+        if (a.guard == 2 && a.sc[pb].outer_done) continue;
+        const int64_t base = (int64_t)pb * a.Vp, lv = v - base;
+        const int i = (int)(lv % a.n1), j = (int)((lv / a.n1) % a.n2), k = (int)(lv / ((int64_t)a.n1 * a.n2));
+        const int im = (i == 0) ? a.n1 - 1 : i - 1;
+        const int jm = (j == 0) ? a.n2 - 1 : j - 1;
+        const int km = (k == 0) ? a.n3 - 1 : k - 1;
+        df32 o[9];
+#pragma unroll
+        for (int c = 0; c < 9; c++) o[c] = df32(0.f, 0.f);
+        auto ld = [&](int64_t idx) {
+            const float2 t = S[idx];
+            return df32(t.x, t.y);
+        };
+#pragma unroll 2
+        for (int l = 0; l < 8; l++) {
+            const int ii = (l & 1) ? im : i, jj = (l & 2) ? jm : j, kk = (l & 4) ? km : k;
+            const int64_t c12 = base + ii + (int64_t)a.n1 * (jj + (int64_t)a.n2 * k);
+            const int64_t c13 = base + ii + (int64_t)a.n1 * (j + (int64_t)a.n2 * kk);
+            const int64_t c23 = base + i + (int64_t)a.n1 * (jj + (int64_t)a.n2 * kk);
+            const int64_t r0 = (int64_t)9 * l * V;
+            o[0] += ld(r0 + 0 * V + v);
+            o[4] += ld(r0 + 4 * V + v);
+            o[8] += ld(r0 + 8 * V + v);
+            o[1] += ld(r0 + 1 * V + c12);
+            o[3] += ld(r0 + 3 * V + c12);
+            o[2] += ld(r0 + 2 * V + c13);
+            o[6] += ld(r0 + 6 * V + c13);
+            o[5] += ld(r0 + 5 * V + c23);
+            o[7] += ld(r0 + 7 * V + c23);
+        }
+#pragma unroll
+        for (int c = 0; c < 9; c++) a.P[(int64_t)c * V + v] = 0.125 * (double)o[c];
+    }
+}
+
 __global__ void __launch_bounds__(256) k_dfmg_pure(DfmgArgs a)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -110,9 +244,21 @@ __global__ void k_dfmg_amean(const double* __restrict__ ba8, double* __restrict_
     ba[t] = 0.125 * s;
 }
 
-void launch_dfmg_pure(const DfmgArgs& a, cudaStream_t st) { k_dfmg_pure<<<dfmg_grid(a.V), 256, 0, st>>>(a); }
+void launch_dfmg_pure(const DfmgArgs& a, cudaStream_t st)
+{
+    if (a.dfloat)
+        k_dfmg_pure_df<<<dfmg_grid(a.V), 256, 0, st>>>(a);
+    else
+        k_dfmg_pure<<<dfmg_grid(a.V), 256, 0, st>>>(a);
+}
 
-void launch_dfmg_gather(const DfmgArgs& a, cudaStream_t st) { k_dfmg_gather<<<dfmg_grid(a.V), 256, 0, st>>>(a); }
+void launch_dfmg_gather(const DfmgArgs& a, cudaStream_t st)
+{
+    if (a.dfloat)
+        k_dfmg_gather_df<<<dfmg_grid(a.V), 256, 0, st>>>(a);
+    else
+        k_dfmg_gather<<<dfmg_grid(a.V), 256, 0, st>>>(a);
+}
 
 void launch_dfmg_amean(const double* ba8, double* ba, int64_t nb, cudaStream_t st)
 {

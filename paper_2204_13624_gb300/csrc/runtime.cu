@@ -907,8 +907,9 @@ static int check_options(combo_options& o)
         return fail(COMBO_E_INVALID_ARG, "bad kspace");
     if (o.solver != COMBO_FIXED_POINT && o.solver != COMBO_NEWTON_CG && o.solver != COMBO_NONLINEAR_CG)
         return fail(COMBO_E_INVALID_ARG, "bad solver");
-    if (o.solver != COMBO_NEWTON_CG && o.precision != COMBO_FP64)
-        return fail(COMBO_E_INVALID_ARG, "the fixed point and nonlinear CG run in FP64 only");
+    if (o.solver != COMBO_NEWTON_CG && o.precision == COMBO_FP32_REFINED)
+        return fail(COMBO_E_INVALID_ARG,
+                    "the fixed point and nonlinear CG run in FP64 or the double-float residual form");
     if (o.theory != COMBO_FINITE_STRAIN && o.theory != COMBO_INFINITESIMAL_STRAIN)
         return fail(COMBO_E_INVALID_ARG, "bad theory");
     if (o.kspace == COMBO_STAGGERED_DFMG && o.theory == COMBO_INFINITESIMAL_STRAIN)
@@ -1403,6 +1404,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         d.n3 = hp.n[2];
         d.sc = d_sc;
         d.guard = guard;
+        d.dfloat = std::is_same<Rt, df32>::value ? 1 : 0;
         if (nb > 0) {
             BoxelArgs<double> a{};
             a.nb = nb;
@@ -1424,6 +1426,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             a.sc = d_sc;
             a.guard = guard;
             a.S = d_S;
+            a.dfloat = d.dfloat;
             a.Vp = d.Vp;
             a.n1 = d.n1;
             a.n2 = d.n2;

@@ -77,6 +77,28 @@ def test_converged_sphere(cb, orc):
     assert g0["iters"].sum() > g["iters"].sum()
 
 
+@pytest.mark.parametrize("kspace", [0, DFMG])
+@pytest.mark.parametrize("solver", [0, 2])
+@pytest.mark.parametrize("k", [0, 1])
+def test_double_float_residual_form(cb, orc, k, solver, kspace):
+    """The fixed point and nonlinear CG with the double-float residual form
+    (COMBO_FP32_REFINED_DF: the law -- the doubly-fine sub-cell laws and their
+    gather included -- and the transforms in double-float, F in FP64):
+    iteration by iteration within 1e-10 of the FP64 oracle."""
+    p = problems()[k]
+    g, r = solve_both(cb, orc, p, solver=solver, kspace=kspace, precision=2, fixed_iterations=6)
+    assert rel(g["F"], r["F"]) < 1e-10
+    assert rel(g["Pbar"], r["Pbar"]) < 1e-9
+    assert list(g["iters"]) == list(r["iters"])
+
+
+def test_refined_fp32_form_rejected_without_newton(cb):
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    with pytest.raises(Exception):
+        cb.solve(ms.homogeneous((8, 8, 8)), solver=2, precision=1)
+
+
 def test_newton_rejected(cb):
     from paper_2204_13624_gb300 import microstructure as ms
 
