@@ -622,7 +622,7 @@ template <typename Tc> void launch_boxel(const BoxelArgs<Tc>& a, cudaStream_t st
 // a [nb][8][3]; the boxel stress c+ P+ + c- P- goes to S[9 l + comp][v].
 // One thread per (boxel, sub-cell), FP64 (the fixed point and nonlinear CG
 // run in FP64 only).
-__global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArgs<double> A)
+template <bool DFM> __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArgs<double> A)
 {
     __shared__ double red[64];
     __shared__ int same_problem;
@@ -650,10 +650,27 @@ __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArgs<double> A)
         const double mu[2] = {mp ? mp[0] : A.mu[0], mp ? mp[1] : A.mu[1]};
         const double lam[2] = {mp ? mp[2] : A.lam[0], mp ? mp[3] : A.lam[1]};
         int status = 0, reason = 0;
-        Phase box;
+        double gbox[3];
+        df32 Fd[9], Nd[3], icp, icm;
+        if constexpr (DFM) {
 #pragma unroll
-        for (int c = 0; c < 9; c++) box.F[c] = Fb[c];
-        if (!nh_phase(box, mu[0], lam[0], N)) status = COMBO_E_INADMISSIBLE;
+            for (int c = 0; c < 9; c++) Fd[c] = df32(Fb[c]);
+#pragma unroll
+            for (int q = 0; q < 3; q++) Nd[q] = df32(N[q]);
+            icp = df32(1.0 / cp);
+            icm = df32(1.0 / cm);
+            PhaseD box;
+#pragma unroll
+            for (int c = 0; c < 9; c++) box.F[c] = Fd[c];
+            if (!nh_phase_df(box, mu[0], lam[0], Nd, gbox)) status = COMBO_E_INADMISSIBLE;
+        } else {
+            Phase box;
+#pragma unroll
+            for (int c = 0; c < 9; c++) box.F[c] = Fb[c];
+            if (!nh_phase(box, mu[0], lam[0], N)) status = COMBO_E_INADMISSIBLE;
+#pragma unroll
+            for (int q = 0; q < 3; q++) gbox[q] = box.g[q];
+        }
         LamEval e;
         auto eval64 = [&](LamEval& x) { return lam_eval(x, Fb, N, cp, cm, a, mu, lam, A.tol_rel, A.tol_abs); };
         auto inv64 = [&](const LamEval& x, double Di[9]) {
@@ -662,15 +679,34 @@ __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArgs<double> A)
             return inv3(Dl, Di);
         };
         if (!status) {
-            const double ng = sqrt(box.g[0] * box.g[0] + box.g[1] * box.g[1] + box.g[2] * box.g[2]);
-            const double m[3] = {box.g[0] / ng, box.g[1] / ng, box.g[2] / ng};
+            const double ng = sqrt(gbox[0] * gbox[0] + gbox[1] * gbox[1] + gbox[2] * gbox[2]);
+            const double m[3] = {gbox[0] / ng, gbox[1] / ng, gbox[2] / ng};
             const double bcp = -cp / ng, bcm = cm / ng;
             const double beta = a[0] * m[0] + a[1] * m[1] + a[2] * m[2];
             if (!(beta > bcp && beta < bcm)) a[0] = a[1] = a[2] = 0.0;
-            int it = 0;
+            int it = 0, it_df = 0;
+            if constexpr (DFM) {
+                // double-float iterations first (as in k_boxel's refined
+                // form); the FP64 residual then decides convergence
+                LamEvalD ed;
+                double ad[3] = {a[0], a[1], a[2]};
+                const int rdf = nr_loop(
+                    ed, ad, m, bcp, bcm, 0.0, it_df, A.max_iter, nbp,
+                    [&](LamEvalD& x) {
+                        if (!lam_eval(x, Fd, Nd, icp, icm, ad, mu, lam, A.tol_rel, A.tol_abs)) return false;
+                        x.eps = fmax(x.eps, x.floor);
+                        return true;
+                    },
+                    [&](const LamEvalD& x, double Dv[9]) { return hessian_inv(x, cp, cm, mu, lam, Dv); });
+                if (rdf == 0) {
+                    a[0] = ad[0];
+                    a[1] = ad[1];
+                    a[2] = ad[2];
+                }
+            }
             reason = nr_loop(e, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp, eval64, inv64);
             if (reason) status = COMBO_E_LAMINATE;
-            its = it;
+            its = it + it_df;
         } else {
             reason = 1;
         }
@@ -731,7 +767,10 @@ void launch_boxel_dfmg(const BoxelArgs<double>& a, cudaStream_t st)
 {
     if (a.nb <= 0) return;
     const int grid = (int)((8 * a.nb + 127) / 128);
-    k_boxel_dfmg<<<grid, 128, 0, st>>>(a);
+    if (a.dfloat)
+        k_boxel_dfmg<true><<<grid, 128, 0, st>>>(a);
+    else
+        k_boxel_dfmg<false><<<grid, 128, 0, st>>>(a);
 }
 
 template void launch_boxel<double>(const BoxelArgs<double>&, cudaStream_t);
