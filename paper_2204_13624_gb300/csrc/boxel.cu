@@ -678,6 +678,8 @@ template <bool DFM> __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArg
             hessian(x, cp, cm, mu, lam, Dl);
             return inv3(Dl, Di);
         };
+        LamEvalD ed;
+        bool df_done = false;  // the double-float iterations converged: their state is the result
         if (!status) {
             const double ng = sqrt(gbox[0] * gbox[0] + gbox[1] * gbox[1] + gbox[2] * gbox[2]);
             const double m[3] = {gbox[0] / ng, gbox[1] / ng, gbox[2] / ng};
@@ -686,9 +688,10 @@ template <bool DFM> __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArg
             if (!(beta > bcp && beta < bcm)) a[0] = a[1] = a[2] = 0.0;
             int it = 0, it_df = 0;
             if constexpr (DFM) {
-                // double-float iterations first (as in k_boxel's refined
-                // form); the FP64 residual then decides convergence
-                LamEvalD ed;
+                // the double-float residual form: Newton iterations on the
+                // double-float residual down to its rounding level; FP64
+                // iterations only where they stop early (a phase near
+                // collapse, an ill-conditioned Hessian)
                 double ad[3] = {a[0], a[1], a[2]};
                 const int rdf = nr_loop(
                     ed, ad, m, bcp, bcm, 0.0, it_df, A.max_iter, nbp,
@@ -702,10 +705,13 @@ template <bool DFM> __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArg
                     a[0] = ad[0];
                     a[1] = ad[1];
                     a[2] = ad[2];
+                    df_done = true;
                 }
             }
-            reason = nr_loop(e, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp, eval64, inv64);
-            if (reason) status = COMBO_E_LAMINATE;
+            if (!df_done) {
+                reason = nr_loop(e, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp, eval64, inv64);
+                if (reason) status = COMBO_E_LAMINATE;
+            }
             its = it + it_df;
         } else {
             reason = 1;
@@ -726,9 +732,10 @@ template <bool DFM> __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArg
         } else {
             if (A.dfloat) {  // S in (hi, lo) pairs: the double-float residual form
                 float2* S2 = reinterpret_cast<float2*>(A.S);
+                const df32 cpd(cp), cmd(cm);
 #pragma unroll
                 for (int c = 0; c < 9; c++) {
-                    const df32 t(cp * e.p.P[c] + cm * e.m.P[c]);
+                    const df32 t = df_done ? cpd * ed.p.P[c] + cmd * ed.m.P[c] : df32(cp * e.p.P[c] + cm * e.m.P[c]);
                     S2[(int64_t)(9 * l + c) * A.V + v] = make_float2(t.hi, t.lo);
                 }
             } else {
