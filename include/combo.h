@@ -161,7 +161,9 @@ typedef struct {
  *                    (COMBO_FP32_REFINED with COMBO_NEWTON_CG only; with the fixed
  *                    point and nonlinear CG, COMBO_FP32_REFINED_DF evaluates every
  *                    residual -- law, doubly-fine sub-cell laws and gather, transforms --
- *                    in double-float arithmetic and keeps F in FP64)
+ *                    in double-float arithmetic and keeps F in FP64; a doubly-fine boxel
+ *                    sub-cell laminate converges to the tolerance or the double-float
+ *                    rounding level)
  *   kspace           COMBO_ROTATED (default), COMBO_SPECTRAL, COMBO_STAGGERED or
  *                    COMBO_STAGGERED_DFMG
  *   solver           COMBO_NEWTON_CG (default), COMBO_FIXED_POINT or COMBO_NONLINEAR_CG
