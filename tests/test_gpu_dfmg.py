@@ -75,6 +75,11 @@ def test_converged_sphere(cb, orc):
     g0 = cb.solve(p, solver=0, kspace=DFMG, tol=1e-8)
     assert rel(g0["Pbar"][-1], g["Pbar"][-1]) < 1e-6
     assert g0["iters"].sum() > g["iters"].sum()
+    # the double-float residual form reaches the same state
+    gd = cb.solve(p, solver=2, kspace=DFMG, precision=2, tol=1e-8)
+    assert np.all(gd["resid"] <= 1e-8)
+    assert rel(gd["Pbar"], r["Pbar"]) < 1e-8
+    assert rel(gd["Pbar_phase"][-1], pa) < 1e-7
 
 
 @pytest.mark.parametrize("kspace", [0, DFMG])
