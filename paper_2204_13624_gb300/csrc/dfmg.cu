@@ -14,9 +14,12 @@
 //   (boxel.cu)     composite boxels: 8 laminates per boxel -> S
 //   k_dfmg_gather  S -> P [9][V], the operand of the residual's x-pass
 //
-// The work is FP64 arithmetic (8 logarithms, divisions and ~70 FMAs per cell)
-// and 2 x 576 B of S traffic per cell; on this part FP64 issues at a small
-// fraction of the FP32 rate, so the pure-cell kernel is FP64-pipe bound.
+// The work is FP64 arithmetic (per sub-cell a logarithm, a division and ~70
+// FMAs) and 2 x 576 B of S traffic per cell; on this part FP64 issues at a
+// small fraction of the FP32 rate, so both kernels are FP64-pipe bound.  The
+// double-float residual form (k_dfmg_pure_df, k_dfmg_gather_df) keeps only
+// the logarithm and the conversions on the FP64 pipe and stores S as (hi, lo)
+// float pairs of the same size.
 #include <cuda_runtime.h>
 
 #include "../../include/combo.h"

@@ -25,7 +25,7 @@ def cb():
     return combo
 
 
-@pytest.mark.parametrize("n", [(12, 9, 18), (16, 16, 16), (64, 32, 8), (8, 64, 6)])
+@pytest.mark.parametrize("n", [(12, 9, 18), (16, 16, 16), (64, 32, 8), (8, 64, 6), (64, 48, 96)])
 def test_law_parity(cb, orc, n):
     from paper_2204_13624_gb300 import microstructure as ms
 
