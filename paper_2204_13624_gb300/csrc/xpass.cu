@@ -348,6 +348,35 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
         acc += (double)accp;
         __syncthreads();
 
+        if constexpr (TAN) {
+            // the next group's operand rows (r, p, x, tangent cache) are
+            // prefetched into L2 while this group is transformed, so that its
+            // voxel phase finds them there
+            const int gn = grp + gp;
+            if (gn < ngroups) {
+                const int L0n = Lbase + gn * LB;
+                const int nlines = min(LB, Lend - L0n);
+                const int chunks = (g.n1 * (int)sizeof(Tc) + 127) / 128;  // 128-B lines per x-line
+                const int ncomp = 19 + (first ? 0 : 9) + (apend != (Tc)0 ? 9 : 0);
+                const int total = ncomp * nlines * chunks;
+                for (int e = threadIdx.x; e < total; e += blockDim.x) {
+                    const int q = e % chunks, rest = e / chunks;
+                    const int l = rest % nlines, c = rest / nlines;
+                    const Tc* base;
+                    if (c < 9)
+                        base = a.r + (int64_t)c * V;
+                    else if (c < 19)
+                        base = a.tc + (int64_t)(c - 9) * V;
+                    else if (!first && c < 28)
+                        base = a.p + (int64_t)(c - 19) * V;
+                    else
+                        base = a.x + (int64_t)(c - (first ? 19 : 28)) * V;
+                    const char* ptr = reinterpret_cast<const char*>(base + (int64_t)(L0n + l) * g.n1) + 128 * q;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+                }
+            }
+        }
+
         const int nl = 9 * LB;
         cx<T>* Z = xpass_fft<T, MF, false>(buf0, buf1, a.plan, nl, ls, tws);
 
