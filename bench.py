@@ -661,6 +661,28 @@ def variants_bench(combo, ctx):
                      "voxel_iterations_per_s": int(r["n_operator"]) * V / dt,
                      "Pbar_rel_diff_vs_rotated_newton": float(np.linalg.norm(r["Pbar"][-1] - ref) / np.linalg.norm(ref))}
     out["dfmg_kernels"] = dfmg_kernels(combo, ctx, p)
+    out["oracle"] = variants_oracle(combo, p)
+    return out
+
+
+def variants_oracle(combo, p):
+    """The oracle beside the variants: one load step of the same 128^3 problem,
+    a bounded number of operator applications per variant (FP64, the host
+    cores), as voxel-iterations/s."""
+    import oracle
+
+    cores = len(os.sched_getaffinity(0))
+    V = p["n"][0] * p["n"][1] * p["n"][2]
+    runs = [("nonlinear_cg_rotated", dict(solver=2, fixed_iter=2)),
+            ("nonlinear_cg_staggered_dfmg", dict(solver=2, kspace=3, fixed_iter=2)),
+            ("newton_cg_rotated_infinitesimal_strain", dict(solver=1, theory=1, fixed_iter=1, cg_fixed_iter=4))]
+    out = {"cores": cores, "kind": "oracle", "sample": "first load step of the 128^3 problem, FP64"}
+    for name, o in runs:
+        t0 = time.perf_counter()
+        r = oracle.solve(dict(p, n_steps=1), dict(o, nthreads=cores), fields=False)
+        dt = time.perf_counter() - t0
+        ops = int(r["n_operator"])
+        out[name] = {"operator_applications": ops, "seconds": dt, "voxel_iterations_per_s": ops * V / dt}
     return out
 
 
