@@ -389,12 +389,24 @@ int combo_solve_profile_read(combo_solve_state* s, int32_t max_classes, char* na
  *   *sumsq receives sum_x |Y(x)|^2.
  * combo_constitutive: P[9][V] (FP64) of the field F[9][V] (FP64): pure
  *   voxels Neo-Hookean (Sec. 6.1), boxels the laminate (Algorithms 1-2)
- *   started from a_io[n_boxels][3] (updated in place).  All in `mem`.
+ *   started from a_io[n_boxels][3] (updated in place); o->kspace and
+ *   o->theory select the doubly-fine law and the infinitesimal-strain law,
+ *   the arithmetic is FP64.  All in `mem`.
  */
 int combo_apply_G(combo_ctx* ctx, const int32_t n[3], const double l[3], int32_t kspace, int32_t precision,
                   const double* X, double* Y, double* sumsq, int32_t mem);
 int combo_constitutive(combo_ctx* ctx, const combo_problem* p, const combo_options* o, const double* F,
                        double* a_io, double* P, int32_t mem);
+
+/*
+ * combo_df_log: the double-float natural logarithm that the double-float
+ * forms use for ln J (series of 2 atanh((m - 1)/(m + 1)) after a power-of-two
+ * range reduction), exposed so that its accuracy can be tested:
+ * y[i] = ln x[i] evaluated in double-float and returned as FP64.  x, y host
+ * arrays of n >= 0 doubles; every x[i] must be positive and within the
+ * normal FP32 range (COMBO_E_INVALID_ARG otherwise, nothing computed).
+ */
+int combo_df_log(combo_ctx* ctx, const double* x, double* y, int64_t n);
 
 /*
  * combo_coarse_grain: composite boxels from a binary fine image (Sec. 5).

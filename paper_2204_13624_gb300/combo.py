@@ -64,7 +64,7 @@ EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_o
            "combo_constitutive", "combo_apply_G_noalloc", "combo_server_create", "combo_server_destroy",
            "combo_submit", "combo_poll", "combo_wait", "combo_cancel", "combo_server_stats",
            "combo_autotune_enable", "combo_autotune_force", "combo_autotune_report", "combo_coarse_grain",
-           "combo_coarse_grain_profile", "combo_coarse_grain_profile_read"]
+           "combo_coarse_grain_profile", "combo_coarse_grain_profile_read", "combo_df_log"]
 
 _lib = None
 
@@ -118,6 +118,8 @@ def load(path: str = LIB_PATH):
     L.combo_coarse_grain_profile.restype = C.c_int
     L.combo_coarse_grain_profile_read.argtypes = [vp]
     L.combo_coarse_grain_profile_read.restype = C.c_int
+    L.combo_df_log.argtypes = [vp, vp, vp, C.c_int64]
+    L.combo_df_log.restype = C.c_int
     _lib = L
     return L
 
@@ -415,6 +417,16 @@ def constitutive(prob: dict, F, a=None, ctx: Context | None = None, **opts):
     P = np.zeros_like(F)
     _check(load().combo_constitutive(ctx.h, C.byref(pb.s), C.byref(o), _ptr(F), _ptr(a), _ptr(P), MEM_HOST))
     return P, a[:nb]
+
+
+def df_log(x, ctx: Context | None = None):
+    """combo_df_log: ln x in the double-float arithmetic of the double-float
+    forms (for accuracy tests); x a host array of positive doubles."""
+    ctx = ctx or default_context()
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    y = np.zeros_like(x)
+    _check(load().combo_df_log(ctx.h, _ptr(x), _ptr(y), x.size))
+    return y
 
 
 NORMAL_LAPLACE = 0

@@ -155,8 +155,9 @@ __device__ __forceinline__ bool nh_phase_df(PhaseD& s, double mu, double lam, co
     s.G[6] = c2 * iJ;
     s.G[7] = (F[1] * F[6] - F[0] * F[7]) * iJ;
     s.G[8] = (F[0] * F[4] - F[1] * F[3]) * iJ;
-    s.lnJ = log((double)J);
-    const df32 k = df32(lam * s.lnJ - mu), mud = df32(mu);
+    const df32 lnJd = df_log(J), mud = df32(mu);
+    s.lnJ = (double)lnJd;
+    const df32 k = df32(lam) * lnJd - mud;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
 #pragma unroll

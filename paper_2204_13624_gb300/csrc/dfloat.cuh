@@ -77,4 +77,33 @@ __device__ __forceinline__ df32& operator*=(df32& a, df32 b) { return a = a * b;
 __device__ __forceinline__ bool operator>(df32 a, df32 b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 __device__ __forceinline__ bool operator<(df32 a, df32 b) { return b > a; }
 
+// Natural logarithm of x > 0 (x.hi a normal FP32 number) in double-float
+// arithmetic, from the series ln m = 2 atanh((m - 1)/(m + 1)) =
+// 2 sum_j u^(2j+1) / (2j+1) (Abramowitz & Stegun 4.1.27) after the range
+// reduction x = 2^k m, m in [1/sqrt(2), sqrt(2)) (scaling by a power of two is
+// exact), so |u| <= 0.1716 and u^2 <= 0.0295: the terms up to j = 10 leave a
+// truncation below 0.0295^11 / 23 < 2^-60 relative.  Horner in w = u^2, all in
+// double-float; ln 2 enters as the double-float split of its FP64 value.
+// Keeps the logarithm of the double-float Neo-Hookean stress off the FP64 pipe.
+__device__ __forceinline__ df32 df_log(df32 x)
+{
+    int k;
+    float mh = frexpf(x.hi, &k);  // x.hi = mh 2^k, mh in [0.5, 1)
+    if (mh < 0.70710678f) k -= 1;
+    const float sc = ldexpf(1.f, -k);
+    const df32 m(x.hi * sc, x.lo * sc);
+    const df32 one(1.f, 0.f);
+    const df32 u = (m - one) / (m + one);
+    const df32 w = u * u;
+    constexpr df32 c[12] = {df32(1.0),        df32(1.0 / 3.0),  df32(1.0 / 5.0),  df32(1.0 / 7.0),
+                            df32(1.0 / 9.0),  df32(1.0 / 11.0), df32(1.0 / 13.0), df32(1.0 / 15.0),
+                            df32(1.0 / 17.0), df32(1.0 / 19.0), df32(1.0 / 21.0), df32(1.0 / 23.0)};
+    df32 s = c[11];
+#pragma unroll
+    for (int j = 10; j >= 1; j--) s = c[j] + w * s;
+    const df32 at = u + u * (w * s);
+    constexpr df32 ln2(0.6931471805599453);
+    return ln2 * df32((float)k, 0.f) + (at + at);
+}
+
 }  // namespace combo

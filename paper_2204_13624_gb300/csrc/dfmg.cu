@@ -18,8 +18,8 @@
 // FMAs) and 2 x 576 B of S traffic per cell; on this part FP64 issues at a
 // small fraction of the FP32 rate, so both kernels are FP64-pipe bound.  The
 // double-float residual form (k_dfmg_pure_df, k_dfmg_gather_df) keeps only
-// the logarithm and the conversions on the FP64 pipe and stores S as (hi, lo)
-// float pairs of the same size.
+// the conversions on the FP64 pipe and stores S as (hi, lo) float pairs of
+// the same size.
 #include <cuda_runtime.h>
 
 #include "../../include/combo.h"
@@ -33,8 +33,8 @@ static int dfmg_grid(int64_t n)
     return (int)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
 }
 
-// Neo-Hookean P of F_sub in double-float: cofactors, J, 1/J and P in df32,
-// ln J in FP64 (one logarithm per sub-cell).  False if J <= 0.
+// Neo-Hookean P of F_sub in double-float: cofactors, J, 1/J, ln J (df_log)
+// and P in df32.  False if J <= 0.
 __device__ __forceinline__ bool nh_P_df(const df32 F[9], double mu, double lam, df32 P[9])
 {
     const df32 c0 = F[4] * F[8] - F[5] * F[7];
@@ -53,7 +53,8 @@ __device__ __forceinline__ bool nh_P_df(const df32 F[9], double mu, double lam, 
     G[6] = c2 * iJ;
     G[7] = (F[1] * F[6] - F[0] * F[7]) * iJ;
     G[8] = (F[0] * F[4] - F[1] * F[3]) * iJ;
-    const df32 k = df32(lam * log((double)J) - mu), mud = df32(mu);
+    const df32 mud = df32(mu);
+    const df32 k = df32(lam) * df_log(J) - mud;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll

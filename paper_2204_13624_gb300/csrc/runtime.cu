@@ -2331,6 +2331,36 @@ extern "C" int combo_apply_G(combo_ctx* ctx, const int32_t n[3], const double l[
     return fail(COMBO_E_INVALID_ARG, "bad precision");
 }
 
+__global__ void k_df_log(const double* x, double* y, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (double)df_log(df32(x[i]));
+}
+
+extern "C" int combo_df_log(combo_ctx* ctx, const double* x, double* y, int64_t n)
+{
+    if (!ctx || n < 0 || (n > 0 && (!x || !y))) return fail(COMBO_E_INVALID_ARG, "null argument");
+    for (int64_t i = 0; i < n; i++)
+        if (!(x[i] >= 1.1754944e-38 && x[i] <= 3.4e38)) return fail(COMBO_E_INVALID_ARG, "x outside the FP32 normal range");
+    if (n == 0) return COMBO_OK;
+    CK(cudaSetDevice(ctx->device));
+    double *dx = nullptr, *dy = nullptr;
+    CK(cudaMalloc(&dx, 8 * n));
+    CK(cudaMalloc(&dy, 8 * n));
+    int rc = COMBO_OK;
+    if (cudaMemcpyAsync(dx, x, 8 * n, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) rc = COMBO_E_CUDA;
+    if (!rc) {
+        k_df_log<<<(int)((n + 255) / 256), 256, 0, ctx->stream>>>(dx, dy, n);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(y, dy, 8 * n, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            rc = COMBO_E_CUDA;
+    }
+    cudaFree(dx);
+    cudaFree(dy);
+    return rc ? fail(rc, "combo_df_log: CUDA error") : COMBO_OK;
+}
+
 extern "C" int combo_constitutive(combo_ctx* ctx, const combo_problem* p, const combo_options* o_in, const double* F,
                                   double* a_io, double* P, int32_t mem)
 {

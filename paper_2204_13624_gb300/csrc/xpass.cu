@@ -123,9 +123,9 @@ __device__ __forceinline__ bool nh_stress(const double F[9], double mu, double l
     return true;
 }
 
-// The same stress with the cofactors, J, F^{-1} and P in double-float and
-// ln J in FP64 (one log per voxel); G and m, the tangent cache of the FP32
-// Krylov iterations, are rounded to FP32.  False if J <= 0.
+// The same stress with the cofactors, J, F^{-1}, ln J (df_log) and P in
+// double-float; G and m, the tangent cache of the FP32 Krylov iterations, are
+// rounded to FP32.  False if J <= 0.
 __device__ __forceinline__ bool nh_stress_df(const double Fd[9], double mu, double lam, df32 P[9], float G[9],
                                              float& m)
 {
@@ -148,15 +148,15 @@ __device__ __forceinline__ bool nh_stress_df(const double Fd[9], double mu, doub
     Gi[6] = c2 * iJ;
     Gi[7] = (F[1] * F[6] - F[0] * F[7]) * iJ;
     Gi[8] = (F[0] * F[4] - F[1] * F[3]) * iJ;
-    const double lnJ = log((double)J);
-    const df32 k = df32(lam * lnJ - mu), mud = df32(mu);
+    const df32 lnJ = df_log(J), mud = df32(mu);
+    const df32 k = df32(lam) * lnJ - mud;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) P[3 * i + j] = mud * F[3 * i + j] + k * Gi[3 * j + i];
 #pragma unroll
     for (int c = 0; c < 9; c++) G[c] = (float)Gi[c];
-    m = (float)(mu - lam * lnJ);
+    m = -(float)k;
     return true;
 }
 

@@ -109,3 +109,19 @@ def test_newton_rejected(cb):
 
     with pytest.raises(Exception):
         cb.solve(ms.homogeneous((8, 8, 8)), solver=1, kspace=DFMG)
+
+
+def test_double_float_log_accuracy(cb):
+    """The double-float logarithm of the double-float forms against the FP64
+    logarithm: absolute error <= 2^-46 max(1, |ln x|) over [1e-3, 1e3], where
+    the inputs are first rounded to double-float (48-bit significand)."""
+    rng = np.random.default_rng(9)
+    x = np.concatenate([np.exp(rng.uniform(np.log(1e-3), np.log(1e3), 20000)),
+                        1.0 + rng.uniform(-1e-3, 1e-3, 5000), [1.0, 2.0, 0.5, np.sqrt(2.0), 1 / np.sqrt(2.0)]])
+    hi = x.astype(np.float32).astype(np.float64)
+    xd = hi + (x - hi).astype(np.float32).astype(np.float64)  # the double-float value the kernel sees
+    y = cb.df_log(x)
+    ref = np.log(xd)
+    err = np.abs(y - ref) / np.maximum(1.0, np.abs(ref))
+    assert err.max() < 2.0 ** -46, err.max()
+    assert y[-5] == 0.0
