@@ -8,8 +8,10 @@ The oracle is plain C (``combo_oracle.c``) compiled with gcc and reached
 through ctypes.  It shares no code with the CUDA library.  See the C file's
 header for what each function computes and which part of the paper it
 follows (Sec. 3 Lippmann-Schwinger / Green operator, Sec. 4 laminate
-Algorithms 1 and 2, Sec. 6.1 Neo-Hookean material, App. A staggered grid).  ``normals.py`` (plain
-numpy) is the oracle of the coarse-graining with the Sec. 5 normal detection.
+Algorithms 1 and 2, Sec. 6.1 Neo-Hookean material, App. A staggered grid and
+doubly-fine material grid, the appendix cheat sheet's infinitesimal-strain
+column).  ``normals.py`` (plain numpy) is the oracle of the coarse-graining
+with the Sec. 5 normal detection.
 
 Parity pins: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, invariants, brute force and the paper's printed facts.
