@@ -25,7 +25,7 @@ def cb():
     return combo
 
 
-@pytest.mark.parametrize("n", [(12, 9, 18), (16, 16, 16), (64, 32, 8), (8, 64, 6), (64, 48, 96)])
+@pytest.mark.parametrize("n", [(12, 9, 18), (16, 16, 16), (64, 32, 8), (8, 64, 6), (64, 48, 96), (2, 2, 2), (2, 4, 6)])
 def test_law_parity(cb, orc, n):
     from paper_2204_13624_gb300 import microstructure as ms
 
@@ -36,7 +36,8 @@ def test_law_parity(cb, orc, n):
     Pg, ag = cb.constitutive(p, F, kspace=DFMG)
     Po, ao = orc.constitutive_field(p, F, opts=dict(kspace=DFMG))
     assert rel(Pg, Po) < 1e-12
-    assert rel(ag, ao) < 1e-9
+    if len(ao):
+        assert rel(ag, ao) < 1e-9
     # the plain law differs: the gather is not the identity
     P2, _ = cb.constitutive(p, F, kspace=2)
     assert rel(P2, Po) > 1e-3
