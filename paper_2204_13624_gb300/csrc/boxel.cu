@@ -126,7 +126,7 @@ __device__ __forceinline__ bool inv3(const double A[9], double B[9])
 
 // ---- double-float form of the laminate solve (refined precision form with
 // double-float residuals): the phase states F, F^{-1}, J and P and the
-// traction residual f in df32, ln J in FP64, the Hessian and its inverse in
+// traction residual f in df32, ln J in df32 (df_log, kept as FP64), the Hessian and its inverse in
 // FP32 (a Newton direction needs no more), the jump a and the back-projection
 // in FP64.  These iterations stop at the rounding level of the df32 residual;
 // the FP64 residual then decides convergence.
