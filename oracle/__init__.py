@@ -79,6 +79,8 @@ def lib():
         L.orc_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_solve.restype = C.c_int
         L.orc_constitutive_field.argtypes = [C.c_void_p, C.c_void_p, dp, dp, dp, dp]
+        L.orc_dfmg_tangent_apply.argtypes = [C.c_void_p, C.c_void_p, dp, dp, dp]
+        L.orc_dfmg_tangent_apply.restype = C.c_int
         L.orc_constitutive_field.restype = C.c_int
         L.orc_num_threads.restype = C.c_int
         _lib = L
@@ -343,6 +345,21 @@ def dfmg_subcell_F(F, n, l):
         shift[npax[b_]] = -l[b_]
         out[comp] = np.roll(G[comp], shift, axis=(0, 1, 2))
     return out.reshape(9, -1)
+
+
+def dfmg_tangent_apply(prob, F, X, opts=None):
+    """The tangent of the doubly-fine material grid law at F applied to X
+    ([9][V] each): the Hessian of the sub-cell energy acting on X."""
+    keep = []
+    ps, V = _problem_struct(prob, keep)
+    os_ = _options_struct(dict(opts or {}, kspace=STAGGERED_DFMG))
+    F = _f64(F).reshape(9, V)
+    X = _f64(X).reshape(9, V)
+    Y = np.zeros((9, V))
+    rc = lib().orc_dfmg_tangent_apply(C.byref(ps), C.byref(os_), _d(F), _d(X), _d(Y))
+    if rc:
+        raise RuntimeError(f"oracle doubly-fine tangent failed: {STATUS.get(rc, rc)}")
+    return Y
 
 
 def phase_averages(prob, F, a, c_min=1e-6, kspace=None, theory=0):

@@ -757,8 +757,8 @@ typedef struct {
 
 /* Material law of cell v at Fs (pure Neo-Hookean, or the laminate of a boxel
  * cell from the warm start a_ws, updated). */
-static int cell_law(orc_ctx* cx, long v, const double Fs[9], double a_ws[3], double P[9], int64_t* its_o,
-                    int64_t* nbp_o)
+static int cell_law(orc_ctx* cx, long v, const double Fs[9], double a_ws[3], double P[9], double* A,
+                    int64_t* its_o, int64_t* nbp_o)
 {
     const orc_problem* pb = cx->pb;
     int b = cx->vox2box[v];
@@ -773,15 +773,67 @@ static int cell_law(orc_ctx* cx, long v, const double Fs[9], double a_ws[3], dou
         double mat[4] = {pb->mu[0], pb->lam[0], pb->mu[1], pb->lam[1]};
         int its = 0, nbpv = 0;
         int rc = orc_laminate(Fs, pb->bN + 3 * (size_t)b, cpl, mat, a_ws, cx->op->nr_tol_rel, cx->op->nr_tol_abs,
-                              cx->op->nr_max_iter, P, NULL, &its, &nbpv, NULL);
+                              cx->op->nr_max_iter, P, A, &its, &nbpv, NULL);
         *its_o += its;
         *nbp_o += nbpv;
         return rc;
     }
-    return orc_neohooke(Fs, pb->mu[ph], pb->lam[ph], P, NULL);
+    return orc_neohooke(Fs, pb->mu[ph], pb->lam[ph], P, A);
 }
 
 static long wrapi(long i, long n) { return ((i % n) + n) % n; }
+
+/* F_sub(c, l) of the field X [9][V] at cell v (see constitutive_dfmg). */
+static void dfmg_assemble(const orc_problem* pb, const double* X, long v, int l, double out[9])
+{
+    const long n1 = pb->n[0], n2 = pb->n[1], n3 = pb->n[2];
+    const size_t V = (size_t)n1 * n2 * n3;
+    const long i = v % n1, j = (v / n1) % n2, k = v / (n1 * n2);
+    const long l1 = l & 1, l2 = (l >> 1) & 1, l3 = (l >> 2) & 1;
+    const long v12 = wrapi(i + l1, n1) + n1 * (wrapi(j + l2, n2) + n2 * k);
+    const long v13 = wrapi(i + l1, n1) + n1 * (j + n2 * wrapi(k + l3, n3));
+    const long v23 = i + n1 * (wrapi(j + l2, n2) + n2 * wrapi(k + l3, n3));
+    out[0] = X[0 * V + v];
+    out[4] = X[4 * V + v];
+    out[8] = X[8 * V + v];
+    out[1] = X[1 * V + v12];
+    out[3] = X[3 * V + v12];
+    out[2] = X[2 * V + v13];
+    out[6] = X[6 * V + v13];
+    out[5] = X[5 * V + v23];
+    out[7] = X[7 * V + v23];
+}
+
+/* The gather of the sub-cell values S [V][8][9] into Y [9][V] (see
+ * constitutive_dfmg): diagonal from the cell's own sub-cells, off-diagonal
+ * (a, b) of sub-cell l from the cell xi - l_a e_a - l_b e_b. */
+static void dfmg_gather(const orc_problem* pb, const double* S, double* Y)
+{
+    const long n1 = pb->n[0], n2 = pb->n[1], n3 = pb->n[2];
+    const size_t V = (size_t)n1 * n2 * n3;
+#pragma omp parallel for schedule(static)
+    for (long v = 0; v < (long)V; v++) {
+        const long i = v % n1, j = (v / n1) % n2, k = v / (n1 * n2);
+        double out[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int l = 0; l < 8; l++) {
+            const long l1 = l & 1, l2 = (l >> 1) & 1, l3 = (l >> 2) & 1;
+            const double* Sv = S + 72 * (size_t)v + 9 * l;
+            out[0] += Sv[0];
+            out[4] += Sv[4];
+            out[8] += Sv[8];
+            const long c12 = wrapi(i - l1, n1) + n1 * (wrapi(j - l2, n2) + n2 * k);
+            const long c13 = wrapi(i - l1, n1) + n1 * (j + n2 * wrapi(k - l3, n3));
+            const long c23 = i + n1 * (wrapi(j - l2, n2) + n2 * wrapi(k - l3, n3));
+            out[1] += S[72 * (size_t)c12 + 9 * l + 1];
+            out[3] += S[72 * (size_t)c12 + 9 * l + 3];
+            out[2] += S[72 * (size_t)c13 + 9 * l + 2];
+            out[6] += S[72 * (size_t)c13 + 9 * l + 6];
+            out[5] += S[72 * (size_t)c23 + 9 * l + 5];
+            out[7] += S[72 * (size_t)c23 + 9 * l + 7];
+        }
+        for (int c = 0; c < 9; c++) Y[(size_t)c * V + v] = 0.125 * out[c];
+    }
+}
 
 /*
  * Doubly-fine material grid (App. A, Eq. constitutive_law): every cell is cut
@@ -800,37 +852,25 @@ static long wrapi(long i, long n) { return ((i % n) + n) % n; }
  * Each sub-cell's law is evaluated once (S below) and gathered per the
  * equation; boxel cells keep one jump-vector warm start per sub-cell.
  */
-static int constitutive_dfmg(orc_ctx* cx, const double* F, double* P, int64_t* nr_it, int64_t* nbp, int64_t* nevals)
+static int constitutive_dfmg(orc_ctx* cx, const double* F, double* P, double* A8, int64_t* nr_it, int64_t* nbp,
+                             int64_t* nevals)
 {
     const orc_problem* pb = cx->pb;
-    const long n1 = pb->n[0], n2 = pb->n[1], n3 = pb->n[2];
-    size_t V = (size_t)n1 * n2 * n3;
+    size_t V = (size_t)pb->n[0] * pb->n[1] * pb->n[2];
     double* S = (double*)malloc(sizeof(double) * 72 * V); /* [V][8][9] */
     int status = ORC_OK;
     int64_t it_sum = 0, bp_sum = 0, ev_sum = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : it_sum, bp_sum, ev_sum)
     for (long v = 0; v < (long)V; v++) {
-        const long i = v % n1, j = (v / n1) % n2, k = v / (n1 * n2);
         const int b = cx->vox2box[v];
         for (int l = 0; l < 8; l++) {
-            const long l1 = l & 1, l2 = (l >> 1) & 1, l3 = (l >> 2) & 1;
-            const long v12 = wrapi(i + l1, n1) + n1 * (wrapi(j + l2, n2) + n2 * k);
-            const long v13 = wrapi(i + l1, n1) + n1 * (j + n2 * wrapi(k + l3, n3));
-            const long v23 = i + n1 * (wrapi(j + l2, n2) + n2 * wrapi(k + l3, n3));
             double Fs[9];
-            Fs[0] = F[0 * V + v];
-            Fs[4] = F[4 * V + v];
-            Fs[8] = F[8 * V + v];
-            Fs[1] = F[1 * V + v12];
-            Fs[3] = F[3 * V + v12];
-            Fs[2] = F[2 * V + v13];
-            Fs[6] = F[6 * V + v13];
-            Fs[5] = F[5 * V + v23];
-            Fs[7] = F[7 * V + v23];
+            dfmg_assemble(pb, F, v, l, Fs);
             double aw[3] = {0.0, 0.0, 0.0};
             if (b >= 0) memcpy(aw, cx->a8 + 24 * (size_t)b + 3 * l, sizeof(aw));
             int64_t its = 0, nbpv = 0;
-            int rc = cell_law(cx, v, Fs, aw, S + 72 * (size_t)v + 9 * l, &its, &nbpv);
+            int rc = cell_law(cx, v, Fs, aw, S + 72 * (size_t)v + 9 * l, A8 ? A8 + 81 * (8 * (size_t)v + l) : NULL,
+                              &its, &nbpv);
             if (b >= 0) {
                 memcpy(cx->a8 + 24 * (size_t)b + 3 * l, aw, sizeof(aw));
                 ev_sum += 1;
@@ -845,30 +885,7 @@ static int constitutive_dfmg(orc_ctx* cx, const double* F, double* P, int64_t* n
             }
         }
     }
-    if (status == ORC_OK) {
-#pragma omp parallel for schedule(static)
-        for (long v = 0; v < (long)V; v++) {
-            const long i = v % n1, j = (v / n1) % n2, k = v / (n1 * n2);
-            double out[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-            for (int l = 0; l < 8; l++) {
-                const long l1 = l & 1, l2 = (l >> 1) & 1, l3 = (l >> 2) & 1;
-                const double* Sv = S + 72 * (size_t)v + 9 * l;
-                out[0] += Sv[0];
-                out[4] += Sv[4];
-                out[8] += Sv[8];
-                const long c12 = wrapi(i - l1, n1) + n1 * (wrapi(j - l2, n2) + n2 * k);
-                const long c13 = wrapi(i - l1, n1) + n1 * (j + n2 * wrapi(k - l3, n3));
-                const long c23 = i + n1 * (wrapi(j - l2, n2) + n2 * wrapi(k - l3, n3));
-                out[1] += S[72 * (size_t)c12 + 9 * l + 1];
-                out[3] += S[72 * (size_t)c12 + 9 * l + 3];
-                out[2] += S[72 * (size_t)c13 + 9 * l + 2];
-                out[6] += S[72 * (size_t)c13 + 9 * l + 6];
-                out[5] += S[72 * (size_t)c23 + 9 * l + 5];
-                out[7] += S[72 * (size_t)c23 + 9 * l + 7];
-            }
-            for (int c = 0; c < 9; c++) P[(size_t)c * V + v] = 0.125 * out[c];
-        }
-    }
+    if (status == ORC_OK) dfmg_gather(pb, S, P);
     free(S);
     if (nr_it) *nr_it += it_sum;
     if (nbp) *nbp += bp_sum;
@@ -876,6 +893,30 @@ static int constitutive_dfmg(orc_ctx* cx, const double* F, double* P, int64_t* n
     return status;
 }
 
+/* Tangent of the doubly-fine law applied to a field X [9][V]: with the
+ * sub-cell tangents A8 [V][8][81] of the last law evaluation, Y = the gather
+ * of A_sub(c, l) : X_sub(c, l), X_sub assembled like F_sub.  It is the
+ * Hessian of the sub-cell energy, hence symmetric (pinned). */
+static void dfmg_tangent_apply(const orc_problem* pb, const double* A8, const double* X, double* Y)
+{
+    size_t V = (size_t)pb->n[0] * pb->n[1] * pb->n[2];
+    double* S = (double*)malloc(sizeof(double) * 72 * V);
+#pragma omp parallel for schedule(static)
+    for (long v = 0; v < (long)V; v++) {
+        for (int l = 0; l < 8; l++) {
+            double xs[9];
+            dfmg_assemble(pb, X, v, l, xs);
+            const double* Al = A8 + 81 * (8 * (size_t)v + l);
+            for (int r = 0; r < 9; r++) {
+                double t = 0.0;
+                for (int c = 0; c < 9; c++) t += Al[9 * r + c] * xs[c];
+                S[72 * (size_t)v + 9 * l + r] = t;
+            }
+        }
+    }
+    dfmg_gather(pb, S, Y);
+    free(S);
+}
 /* Reported jump vector of a boxel under the doubly-fine material grid: the
  * mean of its 8 sub-cell jumps (the sub-cell jumps themselves are internal
  * warm-start state). */
@@ -894,10 +935,8 @@ static int constitutive(orc_ctx* cx, const double* F, double* P, double* A, int6
                         int64_t* nevals)
 {
     const orc_problem* pb = cx->pb;
-    if (cx->op->kspace == ORC_STAGGERED_DFMG) {
-        if (A) return ORC_E_INVALID; /* no tangent of the doubly-fine material grid */
-        return constitutive_dfmg(cx, F, P, nr_it, nbp, nevals);
-    }
+    if (cx->op->kspace == ORC_STAGGERED_DFMG) /* A, if given, receives the sub-cell tangents [V][8][81] */
+        return constitutive_dfmg(cx, F, P, A, nr_it, nbp, nevals);
     size_t V = (size_t)pb->n[0] * pb->n[1] * pb->n[2];
     int status = ORC_OK;
     int64_t it_sum = 0, bp_sum = 0, ev_sum = 0;
@@ -953,6 +992,7 @@ static int constitutive(orc_ctx* cx, const double* F, double* P, double* A, int6
 int orc_constitutive_field(const orc_problem* pb, const orc_options* op, const double* F, double* a_io, double* P,
                            double* A)
 {
+    if (A && op->kspace == ORC_STAGGERED_DFMG) return ORC_E_INVALID; /* no per-voxel tangent: orc_dfmg_tangent_apply */
     size_t V = (size_t)pb->n[0] * pb->n[1] * pb->n[2];
     orc_ctx cx = {pb, op, (int32_t*)malloc(sizeof(int32_t) * V), a_io,
                   (double*)calloc(24 * (size_t)(pb->nb > 0 ? pb->nb : 1), sizeof(double))};
@@ -960,6 +1000,26 @@ int orc_constitutive_field(const orc_problem* pb, const orc_options* op, const d
     for (int64_t b = 0; b < pb->nb; b++) cx.vox2box[pb->bidx[b]] = (int32_t)b;
     int rc = constitutive(&cx, F, P, A, NULL, NULL, NULL);
     if (op->kspace == ORC_STAGGERED_DFMG) dfmg_mean_jumps(cx.a8, pb->nb, a_io);
+    free(cx.vox2box);
+    free(cx.a8);
+    return rc;
+}
+
+/* The tangent of the doubly-fine law at F applied to X: Y = dP/dF [X]
+ * (test entry of dfmg_tangent_apply; boxel sub-cells start from a = 0). */
+int orc_dfmg_tangent_apply(const orc_problem* pb, const orc_options* op, const double* F, const double* X, double* Y)
+{
+    size_t V = (size_t)pb->n[0] * pb->n[1] * pb->n[2];
+    orc_ctx cx = {pb, op, (int32_t*)malloc(sizeof(int32_t) * V), NULL,
+                  (double*)calloc(24 * (size_t)(pb->nb > 0 ? pb->nb : 1), sizeof(double))};
+    for (size_t v = 0; v < V; v++) cx.vox2box[v] = -1;
+    for (int64_t b = 0; b < pb->nb; b++) cx.vox2box[pb->bidx[b]] = (int32_t)b;
+    double* A8 = (double*)malloc(sizeof(double) * 648 * V);
+    double* P = (double*)malloc(sizeof(double) * 9 * V);
+    int rc = constitutive_dfmg(&cx, F, P, A8, NULL, NULL, NULL);
+    if (rc == ORC_OK) dfmg_tangent_apply(pb, A8, X, Y);
+    free(P);
+    free(A8);
     free(cx.vox2box);
     free(cx.a8);
     return rc;
@@ -1052,7 +1112,7 @@ int orc_solve(const orc_problem* pb, const orc_options* op, orc_result* res)
     for (int64_t b = 0; b < pb->nb; b++) cx.vox2box[pb->bidx[b]] = (int32_t)b;
     cx.a = (double*)calloc(3 * (size_t)(pb->nb > 0 ? pb->nb : 1), sizeof(double));
     cx.a8 = (double*)calloc(24 * (size_t)(pb->nb > 0 ? pb->nb : 1), sizeof(double));
-    if (op->kspace == ORC_STAGGERED_DFMG && (op->solver == 1 || op->theory == 1)) {
+    if (op->kspace == ORC_STAGGERED_DFMG && op->theory == 1) {
         free(cx.vox2box);
         free(cx.a);
         free(cx.a8);
@@ -1066,7 +1126,8 @@ int orc_solve(const orc_problem* pb, const orc_options* op, orc_result* res)
     double *x = NULL, *r = NULL, *p = NULL, *q = NULL, *t = NULL, *dir = NULL;
     if (op->solver == 2) dir = (double*)calloc(N9, sizeof(double));
     if (op->solver == 1) {
-        A = (double*)malloc(sizeof(double) * 81 * V);
+        /* (the doubly-fine grid keeps one tangent per sub-cell) */
+        A = (double*)malloc(sizeof(double) * 81 * V * (op->kspace == ORC_STAGGERED_DFMG ? 8 : 1));
         x = (double*)malloc(sizeof(double) * N9);
         r = (double*)malloc(sizeof(double) * N9);
         p = (double*)malloc(sizeof(double) * N9);
@@ -1142,7 +1203,10 @@ int orc_solve(const orc_problem* pb, const orc_options* op, orc_result* res)
                     } else if (sqrt(rr) <= op->cg_tol * sqrt(rr0) || j >= op->cg_max_iter)
                         break;
                     if (rr == 0.0) break;
-                    tangent_apply(A, p, t, V);
+                    if (op->kspace == ORC_STAGGERED_DFMG)
+                        dfmg_tangent_apply(pb, A, p, t);
+                    else
+                        tangent_apply(A, p, t, V);
                     apply_G(op->kspace, n, pb->l, t, q);
                     res->n_operator += 1;
                     double pq = dot(p, q, N9);

@@ -19,7 +19,10 @@ converged laminate jump of a composite boxel (Sec. 4.1).
   over staggered displacements: a displacement-based Newton (finite-difference
   Hessian of the oracle's own, pinned gradient) on a 4^3 grid must reach the
   F the FFT solve reaches;
-* Hill-Mandel holds at convergence, and fixed point and nonlinear CG agree.
+* Hill-Mandel holds at convergence, and fixed point and nonlinear CG agree;
+* the tangent (the sub-cell tangents applied to the assembled direction and
+  gathered) is the derivative of the law and symmetric, and Newton-CG with it
+  reaches the nonlinear-CG state.
 """
 import numpy as np
 import pytest
@@ -166,9 +169,37 @@ def test_fixed_point_and_ncg_agree_hill_mandel(orc):
     assert 1e-6 < d < 5e-2 * np.abs(r2["Pbar"][-1]).max()
 
 
-def test_newton_is_rejected(orc):
+def test_tangent_is_the_derivative_of_the_law(orc):
+    """The doubly-fine tangent (the gather of the sub-cell tangents applied to
+    the assembled direction) equals central differences of the pinned law,
+    and it is symmetric (the Hessian of the sub-cell energy)."""
+    p = ms.random_boxels((5, 4, 6), seed=45, boxel_frac=0.3, incl_frac=0.3, contrast=10.0)
+    V = 120
+    rng = np.random.default_rng(6)
+    F = np.eye(3).reshape(9, 1) + 0.08 * rng.uniform(-1, 1, (9, V))
+    X1, X2 = rng.normal(size=(9, V)), rng.normal(size=(9, V))
+    T1 = orc.dfmg_tangent_apply(p, F, X1)
+    T2 = orc.dfmg_tangent_apply(p, F, X2)
+    h = 1e-5
+    Pp, _ = orc.constitutive_field(p, F + h * X1, opts=dict(kspace=DFMG))
+    Pm, _ = orc.constitutive_field(p, F - h * X1, opts=dict(kspace=DFMG))
+    fd = (Pp - Pm) / (2 * h)
+    assert np.abs(fd - T1).max() < 1e-6 * np.abs(T1).max()
+    assert abs(np.sum(X2 * T1) - np.sum(X1 * T2)) < 1e-10 * np.sqrt(np.sum(X1 * T1) * np.sum(X2 * T2))
+
+
+def test_newton_reaches_the_nonlinear_cg_state(orc):
+    p = ms.centred_sphere((12, 12, 12), 0.2, 10.0, np.diag([1.04, 1.0, 0.99]) + 0.02 * np.eye(3)[[1, 0, 2]], 2)
+    rn = orc.solve(p, dict(solver=1, kspace=DFMG, tol=1e-11, cg_tol=1e-6))
+    r2 = orc.solve(p, dict(solver=2, kspace=DFMG, tol=1e-11, max_iter=5000))
+    assert np.allclose(rn["F"], r2["F"], atol=1e-8)
+    assert np.allclose(rn["Pbar"], r2["Pbar"], atol=1e-10)
+    assert rn["iters"].max() <= 8
+
+
+def test_infinitesimal_strain_is_rejected(orc):
     p = ms.homogeneous((4, 4, 4))
-    r = orc.solve(p, dict(solver=1, kspace=DFMG), raise_on_error=False)
+    r = orc.solve(p, dict(solver=2, kspace=DFMG, theory=1), raise_on_error=False)
     assert r["status"] != 0
 
 
