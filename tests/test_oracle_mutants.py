@@ -1,0 +1,79 @@
+"""Planted mistakes: a copy of the oracle with one plausible error must fail
+the pin written for that part, so that the pins are known to bite.
+
+Each case copies ``oracle/`` to a temporary directory, plants one mistake in
+the C source by a textual substitution (the substituted text must occur
+exactly once), builds the copy and runs the pin's check on it in a separate
+interpreter; the check prints the pin's error measure, which must be far above
+its tolerance (and the unmodified oracle passes the same pin in
+``test_oracle_dfmg.py`` / ``test_oracle_small_strain.py``).
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# the doubly-fine gather with the material taken at xi + l (the printed sign)
+# instead of xi - l: the uniform-deformation pin (mean of the four cells that
+# share the edge, on the minus side) must fail
+GATHER = ("const long c12 = wrapi(i - l1, n1) + n1 * (wrapi(j - l2, n2) + n2 * k);",
+          "const long c12 = wrapi(i + l1, n1) + n1 * (wrapi(j + l2, n2) + n2 * k);")
+CHECK_GATHER = r"""
+import numpy as np, oracle as orc
+from paper_2204_13624_gb300 import microstructure as ms
+p = ms.random_boxels((6, 5, 4), seed=42, boxel_frac=0.3, incl_frac=0.3, contrast=10.0)
+n = p["n"]; V = n[0] * n[1] * n[2]
+F = np.tile((np.eye(3) + 0.05 * np.arange(9).reshape(3, 3) / 9).reshape(9, 1), (1, V))
+P3, _ = orc.constitutive_field(p, F, opts=dict(kspace=3))
+P0, _ = orc.constitutive_field(p, F)
+G = P0[1].reshape(n[2], n[1], n[0])
+m = sum(np.roll(G, (0, lb, la), axis=(0, 1, 2)) for la in (0, 1) for lb in (0, 1)) / 4
+print(np.abs(P3[1] - m.ravel()).max())
+"""
+
+# the small-strain jump with the wrong sign of the stiffness difference: the
+# traction-balance pin must fail
+JUMP = ("t += (Cm[9 * (3 * i + J) + q] - Cp[9 * (3 * i + J) + q]) * eps[q] * N[J];",
+        "t += (Cp[9 * (3 * i + J) + q] - Cm[9 * (3 * i + J) + q]) * eps[q] * N[J];")
+CHECK_JUMP = r"""
+import numpy as np, oracle as orc
+rng = np.random.default_rng(3)
+N = rng.normal(size=3); N /= np.linalg.norm(N)
+c = 0.4; H = rng.uniform(-1, 1, 9); mat = (1.0, 2.0, 7.0, 4.0)
+out = orc.laminate_linear(np.eye(3).ravel() + H, N, c, mat)
+a = out["a"]
+eps = 0.5 * (H.reshape(3, 3) + H.reshape(3, 3).T)
+san = 0.5 * (np.outer(a, N) + np.outer(N, a))
+sig = lambda e, mu, lam: lam * np.trace(e) * np.eye(3) + 2 * mu * e
+sp = sig(eps + san / c, 7.0, 4.0); sm = sig(eps - san / (1 - c), 1.0, 2.0)
+print(np.abs((sp - sm) @ N).max() / np.abs(sp).max())
+"""
+
+
+def _mutant_run(tmp_path, old, new, check):
+    tmp_path.mkdir()
+    dst = tmp_path / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), dst,
+                    ignore=shutil.ignore_patterns("*.so", "*.tmp", "__pycache__"))
+    src = (dst / "combo_oracle.c").read_text()
+    assert src.count(old) == 1, "the planted text must occur exactly once"
+    (dst / "combo_oracle.c").write_text(src.replace(old, new))
+    env = dict(os.environ, PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT]))
+    out = subprocess.run([sys.executable, "-c", check], env=env, cwd=str(tmp_path), capture_output=True,
+                         text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    return float(out.stdout.strip().splitlines()[-1])
+
+
+@pytest.mark.parametrize("case", ["gather", "jump"])
+def test_planted_mistake_fails_its_pin(tmp_path, case):
+    old, new, check, tol = {"gather": (GATHER[0], GATHER[1], CHECK_GATHER, 1e-12),
+                            "jump": (JUMP[0], JUMP[1], CHECK_JUMP, 1e-13)}[case]
+    ctrl = _mutant_run(tmp_path / "control", old, old, check)  # the unmodified oracle passes
+    err = _mutant_run(tmp_path / "mutant", old, new, check)
+    assert ctrl < tol, (case, ctrl)
+    assert err > 1e3 * tol, (case, err)
