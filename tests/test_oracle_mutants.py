@@ -54,6 +54,36 @@ print(np.abs((sp - sm) @ N).max() / np.abs(sp).max())
 """
 
 
+# the Neo-Hookean stress with F^{-1} where F^{-T} belongs: the pin P = dW/dF
+# (central differences of the paper's energy) must fail
+NH = ("P[3 * i + Jx] = mu * F[3 * i + Jx] + (lam * lnJ - mu) * G[3 * Jx + i];",
+      "P[3 * i + Jx] = mu * F[3 * i + Jx] + (lam * lnJ - mu) * G[3 * i + Jx];")
+CHECK_NH = r"""
+import numpy as np, oracle as orc
+rng = np.random.default_rng(4)
+F = (np.eye(3) + 0.2 * rng.uniform(-1, 1, (3, 3))).ravel()
+P = orc.neohooke(F, 1.3, 2.1, tangent=False)
+h = 1e-6
+fd = np.array([(orc.neohooke_energy(F + h * e, 1.3, 2.1) - orc.neohooke_energy(F - h * e, 1.3, 2.1)) / (2 * h)
+               for e in np.eye(9)])
+print(np.abs(fd - P).max() / np.abs(P).max())
+"""
+
+# the staggered symbol with forward differences off the diagonal too: the
+# pin that G leaves the printed staggered gradient unchanged must fail
+STAG = ("for (int a = 0; a < 3; a++) kr[a][B] = (a == B) ? fwd : bwd;",
+        "for (int a = 0; a < 3; a++) kr[a][B] = fwd;")
+CHECK_STAG = r"""
+import numpy as np, oracle as orc
+from test_oracle_fft_gamma import staggered_gradient
+n, l = (6, 4, 8), (1.0, 0.8, 1.3)
+U = np.random.default_rng(11).normal(size=(3, n[2], n[1], n[0]))
+X = staggered_gradient(U, [l[j] / n[j] for j in range(3)])
+Y, _ = orc.apply_G(X, n, l, orc.STAGGERED)
+print(np.abs(Y - X).max() / np.abs(X).max())
+"""
+
+
 def _mutant_run(tmp_path, old, new, check):
     tmp_path.mkdir()
     dst = tmp_path / "oracle"
@@ -62,17 +92,19 @@ def _mutant_run(tmp_path, old, new, check):
     src = (dst / "combo_oracle.c").read_text()
     assert src.count(old) == 1, "the planted text must occur exactly once"
     (dst / "combo_oracle.c").write_text(src.replace(old, new))
-    env = dict(os.environ, PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT]))
+    env = dict(os.environ, PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT, os.path.join(ROOT, "tests")]))
     out = subprocess.run([sys.executable, "-c", check], env=env, cwd=str(tmp_path), capture_output=True,
                          text=True, timeout=300)
     assert out.returncode == 0, out.stderr
     return float(out.stdout.strip().splitlines()[-1])
 
 
-@pytest.mark.parametrize("case", ["gather", "jump"])
+@pytest.mark.parametrize("case", ["gather", "jump", "neohooke", "staggered"])
 def test_planted_mistake_fails_its_pin(tmp_path, case):
     old, new, check, tol = {"gather": (GATHER[0], GATHER[1], CHECK_GATHER, 1e-12),
-                            "jump": (JUMP[0], JUMP[1], CHECK_JUMP, 1e-13)}[case]
+                            "jump": (JUMP[0], JUMP[1], CHECK_JUMP, 1e-13),
+                            "neohooke": (NH[0], NH[1], CHECK_NH, 1e-8),
+                            "staggered": (STAG[0], STAG[1], CHECK_STAG, 1e-12)}[case]
     ctrl = _mutant_run(tmp_path / "control", old, old, check)  # the unmodified oracle passes
     err = _mutant_run(tmp_path / "mutant", old, new, check)
     assert ctrl < tol, (case, ctrl)
