@@ -84,6 +84,35 @@ print(np.abs(Y - X).max() / np.abs(X).max())
 """
 
 
+# the laminate with the D matrix of the printed form (diag(N) in every block of
+# rows: a -> N (x) a instead of a (x) N).  The residual f = (P+ - P-) N is
+# formed without D, so Newton still finds the traction-balanced jump (with a
+# wrong Hessian); the boxel tangent A_box = dP_box/dF_box (Eq. Peff:Seff, the
+# pin by central differences) must fail
+DMAT = ("D[(3 * i + Jx) * 3 + k] = (i == k) ? N[Jx] : 0.0;",
+        "D[(3 * i + Jx) * 3 + k] = (Jx == k) ? N[i] : 0.0;")
+CHECK_DMAT = r"""
+import numpy as np, oracle as orc
+rng = np.random.default_rng(5)
+mat = (1.0, 2.0, 10.0, 20.0)
+worst = 0.0
+for _ in range(3):
+    N = rng.normal(size=3); N /= np.linalg.norm(N)
+    c = rng.uniform(0.2, 0.8)
+    F = (np.eye(3) + 0.1 * rng.uniform(-1, 1, (3, 3))).ravel()
+    try:
+        A = orc.laminate(F, N, c, mat)["A"]
+        h = 1e-6
+        fd = np.array([(orc.laminate(F + h * e, N, c, mat)["P"] - orc.laminate(F - h * e, N, c, mat)["P"]) / (2 * h)
+                       for e in np.eye(9)]).T
+    except Exception:
+        worst = 1e300
+        continue
+    worst = max(worst, np.abs(fd - A).max() / np.abs(A).max())
+print(worst)
+"""
+
+
 def _mutant_run(tmp_path, old, new, check):
     tmp_path.mkdir()
     dst = tmp_path / "oracle"
@@ -99,12 +128,13 @@ def _mutant_run(tmp_path, old, new, check):
     return float(out.stdout.strip().splitlines()[-1])
 
 
-@pytest.mark.parametrize("case", ["gather", "jump", "neohooke", "staggered"])
+@pytest.mark.parametrize("case", ["gather", "jump", "neohooke", "staggered", "dmatrix"])
 def test_planted_mistake_fails_its_pin(tmp_path, case):
     old, new, check, tol = {"gather": (GATHER[0], GATHER[1], CHECK_GATHER, 1e-12),
                             "jump": (JUMP[0], JUMP[1], CHECK_JUMP, 1e-13),
                             "neohooke": (NH[0], NH[1], CHECK_NH, 1e-8),
-                            "staggered": (STAG[0], STAG[1], CHECK_STAG, 1e-12)}[case]
+                            "staggered": (STAG[0], STAG[1], CHECK_STAG, 1e-12),
+                            "dmatrix": (DMAT[0], DMAT[1], CHECK_DMAT, 1e-6)}[case]
     ctrl = _mutant_run(tmp_path / "control", old, old, check)  # the unmodified oracle passes
     err = _mutant_run(tmp_path / "mutant", old, new, check)
     assert ctrl < tol, (case, ctrl)
