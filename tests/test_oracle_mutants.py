@@ -84,6 +84,21 @@ print(np.abs(Y - X).max() / np.abs(X).max())
 """
 
 
+# the rotated symbol without the cosine factors of the other axes (a plain
+# central-difference symbol): the pin that G leaves the HEX8R gradient of
+# random nodal displacements unchanged must fail
+ROT = ("if (m != j) prod *= c[m];", "if (m != j) prod *= 1.0;")
+CHECK_ROT = r"""
+import numpy as np, oracle as orc
+from test_oracle_fft_gamma import hex8r_gradient
+n, l = (6, 4, 8), (1.0, 0.5, 2.0)
+U = np.random.default_rng(7).normal(size=(3, n[2], n[1], n[0]))
+X = hex8r_gradient(U, [l[j] / n[j] for j in range(3)])
+Y, _ = orc.apply_G(X, n, l, orc.ROTATED)
+print(np.abs(Y - X).max() / np.abs(X).max())
+"""
+
+
 # the laminate with the D matrix of the printed form (diag(N) in every block of
 # rows: a -> N (x) a instead of a (x) N).  The residual f = (P+ - P-) N is
 # formed without D, so Newton still finds the traction-balanced jump (with a
@@ -128,12 +143,13 @@ def _mutant_run(tmp_path, old, new, check):
     return float(out.stdout.strip().splitlines()[-1])
 
 
-@pytest.mark.parametrize("case", ["gather", "jump", "neohooke", "staggered", "dmatrix"])
+@pytest.mark.parametrize("case", ["gather", "jump", "neohooke", "staggered", "rotated", "dmatrix"])
 def test_planted_mistake_fails_its_pin(tmp_path, case):
     old, new, check, tol = {"gather": (GATHER[0], GATHER[1], CHECK_GATHER, 1e-12),
                             "jump": (JUMP[0], JUMP[1], CHECK_JUMP, 1e-13),
                             "neohooke": (NH[0], NH[1], CHECK_NH, 1e-8),
                             "staggered": (STAG[0], STAG[1], CHECK_STAG, 1e-12),
+                            "rotated": (ROT[0], ROT[1], CHECK_ROT, 1e-12),
                             "dmatrix": (DMAT[0], DMAT[1], CHECK_DMAT, 1e-6)}[case]
     ctrl = _mutant_run(tmp_path / "control", old, old, check)  # the unmodified oracle passes
     err = _mutant_run(tmp_path / "mutant", old, new, check)
