@@ -96,7 +96,8 @@ extern "C" {
 /* nonlinear conjugate gradients on the nonlinear LSE (cited in Sec. 3; the
    paper gives no steps): Fletcher-Reeves directions d = -G[P]/mu0 + beta d,
    beta = ||G[P]||^2 / ||G[P]_prev||^2, and the basic scheme's step F += d.
-   FP64, like the fixed point. */
+   Like the fixed point: FP64, or the double-float residual form
+   (COMBO_FP32_REFINED_DF). */
 #define COMBO_NONLINEAR_CG 2
 
 typedef struct combo_ctx combo_ctx;
