@@ -288,6 +288,32 @@ int combo_solve_finish(combo_solve_state* s, combo_result* r);
 void combo_solve_end(combo_solve_state* s);
 
 /*
+ * Checkpoint / resume of a solve between load steps (no counterpart in the
+ * paper; the load stepping F_n = I + (n/S)(Fbar - I) is this library's
+ * reading).  The state that carries over a load step is F (FP64), the boxel
+ * jump vectors (per sub-cell for COMBO_STAGGERED_DFMG), the step index, the
+ * per-step results so far and the counters; everything else restarts with
+ * each step.
+ *   advance_steps  runs until k more load steps are done (COMBO_PENDING) or
+ *                  the solve is (COMBO_OK); it stops between load steps.
+ *   state_export   buf NULL: *bytes receives the size of the image; else
+ *                  writes the host byte image into buf (*bytes its capacity
+ *                  in, the size out).  Only between load steps (after
+ *                  advance_steps, or when done); COMBO_E_INVALID_ARG else.
+ *                  Single solves only (not batches).
+ *   state_import   into a solve begun with the same problem and options and
+ *                  not yet advanced; the header's grid, boxel count, step
+ *                  count, k-space, solver, precision and theory must match
+ *                  (COMBO_E_INVALID_ARG otherwise).  Advancing it then
+ *                  continues with the next load step: with the same launch
+ *                  shapes the result equals the uninterrupted solve's bit for
+ *                  bit.  The image is host-endian and not a portable format.
+ */
+int combo_solve_advance_steps(combo_solve_state* s, int32_t k);
+int combo_state_export(combo_solve_state* s, void* buf, int64_t* bytes);
+int combo_state_import(combo_solve_state* s, const void* buf, int64_t bytes);
+
+/*
  * Serving: a request loop for many solves of different grid sizes,
  * microstructures and load paths (no counterpart in the paper, which solves
  * one RVE at a time; each request is the problem of Sec. 2).
@@ -398,6 +424,24 @@ int combo_apply_G(combo_ctx* ctx, const int32_t n[3], const double l[3], int32_t
                   const double* X, double* Y, double* sumsq, int32_t mem);
 int combo_constitutive(combo_ctx* ctx, const combo_problem* p, const combo_options* o, const double* F,
                        double* a_io, double* P, int32_t mem);
+
+/*
+ * Unit-level entry points, evaluated on the device by the solver's own code
+ * (host arguments; for tests of the material routines in isolation):
+ * combo_neohooke_eval: P(F) (Sec. 6.1, P = mu F + (lam ln J - mu) F^{-T}) and,
+ *   if A is not NULL, the tangent A[9*(3i+J) + 3k+L] = dP_iJ/dF_kL; F, P
+ *   row-major 3x3.  COMBO_E_INADMISSIBLE if det F <= 0.
+ * combo_laminate_eval: one composite boxel (Sec. 4, Algorithms 1 and 2, FP64,
+ *   NR tolerance 1e-12 relative / 1e-14 absolute, at most 50 iterations):
+ *   F the boxel's F, N its normal (normalised here), c = c+ in (0, 1),
+ *   mat = {mu-, lam-, mu+, lam+}; a_io the jump vector (warm start in,
+ *   converged out); P = c+ P+ + c- P-; A (or NULL) the boxel tangent
+ *   (Eq. Peff:Seff); *iters (or NULL) the Newton iterations.
+ *   COMBO_E_LAMINATE / COMBO_E_INADMISSIBLE when the solve fails.
+ */
+int combo_neohooke_eval(combo_ctx* ctx, const double F[9], double mu, double lam, double P[9], double A[81]);
+int combo_laminate_eval(combo_ctx* ctx, const double F[9], const double N[3], double c, const double mat[4],
+                        double a_io[3], double P[9], double A[81], int32_t* iters);
 
 /*
  * combo_df_log: the double-float natural logarithm that the double-float

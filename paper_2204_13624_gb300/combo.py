@@ -64,7 +64,9 @@ EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_o
            "combo_constitutive", "combo_apply_G_noalloc", "combo_server_create", "combo_server_destroy",
            "combo_submit", "combo_poll", "combo_wait", "combo_cancel", "combo_server_stats",
            "combo_autotune_enable", "combo_autotune_force", "combo_autotune_report", "combo_coarse_grain",
-           "combo_coarse_grain_profile", "combo_coarse_grain_profile_read", "combo_df_log"]
+           "combo_coarse_grain_profile", "combo_coarse_grain_profile_read", "combo_df_log",
+           "combo_solve_advance_steps", "combo_state_export", "combo_state_import", "combo_neohooke_eval",
+           "combo_laminate_eval"]
 
 _lib = None
 
@@ -120,6 +122,16 @@ def load(path: str = LIB_PATH):
     L.combo_coarse_grain_profile_read.restype = C.c_int
     L.combo_df_log.argtypes = [vp, vp, vp, C.c_int64]
     L.combo_df_log.restype = C.c_int
+    L.combo_solve_advance_steps.argtypes = [vp, i32]
+    L.combo_solve_advance_steps.restype = C.c_int
+    L.combo_state_export.argtypes = [vp, vp, C.POINTER(C.c_int64)]
+    L.combo_state_export.restype = C.c_int
+    L.combo_state_import.argtypes = [vp, vp, C.c_int64]
+    L.combo_state_import.restype = C.c_int
+    L.combo_neohooke_eval.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp]
+    L.combo_neohooke_eval.restype = C.c_int
+    L.combo_laminate_eval.argtypes = [vp, vp, vp, C.c_double, vp, vp, vp, vp, vp]
+    L.combo_laminate_eval.restype = C.c_int
     _lib = L
     return L
 
@@ -348,6 +360,24 @@ class Solve:
         _check(load().combo_solve_finish(self.h, C.byref(r)))
         return _collect(out, r, self.pb.n_boxels)
 
+    def advance_steps(self, k: int) -> bool:
+        """Run k more load steps (stopping between steps); True when finished."""
+        return _check(load().combo_solve_advance_steps(self.h, int(k))) == OK
+
+    def export_state(self) -> bytes:
+        """combo_state_export: the solve's state between load steps, as bytes."""
+        n = C.c_int64(0)
+        _check(load().combo_state_export(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(load().combo_state_export(self.h, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def import_state(self, blob: bytes):
+        """combo_state_import into this solve (begun with the same problem and
+        options, not yet advanced)."""
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        _check(load().combo_state_import(self.h, buf, len(blob)))
+
     def profile(self, enable: bool = True):
         """Start (reset) or stop per-kernel CUDA-event timing."""
         _check(load().combo_solve_profile(self.h, 1 if enable else 0))
@@ -417,6 +447,30 @@ def constitutive(prob: dict, F, a=None, ctx: Context | None = None, **opts):
     P = np.zeros_like(F)
     _check(load().combo_constitutive(ctx.h, C.byref(pb.s), C.byref(o), _ptr(F), _ptr(a), _ptr(P), MEM_HOST))
     return P, a[:nb]
+
+
+def neohooke_eval(F, mu, lam, ctx: Context | None = None):
+    """combo_neohooke_eval: (P [9], A [9, 9]) of one Neo-Hookean phase at F."""
+    ctx = ctx or default_context()
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(9)
+    P, A = np.zeros(9), np.zeros(81)
+    _check(load().combo_neohooke_eval(ctx.h, _ptr(F), float(mu), float(lam), _ptr(P), _ptr(A)))
+    return P, A.reshape(9, 9)
+
+
+def laminate_eval(F, N, c, mat, a0=None, ctx: Context | None = None):
+    """combo_laminate_eval: one composite boxel; mat = (mu-, lam-, mu+, lam+).
+    Returns dict(P, A, a, iters)."""
+    ctx = ctx or default_context()
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(9)
+    N = np.ascontiguousarray(N, dtype=np.float64).reshape(3)
+    m = np.ascontiguousarray(mat, dtype=np.float64).reshape(4)
+    a = np.zeros(3) if a0 is None else np.ascontiguousarray(a0, dtype=np.float64).reshape(3).copy()
+    P, A = np.zeros(9), np.zeros(81)
+    it = np.zeros(1, np.int32)
+    _check(load().combo_laminate_eval(ctx.h, _ptr(F), _ptr(N), float(c), _ptr(m), _ptr(a), _ptr(P), _ptr(A),
+                                      _ptr(it)))
+    return dict(P=P, A=A.reshape(9, 9), a=a, iters=int(it[0]))
 
 
 def df_log(x, ctx: Context | None = None):

@@ -978,6 +978,9 @@ struct SolveBase {
     virtual int batch_results(combo_result* rs) = 0;
     virtual Profiler& profiler() = 0;
     virtual void request_cancel() = 0;
+    virtual int advance_steps(int32_t k) = 0;
+    virtual int export_state(void* buf, int64_t* bytes) = 0;
+    virtual int import_state(const void* buf, int64_t bytes) = 0;
 };
 
 struct combo_solve_state {
@@ -1037,6 +1040,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     std::vector<double> Pphase;  // [n_steps][2][9] phase averages Pbar_-, Pbar_+
     std::vector<int32_t> iters, cg_iters;
     int64_t ops_done = 0;
+    int64_t step_target = -1;  // advance_steps: stop between load steps once step reaches it
     int error = 0;
 
     ~Solve() override
@@ -1662,6 +1666,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                         state = ST_DONE;
                         break;
                     }
+                    if (step_target >= 0 && step >= step_target) return COMBO_PENDING;
                     if ((rc = begin_step())) return error = rc;
                     state = newton() ? ST_RESID : ST_FP;
                     break;
@@ -1977,6 +1982,138 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     Profiler& profiler() override { return prof; }
     void request_cancel() override { cancel_requested = 1; }
 
+    int advance_steps(int32_t k) override
+    {
+        if (k < 0) return fail(COMBO_E_INVALID_ARG, "negative step count");
+        step_target = (int64_t)step + k;
+        const int rc = advance(0);
+        step_target = -1;
+        return rc;
+    }
+
+    // Checkpoint of a single solve between load steps (host byte image):
+    // header, the per-step results so far, the counters, F [9][V] and the
+    // boxel jumps (per sub-cell for the doubly-fine grid).  Nothing else
+    // carries over a load step: the Krylov vectors, tangent caches and the
+    // nonlinear-CG direction restart with every step.
+    struct CkptHeader {
+        char magic[8];
+        int64_t version, V, nb, n_steps, step;
+        int32_t kspace, solver, precision, theory;
+        double Fprev[9];
+        uint64_t nr_iters, n_backproj, n_lam, n_operator, n_operator64;
+    };
+    int64_t ckpt_bytes() const
+    {
+        const int64_t S = hp.n_steps;
+        return (int64_t)sizeof(CkptHeader) + 8 * (9 * S + 18 * S + S) + 4 * (2 * S) + 8 * 9 * g.V + 8 * 3 * nb +
+               (dfmg() ? 8 * 24 * nb : 0);
+    }
+    void ckpt_fill(CkptHeader& h) const
+    {
+        std::memset(&h, 0, sizeof h);
+        std::memcpy(h.magic, "COMBOCK1", 8);
+        h.version = 1;
+        h.V = g.V;
+        h.nb = nb;
+        h.n_steps = hp.n_steps;
+        h.step = step;
+        h.kspace = opt.kspace;
+        h.solver = opt.solver;
+        h.precision = opt.precision;
+        h.theory = opt.theory;
+        std::memcpy(h.Fprev, Fprev, sizeof Fprev);
+    }
+
+    int export_state(void* buf, int64_t* bytes) override
+    {
+        if (!bytes) return fail(COMBO_E_INVALID_ARG, "null size");
+        if (B != 1) return fail(COMBO_E_INVALID_ARG, "checkpoints cover single solves");
+        if (error) return error;
+        if (state != ST_STEP && state != ST_DONE)
+            return fail(COMBO_E_INVALID_ARG, "a checkpoint is taken between load steps (combo_solve_advance_steps)");
+        const int64_t need = ckpt_bytes();
+        if (!buf) {
+            *bytes = need;
+            return COMBO_OK;
+        }
+        if (*bytes < need) return fail(COMBO_E_INVALID_ARG, "checkpoint buffer too small");
+        CK(cudaSetDevice(ctx->device));
+        Scalars sc;
+        int rc;
+        if ((rc = read_scalars(sc))) return rc;
+        CkptHeader h;
+        ckpt_fill(h);
+        h.nr_iters = sc.nr_iters;
+        h.n_backproj = sc.n_backproj;
+        h.n_lam = sc.n_lam;
+        h.n_operator = sc.n_operator;
+        h.n_operator64 = sc.n_operator64;
+        char* o = static_cast<char*>(buf);
+        auto put = [&](const void* src, size_t n) {
+            std::memcpy(o, src, n);
+            o += n;
+        };
+        const size_t S = (size_t)hp.n_steps;
+        put(&h, sizeof h);
+        put(Pbar.data(), 8 * 9 * S);
+        put(Pphase.data(), 8 * 18 * S);
+        put(resid.data(), 8 * S);
+        put(iters.data(), 4 * S);
+        put(cg_iters.data(), 4 * S);
+        CK(cudaMemcpyAsync(o, d_F, 8 * 9 * (size_t)g.V, cudaMemcpyDeviceToHost, st));
+        o += 8 * 9 * (size_t)g.V;
+        if (nb > 0) CK(cudaMemcpyAsync(o, d_ba, 8 * 3 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+        o += 8 * 3 * (size_t)nb;
+        if (dfmg() && nb > 0) CK(cudaMemcpyAsync(o, d_ba8, 8 * 24 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        *bytes = need;
+        return COMBO_OK;
+    }
+
+    int import_state(const void* buf, int64_t bytes) override
+    {
+        if (!buf) return fail(COMBO_E_INVALID_ARG, "null checkpoint");
+        if (B != 1) return fail(COMBO_E_INVALID_ARG, "checkpoints cover single solves");
+        if (error) return error;
+        if (state != ST_STEP || step != 0 || ops_done != 0)
+            return fail(COMBO_E_INVALID_ARG, "a checkpoint is imported into a solve that has not advanced");
+        if (bytes != ckpt_bytes()) return fail(COMBO_E_INVALID_ARG, "checkpoint size does not match this solve");
+        CkptHeader h, mine;
+        std::memcpy(&h, buf, sizeof h);
+        ckpt_fill(mine);
+        if (std::memcmp(h.magic, mine.magic, 8) != 0 || h.version != 1)
+            return fail(COMBO_E_INVALID_ARG, "not a checkpoint of this library");
+        if (h.V != mine.V || h.nb != mine.nb || h.n_steps != mine.n_steps || h.kspace != mine.kspace ||
+            h.solver != mine.solver || h.precision != mine.precision || h.theory != mine.theory)
+            return fail(COMBO_E_INVALID_ARG, "checkpoint of another problem or other options");
+        if (h.step < 0 || h.step > h.n_steps) return fail(COMBO_E_INVALID_ARG, "checkpoint step out of range");
+        CK(cudaSetDevice(ctx->device));
+        const char* in = static_cast<const char*>(buf) + sizeof h;
+        auto get = [&](void* dst, size_t n) {
+            std::memcpy(dst, in, n);
+            in += n;
+        };
+        const size_t S = (size_t)hp.n_steps;
+        get(Pbar.data(), 8 * 9 * S);
+        get(Pphase.data(), 8 * 18 * S);
+        get(resid.data(), 8 * S);
+        get(iters.data(), 4 * S);
+        get(cg_iters.data(), 4 * S);
+        CK(cudaMemcpyAsync(d_F, in, 8 * 9 * (size_t)g.V, cudaMemcpyHostToDevice, st));
+        in += 8 * 9 * (size_t)g.V;
+        if (nb > 0) CK(cudaMemcpyAsync(d_ba, in, 8 * 3 * (size_t)nb, cudaMemcpyHostToDevice, st));
+        in += 8 * 3 * (size_t)nb;
+        if (dfmg() && nb > 0) CK(cudaMemcpyAsync(d_ba8, in, 8 * 24 * (size_t)nb, cudaMemcpyHostToDevice, st));
+        const uint64_t cnt[5] = {h.nr_iters, h.n_backproj, h.n_lam, h.n_operator, h.n_operator64};
+        CK(cudaMemcpyAsync((char*)d_sc + offsetof(Scalars, nr_iters), cnt, sizeof cnt, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        std::memcpy(Fprev, h.Fprev, sizeof Fprev);
+        step = (int)h.step;
+        ops_done = (int64_t)h.n_operator;
+        return COMBO_OK;
+    }
+
     int finish(combo_result* r) override
     {
         if (!r || !r->Pbar) return fail(COMBO_E_INVALID_ARG, "result needs Pbar");
@@ -2101,6 +2238,24 @@ extern "C" int combo_solve_advance(combo_solve_state* s, int64_t max_ops)
 {
     if (!s) return fail(COMBO_E_INVALID_ARG, "null solve");
     return s->impl->advance(max_ops);
+}
+
+extern "C" int combo_solve_advance_steps(combo_solve_state* s, int32_t k)
+{
+    if (!s) return fail(COMBO_E_INVALID_ARG, "null solve");
+    return s->impl->advance_steps(k);
+}
+
+extern "C" int combo_state_export(combo_solve_state* s, void* buf, int64_t* bytes)
+{
+    if (!s) return fail(COMBO_E_INVALID_ARG, "null solve");
+    return s->impl->export_state(buf, bytes);
+}
+
+extern "C" int combo_state_import(combo_solve_state* s, const void* buf, int64_t bytes)
+{
+    if (!s) return fail(COMBO_E_INVALID_ARG, "null solve");
+    return s->impl->import_state(buf, bytes);
 }
 
 extern "C" int combo_solve_finish(combo_solve_state* s, combo_result* r)
@@ -2329,6 +2484,132 @@ extern "C" int combo_apply_G(combo_ctx* ctx, const int32_t n[3], const double l[
     if (precision == COMBO_FP32_REFINED) return apply_G_impl<float>(ctx, n, l, kspace, X, Y, sumsq, mem);
     if (precision == COMBO_FP32_REFINED_DF) return apply_G_impl<df32>(ctx, n, l, kspace, X, Y, sumsq, mem);
     return fail(COMBO_E_INVALID_ARG, "bad precision");
+}
+
+// One Neo-Hookean evaluation (Sec. 6.1) with its tangent
+// A_iJkL = mu d_ik d_JL + lam G_Ji G_Lk + (mu - lam ln J) G_Jk G_Li, G = F^{-1}.
+__global__ void k_nh_eval(const double* F, double mu, double lam, double* P, double* A, int* ok)
+{
+    const double* f = F;
+    const double c0 = f[4] * f[8] - f[5] * f[7], c1 = f[5] * f[6] - f[3] * f[8], c2 = f[3] * f[7] - f[4] * f[6];
+    const double J = f[0] * c0 + f[1] * c1 + f[2] * c2;
+    if (!nh_P64(f, mu, lam, P)) {
+        *ok = 0;
+        return;
+    }
+    const double iJ = 1.0 / J;
+    const double G[9] = {c0 * iJ, (f[2] * f[7] - f[1] * f[8]) * iJ, (f[1] * f[5] - f[2] * f[4]) * iJ,
+                         c1 * iJ, (f[0] * f[8] - f[2] * f[6]) * iJ, (f[2] * f[3] - f[0] * f[5]) * iJ,
+                         c2 * iJ, (f[1] * f[6] - f[0] * f[7]) * iJ, (f[0] * f[4] - f[1] * f[3]) * iJ};
+    const double m = mu - lam * log(J);
+    for (int i = 0; i < 3; i++)
+        for (int Jx = 0; Jx < 3; Jx++)
+            for (int k = 0; k < 3; k++)
+                for (int L = 0; L < 3; L++)
+                    A[9 * (3 * i + Jx) + 3 * k + L] = ((i == k && Jx == L) ? mu : 0.0) +
+                                                      lam * G[3 * Jx + i] * G[3 * L + k] +
+                                                      m * G[3 * Jx + k] * G[3 * L + i];
+    *ok = 1;
+}
+
+extern "C" int combo_neohooke_eval(combo_ctx* ctx, const double F[9], double mu, double lam, double P[9],
+                                   double A[81])
+{
+    if (!ctx || !F || !P) return fail(COMBO_E_INVALID_ARG, "null argument");
+    CK(cudaSetDevice(ctx->device));
+    double* d = nullptr;
+    int* dok = nullptr;
+    CK(cudaMalloc(&d, 8 * (9 + 9 + 81)));
+    CK(cudaMalloc(&dok, 4));
+    int rc = COMBO_OK, ok = 0;
+    double hP[9], hA[81];
+    if (cudaMemcpyAsync(d, F, 72, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) rc = COMBO_E_CUDA;
+    if (!rc) {
+        k_nh_eval<<<1, 1, 0, ctx->stream>>>(d, mu, lam, d + 9, d + 18, dok);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(hP, d + 9, 72, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaMemcpyAsync(hA, d + 18, 648, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaMemcpyAsync(&ok, dok, 4, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            rc = COMBO_E_CUDA;
+    }
+    cudaFree(d);
+    cudaFree(dok);
+    if (rc) return fail(rc, "combo_neohooke_eval: CUDA error");
+    if (!ok) return fail(COMBO_E_INADMISSIBLE, "det F <= 0");
+    std::memcpy(P, hP, 72);
+    if (A) std::memcpy(A, hA, 648);
+    return COMBO_OK;
+}
+
+// One composite boxel through the solver's own laminate kernel (FP64,
+// Algorithms 1 and 2, the tangent of Eq. Peff:Seff unpacked from its packed
+// upper triangle).  mat = {mu-, lam-, mu+, lam+}.
+extern "C" int combo_laminate_eval(combo_ctx* ctx, const double F[9], const double N[3], double c,
+                                   const double mat[4], double a_io[3], double P[9], double A[81], int32_t* iters)
+{
+    if (!ctx || !F || !N || !mat || !a_io || !P) return fail(COMBO_E_INVALID_ARG, "null argument");
+    if (!(c > 0.0 && c < 1.0)) return fail(COMBO_E_INVALID_ARG, "volume fraction outside (0, 1)");
+    const double nn = std::sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    if (!(nn >= 1e-12)) return fail(COMBO_E_INVALID_ARG, "normal of zero length");
+    CK(cudaSetDevice(ctx->device));
+    // device block: F 9 | N 3 | c 1 | a 3 | P 9 | A packed 45, then the boxel index and the scalars
+    double h[70];
+    std::memcpy(h, F, 72);
+    for (int i = 0; i < 3; i++) h[9 + i] = N[i] / nn;
+    h[12] = c;
+    std::memcpy(h + 13, a_io, 24);
+    double* d = nullptr;
+    int32_t* didx = nullptr;
+    Scalars* dsc = nullptr;
+    CK(cudaMalloc(&d, sizeof h));
+    CK(cudaMalloc(&didx, 4));
+    CK(cudaMalloc(&dsc, sizeof(Scalars)));
+    int rc = COMBO_OK;
+    const int32_t zero = 0;
+    Scalars sc{};
+    if (cudaMemcpyAsync(d, h, sizeof h, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(didx, &zero, 4, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(dsc, 0, sizeof(Scalars), ctx->stream) != cudaSuccess)
+        rc = COMBO_E_CUDA;
+    if (!rc) {
+        BoxelArgs<double> b{};
+        b.nb = 1;
+        b.V = 1;
+        b.bidx = didx;
+        b.bN = d + 9;
+        b.bc = d + 12;
+        b.ba = d + 13;
+        b.bP = d + 16;
+        b.bA = A ? d + 25 : nullptr;
+        b.F = d;
+        b.mu[0] = mat[0];
+        b.lam[0] = mat[1];
+        b.mu[1] = mat[2];
+        b.lam[1] = mat[3];
+        b.tol_rel = 1e-12;
+        b.tol_abs = 1e-14;
+        b.max_iter = 50;
+        b.sc = dsc;
+        launch_boxel<double>(b, ctx->stream);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaMemcpyAsync(&sc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            rc = COMBO_E_CUDA;
+    }
+    cudaFree(d);
+    cudaFree(didx);
+    cudaFree(dsc);
+    if (rc) return fail(rc, "combo_laminate_eval: CUDA error");
+    if (sc.status) return fail(sc.status, "laminate solve failed");
+    std::memcpy(a_io, h + 13, 24);
+    std::memcpy(P, h + 16, 72);
+    if (A)
+        for (int r = 0; r < 9; r++)
+            for (int q = 0; q < 9; q++) A[9 * r + q] = h[25 + sym_idx(r, q)];
+    if (iters) *iters = (int32_t)sc.nr_iters;
+    return COMBO_OK;
 }
 
 __global__ void k_df_log(const double* x, double* y, int64_t n)
