@@ -303,6 +303,35 @@ def solve(prob: dict, ctx: Context | None = None, fields: bool = True, device_re
     return _collect(out, r, pb.n_boxels)
 
 
+def solve_record(prob: dict, result: dict, seconds: float | None = None, **opts) -> str:
+    """One JSON line describing a finished solve: grid, boxels, options,
+    load steps, per-step outer / CG iterations and residuals, Pbar per step,
+    the laminate and operator counters, wall time if given, and the bytes of
+    the fields a solve keeps resident (nine FP64 components of F and the
+    spectrum).  Host-side formatting of a result dict returned by solve(),
+    Solve.finish() or solve_batch()."""
+    import json
+
+    o = options(**opts)
+    n = [int(v) for v in prob["n"]]
+    V = n[0] * n[1] * n[2]
+    nhp = (n[0] // 2 + 1 + 3) // 4 * 4
+    rec = {"grid": n, "voxels": V, "boxels": int(len(prob.get("boxel_idx", []))),
+           "precision": int(o.precision), "kspace": int(o.kspace), "solver": int(o.solver),
+           "theory": int(o.theory), "tol": float(o.tol), "load_steps": int(result.get("steps_done", 0)),
+           "outer_iterations": [int(v) for v in np.asarray(result["iters"]).ravel()],
+           "cg_iterations": [int(v) for v in np.asarray(result.get("cg_iters", [])).ravel()],
+           "residuals": [float(v) for v in np.asarray(result["resid"]).ravel()],
+           "Pbar": np.asarray(result["Pbar"], dtype=float).reshape(-1, 9).tolist(),
+           "nr_iterations": int(result.get("nr_iters", 0)), "back_projections": int(result.get("n_backproj", 0)),
+           "laminate_evaluations": int(result.get("n_laminate_evals", 0)),
+           "operator_applications": int(result.get("n_operator", 0)),
+           "resident_field_bytes": 8 * 9 * V + 16 * 9 * n[2] * n[1] * nhp}
+    if seconds is not None:
+        rec["seconds"] = float(seconds)
+    return json.dumps(rec)
+
+
 def autotune_enable(enable: bool = True):
     load().combo_autotune_enable(1 if enable else 0)
 
