@@ -128,14 +128,47 @@ print(worst)
 """
 
 
-def _mutant_run(tmp_path, old, new, check):
+# Sec. 5 normal detection (oracle/normals.py): the second moments taken about
+# the boxel's plain centroid instead of the weighted barycentre of its interface
+# voxels, or the 1D stencils without their weights r_i = h_j h_k / h_i on
+# anisotropic voxels: the planar-interface pin (N . n >= 0.998 where the plane
+# cuts across a boxel, for the centroid) or the direct-stencil pin (for the
+# weights) must fail.
+BARY = ("P = P_all - (wb @ P_all) / wb.sum()", "P = P_all - P_all.mean(axis=0)")
+RW = ("r = (hy * hz / hx, hx * hz / hy, hx * hy / hz)", "r = (1.0, 1.0, 1.0)")
+CHECK_PLANE = r"""
+import numpy as np
+from oracle import normals as nrm
+from paper_2204_13624_gb300 import microstructure as ms
+b, h = %s, %s
+nt = np.array([0.48, 0.6, 0.64])
+chi = ms.fine_plane_image((64, 64, 64), nt, 3.3, h)
+phase, idx, c, N = nrm.block_normals(chi, b, h)
+nc = (64 // b[0], 64 // b[1], 64 // b[2])
+I, J, K = idx %% nc[0], (idx // nc[0]) %% nc[1], idx // (nc[0] * nc[1])
+inner = (I > 0) & (I < nc[0] - 1) & (J > 0) & (J < nc[1] - 1) & (K > 0) & (K < nc[2] - 1)
+cut = inner & (c > 0.1) & (c < 0.9)
+print(1.0 - float(np.min(N[cut] @ nt)))
+"""
+CHECK_STENCIL = r"""
+import numpy as np
+from oracle import normals as nrm
+chi = (np.random.default_rng(1).random((6, 8, 10)) < 0.5).astype(np.float64)
+h = (0.7, 1.3, 2.1)
+r = (h[1] * h[2] / h[0], h[0] * h[2] / h[1], h[0] * h[1] / h[2])
+direct = sum(ri * (np.roll(chi, 1, ax) - 2 * chi + np.roll(chi, -1, ax)) for ax, ri in zip((2, 1, 0), r))
+print(np.abs(nrm.stencil_weights(chi, h) - np.abs(direct)).max())
+"""
+
+
+def _mutant_run(tmp_path, old, new, check, fname="combo_oracle.c"):
     tmp_path.mkdir()
     dst = tmp_path / "oracle"
     shutil.copytree(os.path.join(ROOT, "oracle"), dst,
                     ignore=shutil.ignore_patterns("*.so", "*.tmp", "__pycache__"))
-    src = (dst / "combo_oracle.c").read_text()
+    src = (dst / fname).read_text()
     assert src.count(old) == 1, "the planted text must occur exactly once"
-    (dst / "combo_oracle.c").write_text(src.replace(old, new))
+    (dst / fname).write_text(src.replace(old, new))
     env = dict(os.environ, PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT, os.path.join(ROOT, "tests")]))
     out = subprocess.run([sys.executable, "-c", check], env=env, cwd=str(tmp_path), capture_output=True,
                          text=True, timeout=300)
@@ -155,3 +188,17 @@ def test_planted_mistake_fails_its_pin(tmp_path, case):
     err = _mutant_run(tmp_path / "mutant", old, new, check)
     assert ctrl < tol, (case, ctrl)
     assert err > 1e3 * tol, (case, err)
+
+
+@pytest.mark.parametrize("case", ["barycentre", "stencil_weights"])
+def test_planted_mistake_in_the_normal_detection(tmp_path, case):
+    """The moments about the plain centroid fail the planar-interface pin; the
+    unweighted stencil (which still fits planes well) fails the direct-stencil
+    pin on anisotropic voxels."""
+    old, new, check, tol, worse = {
+        "barycentre": (BARY[0], BARY[1], CHECK_PLANE % (repr((16, 8, 4)), repr((1, 1, 1))), 0.002, 0.01),
+        "stencil_weights": (RW[0], RW[1], CHECK_STENCIL, 1e-12, 1e-3)}[case]
+    ctrl = _mutant_run(tmp_path / "control", old, old, check, "normals.py")
+    err = _mutant_run(tmp_path / "mutant", old, new, check, "normals.py")
+    assert ctrl < tol, (case, ctrl)
+    assert err > worse, (case, err)
