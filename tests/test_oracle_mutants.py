@@ -202,3 +202,35 @@ def test_planted_mistake_in_the_normal_detection(tmp_path, case):
     err = _mutant_run(tmp_path / "mutant", old, new, check, "normals.py")
     assert ctrl < tol, (case, ctrl)
     assert err > worse, (case, err)
+
+
+# Algorithm 2 with the new beta a quarter of the way to the crossed bound
+# instead of the midpoint: iterates stay admissible, but the pin that a
+# projected step halves one phase Jacobian exactly (J affine in beta by the
+# matrix determinant lemma) must fail.  The check prints the number of
+# back-projected solves without as many halvings as projections.
+BP = ("double bstar = 0.5 * (b0 + bc);", "double bstar = 0.75 * b0 + 0.25 * bc;")
+CHECK_BP = r"""
+import numpy as np, oracle as orc
+from test_oracle_laminate import MAT, critical_cases
+bad = 0
+for F, N in critical_cases():
+    try:
+        r = orc.laminate(F.ravel(), N, 0.99625, MAT, trace=True)
+    except ValueError:
+        continue
+    if r["nbp"] == 0:
+        continue
+    tr = r["trace"]
+    halved = sum(abs(tr[k, col] - 0.5 * tr[k - 1, col]) < 1e-12 * max(1.0, tr[k - 1, col])
+                 for k in range(1, tr.shape[0]) for col in (1, 2))
+    bad += int(halved < r["nbp"])
+print(bad)
+"""
+
+
+def test_planted_mistake_in_the_back_projection(tmp_path):
+    ctrl = _mutant_run(tmp_path / "control", BP[0], BP[0], CHECK_BP)
+    err = _mutant_run(tmp_path / "mutant", BP[0], BP[1], CHECK_BP)
+    assert ctrl == 0
+    assert err >= 3
