@@ -234,3 +234,36 @@ def test_planted_mistake_in_the_back_projection(tmp_path):
     err = _mutant_run(tmp_path / "mutant", BP[0], BP[1], CHECK_BP)
     assert ctrl == 0
     assert err >= 3
+
+
+# the doubly-fine assembly with the F_12 / F_21 pair taken at c - (l1, l2, 0)
+# instead of c + (l1, l2, 0): the law is then no longer the gradient of the
+# sub-cell energy, and the finite-difference pin must fail (the check prints
+# the largest error relative to |P| over a few entries)
+ASM = ("const long v12 = wrapi(i + l1, n1) + n1 * (wrapi(j + l2, n2) + n2 * k);",
+       "const long v12 = wrapi(i - l1, n1) + n1 * (wrapi(j - l2, n2) + n2 * k);")
+CHECK_ASM = r"""
+import numpy as np, oracle as orc
+from paper_2204_13624_gb300 import microstructure as ms
+from test_oracle_dfmg import cell_energies
+p = ms.random_boxels((5, 4, 3), seed=41, boxel_frac=0.35, incl_frac=0.3, contrast=10.0)
+V = 60
+rng = np.random.default_rng(5)
+F = np.eye(3).reshape(9, 1) + 0.08 * rng.uniform(-1, 1, (9, V))
+P, _ = orc.constitutive_field(p, F, opts=dict(kspace=3))
+worst, h = 0.0, 1e-5
+for comp, v in [(1, 7), (3, 30), (1, 44), (0, 12)]:
+    Fp, Fm = F.copy(), F.copy()
+    Fp[comp, v] += h
+    Fm[comp, v] -= h
+    dE = (cell_energies(orc, p, Fp) - cell_energies(orc, p, Fm)).sum() / 8.0
+    worst = max(worst, abs(dE / (2 * h) - P[comp, v]) / np.abs(P).max())
+print(worst)
+"""
+
+
+def test_planted_mistake_in_the_doubly_fine_assembly(tmp_path):
+    ctrl = _mutant_run(tmp_path / "control", ASM[0], ASM[0], CHECK_ASM)
+    err = _mutant_run(tmp_path / "mutant", ASM[0], ASM[1], CHECK_ASM)
+    assert ctrl < 1e-7
+    assert err > 1e-3
