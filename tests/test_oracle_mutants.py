@@ -267,3 +267,28 @@ def test_planted_mistake_in_the_doubly_fine_assembly(tmp_path):
     err = _mutant_run(tmp_path / "mutant", ASM[0], ASM[1], CHECK_ASM)
     assert ctrl < 1e-7
     assert err > 1e-3
+
+
+# the normal without the sign step of Eq. normal:flip: the pin that the ball's
+# normals point out of the inclusion (N . x > 0, x from the ball's centre) must
+# fail; the check prints the fraction of boxels whose normal points inwards
+FLIP = ("return N if float(Nt @ N) > 0.0 else -N  # Eq. normal:flip", "return N")
+CHECK_FLIP = r"""
+import numpy as np
+from oracle import normals as nrm
+from paper_2204_13624_gb300 import microstructure as ms
+chi = ms.fine_ball_image(64, 0.4)
+b = (8, 8, 8)
+phase, idx, c, N = nrm.block_normals(chi, b, (1, 1, 1))
+nc = 8
+I, J, K = idx % nc, (idx // nc) % nc, idx // (nc * nc)
+x = np.stack([(I + 0.5) / nc - 0.5, (J + 0.5) / nc - 0.5, (K + 0.5) / nc - 0.5], axis=1)
+print(float(np.mean(np.sum(N * x, axis=1) < 0.0)))
+"""
+
+
+def test_planted_mistake_in_the_normal_sign(tmp_path):
+    ctrl = _mutant_run(tmp_path / "control", FLIP[0], FLIP[0], CHECK_FLIP, "normals.py")
+    err = _mutant_run(tmp_path / "mutant", FLIP[0], FLIP[1], CHECK_FLIP, "normals.py")
+    assert ctrl == 0.0
+    assert err > 0.1
