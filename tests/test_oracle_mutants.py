@@ -292,3 +292,24 @@ def test_planted_mistake_in_the_normal_sign(tmp_path):
     err = _mutant_run(tmp_path / "mutant", FLIP[0], FLIP[1], CHECK_FLIP, "normals.py")
     assert ctrl == 0.0
     assert err > 0.1
+
+
+# nonlinear CG with the Fletcher-Reeves beta dropped (every step the basic
+# scheme's): the pin that it needs fewer than a third of the basic scheme's
+# iterations must fail; the check prints 3 x its iterations / the basic scheme's
+NCG = ("const double beta = (it == 0) ? 0.0 : ss / gg_prev;", "const double beta = 0.0;")
+CHECK_NCG = r"""
+import numpy as np, oracle as orc
+from paper_2204_13624_gb300 import microstructure as ms
+p = ms.centred_sphere((12, 12, 12), 0.2, 10.0, np.diag([1.04, 1.0, 0.99]), 2)
+rn = orc.solve(p, dict(solver=2, tol=1e-10, max_iter=20000))
+rb = orc.solve(p, dict(solver=0, tol=1e-10, max_iter=20000))
+print(3.0 * rn["iters"].sum() / rb["iters"].sum())
+"""
+
+
+def test_planted_mistake_in_the_nonlinear_cg(tmp_path):
+    ctrl = _mutant_run(tmp_path / "control", NCG[0], NCG[0], CHECK_NCG)
+    err = _mutant_run(tmp_path / "mutant", NCG[0], NCG[1], CHECK_NCG)
+    assert ctrl < 1.0
+    assert err > 2.0
