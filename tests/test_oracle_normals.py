@@ -164,3 +164,15 @@ def test_windowed_boxels_equal_the_whole_image_pass(nrm, method):
     assert np.array_equal(ph2, phase.ravel())
     assert np.array_equal(c2[idx], c)
     assert np.allclose(N2[idx], N, atol=1e-12)
+
+
+@pytest.mark.parametrize("b", [16, 32])
+def test_coarser_composite_voxel_counts(nrm, ball, b):
+    """The same ball coarse-grained to 16^3 and 8^3: the oracle's composite
+    voxels (mixed blocks of the fine image) are the mixed blocks counted by the
+    input generator's independent block-by-block scan (704 and 224)."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    phase, idx, c, N = nrm.block_normals(ball, (b, b, b), (1, 1, 1))
+    assert int((phase == 2).sum()) == idx.size == ms.fine_sphere_block_count(256, 256 // b, 0.4)
+    assert idx.size == {16: 704, 32: 224}[b]
