@@ -180,6 +180,13 @@ typedef struct {
  *   mu0              reference shear modulus of the fixed point; <= 0 picks
  *                    (min mu + max(lambda + 2 mu)) / 2
  *   theory           COMBO_FINITE_STRAIN (default) or COMBO_INFINITESIMAL_STRAIN
+ *   wait_poll_cap    bound of every wait of the bulk-copy (TMA) kernels on their
+ *                    copies: 0 (default) = 2^24 polls, k > 0 = k polls, -1 = none
+ *                    (each such wait runs out at once; for testing the timeout
+ *                    path).  A wait that runs out makes the kernel wait for its own
+ *                    copies in flight, skip the rest of its work and raise
+ *                    COMBO_E_TIMEOUT, which the call returns; the context stays
+ *                    usable.
  */
 typedef struct {
     int32_t precision;
@@ -197,6 +204,7 @@ typedef struct {
     double c_min;
     double mu0;
     int32_t theory; /* COMBO_FINITE_STRAIN (default) or COMBO_INFINITESIMAL_STRAIN */
+    int32_t wait_poll_cap;
 } combo_options;
 
 /*
@@ -276,14 +284,25 @@ int combo_solve_batch(combo_ctx* ctx, int32_t n_problems, const combo_problem* p
  * Incremental interface (used for timing and by the serving loop):
  *   begin    validates and copies the problem to the device, allocates the
  *            solve's fields; nothing runs yet.
- *   advance  runs at most max_operator operator applications (<= 0: no
- *            limit) and returns COMBO_OK when every load step is done,
- *            COMBO_PENDING (1) when the limit stopped it, or an error.
+ *   advance  runs until max_operator more operator applications are done
+ *            (<= 0: no limit; the solver checks the count between its device
+ *            loop chunks, so it may run a chunk past it) and returns COMBO_OK
+ *            when every load step is done, COMBO_PENDING (1) when the limit
+ *            stopped it, or an error.
+ *   advance_newton  the same with min_operator > 0, but a reached limit
+ *            stops the solve only between Newton steps (before the residual
+ *            evaluation of the next Newton iteration, or between load steps),
+ *            so every Newton step it starts -- residual, laminate solves, CG
+ *            iterations and F update -- runs in full inside the call (used to
+ *            time whole Newton steps); the fixed point and nonlinear CG stop
+ *            between chunks as with advance.  COMBO_E_INVALID_ARG for
+ *            min_operator <= 0.
  *   finish   writes the results; end frees the state.
  */
 #define COMBO_PENDING 1
 int combo_solve_begin(combo_ctx* ctx, const combo_problem* p, const combo_options* o, combo_solve_state** s);
 int combo_solve_advance(combo_solve_state* s, int64_t max_operator);
+int combo_solve_advance_newton(combo_solve_state* s, int64_t min_operator);
 int combo_solve_finish(combo_solve_state* s, combo_result* r);
 void combo_solve_end(combo_solve_state* s);
 
@@ -310,6 +329,8 @@ void combo_solve_end(combo_solve_state* s);
  *                  bit.  The image is host-endian and not a portable format.
  */
 int combo_solve_advance_steps(combo_solve_state* s, int32_t k);
+/* (the image: a header, the per-step results so far, then F [9][V] FP64 and
+   the jump vectors [nb][3] FP64, and [nb][8][3] more on the doubly-fine grid) */
 int combo_state_export(combo_solve_state* s, void* buf, int64_t* bytes);
 int combo_state_import(combo_solve_state* s, const void* buf, int64_t bytes);
 
@@ -513,8 +534,19 @@ int combo_coarse_grain_profile(int32_t enable);
 int combo_coarse_grain_profile_read(double ms[5]);
 
 /*
- * combo_apply_G_noalloc: the same Green operator as combo_apply_G (FP64),
- * for callers that cannot allocate device memory -- code that runs inside a
+ * Fault injection for tests of the failure paths (no counterpart in the
+ * paper).  combo_fault_inject_alloc(k), k >= 0: the device allocations of
+ * solves, batches and servers set up afterwards succeed k more times, then
+ * one fails as cudaMalloc does when the device is out of memory (the hook
+ * then disarms); the call that hit it frees what it had allocated and
+ * returns COMBO_E_OOM (combo_solve, combo_solve_begin, combo_solve_batch).
+ * k < 0 disarms the hook.  Process-wide; returns COMBO_OK.
+ */
+int combo_fault_inject_alloc(int64_t after);
+
+/*
+ * combo_apply_G_noalloc: the Green operator of combo_apply_G (FP64) for the
+ * rotated and spectral schemes, for callers that cannot allocate device memory -- code that runs inside a
  * memory arena or pool it does not own, a loop that must not allocate, or a
  * host framework that owns all device memory.  It has no counterpart in the
  * paper; it is a deployment variant of the Green-operator entry point.
@@ -523,10 +555,12 @@ int combo_coarse_grain_profile_read(double ms[5]);
  * passes X and Y, [9][V] FP64 in device memory (they may be the same buffer).  The
  * half spectrum, the reduction partials, the solver scalars and the
  * twiddle / symbol tables live in one library-owned device array of 4 MiB,
- * which every GPU that loads libcombo.so holds until the process exits.
- * Limits: each side 2^a 3^b in [2, 64], n1 even, and
- * 9 n3 n2 (n1/2 + 1 rounded up to 4) <= 259504 (every grid up to 32^3 fits);
- * larger grids return COMBO_E_INVALID_ARG with a message.
+ * which every GPU that loads libcombo.so holds until the process exits; each
+ * call fills the tables on the device (no host copy).
+ * Limits: each side 2^a 3^b in [2, 64], n1 even, kspace COMBO_ROTATED or
+ * COMBO_SPECTRAL (not the staggered grid), and
+ * 9 n3 n2 (n1/2 + 1 rounded up to 4) <= 259520 (every grid up to 32^3 fits);
+ * anything else returns COMBO_E_INVALID_ARG with a message.
  *   device  CUDA device ordinal to run on (made current for the call).
  *   stream  cudaStream_t (NULL = the default stream).
  *   sumsq   optional host pointer: receives sum_x |Y(x)|^2; when given, the

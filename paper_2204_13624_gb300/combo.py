@@ -47,7 +47,7 @@ class OptionsS(C.Structure):
                 ("max_iter", C.c_int32), ("fixed_iterations", C.c_int32), ("cg_tol", C.c_double),
                 ("cg_max_iter", C.c_int32), ("cg_fixed_iterations", C.c_int32), ("nr_tol_rel", C.c_double),
                 ("nr_tol_abs", C.c_double), ("nr_max_iter", C.c_int32), ("c_min", C.c_double), ("mu0", C.c_double),
-                ("theory", C.c_int32)]
+                ("theory", C.c_int32), ("wait_poll_cap", C.c_int32)]
 
 
 class ResultS(C.Structure):
@@ -59,14 +59,14 @@ class ResultS(C.Structure):
 
 
 EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_options_default",
-           "combo_solve_footprint", "combo_solve", "combo_solve_begin", "combo_solve_advance", "combo_solve_finish",
+           "combo_solve_footprint", "combo_solve", "combo_solve_begin", "combo_solve_advance", "combo_solve_advance_newton", "combo_solve_finish",
            "combo_solve_end", "combo_solve_batch", "combo_solve_profile", "combo_solve_profile_read", "combo_apply_G",
            "combo_constitutive", "combo_apply_G_noalloc", "combo_server_create", "combo_server_destroy",
            "combo_submit", "combo_poll", "combo_wait", "combo_cancel", "combo_server_stats",
            "combo_autotune_enable", "combo_autotune_force", "combo_autotune_report", "combo_coarse_grain",
            "combo_coarse_grain_profile", "combo_coarse_grain_profile_read", "combo_df_log",
            "combo_solve_advance_steps", "combo_state_export", "combo_state_import", "combo_neohooke_eval",
-           "combo_laminate_eval"]
+           "combo_laminate_eval", "combo_fault_inject_alloc"]
 
 _lib = None
 
@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH):
     L.combo_solve_begin.restype = C.c_int
     L.combo_solve_advance.argtypes = [vp, i64]
     L.combo_solve_advance.restype = C.c_int
+    L.combo_solve_advance_newton.argtypes = [vp, i64]
+    L.combo_solve_advance_newton.restype = C.c_int
     L.combo_solve_finish.argtypes = [vp, vp]
     L.combo_solve_finish.restype = C.c_int
     L.combo_solve_end.argtypes = [vp]
@@ -132,6 +134,8 @@ def load(path: str = LIB_PATH):
     L.combo_neohooke_eval.restype = C.c_int
     L.combo_laminate_eval.argtypes = [vp, vp, vp, C.c_double, vp, vp, vp, vp, vp]
     L.combo_laminate_eval.restype = C.c_int
+    L.combo_fault_inject_alloc.argtypes = [i64]
+    L.combo_fault_inject_alloc.restype = C.c_int
     _lib = L
     return L
 
@@ -382,6 +386,11 @@ class Solve:
         """Run up to max_operator operator applications; True when finished."""
         return _check(load().combo_solve_advance(self.h, int(max_operator))) == OK
 
+    def advance_newton(self, min_operator: int) -> bool:
+        """Run at least min_operator operator applications and on to the end
+        of the Newton step reached; True when finished."""
+        return _check(load().combo_solve_advance_newton(self.h, int(min_operator))) == OK
+
     def finish(self, fields: bool = True, device_results: bool = False):
         out, r = _result_buffers(self.pb, fields, device_results)
         if device_results:
@@ -500,6 +509,12 @@ def laminate_eval(F, N, c, mat, a0=None, ctx: Context | None = None):
     _check(load().combo_laminate_eval(ctx.h, _ptr(F), _ptr(N), float(c), _ptr(m), _ptr(a), _ptr(P), _ptr(A),
                                       _ptr(it)))
     return dict(P=P, A=A.reshape(9, 9), a=a, iters=int(it[0]))
+
+
+def fault_inject_alloc(after: int):
+    """Test hook: the device allocation after `after` more successful ones
+    fails as out of memory (then the hook disarms); after < 0 disarms it."""
+    _check(load().combo_fault_inject_alloc(int(after)))
 
 
 def df_log(x, ctx: Context | None = None):

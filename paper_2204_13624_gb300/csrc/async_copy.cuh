@@ -69,6 +69,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
+// Poll cap of a bounded wait from a launch argument: 0 = the default 2^24
+// polls, kWaitNone = no poll at all (every such wait runs out at once: the
+// test of the timeout path), else that many polls.  Waits that drain copies
+// still in flight after a timeout always use the default.
+constexpr uint32_t kWaitNone = 0xffffffffu;
+__host__ __device__ __forceinline__ uint32_t wait_cap_of(uint32_t arg)
+{
+    return arg == 0u ? (1u << 24) : (arg == kWaitNone ? 0u : arg);
+}
+
 // Wait for phase `parity` of bar with an iteration cap; false if the cap was
 // reached (the caller reports a timeout instead of hanging).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t max_iters = 1u << 24)

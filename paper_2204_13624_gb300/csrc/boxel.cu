@@ -353,12 +353,12 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
             PhaseD box;
 #pragma unroll
             for (int c = 0; c < 9; c++) box.F[c] = Fd[c];
-            if (!nh_phase_df(box, mu[0], lam[0], Nd, gbox)) status = COMBO_E_INADMISSIBLE;
+            if (!nh_phase_df(box, mu[0], lam[0], Nd, gbox)) status = finite9(Fb) ? COMBO_E_INADMISSIBLE : COMBO_E_NAN;
         } else {
             Phase box;
 #pragma unroll
             for (int c = 0; c < 9; c++) box.F[c] = Fb[c];
-            if (!nh_phase(box, mu[0], lam[0], N)) status = COMBO_E_INADMISSIBLE;
+            if (!nh_phase(box, mu[0], lam[0], N)) status = finite9(Fb) ? COMBO_E_INADMISSIBLE : COMBO_E_NAN;
 #pragma unroll
             for (int i = 0; i < 3; i++) gbox[i] = box.g[i];
         }
@@ -663,12 +663,12 @@ template <bool DFM> __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArg
             PhaseD box;
 #pragma unroll
             for (int c = 0; c < 9; c++) box.F[c] = Fd[c];
-            if (!nh_phase_df(box, mu[0], lam[0], Nd, gbox)) status = COMBO_E_INADMISSIBLE;
+            if (!nh_phase_df(box, mu[0], lam[0], Nd, gbox)) status = finite9(Fb) ? COMBO_E_INADMISSIBLE : COMBO_E_NAN;
         } else {
             Phase box;
 #pragma unroll
             for (int c = 0; c < 9; c++) box.F[c] = Fb[c];
-            if (!nh_phase(box, mu[0], lam[0], N)) status = COMBO_E_INADMISSIBLE;
+            if (!nh_phase(box, mu[0], lam[0], N)) status = finite9(Fb) ? COMBO_E_INADMISSIBLE : COMBO_E_NAN;
 #pragma unroll
             for (int q = 0; q < 3; q++) gbox[q] = box.g[q];
         }

@@ -250,6 +250,16 @@ __device__ __forceinline__ void raise_status(Scalars* sc, int code)
     atomicCAS(&sc->status, 0, code);
 }
 
+// all nine entries finite: tells a NaN / Inf deformation (COMBO_E_NAN) from
+// det F <= 0 (COMBO_E_INADMISSIBLE) where a stress evaluation fails
+__device__ __forceinline__ bool finite9(const double f[9])
+{
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 9; c++) ok = ok && isfinite(f[c]);
+    return ok;
+}
+
 // Deterministic sum of n partials by one block: fixed strided accumulation
 // (4 independent chains) then a fixed tree.  red: >= blockDim.x rounded up to
 // a power of two doubles (blockDim.x <= 256 with the 256-entry buffers).
@@ -417,6 +427,7 @@ template <typename T, typename Tc> struct XinvArgs {
     double cg_tol;
     int cg_max, cg_fixed;
     int cfg;         // launch-shape candidate (autotuner; 0 = default)
+    uint32_t wait_cap;  // poll cap of the bulk-copy waits (wait_cap_of: 0 = default)
 };
 
 template <typename T> struct YArgs {
@@ -429,6 +440,7 @@ template <typename T> struct YArgs {
     int guard;  // 0 none, 1 skip if cg_done, 2 skip if outer_done
     const void* tmap;  // CUtensorMap of spec for the TMA y-pass (FP32), or null
     int cfg;           // launch-shape candidate (autotuner; 0 = default)
+    uint32_t wait_cap;  // poll cap of the tile waits (wait_cap_of: 0 = default)
 };
 
 template <typename T> struct ZArgs {
@@ -447,6 +459,7 @@ template <typename T> struct ZArgs {
     int guard;
     const void* tmap;  // CUtensorMap of spec for the TMA z-pass (FP32), or null
     int cfg;           // launch-shape candidate (autotuner; 0 = default)
+    uint32_t wait_cap;  // poll cap of the tile waits (wait_cap_of: 0 = default)
 };
 
 template <typename T, typename Tc> void launch_xfwd(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st);
@@ -460,6 +473,7 @@ int xpass_partials_max(const GridDims& g);     // upper bound of any x-pass grid
 int xpass_gp(const GridDims& g, int lines, int cap);  // x-pass blocks per problem (grid = nprob * gp)
 int ypass_tx(int n, size_t cxbytes);  // columns per y-pass block (must match the launcher)
 int zpass_tx(int n, size_t cxbytes);  // columns per z-pass block (sets the partial count)
+int zpass_blocks(const GridDims& g, int tx, size_t cxbytes);  // non-TMA z-pass blocks (= partials) per problem
 
 // FP32 CG x-inverse with streamed (bulk asynchronous, double-buffered)
 // inputs, for n1 = 128, 256, 512 (xpass_stream.cu)

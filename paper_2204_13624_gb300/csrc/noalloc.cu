@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -91,6 +92,49 @@ Plan plan_for(int n)
     return p;
 }
 
+// Per-call set-up on the device (no host copy): clears the solver scalars and
+// fills the twiddle tables exp(-2 pi i k / m) and the derivative symbol of
+// the requested scheme in product form k_j = sa_j[xi_j] prod_{m != j} sb_m[xi_m]
+// (rotated: sa = (2/h) sin(pi xi / n), sb = cos(pi xi / n), 0 at Nyquist;
+// spectral: sa = 2 pi xi_signed / l, 0 at Nyquist, sb = 1).  One block.
+__global__ void k_noalloc_tables(int n1, int n2, int n3, double l1, double l2, double l3, int kspace, Scalars* sc,
+                                 double2* twM, double2* tw2, double2* twy, double2* twz, double* sa, double* sb)
+{
+    const int M = n1 / 2;
+    uint32_t* z = reinterpret_cast<uint32_t*>(sc);
+    for (int i = threadIdx.x; i < (int)(sizeof(Scalars) / 4); i += blockDim.x) z[i] = 0u;
+    auto tw = [](int k, int m) {
+        double s, c;
+        sincospi(2.0 * (double)k / (double)m, &s, &c);
+        return double2{c, -s};
+    };
+    const int n[3] = {n1, n2, n3};
+    const double l[3] = {l1, l2, l3};
+    for (int k = threadIdx.x; k < kMaxSide; k += blockDim.x) {
+        if (k < M) twM[k] = tw(k, M);
+        if (k <= M) tw2[k] = tw(k, n1);
+        if (k < n2) twy[k] = tw(k, n2);
+        if (k < n3) twz[k] = tw(k, n3);
+        for (int j = 0; j < 3; j++) {
+            if (k >= n[j]) continue;
+            const bool nyq = (2 * k == n[j]);
+            double a, b;
+            if (kspace == COMBO_ROTATED) {
+                double s, c;
+                sincospi((double)k / (double)n[j], &s, &c);
+                a = (2.0 * n[j] / l[j]) * s;
+                b = nyq ? 0.0 : c;
+            } else {
+                const int ks = (2 * k > n[j]) ? k - n[j] : k;
+                a = nyq ? 0.0 : 2.0 * M_PI * (double)ks / l[j];
+                b = 1.0;
+            }
+            sa[j * kMaxSide + k] = a;
+            sb[j * kMaxSide + k] = b;
+        }
+    }
+}
+
 __global__ void k_noalloc_sumsq(Scalars* sc, const double* part, int n)
 {
     __shared__ double red[256];
@@ -126,10 +170,14 @@ extern "C" int combo_apply_G_noalloc(int32_t device, void* stream, const int32_t
     g.nhp = (g.nh + 3) / 4 * 4;
     g.V = (int64_t)n[0] * n[1] * n[2];
     g.Vs = (int64_t)n[2] * n[1] * g.nhp;
-    if ((size_t)(9 * g.Vs) > kMaxSpectrum)
-        return set_error(COMBO_E_INVALID_ARG,
-                         "combo_apply_G_noalloc: grid too large for the 4 MiB scratch "
-                         "(9 n3 n2 (n1/2+1 rounded up to 4) complex entries must be <= 259504; every grid up to 32^3 fits)");
+    if ((size_t)(9 * g.Vs) > kMaxSpectrum) {
+        char msg[256];
+        snprintf(msg, sizeof msg,
+                 "combo_apply_G_noalloc: grid too large for the 4 MiB scratch (9 n3 n2 (n1/2+1 rounded up to 4) = "
+                 "%lld complex entries; at most %zu fit; every grid up to 32^3 fits)",
+                 (long long)(9 * g.Vs), kMaxSpectrum);
+        return set_error(COMBO_E_INVALID_ARG, msg);
+    }
 
     int prev = 0;
     if (cudaGetDevice(&prev) != cudaSuccess) return set_error(COMBO_E_CUDA, "combo_apply_G_noalloc: no CUDA device");
@@ -173,43 +221,11 @@ extern "C" int combo_apply_G_noalloc(int32_t device, void* stream, const int32_t
     double2* spec = reinterpret_cast<double2*>(s + kOffSpectrum);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-    // tables on the host stack, copied into the scratch
-    double2 htw[kMaxSide / 2 + (kMaxSide / 2 + 1) + 2 * kMaxSide];
-    double hs[6 * kMaxSide];
-    std::memset(htw, 0, sizeof(htw));
-    std::memset(hs, 0, sizeof(hs));
-    auto fill_tw = [](double2* t, int cnt, int denom) {
-        for (int k = 0; k < cnt; k++) {
-            const double ang = 2.0 * M_PI * (double)k / (double)denom;
-            t[k] = double2{std::cos(ang), -std::sin(ang)};
-        }
-    };
-    fill_tw(htw, g.M, g.M);
-    fill_tw(htw + kMaxSide / 2, g.M + 1, g.n1);
-    fill_tw(htw + kMaxSide / 2 + (kMaxSide / 2 + 1), g.n2, g.n2);
-    fill_tw(htw + kMaxSide / 2 + (kMaxSide / 2 + 1) + kMaxSide, g.n3, g.n3);
-    for (int j = 0; j < 3; j++) {
-        const double h = l[j] / n[j];
-        for (int x = 0; x < n[j]; x++) {
-            const bool nyq = (2 * x == n[j]);
-            double a, b;
-            if (kspace == COMBO_ROTATED) {
-                a = (2.0 / h) * std::sin(M_PI * (double)x / n[j]);
-                b = nyq ? 0.0 : std::cos(M_PI * (double)x / n[j]);
-            } else {
-                const int xs = (2 * x > n[j]) ? x - n[j] : x;
-                a = nyq ? 0.0 : 2.0 * M_PI * (double)xs / l[j];
-                b = 1.0;
-            }
-            hs[j * kMaxSide + x] = a;
-            hs[3 * kMaxSide + j * kMaxSide + x] = b;
-        }
-    }
-    // the scratch keeps the previous call's contents: clear what must start at zero
-    if (cudaMemsetAsync(sc, 0, sizeof(Scalars), st) != cudaSuccess ||
-        cudaMemcpyAsync(twM, htw, sizeof(htw), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(sa, hs, sizeof(hs), cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return set_error(COMBO_E_CUDA, "combo_apply_G_noalloc: copying the tables failed");
+    // the scratch keeps the previous call's contents: the set-up kernel
+    // clears the scalars (the spectrum and partials are overwritten in full)
+    k_noalloc_tables<<<1, kMaxSide, 0, st>>>(n[0], n[1], n[2], l[0], l[1], l[2], kspace, sc, twM, tw2, twy, twz, sa,
+                                             sb);
+    if (cudaGetLastError() != cudaSuccess) return set_error(COMBO_E_CUDA, "combo_apply_G_noalloc: set-up failed");
 
     const Plan pM = plan_for(g.M), py = plan_for(g.n2), pz = plan_for(g.n3);
     XfwdArgs<double, double> xf{};
@@ -248,7 +264,7 @@ extern "C" int combo_apply_G_noalloc(int32_t device, void* stream, const int32_t
     z.want_norm = 1;
     z.partial = part;
     z.sc = sc;
-    const int zblocks = ((g.nh + z.tx - 1) / z.tx) * g.n2 * 3;
+    const int zblocks = zpass_blocks(g, z.tx, sizeof(double2));  // the launcher's own block count
     if (zblocks > kMaxPartials) return set_error(COMBO_E_INVALID_ARG, "combo_apply_G_noalloc: grid too large");
     launch_zpass<double>(z, st);
     launch_ypass<double, true>(y, st);

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/combo.h"
+#include "async_copy.cuh"
 #include "combo_internal.cuh"
 
 using namespace combo;
@@ -43,6 +44,30 @@ static int fail(int code, const std::string& msg)
     } while (0)
 
 extern "C" const char* combo_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ allocation
+// Every device allocation of a solve, batch or server goes through
+// dev_malloc, which the fault-injection hook (combo_fault_inject_alloc) can
+// make fail the way cudaMalloc fails when the device is out of memory.
+static std::atomic<int64_t> g_alloc_countdown{-1};
+
+template <typename T> static cudaError_t dev_malloc(T** p, size_t bytes)
+{
+    int64_t c = g_alloc_countdown.load();
+    while (c >= 0 && !g_alloc_countdown.compare_exchange_weak(c, c - 1)) {
+    }
+    if (c == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+extern "C" int combo_fault_inject_alloc(int64_t after)
+{
+    g_alloc_countdown.store(after < 0 ? -1 : after);
+    return COMBO_OK;
+}
 
 // Lets other translation units of the library report an error message.
 int combo::set_error(int code, const char* msg)
@@ -107,6 +132,8 @@ extern "C" void combo_options_default(combo_options* o)
     o->nr_max_iter = 50;
     o->c_min = 1e-6;
     o->mu0 = 0.0;
+    o->theory = COMBO_FINITE_STRAIN;
+    o->wait_poll_cap = 0;
 }
 
 // ------------------------------------------------------------------ plans and tables
@@ -172,7 +199,7 @@ template <typename T> static int upload_tw(cx<T>** d, int n, int denom)
         h[t].x = (T)std::cos(ang);
         h[t].y = (T)(-std::sin(ang));
     }
-    CK(cudaMalloc(d, sizeof(cx<T>) * h.size()));
+    CK(dev_malloc(d, sizeof(cx<T>) * h.size()));
     CK(cudaMemcpy(*d, h.data(), sizeof(cx<T>) * h.size(), cudaMemcpyHostToDevice));
     return COMBO_OK;
 }
@@ -207,12 +234,12 @@ template <typename T> static int upload_symbols(DevTables<T>& t, const int n[3],
                 b[x] = (T)1;
             }
         }
-        CK(cudaMalloc(&t.sa[j], sizeof(T) * n[j]));
-        CK(cudaMalloc(&t.sb[j], sizeof(T) * n[j]));
+        CK(dev_malloc(&t.sa[j], sizeof(T) * n[j]));
+        CK(dev_malloc(&t.sb[j], sizeof(T) * n[j]));
         CK(cudaMemcpy(t.sa[j], a.data(), sizeof(T) * n[j], cudaMemcpyHostToDevice));
         CK(cudaMemcpy(t.sb[j], b.data(), sizeof(T) * n[j], cudaMemcpyHostToDevice));
         if (kspace == COMBO_STAGGERED) {
-            CK(cudaMalloc(&t.ph[j], sizeof(cx<T>) * n[j]));
+            CK(dev_malloc(&t.ph[j], sizeof(cx<T>) * n[j]));
             CK(cudaMemcpy(t.ph[j], ph.data(), sizeof(cx<T>) * n[j], cudaMemcpyHostToDevice));
         }
     }
@@ -377,6 +404,7 @@ template <typename T> struct Engine {
     bool zmap_ok[2] = {false, false}, ymap_ok[2] = {false, false};
     // launch-shape candidates chosen by the autotuner: x-forward, y, z, x-inverse
     int cfg_xf = 0, cfg_y = 0, cfg_z = 0, cfg_xi = 0;
+    uint32_t wait_cap = 0;  // poll cap of the bulk-copy waits (wait_cap_of; 0 = default)
     void bind_spec(void* s)
     {
         spec = (cx<T>*)s;
@@ -422,6 +450,7 @@ template <typename T> struct Engine {
         a.spec = spec;
         a.lines_per_block = lines;
         a.cfg = cfg_xi;
+        a.wait_cap = wait_cap;
         return a;
     }
     // y forward, z forward + projection + z inverse, y inverse
@@ -438,6 +467,7 @@ template <typename T> struct Engine {
         y.guard = guard;
         y.cfg = cfg_y;
         y.tmap = ymap_ok[cfg_y] ? &ymap[cfg_y] : nullptr;
+        y.wait_cap = wait_cap;
         if (pr) pr->begin(kbase);
         launch_ypass<T, false>(y, st);
         if (pr) pr->end();
@@ -459,6 +489,7 @@ template <typename T> struct Engine {
         z.guard = guard;
         z.cfg = cfg_z;
         z.tmap = zmap_ok[cfg_z] ? &zmap[cfg_z] : nullptr;
+        z.wait_cap = wait_cap;
         if (pr) pr->begin(kbase + 1);
         launch_zpass<T>(z, st);
         if (pr) pr->end();
@@ -466,7 +497,7 @@ template <typename T> struct Engine {
         launch_ypass<T, true>(y, st);
         if (pr) pr->end();
     }
-    int zblocks_p() const { return ((g.nh + txz - 1) / txz) * g.n2 * 3; }  // z-pass blocks (partials) per problem
+    int zblocks_p() const { return zpass_blocks(g, txz, sizeof(cx<T>)); }  // z-pass blocks (partials) per problem
     int zblocks() const { return zblocks_p() * g.nprob; }
     int xblocks() const { return xpass_grid(g, lines); }
     int xpartials() const { return std::max(xpass_grid(g, lines), xpass_partials_max(g)); }
@@ -920,6 +951,7 @@ static int check_options(combo_options& o)
     if (!(o.tol >= 0.0) || !(o.cg_tol >= 0.0)) return fail(COMBO_E_INVALID_ARG, "negative tolerance");
     if (o.nr_max_iter <= 0) o.nr_max_iter = 50;
     if (!(o.c_min >= 0.0 && o.c_min < 0.5)) return fail(COMBO_E_INVALID_ARG, "c_min outside [0, 0.5)");
+    if (o.wait_poll_cap < -1) return fail(COMBO_E_INVALID_ARG, "wait_poll_cap below -1");
     return COMBO_OK;
 }
 
@@ -979,6 +1011,7 @@ struct SolveBase {
     virtual Profiler& profiler() = 0;
     virtual void request_cancel() = 0;
     virtual int advance_steps(int32_t k) = 0;
+    virtual int advance_newton(int64_t min_ops) = 0;
     virtual int export_state(void* buf, int64_t* bytes) = 0;
     virtual int import_state(const void* buf, int64_t bytes) = 0;
 };
@@ -1041,6 +1074,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     std::vector<int32_t> iters, cg_iters;
     int64_t ops_done = 0;
     int64_t step_target = -1;  // advance_steps: stop between load steps once step reaches it
+    bool whole_newton = false;  // advance_newton: a reached limit stops only between Newton steps
     int error = 0;
 
     ~Solve() override
@@ -1128,23 +1162,24 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         const int kop = dfmg() ? COMBO_STAGGERED : opt.kspace;
         if ((rc = e64.init(g, hp.l, kop))) return rc;
         if ((rc = ec.init(g, hp.l, kop))) return rc;
-        CK(cudaMalloc(&d_phase, V));
-        CK(cudaMalloc(&d_v2b, 4 * V));
-        CK(cudaMalloc(&d_F, 8 * 9 * V));
-        CK(cudaMalloc(&d_spec, sizeof(double2) * 9 * g.Vs));
+        e64.wait_cap = ec.wait_cap = (opt.wait_poll_cap < 0) ? kWaitNone : (uint32_t)opt.wait_poll_cap;
+        CK(dev_malloc(&d_phase, V));
+        CK(dev_malloc(&d_v2b, 4 * V));
+        CK(dev_malloc(&d_F, 8 * 9 * V));
+        CK(dev_malloc(&d_spec, sizeof(double2) * 9 * g.Vs));
         CK(cudaMemsetAsync(d_spec, 0, sizeof(double2) * 9 * g.Vs, st));
         const int nbuf = std::max(std::max(e64.xpartials(), e64.zblocks()), std::max(ec.xpartials(), ec.zblocks()));
-        CK(cudaMalloc(&d_part, 8 * (size_t)nbuf));
-        CK(cudaMalloc(&d_sc, sizeof(Scalars) * B));
-        CK(cudaMalloc(&d_phpart, sizeof(double) * PHASE_GRID * PHASE_SUMS));
+        CK(dev_malloc(&d_part, 8 * (size_t)nbuf));
+        CK(dev_malloc(&d_sc, sizeof(Scalars) * B));
+        CK(dev_malloc(&d_phpart, sizeof(double) * PHASE_GRID * PHASE_SUMS));
         if (opt.solver == COMBO_NONLINEAR_CG) {
-            CK(cudaMalloc(&d_dir, sizeof(double) * 9 * (size_t)g.V));
+            CK(dev_malloc(&d_dir, sizeof(double) * 9 * (size_t)g.V));
             CK(cudaMemsetAsync(d_dir, 0, sizeof(double) * 9 * (size_t)g.V, st));
         }
         if (dfmg()) {
-            CK(cudaMalloc(&d_S, sizeof(double) * 72 * (size_t)g.V));
-            CK(cudaMalloc(&d_Pd, sizeof(double) * 9 * (size_t)g.V));
-            CK(cudaMalloc(&d_ba8, sizeof(double) * 24 * (size_t)std::max<int64_t>(nb, 1)));
+            CK(dev_malloc(&d_S, sizeof(double) * 72 * (size_t)g.V));
+            CK(dev_malloc(&d_Pd, sizeof(double) * 9 * (size_t)g.V));
+            CK(dev_malloc(&d_ba8, sizeof(double) * 24 * (size_t)std::max<int64_t>(nb, 1)));
             CK(cudaMemsetAsync(d_ba8, 0, sizeof(double) * 24 * (size_t)std::max<int64_t>(nb, 1), st));
         }
         CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars) * B, st));
@@ -1158,28 +1193,28 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                 mat[4 * b + 3] = hps[b].lam[1];
                 for (int64_t k = boff[b]; k < boff[b + 1]; k++) bprob[k] = b;
             }
-            CK(cudaMalloc(&d_mat, 8 * mat.size()));
-            CK(cudaMalloc(&d_dF, 8 * 9 * (size_t)B));
-            CK(cudaMalloc(&d_dv, 8 * (size_t)B));
-            CK(cudaMalloc(&d_bprob, 4 * bprob.size()));
+            CK(dev_malloc(&d_mat, 8 * mat.size()));
+            CK(dev_malloc(&d_dF, 8 * 9 * (size_t)B));
+            CK(dev_malloc(&d_dv, 8 * (size_t)B));
+            CK(dev_malloc(&d_bprob, 4 * bprob.size()));
             CK(cudaMemcpy(d_mat, mat.data(), 8 * mat.size(), cudaMemcpyHostToDevice));
             CK(cudaMemcpy(d_bprob, bprob.data(), 4 * bprob.size(), cudaMemcpyHostToDevice));
         }
         const size_t nbs = std::max<int64_t>(nb, 1);
-        CK(cudaMalloc(&d_bidx, 4 * nbs));
-        CK(cudaMalloc(&d_bN, 24 * nbs));
-        CK(cudaMalloc(&d_bc, 8 * nbs));
-        CK(cudaMalloc(&d_ba, 24 * nbs));
-        CK(cudaMalloc(&d_bP, 72 * nbs));
+        CK(dev_malloc(&d_bidx, 4 * nbs));
+        CK(dev_malloc(&d_bN, 24 * nbs));
+        CK(dev_malloc(&d_bc, 8 * nbs));
+        CK(dev_malloc(&d_ba, 24 * nbs));
+        CK(dev_malloc(&d_bP, 72 * nbs));
         if (newton()) {
-            CK(cudaMalloc(&d_bA, sizeof(Tc) * 45 * nbs));
-            CK(cudaMalloc(&d_rank, 4 * nbs));
-            CK(cudaMalloc(&d_bvox, 4 * nbs));
-            CK(cudaMalloc(&d_lofs, 4 * ((size_t)g.n2 * g.n3 + 1)));
-            CK(cudaMalloc(&d_tc, sizeof(Tc) * 10 * V));
-            CK(cudaMalloc(&d_x, sizeof(Tc) * 9 * V));
-            CK(cudaMalloc(&d_r, sizeof(Tc) * 9 * V));
-            CK(cudaMalloc(&d_p, sizeof(Tc) * 9 * V));
+            CK(dev_malloc(&d_bA, sizeof(Tc) * 45 * nbs));
+            CK(dev_malloc(&d_rank, 4 * nbs));
+            CK(dev_malloc(&d_bvox, 4 * nbs));
+            CK(dev_malloc(&d_lofs, 4 * ((size_t)g.n2 * g.n3 + 1)));
+            CK(dev_malloc(&d_tc, sizeof(Tc) * 10 * V));
+            CK(dev_malloc(&d_x, sizeof(Tc) * 9 * V));
+            CK(dev_malloc(&d_r, sizeof(Tc) * 9 * V));
+            CK(dev_malloc(&d_p, sizeof(Tc) * 9 * V));
         }
         e64.bind_spec(d_spec);
         ec.bind_spec(d_spec);
@@ -1658,7 +1693,8 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         int rc;
         while (true) {
             if (state == ST_DONE) return COMBO_OK;
-            if (ops_done >= limit) return COMBO_PENDING;
+            if (ops_done >= limit && (!whole_newton || state == ST_RESID || state == ST_STEP || state == ST_FP))
+                return COMBO_PENDING;
             if (cancel_requested) return error = fail(COMBO_E_CANCELLED, "solve cancelled");
             switch (state) {
                 case ST_STEP:
@@ -1936,7 +1972,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         bool needP = false;
         for (int b = 0; b < B; b++) needP = needP || rs[b].P_out;
         if (needP) {
-            CK(cudaMalloc(&P, 8 * 9 * (size_t)g.V));
+            CK(dev_malloc(&P, 8 * 9 * (size_t)g.V));
             Mat9 m{};
             k_eval_P<<<grid_for(g.V), 256, 0, st>>>(d_F, d_phase, d_v2b, d_bP, m, P, g.V, d_sc, d_mat, Vp,
                                                     linear() ? 1 : 0);
@@ -1981,6 +2017,15 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
 
     Profiler& profiler() override { return prof; }
     void request_cancel() override { cancel_requested = 1; }
+
+    int advance_newton(int64_t min_ops) override
+    {
+        if (min_ops <= 0) return fail(COMBO_E_INVALID_ARG, "advance_newton needs a positive operator count");
+        whole_newton = true;
+        const int rc = advance(min_ops);
+        whole_newton = false;
+        return rc;
+    }
 
     int advance_steps(int32_t k) override
     {
@@ -2144,7 +2189,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                 CK(cudaGetLastError());
             }
             double* P = dev ? r->P_out : nullptr;
-            if (!dev) CK(cudaMalloc(&P, 8 * 9 * V));
+            if (!dev) CK(dev_malloc(&P, 8 * 9 * V));
             Mat9 m{};
             m.v[0] = hp.mu[0];
             m.v[1] = hp.mu[1];
@@ -2238,6 +2283,12 @@ extern "C" int combo_solve_advance(combo_solve_state* s, int64_t max_ops)
 {
     if (!s) return fail(COMBO_E_INVALID_ARG, "null solve");
     return s->impl->advance(max_ops);
+}
+
+extern "C" int combo_solve_advance_newton(combo_solve_state* s, int64_t min_operator)
+{
+    if (!s) return fail(COMBO_E_INVALID_ARG, "null solve");
+    return s->impl->advance_newton(min_operator);
 }
 
 extern "C" int combo_solve_advance_steps(combo_solve_state* s, int32_t k)
@@ -2437,14 +2488,14 @@ template <typename T> static int apply_G_impl(combo_ctx* ctx, const int32_t n[3]
         dX = const_cast<double*>(X);
         dY = Y;
     } else {
-        CKC(cudaMalloc(&dX, 72 * V));
-        CKC(cudaMalloc(&dY, 72 * V));
+        CKC(dev_malloc(&dX, 72 * V));
+        CKC(dev_malloc(&dY, 72 * V));
         CKC(cudaMemcpyAsync(dX, X, 72 * V, cudaMemcpyHostToDevice, st));
     }
-    CKC(cudaMalloc(&spec, sizeof(cx<T>) * 9 * g.Vs));
+    CKC(dev_malloc(&spec, sizeof(cx<T>) * 9 * g.Vs));
     CKC(cudaMemsetAsync(spec, 0, sizeof(cx<T>) * 9 * g.Vs, st));
-    CKC(cudaMalloc(&part, 8 * (size_t)std::max(e.xblocks(), e.zblocks())));
-    CKC(cudaMalloc(&sc, sizeof(Scalars)));
+    CKC(dev_malloc(&part, 8 * (size_t)std::max(e.xblocks(), e.zblocks())));
+    CKC(dev_malloc(&sc, sizeof(Scalars)));
     CKC(cudaMemsetAsync(sc, 0, sizeof(Scalars), st));
     e.bind_spec(spec);
     // (the Krylov word type only matters for the solver modes of the x-passes)
@@ -2519,8 +2570,8 @@ extern "C" int combo_neohooke_eval(combo_ctx* ctx, const double F[9], double mu,
     CK(cudaSetDevice(ctx->device));
     double* d = nullptr;
     int* dok = nullptr;
-    CK(cudaMalloc(&d, 8 * (9 + 9 + 81)));
-    CK(cudaMalloc(&dok, 4));
+    CK(dev_malloc(&d, 8 * (9 + 9 + 81)));
+    CK(dev_malloc(&dok, 4));
     int rc = COMBO_OK, ok = 0;
     double hP[9], hA[81];
     if (cudaMemcpyAsync(d, F, 72, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) rc = COMBO_E_CUDA;
@@ -2562,9 +2613,9 @@ extern "C" int combo_laminate_eval(combo_ctx* ctx, const double F[9], const doub
     double* d = nullptr;
     int32_t* didx = nullptr;
     Scalars* dsc = nullptr;
-    CK(cudaMalloc(&d, sizeof h));
-    CK(cudaMalloc(&didx, 4));
-    CK(cudaMalloc(&dsc, sizeof(Scalars)));
+    CK(dev_malloc(&d, sizeof h));
+    CK(dev_malloc(&didx, 4));
+    CK(dev_malloc(&dsc, sizeof(Scalars)));
     int rc = COMBO_OK;
     const int32_t zero = 0;
     Scalars sc{};
@@ -2626,8 +2677,8 @@ extern "C" int combo_df_log(combo_ctx* ctx, const double* x, double* y, int64_t 
     if (n == 0) return COMBO_OK;
     CK(cudaSetDevice(ctx->device));
     double *dx = nullptr, *dy = nullptr;
-    CK(cudaMalloc(&dx, 8 * n));
-    CK(cudaMalloc(&dy, 8 * n));
+    CK(dev_malloc(&dx, 8 * n));
+    CK(dev_malloc(&dy, 8 * n));
     int rc = COMBO_OK;
     if (cudaMemcpyAsync(dx, x, 8 * n, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) rc = COMBO_E_CUDA;
     if (!rc) {

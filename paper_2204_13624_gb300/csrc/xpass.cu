@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
                 } else if constexpr (std::is_same<T, df32>::value) {
                     float G[9], m;
                     if (!nh_stress_df(F, mu[ph], lam[ph], o, G, m)) {
-                        raise_status(sc, COMBO_E_INADMISSIBLE);
+                        raise_status(sc, finite9(F) ? COMBO_E_INADMISSIBLE : COMBO_E_NAN);
 #pragma unroll
                         for (int c = 0; c < 9; c++) {
                             o[c] = df32(0.f, 0.f);
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
                 } else {
                     double P[9], G[9], m;
                     if (!nh_stress(F, mu[ph], lam[ph], P, G, m)) {
-                        raise_status(sc, COMBO_E_INADMISSIBLE);
+                        raise_status(sc, finite9(F) ? COMBO_E_INADMISSIBLE : COMBO_E_NAN);
 #pragma unroll
                         for (int c = 0; c < 9; c++) P[c] = G[c] = 0.0;
                         m = 0.0;

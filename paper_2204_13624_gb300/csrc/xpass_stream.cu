@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(xinv_threads<M, LB>()) k_xinv_stream(XinvArgs<
             fence_proxy_async();
             issue(grp + gp, s ^ 1);
         }
-        const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1));
+        const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1), wait_cap_of(a.wait_cap));
         if (__syncthreads_or(!ok)) {
             timed_out = true;
             break;
@@ -158,7 +158,12 @@ __global__ void __launch_bounds__(xinv_threads<M, LB>()) k_xinv_stream(XinvArgs<
     if (timed_out) {
         if (threadIdx.x == 0) {
             raise_status(scp, COMBO_E_TIMEOUT);
-            mbar_wait_bounded(&bar[it & 1 ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            // copies possibly in flight: the group waited on and, if it was
+            // issued, the prefetch of the next one (the block's shared memory
+            // must outlive them)
+            const int s = it & 1;
+            mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1));
+            if (pj + (it + 1) * gp < ngroups) mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
         }
         return;
     }

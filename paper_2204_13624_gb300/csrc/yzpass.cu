@@ -286,6 +286,15 @@ template <typename T> constexpr int ztx_const(int n)
 }
 template <typename T> int ztx_fast(int n) { return ztx_const<T>(n); }
 
+// z-pass blocks per problem of a launch that is not TMA-tiled (a launch
+// that accumulates norm partials writes one per block): the power-of-two
+// kernels fix their tile width by the line length, the generic one takes tx
+int zpass_blocks(const GridDims& g, int tx, size_t cxbytes)
+{
+    const int t = fast_size(g.n3p) ? (cxbytes == 8 ? ztx_const<float>(g.n3p) : ztx_const<double>(g.n3p)) : tx;
+    return ((g.nh + t - 1) / t) * g.n2 * 3;
+}
+
 int zpass_tx(int n, size_t cxbytes)
 {
     if (fast_size(n)) return cxbytes == 8 ? ztx_fast<float>(n) : ztx_fast<double>(n);
@@ -339,6 +348,7 @@ template <typename T, int N> static void zpass_fast_launch(const ZArgs<T>& a, cu
 {
     constexpr int TX = ztx_const<T>(N);
     dim3 grid((a.g.nh + TX - 1) / TX, a.g.n2, 3 * a.g.nprob);
+    static_assert(sizeof(cx<T>) != 8 || TX == ztx_const<float>(N), "zpass_blocks tile width");
     const size_t sm = (size_t)3 * N * TX * sizeof(cx<T>) + 64 * sizeof(double);
     static bool attr = false;
     allow_smem(k_zpass_fast<T, N, TX>, attr);

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL)
             bulk_wait_read_all();  // the store of the previous tile has left buffer s ^ 1
             issue(tn, s ^ 1);
         }
-        const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1));
+        const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1), wait_cap_of(a.wait_cap));
         if (__syncthreads_or(!ok)) {
             timed_out = true;
             break;
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(TX * FastPlan<N>::TPL)
             bulk_wait_read_all();  // the store of the previous tile has left buffer s ^ 1
             issue(tn, s ^ 1);
         }
-        const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1));
+        const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1), wait_cap_of(a.wait_cap));
         if (__syncthreads_or(!ok)) {
             timed_out = true;
             break;

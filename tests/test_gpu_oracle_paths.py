@@ -1,0 +1,146 @@
+"""GPU results against the FP64 oracle on the paths that earlier parity
+tests only compared with the library's own solves:
+
+* the benchmark's problem family (random balls, contrast 100, uniaxial
+  stretch to Fbar11 = 1.10; Sec. 6.1 Neo-Hookean phases) solved to
+  convergence on a 64^3 grid in all three precision forms, against the
+  oracle's Newton-CG solve at tol 1e-10;
+* requests served by the request loop (concurrent slots, mixed grids) and
+  problems solved in a stacked batch, each compared element by element with
+  the oracle: after equal iterations in FP64, and converged in the refined
+  double-float form.
+
+Tolerances (max-abs error relative to the max-abs reference value), as in
+test_gpu_parity.py: FP64 fields after equal iterations <= 1e-10, Pbar <= 1e-9;
+converged FP64 (both sides at tol 1e-10) Pbar <= 1e-9; converged refined
+forms Pbar <= 1e-5, local F <= 1e-4.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cb():
+    from paper_2204_13624_gb300 import build, combo
+
+    build.build()
+    combo.load()
+    return combo
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+# ------------------------------------------------ the benchmark's family, converged
+@pytest.fixture(scope="module")
+def contrast100(orc):
+    """spheres_256 scaled to 64^3 (radius 3 voxels; vf 0.15, the largest
+    the 2-voxel gap lets random sequential addition place at this radius),
+    contrast 100, Fbar11 = 1.10 in 2 load steps; the oracle's Newton-CG
+    solve at tol 1e-10."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.spheres_256(n=64, n_steps=2, vf=0.15)
+    r = orc.solve(p, dict(solver=1, tol=1e-10, cg_tol=1e-3))
+    assert np.all(r["resid"] <= 1e-10)
+    return p, r
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_contrast100_refined_against_oracle(cb, contrast100, prec):
+    p, r = contrast100
+    g = cb.solve(p, solver=1, precision=prec, tol=1e-8)
+    assert g["steps_done"] == 2 and np.all(g["resid"] <= 1e-8)
+    assert rel(g["Pbar"], r["Pbar"]) < 1e-5
+    assert rel(g["F"], r["F"]) < 1e-4
+    assert rel(g["P"], r["P"]) < 1e-4
+
+
+def test_contrast100_fp64_against_oracle(cb, contrast100):
+    p, r = contrast100
+    g = cb.solve(p, solver=1, precision=cb.FP64, tol=1e-10, cg_tol=1e-3)
+    assert g["steps_done"] == 2 and np.all(g["resid"] <= 1e-10)
+    assert rel(g["Pbar"], r["Pbar"]) < 1e-9
+    assert rel(g["F"], r["F"]) < 1e-8
+
+
+# ------------------------------------------------ served and batched results
+def served_problems():
+    """Two requests on different grids: random balls on a ragged grid, and
+    unstructured random boxels (random c+, N) on another."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    Fb = np.eye(3) + np.diag([0.04, -0.02, 0.01])
+    Fb[0, 1] = 0.03
+    a = ms.random_spheres((24, 16, 32), 4.0, 0.1, 101, 10.0, Fb, 2)
+    b = ms.random_boxels((16, 18, 12), seed=202, contrast=20.0, Fbar=Fb.T, n_steps=1)
+    return [a, b]
+
+
+def batch_pair():
+    """Two problems of one grid solved as one stacked batch."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    Fb = np.eye(3) + np.diag([0.05, 0.0, -0.01])
+    Fb[1, 2] = -0.04
+    a = ms.random_spheres((16, 16, 16), 3.5, 0.12, 303, 10.0, Fb, 2)
+    b = ms.random_boxels((16, 16, 16), seed=404, contrast=5.0, Fbar=np.eye(3) + 0.02, n_steps=1)
+    return [a, b]
+
+
+FIXED = dict(solver=1, fixed_iterations=2, cg_fixed_iterations=10)
+
+
+def test_served_fp64_equal_iterations_against_oracle(cb, orc):
+    probs = served_problems()
+    srv = cb.Server(max_slots=2, keep_fields=True)
+    try:
+        tickets = [srv.submit(p, precision=cb.FP64, **FIXED) for p in probs]
+        served = [srv.wait(t, timeout_ms=120000) for t in tickets]
+    finally:
+        srv.close()
+    for p, g in zip(probs, served):
+        r = orc.solve(p, dict(solver=1, fixed_iter=2, cg_fixed_iter=10))
+        assert rel(g["F"], r["F"]) < 1e-10
+        assert rel(g["P"], r["P"]) < 1e-10
+        assert rel(g["Pbar"], r["Pbar"]) < 1e-9
+
+
+def test_served_refined_converged_against_oracle(cb, orc):
+    probs = served_problems()
+    srv = cb.Server(max_slots=2, keep_fields=True)
+    try:
+        tickets = [srv.submit(p, precision=cb.FP32_REFINED_DF, solver=1, tol=1e-8) for p in probs]
+        served = [srv.wait(t, timeout_ms=120000) for t in tickets]
+    finally:
+        srv.close()
+    for p, g in zip(probs, served):
+        r = orc.solve(p, dict(solver=1, tol=1e-10, cg_tol=1e-4))
+        assert g["steps_done"] == p["n_steps"] and np.all(g["resid"] <= 1e-8)
+        assert rel(g["Pbar"], r["Pbar"]) < 1e-5
+        assert rel(g["F"], r["F"]) < 1e-4
+
+
+def test_batched_fp64_equal_iterations_against_oracle(cb, orc):
+    probs = batch_pair()
+    out = cb.solve_batch(probs, precision=cb.FP64, **FIXED)
+    for p, g in zip(probs, out):
+        r = orc.solve(p, dict(solver=1, fixed_iter=2, cg_fixed_iter=10))
+        assert rel(g["F"], r["F"]) < 1e-10
+        assert rel(g["P"], r["P"]) < 1e-10
+        assert rel(g["Pbar"], r["Pbar"]) < 1e-9
+
+
+def test_batched_refined_converged_against_oracle(cb, orc):
+    probs = batch_pair()
+    out = cb.solve_batch(probs, precision=cb.FP32_REFINED_DF, solver=1, tol=1e-8)
+    for p, g in zip(probs, out):
+        r = orc.solve(p, dict(solver=1, tol=1e-10, cg_tol=1e-4))
+        assert g["steps_done"] == p["n_steps"] and np.all(g["resid"] <= 1e-8)
+        assert rel(g["Pbar"], r["Pbar"]) < 1e-5
+        assert rel(g["F"], r["F"]) < 1e-4

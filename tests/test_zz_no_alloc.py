@@ -5,8 +5,10 @@ inside a memory pool or arena it does not own, loops that must not
 allocate): its scratch is one fixed device array inside libcombo.so.  This
 checks it through the C ABI against combo_apply_G, the allocating entry
 point, on two calls in a row, within the FP64 parity tolerance used by the
-other Green-operator tests.  The file name sorts last so that a run stopping
-at the first failure has run every other test before it.
+other Green-operator tests, and against the oracle's Green operator (Sec. 3,
+Eq. Gamma0: explicit 9x9 symbol matrices per frequency, its own complex FFT).
+The file name sorts last so that a run stopping at the first failure has run
+every other test before it.
 """
 import numpy as np
 import pytest
@@ -42,6 +44,38 @@ def test_noalloc_matches_allocating_entry_point(cb, n, kspace):
         assert abs(ss - ss_ref) <= 1e-11 * ss_ref
 
 
+@pytest.mark.parametrize("kspace", [0, 1])
+def test_noalloc_matches_the_oracle(cb, kspace):
+    """Y = G[X] of the entry point against the oracle's Green operator on a
+    ragged grid (odd, mixed 2^a 3^b sides), on two calls in a row."""
+    import torch
+
+    import oracle
+
+    n = (24, 9, 16)
+    V = n[0] * n[1] * n[2]
+    l = (1.0, 0.7, 1.2)
+    rng = np.random.default_rng(11 + kspace)
+    Xh = rng.standard_normal((9, V))
+    ref, _ = oracle.apply_G(Xh.reshape(9, n[2], n[1], n[0]), n, l, kspace)
+    ref = ref.reshape(9, V)
+    X = torch.from_numpy(Xh).cuda()
+    for _ in range(2):
+        Y = torch.full_like(X, float("nan"))
+        cb.apply_G_noalloc(X, Y, n, l, kspace)
+        torch.cuda.synchronize()
+        assert np.max(np.abs(Y.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_noalloc_rejects_the_staggered_grid(cb):
+    import torch
+
+    X = torch.zeros((9, 8 * 8 * 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(cb.ComboError) as e:
+        cb.apply_G_noalloc(X, X, (8, 8, 8), kspace=cb.STAGGERED)
+    assert e.value.code == -1 and "kspace" in str(e.value)
+
+
 def test_noalloc_allocates_nothing_and_works_in_place(cb):
     import torch
 
@@ -73,6 +107,6 @@ def test_noalloc_rejects_oversized_grids(cb):
     X = torch.zeros((9, 64 * 64 * 64), dtype=torch.float64, device="cuda")
     with pytest.raises(cb.ComboError) as e:
         cb.apply_G_noalloc(X, X, (64, 64, 64))
-    assert e.value.code == -1 and "too large" in str(e.value)
+    assert e.value.code == -1 and "too large" in str(e.value) and "259520" in str(e.value)
     with pytest.raises(cb.ComboError):
         cb.apply_G_noalloc(X, X, (128, 4, 4))
