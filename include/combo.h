@@ -262,18 +262,22 @@ int combo_solve(combo_ctx* ctx, const combo_problem* p, const combo_options* o, 
 
 /*
  * Batched solve (no counterpart in the paper, which solves one RVE at a time;
- * each problem is the problem of Sec. 2): n_problems independent problems
- * on the same grid n and cell size l, each with its own phase field, boxels,
- * materials, Fbar and number of load steps, solved together with the
- * Newton-CG solver (Sec. 3).  The problems are stacked along z into one grid,
- * so every kernel launch works on the pencils of all of them (the x-passes
- * give each problem its own blocks and reductions, the z-passes transform
- * each problem's segment); CG scalars, stopping tests, step halving and
- * results are per problem, and a problem that has converged is masked out
- * of the launches until the others finish the load step.
+ * each problem is the problem of Sec. 2): n_problems independent problems,
+ * each with its own grid n, cell size l, phase field, boxels, materials,
+ * Fbar and number of load steps, solved together with the Newton-CG solver
+ * (Sec. 3).  Problems of equal grid and cell size are stacked along z into
+ * one grid (a class), so every kernel launch works on the pencils of all of
+ * them (the x-passes give each problem its own blocks and reductions, the
+ * z-passes transform each problem's segment).  With several classes, every
+ * pass of an operator application -- laminate solves, x-forward, y, z with
+ * the Green operator, y inverse, x-inverse -- is one persistent launch over
+ * a device table of (class, block) work items of all classes, and the CG
+ * loop replays from a captured CUDA graph.  CG scalars, stopping tests, step
+ * halving and results are per problem, and a problem that has converged is
+ * masked out of the launches until the others finish the load step.
  *   problems[n_problems], results[n_problems]: as for combo_solve (each
  *   result's mem, pointers and sizes refer to its own problem).
- *   Errors: COMBO_E_INVALID_ARG for unequal grids or the fixed-point solver
+ *   Errors: COMBO_E_INVALID_ARG for the fixed-point or nonlinear-CG solver
  *   with n_problems > 1; a failing problem fails the batch and the message
  *   names it.  n_problems == 1 is combo_solve.
  */

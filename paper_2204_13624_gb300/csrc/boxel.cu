@@ -314,12 +314,13 @@ __device__ __forceinline__ int nr_loop(LE& e, double a[3], const double m[3], do
 // residual down to its rounding level, then the FP64 residual decides
 // convergence (and takes the last step if needed), so the stopping test and
 // the returned state are those of the FP64 form.
-template <typename Tc, bool DFM>
-__global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
+// (body of block vb of 128 boxels; a grouped launch over several grids
+// calls it once per work item)
+template <typename Tc, bool DFM> __device__ __forceinline__ void boxel_body(const BoxelArgs<Tc>& A, int vb)
 {
     __shared__ double red[64];
     __shared__ int same_problem;
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b = (int64_t)vb * blockDim.x + threadIdx.x;
     // the problem of this boxel (stacked problems: boxels in problem order)
     const int pb = (A.bprob && b < A.nb) ? A.bprob[b] : 0;
     Scalars* sc = A.sc + pb;
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
     }
     // counters: one atomic per block when its boxels share a problem
     if (threadIdx.x == 0) {
-        const int64_t first = (int64_t)blockIdx.x * blockDim.x;
+        const int64_t first = (int64_t)vb * blockDim.x;
         const int64_t last = min(first + (int64_t)blockDim.x, A.nb) - 1;
         same_problem = (!A.bprob || A.bprob[first] == A.bprob[last]) ? 1 : 0;
     }
@@ -474,7 +475,7 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
         __syncthreads();
         const double s3 = block_sum(nev, red);
         if (threadIdx.x == 0) {
-            Scalars* s0 = A.sc + (A.bprob ? A.bprob[(int64_t)blockIdx.x * blockDim.x] : 0);
+            Scalars* s0 = A.sc + (A.bprob ? A.bprob[(int64_t)vb * blockDim.x] : 0);
             atomicAdd(&s0->nr_iters, (unsigned long long)s1);
             atomicAdd(&s0->n_backproj, (unsigned long long)s2);
             atomicAdd(&s0->n_lam, (unsigned long long)s3);
@@ -486,6 +487,11 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
     }
 }
 
+template <typename Tc, bool DFM> __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
+{
+    boxel_body<Tc, DFM>(A, blockIdx.x);
+}
+
 // Infinitesimal-strain composite boxel in closed form (cheat sheet of the
 // appendix, right column), |N| = 1:
 //   Delta = N . (C+/c+ + C-/c-) . N = (mu+/c+ + mu-/c-) I + ((lam+ + mu+)/c+ + (lam- + mu-)/c-) N N^T,
@@ -493,11 +499,11 @@ __global__ void __launch_bounds__(128) k_boxel(BoxelArgs<Tc> A)
 //   eps+- = eps +- sym(a (x) N) / c+-,  sigma_box = c+ sigma+ + c- sigma-,
 //   C_box = (c+ C+ + c- C-) - dC (N (x) Delta^{-1} (x) N) dC  (packed, in Tc).
 // The tangent reuses TanPhase with G = I, g = N, m = mu, which is C.
-template <typename Tc> __global__ void __launch_bounds__(128) k_boxel_linear(BoxelArgs<Tc> A)
+template <typename Tc> __device__ __forceinline__ void boxel_linear_body(const BoxelArgs<Tc>& A, int vb)
 {
     __shared__ double red[32];
     __shared__ int same_problem;
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b = (int64_t)vb * blockDim.x + threadIdx.x;
     const int pb = (A.bprob && b < A.nb) ? A.bprob[b] : 0;
     Scalars* sc = A.sc + pb;
     double nev = 0.0;
@@ -586,7 +592,7 @@ template <typename Tc> __global__ void __launch_bounds__(128) k_boxel_linear(Box
         }
     }
     if (threadIdx.x == 0) {
-        const int64_t first = (int64_t)blockIdx.x * blockDim.x;
+        const int64_t first = (int64_t)vb * blockDim.x;
         const int64_t last = min(first + (int64_t)blockDim.x, A.nb) - 1;
         same_problem = (!A.bprob || A.bprob[first] == A.bprob[last]) ? 1 : 0;
     }
@@ -594,10 +600,15 @@ template <typename Tc> __global__ void __launch_bounds__(128) k_boxel_linear(Box
     if (same_problem) {
         const double s3 = block_sum(nev, red);
         if (threadIdx.x == 0)
-            atomicAdd(&(A.sc + (A.bprob ? A.bprob[(int64_t)blockIdx.x * blockDim.x] : 0))->n_lam, (unsigned long long)s3);
+            atomicAdd(&(A.sc + (A.bprob ? A.bprob[(int64_t)vb * blockDim.x] : 0))->n_lam, (unsigned long long)s3);
     } else if (nev > 0.0) {
         atomicAdd(&sc->n_lam, (unsigned long long)nev);
     }
+}
+
+template <typename Tc> __global__ void __launch_bounds__(128) k_boxel_linear(BoxelArgs<Tc> A)
+{
+    boxel_linear_body<Tc>(A, blockIdx.x);
 }
 
 template <typename Tc> void launch_boxel(const BoxelArgs<Tc>& a, cudaStream_t st)
@@ -616,6 +627,44 @@ template <typename Tc> void launch_boxel(const BoxelArgs<Tc>& a, cudaStream_t st
     }
     k_boxel<Tc, false><<<grid, 128, 0, st>>>(a);
 }
+
+// grouped: items of 128 boxels of several grids' boxel lists
+template <typename Tc, bool DFM, bool LIN>
+__global__ void __launch_bounds__(128)
+    k_group_boxel(const BoxelArgs<Tc>* __restrict__ args, const int* __restrict__ vstart, int nd)
+{
+    const int total = __ldg(vstart + nd);
+    for (int v = blockIdx.x; v < total; v += gridDim.x) {
+        const int d = group_of(vstart, nd, v);
+        if constexpr (LIN)
+            boxel_linear_body<Tc>(args[d], v - __ldg(vstart + d));
+        else
+            boxel_body<Tc, DFM>(args[d], v - __ldg(vstart + d));
+        __syncthreads();  // the next item reuses the block's shared sums
+    }
+}
+
+template <typename Tc> void launch_group_boxel(const GroupTab<BoxelArgs<Tc>>& t, bool dfloat, bool linear,
+                                               cudaStream_t st)
+{
+    if (t.total <= 0) return;
+    if (linear) {
+        auto k = k_group_boxel<Tc, false, true>;
+        k<<<group_grid((const void*)k, 128, 0, t.total), 128, 0, st>>>(t.args, t.vstart, t.nd);
+        return;
+    }
+    if constexpr (std::is_same<Tc, float>::value) {
+        if (dfloat) {
+            auto k = k_group_boxel<Tc, true, false>;
+            k<<<group_grid((const void*)k, 128, 0, t.total), 128, 0, st>>>(t.args, t.vstart, t.nd);
+            return;
+        }
+    }
+    auto k = k_group_boxel<Tc, false, false>;
+    k<<<group_grid((const void*)k, 128, 0, t.total), 128, 0, st>>>(t.args, t.vstart, t.nd);
+}
+template void launch_group_boxel<float>(const GroupTab<BoxelArgs<float>>&, bool, bool, cudaStream_t);
+template void launch_group_boxel<double>(const GroupTab<BoxelArgs<double>>&, bool, bool, cudaStream_t);
 
 // Doubly-fine material grid (App. A): the laminate of every sub-cell l of
 // every composite boxel, at F_sub(c, l) (the cell's diagonal, the staggered

@@ -81,14 +81,43 @@ struct GridDims {
     int n3p;     // z planes of one problem
 };
 
-// x-pass grids give every problem the same number of blocks gp: block ->
-// (problem b, index j within the problem's blocks)
-__device__ __forceinline__ void prob_block(const GridDims& g, int& b, int& j, int& gp)
+// x-pass grids give every problem the same number of blocks gp: block vb of
+// vg -> (problem b, index j within the problem's blocks)
+__device__ __forceinline__ void prob_block(const GridDims& g, int vb, int vg, int& b, int& j, int& gp)
 {
-    gp = (int)gridDim.x / g.nprob;
-    b = (int)blockIdx.x / gp;
-    j = (int)blockIdx.x - b * gp;
+    gp = vg / g.nprob;
+    b = vb / gp;
+    j = vb - b * gp;
 }
+
+// Block index of a pass body: blockIdx / gridDim of a launch of its own, or
+// one work item of a grid in a grouped launch over several grids.
+struct VBlock {
+    int x, y, z, gx, gy, gz;
+    __device__ __forceinline__ static VBlock of_launch()
+    {
+        return VBlock{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+                      (int)gridDim.x,  (int)gridDim.y,  (int)gridDim.z};
+    }
+    // item l of a gx x gy x gz grid, x fastest
+    __device__ __forceinline__ static VBlock of_item(int l, int gx, int gy, int gz)
+    {
+        return VBlock{l % gx, (l / gx) % gy, l / (gx * gy), gx, gy, gz};
+    }
+    __device__ __forceinline__ int linear() const { return x + gx * (y + gy * z); }
+};
+
+// Descriptor of item v of a grouped launch (few descriptors: a linear scan)
+__device__ __forceinline__ int group_of(const int* __restrict__ vstart, int nd, int v)
+{
+    int d = 0;
+    while (d + 1 < nd && v >= __ldg(vstart + d + 1)) d++;
+    return d;
+}
+
+// Persistent-grid size of a grouped launch: as many blocks as fit on the
+// device at once, at most one per item
+int group_grid(const void* kernel, int threads, size_t smem, int items);
 
 // Solver scalars that live on the device between kernels.
 struct Scalars {
@@ -462,6 +491,30 @@ template <typename T> struct ZArgs {
     uint32_t wait_cap;  // poll cap of the tile waits (wait_cap_of: 0 = default)
 };
 
+// Grouped launches: one persistent launch runs the work items of several
+// grids (a batch of problems on different grids).  Descriptor d holds the
+// arguments of one grid, args[d]; its items are [vstart[d], vstart[d + 1]),
+// item l of d standing for block l of the launch that grid would have had
+// on its own (y / z passes: a dims[2d] x dims[2d + 1] x gz grid, x fastest),
+// so per-problem partial sums, last-block reductions and results are those
+// of that launch.  smem: the largest shared memory of any descriptor.
+template <typename A> struct GroupTab {
+    const A* args = nullptr;   // [nd] (device)
+    const int* vstart = nullptr;  // [nd + 1] (device)
+    const int* dims = nullptr;    // [2 nd] (device; y / z passes)
+    int nd = 0, total = 0;
+    size_t smem = 0;
+};
+template <typename T, typename Tc> void launch_group_xfwd(const GroupTab<XfwdArgs<T, Tc>>& t, bool tangent, int guard,
+                                                          cudaStream_t st);
+template <typename T, typename Tc> void launch_group_xinv(const GroupTab<XinvArgs<T, Tc>>& t, int guard,
+                                                          cudaStream_t st);
+template <typename T, bool INV> void launch_group_ypass(const GroupTab<YArgs<T>>& t, cudaStream_t st);
+template <typename T> void launch_group_zpass(const GroupTab<ZArgs<T>>& t, cudaStream_t st);
+// item grids and shared memory of one descriptor of a grouped y / z pass
+void ypass_group_shape(const GridDims& g, int tx, size_t cxbytes, int& gx, int& gy, int& gz, size_t& smem);
+void zpass_group_shape(const GridDims& g, int tx, size_t cxbytes, int& gx, int& gy, int& gz, size_t& smem);
+
 template <typename T, typename Tc> void launch_xfwd(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st);
 template <typename T, typename Tc> void launch_xinv(const XinvArgs<T, Tc>& a, int guard, cudaStream_t st);
 template <typename T, bool INV> void launch_ypass(const YArgs<T>& a, cudaStream_t st);
@@ -607,6 +660,10 @@ template <typename Tc> struct BoxelArgs {
     int n1, n2, n3;
 };
 template <typename Tc> void launch_boxel(const BoxelArgs<Tc>& a, cudaStream_t st);
+// grouped: items of 128 boxels ((nb + 127) / 128 per descriptor); every
+// descriptor has the same form (dfloat, linear)
+template <typename Tc> void launch_group_boxel(const GroupTab<BoxelArgs<Tc>>& t, bool dfloat, bool linear,
+                                               cudaStream_t st);
 void launch_boxel_dfmg(const BoxelArgs<double>& a, cudaStream_t st);
 
 }  // namespace combo

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <condition_variable>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <tuple>
 #include <atomic>
@@ -453,9 +454,7 @@ template <typename T> struct Engine {
         a.wait_cap = wait_cap;
         return a;
     }
-    // y forward, z forward + projection + z inverse, y inverse
-    void yz(Scalars* sc, int guard, bool want_norm, double* partial, cudaStream_t st, Profiler* pr = nullptr,
-            int kbase = 0) const
+    YArgs<T> yargs(Scalars* sc, int guard) const
     {
         YArgs<T> y{};
         y.g = g;
@@ -468,9 +467,10 @@ template <typename T> struct Engine {
         y.cfg = cfg_y;
         y.tmap = ymap_ok[cfg_y] ? &ymap[cfg_y] : nullptr;
         y.wait_cap = wait_cap;
-        if (pr) pr->begin(kbase);
-        launch_ypass<T, false>(y, st);
-        if (pr) pr->end();
+        return y;
+    }
+    ZArgs<T> zargs(Scalars* sc, int guard, bool want_norm, double* partial) const
+    {
         ZArgs<T> z{};
         z.g = g;
         z.plan = pz;
@@ -490,6 +490,17 @@ template <typename T> struct Engine {
         z.cfg = cfg_z;
         z.tmap = zmap_ok[cfg_z] ? &zmap[cfg_z] : nullptr;
         z.wait_cap = wait_cap;
+        return z;
+    }
+    // y forward, z forward + projection + z inverse, y inverse
+    void yz(Scalars* sc, int guard, bool want_norm, double* partial, cudaStream_t st, Profiler* pr = nullptr,
+            int kbase = 0) const
+    {
+        const YArgs<T> y = yargs(sc, guard);
+        if (pr) pr->begin(kbase);
+        launch_ypass<T, false>(y, st);
+        if (pr) pr->end();
+        const ZArgs<T> z = zargs(sc, guard, want_norm, partial);
         if (pr) pr->begin(kbase + 1);
         launch_zpass<T>(z, st);
         if (pr) pr->end();
@@ -1074,6 +1085,11 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     std::vector<int32_t> iters, cg_iters;
     int64_t ops_done = 0;
     int64_t step_target = -1;  // advance_steps: stop between load steps once step reaches it
+    // member of a batch over several grids (MixSolve): batch-form per-problem
+    // arrays even for one problem, scalars in the batch's shared array, no
+    // launch-shape tuning (the batch runs grouped launches)
+    bool member = false;
+    Scalars* ext_sc = nullptr;
     bool whole_newton = false;  // advance_newton: a reached limit stops only between Newton steps
     int error = 0;
 
@@ -1097,7 +1113,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         cudaFree(d_r);
         cudaFree(d_p);
         cudaFree(d_part);
-        cudaFree(d_sc);
+        if (!ext_sc) cudaFree(d_sc);
         cudaFree(d_phpart);
         cudaFree(d_dir);
         cudaFree(d_S);
@@ -1132,7 +1148,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         prof.st = st;
         opt = o;
         B = (int)hs.size();
-        if (B == 1) {
+        if (B == 1 && !member) {
             hp = std::move(hs[0]);
         } else {
             hps = std::move(hs);
@@ -1170,7 +1186,10 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         CK(cudaMemsetAsync(d_spec, 0, sizeof(double2) * 9 * g.Vs, st));
         const int nbuf = std::max(std::max(e64.xpartials(), e64.zblocks()), std::max(ec.xpartials(), ec.zblocks()));
         CK(dev_malloc(&d_part, 8 * (size_t)nbuf));
-        CK(dev_malloc(&d_sc, sizeof(Scalars) * B));
+        if (ext_sc)
+            d_sc = ext_sc;
+        else
+            CK(dev_malloc(&d_sc, sizeof(Scalars) * B));
         CK(dev_malloc(&d_phpart, sizeof(double) * PHASE_GRID * PHASE_SUMS));
         if (opt.solver == COMBO_NONLINEAR_CG) {
             CK(dev_malloc(&d_dir, sizeof(double) * 9 * (size_t)g.V));
@@ -1183,7 +1202,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             CK(cudaMemsetAsync(d_ba8, 0, sizeof(double) * 24 * (size_t)std::max<int64_t>(nb, 1), st));
         }
         CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars) * B, st));
-        if (B > 1) {
+        if (B > 1 || member) {
             std::vector<double> mat(4 * B);
             std::vector<int32_t> bprob(std::max<int64_t>(nb, 1), 0);
             for (int b = 0; b < B; b++) {
@@ -1259,7 +1278,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         iters.assign(hp.n_steps, 0);
         cg_iters.assign(hp.n_steps, 0);
         CK(cudaStreamSynchronize(st));
-        if (newton()) {
+        if (newton() && !member) {
             if ((rc = autotune())) return rc;
             tune_force(ec);
         }
@@ -1389,10 +1408,9 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         }
     }
 
-    // --- kernel sequences
-    void boxels(bool tangent, int guard)
+    // --- kernel arguments and sequences
+    BoxelArgs<Tc> boxel_args(bool tangent, int guard) const
     {
-        if (nb == 0) return;
         BoxelArgs<Tc> a{};
         a.nb = nb;
         a.V = g.V;
@@ -1417,6 +1435,12 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         a.max_iter = opt.nr_max_iter;
         a.sc = d_sc;
         a.guard = guard;
+        return a;
+    }
+    void boxels(bool tangent, int guard)
+    {
+        if (nb == 0) return;
+        const BoxelArgs<Tc> a = boxel_args(tangent, guard);
         prof.begin(K_BOXEL);
         launch_boxel<Tc>(a, st);
         prof.end();
@@ -1483,7 +1507,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     }
 
     // FP64 residual operator: G[P(F)]; mode: XI_FIXEDPOINT (update F) or XI_RHS (r = -G[P], x = 0)
-    void resid_operator(int xi_mode, int guard)
+    XfwdArgs<Rt, Tc> resid_xf(int xi_mode) const
     {
         auto xf = e64.template xf<Tc>();
         xf.mode = XF_RESID;
@@ -1501,15 +1525,10 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         xf.matp = d_mat;
         xf.nb = nb;
         xf.sc = d_sc;
-        prof.begin(K_XFWD_RESID);
-        launch_xfwd<Rt, Tc>(xf, guard, st);
-        prof.end();
-        e64.yz(d_sc, guard, true, d_part, st, &prof, K_YFWD_64);
-        prof.begin(K_FINALIZE);
-        k_fin_resid<<<B, 256, 0, st>>>(d_sc, d_part, e64.zblocks_p(), (double)Vp, opt.tol, opt.fixed_iterations,
-                                       opt.max_iter, (xi_mode == XI_FIXEDPOINT || xi_mode == XI_NCG) ? 1 : 0,
-                                       B > 1 ? 1 : 0, xi_mode == XI_NCG ? 1 : 0);
-        prof.end();
+        return xf;
+    }
+    XinvArgs<Rt, Tc> resid_xi(int xi_mode) const
+    {
         auto xi = e64.template xi<Tc>();
         xi.mode = xi_mode;
         xi.inv_mu0 = 1.0 / mu0;
@@ -1519,18 +1538,38 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         xi.r = d_r;
         xi.partial = d_part;
         xi.sc = d_sc;
+        return xi;
+    }
+    void fin_resid(int xi_mode)
+    {
+        prof.begin(K_FINALIZE);
+        k_fin_resid<<<B, 256, 0, st>>>(d_sc, d_part, e64.zblocks_p(), (double)Vp, opt.tol, opt.fixed_iterations,
+                                       opt.max_iter, (xi_mode == XI_FIXEDPOINT || xi_mode == XI_NCG) ? 1 : 0,
+                                       (B > 1 || member) ? 1 : 0, xi_mode == XI_NCG ? 1 : 0);
+        prof.end();
+    }
+    void fin_rhs()
+    {
+        prof.begin(K_FINALIZE);
+        k_fin_rhs<<<B, 256, 0, st>>>(d_sc, d_part, e64.xblocks() / B, opt.cg_fixed_iterations, opt.cg_max_iter);
+        prof.end();
+    }
+    void resid_operator(int xi_mode, int guard)
+    {
+        const auto xf = resid_xf(xi_mode);
+        prof.begin(K_XFWD_RESID);
+        launch_xfwd<Rt, Tc>(xf, guard, st);
+        prof.end();
+        e64.yz(d_sc, guard, true, d_part, st, &prof, K_YFWD_64);
+        fin_resid(xi_mode);
+        const auto xi = resid_xi(xi_mode);
         prof.begin(K_XINV_64);
         launch_xinv<Rt, Tc>(xi, guard, st);
         prof.end();
-        if (xi_mode == XI_RHS) {
-            prof.begin(K_FINALIZE);
-            k_fin_rhs<<<B, 256, 0, st>>>(d_sc, d_part, e64.xblocks() / B, opt.cg_fixed_iterations, opt.cg_max_iter);
-            prof.end();
-        }
+        if (xi_mode == XI_RHS) fin_rhs();
     }
 
-    // one CG iteration in precision Tc, guarded by cg_done
-    void cg_iteration()
+    XfwdArgs<Tc, Tc> cg_xf() const
     {
         auto xf = ec.template xf<Tc>();
         xf.mode = XF_TANGENT;
@@ -1552,10 +1591,10 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         xf.partial = d_part;
         xf.sc = d_sc;
         xf.fuse = 1;  // the last block computes alpha
-        prof.begin(K_XFWD_TANGENT);
-        launch_xfwd<Tc, Tc>(xf, 1, st);
-        prof.end();
-        ec.yz(d_sc, 1, false, nullptr, st, &prof, K_YFWD_C);
+        return xf;
+    }
+    XinvArgs<Tc, Tc> cg_xi() const
+    {
         auto xi = ec.template xi<Tc>();
         xi.mode = XI_CG;
         xi.x = d_x;
@@ -1567,6 +1606,17 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         xi.cg_tol = opt.cg_tol;
         xi.cg_max = opt.cg_max_iter;
         xi.cg_fixed = opt.cg_fixed_iterations;
+        return xi;
+    }
+    // one CG iteration in precision Tc, guarded by cg_done
+    void cg_iteration()
+    {
+        const auto xf = cg_xf();
+        prof.begin(K_XFWD_TANGENT);
+        launch_xfwd<Tc, Tc>(xf, 1, st);
+        prof.end();
+        ec.yz(d_sc, 1, false, nullptr, st, &prof, K_YFWD_C);
+        const auto xi = cg_xi();
         prof.begin(K_XINV_CG);
         launch_xinv<Tc, Tc>(xi, 1, st);
         prof.end();
@@ -2216,6 +2266,475 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     }
 };
 
+// ------------------------------------------------------------------ batches over several grids
+// Device copy of one grouped launch's table (GroupTab): per descriptor its
+// arguments, its first item and its item grid.
+template <typename A> struct GroupBuf {
+    GroupTab<A> t;
+    void* mem = nullptr;
+    ~GroupBuf() { cudaFree(mem); }
+    int build(const std::vector<A>& args, const std::vector<int>& items, const std::vector<int>& dims, size_t smem,
+              cudaStream_t st)
+    {
+        const int nd = (int)args.size();
+        std::vector<int> vs(nd + 1, 0), dm(2 * std::max(nd, 1), 0);
+        for (int d = 0; d < nd; d++) vs[d + 1] = vs[d] + items[d];
+        for (size_t i = 0; i < dims.size(); i++) dm[i] = dims[i];
+        const size_t ab = (sizeof(A) * std::max(nd, 1) + 255) / 256 * 256;
+        const size_t vb = (sizeof(int) * vs.size() + 255) / 256 * 256;
+        const size_t db = sizeof(int) * dm.size();
+        CK(dev_malloc(&mem, ab + vb + db));
+        char* b = static_cast<char*>(mem);
+        CK(cudaMemcpyAsync(b, args.data(), sizeof(A) * nd, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(b + ab, vs.data(), sizeof(int) * vs.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(b + ab + vb, dm.data(), db, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
+        t.args = reinterpret_cast<const A*>(b);
+        t.vstart = reinterpret_cast<const int*>(b + ab);
+        t.dims = reinterpret_cast<const int*>(b + ab + vb);
+        t.nd = nd;
+        t.total = vs[nd];
+        t.smem = smem;
+        return COMBO_OK;
+    }
+};
+
+// A batch of Newton-CG problems on different grids.  The problems of each
+// distinct grid (sides and cell size) form one stacked solve (a class); the
+// classes advance in lockstep rounds like the stacked batch, and every pass
+// of every operator application -- laminate solves, x-forward, y, z + Green
+// operator, y inverse, x-inverse -- is ONE grouped launch over the work items
+// of all classes (grouped x-, y-, z-pass and boxel kernels).  The CG loop is
+// replayed from a captured CUDA graph of kCgChunk iterations.  A class runs
+// the same pass bodies and reductions as its own stacked solve would with
+// the engine's default launch shapes, so each result equals its single
+// solve within the Krylov rounding.
+template <typename Tc, typename Rt> struct MixSolve : SolveBase {
+    using Cls = Solve<Tc, Rt>;
+    combo_ctx* ctx = nullptr;
+    combo_options opt;
+    cudaStream_t st = nullptr;
+    std::vector<std::unique_ptr<Cls>> cls;
+    std::vector<std::vector<int>> members;  // input index of each class's problems
+    std::vector<int> off;                   // first problem (in the shared scalars) of each class
+    int P = 0;
+    Scalars* d_sc = nullptr;  // [P] scalars of every problem, class-major
+    std::vector<Scalars> hsc;
+    GroupBuf<BoxelArgs<Tc>> g_box;
+    GroupBuf<XfwdArgs<Rt, Tc>> g_xf_res;
+    GroupBuf<YArgs<Rt>> g_y_res;
+    GroupBuf<ZArgs<Rt>> g_z_res;
+    GroupBuf<XinvArgs<Rt, Tc>> g_xi_res;
+    GroupBuf<XfwdArgs<Tc, Tc>> g_xf_cg;
+    GroupBuf<YArgs<Tc>> g_y_cg;
+    GroupBuf<ZArgs<Tc>> g_z_cg;
+    GroupBuf<XinvArgs<Tc, Tc>> g_xi_cg;
+    Profiler prof;
+    cudaGraphExec_t cg_exec = nullptr;
+    int64_t cg_chunks_run = 0;
+    volatile int cancel_requested = 0;
+    int error = 0;
+    static constexpr int kCgChunk = 8;
+
+    ~MixSolve() override
+    {
+        if (cg_exec) cudaGraphExecDestroy(cg_exec);
+        cls.clear();
+        cudaFree(d_sc);
+    }
+    bool linear() const { return opt.theory == COMBO_INFINITESIMAL_STRAIN; }
+
+    int init(combo_ctx* c, std::vector<HostProblem>&& hs, const combo_options& o)
+    {
+        ctx = c;
+        st = c->stream;
+        prof.st = st;
+        opt = o;
+        P = (int)hs.size();
+        // classes: problems of equal sides and cell sizes, in order of first appearance
+        std::vector<std::vector<HostProblem>> groups;
+        for (int i = 0; i < P; i++) {
+            int k = 0;
+            for (; k < (int)groups.size(); k++) {
+                const HostProblem& q = groups[k][0];
+                bool same = true;
+                for (int j = 0; j < 3; j++) same = same && q.n[j] == hs[i].n[j] && q.l[j] == hs[i].l[j];
+                if (same) break;
+            }
+            if (k == (int)groups.size()) {
+                groups.emplace_back();
+                members.emplace_back();
+            }
+            groups[k].push_back(std::move(hs[i]));
+            members[k].push_back(i);
+        }
+        CK(dev_malloc(&d_sc, sizeof(Scalars) * P));
+        CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars) * P, st));
+        hsc.resize(P);
+        int rc, o0 = 0;
+        for (size_t k = 0; k < groups.size(); k++) {
+            off.push_back(o0);
+            auto q = std::make_unique<Cls>();
+            q->member = true;
+            q->ext_sc = d_sc + o0;
+            o0 += (int)groups[k].size();
+            rc = q->init(c, std::move(groups[k]), o);
+            cls.push_back(std::move(q));
+            if (rc) return rc;
+        }
+        return build_groups();
+    }
+
+    // the grouped launches' tables: the arguments each class's own launches
+    // would take (default launch shapes, guards of the lockstep batch)
+    int build_groups()
+    {
+        const int K = (int)cls.size();
+        int rc;
+        {
+            std::vector<BoxelArgs<Tc>> a;
+            std::vector<int> it;
+            for (auto& q : cls)
+                if (q->nb > 0) {
+                    a.push_back(q->boxel_args(true, 2));
+                    it.push_back((int)((q->nb + 127) / 128));
+                }
+            if ((rc = g_box.build(a, it, {}, 0, st))) return rc;
+        }
+        {
+            std::vector<XfwdArgs<Rt, Tc>> a(K);
+            std::vector<XinvArgs<Rt, Tc>> b(K);
+            std::vector<int> it(K);
+            size_t sm = 0;
+            for (int k = 0; k < K; k++) {
+                a[k] = cls[k]->resid_xf(XI_RHS);
+                b[k] = cls[k]->resid_xi(XI_RHS);
+                it[k] = cls[k]->e64.xblocks();
+                sm = std::max(sm, xpass_smem(cls[k]->g, cls[k]->e64.lines, sizeof(cx<Rt>)));
+            }
+            if ((rc = g_xf_res.build(a, it, {}, sm, st))) return rc;
+            if ((rc = g_xi_res.build(b, it, {}, sm, st))) return rc;
+        }
+        {
+            std::vector<XfwdArgs<Tc, Tc>> a(K);
+            std::vector<XinvArgs<Tc, Tc>> b(K);
+            std::vector<int> it(K);
+            size_t sm = 0;
+            for (int k = 0; k < K; k++) {
+                a[k] = cls[k]->cg_xf();
+                b[k] = cls[k]->cg_xi();
+                it[k] = cls[k]->ec.xblocks();
+                sm = std::max(sm, xpass_smem(cls[k]->g, cls[k]->ec.lines, sizeof(cx<Tc>)));
+            }
+            if ((rc = g_xf_cg.build(a, it, {}, sm, st))) return rc;
+            if ((rc = g_xi_cg.build(b, it, {}, sm, st))) return rc;
+        }
+        if ((rc = build_yz<Rt>(g_y_res, g_z_res, true))) return rc;
+        return build_yz<Tc>(g_y_cg, g_z_cg, false);
+    }
+
+    template <typename T> int build_yz(GroupBuf<YArgs<T>>& gy, GroupBuf<ZArgs<T>>& gz, bool resid)
+    {
+        const int K = (int)cls.size();
+        std::vector<YArgs<T>> ya(K);
+        std::vector<ZArgs<T>> za(K);
+        std::vector<int> yi(K), zi(K), yd(2 * K), zd(2 * K);
+        size_t ysm = 0, zsm = 0;
+        for (int k = 0; k < K; k++) {
+            Cls& q = *cls[k];
+            const Engine<T>& e = engine_of<T>(q, resid);
+            ya[k] = e.yargs(q.d_sc, resid ? 2 : 1);
+            za[k] = e.zargs(q.d_sc, resid ? 2 : 1, resid, resid ? q.d_part : nullptr);
+            ya[k].tmap = nullptr;
+            za[k].tmap = nullptr;
+            int gx, gyy, gzz;
+            size_t sm;
+            ypass_group_shape(q.g, ya[k].tx, sizeof(cx<T>), gx, gyy, gzz, sm);
+            yi[k] = gx * gyy * gzz;
+            yd[2 * k] = gx;
+            yd[2 * k + 1] = gyy;
+            ysm = std::max(ysm, sm);
+            zpass_group_shape(q.g, za[k].tx, sizeof(cx<T>), gx, gyy, gzz, sm);
+            zi[k] = gx * gyy * gzz;
+            zd[2 * k] = gx;
+            zd[2 * k + 1] = gyy;
+            zsm = std::max(zsm, sm);
+            if (resid && zi[k] / q.B != q.e64.zblocks_p())
+                return fail(COMBO_E_CUDA, "grouped z-pass partial count differs from the class's reduction");
+        }
+        int rc;
+        if ((rc = gy.build(ya, yi, yd, ysm, st))) return rc;
+        return gz.build(za, zi, zd, zsm, st);
+    }
+    template <typename T> static const Engine<T>& engine_of(const Cls& q, bool resid)
+    {
+        if constexpr (std::is_same<T, Rt>::value && std::is_same<T, Tc>::value)
+            return resid ? q.e64 : q.ec;
+        else if constexpr (std::is_same<T, Rt>::value)
+            return q.e64;
+        else
+            return q.ec;
+    }
+
+    // --- grouped sequences
+    void residual()
+    {
+        prof.begin(K_BOXEL);
+        launch_group_boxel<Tc>(g_box.t, std::is_same<Rt, df32>::value, linear(), st);
+        prof.end();
+        prof.begin(K_XFWD_RESID);
+        launch_group_xfwd<Rt, Tc>(g_xf_res.t, false, 2, st);
+        prof.end();
+        prof.begin(K_YFWD_64);
+        launch_group_ypass<Rt, false>(g_y_res.t, st);
+        prof.end();
+        prof.begin(K_ZGAMMA_64);
+        launch_group_zpass<Rt>(g_z_res.t, st);
+        prof.end();
+        prof.begin(K_YINV_64);
+        launch_group_ypass<Rt, true>(g_y_res.t, st);
+        prof.end();
+        for (auto& q : cls) q->fin_resid(XI_RHS);
+        prof.begin(K_XINV_64);
+        launch_group_xinv<Rt, Tc>(g_xi_res.t, 2, st);
+        prof.end();
+        for (auto& q : cls) q->fin_rhs();
+    }
+    void cg_iteration()
+    {
+        prof.begin(K_XFWD_TANGENT);
+        launch_group_xfwd<Tc, Tc>(g_xf_cg.t, true, 1, st);
+        prof.end();
+        prof.begin(K_YFWD_C);
+        launch_group_ypass<Tc, false>(g_y_cg.t, st);
+        prof.end();
+        prof.begin(K_ZGAMMA_C);
+        launch_group_zpass<Tc>(g_z_cg.t, st);
+        prof.end();
+        prof.begin(K_YINV_C);
+        launch_group_ypass<Tc, true>(g_y_cg.t, st);
+        prof.end();
+        prof.begin(K_XINV_CG);
+        launch_group_xinv<Tc, Tc>(g_xi_cg.t, 1, st);
+        prof.end();
+    }
+    int capture_cg_chunk()
+    {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < kCgChunk; k++) cg_iteration();
+        const cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (e != cudaSuccess) return fail(COMBO_E_CUDA, std::string("CG graph capture: ") + cudaGetErrorString(e));
+        const cudaError_t e2 = cudaGraphInstantiate(&cg_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e2 != cudaSuccess) {
+            cg_exec = nullptr;
+            return fail(COMBO_E_CUDA, std::string("CG graph instantiate: ") + cudaGetErrorString(e2));
+        }
+        return COMBO_OK;
+    }
+    int read_all()
+    {
+        CK(cudaMemcpyAsync(hsc.data(), d_sc, sizeof(Scalars) * P, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        prof.collect();
+        for (size_t k = 0; k < cls.size(); k++)
+            std::copy(hsc.begin() + off[k], hsc.begin() + off[k] + cls[k]->B, cls[k]->hsc.begin());
+        return COMBO_OK;
+    }
+    int set_flag_of(int i, size_t offset, int32_t value)
+    {
+        CK(cudaMemcpyAsync((char*)(d_sc + i) + offset, &value, 4, cudaMemcpyHostToDevice, st));
+        return COMBO_OK;
+    }
+    int status(const char* what)
+    {
+        for (size_t k = 0; k < cls.size(); k++)
+            for (int b = 0; b < cls[k]->B; b++)
+                if (hsc[off[k] + b].status)
+                    return error = fail(hsc[off[k] + b].status,
+                                        std::string(what) + " (problem " + std::to_string(members[k][b]) + ")" +
+                                            cls[k]->boxel_failure(hsc[off[k] + b]));
+        return COMBO_OK;
+    }
+
+    // Newton-CG in lockstep rounds over every problem of every class (the
+    // stacked batch's rounds, with grouped launches)
+    int run_batch() override
+    {
+        CK(cudaSetDevice(ctx->device));
+        if (opt.solver != COMBO_NEWTON_CG) return error = fail(COMBO_E_INVALID_ARG, "a batch runs the Newton-CG solver");
+        const int K = (int)cls.size();
+        for (auto& q : cls) {
+            q->ps.assign(q->B, typename Cls::PState{});
+            q->hsc.resize(q->B);
+            for (int b = 0; b < q->B; b++) {
+                auto& z = q->ps[b];
+                for (int c = 0; c < 9; c++) z.Fprev[c] = (c == 0 || c == 4 || c == 8) ? 1.0 : 0.0;
+                const int S = q->hps[b].n_steps;
+                z.Pbar.assign(9 * (size_t)S, 0.0);
+                z.Pphase.assign(18 * (size_t)S, 0.0);
+                z.resid.assign(S, 0.0);
+                z.iters.assign(S, 0);
+                z.cg_iters.assign(S, 0);
+            }
+        }
+        int rc;
+        while (true) {
+            // next load step of every problem that has one
+            bool any = false;
+            for (int k = 0; k < K; k++) {
+                Cls& q = *cls[k];
+                std::vector<double> dF(9 * (size_t)q.B, 0.0);
+                for (int b = 0; b < q.B; b++) {
+                    auto& z = q.ps[b];
+                    z.active = z.step < q.hps[b].n_steps;
+                    if (z.active) {
+                        any = true;
+                        const double f = (double)(z.step + 1) / q.hps[b].n_steps;
+                        for (int c = 0; c < 9; c++) {
+                            const double I = (c == 0 || c == 4 || c == 8) ? 1.0 : 0.0;
+                            const double Fn = I + f * (q.hps[b].Fbar[c] - I);
+                            dF[9 * b + c] = Fn - z.Fprev[c];
+                            z.Fprev[c] = Fn;
+                        }
+                        z.outer = 0;
+                        z.cg_total = 0;
+                    }
+                    if ((rc = set_flag_of(off[k] + b, offsetof(Scalars, outer_done), z.active ? 0 : 1))) return error = rc;
+                    if ((rc = set_flag_of(off[k] + b, offsetof(Scalars, outer_iter), 0))) return error = rc;
+                }
+                CK(cudaMemcpyAsync(q.d_dF, dF.data(), 8 * dF.size(), cudaMemcpyHostToDevice, st));
+                Mat9 zero{};
+                prof.begin(K_UPDATE);
+                k_add_uniform<<<grid_for(9 * q.g.V), 256, 0, st>>>(q.d_F, q.g.V, zero, q.d_dF, q.Vp);
+                prof.end();
+                CK(cudaStreamSynchronize(st));  // dF goes out of scope
+            }
+            if (!any) break;
+            CK(cudaGetLastError());
+            // Newton iterations of this round
+            while (true) {
+                if (cancel_requested) return error = fail(COMBO_E_CANCELLED, "solve cancelled");
+                residual();
+                CK(cudaGetLastError());
+                if ((rc = read_all())) return error = rc;
+                if ((rc = status("residual evaluation failed"))) return rc;
+                bool any_cg = false;
+                for (int k = 0; k < K; k++) {
+                    Cls& q = *cls[k];
+                    for (int b = 0; b < q.B; b++) {
+                        auto& z = q.ps[b];
+                        if (!z.active) continue;
+                        const Scalars& sb = hsc[off[k] + b];
+                        const bool conv = (opt.fixed_iterations > 0) ? (z.outer >= opt.fixed_iterations) : (sb.eps <= opt.tol);
+                        if (conv) {
+                            if ((rc = q.phase_avg((int64_t)b * q.Vp, (int64_t)(b + 1) * q.Vp, q.boff[b], q.boff[b + 1],
+                                                  q.hps[b].mu, q.hps[b].lam, z.Pphase.data() + 18 * (size_t)z.step)))
+                                return error = rc;
+                            for (int c = 0; c < 9; c++) z.Pbar[9 * z.step + c] = sb.Pbar[c];
+                            z.resid[z.step] = sb.eps;
+                            z.iters[z.step] = z.outer;
+                            z.cg_iters[z.step] = z.cg_total;
+                            z.step++;
+                            z.active = false;
+                            if ((rc = set_flag_of(off[k] + b, offsetof(Scalars, outer_done), 1))) return error = rc;
+                            if ((rc = set_flag_of(off[k] + b, offsetof(Scalars, cg_done), 1))) return error = rc;
+                        } else if (z.outer >= opt.max_iter) {
+                            return error = fail(COMBO_E_NOT_CONVERGED, "Newton did not converge (problem " +
+                                                                         std::to_string(members[k][b]) + ")");
+                        } else {
+                            any_cg = true;
+                        }
+                    }
+                }
+                if (!any_cg) break;
+                // CG on every problem still iterating, kCgChunk iterations per host round trip
+                while (true) {
+                    if (prof.on || cg_chunks_run == 0) {
+                        for (int j = 0; j < kCgChunk; j++) cg_iteration();
+                    } else {
+                        if (!cg_exec && (rc = capture_cg_chunk())) return error = rc;
+                        CK(cudaGraphLaunch(cg_exec, st));
+                    }
+                    cg_chunks_run++;
+                    CK(cudaGetLastError());
+                    if ((rc = read_all())) return error = rc;
+                    if ((rc = status("CG failed"))) return rc;
+                    bool all = true;
+                    for (int i = 0; i < P; i++) all = all && hsc[i].cg_done;
+                    if (all) break;
+                }
+                // F += x with per-problem step halving until every det F > 0
+                std::vector<std::vector<double>> dv(K);
+                for (int k = 0; k < K; k++) {
+                    Cls& q = *cls[k];
+                    dv[k].assign(q.B, 0.0);
+                    for (int b = 0; b < q.B; b++) {
+                        dv[k][b] = q.ps[b].active ? 1.0 : 0.0;
+                        if (q.ps[b].active) q.ps[b].cg_total += hsc[off[k] + b].cg_iter;
+                    }
+                }
+                bool ok = false;
+                for (int h = 0; h <= 10; h++) {
+                    for (int i = 0; i < P; i++)
+                        if ((rc = set_flag_of(i, offsetof(Scalars, admissible), 1))) return error = rc;
+                    for (int k = 0; k < K; k++) {
+                        Cls& q = *cls[k];
+                        CK(cudaMemcpyAsync(q.d_dv, dv[k].data(), 8 * q.B, cudaMemcpyHostToDevice, st));
+                        prof.begin(K_UPDATE);
+                        k_update_F<Tc><<<grid_for(q.g.V), 256, 0, st>>>(q.d_F, q.d_x, q.d_p, 0.0, q.g.V, q.d_sc, q.d_dv,
+                                                                        q.Vp);
+                        prof.end();
+                    }
+                    if ((rc = read_all())) return error = rc;
+                    bool bad = false;
+                    for (int k = 0; k < K; k++)
+                        for (int b = 0; b < cls[k]->B; b++) {
+                            if (dv[k][b] != 0.0 && !hsc[off[k] + b].admissible && !linear()) {
+                                dv[k][b] = -std::ldexp(1.0, -(h + 1));  // F_old + 2^-(h+1) x
+                                bad = true;
+                            } else {
+                                dv[k][b] = 0.0;
+                            }
+                        }
+                    if (!bad) {
+                        ok = true;
+                        break;
+                    }
+                }
+                if (!ok) return error = fail(COMBO_E_INADMISSIBLE, "det F <= 0 after 10 step halvings");
+                for (auto& q : cls)
+                    for (int b = 0; b < q->B; b++)
+                        if (q->ps[b].active) q->ps[b].outer++;
+            }
+        }
+        return COMBO_OK;
+    }
+
+    // per-problem results in input order
+    int batch_results(combo_result* rs) override
+    {
+        for (size_t k = 0; k < cls.size(); k++) {
+            std::vector<combo_result> sub;
+            for (int i : members[k]) sub.push_back(rs[i]);
+            const int rc = cls[k]->batch_results(sub.data());
+            for (size_t j = 0; j < sub.size(); j++) rs[members[k][j]] = sub[j];
+            if (rc) return rc;
+        }
+        return COMBO_OK;
+    }
+
+    Profiler& profiler() override { return prof; }
+    void request_cancel() override { cancel_requested = 1; }
+    int advance(int64_t) override { return fail(COMBO_E_INVALID_ARG, "a batch over several grids runs as a whole"); }
+    int advance_newton(int64_t) override { return advance(0); }
+    int advance_steps(int32_t) override { return advance(0); }
+    int finish(combo_result*) override { return advance(0); }
+    int export_state(void*, int64_t*) override { return fail(COMBO_E_INVALID_ARG, "checkpoints cover single solves"); }
+    int import_state(const void*, int64_t) override { return export_state(nullptr, nullptr); }
+};
+
 // A solve of the requested precision form: plain FP64; FP32 Krylov with FP64
 // residual transforms; FP32 Krylov with double-float residual transforms.
 template <class H> static int make_solve(combo_ctx* ctx, H&& h, const combo_options& o, SolveBase** out)
@@ -2233,6 +2752,26 @@ template <class H> static int make_solve(combo_ctx* ctx, H&& h, const combo_opti
         auto* s = new Solve<float, df32>();
         rc = s->init(ctx, std::move(h), o);
         *out = s;
+    }
+    return rc;
+}
+
+// A batch over several grids in the requested precision form
+static int make_mix(combo_ctx* ctx, std::vector<HostProblem>&& hs, const combo_options& o, SolveBase** out)
+{
+    int rc;
+    if (o.precision == COMBO_FP64) {
+        auto* s = new MixSolve<double, double>();
+        *out = s;
+        rc = s->init(ctx, std::move(hs), o);
+    } else if (o.precision == COMBO_FP32_REFINED) {
+        auto* s = new MixSolve<float, double>();
+        *out = s;
+        rc = s->init(ctx, std::move(hs), o);
+    } else {
+        auto* s = new MixSolve<float, df32>();
+        *out = s;
+        rc = s->init(ctx, std::move(hs), o);
     }
     return rc;
 }
@@ -2416,14 +2955,29 @@ extern "C" int combo_solve_batch(combo_ctx* ctx, int32_t n_problems, const combo
         return fail(COMBO_E_INVALID_ARG, "a batch runs the Newton-CG solver");
     CK(cudaSetDevice(ctx->device));
     std::vector<HostProblem> hs(n_problems);
+    bool same = true;
+    int64_t vmax = 0;
     for (int b = 0; b < n_problems; b++) {
         if ((rc = load_problem(problems + b, &o, hs[b]))) return rc;
-        for (int j = 0; j < 3; j++)
-            if (hs[b].n[j] != hs[0].n[j] || hs[b].l[j] != hs[0].l[j])
-                return fail(COMBO_E_INVALID_ARG, "the problems of a batch need equal grids n and cell sizes l");
+        for (int j = 0; j < 3; j++) same = same && hs[b].n[j] == hs[0].n[j] && hs[b].l[j] == hs[0].l[j];
+        vmax = std::max(vmax, (int64_t)hs[b].n[0] * hs[b].n[1] * hs[b].n[2]);
     }
-    const int64_t V = (int64_t)hs[0].n[0] * hs[0].n[1] * hs[0].n[2];
-    if (V * n_problems >= (int64_t)1 << 31) return fail(COMBO_E_INVALID_ARG, "batch too large");
+    if (vmax * n_problems >= (int64_t)1 << 31) return fail(COMBO_E_INVALID_ARG, "batch too large");
+    if (!same) {
+        // problems on several grids: one stacked class per grid, grouped launches
+        SolveBase* impl = nullptr;
+        rc = make_mix(ctx, std::move(hs), o, &impl);
+        if (!rc) rc = impl->run_batch();
+        const std::string msg = g_err;
+        if (!rc) rc = impl->batch_results(results);
+        delete impl;
+        if (rc) {
+            cudaGetLastError();
+            g_err = msg.empty() ? g_err : msg;
+            return (rc == COMBO_E_CUDA && g_err.find("memory") != std::string::npos) ? COMBO_E_OOM : rc;
+        }
+        return COMBO_OK;
+    }
     if (n_problems == 1) {
         // a batch of one is a plain solve
         SolveBase* impl = nullptr;
@@ -2768,6 +3322,7 @@ extern "C" int combo_constitutive(combo_ctx* ctx, const combo_problem* p, const 
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 

@@ -163,16 +163,18 @@ __device__ __forceinline__ bool nh_stress_df(const double Fd[9], double mu, doub
 // ------------------------------------------------------------- x forward
 // TAN: the Krylov tangent pass (a.mode == XF_TANGENT, no external X), whose
 // FP32 instance is register-capped for three resident blocks per SM
+// The pass body of one block: vb of vg blocks (a launch of its own: the
+// block index and grid size; a grouped launch: a work item of one grid).
 template <typename T, typename Tc, int MF, bool TAN>
-__global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(XfwdArgs<T, Tc> a, int guard)
+__device__ __forceinline__ void xfwd_body(const XfwdArgs<T, Tc>& a, int guard, int vb, int vg,
+                                          unsigned char* smem_raw)
 {
     const GridDims g = a.g;
     int pb, pj, gp;  // problem of this block, index among its gp blocks
-    prob_block(g, pb, pj, gp);
+    prob_block(g, vb, vg, pb, pj, gp);
     Scalars* sc = a.sc + pb;
     if (guard == 1 && sc->cg_done) return;
     if (guard == 2 && sc->outer_done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int LB = a.lines_per_block;
     const int ls = g.M + 1;
     cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
@@ -417,7 +419,7 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
     }
     if (TAN && a.partial) {
         const double s = block_sum(acc, red);
-        if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
+        if (threadIdx.x == 0) a.partial[vb] = s;
         if (a.fuse && last_block(&sc->ticket[0], flag, gp)) {
             const double tot = sum_partials_fixed(a.partial + (size_t)pb * gp, gp, red);
             if (threadIdx.x == 0) cg_alpha(sc, tot);
@@ -425,17 +427,24 @@ __global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(X
     }
 }
 
+template <typename T, typename Tc, int MF, bool TAN>
+__global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(XfwdArgs<T, Tc> a, int guard)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    xfwd_body<T, Tc, MF, TAN>(a, guard, blockIdx.x, gridDim.x, smem_raw);
+}
+
 // ------------------------------------------------------------- x inverse
 template <typename T, typename Tc, int MF>
-__global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
+__device__ __forceinline__ void xinv_body(const XinvArgs<T, Tc>& a, int guard, int vb, int vg,
+                                          unsigned char* smem_raw)
 {
     const GridDims g = a.g;
     int pb, pj, gp;  // problem of this block, index among its gp blocks
-    prob_block(g, pb, pj, gp);
+    prob_block(g, vb, vg, pb, pj, gp);
     Scalars* sc = a.sc + pb;
     if (guard == 1 && sc->cg_done) return;
     if (guard == 2 && sc->outer_done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int LB = a.lines_per_block;
     const int ls = g.M + 1;
     const int M = g.M;
@@ -541,12 +550,19 @@ __global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
     }
     if ((a.mode == XI_RHS || a.mode == XI_CG) && a.partial) {
         const double s = block_sum(acc, red);
-        if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
+        if (threadIdx.x == 0) a.partial[vb] = s;
         if (a.mode == XI_CG && a.fuse && last_block(&sc->ticket[1], flag, gp)) {
             const double tot = sum_partials_fixed(a.partial + (size_t)pb * gp, gp, red);
             if (threadIdx.x == 0) cg_beta(sc, tot, a.cg_tol, a.cg_max, a.cg_fixed);
         }
     }
+}
+
+template <typename T, typename Tc, int MF>
+__global__ void __launch_bounds__(256) k_xinv(XinvArgs<T, Tc> a, int guard)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    xinv_body<T, Tc, MF>(a, guard, blockIdx.x, gridDim.x, smem_raw);
 }
 
 // ------------------------------------------------------------- launchers
@@ -629,6 +645,93 @@ template <typename T, typename Tc> void launch_xinv(const XinvArgs<T, Tc>& a, in
         default: xinv_launch<T, Tc, 0>(a, guard, st); break;
     }
 }
+
+// ------------------------------------------------------------- grouped launches
+int group_grid(const void* kernel, int threads, size_t smem, int items)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int nsm = grid_cap(GridDims{}) / 4;
+    return std::max(1, std::min(items, per_sm * nsm));
+}
+
+// x-forward over the items of several grids; each runs the body of its own
+// grid's transform length (compile-time plan where there is one)
+template <typename T, typename Tc, bool TAN>
+__global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1)
+    k_group_xfwd(const XfwdArgs<T, Tc>* __restrict__ args, const int* __restrict__ vstart, int nd, int guard)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int total = __ldg(vstart + nd);
+    for (int v = blockIdx.x; v < total; v += gridDim.x) {
+        const int d = group_of(vstart, nd, v);
+        const XfwdArgs<T, Tc>& a = args[d];
+        const int vb = v - __ldg(vstart + d), vg = __ldg(vstart + d + 1) - __ldg(vstart + d);
+        switch (a.g.M) {
+            case 32: xfwd_body<T, Tc, 32, TAN>(a, guard, vb, vg, smem_raw); break;
+            case 64: xfwd_body<T, Tc, 64, TAN>(a, guard, vb, vg, smem_raw); break;
+            case 128: xfwd_body<T, Tc, 128, TAN>(a, guard, vb, vg, smem_raw); break;
+            default: xfwd_body<T, Tc, 0, TAN>(a, guard, vb, vg, smem_raw); break;
+        }
+        __syncthreads();  // the next item reuses the shared buffers
+    }
+}
+
+template <typename T, typename Tc>
+__global__ void __launch_bounds__(256)
+    k_group_xinv(const XinvArgs<T, Tc>* __restrict__ args, const int* __restrict__ vstart, int nd, int guard)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int total = __ldg(vstart + nd);
+    for (int v = blockIdx.x; v < total; v += gridDim.x) {
+        const int d = group_of(vstart, nd, v);
+        const XinvArgs<T, Tc>& a = args[d];
+        const int vb = v - __ldg(vstart + d), vg = __ldg(vstart + d + 1) - __ldg(vstart + d);
+        switch (a.g.M) {
+            case 32: xinv_body<T, Tc, 32>(a, guard, vb, vg, smem_raw); break;
+            case 64: xinv_body<T, Tc, 64>(a, guard, vb, vg, smem_raw); break;
+            case 128: xinv_body<T, Tc, 128>(a, guard, vb, vg, smem_raw); break;
+            default: xinv_body<T, Tc, 0>(a, guard, vb, vg, smem_raw); break;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, typename Tc>
+void launch_group_xfwd(const GroupTab<XfwdArgs<T, Tc>>& t, bool tangent, int guard, cudaStream_t st)
+{
+    if (t.total <= 0) return;
+    if (tangent) {
+        if constexpr (std::is_same<T, Tc>::value) {
+            auto k = k_group_xfwd<T, Tc, true>;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+            k<<<group_grid((const void*)k, 256, t.smem, t.total), 256, t.smem, st>>>(t.args, t.vstart, t.nd, guard);
+        }
+        return;
+    }
+    auto k = k_group_xfwd<T, Tc, false>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+    k<<<group_grid((const void*)k, 256, t.smem, t.total), 256, t.smem, st>>>(t.args, t.vstart, t.nd, guard);
+}
+
+template <typename T, typename Tc>
+void launch_group_xinv(const GroupTab<XinvArgs<T, Tc>>& t, int guard, cudaStream_t st)
+{
+    if (t.total <= 0) return;
+    auto k = k_group_xinv<T, Tc>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+    k<<<group_grid((const void*)k, 256, t.smem, t.total), 256, t.smem, st>>>(t.args, t.vstart, t.nd, guard);
+}
+
+template void launch_group_xfwd<float, float>(const GroupTab<XfwdArgs<float, float>>&, bool, int, cudaStream_t);
+template void launch_group_xfwd<double, double>(const GroupTab<XfwdArgs<double, double>>&, bool, int, cudaStream_t);
+template void launch_group_xfwd<double, float>(const GroupTab<XfwdArgs<double, float>>&, bool, int, cudaStream_t);
+template void launch_group_xfwd<df32, float>(const GroupTab<XfwdArgs<df32, float>>&, bool, int, cudaStream_t);
+template void launch_group_xinv<float, float>(const GroupTab<XinvArgs<float, float>>&, int, cudaStream_t);
+template void launch_group_xinv<double, double>(const GroupTab<XinvArgs<double, double>>&, int, cudaStream_t);
+template void launch_group_xinv<double, float>(const GroupTab<XinvArgs<double, float>>&, int, cudaStream_t);
+template void launch_group_xinv<df32, float>(const GroupTab<XinvArgs<df32, float>>&, int, cudaStream_t);
 
 template void launch_xfwd<double, double>(const XfwdArgs<double, double>&, int, cudaStream_t);
 template void launch_xfwd<double, float>(const XfwdArgs<double, float>&, int, cudaStream_t);

@@ -56,7 +56,7 @@ template <int M, int LB>
 __global__ void __launch_bounds__(xinv_threads<M, LB>()) k_xinv_stream(XinvArgs<float, float> a)
 {
     int pb, pj, gp;  // problem of this block, index among its gp blocks
-    prob_block(a.g, pb, pj, gp);
+    prob_block(a.g, blockIdx.x, gridDim.x, pb, pj, gp);
     Scalars* scp = a.sc + pb;
     if (scp->cg_done) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];

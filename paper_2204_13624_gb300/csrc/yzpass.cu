@@ -24,21 +24,22 @@ template <typename K> static void allow_smem(K kernel, bool& done)
 }
 
 // ------------------------------------------------------------- y pass (generic)
+// The pass bodies take the block index explicitly (VBlock): a launch of its
+// own passes blockIdx, a grouped launch the work item of one grid.
 template <typename T, bool INV>
-__global__ void __launch_bounds__(256) k_ypass(YArgs<T> a)
+__device__ __forceinline__ void ypass_body(const YArgs<T>& a, const VBlock& bi, unsigned char* smem_raw)
 {
-    const Scalars* sc = a.sc + blockIdx.y / a.g.n3p;  // this z plane's problem
+    const Scalars* sc = a.sc + bi.y / a.g.n3p;  // this z plane's problem
     if (a.guard == 1 && sc->cg_done) return;
     if (a.guard == 2 && sc->outer_done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const GridDims g = a.g;
     const int TX = a.tx;
     const int n2 = g.n2;
     cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
     cx<T>* buf1 = buf0 + (size_t)n2 * TX;
-    const int x0 = blockIdx.x * TX;
-    const int z = blockIdx.y;
-    cx<T>* base = a.spec + blockIdx.z * g.Vs + (int64_t)z * n2 * g.nhp + x0;
+    const int x0 = bi.x * TX;
+    const int z = bi.y;
+    cx<T>* base = a.spec + bi.z * g.Vs + (int64_t)z * n2 * g.nhp + x0;
     for (int e = threadIdx.x; e < n2 * TX; e += blockDim.x) {
         const int y = e / TX, t = e - y * TX;
         buf0[e] = (x0 + t < g.nh) ? base[(int64_t)y * g.nhp + t] : cx<T>{(T)0, (T)0};
@@ -51,22 +52,28 @@ __global__ void __launch_bounds__(256) k_ypass(YArgs<T> a)
     }
 }
 
+template <typename T, bool INV>
+__global__ void __launch_bounds__(256) k_ypass(YArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ypass_body<T, INV>(a, VBlock::of_launch(), smem_raw);
+}
+
 // ------------------------------------------------------------- y pass (power of two)
 // Block: TX columns x TPL threads; column fastest in the thread index so that
 // every global access of a warp covers TX consecutive complex values.
 template <typename T, int N, int TX, bool INV>
-__global__ void __launch_bounds__(TX * FastPlan<N>::TPL) k_ypass_fast(YArgs<T> a)
+__device__ __forceinline__ void ypass_fast_body(const YArgs<T>& a, const VBlock& bi, unsigned char* smem_raw)
 {
-    const Scalars* sc = a.sc + blockIdx.y / a.g.n3p;  // this z plane's problem
+    const Scalars* sc = a.sc + bi.y / a.g.n3p;  // this z plane's problem
     if (a.guard == 1 && sc->cg_done) return;
     if (a.guard == 2 && sc->outer_done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* ex = reinterpret_cast<cx<T>*>(smem_raw);
     const GridDims g = a.g;
     const int line = threadIdx.x % TX, tau = threadIdx.x / TX;
-    const int x0 = blockIdx.x * TX;
+    const int x0 = bi.x * TX;
     const bool valid = x0 + line < g.nh;
-    cx<T>* base = a.spec + blockIdx.z * g.Vs + (int64_t)blockIdx.y * N * g.nhp + x0 + line;
+    cx<T>* base = a.spec + bi.z * g.Vs + (int64_t)bi.y * N * g.nhp + x0 + line;
     const int64_t st = g.nhp;
     fft_fast<T, N, INV>([&](int e) { return valid ? base[e * st] : cx<T>{(T)0, (T)0}; },
                         [&](int e, cx<T> v) {
@@ -76,15 +83,21 @@ __global__ void __launch_bounds__(TX * FastPlan<N>::TPL) k_ypass_fast(YArgs<T> a
                         a.tw);
 }
 
+template <typename T, int N, int TX, bool INV>
+__global__ void __launch_bounds__(TX * FastPlan<N>::TPL) k_ypass_fast(YArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ypass_fast_body<T, N, TX, INV>(a, VBlock::of_launch(), smem_raw);
+}
+
 // ------------------------------------------------------------- z pass + Gamma (generic)
 template <typename T>
-__global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
+__device__ __forceinline__ void zpass_body(const ZArgs<T>& a, const VBlock& bi, unsigned char* smem_raw)
 {
-    const int pb = blockIdx.z / 3;  // problem; gridDim.z = 3 nprob
+    const int pb = bi.z / 3;  // problem; gz = 3 nprob
     Scalars* sc = a.sc + pb;
     if (a.guard == 1 && sc->cg_done) return;
     if (a.guard == 2 && sc->outer_done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const GridDims g = a.g;
     const int TX = a.tx;
     const int n3 = g.n3p;
@@ -92,9 +105,9 @@ __global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
     cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
     cx<T>* buf1 = buf0 + (size_t)n3 * W;
     double* red = reinterpret_cast<double*>(buf1 + (size_t)n3 * W);
-    const int x0 = blockIdx.x * TX;
-    const int y = blockIdx.y;
-    const int row = blockIdx.z - 3 * pb;  // tensor row i: components 3i, 3i+1, 3i+2
+    const int x0 = bi.x * TX;
+    const int y = bi.y;
+    const int row = bi.z - 3 * pb;  // tensor row i: components 3i, 3i+1, 3i+2
     const int64_t zstride = (int64_t)g.n2 * g.nhp;
     cx<T>* base = a.spec + (int64_t)(3 * row) * g.Vs + (int64_t)pb * g.n3p * zstride + (int64_t)y * g.nhp + x0;
 
@@ -168,8 +181,15 @@ __global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
     }
     if (a.want_norm && a.partial) {
         const double s = block_sum(acc, red);
-        if (threadIdx.x == 0) a.partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+        if (threadIdx.x == 0) a.partial[bi.linear()] = s;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    zpass_body<T>(a, VBlock::of_launch(), smem_raw);
 }
 
 // ------------------------------------------------------------- z pass + Gamma (power of two)
@@ -180,13 +200,12 @@ __global__ void __launch_bounds__(256) k_zpass(ZArgs<T> a)
 // shared memory, the projection runs in place, and each group's inverse
 // transform starts from the positions its own last forward stage wrote.
 template <typename T, int N, int TX>
-__global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<T> a)
+__device__ __forceinline__ void zpass_fast_body(const ZArgs<T>& a, const VBlock& bi, unsigned char* smem_raw)
 {
-    const int pb = blockIdx.z / 3;  // problem; gridDim.z = 3 nprob
+    const int pb = bi.z / 3;  // problem; gz = 3 nprob
     Scalars* sc = a.sc + pb;
     if (a.guard == 1 && sc->cg_done) return;
     if (a.guard == 2 && sc->outer_done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TPL = FastPlan<N>::TPL;
     constexpr int GS = TX * TPL;  // threads per component group
     cx<T>* park = reinterpret_cast<cx<T>*>(smem_raw);  // [3][N][TX]
@@ -195,10 +214,10 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<
     const int c = threadIdx.x / GS;
     const int r = threadIdx.x - c * GS;
     const int line = r % TX, tau = r / TX;
-    const int x0 = blockIdx.x * TX;
+    const int x0 = bi.x * TX;
     const bool valid = x0 + line < g.nh;
-    const int y = blockIdx.y;
-    const int row = blockIdx.z - 3 * pb;
+    const int y = bi.y;
+    const int row = bi.z - 3 * pb;
     const int64_t zst = (int64_t)g.n2 * g.nhp;
     cx<T>* bc = a.spec + (int64_t)(3 * row + c) * g.Vs + (int64_t)pb * N * zst + (int64_t)y * g.nhp + x0 + line;
     cx<T>* pc = park + c * N * TX + line;
@@ -272,8 +291,15 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<
                                       lp, sp, tau, a.tw);
     if (a.want_norm && a.partial) {
         const double s = block_sum(acc, red);
-        if (threadIdx.x == 0) a.partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+        if (threadIdx.x == 0) a.partial[bi.linear()] = s;
     }
+}
+
+template <typename T, int N, int TX>
+__global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL) k_zpass_fast(ZArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    zpass_fast_body<T, N, TX>(a, VBlock::of_launch(), smem_raw);
 }
 
 // ------------------------------------------------------------- launch configuration
@@ -376,6 +402,114 @@ template <typename T> void launch_zpass(const ZArgs<T>& a, cudaStream_t st)
     allow_smem(k_zpass<T>, attr);
     k_zpass<T><<<grid, 256, sm, st>>>(a);
 }
+
+// ------------------------------------------------------------- grouped launches
+// Block size of the grouped y-pass: the power-of-two body's TX x TPL for
+// lengths 64 and 128 (every other length runs the generic body, which takes
+// any block size); z-pass: 3 TX TPL for lengths 64, 128 and 256.
+template <typename T> constexpr int group_y_threads() { return (sizeof(T) == 4 ? 16 : 8) * FastPlan<64>::TPL; }
+template <typename T> constexpr int group_z_threads() { return 3 * ztx_const<T>(64) * FastPlan<64>::TPL; }
+template <typename T> constexpr bool group_y_fast(int n) { return n == 64 || n == 128; }
+template <typename T> constexpr bool group_z_fast(int n)
+{
+    return (n == 64 || n == 128 || n == 256) && 3 * ztx_const<T>(n) * (n == 256 ? 16 : 8) == group_z_threads<T>();
+}
+
+void ypass_group_shape(const GridDims& g, int tx, size_t cxbytes, int& gx, int& gy, int& gz, size_t& smem)
+{
+    const bool fast = (g.n2 == 64 || g.n2 == 128);
+    const int t = fast ? (cxbytes == 8 ? 16 : 8) : tx;
+    gx = (g.nh + t - 1) / t;
+    gy = g.n3;
+    gz = 9;
+    smem = fast ? (size_t)g.n2 * t * cxbytes : 2 * (size_t)g.n2 * t * cxbytes;
+}
+
+void zpass_group_shape(const GridDims& g, int tx, size_t cxbytes, int& gx, int& gy, int& gz, size_t& smem)
+{
+    const int n = g.n3p;
+    const bool fast = cxbytes == 8 ? group_z_fast<float>(n) : group_z_fast<double>(n);
+    const int t = fast ? (cxbytes == 8 ? ztx_const<float>(n) : ztx_const<double>(n)) : tx;
+    gx = (g.nh + t - 1) / t;
+    gy = g.n2;
+    gz = 3 * g.nprob;
+    smem = fast ? (size_t)3 * n * t * cxbytes + 64 * sizeof(double)
+                : 2 * (size_t)n * 3 * t * cxbytes + 64 * sizeof(double);
+}
+
+template <typename T, bool INV>
+__global__ void __launch_bounds__(group_y_threads<T>())
+    k_group_ypass(const YArgs<T>* __restrict__ args, const int* __restrict__ vstart, const int* __restrict__ dims,
+                  int nd)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TX = sizeof(T) == 4 ? 16 : 8;
+    const int total = __ldg(vstart + nd);
+    for (int v = blockIdx.x; v < total; v += gridDim.x) {
+        const int d = group_of(vstart, nd, v);
+        const YArgs<T>& a = args[d];
+        const VBlock bi = VBlock::of_item(v - __ldg(vstart + d), __ldg(dims + 2 * d), __ldg(dims + 2 * d + 1), 9);
+        switch (a.g.n2) {
+            case 64: ypass_fast_body<T, 64, TX, INV>(a, bi, smem_raw); break;
+            case 128: ypass_fast_body<T, 128, TX, INV>(a, bi, smem_raw); break;
+            default: ypass_body<T, INV>(a, bi, smem_raw); break;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(group_z_threads<T>())
+    k_group_zpass(const ZArgs<T>* __restrict__ args, const int* __restrict__ vstart, const int* __restrict__ dims,
+                  int nd)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int total = __ldg(vstart + nd);
+    for (int v = blockIdx.x; v < total; v += gridDim.x) {
+        const int d = group_of(vstart, nd, v);
+        const ZArgs<T>& a = args[d];
+        const VBlock bi = VBlock::of_item(v - __ldg(vstart + d), __ldg(dims + 2 * d), __ldg(dims + 2 * d + 1),
+                                          3 * a.g.nprob);
+        const int n = a.g.n3p;
+        if (n == 64 && group_z_fast<T>(64))
+            zpass_fast_body<T, 64, ztx_const<T>(64)>(a, bi, smem_raw);
+        else if (n == 128 && group_z_fast<T>(128))
+            zpass_fast_body<T, 128, ztx_const<T>(128)>(a, bi, smem_raw);
+        else if (n == 256 && group_z_fast<T>(256))
+            zpass_fast_body<T, 256, ztx_const<T>(256)>(a, bi, smem_raw);
+        else
+            zpass_body<T>(a, bi, smem_raw);
+        __syncthreads();
+    }
+}
+
+template <typename T, bool INV> void launch_group_ypass(const GroupTab<YArgs<T>>& t, cudaStream_t st)
+{
+    if (t.total <= 0) return;
+    auto k = k_group_ypass<T, INV>;
+    constexpr int th = group_y_threads<T>();
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+    k<<<group_grid((const void*)k, th, t.smem, t.total), th, t.smem, st>>>(t.args, t.vstart, t.dims, t.nd);
+}
+
+template <typename T> void launch_group_zpass(const GroupTab<ZArgs<T>>& t, cudaStream_t st)
+{
+    if (t.total <= 0) return;
+    auto k = k_group_zpass<T>;
+    constexpr int th = group_z_threads<T>();
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+    k<<<group_grid((const void*)k, th, t.smem, t.total), th, t.smem, st>>>(t.args, t.vstart, t.dims, t.nd);
+}
+
+template void launch_group_ypass<float, false>(const GroupTab<YArgs<float>>&, cudaStream_t);
+template void launch_group_ypass<float, true>(const GroupTab<YArgs<float>>&, cudaStream_t);
+template void launch_group_ypass<double, false>(const GroupTab<YArgs<double>>&, cudaStream_t);
+template void launch_group_ypass<double, true>(const GroupTab<YArgs<double>>&, cudaStream_t);
+template void launch_group_ypass<df32, false>(const GroupTab<YArgs<df32>>&, cudaStream_t);
+template void launch_group_ypass<df32, true>(const GroupTab<YArgs<df32>>&, cudaStream_t);
+template void launch_group_zpass<float>(const GroupTab<ZArgs<float>>&, cudaStream_t);
+template void launch_group_zpass<double>(const GroupTab<ZArgs<double>>&, cudaStream_t);
+template void launch_group_zpass<df32>(const GroupTab<ZArgs<df32>>&, cudaStream_t);
 
 template void launch_ypass<double, false>(const YArgs<double>&, cudaStream_t);
 template void launch_ypass<double, true>(const YArgs<double>&, cudaStream_t);

@@ -29,10 +29,10 @@ def cb():
     return combo
 
 
-def small_balls(n=(64, 64, 64), steps=1):
+def small_balls(n=(64, 64, 64), steps=1, radius=6.0):
     from paper_2204_13624_gb300 import microstructure as ms
 
-    return ms.random_spheres(n, 6.0, 0.15, 77, 10.0, np.diag([1.04, 1.0, 1.0]), steps)
+    return ms.random_spheres(n, radius, 0.12, 77, 10.0, np.diag([1.04, 1.0, 1.0]), steps)
 
 
 def test_wait_that_runs_out_returns_timeout(cb):
@@ -48,8 +48,10 @@ def test_wait_that_runs_out_returns_timeout(cb):
 
 
 def test_wait_cap_option_is_checked(cb):
+    from paper_2204_13624_gb300 import microstructure as ms
+
     with pytest.raises(cb.ComboError) as e:
-        cb.solve(small_balls((8, 8, 8)), wait_poll_cap=-2)
+        cb.solve(ms.homogeneous((8, 8, 8)), wait_poll_cap=-2)
     assert e.value.code == -1
 
 
@@ -69,7 +71,7 @@ def test_laminate_iteration_cap_returns_laminate_error(cb, prec):
 
 @pytest.mark.parametrize("prec", [0, 2])
 def test_nan_in_an_imported_state_returns_nan(cb, prec):
-    p = small_balls((16, 16, 16), steps=2)
+    p = small_balls((16, 16, 16), steps=2, radius=3.0)
     V = 16 ** 3
     nb = int(p["boxel_idx"].size)
     s = cb.Solve(p, solver=1, precision=prec, tol=1e-8)
@@ -94,7 +96,7 @@ def test_nan_in_an_imported_state_returns_nan(cb, prec):
 def test_allocation_failure_returns_oom_and_leaks_nothing(cb):
     import torch
 
-    p = small_balls((32, 32, 32), steps=1)
+    p = small_balls((32, 32, 32), steps=1, radius=4.0)
     cb.solve(p, solver=1, precision=cb.FP32_REFINED_DF)  # warm: tuner, module load
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
