@@ -56,14 +56,17 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-fibres", action="store_true", help="skip the 512^3 fibre workload")
     ap.add_argument("--no-normals", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--normals-only", default=None, metavar="N1,N2,N3",
                     help="only coarse-grain a seeded spheres image of this size (8^3 boxels), three calls "
                          "(profiling captures of the coarse-graining kernels)")
     ap.add_argument("--serve-full", action="store_true",
-                    help="serving stream of sides 64..256 and 1..10 load steps (takes minutes)")
+                    help="120 requests (24 of them in all three precision forms; takes many minutes)")
+    ap.add_argument("--serve-only", action="store_true", help="only the serving section")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel table here")
+    ap.add_argument("--batch-only", action="store_true", help="only the 64-solve batch section")
     ap.add_argument("--dfmg-only", type=int, default=0, metavar="N",
                     help="only the doubly-fine material grid kernel timings on an N^3 random-ball problem")
     return ap.parse_args()
@@ -279,6 +282,13 @@ def main():
         p = ms.random_spheres((n, n, n), 8.0, 0.2, ms.SEED_BASE + 6, 10.0, np.diag([1.05, 1.0, 1.0]), 2)
         print(json.dumps({"dfmg_only": n, "dfmg_kernels": dfmg_kernels(combo, ctx, p)}))
         return
+    if args.serve_only:
+        print(json.dumps({"serving": serving_bench(combo, ctx, count=120, compare=24) if args.serve_full
+                          else serving_bench(combo, ctx)}))
+        return
+    if args.batch_only:
+        print(json.dumps({"batch": batch_bench(combo, ctx)}))
+        return
     if args.normals_only:
         from paper_2204_13624_gb300 import microstructure as ms
 
@@ -293,67 +303,13 @@ def main():
     p = workload(args.n, args.shape)
     V = p["n"][0] * p["n"][1] * p["n"][2]
     prec = {"refined": combo.FP32_REFINED, "refined-df": combo.FP32_REFINED_DF, "fp64": combo.FP64}[args.precision]
-    s = combo.Solve(p, ctx=ctx, solver=combo.NEWTON_CG, precision=prec, tol=1e-8)
-    # warm-up and timed region end between Newton steps: every Newton step
-    # the timed region starts (residual, laminate solves, CG, F update) runs
-    # in full inside it
-    s.advance_newton(max(args.warmup, 3))
-    torch.cuda.synchronize()
-    r0 = s.finish(fields=False)
-    ops0, res0 = r0["n_operator"], r0["n_operator_fp64"]
-    s.profile(True)
     clk = ClockSampler(local)
-    clk.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    done = s.advance_newton(args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    ms, ops, residuals, prof, done = timed_window(combo, ctx, p, prec, args.steps, args.warmup, stream, dist, clk)
     clocks = clk.stop()
-    ms = ev0.elapsed_time(ev1)
-    res = s.finish(fields=False)
-    ops = res["n_operator"] - ops0
-    residuals = res["n_operator_fp64"] - res0
-    prof = s.profile_read()
-    s.profile(False)
-    s.close()
     t_max, ops_all = replicas_aggregate(ms, ops, dist, "cuda")
     value = ops_all * V / (t_max / 1e3)
-
-    # per-kernel table and the dominant kernel's roofline
-    kb = 8 if prec == combo.FP64 else 4
     peak, peak_kind = peaks()
-    table = {}
-    krylov = ("xfwd_tangent", "yfwd_krylov", "zgamma_krylov", "yinv_krylov", "xinv_cg")
-    for k, (kms, cnt) in prof.items():
-        if cnt == 0:
-            continue
-        b = algorithmic_bytes(k, p, kb)
-        # CG kernels are launched in graph chunks of 8 iterations; launches
-        # past the converged iteration return at once and do no work, so the
-        # per-launch time divides by the iterations that ran (ops)
-        work = min(cnt, ops) if k in krylov else cnt
-        per = kms / work if work else 0.0
-        table[k] = {"ms_total": kms, "launches": cnt, "launches_with_work": work, "ms_per_launch": per,
-                    "alg_bytes_per_launch": b, "GBps": (b / (per / 1e3) / 1e9) if (b and per > 0) else None}
-    hot = {k: v for k, v in table.items() if v["alg_bytes_per_launch"] and k not in ("boxel_laminate",)}
-    dom = max(hot, key=lambda k: hot[k]["ms_total"]) if hot else None
-    launches = int(sum(v["launches"] for v in table.values()))
-    cg_ms = sum(table[k]["ms_total"] for k in krylov if k in table)
-    newton_ms = sum(v["ms_total"] for k, v in table.items() if k not in krylov)
-    roof = None
-    if dom:
-        ach = table[dom]["GBps"]
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_kind": peak_kind,
-                "traffic": ncu_traffic(dom, table[dom]["alg_bytes_per_launch"]),
-                "alg_bytes_per_launch": table[dom]["alg_bytes_per_launch"]}
+    table, roof, cg_ms, newton_ms, launches = kernel_table(combo, prof, p, prec, ops, peak, peak_kind)
 
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -374,13 +330,15 @@ def main():
     serving = None
     if not args.no_serving and rank == 0:
         if args.serve_full:
-            serving = serving_bench(combo, ctx, count=24, sides=(64, 72, 96, 108, 128, 144, 192, 216, 256),
-                                    max_steps=10)
+            serving = serving_bench(combo, ctx, count=120, compare=24)
         else:
             serving = serving_bench(combo, ctx)
     batch = None
     if not args.no_batch and rank == 0:
         batch = batch_bench(combo, ctx)
+    fibres = None
+    if not args.no_fibres and rank == 0:
+        fibres = fibres_bench(combo, ctx, stream, peak, peak_kind)
     variants = None
     if not args.no_variants and rank == 0:
         variants = variants_bench(combo, ctx)
@@ -415,6 +373,7 @@ def main():
                            "autotune": combo.autotune_report().strip().splitlines(),
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "batch": batch,
+                "fibres_512": fibres,
                 "normal_detection": normals, "variants": variants, "gpu_launches": launches,
                 "clocks": clocks, "kernels": table}
         if args.profile_json:
@@ -422,6 +381,95 @@ def main():
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def timed_window(combo, ctx, p, prec, steps, warmup, stream, dist=None, clk=None):
+    """CUDA-event time of a window of whole Newton steps of one solve: after
+    warm-up Newton steps (at least `warmup` operator applications), from a
+    Newton step boundary on to the end of the Newton step in which `steps`
+    operator applications are reached, so the residual evaluation and
+    laminate solves of every Newton step it touches are inside.  Per-kernel
+    CUDA events on the solve's stream are recorded over the window."""
+    import torch
+
+    s = combo.Solve(p, ctx=ctx, solver=combo.NEWTON_CG, precision=prec, tol=1e-8)
+    s.advance_newton(max(warmup, 3))
+    torch.cuda.synchronize()
+    r0 = s.finish(fields=False)
+    ops0, res0 = r0["n_operator"], r0["n_operator_fp64"]
+    s.profile(True)
+    if clk:
+        clk.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    done = s.advance_newton(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    res = s.finish(fields=False)
+    ops = res["n_operator"] - ops0
+    residuals = res["n_operator_fp64"] - res0
+    prof = s.profile_read()
+    s.profile(False)
+    s.close()
+    return ms, ops, residuals, prof, done
+
+
+KRYLOV = ("xfwd_tangent", "yfwd_krylov", "zgamma_krylov", "yinv_krylov", "xinv_cg")
+
+
+def kernel_table(combo, prof, p, prec, ops, peak, peak_kind):
+    """Per-kernel table of a timed window and the dominant kernel's roofline."""
+    kb = 8 if prec == combo.FP64 else 4
+    table = {}
+    for k, (kms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        b = algorithmic_bytes(k, p, kb)
+        # CG kernels are launched in graph chunks of 8 iterations; launches
+        # past the converged iteration return at once and do no work, so the
+        # per-launch time divides by the iterations that ran (ops)
+        work = min(cnt, ops) if k in KRYLOV else cnt
+        per = kms / work if work else 0.0
+        table[k] = {"ms_total": kms, "launches": cnt, "launches_with_work": work, "ms_per_launch": per,
+                    "alg_bytes_per_launch": b, "GBps": (b / (per / 1e3) / 1e9) if (b and per > 0) else None}
+    hot = {k: v for k, v in table.items() if v["alg_bytes_per_launch"] and k not in ("boxel_laminate",)}
+    dom = max(hot, key=lambda k: hot[k]["ms_total"]) if hot else None
+    launches = int(sum(v["launches"] for v in table.values()))
+    cg_ms = sum(table[k]["ms_total"] for k in KRYLOV if k in table)
+    newton_ms = sum(v["ms_total"] for k, v in table.items() if k not in KRYLOV)
+    roof = None
+    if dom:
+        ach = table[dom]["GBps"]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_kind": peak_kind,
+                "traffic": ncu_traffic(dom, table[dom]["alg_bytes_per_launch"]),
+                "alg_bytes_per_launch": table[dom]["alg_bytes_per_launch"]}
+    return table, roof, cg_ms, newton_ms, launches
+
+
+def fibres_bench(combo, ctx, stream, peak, peak_kind, steps=40, warmup=8):
+    """The 512^3 fibre workload (z-fibres of radius 10 voxels, fibre fraction
+    0.3, contrast 50, simple shear Fbar12 = 0.15 in 15 steps; FP32 fields with
+    double-float residuals, FP64 laminates and norms): a timed window of whole
+    Newton steps, its kernel table and the dominant kernel's roofline."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.fibres_512()
+    V = p["n"][0] * p["n"][1] * p["n"][2]
+    prec = combo.FP32_REFINED_DF
+    t, ops, residuals, prof, _ = timed_window(combo, ctx, p, prec, steps, warmup, stream)
+    table, roof, cg_ms, newton_ms, _ = kernel_table(combo, prof, p, prec, ops, peak, peak_kind)
+    return {"workload": "fibres_512", "voxels": V, "boxels": int(p["boxel_idx"].size),
+            "value": ops * V / (t / 1e3), "unit": METRIC, "ms_window": t, "operator_applications": int(ops),
+            "newton_residuals": int(residuals), "ms_per_cg_iteration": cg_ms / max(ops, 1),
+            "newton_residual_ms_per_step": newton_ms / max(residuals, 1), "roofline": roof, "kernels": table}
 
 
 def run_e2e(p, prec, combo, ctx, V):
@@ -446,11 +494,16 @@ def run_e2e(p, prec, combo, ctx, V):
             "note": "one full combo_solve from host buffers; per-step bytes = totals / operator applications"}
 
 
-def serving_problems(count, seed, sides, max_steps):
-    """A stream of solve requests: grid side from ``sides`` (log-uniform),
-    random balls (vf <= 0.18) or z-fibres (vf <= 0.25), vf drawn U(0.1, 0.3)
-    then capped, contrast 10, random Fbar
-    (stretch <= 8 %, shear <= 10 %), 1..max_steps load steps."""
+SERVE_SIDES = (64, 72, 96, 108, 128, 144, 192, 216, 256)
+
+
+def serving_problems(count, seed, sides=SERVE_SIDES, max_steps=10):
+    """The request stream: grid side log-uniform in [64, 256], snapped to the
+    2^a 3^b sides above; half random balls of the 256^3 workload's family
+    (radius 12 voxels, vf 0.25, contrast 100, uniaxial stretch Fbar11 drawn
+    in [1.02, 1.10]), half straight z-fibres of the 512^3 family (radius 10
+    voxels, fibre fraction 0.3, contrast 50, simple shear Fbar12 drawn in
+    [0.03, 0.15]); 1..max_steps load steps."""
     from paper_2204_13624_gb300 import microstructure as ms
 
     rng = np.random.default_rng(seed)
@@ -458,67 +511,77 @@ def serving_problems(count, seed, sides, max_steps):
     out = []
     for i in range(count):
         side = int(sides[int(np.argmin(np.abs(logs - rng.uniform(logs[0], logs[-1]))))])
-        Fb = np.eye(3) + np.diag(rng.uniform(-0.08, 0.08, 3))
-        off = rng.uniform(-0.10, 0.10, (3, 3))
-        np.fill_diagonal(off, 0.0)
-        Fb = Fb + off
         steps = int(rng.integers(1, max_steps + 1))
-        vf = float(rng.uniform(0.1, 0.3))
         sd = int(rng.integers(1 << 30))
-        # centre gap 1.75 voxels (> a voxel diagonal: no voxel is cut twice);
-        # volume fractions capped where random sequential addition jams
+        Fb = np.eye(3)
         if rng.random() < 0.5:
-            p = ms.random_spheres((side,) * 3, max(4.0, side / 10), min(vf, 0.18), sd, 10.0, Fb, steps, gap_vox=1.75)
+            Fb[0, 0] = float(rng.uniform(1.02, 1.10))
+            p = ms.random_spheres((side,) * 3, 12.0, 0.25, sd, 100.0, Fb, steps, gap_vox=2.0)
         else:
-            p = ms.random_fibres((side,) * 3, max(3.0, side / 12), min(vf, 0.25), sd, 10.0, Fb, steps, gap_vox=1.75)
+            Fb[0, 1] = float(rng.uniform(0.03, 0.15))
+            p = ms.random_fibres((side,) * 3, 10.0, 0.3, sd, 50.0, Fb, steps, gap_vox=2.0)
         out.append(p)
     return out
 
 
-def serving_bench(combo, ctx, count=12, sides=(48, 64, 72, 96), max_steps=4, slots=4, seed=2204_13624 + 4):
-    """Saturated throughput of the request stream (all submitted at once),
-    then Poisson arrivals at 0.7 x that rate for latency percentiles; the
-    refined forms (double-float and FP64 residual transforms) against the
-    plain FP64 form on the same requests."""
-    probs = serving_problems(count, seed, sides, max_steps)
-    out = {"requests": count, "sides": list(sides), "load_steps": f"1..{max_steps}", "slots": slots}
+def _serve(combo, ctx, probs, prec, slots, rate=None, seed=0):
+    """All requests through one server: submitted at once (rate None), or at
+    Poisson arrivals of the given rate; wall time, results, statistics."""
+    srv = combo.Server(ctx, max_slots=slots)
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    next_t = 0.0
+    tk = []
+    for p in probs:
+        if rate:
+            next_t += rng.exponential(1.0 / rate)
+            wait = next_t - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+        tk.append(srv.submit(p, precision=prec, tol=1e-8))
+    res = [srv.wait(t) for t in tk]
+    dt = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    return dt, res, st
+
+
+def serving_bench(combo, ctx, count=40, compare=6, slots=4, seed=2204_13624 + 4):
+    """The request stream through the serving loop in the refined double-float
+    form: saturated throughput (all submitted at once), then Poisson arrivals
+    at 0.7 x that rate for p50 / p99 latency.  The first `compare` requests
+    also run in the refined form with FP64 residual transforms and in plain
+    FP64 (saturated), for the speed-up at equal tolerance and the Pbar error
+    against plain FP64."""
+    probs = serving_problems(count, seed)
+    V = [int(np.prod(p["n"])) for p in probs]
+    out = {"requests": count, "sides": list(SERVE_SIDES), "load_steps": "1..10", "slots": slots,
+           "families": "balls r=12 vox vf 0.25 contrast 100 / z-fibres r=10 vox vf 0.3 contrast 50",
+           "voxels_total": int(sum(V))}
+    dt, res, st = _serve(combo, ctx, probs, combo.FP32_REFINED_DF, slots)
+    rate = count / dt
+    vit = sum(int(r["n_operator"]) * v for r, v in zip(res, V))
+    ent = {"saturated_solves_per_s": rate, "saturated_seconds": dt, "voxel_iterations_per_s": vit / dt,
+           "saturated_p50_seconds": st["p50_seconds"], "saturated_p99_seconds": st["p99_seconds"]}
+    lam = 0.7 * rate
+    dt2, _, st2 = _serve(combo, ctx, probs, combo.FP32_REFINED_DF, slots, rate=lam, seed=seed + 1)
+    ent.update(arrival_rate_per_s=lam, solves_per_s=count / dt2, p50_seconds=st2["p50_seconds"],
+               p99_seconds=st2["p99_seconds"], mean_seconds=st2["mean_seconds"],
+               peak_concurrent=st2["peak_running"])
+    out["refined"] = ent
+    sub = probs[:compare]
+    cmp = {"requests": len(sub)}
     pbar = {}
     for form, prec in (("refined", combo.FP32_REFINED_DF), ("refined_fp64_residual", combo.FP32_REFINED),
                        ("fp64", combo.FP64)):
-        srv = combo.Server(ctx, max_slots=slots)
-        t0 = time.perf_counter()
-        tk = [srv.submit(p, precision=prec, tol=1e-8) for p in probs]
-        res = [srv.wait(t) for t in tk]
-        dt = time.perf_counter() - t0
-        srv.close()
-        pbar[form] = [r["Pbar"][-1] for r in res]
-        rate = count / dt
-        entry = {"saturated_solves_per_s": rate, "saturated_seconds": dt}
-        if form == "refined":
-            rng = np.random.default_rng(seed + 1)
-            lam = 0.7 * rate
-            srv = combo.Server(ctx, max_slots=slots)
-            t0 = time.perf_counter()
-            next_t = 0.0
-            tk = []
-            for p in probs:
-                next_t += rng.exponential(1.0 / lam)
-                wait = next_t - (time.perf_counter() - t0)
-                if wait > 0:
-                    time.sleep(wait)
-                tk.append(srv.submit(p, precision=prec, tol=1e-8))
-            for t in tk:
-                srv.wait(t)
-            dt2 = time.perf_counter() - t0
-            st = srv.stats()
-            srv.close()
-            entry.update(arrival_rate_per_s=lam, solves_per_s=count / dt2, p50_seconds=st["p50_seconds"],
-                         p99_seconds=st["p99_seconds"], peak_concurrent=st["peak_running"])
-        out[form] = entry
+        d, r, _ = _serve(combo, ctx, sub, prec, slots)
+        cmp[form] = {"saturated_solves_per_s": len(sub) / d, "saturated_seconds": d}
+        pbar[form] = [x["Pbar"] for x in r]
     for form in ("refined", "refined_fp64_residual"):
         errs = [float(np.max(np.abs(a - b)) / np.max(np.abs(b))) for a, b in zip(pbar[form], pbar["fp64"])]
-        out[f"Pbar_rel_err_{form}_vs_fp64_max"] = max(errs)
-        out[f"speedup_{form}_vs_fp64"] = out[form]["saturated_solves_per_s"] / out["fp64"]["saturated_solves_per_s"]
+        cmp[f"Pbar_rel_err_{form}_vs_fp64_max"] = max(errs)
+        cmp[f"speedup_{form}_vs_fp64"] = cmp["fp64"]["saturated_seconds"] / cmp[form]["saturated_seconds"]
+    out["compare_first_requests"] = cmp
     return out
 
 

@@ -15,10 +15,12 @@
 #include <mutex>
 #include <tuple>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstddef>
 #include <type_traits>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -391,6 +393,32 @@ struct Profiler {
         for (auto e : pool) cudaEventDestroy(e);
     }
 };
+
+static double wall_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// COMBO_PROFILE set in the environment: batches time every kernel launch
+// class with CUDA events and print the table to stderr when they finish
+// (eager launches in place of the captured CG graphs)
+static bool env_profile()
+{
+    const char* e = std::getenv("COMBO_PROFILE");
+    return e && *e && *e != '0';
+}
+
+static void print_profile(const char* what, Profiler& p)
+{
+    p.collect();
+    double tot = 0.0;
+    for (int k = 0; k < K_NCLASS; k++) tot += p.ms[k];
+    std::fprintf(stderr, "[combo profile] %s: %.3f ms in kernels\n", what, tot);
+    for (int k = 0; k < K_NCLASS; k++)
+        if (p.launches[k])
+            std::fprintf(stderr, "[combo profile]   %-16s %8lld launches %10.3f ms\n", kclass_name[k], p.launches[k],
+                         p.ms[k]);
+}
 
 // ------------------------------------------------------------------ operator engine
 // One FFT + Green-operator pipeline in precision T.
@@ -1089,6 +1117,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     // arrays even for one problem, scalars in the batch's shared array, no
     // launch-shape tuning (the batch runs grouped launches)
     bool member = false;
+    bool own_launches = false;  // a member that runs its own (tuned, specialised) launch sequences
     Scalars* ext_sc = nullptr;
     bool whole_newton = false;  // advance_newton: a reached limit stops only between Newton steps
     int error = 0;
@@ -1278,7 +1307,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         iters.assign(hp.n_steps, 0);
         cg_iters.assign(hp.n_steps, 0);
         CK(cudaStreamSynchronize(st));
-        if (newton() && !member) {
+        if (newton() && (!member || own_launches)) {
             if ((rc = autotune())) return rc;
             tune_force(ec);
         }
@@ -1880,6 +1909,16 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
 
     int run_batch() override
     {
+        prof.on = env_profile();
+        const int rc = run_batch_rounds();
+        if (prof.on) {
+            cudaStreamSynchronize(st);
+            print_profile("stacked batch", prof);
+        }
+        return rc;
+    }
+    int run_batch_rounds()
+    {
         CK(cudaSetDevice(ctx->device));
         if (!newton()) return error = fail(COMBO_E_INVALID_ARG, "a batch runs the Newton-CG solver");
         ps.assign(B, PState{});
@@ -2301,14 +2340,18 @@ template <typename A> struct GroupBuf {
 
 // A batch of Newton-CG problems on different grids.  The problems of each
 // distinct grid (sides and cell size) form one stacked solve (a class); the
-// classes advance in lockstep rounds like the stacked batch, and every pass
+// classes advance in lockstep rounds like the stacked batch.  A class whose
+// stacked grid fills the GPU on its own (kOwnVoxels) runs its own tuned
+// launch sequences on a stream of its own; for all other classes every pass
 // of every operator application -- laminate solves, x-forward, y, z + Green
 // operator, y inverse, x-inverse -- is ONE grouped launch over the work items
-// of all classes (grouped x-, y-, z-pass and boxel kernels).  The CG loop is
-// replayed from a captured CUDA graph of kCgChunk iterations.  A class runs
-// the same pass bodies and reductions as its own stacked solve would with
-// the engine's default launch shapes, so each result equals its single
-// solve within the Krylov rounding.
+// of all of them (grouped x-, y-, z-pass and boxel kernels) on another
+// stream, so the small grids run beside the large ones.  Each CG chunk of
+// kCgChunk iterations is replayed from one captured CUDA graph whose
+// branches are these streams.  A class runs the same pass bodies and
+// reductions as its own stacked solve would (grouped classes with the
+// engine's default launch shapes), so each result equals its single solve
+// within the Krylov rounding.
 template <typename Tc, typename Rt> struct MixSolve : SolveBase {
     using Cls = Solve<Tc, Rt>;
     combo_ctx* ctx = nullptr;
@@ -2329,18 +2372,43 @@ template <typename Tc, typename Rt> struct MixSolve : SolveBase {
     GroupBuf<YArgs<Tc>> g_y_cg;
     GroupBuf<ZArgs<Tc>> g_z_cg;
     GroupBuf<XinvArgs<Tc, Tc>> g_xi_cg;
-    Profiler prof;
+    Profiler prof;  // the grouped launches (on st_group)
     cudaGraphExec_t cg_exec = nullptr;
     int64_t cg_chunks_run = 0;
     volatile int cancel_requested = 0;
     int error = 0;
     static constexpr int kCgChunk = 8;
+    static constexpr int64_t kOwnVoxels = int64_t(6) << 20;  // stacked voxels of a class that fills the GPU
+    std::vector<char> own;             // class runs its own launch sequences
+    cudaStream_t st_group = nullptr;   // the grouped launches
+    std::vector<cudaStream_t> sides;   // st_group and the streams of the own-launch classes
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
 
     ~MixSolve() override
     {
         if (cg_exec) cudaGraphExecDestroy(cg_exec);
         cls.clear();
         cudaFree(d_sc);
+        for (auto s2 : sides) cudaStreamDestroy(s2);
+        for (auto e : ev_join) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+    }
+    // every side stream waits for the work queued on st so far; st waits
+    // for all of them (the lockstep's host reads and F updates run on st)
+    int fork()
+    {
+        CK(cudaEventRecord(ev_fork, st));
+        for (auto s2 : sides) CK(cudaStreamWaitEvent(s2, ev_fork, 0));
+        return COMBO_OK;
+    }
+    int join()
+    {
+        for (size_t i = 0; i < sides.size(); i++) {
+            CK(cudaEventRecord(ev_join[i], sides[i]));
+            CK(cudaStreamWaitEvent(st, ev_join[i], 0));
+        }
+        return COMBO_OK;
     }
     bool linear() const { return opt.theory == COMBO_INFINITESIMAL_STRAIN; }
 
@@ -2372,32 +2440,60 @@ template <typename Tc, typename Rt> struct MixSolve : SolveBase {
         CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars) * P, st));
         hsc.resize(P);
         int rc, o0 = 0;
+        CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        CK(cudaStreamCreateWithFlags(&st_group, cudaStreamNonBlocking));
+        sides.push_back(st_group);
+        prof.st = st_group;
         for (size_t k = 0; k < groups.size(); k++) {
             off.push_back(o0);
             auto q = std::make_unique<Cls>();
             q->member = true;
+            const int64_t vox = (int64_t)groups[k].size() * groups[k][0].n[0] * groups[k][0].n[1] * groups[k][0].n[2];
+            q->own_launches = vox >= kOwnVoxels;
+            own.push_back(q->own_launches ? 1 : 0);
             q->ext_sc = d_sc + o0;
             o0 += (int)groups[k].size();
             rc = q->init(c, std::move(groups[k]), o);
             cls.push_back(std::move(q));
             if (rc) return rc;
+            Cls& m = *cls.back();
+            if (m.own_launches) {
+                cudaStream_t s2;
+                CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+                sides.push_back(s2);
+                m.st = s2;
+            } else {
+                m.st = st_group;
+            }
+            m.prof.st = m.st;
         }
+        ev_join.resize(sides.size(), nullptr);
+        for (auto& e : ev_join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        CK(cudaStreamSynchronize(st));
         return build_groups();
     }
 
     // the grouped launches' tables: the arguments each class's own launches
     // would take (default launch shapes, guards of the lockstep batch)
+    std::vector<int> grouped() const
+    {
+        std::vector<int> g;
+        for (int k = 0; k < (int)cls.size(); k++)
+            if (!own[k]) g.push_back(k);
+        return g;
+    }
     int build_groups()
     {
-        const int K = (int)cls.size();
+        const std::vector<int> G = grouped();
+        const int K = (int)G.size();
         int rc;
         {
             std::vector<BoxelArgs<Tc>> a;
             std::vector<int> it;
-            for (auto& q : cls)
-                if (q->nb > 0) {
-                    a.push_back(q->boxel_args(true, 2));
-                    it.push_back((int)((q->nb + 127) / 128));
+            for (int k : G)
+                if (cls[k]->nb > 0) {
+                    a.push_back(cls[k]->boxel_args(true, 2));
+                    it.push_back((int)((cls[k]->nb + 127) / 128));
                 }
             if ((rc = g_box.build(a, it, {}, 0, st))) return rc;
         }
@@ -2406,11 +2502,12 @@ template <typename Tc, typename Rt> struct MixSolve : SolveBase {
             std::vector<XinvArgs<Rt, Tc>> b(K);
             std::vector<int> it(K);
             size_t sm = 0;
-            for (int k = 0; k < K; k++) {
-                a[k] = cls[k]->resid_xf(XI_RHS);
-                b[k] = cls[k]->resid_xi(XI_RHS);
-                it[k] = cls[k]->e64.xblocks();
-                sm = std::max(sm, xpass_smem(cls[k]->g, cls[k]->e64.lines, sizeof(cx<Rt>)));
+            for (int i = 0; i < K; i++) {
+                const Cls& q = *cls[G[i]];
+                a[i] = q.resid_xf(XI_RHS);
+                b[i] = q.resid_xi(XI_RHS);
+                it[i] = q.e64.xblocks();
+                sm = std::max(sm, xpass_smem(q.g, q.e64.lines, sizeof(cx<Rt>)));
             }
             if ((rc = g_xf_res.build(a, it, {}, sm, st))) return rc;
             if ((rc = g_xi_res.build(b, it, {}, sm, st))) return rc;
@@ -2420,11 +2517,12 @@ template <typename Tc, typename Rt> struct MixSolve : SolveBase {
             std::vector<XinvArgs<Tc, Tc>> b(K);
             std::vector<int> it(K);
             size_t sm = 0;
-            for (int k = 0; k < K; k++) {
-                a[k] = cls[k]->cg_xf();
-                b[k] = cls[k]->cg_xi();
-                it[k] = cls[k]->ec.xblocks();
-                sm = std::max(sm, xpass_smem(cls[k]->g, cls[k]->ec.lines, sizeof(cx<Tc>)));
+            for (int i = 0; i < K; i++) {
+                const Cls& q = *cls[G[i]];
+                a[i] = q.cg_xf();
+                b[i] = q.cg_xi();
+                it[i] = q.ec.xblocks();
+                sm = std::max(sm, xpass_smem(q.g, q.ec.lines, sizeof(cx<Tc>)));
             }
             if ((rc = g_xf_cg.build(a, it, {}, sm, st))) return rc;
             if ((rc = g_xi_cg.build(b, it, {}, sm, st))) return rc;
@@ -2435,13 +2533,14 @@ template <typename Tc, typename Rt> struct MixSolve : SolveBase {
 
     template <typename T> int build_yz(GroupBuf<YArgs<T>>& gy, GroupBuf<ZArgs<T>>& gz, bool resid)
     {
-        const int K = (int)cls.size();
+        const std::vector<int> G = grouped();
+        const int K = (int)G.size();
         std::vector<YArgs<T>> ya(K);
         std::vector<ZArgs<T>> za(K);
         std::vector<int> yi(K), zi(K), yd(2 * K), zd(2 * K);
         size_t ysm = 0, zsm = 0;
         for (int k = 0; k < K; k++) {
-            Cls& q = *cls[k];
+            Cls& q = *cls[G[k]];
             const Engine<T>& e = engine_of<T>(q, resid);
             ya[k] = e.yargs(q.d_sc, resid ? 2 : 1);
             za[k] = e.zargs(q.d_sc, resid ? 2 : 1, resid, resid ? q.d_part : nullptr);
@@ -2476,54 +2575,79 @@ template <typename Tc, typename Rt> struct MixSolve : SolveBase {
             return q.ec;
     }
 
-    // --- grouped sequences
-    void residual()
+    // --- launch sequences: the grouped classes on st_group, each own-launch
+    // class on its stream, between a fork from and a join into st
+    int residual()
     {
+        int rc;
+        if ((rc = fork())) return rc;
+        const cudaStream_t sg = st_group;
         prof.begin(K_BOXEL);
-        launch_group_boxel<Tc>(g_box.t, std::is_same<Rt, df32>::value, linear(), st);
+        launch_group_boxel<Tc>(g_box.t, std::is_same<Rt, df32>::value, linear(), sg);
         prof.end();
         prof.begin(K_XFWD_RESID);
-        launch_group_xfwd<Rt, Tc>(g_xf_res.t, false, 2, st);
+        launch_group_xfwd<Rt, Tc>(g_xf_res.t, false, 2, sg);
         prof.end();
         prof.begin(K_YFWD_64);
-        launch_group_ypass<Rt, false>(g_y_res.t, st);
+        launch_group_ypass<Rt, false>(g_y_res.t, sg);
         prof.end();
         prof.begin(K_ZGAMMA_64);
-        launch_group_zpass<Rt>(g_z_res.t, st);
+        launch_group_zpass<Rt>(g_z_res.t, sg);
         prof.end();
         prof.begin(K_YINV_64);
-        launch_group_ypass<Rt, true>(g_y_res.t, st);
+        launch_group_ypass<Rt, true>(g_y_res.t, sg);
         prof.end();
-        for (auto& q : cls) q->fin_resid(XI_RHS);
+        for (int k : grouped()) cls[k]->fin_resid(XI_RHS);
         prof.begin(K_XINV_64);
-        launch_group_xinv<Rt, Tc>(g_xi_res.t, 2, st);
+        launch_group_xinv<Rt, Tc>(g_xi_res.t, 2, sg);
         prof.end();
-        for (auto& q : cls) q->fin_rhs();
+        for (int k : grouped()) cls[k]->fin_rhs();
+        for (size_t k = 0; k < cls.size(); k++)
+            if (own[k]) {
+                cls[k]->boxels(true, 2);
+                cls[k]->resid_operator(XI_RHS, 2);
+            }
+        return join();
     }
-    void cg_iteration()
+    void group_cg_iteration()
     {
+        const cudaStream_t sg = st_group;
         prof.begin(K_XFWD_TANGENT);
-        launch_group_xfwd<Tc, Tc>(g_xf_cg.t, true, 1, st);
+        launch_group_xfwd<Tc, Tc>(g_xf_cg.t, true, 1, sg);
         prof.end();
         prof.begin(K_YFWD_C);
-        launch_group_ypass<Tc, false>(g_y_cg.t, st);
+        launch_group_ypass<Tc, false>(g_y_cg.t, sg);
         prof.end();
         prof.begin(K_ZGAMMA_C);
-        launch_group_zpass<Tc>(g_z_cg.t, st);
+        launch_group_zpass<Tc>(g_z_cg.t, sg);
         prof.end();
         prof.begin(K_YINV_C);
-        launch_group_ypass<Tc, true>(g_y_cg.t, st);
+        launch_group_ypass<Tc, true>(g_y_cg.t, sg);
         prof.end();
         prof.begin(K_XINV_CG);
-        launch_group_xinv<Tc, Tc>(g_xi_cg.t, 1, st);
+        launch_group_xinv<Tc, Tc>(g_xi_cg.t, 1, sg);
         prof.end();
+    }
+    int cg_chunk()
+    {
+        int rc;
+        if ((rc = fork())) return rc;
+        for (int j = 0; j < kCgChunk; j++) group_cg_iteration();
+        for (size_t k = 0; k < cls.size(); k++)
+            if (own[k])
+                for (int j = 0; j < kCgChunk; j++) cls[k]->cg_iteration();
+        return join();
     }
     int capture_cg_chunk()
     {
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        for (int k = 0; k < kCgChunk; k++) cg_iteration();
+        const int rc = cg_chunk();
         const cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
         if (e != cudaSuccess) return fail(COMBO_E_CUDA, std::string("CG graph capture: ") + cudaGetErrorString(e));
         const cudaError_t e2 = cudaGraphInstantiate(&cg_exec, graph, 0);
         cudaGraphDestroy(graph);
@@ -2561,6 +2685,24 @@ template <typename Tc, typename Rt> struct MixSolve : SolveBase {
     // Newton-CG in lockstep rounds over every problem of every class (the
     // stacked batch's rounds, with grouped launches)
     int run_batch() override
+    {
+        prof.on = env_profile();
+        for (auto& q : cls) q->prof.on = prof.on;
+        const int rc = run_rounds();
+        if (prof.on) {
+            cudaDeviceSynchronize();
+            print_profile("batch over several grids: grouped classes", prof);
+            for (size_t k = 0; k < cls.size(); k++)
+                if (own[k]) {
+                    char what[96];
+                    std::snprintf(what, sizeof what, "  own-launch class %dx%dx%d x%d", cls[k]->hp.n[0],
+                                  cls[k]->hp.n[1], cls[k]->hp.n[2], cls[k]->B);
+                    print_profile(what, cls[k]->prof);
+                }
+        }
+        return rc;
+    }
+    int run_rounds()
     {
         CK(cudaSetDevice(ctx->device));
         if (opt.solver != COMBO_NEWTON_CG) return error = fail(COMBO_E_INVALID_ARG, "a batch runs the Newton-CG solver");
@@ -2616,7 +2758,7 @@ template <typename Tc, typename Rt> struct MixSolve : SolveBase {
             // Newton iterations of this round
             while (true) {
                 if (cancel_requested) return error = fail(COMBO_E_CANCELLED, "solve cancelled");
-                residual();
+                if ((rc = residual())) return error = rc;
                 CK(cudaGetLastError());
                 if ((rc = read_all())) return error = rc;
                 if ((rc = status("residual evaluation failed"))) return rc;
@@ -2652,7 +2794,7 @@ template <typename Tc, typename Rt> struct MixSolve : SolveBase {
                 // CG on every problem still iterating, kCgChunk iterations per host round trip
                 while (true) {
                     if (prof.on || cg_chunks_run == 0) {
-                        for (int j = 0; j < kCgChunk; j++) cg_iteration();
+                        if ((rc = cg_chunk())) return error = rc;
                     } else {
                         if (!cg_exec && (rc = capture_cg_chunk())) return error = rc;
                         CK(cudaGraphLaunch(cg_exec, st));
@@ -2966,11 +3108,17 @@ extern "C" int combo_solve_batch(combo_ctx* ctx, int32_t n_problems, const combo
     if (!same) {
         // problems on several grids: one stacked class per grid, grouped launches
         SolveBase* impl = nullptr;
+        const double t0 = wall_s();
         rc = make_mix(ctx, std::move(hs), o, &impl);
+        const double t1 = wall_s();
         if (!rc) rc = impl->run_batch();
+        const double t2 = wall_s();
         const std::string msg = g_err;
         if (!rc) rc = impl->batch_results(results);
         delete impl;
+        if (env_profile())
+            std::fprintf(stderr, "[combo profile] set-up %.3f s, rounds %.3f s, results and release %.3f s\n",
+                         t1 - t0, t2 - t1, wall_s() - t2);
         if (rc) {
             cudaGetLastError();
             g_err = msg.empty() ? g_err : msg;

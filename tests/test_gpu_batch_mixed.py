@@ -101,3 +101,22 @@ def test_mixed_batch_counts_and_errors(cb):
     with pytest.raises(cb.ComboError) as e:
         cb.solve_batch([ms.homogeneous((8, 8, 8)), ms.sphere_32(n_steps=1)], nr_max_iter=1)
     assert e.value.code == -4 and "problem 1" in str(e.value)
+
+
+def test_large_class_runs_its_own_launches_beside_the_grouped_ones(cb):
+    """A 192^3 problem fills the GPU on its own, so its class runs its own
+    tuned launch sequences on a stream of its own while the small grids'
+    classes share the grouped launches on another; every result still
+    equals its single solve."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    Fb = np.eye(3) + np.diag([0.03, -0.01, 0.0])
+    probs = [ms.random_spheres((192, 192, 192), 9.0, 0.15, 21, 10.0, Fb, 2)] + mixed_problems(4)[1:4]
+    for prec in (cb.FP64, cb.FP32_REFINED_DF):
+        tol_pbar = 1e-9 if prec == cb.FP64 else 1e-6
+        alone = [cb.solve(p, precision=prec, tol=1e-8, fields=True) for p in probs]
+        out = cb.solve_batch(probs, precision=prec, tol=1e-8)
+        for p, a, g in zip(probs, alone, out):
+            assert g["steps_done"] == p["n_steps"] and np.all(g["resid"] <= 1e-8)
+            assert rel(g["Pbar"], a["Pbar"]) < tol_pbar
+            assert rel(g["F"], a["F"]) < 1e-4
