@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--serve-only", action="store_true", help="only the serving section")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel table here")
     ap.add_argument("--batch-only", action="store_true", help="only the 64-solve batch section")
+    ap.add_argument("--fibres-only", action="store_true", help="only the 512^3 fibre section")
     ap.add_argument("--dfmg-only", type=int, default=0, metavar="N",
                     help="only the doubly-fine material grid kernel timings on an N^3 random-ball problem")
     return ap.parse_args()
@@ -285,6 +286,10 @@ def main():
     if args.serve_only:
         print(json.dumps({"serving": serving_bench(combo, ctx, count=120, compare=24) if args.serve_full
                           else serving_bench(combo, ctx)}))
+        return
+    if args.fibres_only:
+        peak, peak_kind = peaks()
+        print(json.dumps({"fibres_512": fibres_bench(combo, ctx, stream, peak, peak_kind)}))
         return
     if args.batch_only:
         print(json.dumps({"batch": batch_bench(combo, ctx)}))

@@ -173,6 +173,7 @@ struct LamEvalD {
     PhaseD p, m;
     double f[3];
     double err, eps;
+    double tol;    // the laminate tolerance (eps before the rounding-level floor)
     double floor;  // rounding level of f in double-float: below it only FP64 can decide
 };
 
@@ -204,6 +205,7 @@ __device__ __forceinline__ bool lam_eval(LamEvalD& e, const df32 Fb[9], const df
     }
     e.err = (double)sqrtf(ff);
     e.eps = tol_rel * ((double)sqrtf(tp) + (double)sqrtf(tm)) + tol_abs * fmax(mu[0], mu[1]);
+    e.tol = e.eps;
     // P = mu F + k F^{-T} is formed from terms of size ~(mu + lam) |F|: 2^-44 of that
     e.floor = 0x1p-44 * (fmax(mu[0], mu[1]) + fmax(lam[0], lam[1])) * (1.0 + (double)sqrtf(tp) + (double)sqrtf(tm));
     return true;
@@ -257,6 +259,16 @@ template <typename S> struct TanPhase {
     {
 #pragma unroll
         for (int q = 0; q < 9; q++) G[q] = (S)s.G[q];
+#pragma unroll
+        for (int q = 0; q < 3; q++) g[q] = (S)s.g[q];
+        mu = (S)mu_;
+        lam = (S)lam_;
+        m = (S)(mu_ - lam_ * s.lnJ);
+    }
+    __device__ __forceinline__ void load(const PhaseD& s, double mu_, double lam_)
+    {
+#pragma unroll
+        for (int q = 0; q < 9; q++) G[q] = (S)(double)s.G[q];
 #pragma unroll
         for (int q = 0; q < 3; q++) g[q] = (S)s.g[q];
         mu = (S)mu_;
@@ -371,6 +383,8 @@ template <typename Tc, bool DFM> __device__ __forceinline__ void boxel_body(cons
             return inv3(Dl, Di);
         };
         double Di[9];
+        LamEvalD ed;           // (double-float form) the last double-float evaluation
+        bool df_done = false;  // (double-float form) its state is the converged one
         if (!status) {
             const double ng = sqrt(gbox[0] * gbox[0] + gbox[1] * gbox[1] + gbox[2] * gbox[2]);
             const double m[3] = {gbox[0] / ng, gbox[1] / ng, gbox[2] / ng};
@@ -382,7 +396,6 @@ template <typename Tc, bool DFM> __device__ __forceinline__ void boxel_body(cons
                 // double-float iterations from a copy of the start; if they
                 // stop early (a phase near collapse, an ill-conditioned
                 // Hessian), the FP64 iterations start over from a
-                LamEvalD ed;
                 double ad[3] = {a[0], a[1], a[2]};
                 const int rdf = nr_loop(
                     ed, ad, m, bcp, bcm, 0.0, it_df, A.max_iter, nbp,
@@ -396,10 +409,16 @@ template <typename Tc, bool DFM> __device__ __forceinline__ void boxel_body(cons
                     a[0] = ad[0];
                     a[1] = ad[1];
                     a[2] = ad[2];
+                    // the double-float residual lies below the tolerance by
+                    // more than its own rounding level: the FP64 residual
+                    // passes the same test, and the FP64 evaluation is skipped
+                    df_done = ed.err + ed.floor <= 0.99 * ed.tol && hessian_inv(ed, cp, cm, mu, lam, Di);
                 }
             }
-            reason = nr_loop(e, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp, eval64, inv64);
-            if (reason) status = COMBO_E_LAMINATE;
+            if (!df_done) {
+                reason = nr_loop(e, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp, eval64, inv64);
+                if (reason) status = COMBO_E_LAMINATE;
+            }
             its = it + it_df;
         } else {
             reason = 1;
@@ -418,46 +437,57 @@ template <typename Tc, bool DFM> __device__ __forceinline__ void boxel_body(cons
                 sc->fail_state[12] = cp;
             }
         } else {
+            // The boxel tangent only feeds the Krylov iterations: it is formed
+            // in their precision Tc from the converged state (FP64, or the
+            // accepted double-float state)
+            auto tangent = [&](const auto& ep, const auto& em) {
+                TanPhase<Tc> tp, tm;
+                tp.load(ep, mu[1], lam[1]);
+                tm.load(em, mu[0], lam[0]);
+                Tc Nt[3] = {(Tc)N[0], (Tc)N[1], (Tc)N[2]};
+                Tc Dt[9];
 #pragma unroll
-            for (int c = 0; c < 9; c++) A.bP[9 * b + c] = cp * e.p.P[c] + cm * e.m.P[c];
+                for (int q = 0; q < 9; q++) Dt[q] = (Tc)Di[q];
+                const Tc cpt = (Tc)cp, cmt = (Tc)cm;
+                // B = dA D (9x3), W = B Delta^{-1}
+                Tc B[27], W[27];
+#pragma unroll
+                for (int r = 0; r < 9; r++)
+#pragma unroll
+                    for (int k = 0; k < 3; k++) B[3 * r + k] = tp.AD(Nt, r / 3, r % 3, k) - tm.AD(Nt, r / 3, r % 3, k);
+#pragma unroll
+                for (int r = 0; r < 9; r++)
+#pragma unroll
+                    for (int k = 0; k < 3; k++)
+                        W[3 * r + k] = B[3 * r] * Dt[k] + B[3 * r + 1] * Dt[3 + k] + B[3 * r + 2] * Dt[6 + k];
+                // A_box is major-symmetric (the second derivative of the
+                // condensed energy): its upper triangle is stored
+                const int64_t kb = A.rank ? (int64_t)A.rank[b] : b;
+#pragma unroll
+                for (int r = 0; r < 9; r++)
+#pragma unroll
+                    for (int s = r; s < 9; s++) {
+                        const Tc avg = cpt * tp.A(r / 3, r % 3, s / 3, s % 3) + cmt * tm.A(r / 3, r % 3, s / 3, s % 3);
+                        const Tc corr = W[3 * r] * B[3 * s] + W[3 * r + 1] * B[3 * s + 1] + W[3 * r + 2] * B[3 * s + 2];
+                        A.bA[(int64_t)sym_idx(r, s) * A.nb + kb] = avg - corr;
+                    }
+            };
+            if (df_done) {
+#pragma unroll
+                for (int c = 0; c < 9; c++) A.bP[9 * b + c] = cp * (double)ed.p.P[c] + cm * (double)ed.m.P[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 9; c++) A.bP[9 * b + c] = cp * e.p.P[c] + cm * e.m.P[c];
+            }
 #pragma unroll
             for (int i = 0; i < 3; i++) A.ba[3 * b + i] = a[i];
             if (A.bA) {
-                if (!inv64(e, Di)) {
+                if (df_done) {
+                    tangent(ed.p, ed.m);
+                } else if (!inv64(e, Di)) {
                     raise_status(sc, COMBO_E_LAMINATE);
                 } else {
-                    // The boxel tangent only feeds the Krylov iterations: it is
-                    // formed in their precision Tc from the converged state.
-                    TanPhase<Tc> tp, tm;
-                    tp.load(e.p, mu[1], lam[1]);
-                    tm.load(e.m, mu[0], lam[0]);
-                    Tc Nt[3] = {(Tc)N[0], (Tc)N[1], (Tc)N[2]};
-                    Tc Dt[9];
-#pragma unroll
-                    for (int q = 0; q < 9; q++) Dt[q] = (Tc)Di[q];
-                    const Tc cpt = (Tc)cp, cmt = (Tc)cm;
-                    // B = dA D (9x3), W = B Delta^{-1}
-                    Tc B[27], W[27];
-#pragma unroll
-                    for (int r = 0; r < 9; r++)
-#pragma unroll
-                        for (int k = 0; k < 3; k++) B[3 * r + k] = tp.AD(Nt, r / 3, r % 3, k) - tm.AD(Nt, r / 3, r % 3, k);
-#pragma unroll
-                    for (int r = 0; r < 9; r++)
-#pragma unroll
-                        for (int k = 0; k < 3; k++)
-                            W[3 * r + k] = B[3 * r] * Dt[k] + B[3 * r + 1] * Dt[3 + k] + B[3 * r + 2] * Dt[6 + k];
-                    // A_box is major-symmetric (the second derivative of the
-                    // condensed energy): its upper triangle is stored
-                    const int64_t kb = A.rank ? (int64_t)A.rank[b] : b;
-#pragma unroll
-                    for (int r = 0; r < 9; r++)
-#pragma unroll
-                        for (int s = r; s < 9; s++) {
-                            const Tc avg = cpt * tp.A(r / 3, r % 3, s / 3, s % 3) + cmt * tm.A(r / 3, r % 3, s / 3, s % 3);
-                            const Tc corr = W[3 * r] * B[3 * s] + W[3 * r + 1] * B[3 * s + 1] + W[3 * r + 2] * B[3 * s + 2];
-                            A.bA[(int64_t)sym_idx(r, s) * A.nb + kb] = avg - corr;
-                        }
+                    tangent(e.p, e.m);
                 }
             }
         }

@@ -33,8 +33,9 @@ namespace {
 // autotuner picks one per grid; candidate 0 is the default)
 template <int N, int C> __host__ __device__ constexpr int tma_tx()
 {
-    return (N == 256 ? 8 : 16) >> C;
+    return (N == 512 ? 4 : (N == 256 ? 8 : 16)) >> C;
 }
+__host__ __device__ constexpr int tma_tx_rt(int n, int c) { return (n == 512 ? 4 : (n == 256 ? 8 : 16)) >> c; }
 // x-frequency widths of a y-pass tile
 template <int C> __host__ __device__ constexpr int tma_tyx() { return 16 >> C; }
 
@@ -55,7 +56,47 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 }  // namespace
 
-bool zpass_tma_size(int n3) { return n3 == 64 || n3 == 128 || n3 == 256; }
+bool zpass_tma_size(int n3) { return n3 == 64 || n3 == 128 || n3 == 256 || n3 == 512; }
+
+// Encode a tiled map of the complex FP32 spectrum [9][n3][n2][nhp]; an axis
+// of 512 (the tile's long axis: z for the z-pass, y for the y-pass) is split
+// into 256 x 2 (5-D map), since a box dimension holds at most 256 elements;
+// the box then covers the whole axis as 256 x 2 with the shared-memory
+// layout of the 4-D box.
+static bool encode_spec_map(void* map, const GridDims& g, const void* spec, const cuuint32_t box4[4], int split_axis)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t d4[4] = {(cuuint64_t)g.nhp, (cuuint64_t)g.n2, (cuuint64_t)g.n3, 9};
+    const cuuint64_t s4[4] = {8, (cuuint64_t)g.nhp * 8, (cuuint64_t)g.n2 * g.nhp * 8,
+                              (cuuint64_t)g.n3 * g.n2 * g.nhp * 8};
+    cuuint64_t dim[5], stride[4];
+    cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+    int nd = 0;
+    for (int a = 0; a < 4; a++) {
+        if (a == split_axis) {
+            if (d4[a] % 256 != 0 || box4[a] != 512) return false;
+            dim[nd] = 256;
+            box[nd] = 256;
+            if (nd > 0) stride[nd - 1] = s4[a];
+            nd++;
+            dim[nd] = d4[a] / 256;
+            box[nd] = 2;
+            stride[nd - 1] = s4[a] * 256;
+            nd++;
+        } else {
+            dim[nd] = d4[a];
+            box[nd] = box4[a];
+            if (nd > 0) stride[nd - 1] = s4[a];
+            nd++;
+        }
+    }
+    const CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, nd,
+                          const_cast<void*>(spec), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 // Tensor map of a complex FP32 half spectrum [9][n3][n2][nhp] for the z-pass
 // tile box {TX, 1, n3, 3}.  False (map unusable) for other sizes or when the
@@ -63,20 +104,10 @@ bool zpass_tma_size(int n3) { return n3 == 64 || n3 == 128 || n3 == 256; }
 bool zpass_tma_encode(void* map, const GridDims& g, const void* spec, int cand)
 {
     if (!zpass_tma_size(g.n3p) || !spec) return false;
-    const int tx = (g.n3p == 256 ? 8 : 16) >> cand;
+    const int tx = tma_tx_rt(g.n3p, cand);
     if ((g.nhp * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(spec) & 15) != 0) return false;
-    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-    if (!fn) return false;
-    const cuuint64_t dim[4] = {(cuuint64_t)g.nhp, (cuuint64_t)g.n2, (cuuint64_t)g.n3, 9};
-    const cuuint64_t stride[3] = {(cuuint64_t)g.nhp * 8, (cuuint64_t)g.n2 * g.nhp * 8,
-                                  (cuuint64_t)g.n3 * g.n2 * g.nhp * 8};
     const cuuint32_t box[4] = {(cuuint32_t)tx, 1, (cuuint32_t)g.n3p, 3};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, 4,
-                          const_cast<void*>(spec), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
+    return encode_spec_map(map, g, spec, box, g.n3p > 256 ? 2 : -1);
 }
 
 template <int N, int TX>
@@ -116,7 +147,10 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL)
         const int y = rest % g.n2, rb = rest / g.n2;
         const int b = rb / 3, row = rb - 3 * b;
         mbar_arrive_expect_tx(&bar[s], TILE_BYTES);
-        tma_load_4d(tiles + s * TILE, &tm, xt * TX, y, b * N, 3 * row, &bar[s]);
+        if constexpr (N > 256)
+            tma_load_5d(tiles + s * TILE, &tm, xt * TX, y, 0, b * (N / 256), 3 * row, &bar[s]);
+        else
+            tma_load_4d(tiles + s * TILE, &tm, xt * TX, y, b * N, 3 * row, &bar[s]);
     };
 
     if (threadIdx.x == 0) {
@@ -204,7 +238,10 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL)
         fence_proxy_async();  // this thread's tile writes, before the copy engine reads them
         __syncthreads();
         if (threadIdx.x == 0) {
-            tma_store_4d(&tm, x0, y, pb * N, 3 * row, park);
+            if constexpr (N > 256)
+                tma_store_5d(&tm, x0, y, 0, pb * (N / 256), 3 * row, park);
+            else
+                tma_store_4d(&tm, x0, y, pb * N, 3 * row, park);
             bulk_commit();
         }
     }
@@ -228,18 +265,8 @@ bool ypass_tma_encode(void* map, const GridDims& g, const void* spec, int cand)
     const int TYX = 16 >> cand;
     if (!zpass_tma_size(g.n2) || !spec) return false;
     if ((g.nhp * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(spec) & 15) != 0) return false;
-    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-    if (!fn) return false;
-    const cuuint64_t dim[4] = {(cuuint64_t)g.nhp, (cuuint64_t)g.n2, (cuuint64_t)g.n3, 9};
-    const cuuint64_t stride[3] = {(cuuint64_t)g.nhp * 8, (cuuint64_t)g.n2 * g.nhp * 8,
-                                  (cuuint64_t)g.n3 * g.n2 * g.nhp * 8};
     const cuuint32_t box[4] = {(cuuint32_t)TYX, (cuuint32_t)g.n2, 1, 1};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, 4,
-                          const_cast<void*>(spec), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
+    return encode_spec_map(map, g, spec, box, g.n2 > 256 ? 1 : -1);
 }
 
 template <int N, int TX, bool INV>
@@ -272,7 +299,10 @@ __global__ void __launch_bounds__(TX * FastPlan<N>::TPL)
         const int xt = t % nxt, rest = t / nxt;
         const int z = rest % g.n3, c = rest / g.n3;
         mbar_arrive_expect_tx(&bar[s], TILE_BYTES);
-        tma_load_4d(tiles + s * TILE, &tm, xt * TX, 0, z, c, &bar[s]);
+        if constexpr (N > 256)
+            tma_load_5d(tiles + s * TILE, &tm, xt * TX, 0, 0, z, c, &bar[s]);
+        else
+            tma_load_4d(tiles + s * TILE, &tm, xt * TX, 0, z, c, &bar[s]);
     };
 
     if (threadIdx.x == 0) {
@@ -308,7 +338,10 @@ __global__ void __launch_bounds__(TX * FastPlan<N>::TPL)
         fence_proxy_async();  // this thread's tile writes, before the copy engine reads them
         __syncthreads();
         if (threadIdx.x == 0) {
-            tma_store_4d(&tm, xt * TX, 0, z, c, park);
+            if constexpr (N > 256)
+                tma_store_5d(&tm, xt * TX, 0, 0, z, c, park);
+            else
+                tma_store_4d(&tm, xt * TX, 0, z, c, park);
             bulk_commit();
         }
     }
@@ -359,7 +392,8 @@ template <bool INV> void launch_ypass_tma(const YArgs<float>& a, const void* map
     switch (a.g.n2) {
         case 64: ypass_tma_pick<64, INV>(a, map, st); break;
         case 128: ypass_tma_pick<128, INV>(a, map, st); break;
-        default: ypass_tma_pick<256, INV>(a, map, st); break;
+        case 256: ypass_tma_pick<256, INV>(a, map, st); break;
+        default: ypass_tma_pick<512, INV>(a, map, st); break;
     }
 }
 template void launch_ypass_tma<false>(const YArgs<float>&, const void*, cudaStream_t);
@@ -401,7 +435,8 @@ void launch_zpass_tma(const ZArgs<float>& a, const void* map, cudaStream_t st)
     switch (a.g.n3p) {
         case 64: zpass_tma_pick<64>(a, map, st); break;
         case 128: zpass_tma_pick<128>(a, map, st); break;
-        default: zpass_tma_pick<256>(a, map, st); break;
+        case 256: zpass_tma_pick<256>(a, map, st); break;
+        default: zpass_tma_pick<512>(a, map, st); break;
     }
 }
 

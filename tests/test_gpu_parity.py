@@ -171,6 +171,21 @@ def test_newton_cg_parity_fast_sizes(cb, orc, prec):
         assert rel(g["Pbar"], r["Pbar"]) < (1e-9 if prec == 0 else 2e-5)
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+def test_newton_cg_parity_tma_512(cb, orc, prec):
+    """Sides of 512 along y and z: the TMA-tiled FP32 y- and z-passes through
+    5-D tensor maps (the 512-long axis as 256 x 2), rotated and staggered
+    grids, against the oracle after equal iterations."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    for n, ks in [((8, 8, 512), 0), ((8, 512, 8), 0), ((8, 512, 64), 0), ((16, 64, 512), 0), ((8, 8, 512), 2)]:
+        p = ms.random_spheres(n, 3.0, 0.12, 17, 10.0, np.diag([1.03, 1.0, 1.0]) + 0.01, 1)
+        g, r = solve_both(cb, orc, p, solver=1, kspace=ks, precision=prec, fixed_iterations=1,
+                          cg_fixed_iterations=10)
+        assert rel(g["F"], r["F"]) < 2e-5
+        assert rel(g["Pbar"], r["Pbar"]) < 2e-5
+
+
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_staggered_parity_fast_sizes(cb, orc, prec):
     """The staggered grid (App. A) through every z-pass variant: runtime
