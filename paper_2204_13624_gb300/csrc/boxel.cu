@@ -322,6 +322,44 @@ __device__ __forceinline__ int nr_loop(LE& e, double a[3], const double m[3], do
     return 0;
 }
 
+// The packed boxel tangent A_box = c+ A+ + c- A- - dA D Delta^{-1} D^T dA
+// (Sec. 4.1) in precision Tc from a converged laminate state (FP64 or double-
+// float phases ep, em) and Delta^{-1} (Di): the 45 entries of its upper
+// triangle (major symmetry) go to out[sym_idx * stride + col].
+template <typename Tc, typename PH>
+__device__ __forceinline__ void boxel_tangent_store(const PH& ep, const PH& em, const double N[3], double cp,
+                                                    double cm, const double mu[2], const double lam[2],
+                                                    const double Di[9], Tc* out, int64_t stride, int64_t col)
+{
+    TanPhase<Tc> tp, tm;
+    tp.load(ep, mu[1], lam[1]);
+    tm.load(em, mu[0], lam[0]);
+    Tc Nt[3] = {(Tc)N[0], (Tc)N[1], (Tc)N[2]};
+    Tc Dt[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) Dt[q] = (Tc)Di[q];
+    const Tc cpt = (Tc)cp, cmt = (Tc)cm;
+    // B = dA D (9x3), W = B Delta^{-1}
+    Tc B[27], W[27];
+#pragma unroll
+    for (int r = 0; r < 9; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) B[3 * r + k] = tp.AD(Nt, r / 3, r % 3, k) - tm.AD(Nt, r / 3, r % 3, k);
+#pragma unroll
+    for (int r = 0; r < 9; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            W[3 * r + k] = B[3 * r] * Dt[k] + B[3 * r + 1] * Dt[3 + k] + B[3 * r + 2] * Dt[6 + k];
+#pragma unroll
+    for (int r = 0; r < 9; r++)
+#pragma unroll
+        for (int s2 = r; s2 < 9; s2++) {
+            const Tc avg = cpt * tp.A(r / 3, r % 3, s2 / 3, s2 % 3) + cmt * tm.A(r / 3, r % 3, s2 / 3, s2 % 3);
+            const Tc corr = W[3 * r] * B[3 * s2] + W[3 * r + 1] * B[3 * s2 + 1] + W[3 * r + 2] * B[3 * s2 + 2];
+            out[(int64_t)sym_idx(r, s2) * stride + col] = avg - corr;
+        }
+}
+
 // DFM: the double-float form: the Newton iterations run on the double-float
 // residual down to its rounding level, then the FP64 residual decides
 // convergence (and takes the last step if needed), so the stopping test and
@@ -439,38 +477,12 @@ template <typename Tc, bool DFM> __device__ __forceinline__ void boxel_body(cons
         } else {
             // The boxel tangent only feeds the Krylov iterations: it is formed
             // in their precision Tc from the converged state (FP64, or the
-            // accepted double-float state)
+            // accepted double-float state); A_box is major-symmetric (the
+            // second derivative of the condensed energy): its upper triangle
+            // is stored, column rank[b]
+            const int64_t kb = A.rank ? (int64_t)A.rank[b] : b;
             auto tangent = [&](const auto& ep, const auto& em) {
-                TanPhase<Tc> tp, tm;
-                tp.load(ep, mu[1], lam[1]);
-                tm.load(em, mu[0], lam[0]);
-                Tc Nt[3] = {(Tc)N[0], (Tc)N[1], (Tc)N[2]};
-                Tc Dt[9];
-#pragma unroll
-                for (int q = 0; q < 9; q++) Dt[q] = (Tc)Di[q];
-                const Tc cpt = (Tc)cp, cmt = (Tc)cm;
-                // B = dA D (9x3), W = B Delta^{-1}
-                Tc B[27], W[27];
-#pragma unroll
-                for (int r = 0; r < 9; r++)
-#pragma unroll
-                    for (int k = 0; k < 3; k++) B[3 * r + k] = tp.AD(Nt, r / 3, r % 3, k) - tm.AD(Nt, r / 3, r % 3, k);
-#pragma unroll
-                for (int r = 0; r < 9; r++)
-#pragma unroll
-                    for (int k = 0; k < 3; k++)
-                        W[3 * r + k] = B[3 * r] * Dt[k] + B[3 * r + 1] * Dt[3 + k] + B[3 * r + 2] * Dt[6 + k];
-                // A_box is major-symmetric (the second derivative of the
-                // condensed energy): its upper triangle is stored
-                const int64_t kb = A.rank ? (int64_t)A.rank[b] : b;
-#pragma unroll
-                for (int r = 0; r < 9; r++)
-#pragma unroll
-                    for (int s = r; s < 9; s++) {
-                        const Tc avg = cpt * tp.A(r / 3, r % 3, s / 3, s % 3) + cmt * tm.A(r / 3, r % 3, s / 3, s % 3);
-                        const Tc corr = W[3 * r] * B[3 * s] + W[3 * r + 1] * B[3 * s + 1] + W[3 * r + 2] * B[3 * s + 2];
-                        A.bA[(int64_t)sym_idx(r, s) * A.nb + kb] = avg - corr;
-                    }
+                boxel_tangent_store<Tc>(ep, em, N, cp, cm, mu, lam, Di, A.bA, A.nb, kb);
             };
             if (df_done) {
 #pragma unroll
@@ -824,6 +836,30 @@ template <bool DFM> __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArg
             }
 #pragma unroll
             for (int q = 0; q < 3; q++) A.ba[24 * b + 3 * l + q] = a[q];
+            if (A.bAsub) {
+                // the sub-cell's tangent for the doubly-fine Newton-CG, in
+                // the Krylov precision, from the converged state
+                double Di[9];
+                bool ok;
+                if (df_done && hessian_inv(ed, cp, cm, mu, lam, Di)) {
+                    ok = true;
+                    if (A.sub_f32)
+                        boxel_tangent_store<float>(ed.p, ed.m, N, cp, cm, mu, lam, Di, (float*)A.bAsub, 8 * A.nb, t);
+                    else
+                        boxel_tangent_store<double>(ed.p, ed.m, N, cp, cm, mu, lam, Di, (double*)A.bAsub, 8 * A.nb,
+                                                    t);
+                } else {
+                    ok = (df_done ? eval64(e) : true) && inv64(e, Di);
+                    if (ok) {
+                        if (A.sub_f32)
+                            boxel_tangent_store<float>(e.p, e.m, N, cp, cm, mu, lam, Di, (float*)A.bAsub, 8 * A.nb, t);
+                        else
+                            boxel_tangent_store<double>(e.p, e.m, N, cp, cm, mu, lam, Di, (double*)A.bAsub, 8 * A.nb,
+                                                        t);
+                    }
+                }
+                if (!ok) raise_status(sc, COMBO_E_LAMINATE);
+            }
         }
     }
     if (threadIdx.x == 0) {

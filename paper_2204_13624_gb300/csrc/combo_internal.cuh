@@ -426,8 +426,10 @@ template <typename T, typename Tc> struct XfwdArgs {
     const int32_t* bvox; // [nb] voxel of the k-th boxel in voxel order
     const int32_t* lofs; // [n2 n3 + 1] first boxel (voxel order) of each x-line
     int64_t nb;
-    // plain operand (no constitutive law): X [9][V] real
+    // plain operand (no constitutive law): X [9][V] real, FP64 (X) or in the
+    // Krylov precision (Xc, the doubly-fine tangent's gathered A : p)
     const double* X;
+    const Tc* Xc;
     double* partial;     // [gridDim.x] pAp partials
     Scalars* sc;
     int fuse;            // last block turns the pAp partials into alpha
@@ -627,6 +629,53 @@ struct DfmgArgs {
     int dfloat;          // double-float residual form: the pure-cell laws and the gather in double-float,
                          // S holds (hi, lo) float pairs in place of doubles
 };
+// doubly-fine Newton-CG (single problem): the CG vectors, the tangent
+// operands and results; stage 0 direction update, 1 sub-cell tangents, 2
+// gather and alpha (partials: dfmg_cg_blocks(V) doubles)
+template <typename Tc> struct DfmgTanArgs {
+    const double* F;        // [9][V]
+    const uint8_t* phase;
+    const int32_t* vox2box;
+    const Tc* bAsub;        // [45][8 nb] packed boxel sub-cell tangents
+    int64_t nb;
+    double mu[2], lam[2];
+    const Tc* r;
+    Tc* p;
+    Tc* x;
+    Tc* St;                 // [72][V] sub-cell values of A : p
+    Tc* y;                  // [9][V] gathered A : p
+    double* partial;
+    Scalars* sc;
+    int64_t V;
+    int n1, n2, n3;
+};
+template <typename Tc> void launch_dfmg_cg(const DfmgTanArgs<Tc>& a, int stage, cudaStream_t st);
+int dfmg_cg_blocks(int64_t V);
+
+// a field X [9][V] at the doubly-fine positions of sub-cell l of cell (i, j, k)
+// (one problem), like dfmg_fsub
+template <typename S>
+__device__ __forceinline__ void dfmg_fsub_t(const S* __restrict__ X, int64_t V, int n1, int n2, int n3, int i, int j,
+                                            int k, int l, double f[9])
+{
+    const int ip = (l & 1) ? (i + 1 == n1 ? 0 : i + 1) : i;
+    const int jp = (l & 2) ? (j + 1 == n2 ? 0 : j + 1) : j;
+    const int kp = (l & 4) ? (k + 1 == n3 ? 0 : k + 1) : k;
+    const int64_t vc = i + (int64_t)n1 * (j + (int64_t)n2 * k);
+    const int64_t v12 = ip + (int64_t)n1 * (jp + (int64_t)n2 * k);
+    const int64_t v13 = ip + (int64_t)n1 * (j + (int64_t)n2 * kp);
+    const int64_t v23 = i + (int64_t)n1 * (jp + (int64_t)n2 * kp);
+    f[0] = X[0 * V + vc];
+    f[4] = X[4 * V + vc];
+    f[8] = X[8 * V + vc];
+    f[1] = X[1 * V + v12];
+    f[3] = X[3 * V + v12];
+    f[2] = X[2 * V + v13];
+    f[6] = X[6 * V + v13];
+    f[5] = X[5 * V + v23];
+    f[7] = X[7 * V + v23];
+}
+
 void launch_dfmg_pure(const DfmgArgs& a, cudaStream_t st);
 void launch_dfmg_gather(const DfmgArgs& a, cudaStream_t st);
 // mean over the 8 sub-cells of the jump vectors ba8 [nb][8][3] -> ba [nb][3]
@@ -658,6 +707,10 @@ template <typename Tc> struct BoxelArgs {
     double* S;
     int64_t Vp;
     int n1, n2, n3;
+    // doubly-fine Newton-CG: packed tangent of every boxel sub-cell,
+    // [45][8 nb] (column 8 b + l) in FP32 (sub_f32) or FP64; or null
+    void* bAsub;
+    int sub_f32;
 };
 template <typename Tc> void launch_boxel(const BoxelArgs<Tc>& a, cudaStream_t st);
 // grouped: items of 128 boxels ((nb + 127) / 128 per descriptor); every

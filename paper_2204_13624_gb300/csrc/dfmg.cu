@@ -270,4 +270,164 @@ void launch_dfmg_amean(const double* ba8, double* ba, int64_t nb, cudaStream_t s
     k_dfmg_amean<<<(int)((3 * nb + 255) / 256), 256, 0, st>>>(ba8, ba, nb);
 }
 
+// ---------------------------------------------------------------- Newton-CG
+// The tangent of the doubly-fine law is the Hessian of the sub-cell energy:
+// applied to a direction p it is the gather of A_sub(c, l) : p_sub(c, l),
+// p_sub assembled from p like F_sub from F and A_sub the tangent of the
+// material of c at F_sub(c, l) (symmetric).  One CG iteration runs
+//   k_dfmg_cg_update  x += alpha_prev p, p = r + beta p          (elementwise)
+//   k_dfmg_tangent    S_t(c, l) = A_sub(c, l) : p_sub(c, l)     [72][V]
+//   k_dfmg_tgather    y = gather of S_t, (p, y) -> alpha         [9][V]
+// then the x-pass transform of y and the unchanged y-, z- and x-inverse
+// passes.  A pure sub-cell's tangent is formed from F_sub on the fly in the
+// Krylov precision (G = F_sub^{-1}, m = mu - lam ln J: cheaper than storing
+// it); a composite boxel's sub-cells read the packed tangents the laminate
+// kernel stored at the last residual evaluation.
+
+// Neo-Hookean tangent data of F in precision S: G = F^{-1}, m = mu - lam ln J
+template <typename S> __device__ __forceinline__ void nh_tan_data(const S f[9], S mu, S lam, S G[9], S& m)
+{
+    const S c0 = f[4] * f[8] - f[5] * f[7];
+    const S c1 = f[5] * f[6] - f[3] * f[8];
+    const S c2 = f[3] * f[7] - f[4] * f[6];
+    const S J = f[0] * c0 + f[1] * c1 + f[2] * c2;
+    const S iJ = (S)1 / J;
+    G[0] = c0 * iJ;
+    G[1] = (f[2] * f[7] - f[1] * f[8]) * iJ;
+    G[2] = (f[1] * f[5] - f[2] * f[4]) * iJ;
+    G[3] = c1 * iJ;
+    G[4] = (f[0] * f[8] - f[2] * f[6]) * iJ;
+    G[5] = (f[2] * f[3] - f[0] * f[5]) * iJ;
+    G[6] = c2 * iJ;
+    G[7] = (f[1] * f[6] - f[0] * f[7]) * iJ;
+    G[8] = (f[0] * f[4] - f[1] * f[3]) * iJ;
+    m = mu - lam * log(J);
+}
+
+template <typename Tc> __global__ void __launch_bounds__(256) k_dfmg_cg_update(DfmgTanArgs<Tc> a)
+{
+    Scalars* sc = a.sc;
+    if (sc->cg_done) return;
+    const bool first = sc->cg_iter == 0;
+    const Tc beta = first ? (Tc)0 : (Tc)sc->beta;
+    const Tc apend = first ? (Tc)0 : (Tc)sc->alpha_pending;
+    const int64_t V = a.V;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 9; c++) {
+            const Tc rv = a.r[c * V + v];
+            Tc pn = rv;
+            if (!first) {
+                const Tc po = a.p[c * V + v];
+                if (apend != (Tc)0) a.x[c * V + v] += apend * po;
+                pn = rv + beta * po;
+            }
+            a.p[c * V + v] = pn;
+        }
+    }
+}
+
+template <typename Tc> __global__ void __launch_bounds__(256) k_dfmg_tangent(DfmgTanArgs<Tc> a)
+{
+    if (a.sc->cg_done) return;
+    const int64_t V = a.V;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(v % a.n1), j = (int)((v / a.n1) % a.n2), k = (int)(v / ((int64_t)a.n1 * a.n2));
+        const int ph = a.phase[v];
+        const int64_t b = (ph == 2) ? (int64_t)a.vox2box[v] : -1;
+        const Tc mu = (Tc)a.mu[ph == 1 ? 1 : 0], lam = (Tc)a.lam[ph == 1 ? 1 : 0];
+#pragma unroll 1
+        for (int l = 0; l < 8; l++) {
+            double fd[9];
+            double pd[9];
+            dfmg_fsub(a.F, V, 0, a.n1, a.n2, a.n3, i, j, k, l, fd);
+            dfmg_fsub_t(a.p, V, a.n1, a.n2, a.n3, i, j, k, l, pd);
+            Tc ps[9], y[9];
+#pragma unroll
+            for (int c = 0; c < 9; c++) ps[c] = (Tc)pd[c];
+            if (b < 0) {
+                Tc f[9], G[9], m;
+#pragma unroll
+                for (int c = 0; c < 9; c++) f[c] = (Tc)fd[c];
+                nh_tan_data<Tc>(f, mu, lam, G, m);
+                nh_tangent<Tc>(G, m, mu, lam, ps, y);
+            } else {
+                const int64_t col = 8 * b + l, stride = 8 * a.nb;
+#pragma unroll
+                for (int r = 0; r < 9; r++) {
+                    Tc yr = 0;
+#pragma unroll
+                    for (int c = 0; c < 9; c++) yr += a.bAsub[(int64_t)sym_idx(r, c) * stride + col] * ps[c];
+                    y[r] = yr;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 9; r++) a.St[(int64_t)(9 * l + r) * V + v] = y[r];
+        }
+    }
+}
+
+template <typename Tc> __global__ void __launch_bounds__(256) k_dfmg_tgather(DfmgTanArgs<Tc> a)
+{
+    __shared__ double red[256];
+    __shared__ int flag;
+    Scalars* sc = a.sc;
+    if (sc->cg_done) return;
+    const int64_t V = a.V;
+    double acc = 0.0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(v % a.n1), j = (int)((v / a.n1) % a.n2), k = (int)(v / ((int64_t)a.n1 * a.n2));
+        Tc o[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int l = 0; l < 8; l++) {
+            const int l1 = l & 1, l2 = (l >> 1) & 1, l3 = (l >> 2) & 1;
+            const int im = l1 ? (i == 0 ? a.n1 - 1 : i - 1) : i;
+            const int jm = l2 ? (j == 0 ? a.n2 - 1 : j - 1) : j;
+            const int km = l3 ? (k == 0 ? a.n3 - 1 : k - 1) : k;
+            const int64_t c12 = im + (int64_t)a.n1 * (jm + (int64_t)a.n2 * k);
+            const int64_t c13 = im + (int64_t)a.n1 * (j + (int64_t)a.n2 * km);
+            const int64_t c23 = i + (int64_t)a.n1 * (jm + (int64_t)a.n2 * km);
+            const Tc* S = a.St + (int64_t)(9 * l) * V;
+            o[0] += S[0 * V + v];
+            o[4] += S[4 * V + v];
+            o[8] += S[8 * V + v];
+            o[1] += S[1 * V + c12];
+            o[3] += S[3 * V + c12];
+            o[2] += S[2 * V + c13];
+            o[6] += S[6 * V + c13];
+            o[5] += S[5 * V + c23];
+            o[7] += S[7 * V + c23];
+        }
+        Tc s = 0;
+#pragma unroll
+        for (int c = 0; c < 9; c++) {
+            const Tc yc = (Tc)0.125 * o[c];
+            a.y[c * V + v] = yc;
+            s += a.p[c * V + v] * yc;
+        }
+        acc += (double)s;
+    }
+    const double tot_b = block_sum(acc, red);
+    if (threadIdx.x == 0) a.partial[blockIdx.x] = tot_b;
+    if (last_block(&sc->ticket[0], &flag, gridDim.x)) {
+        const double tot = sum_partials_fixed(a.partial, gridDim.x, red);
+        if (threadIdx.x == 0) cg_alpha(sc, tot);
+    }
+}
+
+int dfmg_cg_blocks(int64_t V) { return dfmg_grid(V); }
+
+template <typename Tc> void launch_dfmg_cg(const DfmgTanArgs<Tc>& a, int stage, cudaStream_t st)
+{
+    const int grid = dfmg_grid(a.V);
+    if (stage == 0)
+        k_dfmg_cg_update<Tc><<<grid, 256, 0, st>>>(a);
+    else if (stage == 1)
+        k_dfmg_tangent<Tc><<<grid, 256, 0, st>>>(a);
+    else
+        k_dfmg_tgather<Tc><<<grid, 256, 0, st>>>(a);
+}
+template void launch_dfmg_cg<float>(const DfmgTanArgs<float>&, int, cudaStream_t);
+template void launch_dfmg_cg<double>(const DfmgTanArgs<double>&, int, cudaStream_t);
+
 }  // namespace combo

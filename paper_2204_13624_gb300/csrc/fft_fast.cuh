@@ -1,9 +1,13 @@
 // fft_fast.cuh -- compile-time power-of-two FFT plans for the hot sizes.
 //
-// A line of N complex values is transformed by TPL = N / max(R) threads with
-// a self-sorting Stockham decomposition whose radices are template
-// constants (N = 64: 8x8, 128: 16x8, 256: 16x16, 512: 8x8x8), so every index
-// is a shift or a mask.  Each stage keeps its R values in registers and runs
+// A line of N complex values is transformed by TPL threads with a
+// self-sorting Stockham decomposition whose radices are template constants:
+// powers of two (N = 64: 8x8, 128: 16x8, 256: 16x16, 512: 8x8x8), where every
+// index is a shift or a mask, and 2^a 3^b lengths of the grids between them
+// (48: 12x4, 72: 12x6, 96: 4x4x6, 108: 6x6x3, 144: 12x12, 192: 4x4x12,
+// 216: 6x6x6, and the half lengths 24 .. 108 of the x transforms), whose
+// register DFTs of sizes 3, 6, 12 split by radices 2 and 3 with the
+// constants cos(2 pi m / 144).  Each stage keeps its R values in registers and runs
 // a register DFT of size R; consecutive stages exchange through shared
 // memory.  The first stage may read global memory directly and the last one
 // may write it directly.  The last forward stage leaves thread tau holding
@@ -34,9 +38,115 @@ __host__ __device__ __forceinline__ constexpr double kcos32(int m)
 }
 __host__ __device__ __forceinline__ constexpr double ksin32(int m) { return kcos32(m - 8); }
 
-// DFT of size R in registers, natural order in and out (radix-2 decimation in time).
+// cos(2 pi m / 144) for integer m (mathematical constants): the twiddles of
+// register DFTs whose size divides 144
+__host__ __device__ __forceinline__ constexpr double kcos144(int m)
+{
+    m %= 144;
+    if (m < 0) m += 144;
+    constexpr double C[37] = {
+                             1.000000000000000000000,
+                             0.9990482215818577624037,
+                             0.9961946980917455322950,
+                             0.9914448613738104111446,
+                             0.9848077530122080593667,
+                             0.9762960071199333659709,
+                             0.9659258262890682867497,
+                             0.9537169507482269211438,
+                             0.9396926207859083840541,
+                             0.9238795325112867561282,
+                             0.9063077870366499632426,
+                             0.8870108331782217010546,
+                             0.8660254037844386467637,
+                             0.8433914458128857012729,
+                             0.8191520442889917896845,
+                             0.7933533402912351645798,
+                             0.7660444431189780352024,
+                             0.7372773368101240413843,
+                             0.7071067811865475244008,
+                             0.6755902076156602443483,
+                             0.6427876096865393263226,
+                             0.6087614290087206394161,
+                             0.5735764363510460961080,
+                             0.5372996083468238318408,
+                             0.5000000000000000000000,
+                             0.4617486132350339305629,
+                             0.4226182617406994361870,
+                             0.3826834323650897717285,
+                             0.3420201433256687330441,
+                             0.3007057995042731216225,
+                             0.2588190451025207623489,
+                             0.2164396139381028797596,
+                             0.1736481776669303488517,
+                             0.1305261922200515915484,
+                             0.08715574274765817355806,
+                             0.04361938736533599978175,
+                             0.0};
+    return m <= 36 ? C[m] : (m <= 72 ? -C[72 - m] : (m <= 108 ? -C[m - 72] : C[144 - m]));
+}
+__host__ __device__ __forceinline__ constexpr double ksin144(int m) { return kcos144(m - 36); }
+
+__host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// v * exp(-/+ 2 pi i m / 144) (forward / inverse)
+template <bool INV, typename V> __device__ __forceinline__ V tw144(V o, int m)
+{
+    typedef decltype(o.x) S;
+    const S cr = (S)kcos144(m), si = (S)ksin144(m);
+    return INV ? V{o.x * cr - o.y * si, o.x * si + o.y * cr} : V{o.x * cr + o.y * si, o.y * cr - o.x * si};
+}
+
+// DFT of size R in registers, natural order in and out: decimation in time by
+// radix 2 (powers of two: constants cos(2 pi m / 32); even sizes with a factor
+// 3: cos(2 pi m / 144)) or by radix 3 (odd sizes).
 template <int R, bool INV> struct RegDFT {
     template <typename V> static __device__ __forceinline__ void run(V* v)
+    {
+        if constexpr (is_pow2(R)) {
+            run_pow2(v);
+        } else if constexpr (R == 3) {
+            dft3<INV>(v);
+        } else if constexpr (R % 2 == 0) {
+            static_assert(144 % R == 0, "register DFT size must divide 144");
+            V e[R / 2], o[R / 2];
+#pragma unroll
+            for (int k = 0; k < R / 2; k++) {
+                e[k] = v[2 * k];
+                o[k] = v[2 * k + 1];
+            }
+            RegDFT<R / 2, INV>::run(e);
+            RegDFT<R / 2, INV>::run(o);
+#pragma unroll
+            for (int k = 0; k < R / 2; k++) {
+                const V t = (k == 0) ? o[0] : (4 * k == R ? c_rot<INV>(o[k]) : tw144<INV>(o[k], k * (144 / R)));
+                v[k] = c_add(e[k], t);
+                v[k + R / 2] = c_sub(e[k], t);
+            }
+        } else {
+            static_assert(R % 3 == 0 && 144 % R == 0, "odd register DFT sizes: 3, 9");
+            constexpr int Q = R / 3;
+            V x0[Q], x1[Q], x2[Q];
+#pragma unroll
+            for (int k = 0; k < Q; k++) {
+                x0[k] = v[3 * k];
+                x1[k] = v[3 * k + 1];
+                x2[k] = v[3 * k + 2];
+            }
+            RegDFT<Q, INV>::run(x0);
+            RegDFT<Q, INV>::run(x1);
+            RegDFT<Q, INV>::run(x2);
+#pragma unroll
+            for (int k = 0; k < Q; k++) {
+                V y[3] = {x0[k], k == 0 ? x1[0] : tw144<INV>(x1[k], k * (144 / R)),
+                          k == 0 ? x2[0] : tw144<INV>(x2[k], 2 * k * (144 / R))};
+                dft3<INV>(y);
+                v[k] = y[0];
+                v[k + Q] = y[1];
+                v[k + 2 * Q] = y[2];
+            }
+        }
+    }
+    template <typename V> static __device__ __forceinline__ void run_pow2(V* v)
     {
         typedef decltype(v[0].x) S;
         V e[R / 2], o[R / 2];
@@ -67,6 +177,7 @@ template <int R, bool INV> struct RegDFT {
 };
 template <bool INV> struct RegDFT<1, INV> {
     template <typename V> static __device__ __forceinline__ void run(V*) {}
+    template <typename V> static __device__ __forceinline__ void run_pow2(V*) {}
 };
 
 template <int N> struct FastPlan;
@@ -83,11 +194,52 @@ template <> struct FastPlan<256> {
     static constexpr int NST = 2, R0 = 16, R1 = 16, R2 = 1, TPL = 16;
 };
 template <> struct FastPlan<512> {
-    static constexpr int NST = 3, R0 = 8, R1 = 8, R2 = 8, TPL = 64;
+    static constexpr int NST = 3, R0 = 8, R1 = 8, R2 = 8, TPL = 32;  // two butterflies per thread and stage
+};
+// 2^a 3^b lengths: every stage's butterfly count N / R is a multiple of TPL
+template <> struct FastPlan<24> {
+    static constexpr int NST = 2, R0 = 6, R1 = 4, R2 = 1, TPL = 2;
+};
+template <> struct FastPlan<36> {
+    static constexpr int NST = 2, R0 = 6, R1 = 6, R2 = 1, TPL = 6;
+};
+template <> struct FastPlan<48> {
+    static constexpr int NST = 2, R0 = 12, R1 = 4, R2 = 1, TPL = 4;
+};
+template <> struct FastPlan<54> {
+    static constexpr int NST = 3, R0 = 3, R1 = 3, R2 = 6, TPL = 9;
+};
+template <> struct FastPlan<72> {
+    static constexpr int NST = 2, R0 = 12, R1 = 6, R2 = 1, TPL = 6;
+};
+template <> struct FastPlan<96> {
+    static constexpr int NST = 3, R0 = 4, R1 = 4, R2 = 6, TPL = 8;
+};
+template <> struct FastPlan<108> {
+    static constexpr int NST = 3, R0 = 6, R1 = 6, R2 = 3, TPL = 18;
+};
+template <> struct FastPlan<144> {
+    static constexpr int NST = 2, R0 = 12, R1 = 12, R2 = 1, TPL = 12;
+};
+template <> struct FastPlan<192> {
+    static constexpr int NST = 3, R0 = 4, R1 = 4, R2 = 12, TPL = 16;
+};
+template <> struct FastPlan<216> {
+    static constexpr int NST = 3, R0 = 6, R1 = 6, R2 = 6, TPL = 36;
 };
 
 __host__ __device__ constexpr bool fast_size(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
 __host__ __device__ constexpr bool fast_size_x(int m) { return m == 32 || m == 64 || m == 128 || m == 256; }
+// 2^a 3^b lengths with compile-time plans on the FP32 Krylov passes (the
+// TMA-tiled y- and z-passes, the x-forward tangent pass and the x-inverse)
+__host__ __device__ constexpr bool fast3_size(int n)
+{
+    return n == 48 || n == 72 || n == 96 || n == 108 || n == 144 || n == 192 || n == 216;
+}
+__host__ __device__ constexpr bool fast3_size_x(int m)
+{
+    return m == 24 || m == 36 || m == 48 || m == 54 || m == 72 || m == 96 || m == 108;
+}
 
 // Radix of stage s of the forward (INV = false) or inverse (reversed) plan.
 template <int N, bool INV, int S> struct StageR {
@@ -104,6 +256,7 @@ __device__ __forceinline__ void stage_load(cx<T> (&v)[(N / R) / TPL][R], const L
 {
     constexpr int B = N / R;
     constexpr int U = B / TPL;
+    static_assert(B % TPL == 0, "every stage gives each thread whole butterflies");
 #pragma unroll
     for (int u = 0; u < U; u++) {
         const int j = tau + TPL * u;
@@ -114,7 +267,7 @@ __device__ __forceinline__ void stage_load(cx<T> (&v)[(N / R) / TPL][R], const L
     for (int u = 0; u < U; u++) {
         const int j = tau + TPL * u;
         if (NS > 1) {
-            const int k = j & (NS - 1);
+            const int k = (int)((unsigned)j % (unsigned)NS);
 #pragma unroll
             for (int t = 1; t < R; t++) {
                 cx<T> w = tw[t * k * (N / (NS * R))];
@@ -135,7 +288,7 @@ __device__ __forceinline__ void stage_store(cx<T> (&v)[(N / R) / TPL][R], const 
 #pragma unroll
     for (int u = 0; u < U; u++) {
         const int j = tau + TPL * u;
-        const int d = (j / NS) * NS * R + (j & (NS - 1));
+        const int d = (int)((unsigned)j / (unsigned)NS) * NS * R + (int)((unsigned)j % (unsigned)NS);
 #pragma unroll
         for (int t = 0; t < R; t++) st(d + t * NS, v[u][t]);
     }

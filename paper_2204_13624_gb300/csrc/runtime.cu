@@ -316,12 +316,13 @@ enum KClass {
     K_UPDATE,
     K_DFMG_PURE,
     K_DFMG_GATHER,
+    K_DFMG_CG,
     K_NCLASS
 };
 static const char* kclass_name[K_NCLASS] = {"boxel_laminate", "xfwd_resid_fp64", "yfwd_fp64", "zgamma_fp64",
                                              "yinv_fp64", "xinv_fp64", "xfwd_tangent", "yfwd_krylov",
                                              "zgamma_krylov", "yinv_krylov", "xinv_cg", "finalize", "update_F",
-                                             "dfmg_pure", "dfmg_gather"};
+                                             "dfmg_pure", "dfmg_gather", "dfmg_cg_tangent"};
 
 struct Profiler {
     bool on = false;
@@ -984,8 +985,6 @@ static int check_options(combo_options& o)
         return fail(COMBO_E_INVALID_ARG, "bad theory");
     if (o.kspace == COMBO_STAGGERED_DFMG && o.theory == COMBO_INFINITESIMAL_STRAIN)
         return fail(COMBO_E_INVALID_ARG, "the doubly-fine material grid is built for finite strain only");
-    if (o.kspace == COMBO_STAGGERED_DFMG && o.solver == COMBO_NEWTON_CG)
-        return fail(COMBO_E_INVALID_ARG, "the doubly-fine material grid runs with the fixed point or nonlinear CG");
     if (o.max_iter <= 0) o.max_iter = (o.solver == COMBO_NEWTON_CG) ? 200 : 100000;
     if (!(o.tol >= 0.0) || !(o.cg_tol >= 0.0)) return fail(COMBO_E_INVALID_ARG, "negative tolerance");
     if (o.nr_max_iter <= 0) o.nr_max_iter = 50;
@@ -1093,6 +1092,9 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     double* d_S = nullptr;             // doubly-fine material grid: [72][V] sub-cell stresses
     double* d_Pd = nullptr;            //   [9][V] gathered stress
     double* d_ba8 = nullptr;           //   [nb][8][3] sub-cell jump vectors
+    Tc* d_bA8 = nullptr;               //   Newton-CG: [45][8 nb] packed sub-cell boxel tangents
+    Tc* d_St = nullptr;                //   Newton-CG: [72][V] sub-cell values of A : p
+    Tc* d_yd = nullptr;                //   Newton-CG: [9][V] gathered A : p
     double* d_mat = nullptr;           // [B][4] materials (batch only)
     double* d_dF = nullptr;            // [B][9] load-step increments (batch only)
     double* d_dv = nullptr;            // [B] F-update factors (batch only)
@@ -1148,6 +1150,9 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         cudaFree(d_S);
         cudaFree(d_Pd);
         cudaFree(d_ba8);
+        cudaFree(d_bA8);
+        cudaFree(d_St);
+        cudaFree(d_yd);
         cudaFree(d_mat);
         cudaFree(d_dF);
         cudaFree(d_dv);
@@ -1213,7 +1218,8 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         CK(dev_malloc(&d_F, 8 * 9 * V));
         CK(dev_malloc(&d_spec, sizeof(double2) * 9 * g.Vs));
         CK(cudaMemsetAsync(d_spec, 0, sizeof(double2) * 9 * g.Vs, st));
-        const int nbuf = std::max(std::max(e64.xpartials(), e64.zblocks()), std::max(ec.xpartials(), ec.zblocks()));
+        int nbuf = std::max(std::max(e64.xpartials(), e64.zblocks()), std::max(ec.xpartials(), ec.zblocks()));
+        if (dfmg()) nbuf = std::max(nbuf, dfmg_cg_blocks(V));
         CK(dev_malloc(&d_part, 8 * (size_t)nbuf));
         if (ext_sc)
             d_sc = ext_sc;
@@ -1223,6 +1229,11 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         if (opt.solver == COMBO_NONLINEAR_CG) {
             CK(dev_malloc(&d_dir, sizeof(double) * 9 * (size_t)g.V));
             CK(cudaMemsetAsync(d_dir, 0, sizeof(double) * 9 * (size_t)g.V, st));
+        }
+        if (dfmg() && newton()) {
+            CK(dev_malloc(&d_bA8, sizeof(Tc) * 45 * 8 * (size_t)std::max<int64_t>(nb, 1)));
+            CK(dev_malloc(&d_St, sizeof(Tc) * 72 * (size_t)g.V));
+            CK(dev_malloc(&d_yd, sizeof(Tc) * 9 * (size_t)g.V));
         }
         if (dfmg()) {
             CK(dev_malloc(&d_S, sizeof(double) * 72 * (size_t)g.V));
@@ -1477,7 +1488,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
 
     // doubly-fine material grid law (App. A): sub-cell stresses of the pure
     // cells and of the composite boxels into d_S, gathered into d_Pd
-    void dfmg_law(int guard)
+    void dfmg_law(int guard, bool tangent = false)
     {
         DfmgArgs d{};
         d.F = d_F;
@@ -1523,6 +1534,8 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             a.n1 = d.n1;
             a.n2 = d.n2;
             a.n3 = d.n3;
+            a.bAsub = tangent ? (void*)d_bA8 : nullptr;
+            a.sub_f32 = sizeof(Tc) == 4 ? 1 : 0;
             prof.begin(K_BOXEL);
             launch_boxel_dfmg(a, st);
             prof.end();
@@ -1640,7 +1653,56 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     // one CG iteration in precision Tc, guarded by cg_done
     void cg_iteration()
     {
+        if (dfmg()) {
+            dfmg_cg_iteration();
+            return;
+        }
         const auto xf = cg_xf();
+        prof.begin(K_XFWD_TANGENT);
+        launch_xfwd<Tc, Tc>(xf, 1, st);
+        prof.end();
+        ec.yz(d_sc, 1, false, nullptr, st, &prof, K_YFWD_C);
+        const auto xi = cg_xi();
+        prof.begin(K_XINV_CG);
+        launch_xinv<Tc, Tc>(xi, 1, st);
+        prof.end();
+    }
+
+    // doubly-fine material grid: the direction update, the sub-cell tangents
+    // applied to p and their gather with (p, A : p) -> alpha, then the
+    // transforms of A : p and the CG x-inverse
+    void dfmg_cg_iteration()
+    {
+        DfmgTanArgs<Tc> d{};
+        d.F = d_F;
+        d.phase = d_phase;
+        d.vox2box = d_v2b;
+        d.bAsub = d_bA8;
+        d.nb = std::max<int64_t>(nb, 1);
+        for (int i = 0; i < 2; i++) {
+            d.mu[i] = hp.mu[i];
+            d.lam[i] = hp.lam[i];
+        }
+        d.r = d_r;
+        d.p = d_p;
+        d.x = d_x;
+        d.St = d_St;
+        d.y = d_yd;
+        d.partial = d_part;
+        d.sc = d_sc;
+        d.V = g.V;
+        d.n1 = g.n1;
+        d.n2 = g.n2;
+        d.n3 = g.n3;
+        for (int stage = 0; stage < 3; stage++) {
+            prof.begin(K_DFMG_CG);
+            launch_dfmg_cg<Tc>(d, stage, st);
+            prof.end();
+        }
+        auto xf = ec.template xf<Tc>();
+        xf.mode = XF_RESID;
+        xf.Xc = d_yd;
+        xf.sc = d_sc;
         prof.begin(K_XFWD_TANGENT);
         launch_xfwd<Tc, Tc>(xf, 1, st);
         prof.end();
@@ -1806,7 +1868,10 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                     break;
                 }
                 case ST_RESID: {
-                    boxels(true, 0);
+                    if (dfmg())
+                        dfmg_law(0, true);
+                    else
+                        boxels(true, 0);
                     resid_operator(XI_RHS, 0);
                     CK(cudaGetLastError());
                     if ((rc = read_scalars(s))) return error = rc;
@@ -3095,6 +3160,8 @@ extern "C" int combo_solve_batch(combo_ctx* ctx, int32_t n_problems, const combo
     if (rc) return rc;
     if (n_problems > 1 && o.solver != COMBO_NEWTON_CG)
         return fail(COMBO_E_INVALID_ARG, "a batch runs the Newton-CG solver");
+    if (n_problems > 1 && o.kspace == COMBO_STAGGERED_DFMG)
+        return fail(COMBO_E_INVALID_ARG, "the doubly-fine material grid runs as single solves");
     CK(cudaSetDevice(ctx->device));
     std::vector<HostProblem> hs(n_problems);
     bool same = true;
@@ -3547,7 +3614,8 @@ static ServeReq* pick_request(combo_server* S)
 static bool batchable(const combo_server* S, const ServeReq* r)
 {
     const int64_t V = (int64_t)r->hp.n[0] * r->hp.n[1] * r->hp.n[2];
-    return S->batch_max >= 2 && r->opt.solver == COMBO_NEWTON_CG && !r->cancel && V <= S->batch_max_voxels;
+    return S->batch_max >= 2 && r->opt.solver == COMBO_NEWTON_CG && r->opt.kspace != COMBO_STAGGERED_DFMG &&
+           !r->cancel && V <= S->batch_max_voxels;
 }
 
 // a request that may share a batch with `first`: same grid, cell size and options

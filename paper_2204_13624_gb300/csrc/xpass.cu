@@ -216,6 +216,9 @@ __device__ __forceinline__ void xfwd_body(const XfwdArgs<T, Tc>& a, int guard, i
               if (a.X) {
 #pragma unroll
                 for (int c = 0; c < 9; c++) o[c] = (T)a.X[c * V + v];
+              } else if (a.Xc) {
+#pragma unroll
+                for (int c = 0; c < 9; c++) o[c] = (T)a.Xc[c * V + v];
               } else {  // XF_RESID
                 const int ph = phase[v];
                 double F[9];
@@ -611,6 +614,19 @@ template <typename T, typename Tc, int MF> static void xfwd_launch(const XfwdArg
 
 template <typename T, typename Tc> void launch_xfwd(const XfwdArgs<T, Tc>& a, int guard, cudaStream_t st)
 {
+    if constexpr (std::is_same<T, float>::value && std::is_same<Tc, float>::value) {
+        // 2^a 3^b half lengths: compile-time plans in the FP32 passes
+        switch (a.g.M) {
+            case 24: xfwd_launch<T, Tc, 24>(a, guard, st); return;
+            case 36: xfwd_launch<T, Tc, 36>(a, guard, st); return;
+            case 48: xfwd_launch<T, Tc, 48>(a, guard, st); return;
+            case 54: xfwd_launch<T, Tc, 54>(a, guard, st); return;
+            case 72: xfwd_launch<T, Tc, 72>(a, guard, st); return;
+            case 96: xfwd_launch<T, Tc, 96>(a, guard, st); return;
+            case 108: xfwd_launch<T, Tc, 108>(a, guard, st); return;
+            default: break;
+        }
+    }
     switch (a.g.M) {
         case 32: xfwd_launch<T, Tc, 32>(a, guard, st); break;
         case 64: xfwd_launch<T, Tc, 64>(a, guard, st); break;
@@ -635,6 +651,18 @@ template <typename T, typename Tc> void launch_xinv(const XinvArgs<T, Tc>& a, in
         if (a.mode == XI_CG && guard == 1 && stream_xpass_ok(a.g)) {
             launch_xinv_stream(a, st);
             return;
+        }
+    }
+    if constexpr (std::is_same<T, float>::value && std::is_same<Tc, float>::value) {
+        switch (a.g.M) {
+            case 24: xinv_launch<T, Tc, 24>(a, guard, st); return;
+            case 36: xinv_launch<T, Tc, 36>(a, guard, st); return;
+            case 48: xinv_launch<T, Tc, 48>(a, guard, st); return;
+            case 54: xinv_launch<T, Tc, 54>(a, guard, st); return;
+            case 72: xinv_launch<T, Tc, 72>(a, guard, st); return;
+            case 96: xinv_launch<T, Tc, 96>(a, guard, st); return;
+            case 108: xinv_launch<T, Tc, 108>(a, guard, st); return;
+            default: break;
         }
     }
     switch (a.g.M) {

@@ -33,9 +33,9 @@ namespace {
 // autotuner picks one per grid; candidate 0 is the default)
 template <int N, int C> __host__ __device__ constexpr int tma_tx()
 {
-    return (N == 512 ? 4 : (N == 256 ? 8 : 16)) >> C;
+    return (N > 128 ? 8 : 16) >> C;
 }
-__host__ __device__ constexpr int tma_tx_rt(int n, int c) { return (n == 512 ? 4 : (n == 256 ? 8 : 16)) >> c; }
+__host__ __device__ constexpr int tma_tx_rt(int n, int c) { return (n > 128 ? 8 : 16) >> c; }
 // x-frequency widths of a y-pass tile
 template <int C> __host__ __device__ constexpr int tma_tyx() { return 16 >> C; }
 
@@ -56,7 +56,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 }  // namespace
 
-bool zpass_tma_size(int n3) { return n3 == 64 || n3 == 128 || n3 == 256 || n3 == 512; }
+bool zpass_tma_size(int n3) { return n3 == 64 || n3 == 128 || n3 == 256 || n3 == 512 || fast3_size(n3); }
 
 // Encode a tiled map of the complex FP32 spectrum [9][n3][n2][nhp]; an axis
 // of 512 (the tile's long axis: z for the z-pass, y for the y-pass) is split
@@ -390,8 +390,15 @@ template <int N, bool INV> static void ypass_tma_pick(const YArgs<float>& a, con
 template <bool INV> void launch_ypass_tma(const YArgs<float>& a, const void* map, cudaStream_t st)
 {
     switch (a.g.n2) {
+        case 48: ypass_tma_pick<48, INV>(a, map, st); break;
         case 64: ypass_tma_pick<64, INV>(a, map, st); break;
+        case 72: ypass_tma_pick<72, INV>(a, map, st); break;
+        case 96: ypass_tma_pick<96, INV>(a, map, st); break;
+        case 108: ypass_tma_pick<108, INV>(a, map, st); break;
         case 128: ypass_tma_pick<128, INV>(a, map, st); break;
+        case 144: ypass_tma_pick<144, INV>(a, map, st); break;
+        case 192: ypass_tma_pick<192, INV>(a, map, st); break;
+        case 216: ypass_tma_pick<216, INV>(a, map, st); break;
         case 256: ypass_tma_pick<256, INV>(a, map, st); break;
         default: ypass_tma_pick<512, INV>(a, map, st); break;
     }
@@ -433,8 +440,15 @@ template <int N> static void zpass_tma_pick(const ZArgs<float>& a, const void* m
 void launch_zpass_tma(const ZArgs<float>& a, const void* map, cudaStream_t st)
 {
     switch (a.g.n3p) {
+        case 48: zpass_tma_pick<48>(a, map, st); break;
         case 64: zpass_tma_pick<64>(a, map, st); break;
+        case 72: zpass_tma_pick<72>(a, map, st); break;
+        case 96: zpass_tma_pick<96>(a, map, st); break;
+        case 108: zpass_tma_pick<108>(a, map, st); break;
         case 128: zpass_tma_pick<128>(a, map, st); break;
+        case 144: zpass_tma_pick<144>(a, map, st); break;
+        case 192: zpass_tma_pick<192>(a, map, st); break;
+        case 216: zpass_tma_pick<216>(a, map, st); break;
         case 256: zpass_tma_pick<256>(a, map, st); break;
         default: zpass_tma_pick<512>(a, map, st); break;
     }

@@ -172,6 +172,22 @@ def test_newton_cg_parity_fast_sizes(cb, orc, prec):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
+def test_newton_cg_parity_mixed_radix_plans(cb, orc, prec):
+    """Every 2^a 3^b side with a compile-time plan in the FP32 passes (48, 72,
+    96, 108, 144, 192, 216 along y and z through the TMA-tiled passes; half
+    lengths 24 .. 108 in the x-passes), against the oracle after equal
+    iterations."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    for n in [(48, 72, 96), (72, 108, 48), (96, 48, 144), (108, 16, 192), (144, 216, 8), (192, 8, 216),
+              (216, 144, 8)]:
+        p = ms.random_spheres(n, 3.0, 0.1, 19, 10.0, np.diag([1.03, 1.0, 1.0]) + 0.01, 1)
+        g, r = solve_both(cb, orc, p, solver=1, precision=prec, fixed_iterations=1, cg_fixed_iterations=10)
+        assert rel(g["F"], r["F"]) < 2e-5, n
+        assert rel(g["Pbar"], r["Pbar"]) < 2e-5, n
+
+
+@pytest.mark.parametrize("prec", [1, 2])
 def test_newton_cg_parity_tma_512(cb, orc, prec):
     """Sides of 512 along y and z: the TMA-tiled FP32 y- and z-passes through
     5-D tensor maps (the 512-long axis as 256 x 2), rotated and staggered
