@@ -85,10 +85,12 @@ extern "C" {
    each with its own jump vector), and the stress gathers
    P_aa[xi] = 1/8 sum_l S(xi, l)_aa, P_ab[xi] = 1/8 sum_l S(xi - l_a e_a - l_b e_b, l)_ab,
    the gradient of the sub-cell energy 1/8 sum_c sum_l W_c(F_sub(c, l)).  The
-   operator is that of COMBO_STAGGERED.  Fixed point and nonlinear CG only
-   (COMBO_E_INVALID_ARG with Newton-CG); combo_solve and combo_solve_begin
-   only (not the batch, not combo_apply_G).  combo_result.a_out holds the mean
-   of a boxel's 8 sub-cell jumps; Pbar_phase averages over sub-cells. */
+   operator is that of COMBO_STAGGERED.  All three solvers; Newton-CG applies
+   the Hessian of the sub-cell energy (the sub-cell tangents applied to the
+   direction assembled like F_sub and gathered like P).  combo_solve and
+   combo_solve_begin only (not the batch, not combo_apply_G).
+   combo_result.a_out holds the mean of a boxel's 8 sub-cell jumps;
+   Pbar_phase averages over sub-cells. */
 #define COMBO_STAGGERED_DFMG 3
 /* solver */
 #define COMBO_FIXED_POINT 0 /* basic scheme on the nonlinear LSE, Sec. 3 */
@@ -268,11 +270,13 @@ int combo_solve(combo_ctx* ctx, const combo_problem* p, const combo_options* o, 
  * (Sec. 3).  Problems of equal grid and cell size are stacked along z into
  * one grid (a class), so every kernel launch works on the pencils of all of
  * them (the x-passes give each problem its own blocks and reductions, the
- * z-passes transform each problem's segment).  With several classes, every
- * pass of an operator application -- laminate solves, x-forward, y, z with
- * the Green operator, y inverse, x-inverse -- is one persistent launch over
- * a device table of (class, block) work items of all classes, and the CG
- * loop replays from a captured CUDA graph.  CG scalars, stopping tests, step
+ * z-passes transform each problem's segment).  With several classes, a class
+ * of at least 2^20 stacked voxels runs its own tuned launch sequences on a
+ * stream of its own, and for all smaller classes every pass of an operator
+ * application -- laminate solves, x-forward, y, z with the Green operator, y
+ * inverse, x-inverse -- is one persistent launch over a device table of
+ * (class, block) work items on another stream, beside them; each CG chunk
+ * replays from one captured CUDA graph with these streams as branches.  CG scalars, stopping tests, step
  * halving and results are per problem, and a problem that has converged is
  * masked out of the launches until the others finish the load step.
  *   problems[n_problems], results[n_problems]: as for combo_solve (each

@@ -2406,8 +2406,9 @@ template <typename A> struct GroupBuf {
 // A batch of Newton-CG problems on different grids.  The problems of each
 // distinct grid (sides and cell size) form one stacked solve (a class); the
 // classes advance in lockstep rounds like the stacked batch.  A class whose
-// stacked grid fills the GPU on its own (kOwnVoxels) runs its own tuned
-// launch sequences on a stream of its own; for all other classes every pass
+// stacked grid has at least kOwnVoxels voxels (enough work to keep its own
+// tuned, specialised launches busy) runs them on a stream of its own; for all
+// smaller classes every pass
 // of every operator application -- laminate solves, x-forward, y, z + Green
 // operator, y inverse, x-inverse -- is ONE grouped launch over the work items
 // of all of them (grouped x-, y-, z-pass and boxel kernels) on another
@@ -2443,7 +2444,7 @@ template <typename Tc, typename Rt> struct MixSolve : SolveBase {
     volatile int cancel_requested = 0;
     int error = 0;
     static constexpr int kCgChunk = 8;
-    static constexpr int64_t kOwnVoxels = int64_t(6) << 20;  // stacked voxels of a class that fills the GPU
+    static constexpr int64_t kOwnVoxels = int64_t(1) << 20;  // stacked voxels of a class that runs its own launches
     std::vector<char> own;             // class runs its own launch sequences
     cudaStream_t st_group = nullptr;   // the grouped launches
     std::vector<cudaStream_t> sides;   // st_group and the streams of the own-launch classes

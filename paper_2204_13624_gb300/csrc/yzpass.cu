@@ -308,7 +308,7 @@ template <typename T> int ytx_fast(int n) { return sizeof(T) == 4 ? 16 : 8; }
 // at N >= 256)
 template <typename T> constexpr int ztx_const(int n)
 {
-    return sizeof(T) == 4 ? (n == 512 ? 4 : (n == 256 ? 8 : 16)) : (n == 512 ? 2 : (n == 256 ? 4 : 8));
+    return sizeof(T) == 4 ? (n == 512 ? 4 : (n == 256 ? 8 : 16)) : (n == 512 ? 4 : (n == 256 ? 4 : 8));
 }
 template <typename T> int ztx_fast(int n) { return ztx_const<T>(n); }
 

@@ -105,11 +105,42 @@ def test_refined_fp32_form_rejected_without_newton(cb):
         cb.solve(ms.homogeneous((8, 8, 8)), solver=2, precision=1)
 
 
-def test_newton_rejected(cb):
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_newton_cg_iteration_parity(cb, orc, k):
+    """Newton-CG on the doubly-fine grid (the Hessian of the sub-cell energy
+    in CG) in FP64 against the oracle's Newton-CG, equal iterations."""
+    p = problems()[k]
+    g, r = solve_both(cb, orc, p, solver=1, kspace=DFMG, fixed_iterations=2, cg_fixed_iterations=8)
+    assert rel(g["F"], r["F"]) < 1e-10
+    assert rel(g["P"], r["P"]) < 1e-10
+    assert rel(g["Pbar"], r["Pbar"]) < 1e-9
+    assert g["n_operator"] == r["n_operator"]
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_newton_cg_converged(cb, orc, prec):
+    """Converged Newton-CG on the doubly-fine grid in every precision form
+    against the oracle's converged Newton-CG (FP64 Pbar <= 1e-8; refined
+    forms Pbar <= 1e-5, F <= 1e-4), and against the GPU's nonlinear CG."""
+    from paper_2204_13624_gb300 import microstructure as ms
+
+    p = ms.random_spheres((24, 24, 24), 4.0, 0.15, 31, 10.0, np.diag([1.04, 1.0, 1.0]), 2)
+    r = orc.solve(p, dict(solver=1, kspace=DFMG, tol=1e-10, cg_tol=1e-4))
+    tol = 1e-10 if prec == 0 else 1e-8  # FP64: the oracle's tolerance
+    g = cb.solve(p, solver=1, kspace=DFMG, precision=prec, tol=tol, cg_tol=1e-4 if prec == 0 else 1e-3)
+    assert g["steps_done"] == 2 and np.all(g["resid"] <= tol)
+    assert rel(g["Pbar"], r["Pbar"]) < (1e-9 if prec == 0 else 1e-5)
+    assert rel(g["F"], r["F"]) < (1e-8 if prec == 0 else 1e-4)
+    n = cb.solve(p, solver=2, kspace=DFMG, tol=1e-8)
+    assert rel(g["Pbar"], n["Pbar"]) < 1e-5
+    assert g["n_operator"] > 0 and g["n_operator_fp64"] < n["n_operator_fp64"]
+
+
+def test_newton_cg_batch_rejected(cb):
     from paper_2204_13624_gb300 import microstructure as ms
 
     with pytest.raises(Exception):
-        cb.solve(ms.homogeneous((8, 8, 8)), solver=1, kspace=DFMG)
+        cb.solve_batch([ms.homogeneous((8, 8, 8))] * 2, solver=1, kspace=DFMG)
 
 
 def test_double_float_log_accuracy(cb):
