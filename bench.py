@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--profile-json", default=None, help="write the per-kernel table here")
     ap.add_argument("--batch-only", action="store_true", help="only the 64-solve batch section")
     ap.add_argument("--fibres-only", action="store_true", help="only the 512^3 fibre section")
+    ap.add_argument("--variants-only", action="store_true", help="only the solver / discretisation variants")
     ap.add_argument("--dfmg-only", type=int, default=0, metavar="N",
                     help="only the doubly-fine material grid kernel timings on an N^3 random-ball problem")
     return ap.parse_args()
@@ -290,6 +291,9 @@ def main():
     if args.fibres_only:
         peak, peak_kind = peaks()
         print(json.dumps({"fibres_512": fibres_bench(combo, ctx, stream, peak, peak_kind)}))
+        return
+    if args.variants_only:
+        print(json.dumps({"variants": variants_bench(combo, ctx)}))
         return
     if args.batch_only:
         print(json.dumps({"batch": batch_bench(combo, ctx)}))
@@ -752,6 +756,10 @@ def variants_bench(combo, ctx):
             ("nonlinear_cg_rotated_df", dict(solver=combo.NONLINEAR_CG, precision=combo.FP32_REFINED_DF)),
             ("nonlinear_cg_staggered_dfmg_df", dict(solver=combo.NONLINEAR_CG, precision=combo.FP32_REFINED_DF,
                                                     kspace=combo.STAGGERED_DFMG)),
+            ("newton_cg_staggered_dfmg_refined_df", dict(solver=combo.NEWTON_CG, precision=combo.FP32_REFINED_DF,
+                                                         kspace=combo.STAGGERED_DFMG)),
+            ("newton_cg_staggered_dfmg_fp64", dict(solver=combo.NEWTON_CG, precision=combo.FP64,
+                                                   kspace=combo.STAGGERED_DFMG)),
             ("basic_scheme_rotated_fp64", dict(solver=combo.FIXED_POINT, precision=combo.FP64)),
             ("newton_cg_rotated_refined_df_infinitesimal_strain",
              dict(solver=combo.NEWTON_CG, precision=combo.FP32_REFINED_DF, theory=combo.INFINITESIMAL_STRAIN)),
