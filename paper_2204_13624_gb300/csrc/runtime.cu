@@ -7,6 +7,7 @@
 // solver), Sec. 4 (composite boxels), Sec. 6.1 (Neo-Hookean phases).
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <condition_variable>
@@ -348,8 +349,11 @@ struct Profiler {
         cudaEventCreate(&e);
         return e;
     }
+    // every launch class is also an NVTX range named after it (a no-op
+    // unless a profiler that records NVTX is attached)
     void begin(int k)
     {
+        nvtxRangePushA(kclass_name[k]);
         if (!on) {
             launches[k]++;
             return;
@@ -360,6 +364,7 @@ struct Profiler {
     }
     void end()
     {
+        nvtxRangePop();
         if (!on) return;
         cudaEvent_t b = get();
         cudaEventRecord(b, st);
@@ -420,6 +425,14 @@ static void print_profile(const char* what, Profiler& p)
             std::fprintf(stderr, "[combo profile]   %-16s %8lld launches %10.3f ms\n", kclass_name[k], p.launches[k],
                          p.ms[k]);
 }
+
+// a named NVTX range over a host scope (solve phases)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ------------------------------------------------------------------ operator engine
 // One FFT + Green-operator pipeline in precision T.
@@ -1868,6 +1881,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                     break;
                 }
                 case ST_RESID: {
+                    const NvtxRange nr("newton_residual");
                     if (dfmg())
                         dfmg_law(0, true);
                     else
@@ -1888,6 +1902,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                     break;
                 }
                 case ST_CG: {
+                    const NvtxRange nr("cg_chunk");
                     // 8 CG iterations per host round trip; iterations after the
                     // device-side stop test are no-ops.  Without per-kernel
                     // timing the chunk is replayed from a captured CUDA graph.
@@ -3012,6 +3027,7 @@ extern "C" int combo_solve_begin(combo_ctx* ctx, const combo_problem* p, const c
     if (rc) return rc;
     CK(cudaSetDevice(ctx->device));
     HostProblem h;
+    const NvtxRange nr("solve_setup");
     if ((rc = load_problem(p, &o, h))) return rc;
     SolveBase* impl = nullptr;
     rc = make_solve(ctx, std::move(h), o, &impl);
