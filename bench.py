@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--variants-only", action="store_true", help="only the solver / discretisation variants")
     ap.add_argument("--dfmg-only", type=int, default=0, metavar="N",
                     help="only the doubly-fine material grid kernel timings on an N^3 random-ball problem")
+    ap.add_argument("--nine-component", action="store_true",
+                    help="Krylov operator in the nine-component form (no displacement form)")
     return ap.parse_args()
 
 
@@ -138,15 +140,28 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline
-def algorithmic_bytes(kernel, p, krylov_bytes):
+def algorithmic_bytes(kernel, p, krylov_bytes, disp=False):
     """Bytes the method must move per launch of a kernel class (reads + writes
-    of the fields it touches, each once), for the roofline."""
+    of the fields it touches, each once), for the roofline.  disp: the Krylov
+    operator runs in the displacement form (one nodal spectrum per tensor row
+    leaves the z-pass; the y-inverse and x-inverse take three components; the
+    gradient pass reads the three nodal fields and r, and writes r)."""
     n1, n2, n3 = p["n"]
     V = n1 * n2 * n3
     nb = int(p["boxel_idx"].size)
     nh = n1 // 2 + 1
     spec_c = 9 * n3 * n2 * nh  # stored half-spectrum complex entries
     w = krylov_bytes
+    if disp and kernel == "zgamma_krylov":
+        return (spec_c + spec_c // 3) * 2 * w
+    if disp and kernel == "yinv_krylov":
+        return 2 * (spec_c // 3) * 2 * w
+    if disp and kernel == "xinv_cg":
+        # three spectra read, three real nodal fields written
+        return (spec_c // 3) * 2 * w + 3 * V * w
+    if kernel == "grad_cg":
+        # nodal fields read, r read + written
+        return 3 * V * w + V * 18 * w
     if kernel in ("yfwd_krylov", "zgamma_krylov", "yinv_krylov"):
         return 2 * spec_c * 2 * w
     if kernel in ("yfwd_fp64", "zgamma_fp64", "yinv_fp64"):
@@ -282,6 +297,7 @@ def main():
     if dist:
         dist.barrier()
     combo.load()
+    combo.krylov_displacement_form(not args.nine_component)
     # one explicit stream for torch and the library, so that the CUDA events
     # bracket the library's launches and torch's allocations are ordered
     # with them (the default stream's handle would give the library its own)
@@ -441,7 +457,7 @@ def timed_window(combo, ctx, p, prec, steps, warmup, stream, dist=None, clk=None
     return ms, ops, residuals, prof, done
 
 
-KRYLOV = ("xfwd_tangent", "yfwd_krylov", "zgamma_krylov", "yinv_krylov", "xinv_cg")
+KRYLOV = ("xfwd_tangent", "yfwd_krylov", "zgamma_krylov", "yinv_krylov", "xinv_cg", "grad_cg")
 
 
 def kernel_table(combo, prof, p, prec, ops, peak, peak_kind):
@@ -451,7 +467,7 @@ def kernel_table(combo, prof, p, prec, ops, peak, peak_kind):
     for k, (kms, cnt) in prof.items():
         if cnt == 0:
             continue
-        b = algorithmic_bytes(k, p, kb)
+        b = algorithmic_bytes(k, p, kb, disp="grad_cg" in prof)
         # CG kernels are launched in graph chunks of 8 iterations; launches
         # past the converged iteration return at once and do no work, so the
         # per-launch time divides by the iterations that ran (ops)

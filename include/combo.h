@@ -424,6 +424,28 @@ int combo_autotune_force(int32_t pass, int32_t cand);
 int64_t combo_autotune_report(char* buf, int64_t len);
 
 /*
+ * Displacement form of the rotated Green operator in the FP32 Newton-CG
+ * Krylov passes (Sec. 3, the rotated scheme; an evaluation order, not a
+ * different operator).  The rotated symbol k_J is, up to the unit factor
+ * i e^{i (theta_1 + theta_2 + theta_3) / 2}, the real kr_J of the symbol
+ * tables, and it is the Fourier symbol of the HEX8R gradient of a nodal
+ * field (edge differences along J averaged over a voxel's 4 such edges).
+ * So row i of G X is that gradient of one periodic nodal field u_i, whose
+ * spectrum is k^H X_i / |k|^2: the inverse z, y and x transforms run on 3
+ * fields instead of 9 components, and the gradient is taken in real space,
+ * fused with the CG update.  It applies to single and stacked solves (and
+ * the own-launch classes of batches over several grids) with the rotated
+ * scheme, FP32 Krylov words, the TMA y- and z-passes (sides 48 ... 512 of
+ * the compile-time plans) and n1 = 128, 256 or 512 with n2 a multiple of 4;
+ * other solves run the nine-component form.  Results agree with the
+ * nine-component form up to FP32 rounding.
+ *   combo_krylov_displacement_form(0) makes solves set up afterwards use the
+ *     nine-component form everywhere; (1, the default) restores the switch.
+ * Process-wide; takes effect when a solve is set up.
+ */
+void combo_krylov_displacement_form(int32_t enable);
+
+/*
  * Per-kernel timing of a solve (instrumentation, no effect on results).
  *   combo_solve_profile(s, 1) resets the counters and records a CUDA event
  *   pair around every kernel launch of the solve on its stream; 0 stops.

@@ -472,6 +472,7 @@ template <typename T> struct YArgs {
     const void* tmap;  // CUtensorMap of spec for the TMA y-pass (FP32), or null
     int cfg;           // launch-shape candidate (autotuner; 0 = default)
     uint32_t wait_cap;  // poll cap of the tile waits (wait_cap_of: 0 = default)
+    int disp;           // TMA y-inverse: only components 0, 3, 6 (displacement form)
 };
 
 template <typename T> struct ZArgs {
@@ -491,6 +492,13 @@ template <typename T> struct ZArgs {
     const void* tmap;  // CUtensorMap of spec for the TMA z-pass (FP32), or null
     int cfg;           // launch-shape candidate (autotuner; 0 = default)
     uint32_t wait_cap;  // poll cap of the tile waits (wait_cap_of: 0 = default)
+    // displacement form of the rotated operator (TMA z-pass only): row i
+    // leaves as one spectrum, u_i = -i conj(P) (k . X_i) / |k|^2, into
+    // component 3 i, through tmap_u (tile box of one component); rph[j][xi] =
+    // e^{i pi xi / n_j}, P = prod_j rph[j][xi_j]
+    int disp;
+    const void* tmap_u;
+    const cx<T>* rph[3];
 };
 
 // Grouped launches: one persistent launch runs the work items of several
@@ -538,10 +546,39 @@ bool zpass_tma_size(int n3);
 // (cand: tile-width candidate; the tensor map must be encoded for the
 // candidate the launch's cfg selects)
 bool zpass_tma_encode(void* map, const GridDims& g, const void* spec, int cand);
+bool zpass_tma_encode_u(void* map, const GridDims& g, const void* spec, int cand);  // one-component box
 void launch_zpass_tma(const ZArgs<float>& a, const void* map, cudaStream_t st);
 bool ypass_tma_encode(void* map, const GridDims& g, const void* spec, int cand);
 template <bool INV> void launch_ypass_tma(const YArgs<float>& a, const void* map, cudaStream_t st);
 void launch_xinv_stream(const XinvArgs<float, float>& a, cudaStream_t st);
+
+// Displacement form of the rotated Green operator in the FP32 CG (xdisp.cu):
+// after the displacement z-pass and the y-inverse of components 0, 3, 6, the
+// x-inverse turns those three spectra into the nodal fields u_i (real,
+// [n3][n2][n1] each, at u + i * ustride), and the gradient pass forms the
+// HEX8R gradient F_iJ = c_J sum over the 4 voxel edges along J of the
+// differences of u_i (c_J = 1 / (4 h_J)) with the CG update r -= alpha F and
+// the fused (r, r) reduction of the CG x-inverse.
+struct DispArgs {
+    GridDims g;
+    const cx<float>* tw;   // exp(-2 pi i t / M)
+    const cx<float>* tw2;  // exp(-2 pi i k / n1)
+    const cx<float>* spec;
+    float* u;              // three real fields
+    int64_t ustride;       // floats between them
+    float* r;              // [9][V]
+    float cJ[3];           // 1 / (4 h_J)
+    double* partial;
+    Scalars* sc;
+    int fuse;              // the last block turns the (r, r) partials into beta / stop
+    double cg_tol;
+    int cg_max, cg_fixed;
+    uint32_t wait_cap;
+};
+bool disp_x_ok(const GridDims& g);  // sizes the two x kernels take
+void launch_xinv_disp(const DispArgs& a, cudaStream_t st);
+void launch_disp_grad_cg(const DispArgs& a, cudaStream_t st);
+int disp_grad_partials_max();  // largest grid of the gradient pass (its partials)
 
 // Record msg as the calling thread's last error; returns code.
 int set_error(int code, const char* msg);

@@ -300,9 +300,19 @@ __device__ __forceinline__ void stage_store(cx<T> (&v)[(N / R) / TPL][R], const 
 // between the loads and the stores of the first / last stage, for when lg or
 // sg alias the exchange buffer.  Every thread of the block must call it with
 // the same plan (it holds __syncthreads); the caller synchronises before
-// reusing the exchange buffer.
-template <typename T, int N, bool INV, bool SYNC_FIRST = false, bool SYNC_LAST = false, class LG, class SG, class LX,
-          class SX>
+// reusing the exchange buffer.  NBAR > 0: the calling threads are only the
+// first NBAR of the block (a multiple of 32), which synchronise on named
+// barrier 1 instead; the rest of the block must not use that barrier meanwhile.
+template <int NBAR> __device__ __forceinline__ void fft_sync()
+{
+    if constexpr (NBAR == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync 1, %0;" ::"n"(NBAR) : "memory");
+}
+
+template <typename T, int N, bool INV, bool SYNC_FIRST = false, bool SYNC_LAST = false, int NBAR = 0, class LG,
+          class SG, class LX, class SX>
 __device__ __forceinline__ void fft_fast(const LG& lg, const SG& sg, const LX& lx, const SX& sx, int tau,
                                          const cx<T>* __restrict__ tw)
 {
@@ -314,14 +324,14 @@ __device__ __forceinline__ void fft_fast(const LG& lg, const SG& sg, const LX& l
         {
             cx<T> v[(N / RA) / TPL][RA];
             stage_load<T, N, RA, 1, TPL, INV>(v, lg, tau, tw);
-            if constexpr (SYNC_FIRST) __syncthreads();
+            if constexpr (SYNC_FIRST) fft_sync<NBAR>();
             stage_store<T, N, RA, 1, TPL>(v, sx, tau);
         }
-        __syncthreads();
+        fft_sync<NBAR>();
         {
             cx<T> v[(N / RB) / TPL][RB];
             stage_load<T, N, RB, RA, TPL, INV>(v, lx, tau, tw);
-            if constexpr (SYNC_LAST) __syncthreads();
+            if constexpr (SYNC_LAST) fft_sync<NBAR>();
             stage_store<T, N, RB, RA, TPL>(v, sg, tau);
         }
     } else {
@@ -330,21 +340,21 @@ __device__ __forceinline__ void fft_fast(const LG& lg, const SG& sg, const LX& l
         {
             cx<T> v[(N / RA) / TPL][RA];
             stage_load<T, N, RA, 1, TPL, INV>(v, lg, tau, tw);
-            if constexpr (SYNC_FIRST) __syncthreads();
+            if constexpr (SYNC_FIRST) fft_sync<NBAR>();
             stage_store<T, N, RA, 1, TPL>(v, sx, tau);
         }
-        __syncthreads();
+        fft_sync<NBAR>();
         {
             cx<T> v[(N / RB) / TPL][RB];
             stage_load<T, N, RB, RA, TPL, INV>(v, lx, tau, tw);
-            __syncthreads();
+            fft_sync<NBAR>();
             stage_store<T, N, RB, RA, TPL>(v, sx, tau);
         }
-        __syncthreads();
+        fft_sync<NBAR>();
         {
             cx<T> v[(N / RC) / TPL][RC];
             stage_load<T, N, RC, RA * RB, TPL, INV>(v, lx, tau, tw);
-            if constexpr (SYNC_LAST) __syncthreads();
+            if constexpr (SYNC_LAST) fft_sync<NBAR>();
             stage_store<T, N, RC, RA * RB, TPL>(v, sg, tau);
         }
     }

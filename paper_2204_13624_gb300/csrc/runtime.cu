@@ -193,6 +193,7 @@ template <typename T> struct DevTables {
     T* sa[3] = {nullptr, nullptr, nullptr};
     T* sb[3] = {nullptr, nullptr, nullptr};
     cx<T>* ph[3] = {nullptr, nullptr, nullptr};  // staggered grid only
+    cx<T>* rph[3] = {nullptr, nullptr, nullptr};  // rotated scheme only: the same e^{i pi xi / n}
 };
 
 template <typename T> static int upload_tw(cx<T>** d, int n, int denom)
@@ -245,6 +246,9 @@ template <typename T> static int upload_symbols(DevTables<T>& t, const int n[3],
         if (kspace == COMBO_STAGGERED) {
             CK(dev_malloc(&t.ph[j], sizeof(cx<T>) * n[j]));
             CK(cudaMemcpy(t.ph[j], ph.data(), sizeof(cx<T>) * n[j], cudaMemcpyHostToDevice));
+        } else if (kspace == COMBO_ROTATED && sizeof(T) == 4) {
+            CK(dev_malloc(&t.rph[j], sizeof(cx<T>) * n[j]));
+            CK(cudaMemcpy(t.rph[j], ph.data(), sizeof(cx<T>) * n[j], cudaMemcpyHostToDevice));
         }
     }
     return COMBO_OK;
@@ -271,6 +275,7 @@ template <typename T> static void free_tables(DevTables<T>& t)
         cudaFree(t.sa[j]);
         cudaFree(t.sb[j]);
         cudaFree(t.ph[j]);
+        cudaFree(t.rph[j]);
     }
 }
 
@@ -318,12 +323,13 @@ enum KClass {
     K_DFMG_PURE,
     K_DFMG_GATHER,
     K_DFMG_CG,
+    K_DISP_GRAD,
     K_NCLASS
 };
 static const char* kclass_name[K_NCLASS] = {"boxel_laminate", "xfwd_resid_fp64", "yfwd_fp64", "zgamma_fp64",
                                              "yinv_fp64", "xinv_fp64", "xfwd_tangent", "yfwd_krylov",
                                              "zgamma_krylov", "yinv_krylov", "xinv_cg", "finalize", "update_F",
-                                             "dfmg_pure", "dfmg_gather", "dfmg_cg_tangent"};
+                                             "dfmg_pure", "dfmg_gather", "dfmg_cg_tangent", "grad_cg"};
 
 struct Profiler {
     bool on = false;
@@ -445,6 +451,11 @@ template <typename T> struct Engine {
     // TMA views of spec for the FP32 z- and y-passes, one per tile-width candidate
     CUtensorMap zmap[2], ymap[2];
     bool zmap_ok[2] = {false, false}, ymap_ok[2] = {false, false};
+    // displacement form of the rotated operator in the FP32 Krylov passes:
+    // the z-pass's one-component store maps and the switch (set per solve)
+    CUtensorMap zumap[2];
+    bool zumap_ok[2] = {false, false};
+    int use_disp = 0;
     // launch-shape candidates chosen by the autotuner: x-forward, y, z, x-inverse
     int cfg_xf = 0, cfg_y = 0, cfg_z = 0, cfg_xi = 0;
     uint32_t wait_cap = 0;  // poll cap of the bulk-copy waits (wait_cap_of; 0 = default)
@@ -454,6 +465,7 @@ template <typename T> struct Engine {
         for (int c = 0; c < 2; c++) {
             zmap_ok[c] = (sizeof(T) == 4) && zpass_tma_encode(&zmap[c], g, s, c);
             ymap_ok[c] = (sizeof(T) == 4) && ypass_tma_encode(&ymap[c], g, s, c);
+            zumap_ok[c] = (sizeof(T) == 4) && tab.rph[0] && zpass_tma_encode_u(&zumap[c], g, s, c);
         }
         if (!zmap_ok[cfg_z]) cfg_z = 0;
         if (!ymap_ok[cfg_y]) cfg_y = 0;
@@ -470,6 +482,16 @@ template <typename T> struct Engine {
         return make_tables<T>(tab, g, l, kspace);
     }
     void release() { free_tables<T>(tab); }
+    // the displacement form applies: rotated FP32 tables, TMA y- and z-passes
+    // at the chosen tile widths and an x side for this grid
+    bool disp_capable() const
+    {
+        return sizeof(T) == 4 && tab.rph[0] && zmap_ok[cfg_z] && zumap_ok[cfg_z] && ymap_ok[cfg_y] && disp_x_ok(g);
+    }
+    // the nodal fields of the displacement form: components 1, 4, 7 of the
+    // FP32 spectrum (free once the z-pass has read them), V floats each
+    float* disp_u() const { return reinterpret_cast<float*>(spec + g.Vs); }
+    int64_t disp_ustride() const { return 3 * 2 * g.Vs; }
 
     template <typename Tc> XfwdArgs<T, Tc> xf() const
     {
@@ -532,6 +554,11 @@ template <typename T> struct Engine {
         z.cfg = cfg_z;
         z.tmap = zmap_ok[cfg_z] ? &zmap[cfg_z] : nullptr;
         z.wait_cap = wait_cap;
+        if (use_disp && guard == 1 && !want_norm && z.tmap && zumap_ok[cfg_z]) {
+            z.disp = 1;
+            z.tmap_u = &zumap[cfg_z];
+            for (int j = 0; j < 3; j++) z.rph[j] = tab.rph[j];
+        }
         return z;
     }
     // y forward, z forward + projection + z inverse, y inverse
@@ -546,8 +573,10 @@ template <typename T> struct Engine {
         if (pr) pr->begin(kbase + 1);
         launch_zpass<T>(z, st);
         if (pr) pr->end();
+        YArgs<T> yi = y;
+        yi.disp = z.disp;  // the displacement form leaves components 0, 3, 6 only
         if (pr) pr->begin(kbase + 2);
-        launch_ypass<T, true>(y, st);
+        launch_ypass<T, true>(yi, st);
         if (pr) pr->end();
     }
     int zblocks_p() const { return zpass_blocks(g, txz, sizeof(cx<T>)); }  // z-pass blocks (partials) per problem
@@ -1021,6 +1050,9 @@ struct TuneRec {
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneRec> g_tune;
 static std::atomic<int> g_tune_enabled{1};
+// displacement form of the rotated operator in the FP32 Krylov passes (on by
+// default wherever it applies; read when a solve is set up)
+static std::atomic<int> g_disp_enabled{1};
 static std::atomic<int> g_tune_force[4] = {{-1}, {-1}, {-1}, {-1}};  // per pass: forced candidate or -1
 
 static void tune_store(const TuneKey& k, const TuneRec& r)
@@ -1233,6 +1265,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         CK(cudaMemsetAsync(d_spec, 0, sizeof(double2) * 9 * g.Vs, st));
         int nbuf = std::max(std::max(e64.xpartials(), e64.zblocks()), std::max(ec.xpartials(), ec.zblocks()));
         if (dfmg()) nbuf = std::max(nbuf, dfmg_cg_blocks(V));
+        nbuf = std::max(nbuf, disp_grad_partials_max() + g.nprob);  // the displacement form's gradient pass
         CK(dev_malloc(&d_part, 8 * (size_t)nbuf));
         if (ext_sc)
             d_sc = ext_sc;
@@ -1334,6 +1367,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         if (newton() && (!member || own_launches)) {
             if ((rc = autotune())) return rc;
             tune_force(ec);
+            ec.use_disp = (g_disp_enabled.load() && ec.disp_capable()) ? 1 : 0;
         }
         return COMBO_OK;
     }
@@ -1663,6 +1697,45 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         xi.cg_fixed = opt.cg_fixed_iterations;
         return xi;
     }
+    // the x side of the Krylov operator with the CG update: the CG x-inverse,
+    // or, in the displacement form, the x-inverse of the three nodal fields
+    // and their gradient with the update
+    void krylov_xinv()
+    {
+        if constexpr (std::is_same<Tc, float>::value) {
+            if (ec.use_disp) {
+                DispArgs d{};
+                d.g = g;
+                d.tw = ec.tab.twM;
+                d.tw2 = ec.tab.tw2;
+                d.spec = ec.spec;
+                d.u = ec.disp_u();
+                d.ustride = ec.disp_ustride();
+                d.r = d_r;
+                const int n[3] = {g.n1, g.n2, g.n3p};
+                for (int j = 0; j < 3; j++) d.cJ[j] = (float)(n[j] / (4.0 * hp.l[j]));  // 1 / (4 h_J)
+                d.partial = d_part;
+                d.sc = d_sc;
+                d.fuse = 1;
+                d.cg_tol = opt.cg_tol;
+                d.cg_max = opt.cg_max_iter;
+                d.cg_fixed = opt.cg_fixed_iterations;
+                d.wait_cap = ec.wait_cap;
+                prof.begin(K_XINV_CG);
+                launch_xinv_disp(d, st);
+                prof.end();
+                prof.begin(K_DISP_GRAD);
+                launch_disp_grad_cg(d, st);
+                prof.end();
+                return;
+            }
+        }
+        const auto xi = cg_xi();
+        prof.begin(K_XINV_CG);
+        launch_xinv<Tc, Tc>(xi, 1, st);
+        prof.end();
+    }
+
     // one CG iteration in precision Tc, guarded by cg_done
     void cg_iteration()
     {
@@ -1675,10 +1748,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         launch_xfwd<Tc, Tc>(xf, 1, st);
         prof.end();
         ec.yz(d_sc, 1, false, nullptr, st, &prof, K_YFWD_C);
-        const auto xi = cg_xi();
-        prof.begin(K_XINV_CG);
-        launch_xinv<Tc, Tc>(xi, 1, st);
-        prof.end();
+        krylov_xinv();
     }
 
     // doubly-fine material grid: the direction update, the sub-cell tangents
@@ -1720,10 +1790,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         launch_xfwd<Tc, Tc>(xf, 1, st);
         prof.end();
         ec.yz(d_sc, 1, false, nullptr, st, &prof, K_YFWD_C);
-        const auto xi = cg_xi();
-        prof.begin(K_XINV_CG);
-        launch_xinv<Tc, Tc>(xi, 1, st);
-        prof.end();
+        krylov_xinv();
     }
 
     // capture one chunk of kCgChunk CG iterations (kernel arguments are fixed
@@ -3131,6 +3198,8 @@ extern "C" int combo_solve(combo_ctx* ctx, const combo_problem* p, const combo_o
 }
 
 extern "C" void combo_autotune_enable(int32_t enable) { g_tune_enabled.store(enable ? 1 : 0); }
+
+extern "C" void combo_krylov_displacement_form(int32_t enable) { g_disp_enabled.store(enable ? 1 : 0); }
 
 extern "C" int combo_autotune_force(int32_t pass, int32_t cand)
 {

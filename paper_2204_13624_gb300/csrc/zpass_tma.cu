@@ -110,9 +110,29 @@ bool zpass_tma_encode(void* map, const GridDims& g, const void* spec, int cand)
     return encode_spec_map(map, g, spec, box, g.n3p > 256 ? 2 : -1);
 }
 
-template <int N, int TX>
+// Tensor map of the same spectrum with a one-component tile box {TX, 1, n3,
+// 1}: the store of the displacement form's z-pass (one spectrum per row).
+bool zpass_tma_encode_u(void* map, const GridDims& g, const void* spec, int cand)
+{
+    if (!zpass_tma_size(g.n3p) || !spec) return false;
+    const int tx = tma_tx_rt(g.n3p, cand);
+    if ((g.nhp * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(spec) & 15) != 0) return false;
+    const cuuint32_t box[4] = {(cuuint32_t)tx, 1, (cuuint32_t)g.n3p, 1};
+    return encode_spec_map(map, g, spec, box, g.n3p > 256 ? 2 : -1);
+}
+
+// DISP: the displacement form of the rotated operator.  The rotated symbol is
+// k_J = i P kr_J with P = e^{i (theta_1 + theta_2 + theta_3) / 2} and the real
+// kr of the symbol tables, so G X_i = k (k^H X_i) / |k|^2 is the HEX8R
+// gradient (the 8-node trilinear element's average gradient, an edge
+// difference averaged over the 4 parallel edges of the voxel) of the nodal
+// field u_i = IFFT(-i conj(P) (kr . X_i) / |kr|^2).  The tile's row then
+// leaves as that one spectrum, into component 3 i: the inverse z transform
+// runs on one component instead of three, by the first component group of
+// threads on named barrier 1 while the others wait at the block barrier.
+template <int N, int TX, bool DISP>
 __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL)
-    k_zpass_tma(const __grid_constant__ CUtensorMap tm, ZArgs<float> a)
+    k_zpass_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUtensorMap tmu, ZArgs<float> a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr int TPL = FastPlan<N>::TPL;
@@ -213,6 +233,19 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL)
             const float az = a.sa[2][z], bz = a.sb[2][z];
             const float k0 = ax * by * bz, k1 = ay * bx * bz, k2 = az * bx * by;
             const float kk = k0 * k0 + k1 * k1 + k2 * k2;
+            if constexpr (DISP) {
+                C o{0.f, 0.f};
+                if (kk > 0.f) {
+                    const float ik = a.scale / kk;
+                    const float sr = (k0 * X0.x + k1 * X1.x + k2 * X2.x) * ik;
+                    const float si = (k0 * X0.y + k1 * X1.y + k2 * X2.y) * ik;
+                    const C P = c_mul(c_mul(a.rph[0][xi1], a.rph[1][y]), a.rph[2][z]);
+                    // -i conj(P) (sr + i si)
+                    o = C{P.x * si - P.y * sr, -(P.x * sr + P.y * si)};
+                }
+                p[0] = o;
+                continue;
+            }
             C o0{0.f, 0.f}, o1{0.f, 0.f}, o2{0.f, 0.f};
             if (kk > 0.f) {
                 const float ik = 1.f / kk;
@@ -234,14 +267,23 @@ __global__ void __launch_bounds__(3 * TX * FastPlan<N>::TPL)
         __syncthreads();
 
         // inverse along z, in place; then the whole tile leaves by one store
-        fft_fast<float, N, true, true, true>(lp, sp, lp, sp, tau, tws);
+        if constexpr (DISP) {
+            // component 0 only, by the warps of the first group (threads of
+            // its last warp beyond GS transform lines of component 1, which
+            // is not stored)
+            constexpr int GSW = (GS + 31) / 32 * 32;
+            if (threadIdx.x < GSW) fft_fast<float, N, true, true, true, GSW>(lp, sp, lp, sp, tau, tws);
+        } else {
+            fft_fast<float, N, true, true, true>(lp, sp, lp, sp, tau, tws);
+        }
         fence_proxy_async();  // this thread's tile writes, before the copy engine reads them
         __syncthreads();
         if (threadIdx.x == 0) {
+            const CUtensorMap* ts = DISP ? &tmu : &tm;
             if constexpr (N > 256)
-                tma_store_5d(&tm, x0, y, 0, pb * (N / 256), 3 * row, park);
+                tma_store_5d(ts, x0, y, 0, pb * (N / 256), 3 * row, park);
             else
-                tma_store_4d(&tm, x0, y, pb * N, 3 * row, park);
+                tma_store_4d(ts, x0, y, pb * N, 3 * row, park);
             bulk_commit();
         }
     }
@@ -284,7 +326,8 @@ __global__ void __launch_bounds__(TX * FastPlan<N>::TPL)
     for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = a.tw[i];
     const int line = threadIdx.x % TX, tau = threadIdx.x / TX;
     const int nxt = (g.nh + TX - 1) / TX;
-    const int ntiles = nxt * g.n3 * 9;
+    const int cs = a.disp ? 3 : 1;  // component stride: the displacement form's y-inverse takes 0, 3, 6
+    const int ntiles = nxt * g.n3 * (9 / cs);
     // a tile of a finished problem (the problem of its z plane) is skipped
     auto done_of = [&](const Scalars* q) { return (a.guard == 1 && q->cg_done) || (a.guard == 2 && q->outer_done); };
     const bool done0 = done_of(a.sc);
@@ -297,7 +340,7 @@ __global__ void __launch_bounds__(TX * FastPlan<N>::TPL)
     // tile t = (c * n3 + z) * nxt + xt
     auto issue = [&](int t, int s) {
         const int xt = t % nxt, rest = t / nxt;
-        const int z = rest % g.n3, c = rest / g.n3;
+        const int z = rest % g.n3, c = (rest / g.n3) * cs;
         mbar_arrive_expect_tx(&bar[s], TILE_BYTES);
         if constexpr (N > 256)
             tma_load_5d(tiles + s * TILE, &tm, xt * TX, 0, 0, z, c, &bar[s]);
@@ -329,7 +372,7 @@ __global__ void __launch_bounds__(TX * FastPlan<N>::TPL)
             break;
         }
         const int xt = t % nxt, rest = t / nxt;
-        const int z = rest % g.n3, c = rest / g.n3;
+        const int z = rest % g.n3, c = (rest / g.n3) * cs;
         C* park = tiles + s * TILE;
         C* pc = park + line;
         auto lp = [&](int e) { return pc[e * TX]; };
@@ -374,7 +417,7 @@ static void ypass_tma_launch(const YArgs<float>& a, const void* map, cudaStream_
             per = 1;
         grid_per_sm = per;
     }
-    const int ntiles = ((a.g.nh + TX - 1) / TX) * a.g.n3 * 9;
+    const int ntiles = ((a.g.nh + TX - 1) / TX) * a.g.n3 * (a.disp ? 3 : 9);
     const int grid = std::min(ntiles, grid_per_sm * nsm);
     k_ypass_tma<N, TX, INV><<<grid, threads, sm, st>>>(*reinterpret_cast<const CUtensorMap*>(map), a);
 }
@@ -407,34 +450,46 @@ template void launch_ypass_tma<false>(const YArgs<float>&, const void*, cudaStre
 template void launch_ypass_tma<true>(const YArgs<float>&, const void*, cudaStream_t);
 
 // ------------------------------------------------------------- z-pass launch
-template <int N, int TX> static void zpass_tma_launch(const ZArgs<float>& a, const void* map, cudaStream_t st)
+template <int N, int TX, bool DISP>
+static void zpass_tma_launch(const ZArgs<float>& a, const void* map, cudaStream_t st)
 {
     constexpr int threads = 3 * TX * FastPlan<N>::TPL;
     const size_t sm = (size_t)2 * 3 * N * TX * 8 + 16 + (size_t)N * 8;
     static int grid_per_sm = 0;
     static int nsm = 0;
     if (grid_per_sm == 0) {
-        cudaFuncSetAttribute(k_zpass_tma<N, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_zpass_tma<N, TX, DISP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         int dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
         int per = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zpass_tma<N, TX>, threads, sm) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zpass_tma<N, TX, DISP>, threads, sm) !=
+                cudaSuccess ||
             per < 1)
             per = 1;
         grid_per_sm = per;
     }
     const int ntiles = ((a.g.nh + TX - 1) / TX) * a.g.n2 * 3 * a.g.nprob;
     const int grid = std::min(ntiles, grid_per_sm * nsm);
-    k_zpass_tma<N, TX><<<grid, threads, sm, st>>>(*reinterpret_cast<const CUtensorMap*>(map), a);
+    const CUtensorMap& tm = *reinterpret_cast<const CUtensorMap*>(map);
+    const CUtensorMap& tmu = DISP ? *reinterpret_cast<const CUtensorMap*>(a.tmap_u) : tm;
+    k_zpass_tma<N, TX, DISP><<<grid, threads, sm, st>>>(tm, tmu, a);
 }
 
 template <int N> static void zpass_tma_pick(const ZArgs<float>& a, const void* map, cudaStream_t st)
 {
-    if (a.cfg == 1)
-        zpass_tma_launch<N, tma_tx<N, 1>()>(a, map, st);
-    else
-        zpass_tma_launch<N, tma_tx<N, 0>()>(a, map, st);
+    const bool disp = a.disp && a.tmap_u;
+    if (a.cfg == 1) {
+        if (disp)
+            zpass_tma_launch<N, tma_tx<N, 1>(), true>(a, map, st);
+        else
+            zpass_tma_launch<N, tma_tx<N, 1>(), false>(a, map, st);
+    } else {
+        if (disp)
+            zpass_tma_launch<N, tma_tx<N, 0>(), true>(a, map, st);
+        else
+            zpass_tma_launch<N, tma_tx<N, 0>(), false>(a, map, st);
+    }
 }
 
 void launch_zpass_tma(const ZArgs<float>& a, const void* map, cudaStream_t st)
