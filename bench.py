@@ -467,7 +467,7 @@ def kernel_table(combo, prof, p, prec, ops, peak, peak_kind):
     for k, (kms, cnt) in prof.items():
         if cnt == 0:
             continue
-        b = algorithmic_bytes(k, p, kb, disp="grad_cg" in prof)
+        b = algorithmic_bytes(k, p, kb, disp=prof.get("grad_cg", (0.0, 0))[1] > 0)
         # CG kernels are launched in graph chunks of 8 iterations; launches
         # past the converged iteration return at once and do no work, so the
         # per-launch time divides by the iterations that ran (ops)
