@@ -71,8 +71,8 @@ def parse():
     ap.add_argument("--variants-only", action="store_true", help="only the solver / discretisation variants")
     ap.add_argument("--dfmg-only", type=int, default=0, metavar="N",
                     help="only the doubly-fine material grid kernel timings on an N^3 random-ball problem")
-    ap.add_argument("--nine-component", action="store_true",
-                    help="Krylov operator in the nine-component form (no displacement form)")
+    ap.add_argument("--krylov-form", default="nodal", choices=["nine", "displacement", "nodal"],
+                    help="most reduced evaluation form of the rotated Krylov operator")
     return ap.parse_args()
 
 
@@ -140,18 +140,24 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline
-def algorithmic_bytes(kernel, p, krylov_bytes, disp=False):
+def algorithmic_bytes(kernel, p, krylov_bytes, disp=False, nodal=False):
     """Bytes the method must move per launch of a kernel class (reads + writes
     of the fields it touches, each once), for the roofline.  disp: the Krylov
     operator runs in the displacement form (one nodal spectrum per tensor row
     leaves the z-pass; the y-inverse and x-inverse take three components; the
-    gradient pass reads the three nodal fields and r, and writes r)."""
+    gradient pass reads the three nodal fields and r, and writes r).  nodal:
+    also the forward side takes three components (the tangent pass writes
+    the nodal forces' spectra; the halo lines it re-reads are not counted)."""
     n1, n2, n3 = p["n"]
     V = n1 * n2 * n3
     nb = int(p["boxel_idx"].size)
     nh = n1 // 2 + 1
     spec_c = 9 * n3 * n2 * nh  # stored half-spectrum complex entries
     w = krylov_bytes
+    if kernel == "xfwd_nodal":
+        return V * (45 * w + 1) + (V - nb) * 10 * w + nb * (4 + 45 * w) + (spec_c // 3) * 2 * w
+    if nodal and kernel in ("yfwd_krylov", "zgamma_krylov"):
+        return 2 * (spec_c // 3) * 2 * w
     if disp and kernel == "zgamma_krylov":
         return (spec_c + spec_c // 3) * 2 * w
     if disp and kernel == "yinv_krylov":
@@ -297,7 +303,7 @@ def main():
     if dist:
         dist.barrier()
     combo.load()
-    combo.krylov_displacement_form(not args.nine_component)
+    combo.krylov_form({"nine": 0, "displacement": 1, "nodal": 2}[args.krylov_form])
     # one explicit stream for torch and the library, so that the CUDA events
     # bracket the library's launches and torch's allocations are ordered
     # with them (the default stream's handle would give the library its own)
@@ -457,7 +463,7 @@ def timed_window(combo, ctx, p, prec, steps, warmup, stream, dist=None, clk=None
     return ms, ops, residuals, prof, done
 
 
-KRYLOV = ("xfwd_tangent", "yfwd_krylov", "zgamma_krylov", "yinv_krylov", "xinv_cg", "grad_cg")
+KRYLOV = ("xfwd_tangent", "xfwd_nodal", "yfwd_krylov", "zgamma_krylov", "yinv_krylov", "xinv_cg", "grad_cg")
 
 
 def kernel_table(combo, prof, p, prec, ops, peak, peak_kind):
@@ -467,7 +473,8 @@ def kernel_table(combo, prof, p, prec, ops, peak, peak_kind):
     for k, (kms, cnt) in prof.items():
         if cnt == 0:
             continue
-        b = algorithmic_bytes(k, p, kb, disp=prof.get("grad_cg", (0.0, 0))[1] > 0)
+        b = algorithmic_bytes(k, p, kb, disp=prof.get("grad_cg", (0.0, 0))[1] > 0,
+                              nodal=prof.get("xfwd_nodal", (0.0, 0))[1] > 0)
         # CG kernels are launched in graph chunks of 8 iterations; launches
         # past the converged iteration return at once and do no work, so the
         # per-launch time divides by the iterations that ran (ops)

@@ -424,26 +424,38 @@ int combo_autotune_force(int32_t pass, int32_t cand);
 int64_t combo_autotune_report(char* buf, int64_t len);
 
 /*
- * Displacement form of the rotated Green operator in the FP32 Newton-CG
- * Krylov passes (Sec. 3, the rotated scheme; an evaluation order, not a
- * different operator).  The rotated symbol k_J is, up to the unit factor
- * i e^{i (theta_1 + theta_2 + theta_3) / 2}, the real kr_J of the symbol
- * tables, and it is the Fourier symbol of the HEX8R gradient of a nodal
- * field (edge differences along J averaged over a voxel's 4 such edges).
- * So row i of G X is that gradient of one periodic nodal field u_i, whose
- * spectrum is k^H X_i / |k|^2: the inverse z, y and x transforms run on 3
- * fields instead of 9 components, and the gradient is taken in real space,
- * fused with the CG update.  It applies to single and stacked solves (and
- * the own-launch classes of batches over several grids) with the rotated
- * scheme, FP32 Krylov words, the TMA y- and z-passes (sides 48 ... 512 of
- * the compile-time plans) and n1 = 128, 256 or 512 with n2 a multiple of 4;
- * other solves run the nine-component form.  Results agree with the
- * nine-component form up to FP32 rounding.
- *   combo_krylov_displacement_form(0) makes solves set up afterwards use the
- *     nine-component form everywhere; (1, the default) restores the switch.
- * Process-wide; takes effect when a solve is set up.
+ * Evaluation forms of the rotated Green operator in the FP32 Newton-CG
+ * Krylov passes (no counterpart in the paper; Sec. 3, the rotated scheme).
+ * The rotated symbol k_J is, up to the unit factor i e^{i (theta_1 + theta_2
+ * + theta_3) / 2}, the real kr_J of the symbol tables, and it is the Fourier
+ * symbol of the HEX8R gradient D of a nodal field (edge differences along J
+ * averaged over a voxel's 4 such edges, over h_J).  So G = D (D^T D)^+ D^T,
+ * with D^T D the scalar |k|^2, and
+ *   COMBO_KRYLOV_NINE          transforms all nine components of A : p both
+ *                              ways and projects with k (k . X_i) / |k|^2;
+ *   COMBO_KRYLOV_DISPLACEMENT  transforms nine components forward, leaves the
+ *                              z-pass with the nodal field u_i = k^H X_i /
+ *                              |k|^2 of each row and takes its gradient D u_i
+ *                              in real space (three inverse transforms);
+ *   COMBO_KRYLOV_NODAL         also assembles the nodal forces f_i = D^T (A :
+ *                              p)_i in real space in the tangent pass (three
+ *                              forward transforms, the z-pass divides by
+ *                              |kr|^2); the direction p alternates between
+ *                              two buffers (36 bytes more per voxel).
+ * Each is an evaluation order of the same operator: results agree up to FP32
+ * rounding.  The reduced forms apply to single and stacked solves (and the
+ * own-launch classes of batches over several grids) with the rotated scheme,
+ * FP32 Krylov words, the TMA y- and z-passes (sides 48 ... 512 with
+ * compile-time plans) and n1 = 128, 256 or 512 with n2 a multiple of 4;
+ * other solves take the most reduced form that applies.
+ *   combo_krylov_form(form) sets the most reduced form that solves set up
+ *     afterwards may use (default COMBO_KRYLOV_NODAL); COMBO_E_INVALID_ARG
+ *     outside 0..2.  Process-wide.
  */
-void combo_krylov_displacement_form(int32_t enable);
+#define COMBO_KRYLOV_NINE 0
+#define COMBO_KRYLOV_DISPLACEMENT 1
+#define COMBO_KRYLOV_NODAL 2
+int combo_krylov_form(int32_t form);
 
 /*
  * Per-kernel timing of a solve (instrumentation, no effect on results).

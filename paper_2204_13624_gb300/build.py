@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcombo.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["xpass.cu", "xpass_stream.cu", "xdisp.cu", "yzpass.cu", "boxel.cu", "runtime.cu", "noalloc.cu", "zpass_tma.cu", "coarse.cu", "dfmg.cu"]
+SOURCES = ["xpass.cu", "xpass_stream.cu", "xdisp.cu", "xnodal.cu", "yzpass.cu", "boxel.cu", "runtime.cu", "noalloc.cu", "zpass_tma.cu", "coarse.cu", "dfmg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

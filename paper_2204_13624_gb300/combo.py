@@ -66,7 +66,7 @@ EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_o
            "combo_autotune_enable", "combo_autotune_force", "combo_autotune_report", "combo_coarse_grain",
            "combo_coarse_grain_profile", "combo_coarse_grain_profile_read", "combo_df_log",
            "combo_solve_advance_steps", "combo_state_export", "combo_state_import", "combo_neohooke_eval",
-           "combo_laminate_eval", "combo_fault_inject_alloc", "combo_krylov_displacement_form"]
+           "combo_laminate_eval", "combo_fault_inject_alloc", "combo_krylov_form"]
 
 _lib = None
 
@@ -112,8 +112,8 @@ def load(path: str = LIB_PATH):
     L.combo_apply_G_noalloc.restype = C.c_int
     L.combo_autotune_enable.argtypes = [i32]
     L.combo_autotune_enable.restype = None
-    L.combo_krylov_displacement_form.argtypes = [i32]
-    L.combo_krylov_displacement_form.restype = None
+    L.combo_krylov_form.argtypes = [i32]
+    L.combo_krylov_form.restype = C.c_int
     L.combo_autotune_force.argtypes = [i32, i32]
     L.combo_autotune_force.restype = C.c_int
     L.combo_autotune_report.argtypes = [C.c_char_p, i64]
@@ -342,10 +342,14 @@ def autotune_enable(enable: bool = True):
     load().combo_autotune_enable(1 if enable else 0)
 
 
-def krylov_displacement_form(enable: bool = True):
-    """Use (default) or not the displacement form of the rotated operator in
-    the FP32 Krylov passes of solves set up afterwards."""
-    load().combo_krylov_displacement_form(1 if enable else 0)
+KRYLOV_NINE, KRYLOV_DISPLACEMENT, KRYLOV_NODAL = 0, 1, 2
+
+
+def krylov_form(form: int = KRYLOV_NODAL):
+    """Most reduced evaluation form of the rotated operator that the FP32
+    Krylov passes of solves set up afterwards may use (nine-component,
+    displacement, nodal)."""
+    _check(load().combo_krylov_form(int(form)))
 
 
 def autotune_force(pass_index: int, candidate: int):

@@ -575,6 +575,44 @@ struct DispArgs {
     int cg_max, cg_fixed;
     uint32_t wait_cap;
 };
+// Nodal form of the rotated operator in the FP32 CG (xnodal.cu): G = D (D^T
+// D)^+ D^T with D the HEX8R gradient.  The tangent pass assembles the nodal
+// forces f_i = D^T (A : p)_i of the direction in real space (three fields
+// instead of nine components) and transforms them along x into components
+// 0, 3, 6 of the spectrum; the y-passes take those three; the z-pass divides
+// by |kr|^2 (D^T D's symbol) between its transforms; the x side is that of
+// the displacement form.  The direction p alternates between two buffers
+// (p of CG iteration k in p[k & 1]): a block reads its neighbours' old p.
+struct NodalArgs {
+    GridDims g;
+    const cx<float>* tw;   // exp(-2 pi i t / M)
+    const cx<float>* tw2;  // exp(-2 pi i k / n1)
+    cx<float>* spec;
+    const uint8_t* phase;
+    const float* r;
+    float* p[2];           // p of iteration k in p[k & 1]
+    float* x;              // receives the previous iteration's x += alpha p
+    const float* tc;       // [10][V] tangent cache (F^{-1}, mu - lam ln J)
+    const double* matp;    // [nprob][4] per problem, or null: mu, lam
+    double mu[2], lam[2];
+    const float* bA;       // [45][nb] packed boxel tangents, boxels in voxel order
+    const int32_t* bvox;
+    const int32_t* lofs;
+    int64_t nb;
+    float cJ[3];           // 1 / (4 h_J)
+    int zc;                // z planes per work item (set by the launcher)
+    double* partial;       // pAp partials
+    Scalars* sc;
+    int fuse;              // the last block turns the pAp partials into alpha
+};
+bool nodal_ok(const GridDims& g);  // sizes the nodal tangent pass takes
+void launch_xfwd_nodal(NodalArgs a, cudaStream_t st);
+int nodal_partials_max();  // largest grid of the nodal tangent pass
+// z-pass of the nodal form: one component per tile (components 0, 3, 6),
+// forward z FFT, scale / |kr|^2, inverse z FFT (tmap_u: one-component box)
+void launch_zpass_scalar(const ZArgs<float>& a, cudaStream_t st);
+bool zpass_scalar_encode(void* map, const GridDims& g, const void* spec);  // its map (box {16 or 8, 1, n3, 1})
+
 bool disp_x_ok(const GridDims& g);  // sizes the two x kernels take
 void launch_xinv_disp(const DispArgs& a, cudaStream_t st);
 void launch_disp_grad_cg(const DispArgs& a, cudaStream_t st);

@@ -324,12 +324,13 @@ enum KClass {
     K_DFMG_GATHER,
     K_DFMG_CG,
     K_DISP_GRAD,
+    K_XFWD_NODAL,
     K_NCLASS
 };
 static const char* kclass_name[K_NCLASS] = {"boxel_laminate", "xfwd_resid_fp64", "yfwd_fp64", "zgamma_fp64",
                                              "yinv_fp64", "xinv_fp64", "xfwd_tangent", "yfwd_krylov",
                                              "zgamma_krylov", "yinv_krylov", "xinv_cg", "finalize", "update_F",
-                                             "dfmg_pure", "dfmg_gather", "dfmg_cg_tangent", "grad_cg"};
+                                             "dfmg_pure", "dfmg_gather", "dfmg_cg_tangent", "grad_cg", "xfwd_nodal"};
 
 struct Profiler {
     bool on = false;
@@ -456,6 +457,11 @@ template <typename T> struct Engine {
     CUtensorMap zumap[2];
     bool zumap_ok[2] = {false, false};
     int use_disp = 0;
+    // nodal form (the tangent pass assembles nodal forces): the scalar
+    // z-pass's map and the switch (set per solve)
+    CUtensorMap zsmap;
+    bool zsmap_ok = false;
+    int use_nodal = 0;
     // launch-shape candidates chosen by the autotuner: x-forward, y, z, x-inverse
     int cfg_xf = 0, cfg_y = 0, cfg_z = 0, cfg_xi = 0;
     uint32_t wait_cap = 0;  // poll cap of the bulk-copy waits (wait_cap_of; 0 = default)
@@ -467,6 +473,7 @@ template <typename T> struct Engine {
             ymap_ok[c] = (sizeof(T) == 4) && ypass_tma_encode(&ymap[c], g, s, c);
             zumap_ok[c] = (sizeof(T) == 4) && tab.rph[0] && zpass_tma_encode_u(&zumap[c], g, s, c);
         }
+        zsmap_ok = (sizeof(T) == 4) && tab.rph[0] && zpass_scalar_encode(&zsmap, g, s);
         if (!zmap_ok[cfg_z]) cfg_z = 0;
         if (!ymap_ok[cfg_y]) cfg_y = 0;
     }
@@ -491,6 +498,8 @@ template <typename T> struct Engine {
     // the nodal fields of the displacement form: components 1, 4, 7 of the
     // FP32 spectrum (free once the z-pass has read them), V floats each
     float* disp_u() const { return reinterpret_cast<float*>(spec + g.Vs); }
+    // the nodal form applies on top: its tangent pass and scalar z-pass
+    bool nodal_capable() const { return disp_capable() && zsmap_ok && nodal_ok(g); }
     int64_t disp_ustride() const { return 3 * 2 * g.Vs; }
 
     template <typename Tc> XfwdArgs<T, Tc> xf() const
@@ -554,7 +563,10 @@ template <typename T> struct Engine {
         z.cfg = cfg_z;
         z.tmap = zmap_ok[cfg_z] ? &zmap[cfg_z] : nullptr;
         z.wait_cap = wait_cap;
-        if (use_disp && guard == 1 && !want_norm && z.tmap && zumap_ok[cfg_z]) {
+        if (use_nodal && guard == 1 && !want_norm && zsmap_ok) {
+            z.disp = 2;  // nodal form: scalar z-pass on components 0, 3, 6
+            z.tmap_u = &zsmap;
+        } else if (use_disp && guard == 1 && !want_norm && z.tmap && zumap_ok[cfg_z]) {
             z.disp = 1;
             z.tmap_u = &zumap[cfg_z];
             for (int j = 0; j < 3; j++) z.rph[j] = tab.rph[j];
@@ -565,16 +577,24 @@ template <typename T> struct Engine {
     void yz(Scalars* sc, int guard, bool want_norm, double* partial, cudaStream_t st, Profiler* pr = nullptr,
             int kbase = 0) const
     {
-        const YArgs<T> y = yargs(sc, guard);
+        const ZArgs<T> z = zargs(sc, guard, want_norm, partial);
+        YArgs<T> y = yargs(sc, guard);
+        y.disp = (z.disp == 2) ? 1 : 0;  // the nodal form's forward spectrum: components 0, 3, 6
         if (pr) pr->begin(kbase);
         launch_ypass<T, false>(y, st);
         if (pr) pr->end();
-        const ZArgs<T> z = zargs(sc, guard, want_norm, partial);
         if (pr) pr->begin(kbase + 1);
-        launch_zpass<T>(z, st);
+        if constexpr (sizeof(T) == 4) {
+            if (z.disp == 2)
+                launch_zpass_scalar(z, st);
+            else
+                launch_zpass<T>(z, st);
+        } else {
+            launch_zpass<T>(z, st);
+        }
         if (pr) pr->end();
         YArgs<T> yi = y;
-        yi.disp = z.disp;  // the displacement form leaves components 0, 3, 6 only
+        yi.disp = z.disp ? 1 : 0;  // the displacement and nodal forms leave components 0, 3, 6 only
         if (pr) pr->begin(kbase + 2);
         launch_ypass<T, true>(yi, st);
         if (pr) pr->end();
@@ -687,9 +707,12 @@ __global__ void k_fin_rhs(Scalars* scs, const double* part_all, int n, int cg_fi
 // Stacked problems: dv[b] per problem of Vp voxels (0: F of that problem is
 // left unchanged), the pending alpha and the admissibility flag per problem.
 template <typename Tc>
-__global__ void k_update_F(double* __restrict__ F, const Tc* __restrict__ x, const Tc* __restrict__ p, double d0,
-                           int64_t V, Scalars* scs, const double* dv, int64_t Vp)
+__global__ void k_update_F(double* __restrict__ F, const Tc* __restrict__ x, const Tc* __restrict__ p,
+                           const Tc* __restrict__ p_odd, double d0, int64_t V, Scalars* scs, const double* dv,
+                           int64_t Vp)
 {
+    // p_odd (nodal form): the direction of odd CG iterations; the owed update
+    // is that of the last iteration, cg_iter - 1
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = dv ? v / Vp : 0;
         const double d = dv ? dv[b] : d0;
@@ -705,8 +728,9 @@ __global__ void k_update_F(double* __restrict__ F, const Tc* __restrict__ x, con
             xv[c] = x[c * V + v];
         }
         if (ap != (Tc)0) {
+            const Tc* pl = (p_odd && ((sc->cg_iter - 1) & 1)) ? p_odd : p;
 #pragma unroll
-            for (int c = 0; c < 9; c++) xv[c] += ap * p[c * V + v];
+            for (int c = 0; c < 9; c++) xv[c] += ap * pl[c * V + v];
         }
 #pragma unroll
         for (int c = 0; c < 9; c++) {
@@ -1050,9 +1074,9 @@ struct TuneRec {
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneRec> g_tune;
 static std::atomic<int> g_tune_enabled{1};
-// displacement form of the rotated operator in the FP32 Krylov passes (on by
-// default wherever it applies; read when a solve is set up)
-static std::atomic<int> g_disp_enabled{1};
+// most reduced form of the rotated Krylov operator a solve set up from now on
+// may use (COMBO_KRYLOV_NINE / _DISPLACEMENT / _NODAL), where it applies
+static std::atomic<int> g_krylov_form{COMBO_KRYLOV_NODAL};
 static std::atomic<int> g_tune_force[4] = {{-1}, {-1}, {-1}, {-1}};  // per pass: forced candidate or -1
 
 static void tune_store(const TuneKey& k, const TuneRec& r)
@@ -1124,6 +1148,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     double* d_F = nullptr;
     void* d_spec = nullptr;
     Tc *d_tc = nullptr, *d_x = nullptr, *d_r = nullptr, *d_p = nullptr;
+    Tc* d_p2 = nullptr;  // nodal form: p of odd CG iterations
     double* d_part = nullptr;
     Scalars* d_sc = nullptr;  // [B]
     double* d_phpart = nullptr;  // [PHASE_GRID][PHASE_SUMS] phase-average partials
@@ -1188,6 +1213,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         cudaFree(d_x);
         cudaFree(d_r);
         cudaFree(d_p);
+        cudaFree(d_p2);
         cudaFree(d_part);
         if (!ext_sc) cudaFree(d_sc);
         cudaFree(d_phpart);
@@ -1266,6 +1292,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         int nbuf = std::max(std::max(e64.xpartials(), e64.zblocks()), std::max(ec.xpartials(), ec.zblocks()));
         if (dfmg()) nbuf = std::max(nbuf, dfmg_cg_blocks(V));
         nbuf = std::max(nbuf, disp_grad_partials_max() + g.nprob);  // the displacement form's gradient pass
+        nbuf = std::max(nbuf, nodal_partials_max() + g.nprob);      // the nodal form's tangent pass
         CK(dev_malloc(&d_part, 8 * (size_t)nbuf));
         if (ext_sc)
             d_sc = ext_sc;
@@ -1323,6 +1350,10 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         }
         e64.bind_spec(d_spec);
         ec.bind_spec(d_spec);
+        // the nodal form's second direction buffer, where that form may apply
+        if (newton() && !dfmg() && (!member || own_launches) && g_krylov_form.load() >= COMBO_KRYLOV_NODAL &&
+            ec.zsmap_ok && nodal_ok(g))
+            CK(dev_malloc(&d_p2, sizeof(Tc) * 9 * V));
         CK(cudaMemcpyAsync(d_phase, hp.phase.data(), V, cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(d_v2b, 0xff, 4 * V, st));
         if (nb > 0) {
@@ -1367,7 +1398,9 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         if (newton() && (!member || own_launches)) {
             if ((rc = autotune())) return rc;
             tune_force(ec);
-            ec.use_disp = (g_disp_enabled.load() && ec.disp_capable()) ? 1 : 0;
+            const int form = g_krylov_form.load();
+            ec.use_disp = (form >= COMBO_KRYLOV_DISPLACEMENT && ec.disp_capable()) ? 1 : 0;
+            ec.use_nodal = (form >= COMBO_KRYLOV_NODAL && ec.use_disp && d_p2 && ec.nodal_capable()) ? 1 : 0;
         }
         return COMBO_OK;
     }
@@ -1697,6 +1730,15 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         xi.cg_fixed = opt.cg_fixed_iterations;
         return xi;
     }
+    // the nodal form's direction of odd CG iterations (else null)
+    const Tc* p_odd() const { return ec.use_nodal ? d_p2 : nullptr; }
+    // 1 / (4 h_J), the HEX8R gradient's edge weights
+    void edge_weights(float cJ[3]) const
+    {
+        const int n[3] = {g.n1, g.n2, g.n3p};
+        for (int j = 0; j < 3; j++) cJ[j] = (float)(n[j] / (4.0 * hp.l[j]));
+    }
+
     // the x side of the Krylov operator with the CG update: the CG x-inverse,
     // or, in the displacement form, the x-inverse of the three nodal fields
     // and their gradient with the update
@@ -1712,8 +1754,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                 d.u = ec.disp_u();
                 d.ustride = ec.disp_ustride();
                 d.r = d_r;
-                const int n[3] = {g.n1, g.n2, g.n3p};
-                for (int j = 0; j < 3; j++) d.cJ[j] = (float)(n[j] / (4.0 * hp.l[j]));  // 1 / (4 h_J)
+                edge_weights(d.cJ);
                 d.partial = d_part;
                 d.sc = d_sc;
                 d.fuse = 1;
@@ -1742,6 +1783,40 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         if (dfmg()) {
             dfmg_cg_iteration();
             return;
+        }
+        if constexpr (std::is_same<Tc, float>::value) {
+            if (ec.use_nodal) {
+                NodalArgs n{};
+                n.g = g;
+                n.tw = ec.tab.twM;
+                n.tw2 = ec.tab.tw2;
+                n.spec = ec.spec;
+                n.phase = d_phase;
+                n.r = d_r;
+                n.p[0] = d_p;
+                n.p[1] = d_p2;
+                n.x = d_x;
+                n.tc = d_tc;
+                n.matp = d_mat;
+                for (int i = 0; i < 2; i++) {
+                    n.mu[i] = hp.mu[i];
+                    n.lam[i] = hp.lam[i];
+                }
+                n.bA = d_bA;
+                n.bvox = d_bvox;
+                n.lofs = d_lofs;
+                n.nb = std::max<int64_t>(nb, 1);
+                edge_weights(n.cJ);
+                n.partial = d_part;
+                n.sc = d_sc;
+                n.fuse = 1;
+                prof.begin(K_XFWD_NODAL);
+                launch_xfwd_nodal(n, st);
+                prof.end();
+                ec.yz(d_sc, 1, false, nullptr, st, &prof, K_YFWD_C);
+                krylov_xinv();
+                return;
+            }
         }
         const auto xf = cg_xf();
         prof.begin(K_XFWD_TANGENT);
@@ -1996,7 +2071,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                     for (int h = 0; h <= 10; h++) {
                         if ((rc = set_flag(offsetof(Scalars, admissible), 1))) return error = rc;
                         prof.begin(K_UPDATE);
-                        k_update_F<Tc><<<grid_for(g.V), 256, 0, st>>>(d_F, d_x, d_p, d, g.V, d_sc, nullptr, g.V);
+                        k_update_F<Tc><<<grid_for(g.V), 256, 0, st>>>(d_F, d_x, d_p, p_odd(), d, g.V, d_sc, nullptr, g.V);
                         prof.end();
                         if ((rc = read_scalars(s))) return error = rc;
                         if (s.admissible || linear()) {  // (det F is not constrained on small strains)
@@ -2171,7 +2246,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                         if ((rc = set_flag_of(b, offsetof(Scalars, admissible), 1))) return error = rc;
                     CK(cudaMemcpyAsync(d_dv, dv.data(), 8 * B, cudaMemcpyHostToDevice, st));
                     prof.begin(K_UPDATE);
-                    k_update_F<Tc><<<grid_for(g.V), 256, 0, st>>>(d_F, d_x, d_p, 0.0, g.V, d_sc, d_dv, Vp);
+                    k_update_F<Tc><<<grid_for(g.V), 256, 0, st>>>(d_F, d_x, d_p, p_odd(), 0.0, g.V, d_sc, d_dv, Vp);
                     prof.end();
                     if ((rc = read_all())) return error = rc;
                     bool bad = false;
@@ -2973,7 +3048,7 @@ template <typename Tc, typename Rt> struct MixSolve : SolveBase {
                         Cls& q = *cls[k];
                         CK(cudaMemcpyAsync(q.d_dv, dv[k].data(), 8 * q.B, cudaMemcpyHostToDevice, st));
                         prof.begin(K_UPDATE);
-                        k_update_F<Tc><<<grid_for(q.g.V), 256, 0, st>>>(q.d_F, q.d_x, q.d_p, 0.0, q.g.V, q.d_sc, q.d_dv,
+                        k_update_F<Tc><<<grid_for(q.g.V), 256, 0, st>>>(q.d_F, q.d_x, q.d_p, q.p_odd(), 0.0, q.g.V, q.d_sc, q.d_dv,
                                                                         q.Vp);
                         prof.end();
                     }
@@ -3076,6 +3151,7 @@ extern "C" int64_t combo_solve_footprint(const combo_problem* p, const combo_opt
     const int64_t tc = (o->precision == COMBO_FP64) ? 8 : 4;
     int64_t b = V * (1 + 4 + 72) + 16 * 9 * g.Vs + nb * (4 + 24 + 8 + 24 + 72);
     if (o->solver == COMBO_NEWTON_CG) b += tc * (81 * nb + 37 * V);
+    if (o->solver == COMBO_NEWTON_CG && tc == 4 && o->kspace == COMBO_ROTATED) b += 36 * V;  // nodal form's p
     if (o->solver == COMBO_NONLINEAR_CG) b += 72 * V;
     if (o->kspace == COMBO_STAGGERED_DFMG) b += 8 * 81 * V + 192 * nb;
     return b;
@@ -3199,7 +3275,13 @@ extern "C" int combo_solve(combo_ctx* ctx, const combo_problem* p, const combo_o
 
 extern "C" void combo_autotune_enable(int32_t enable) { g_tune_enabled.store(enable ? 1 : 0); }
 
-extern "C" void combo_krylov_displacement_form(int32_t enable) { g_disp_enabled.store(enable ? 1 : 0); }
+extern "C" int combo_krylov_form(int32_t form)
+{
+    if (form < COMBO_KRYLOV_NINE || form > COMBO_KRYLOV_NODAL)
+        return fail(COMBO_E_INVALID_ARG, "Krylov operator form outside 0..2");
+    g_krylov_form.store(form);
+    return COMBO_OK;
+}
 
 extern "C" int combo_autotune_force(int32_t pass, int32_t cand)
 {
@@ -3642,6 +3724,7 @@ int64_t footprint_of(const HostProblem& h, const combo_options& o)
     const int64_t tc = (o.precision == COMBO_FP64) ? 8 : 4;
     int64_t b = V * (1 + 4 + 72) + 16 * 9 * g.Vs + nb * (4 + 24 + 8 + 24 + 72) + (1 << 20);
     if (o.solver == COMBO_NEWTON_CG) b += tc * (45 * nb + 37 * V) + 8 * nb + 4 * ((int64_t)g.n2 * g.n3 + 1);
+    if (o.solver == COMBO_NEWTON_CG && tc == 4 && o.kspace == COMBO_ROTATED) b += 36 * V;  // nodal form's p
     if (o.solver == COMBO_NONLINEAR_CG) b += 72 * V;
     if (o.kspace == COMBO_STAGGERED_DFMG) b += 8 * 81 * V + 192 * nb;
     return b;

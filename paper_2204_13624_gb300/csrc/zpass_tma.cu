@@ -509,4 +509,164 @@ void launch_zpass_tma(const ZArgs<float>& a, const void* map, cudaStream_t st)
     }
 }
 
+// ------------------------------------------------------------- scalar z-pass
+// The nodal form's z-pass: a tile is one of the components 0, 3, 6 (the
+// nodal forces f_i), all N z-planes, one y and TX x-frequencies (box {TX, 1,
+// N, 1}); forward z FFT, multiplication by scale / |kr|^2 (zero where |kr| is
+// zero), inverse z FFT, in place, then one TMA store.
+__host__ __device__ constexpr int tma_txs(int n) { return n > 256 ? 8 : 16; }
+
+bool zpass_scalar_encode(void* map, const GridDims& g, const void* spec)
+{
+    if (!zpass_tma_size(g.n3p) || !spec) return false;
+    if ((g.nhp * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(spec) & 15) != 0) return false;
+    const cuuint32_t box[4] = {(cuuint32_t)tma_txs(g.n3p), 1, (cuuint32_t)g.n3p, 1};
+    return encode_spec_map(map, g, spec, box, g.n3p > 256 ? 2 : -1);
+}
+
+template <int N, int TX>
+__global__ void __launch_bounds__(TX * FastPlan<N>::TPL)
+    k_zpass_scalar(const __grid_constant__ CUtensorMap tm, ZArgs<float> a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    constexpr int TILE = N * TX;
+    constexpr uint32_t TILE_BYTES = TILE * 8;
+    typedef cx<float> C;
+    C* tiles = reinterpret_cast<C*>(smem_raw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * TILE_BYTES);
+    C* tws = reinterpret_cast<C*>(bar + 2);
+    const GridDims g = a.g;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = a.tw[i];
+    const int line = threadIdx.x % TX, tau = threadIdx.x / TX;
+    const int nxt = (g.nh + TX - 1) / TX;
+    const int tpp = nxt * g.n2 * 3;  // tiles per problem
+    const int ntiles = tpp * g.nprob;
+    auto done_of = [&](const Scalars* q) { return (a.guard == 1 && q->cg_done) || (a.guard == 2 && q->outer_done); };
+    const bool done0 = done_of(a.sc);
+    auto active = [&](int t) { return g.nprob == 1 ? !done0 : !done_of(a.sc + t / tpp); };
+    auto next_tile = [&](int t) {
+        while (t < ntiles && !active(t)) t += gridDim.x;
+        return t;
+    };
+    // tile t = ((b * 3 + row) * n2 + y) * nxt + xt
+    auto issue = [&](int t, int s) {
+        const int xt = t % nxt, rest = t / nxt;
+        const int y = rest % g.n2, rb = rest / g.n2;
+        const int b = rb / 3, row = rb - 3 * b;
+        mbar_arrive_expect_tx(&bar[s], TILE_BYTES);
+        if constexpr (N > 256)
+            tma_load_5d(tiles + s * TILE, &tm, xt * TX, y, 0, b * (N / 256), 3 * row, &bar[s]);
+        else
+            tma_load_4d(tiles + s * TILE, &tm, xt * TX, y, b * N, 3 * row, &bar[s]);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_proxy_async();
+    }
+    __syncthreads();
+    const int t0 = next_tile(blockIdx.x);
+    if (threadIdx.x == 0 && t0 < ntiles) issue(t0, 0);
+
+    int it = 0, tn = ntiles;
+    bool timed_out = false;
+    for (int t = t0; t < ntiles; t = tn, it++) {
+        const int s = it & 1;
+        tn = next_tile(t + gridDim.x);
+        if (threadIdx.x == 0 && tn < ntiles) {
+            bulk_wait_read_all();  // the store of the previous tile has left buffer s ^ 1
+            issue(tn, s ^ 1);
+        }
+        const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1), wait_cap_of(a.wait_cap));
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        const int xt = t % nxt, rest = t / nxt;
+        const int y = rest % g.n2, rb = rest / g.n2;
+        const int pb = rb / 3, row = rb - 3 * pb;
+        const int x0 = xt * TX;
+        C* park = tiles + s * TILE;
+        C* pc = park + line;
+        auto lp = [&](int e) { return pc[e * TX]; };
+        auto sp = [&](int e, C v) { pc[e * TX] = v; };
+        fft_fast<float, N, false, true, true>(lp, sp, lp, sp, tau, tws);
+        __syncthreads();
+        const float ay = a.sa[1][y], by = a.sb[1][y];
+        for (int f = threadIdx.x; f < N * TX; f += blockDim.x) {
+            const int z = f / TX, ln = f - z * TX;
+            const int xi1 = x0 + ln;
+            float w = 0.f;
+            if (xi1 < g.nh) {
+                const float ax = a.sa[0][xi1], bx = a.sb[0][xi1];
+                const float az = a.sa[2][z], bz = a.sb[2][z];
+                const float k0 = ax * by * bz, k1 = ay * bx * bz, k2 = az * bx * by;
+                const float kk = k0 * k0 + k1 * k1 + k2 * k2;
+                if (kk > 0.f) w = a.scale / kk;
+            }
+            park[f] = c_scale(park[f], w);
+        }
+        __syncthreads();
+        fft_fast<float, N, true, true, true>(lp, sp, lp, sp, tau, tws);
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if constexpr (N > 256)
+                tma_store_5d(&tm, x0, y, 0, pb * (N / 256), 3 * row, park);
+            else
+                tma_store_4d(&tm, x0, y, pb * N, 3 * row, park);
+            bulk_commit();
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (timed_out) {
+            raise_status(a.sc, COMBO_E_TIMEOUT);
+            const int s = it & 1;
+            mbar_wait_bounded(&bar[s], (uint32_t)((it >> 1) & 1));
+            if (tn < ntiles) mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+        }
+        bulk_wait_all();
+    }
+}
+
+template <int N> static void zpass_scalar_launch(const ZArgs<float>& a, cudaStream_t st)
+{
+    constexpr int TX = tma_txs(N);
+    constexpr int threads = TX * FastPlan<N>::TPL;
+    const size_t sm = (size_t)2 * N * TX * 8 + 16 + (size_t)N * 8;
+    static int grid_per_sm = 0;
+    static int nsm = 0;
+    if (grid_per_sm == 0) {
+        cudaFuncSetAttribute(k_zpass_scalar<N, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zpass_scalar<N, TX>, threads, sm) != cudaSuccess ||
+            per < 1)
+            per = 1;
+        grid_per_sm = per;
+    }
+    const int ntiles = ((a.g.nh + TX - 1) / TX) * a.g.n2 * 3 * a.g.nprob;
+    const int grid = std::min(ntiles, grid_per_sm * nsm);
+    k_zpass_scalar<N, TX><<<grid, threads, sm, st>>>(*reinterpret_cast<const CUtensorMap*>(a.tmap_u), a);
+}
+
+void launch_zpass_scalar(const ZArgs<float>& a, cudaStream_t st)
+{
+    switch (a.g.n3p) {
+        case 48: zpass_scalar_launch<48>(a, st); break;
+        case 64: zpass_scalar_launch<64>(a, st); break;
+        case 72: zpass_scalar_launch<72>(a, st); break;
+        case 96: zpass_scalar_launch<96>(a, st); break;
+        case 108: zpass_scalar_launch<108>(a, st); break;
+        case 128: zpass_scalar_launch<128>(a, st); break;
+        case 144: zpass_scalar_launch<144>(a, st); break;
+        case 192: zpass_scalar_launch<192>(a, st); break;
+        case 216: zpass_scalar_launch<216>(a, st); break;
+        case 256: zpass_scalar_launch<256>(a, st); break;
+        default: zpass_scalar_launch<512>(a, st); break;
+    }
+}
+
 }  // namespace combo
