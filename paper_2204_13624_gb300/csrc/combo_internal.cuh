@@ -601,6 +601,7 @@ struct NodalArgs {
     int64_t nb;
     float cJ[3];           // 1 / (4 h_J)
     int zc;                // z planes per work item (set by the launcher)
+    int cfg;               // launch-shape candidate (0: 3 blocks per SM, 1: 2)
     double* partial;       // pAp partials
     Scalars* sc;
     int fuse;              // the last block turns the pAp partials into alpha

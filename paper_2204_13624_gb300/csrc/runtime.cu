@@ -1810,6 +1810,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                 n.partial = d_part;
                 n.sc = d_sc;
                 n.fuse = 1;
+                n.cfg = ec.cfg_xf;
                 prof.begin(K_XFWD_NODAL);
                 launch_xfwd_nodal(n, st);
                 prof.end();

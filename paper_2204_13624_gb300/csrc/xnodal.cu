@@ -50,7 +50,9 @@ int num_sms_nodal()
 
 // threads per block (one or two voxels of a line per thread) and blocks per SM
 template <int M> __host__ __device__ constexpr int nodal_threads() { return M == 64 ? 128 : 256; }
-template <int M> __host__ __device__ constexpr int nodal_minb() { return M == 256 ? 2 : 3; }
+// blocks per SM the registers are capped for: candidate 0 (M = 128: 3, at
+// about 80 registers) or 1 (2, no cap below 128 registers)
+template <int M, int C> __host__ __device__ constexpr int nodal_minb() { return (M == 256 || C == 1) ? 2 : 3; }
 // threads that transform the 3 TY nodal lines of a plane (named barrier 1)
 template <int M, int TY> __host__ __device__ constexpr int nodal_fft_threads()
 {
@@ -75,8 +77,8 @@ bool nodal_ok(const GridDims& g)
 
 int nodal_partials_max() { return 3 * num_sms_nodal(); }  // per_sm is capped at 3
 
-template <int M, int TY>
-__global__ void __launch_bounds__(nodal_threads<M>(), nodal_minb<M>()) k_xfwd_nodal(NodalArgs a)
+template <int M, int TY, int C>
+__global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xfwd_nodal(NodalArgs a)
 {
     constexpr int n1 = 2 * M;
     constexpr int NT = nodal_threads<M>();
@@ -139,6 +141,42 @@ __global__ void __launch_bounds__(nodal_threads<M>(), nodal_minb<M>()) k_xfwd_no
                 const bool own = zown && yy >= 0;
                 const int64_t L = zrow + yl;
                 float* LB = lbuf + (s & 1) * 9 * n1;
+                {
+                    // the operand rows and boxel tangents of the voxel line two
+                    // steps ahead (within this item) into L2: each step waits on
+                    // its loads, so they should find L2 rather than DRAM
+                    int ya = yy + 2, za = zv;
+                    if (ya >= TY) {
+                        ya -= TY + 1;
+                        za++;
+                    }
+                    if (za < z1) {
+                        const int zla = za < 0 ? za + g.n3p : za;
+                        const int yla = (y0 + ya < 0) ? y0 + ya + g.n2 : y0 + ya;
+                        const int64_t La = (int64_t)(pb * g.n3p + zla) * g.n2 + yla;
+                        const bool owna = za >= z0 && ya >= 0;
+                        constexpr int CH = n1 * 4 / 128;  // 128-byte chunks per row
+                        const int nrow = 19 + (first ? 0 : 9) + ((owna && apend != 0.f) ? 9 : 0);
+                        for (int e = tid; e < nrow * CH; e += NT) {
+                            const int row = e / CH, q = e - row * CH;
+                            const float* base = row < 9 ? rg + (int64_t)row * V
+                                                : row < 19 ? tg + (int64_t)(row - 9) * V
+                                                : (!first && row < 28) ? pin + (int64_t)(row - 19) * V
+                                                : xg + (int64_t)(row - (first ? 19 : 28)) * V;
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(base + La * n1 + q * 32));
+                        }
+                        const int b0 = a.lofs[La], b1 = a.lofs[La + 1];
+                        if (b1 > b0) {
+                            const int nch = (b1 - b0 + 31) / 32 + 1;  // 128-byte chunks a row segment may touch
+                            for (int e = tid; e < 45 * nch; e += NT) {
+                                const int j = e / nch, q = e - j * nch;
+                                const float* pa = a.bA + (int64_t)j * a.nb + b0 + 32 * q;
+                                if (pa < a.bA + (int64_t)j * a.nb + b1)
+                                    asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+                            }
+                        }
+                    }
+                }
                 // (1) voxels of the line
 #pragma unroll
                 for (int v = 0; v < VPT; v++) {
@@ -299,14 +337,15 @@ __global__ void __launch_bounds__(nodal_threads<M>(), nodal_minb<M>()) k_xfwd_no
 }
 
 // ------------------------------------------------------------- launcher
-template <int M, int TY> static void xfwd_nodal_launch(NodalArgs a, cudaStream_t st)
+template <int M, int TY, int C> static void xfwd_nodal_launch(NodalArgs a, cudaStream_t st)
 {
     constexpr int threads = nodal_threads<M>();
     constexpr size_t sm = nodal_smem<M, TY>();
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaFuncSetAttribute(k_xfwd_nodal<M, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xfwd_nodal<M, TY>, threads, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_xfwd_nodal<M, TY, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xfwd_nodal<M, TY, C>, threads, sm) !=
+                cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
         per_sm = std::min(per_sm, 3);
@@ -320,21 +359,29 @@ template <int M, int TY> static void xfwd_nodal_launch(NodalArgs a, cudaStream_t
     a.zc = (g.n3p + chunks - 1) / chunks;
     const int items = ncol * ((g.n3p + a.zc - 1) / a.zc);
     const int gp = std::max(1, std::min(items, std::max(1, slots / g.nprob)));
-    k_xfwd_nodal<M, TY><<<g.nprob * gp, threads, sm, st>>>(a);
+    k_xfwd_nodal<M, TY, C><<<g.nprob * gp, threads, sm, st>>>(a);
+}
+
+template <int C> static void xfwd_nodal_pick(const NodalArgs& a, cudaStream_t st)
+{
+    switch (a.g.M) {
+        case 64: xfwd_nodal_launch<64, 4, C>(a, st); break;
+        case 128:
+            if (a.g.n2 % 8 == 0)
+                xfwd_nodal_launch<128, 8, C>(a, st);
+            else
+                xfwd_nodal_launch<128, 4, C>(a, st);
+            break;
+        default: xfwd_nodal_launch<256, 4, C>(a, st); break;
+    }
 }
 
 void launch_xfwd_nodal(NodalArgs a, cudaStream_t st)
 {
-    switch (a.g.M) {
-        case 64: xfwd_nodal_launch<64, 4>(a, st); break;
-        case 128:
-            if (a.g.n2 % 8 == 0)
-                xfwd_nodal_launch<128, 8>(a, st);
-            else
-                xfwd_nodal_launch<128, 4>(a, st);
-            break;
-        default: xfwd_nodal_launch<256, 4>(a, st); break;
-    }
+    if (a.cfg == 1)
+        xfwd_nodal_pick<1>(a, st);
+    else
+        xfwd_nodal_pick<0>(a, st);
 }
 
 }  // namespace combo
