@@ -1062,9 +1062,10 @@ static int check_options(combo_options& o)
 // ------------------------------------------------------------------ autotuner store
 struct TuneKey {
     int word, n1, n2, n3p, nprob;
+    int nodal;  // pass 0 is the nodal form's tangent pass
     bool operator<(const TuneKey& o) const
     {
-        return std::tie(word, n1, n2, n3p, nprob) < std::tie(o.word, o.n1, o.n2, o.n3p, o.nprob);
+        return std::tie(word, n1, n2, n3p, nprob, nodal) < std::tie(o.word, o.n1, o.n2, o.n3p, o.nprob, o.nodal);
     }
 };
 struct TuneRec {
@@ -1415,7 +1416,8 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         if constexpr (sizeof(Tc) != 4) {
             return COMBO_OK;  // the candidates are shapes of the FP32 passes
         } else {
-            const TuneKey key{sizeof(Tc), g.n1, g.n2, g.n3p, g.nprob};
+            const int nodal_pass = d_p2 ? 1 : 0;  // the nodal form may run: tune its tangent pass
+            const TuneKey key{sizeof(Tc), g.n1, g.n2, g.n3p, g.nprob, nodal_pass};
             if (tune_lookup(key, ec)) return COMBO_OK;
             if (!g_tune_enabled.load()) return COMBO_OK;
             CK(cudaMemsetAsync(d_r, 0, sizeof(Tc) * 9 * g.V, st));
@@ -1468,8 +1470,19 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             auto xf1 = xf;
             xf.cfg = 0;
             xf1.cfg = 1;
-            time_pair([&] { launch_xfwd<Tc, Tc>(xf, 0, st); }, [&] { launch_xfwd<Tc, Tc>(xf1, 0, st); }, true,
-                      rec.ms[0]);
+            if (nodal_pass) {
+                // (cg_iter is 0 and cg_done 0 here: the first iteration's pass,
+                // which reads no previous direction; no alpha is formed)
+                NodalArgs n0 = nodal_args();
+                n0.fuse = 0;
+                NodalArgs n1 = n0;
+                n0.cfg = 0;
+                n1.cfg = 1;
+                time_pair([&] { launch_xfwd_nodal(n0, st); }, [&] { launch_xfwd_nodal(n1, st); }, true, rec.ms[0]);
+            } else {
+                time_pair([&] { launch_xfwd<Tc, Tc>(xf, 0, st); }, [&] { launch_xfwd<Tc, Tc>(xf1, 0, st); }, true,
+                          rec.ms[0]);
+            }
             // y forward and z (+ projection): tile widths with a valid tensor map
             YArgs<Tc> y0{};
             y0.g = g;
@@ -1730,6 +1743,38 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         xi.cg_fixed = opt.cg_fixed_iterations;
         return xi;
     }
+    // arguments of the nodal form's tangent pass (Tc = float)
+    NodalArgs nodal_args() const
+    {
+        NodalArgs n{};
+        if constexpr (std::is_same<Tc, float>::value) {
+            n.g = g;
+            n.tw = ec.tab.twM;
+            n.tw2 = ec.tab.tw2;
+            n.spec = ec.spec;
+            n.phase = d_phase;
+            n.r = d_r;
+            n.p[0] = d_p;
+            n.p[1] = d_p2;
+            n.x = d_x;
+            n.tc = d_tc;
+            n.matp = d_mat;
+            for (int i = 0; i < 2; i++) {
+                n.mu[i] = hp.mu[i];
+                n.lam[i] = hp.lam[i];
+            }
+            n.bA = d_bA;
+            n.bvox = d_bvox;
+            n.lofs = d_lofs;
+            n.nb = std::max<int64_t>(nb, 1);
+            edge_weights(n.cJ);
+            n.partial = d_part;
+            n.sc = d_sc;
+            n.fuse = 1;
+            n.cfg = ec.cfg_xf;
+        }
+        return n;
+    }
     // the nodal form's direction of odd CG iterations (else null)
     const Tc* p_odd() const { return ec.use_nodal ? d_p2 : nullptr; }
     // 1 / (4 h_J), the HEX8R gradient's edge weights
@@ -1786,31 +1831,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         }
         if constexpr (std::is_same<Tc, float>::value) {
             if (ec.use_nodal) {
-                NodalArgs n{};
-                n.g = g;
-                n.tw = ec.tab.twM;
-                n.tw2 = ec.tab.tw2;
-                n.spec = ec.spec;
-                n.phase = d_phase;
-                n.r = d_r;
-                n.p[0] = d_p;
-                n.p[1] = d_p2;
-                n.x = d_x;
-                n.tc = d_tc;
-                n.matp = d_mat;
-                for (int i = 0; i < 2; i++) {
-                    n.mu[i] = hp.mu[i];
-                    n.lam[i] = hp.lam[i];
-                }
-                n.bA = d_bA;
-                n.bvox = d_bvox;
-                n.lofs = d_lofs;
-                n.nb = std::max<int64_t>(nb, 1);
-                edge_weights(n.cJ);
-                n.partial = d_part;
-                n.sc = d_sc;
-                n.fuse = 1;
-                n.cfg = ec.cfg_xf;
+                const NodalArgs n = nodal_args();
                 prof.begin(K_XFWD_NODAL);
                 launch_xfwd_nodal(n, st);
                 prof.end();
@@ -3299,8 +3320,8 @@ extern "C" int64_t combo_autotune_report(char* buf, int64_t len)
         static const char* pass[4] = {"x-forward", "y", "z", "x-inverse"};
         for (const auto& kv : g_tune) {
             char line[512];
-            int n = snprintf(line, sizeof line, "%dx%dx%d x%d FP%d:", kv.first.n1, kv.first.n2, kv.first.n3p,
-                             kv.first.nprob, kv.first.word * 8);
+            int n = snprintf(line, sizeof line, "%dx%dx%d x%d FP%d%s:", kv.first.n1, kv.first.n2, kv.first.n3p,
+                             kv.first.nprob, kv.first.word * 8, kv.first.nodal ? " nodal" : "");
             for (int k = 0; k < 4; k++)
                 n += snprintf(line + n, sizeof line - n, " %s=%d (%.3f/%.3f ms)", pass[k], kv.second.cfg[k],
                               kv.second.ms[k][0] / 3.0, kv.second.ms[k][1] >= 1e29f ? -1.0 : kv.second.ms[k][1] / 3.0);
