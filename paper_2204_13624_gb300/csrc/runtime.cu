@@ -484,6 +484,15 @@ template <typename T> struct Engine {
         py = make_plan(g.n2);
         pz = make_plan(g.n3p);
         lines = xpass_lines(g, sizeof(cx<T>));
+        if (sizeof(cx<T>) == 16) {
+            // residual transforms (FP64 or double-float words): groups of
+            // lines large enough (>= 1024 voxels) that the FFT phase keeps a
+            // 256-thread block busy; these register-heavy blocks run one or
+            // two per SM anyway, so the larger shared buffers cost no residency
+            while (lines * g.n1 < 1024 && xpass_smem(g, lines * 2, sizeof(cx<T>)) <= 160 * 1024 &&
+                   (g.n2 * g.n3p) % (lines * 2) == 0)
+                lines *= 2;
+        }
         txy = ypass_tx(g.n2, sizeof(cx<T>));
         txz = zpass_tx(g.n3p, sizeof(cx<T>));
         return make_tables<T>(tab, g, l, kspace);
@@ -1471,8 +1480,19 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             xf.cfg = 0;
             xf1.cfg = 1;
             if (nodal_pass) {
-                // (cg_iter is 0 and cg_done 0 here: the first iteration's pass,
-                // which reads no previous direction; no alpha is formed)
+                // timed as a later iteration (cg_iter 1, a nonzero owed alpha):
+                // the previous direction is read and x updated, as in every
+                // iteration but the first; all of them zero, and no alpha is
+                // formed (fuse 0); the scalars are cleared afterwards
+                CK(cudaMemsetAsync(d_p2, 0, sizeof(Tc) * 9 * g.V, st));
+                std::vector<Scalars> hs(B);
+                for (auto& q : hs) {
+                    std::memset(&q, 0, sizeof(Scalars));
+                    q.cg_iter = 1;
+                    q.alpha_pending = 1e-30;
+                }
+                CK(cudaMemcpyAsync(d_sc, hs.data(), sizeof(Scalars) * B, cudaMemcpyHostToDevice, st));
+                CK(cudaStreamSynchronize(st));
                 NodalArgs n0 = nodal_args();
                 n0.fuse = 0;
                 NodalArgs n1 = n0;
