@@ -442,7 +442,8 @@ int64_t combo_autotune_report(char* buf, int64_t len);
  *                              p)_i in real space in the tangent pass (three
  *                              forward transforms, the z-pass divides by
  *                              |kr|^2); the direction p alternates between
- *                              two buffers (36 bytes more per voxel).
+ *                              two buffers (with a voxel map: 40 bytes
+ *                              more per voxel).
  * Each is an evaluation order of the same operator: results agree up to FP32
  * rounding.  The reduced forms apply to single and stacked solves (and the
  * own-launch classes of batches over several grids) with the rotated scheme,

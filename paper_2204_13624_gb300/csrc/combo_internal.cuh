@@ -588,7 +588,7 @@ struct NodalArgs {
     const cx<float>* tw;   // exp(-2 pi i t / M)
     const cx<float>* tw2;  // exp(-2 pi i k / n1)
     cx<float>* spec;
-    const uint8_t* phase;
+    const int32_t* vrank;  // [V] boxel voxels: column of their packed tangent (>= 0); else -1 - phase
     const float* r;
     float* p[2];           // p of iteration k in p[k & 1]
     float* x;              // receives the previous iteration's x += alpha p
@@ -596,8 +596,7 @@ struct NodalArgs {
     const double* matp;    // [nprob][4] per problem, or null: mu, lam
     double mu[2], lam[2];
     const float* bA;       // [45][nb] packed boxel tangents, boxels in voxel order
-    const int32_t* bvox;
-    const int32_t* lofs;
+    const int32_t* lofs;   // [n2 n3 + 1] first boxel (voxel order) of each x-line (L2 prefetch)
     int64_t nb;
     float cJ[3];           // 1 / (4 h_J)
     int zc;                // z planes per work item (set by the launcher)

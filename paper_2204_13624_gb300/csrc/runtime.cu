@@ -642,6 +642,16 @@ __global__ void k_vox2box(int32_t* map, const int32_t* bidx, int64_t nb)
     if (b < nb) map[bidx[b]] = (int32_t)b;
 }
 
+// nodal form's voxel map: a boxel voxel's column of the packed tangents (its
+// rank in voxel order), else -1 - phase
+__global__ void k_vrank(int32_t* vrank, const uint8_t* phase, const int32_t* v2b, const int32_t* rank, int64_t V)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        const int ph = phase[v];
+        vrank[v] = ph == 2 ? rank[v2b[v]] : -1 - ph;
+    }
+}
+
 // deterministic fixed-order sum of n partials by one block
 __device__ double sum_partials(const double* p, int n, double* red) { return sum_partials_fixed(p, n, red); }
 
@@ -1159,6 +1169,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
     void* d_spec = nullptr;
     Tc *d_tc = nullptr, *d_x = nullptr, *d_r = nullptr, *d_p = nullptr;
     Tc* d_p2 = nullptr;  // nodal form: p of odd CG iterations
+    int32_t* d_vrank = nullptr;  // nodal form: packed-tangent column of boxel voxels, else -1 - phase
     double* d_part = nullptr;
     Scalars* d_sc = nullptr;  // [B]
     double* d_phpart = nullptr;  // [PHASE_GRID][PHASE_SUMS] phase-average partials
@@ -1224,6 +1235,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         cudaFree(d_r);
         cudaFree(d_p);
         cudaFree(d_p2);
+        cudaFree(d_vrank);
         cudaFree(d_part);
         if (!ext_sc) cudaFree(d_sc);
         cudaFree(d_phpart);
@@ -1363,7 +1375,10 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         // the nodal form's second direction buffer, where that form may apply
         if (newton() && !dfmg() && (!member || own_launches) && g_krylov_form.load() >= COMBO_KRYLOV_NODAL &&
             ec.zsmap_ok && nodal_ok(g))
+        {
             CK(dev_malloc(&d_p2, sizeof(Tc) * 9 * V));
+            CK(dev_malloc(&d_vrank, 4 * V));
+        }
         CK(cudaMemcpyAsync(d_phase, hp.phase.data(), V, cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(d_v2b, 0xff, 4 * V, st));
         if (nb > 0) {
@@ -1391,6 +1406,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             CK(cudaMemcpyAsync(d_rank, rank.data(), 4 * rank.size(), cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(d_bvox, bvox.data(), 4 * bvox.size(), cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(d_lofs, lofs.data(), 4 * lofs.size(), cudaMemcpyHostToDevice, st));
+            if (d_vrank) k_vrank<<<grid_for(V), 256, 0, st>>>(d_vrank, d_phase, d_v2b, d_rank, V);
             CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
         }
         k_fill_identity<<<grid_for(9 * V), 256, 0, st>>>(d_F, V);
@@ -1772,7 +1788,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             n.tw = ec.tab.twM;
             n.tw2 = ec.tab.tw2;
             n.spec = ec.spec;
-            n.phase = d_phase;
+            n.vrank = d_vrank;
             n.r = d_r;
             n.p[0] = d_p;
             n.p[1] = d_p2;
@@ -1784,7 +1800,6 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                 n.lam[i] = hp.lam[i];
             }
             n.bA = d_bA;
-            n.bvox = d_bvox;
             n.lofs = d_lofs;
             n.nb = std::max<int64_t>(nb, 1);
             edge_weights(n.cJ);
@@ -3193,7 +3208,7 @@ extern "C" int64_t combo_solve_footprint(const combo_problem* p, const combo_opt
     const int64_t tc = (o->precision == COMBO_FP64) ? 8 : 4;
     int64_t b = V * (1 + 4 + 72) + 16 * 9 * g.Vs + nb * (4 + 24 + 8 + 24 + 72);
     if (o->solver == COMBO_NEWTON_CG) b += tc * (81 * nb + 37 * V);
-    if (o->solver == COMBO_NEWTON_CG && tc == 4 && o->kspace == COMBO_ROTATED) b += 36 * V;  // nodal form's p
+    if (o->solver == COMBO_NEWTON_CG && tc == 4 && o->kspace == COMBO_ROTATED) b += 40 * V;  // nodal form's second p and voxel map
     if (o->solver == COMBO_NONLINEAR_CG) b += 72 * V;
     if (o->kspace == COMBO_STAGGERED_DFMG) b += 8 * 81 * V + 192 * nb;
     return b;
@@ -3766,7 +3781,7 @@ int64_t footprint_of(const HostProblem& h, const combo_options& o)
     const int64_t tc = (o.precision == COMBO_FP64) ? 8 : 4;
     int64_t b = V * (1 + 4 + 72) + 16 * 9 * g.Vs + nb * (4 + 24 + 8 + 24 + 72) + (1 << 20);
     if (o.solver == COMBO_NEWTON_CG) b += tc * (45 * nb + 37 * V) + 8 * nb + 4 * ((int64_t)g.n2 * g.n3 + 1);
-    if (o.solver == COMBO_NEWTON_CG && tc == 4 && o.kspace == COMBO_ROTATED) b += 36 * V;  // nodal form's p
+    if (o.solver == COMBO_NEWTON_CG && tc == 4 && o.kspace == COMBO_ROTATED) b += 40 * V;  // nodal form's second p and voxel map
     if (o.solver == COMBO_NONLINEAR_CG) b += 72 * V;
     if (o.kspace == COMBO_STAGGERED_DFMG) b += 8 * 81 * V + 192 * nb;
     return b;

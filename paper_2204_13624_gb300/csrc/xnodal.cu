@@ -18,9 +18,10 @@
 // lines y0 - 1 .. y0 + TY - 1 (the first one, and the plane below its first,
 // are halo: their A : p is formed but neither p, x nor pAp is written).  Per
 // voxel line: (1) the voxels' direction update p = r + beta p_old, the
-// deferred x += alpha_prev p_old and A : p at pure voxels, scaled by c_J into
-// a shared line buffer; (2) the line's boxels replace their entries by the
-// packed boxel tangent applied to p; (3) each thread combines its node's two
+// deferred x += alpha_prev p_old and A : p -- at pure voxels from the tangent
+// cache, at boxels from the packed boxel tangent (its column from the voxel's
+// vrank entry) -- scaled by c_J into a shared line buffer; (2) (one barrier
+// later) each thread combines its node's two
 // x-neighbours (e = A(x-1) - A(x), f = B(x-1) + B(x), q = C(x-1) + C(x), with
 // A, B, C the c_J-scaled columns J = 0, 1, 2 of row i), then the two voxel
 // lines along y (P = e' + e + f' - f, Q = q' + q), and the two voxel planes
@@ -116,7 +117,6 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
     const float* __restrict__ rg = a.r;
     float* __restrict__ xg = a.x;
     const float* __restrict__ tg = a.tc;
-    const uint8_t* __restrict__ phase = a.phase;
     const float c0 = a.cJ[0], c1 = a.cJ[1], c2 = a.cJ[2];
     float mu[2], lam[2];
     for (int i = 0; i < 2; i++) {
@@ -156,13 +156,14 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
                         const int64_t La = (int64_t)(pb * g.n3p + zla) * g.n2 + yla;
                         const bool owna = za >= z0 && ya >= 0;
                         constexpr int CH = n1 * 4 / 128;  // 128-byte chunks per row
-                        const int nrow = 19 + (first ? 0 : 9) + ((owna && apend != 0.f) ? 9 : 0);
+                        const int nrow = 20 + (first ? 0 : 9) + ((owna && apend != 0.f) ? 9 : 0);
                         for (int e = tid; e < nrow * CH; e += NT) {
                             const int row = e / CH, q = e - row * CH;
-                            const float* base = row < 9 ? rg + (int64_t)row * V
-                                                : row < 19 ? tg + (int64_t)(row - 9) * V
-                                                : (!first && row < 28) ? pin + (int64_t)(row - 19) * V
-                                                : xg + (int64_t)(row - (first ? 19 : 28)) * V;
+                            const float* base = row == 0 ? reinterpret_cast<const float*>(a.vrank)
+                                                : row < 10 ? rg + (int64_t)(row - 1) * V
+                                                : row < 20 ? tg + (int64_t)(row - 10) * V
+                                                : (!first && row < 29) ? pin + (int64_t)(row - 20) * V
+                                                : xg + (int64_t)(row - (first ? 20 : 29)) * V;
                             asm volatile("prefetch.global.L2 [%0];" ::"l"(base + La * n1 + q * 32));
                         }
                         const int b0 = a.lofs[La], b1 = a.lofs[La + 1];
@@ -177,17 +178,16 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
                         }
                     }
                 }
-                // (1) voxels of the line
+                // (1) voxels of the line: A : p at pure voxels from the tangent
+                // cache, at boxels from their packed tangent (column vrank)
 #pragma unroll
                 for (int v = 0; v < VPT; v++) {
                     const int xx = tid + v * NT;
                     const int64_t vox = L * n1 + xx;
-                    const int ph = phase[vox];
-                    float p[9], po[9], xo[9], t[10];
+                    const int vr = a.vrank[vox];
+                    float p[9], po[9], xo[9];
 #pragma unroll
                     for (int c = 0; c < 9; c++) p[c] = rg[c * V + vox];
-#pragma unroll
-                    for (int c = 0; c < 10; c++) t[c] = tg[c * V + vox];
                     if (!first) {
 #pragma unroll
                         for (int c = 0; c < 9; c++) po[c] = pin[c * V + vox];
@@ -204,58 +204,40 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
 #pragma unroll
                         for (int c = 0; c < 9; c++) pout[c * V + vox] = p[c];
                     }
-                    if (ph == 2) {
-                        // boxel: p parks in the line buffer; (2) replaces it
+                    float y[9];
+                    if (vr >= 0) {
+                        float Ak[45];
 #pragma unroll
-                        for (int c = 0; c < 9; c++) LB[c * n1 + xx] = p[c];
-                    } else {
-                        float y[9];
-                        nh_tangent<float>(t, t[9], mu[ph], lam[ph], p, y);
-                        if (own) {
-                            float sp = 0.f;
-#pragma unroll
-                            for (int c = 0; c < 9; c++) sp += p[c] * y[c];
-                            accp += sp;
-                        }
-#pragma unroll
-                        for (int i = 0; i < 3; i++) {
-                            LB[(3 * i) * n1 + xx] = c0 * y[3 * i];
-                            LB[(3 * i + 1) * n1 + xx] = c1 * y[3 * i + 1];
-                            LB[(3 * i + 2) * n1 + xx] = c2 * y[3 * i + 2];
-                        }
-                    }
-                }
-                __syncthreads();
-                // (2) boxels of the line, in voxel order
-                const int k0 = a.lofs[L], k1 = a.lofs[L + 1];
-                if (k1 > k0) {
-                    for (int k = k0 + tid; k < k1; k += NT) {
-                        const int xb = (int)(a.bvox[k] - L * n1);
-                        float Ak[45], p[9];
-#pragma unroll
-                        for (int j = 0; j < 45; j++) Ak[j] = a.bA[(int64_t)j * a.nb + k];
-#pragma unroll
-                        for (int c = 0; c < 9; c++) p[c] = LB[c * n1 + xb];
-                        float sp = 0.f, y[9];
+                        for (int j = 0; j < 45; j++) Ak[j] = a.bA[(int64_t)j * a.nb + vr];
 #pragma unroll
                         for (int r = 0; r < 9; r++) {
                             float yr = 0.f;
 #pragma unroll
                             for (int c = 0; c < 9; c++) yr += Ak[sym_idx(r, c)] * p[c];
                             y[r] = yr;
-                            sp += p[r] * yr;
                         }
-                        if (own) accp += sp;
+                    } else {
+                        const int ph = -1 - vr;
+                        float t[10];
 #pragma unroll
-                        for (int i = 0; i < 3; i++) {
-                            LB[(3 * i) * n1 + xb] = c0 * y[3 * i];
-                            LB[(3 * i + 1) * n1 + xb] = c1 * y[3 * i + 1];
-                            LB[(3 * i + 2) * n1 + xb] = c2 * y[3 * i + 2];
-                        }
+                        for (int c = 0; c < 10; c++) t[c] = tg[c * V + vox];
+                        nh_tangent<float>(t, t[9], mu[ph], lam[ph], p, y);
                     }
-                    __syncthreads();
+                    if (own) {
+                        float sp = 0.f;
+#pragma unroll
+                        for (int c = 0; c < 9; c++) sp += p[c] * y[c];
+                        accp += sp;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 3; i++) {
+                        LB[(3 * i) * n1 + xx] = c0 * y[3 * i];
+                        LB[(3 * i + 1) * n1 + xx] = c1 * y[3 * i + 1];
+                        LB[(3 * i + 2) * n1 + xx] = c2 * y[3 * i + 2];
+                    }
                 }
-                // (3) x-neighbours, then the y and z accumulation of the nodes
+                __syncthreads();
+                // (2) x-neighbours, then the y and z accumulation of the nodes
 #pragma unroll
                 for (int v = 0; v < VPT; v++) {
                     const int xx = tid + v * NT;
