@@ -448,6 +448,7 @@ template <typename T> struct Engine {
     DevTables<T> tab;
     Plan pM, py, pz;
     int lines, txy, txz;
+    int lines_fwd;  // x-lines per group of the x-forward (lines: of the x-inverse)
     cx<T>* spec = nullptr;  // not owned
     // TMA views of spec for the FP32 z- and y-passes, one per tile-width candidate
     CUtensorMap zmap[2], ymap[2];
@@ -483,15 +484,16 @@ template <typename T> struct Engine {
         pM = make_plan(g.M);
         py = make_plan(g.n2);
         pz = make_plan(g.n3p);
-        lines = xpass_lines(g, sizeof(cx<T>));
+        lines = lines_fwd = xpass_lines(g, sizeof(cx<T>));
         if (sizeof(cx<T>) == 16) {
-            // residual transforms (FP64 or double-float words): groups of
-            // lines large enough (>= 1024 voxels) that the FFT phase keeps a
-            // 256-thread block busy; these register-heavy blocks run one or
-            // two per SM anyway, so the larger shared buffers cost no residency
-            while (lines * g.n1 < 1024 && xpass_smem(g, lines * 2, sizeof(cx<T>)) <= 160 * 1024 &&
-                   (g.n2 * g.n3p) % (lines * 2) == 0)
-                lines *= 2;
+            // x-forward passes in FP64 or double-float words: groups of lines
+            // large enough (>= 1024 voxels) that the FFT phase keeps a
+            // 256-thread block busy; these register-heavy blocks run one per
+            // SM anyway, so the larger shared buffers cost no residency (the
+            // x-inverse keeps its groups: it runs two blocks per SM)
+            while (lines_fwd * g.n1 < 1024 && xpass_smem(g, lines_fwd * 2, sizeof(cx<T>)) <= 160 * 1024 &&
+                   (g.n2 * g.n3p) % (lines_fwd * 2) == 0)
+                lines_fwd *= 2;
         }
         txy = ypass_tx(g.n2, sizeof(cx<T>));
         txz = zpass_tx(g.n3p, sizeof(cx<T>));
@@ -519,7 +521,7 @@ template <typename T> struct Engine {
         a.tw = tab.twM;
         a.tw2 = tab.tw2;
         a.spec = spec;
-        a.lines_per_block = lines;
+        a.lines_per_block = lines_fwd;
         a.cfg = cfg_xf;
         return a;
     }
@@ -611,7 +613,10 @@ template <typename T> struct Engine {
     int zblocks_p() const { return zpass_blocks(g, txz, sizeof(cx<T>)); }  // z-pass blocks (partials) per problem
     int zblocks() const { return zblocks_p() * g.nprob; }
     int xblocks() const { return xpass_grid(g, lines); }
-    int xpartials() const { return std::max(xpass_grid(g, lines), xpass_partials_max(g)); }
+    int xpartials() const
+    {
+        return std::max(std::max(xpass_grid(g, lines), xpass_grid(g, lines_fwd)), xpass_partials_max(g));
+    }
 };
 
 // ------------------------------------------------------------------ small kernels
@@ -2780,32 +2785,36 @@ template <typename Tc, typename Rt> struct MixSolve : SolveBase {
         {
             std::vector<XfwdArgs<Rt, Tc>> a(K);
             std::vector<XinvArgs<Rt, Tc>> b(K);
-            std::vector<int> it(K);
-            size_t sm = 0;
+            std::vector<int> itf(K), iti(K);
+            size_t smf = 0, smi = 0;
             for (int i = 0; i < K; i++) {
                 const Cls& q = *cls[G[i]];
                 a[i] = q.resid_xf(XI_RHS);
                 b[i] = q.resid_xi(XI_RHS);
-                it[i] = q.e64.xblocks();
-                sm = std::max(sm, xpass_smem(q.g, q.e64.lines, sizeof(cx<Rt>)));
+                itf[i] = xpass_grid(q.g, q.e64.lines_fwd);
+                iti[i] = q.e64.xblocks();
+                smf = std::max(smf, xpass_smem(q.g, q.e64.lines_fwd, sizeof(cx<Rt>)));
+                smi = std::max(smi, xpass_smem(q.g, q.e64.lines, sizeof(cx<Rt>)));
             }
-            if ((rc = g_xf_res.build(a, it, {}, sm, st))) return rc;
-            if ((rc = g_xi_res.build(b, it, {}, sm, st))) return rc;
+            if ((rc = g_xf_res.build(a, itf, {}, smf, st))) return rc;
+            if ((rc = g_xi_res.build(b, iti, {}, smi, st))) return rc;
         }
         {
             std::vector<XfwdArgs<Tc, Tc>> a(K);
             std::vector<XinvArgs<Tc, Tc>> b(K);
-            std::vector<int> it(K);
-            size_t sm = 0;
+            std::vector<int> itf(K), iti(K);
+            size_t smf = 0, smi = 0;
             for (int i = 0; i < K; i++) {
                 const Cls& q = *cls[G[i]];
                 a[i] = q.cg_xf();
                 b[i] = q.cg_xi();
-                it[i] = q.ec.xblocks();
-                sm = std::max(sm, xpass_smem(q.g, q.ec.lines, sizeof(cx<Tc>)));
+                itf[i] = xpass_grid(q.g, q.ec.lines_fwd);
+                iti[i] = q.ec.xblocks();
+                smf = std::max(smf, xpass_smem(q.g, q.ec.lines_fwd, sizeof(cx<Tc>)));
+                smi = std::max(smi, xpass_smem(q.g, q.ec.lines, sizeof(cx<Tc>)));
             }
-            if ((rc = g_xf_cg.build(a, it, {}, sm, st))) return rc;
-            if ((rc = g_xi_cg.build(b, it, {}, sm, st))) return rc;
+            if ((rc = g_xf_cg.build(a, itf, {}, smf, st))) return rc;
+            if ((rc = g_xi_cg.build(b, iti, {}, smi, st))) return rc;
         }
         if ((rc = build_yz<Rt>(g_y_res, g_z_res, true))) return rc;
         return build_yz<Tc>(g_y_cg, g_z_cg, false);
