@@ -30,6 +30,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
+// per-thread asynchronous 4-byte global -> shared copies (completion per
+// thread by commit groups; the copying thread is the reader)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still pending
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // 4-D tiled tensor copies (TMA) through a tensor map held in kernel-parameter
 // space; coordinates are element indices, innermost first.  The innermost
 // coordinate times the element size must be a multiple of 16 bytes.
