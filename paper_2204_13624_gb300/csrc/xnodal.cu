@@ -32,7 +32,6 @@
 // FFT + Hermitian split) into components 0, 3, 6 of the spectrum.
 #include <algorithm>
 
-#include "async_copy.cuh"
 #include "combo_internal.cuh"
 #include "fft_fast.cuh"
 #include "../../include/combo.h"
@@ -54,24 +53,21 @@ int num_sms_nodal()
 
 // threads per block (one or two voxels of a line per thread) and blocks per SM
 template <int M> __host__ __device__ constexpr int nodal_threads() { return M == 64 ? 128 : 256; }
-// variants: C = 1, two blocks per SM (up to 128 registers), operands loaded
-// (and prefetched into L2 two lines ahead) by the voxel phase; C = 2, one
-// block per SM whose operand rows of the next voxel line arrive in shared
-// memory by per-thread asynchronous copies while the current line is formed
-template <int M, int C> __host__ __device__ constexpr int nodal_minb() { return C == 2 ? 1 : 2; }
-constexpr int kNodalRows = 29;  // staged rows per voxel: vrank, r (9), p_old (9), tangent cache (10)
+// variants (two blocks per SM, up to 128 registers): C = 1, the operand rows
+// of the voxel line two steps ahead are prefetched into L2; C = 2, also those
+// of the next line into L1
+template <int M, int C> __host__ __device__ constexpr int nodal_minb() { return 2; }
 // threads that transform the 3 TY nodal lines of a plane (named barrier 1)
 template <int M, int TY> __host__ __device__ constexpr int nodal_fft_threads()
 {
     return (3 * TY * FastPlan<M>::TPL + 31) / 32 * 32;
 }
-template <int M, int TY, int C> __host__ __device__ constexpr size_t nodal_smem()
+template <int M, int TY> __host__ __device__ constexpr size_t nodal_smem()
 {
     // line buffers [2][9][n1], T [3][TY][n1] floats; nodal lines [3 TY][M + 1]
-    // complex; (candidate 2) operand stages [2][kNodalRows][n1]; twiddles [M];
-    // reduction [256] doubles; flag
-    return (size_t)2 * 9 * 2 * M * 4 + (size_t)3 * TY * 2 * M * 4 + (size_t)3 * TY * (M + 1) * 8 +
-           (C == 2 ? (size_t)2 * kNodalRows * 2 * M * 4 : 0) + (size_t)M * 8 + 256 * 8 + 16;
+    // complex; twiddles [M]; reduction [256] doubles; flag
+    return (size_t)2 * 9 * 2 * M * 4 + (size_t)3 * TY * 2 * M * 4 + (size_t)3 * TY * (M + 1) * 8 + (size_t)M * 8 +
+           256 * 8 + 16;
 }
 
 }  // namespace
@@ -104,9 +100,7 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
     float* lbuf = reinterpret_cast<float*>(smem_raw);      // [2][9][n1]
     float* tp = lbuf + 2 * 9 * n1;                          // [3][TY][n1]
     float2* W = reinterpret_cast<float2*>(tp + 3 * TY * n1);  // [NLF][lsw]
-    constexpr bool STAGED = (C == 2);
-    float* stage = reinterpret_cast<float*>(W + (size_t)NLF * lsw);  // [2][kNodalRows][n1] (STAGED)
-    float2* tws = reinterpret_cast<float2*>(stage + (STAGED ? 2 * kNodalRows * n1 : 0));  // exp(-2 pi i t / M)
+    float2* tws = W + (size_t)NLF * lsw;  // exp(-2 pi i t / M)
     double* red = reinterpret_cast<double*>(tws + M);
     int* flag = reinterpret_cast<int*>(red + 256);
     for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = a.tw[i];
@@ -136,30 +130,6 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
     }
     __syncthreads();
 
-    // (STAGED) this thread's operands of voxel line La into stage slot sl
-    auto stage_line = [&](int64_t La, int sl) {
-        float* st = stage + sl * kNodalRows * n1;
-#pragma unroll
-        for (int v = 0; v < VPT; v++) {
-            const int xx = tid + v * NT;
-            const int64_t vox = La * n1 + xx;
-            cp_async4(st + xx, a.vrank + vox);
-#pragma unroll
-            for (int c = 0; c < 9; c++) cp_async4(st + (1 + c) * n1 + xx, rg + c * V + vox);
-            if (!first) {
-#pragma unroll
-                for (int c = 0; c < 9; c++) cp_async4(st + (10 + c) * n1 + xx, pin + c * V + vox);
-            }
-#pragma unroll
-            for (int c = 0; c < 10; c++) cp_async4(st + (19 + c) * n1 + xx, tg + c * V + vox);
-        }
-    };
-    auto line_of = [&](int y0, int zv, int yy) -> int64_t {
-        const int zl = zv < 0 ? zv + g.n3p : zv;
-        const int yl = (y0 + yy < 0) ? y0 + yy + g.n2 : y0 + yy;
-        return (int64_t)(pb * g.n3p + zl) * g.n2 + yl;
-    };
-
     double acc = 0.0;
     int s = 0;  // voxel lines swept (line buffer parity)
     for (int64_t lin = lin_b; lin < lin_e;) {
@@ -168,34 +138,40 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
         lin += z1 - z0;
         const int y0 = col * TY;
         float accp = 0.f;
-        int q = 0;  // (STAGED) lines of this item swept: stage slot parity
-        if constexpr (STAGED) {
-            stage_line(line_of(y0, z0 - 1, -1), 0);
-            cp_async_commit();
-        }
         for (int zv = z0 - 1; zv < z1; zv++) {
             const bool zown = zv >= z0;
             const int zl = zv < 0 ? zv + g.n3p : zv;
             const int64_t zrow = (int64_t)(pb * g.n3p + zl) * g.n2;  // first line of the plane
             float pe[VPT][3], pf[VPT][3], pq[VPT][3];  // e, f, q of the previous voxel line
-            for (int yy = -1; yy < TY; yy++, s++, q++) {
+            for (int yy = -1; yy < TY; yy++, s++) {
                 const int yl = (y0 + yy < 0) ? y0 + yy + g.n2 : y0 + yy;
                 const bool own = zown && yy >= 0;
                 const int64_t L = zrow + yl;
                 float* LB = lbuf + (s & 1) * 9 * n1;
-                const float* st = stage + (q & 1) * kNodalRows * n1;
-                if constexpr (STAGED) {
-                    // the next line of the item into the other slot (this
-                    // thread read that slot one line ago), then this line's
-                    // copies are complete
+                if constexpr (C == 2) {
+                    // the operand rows of the next voxel line of the run into L1
                     int yn = yy + 1, zn = zv;
                     if (yn >= TY) {
                         yn = -1;
                         zn++;
                     }
-                    if (zn < z1) stage_line(line_of(y0, zn, yn), (q + 1) & 1);
-                    cp_async_commit();
-                    cp_async_wait<1>();
+                    if (zn < z1) {
+                        const int zln = zn < 0 ? zn + g.n3p : zn;
+                        const int yln = (y0 + yn < 0) ? y0 + yn + g.n2 : y0 + yn;
+                        const int64_t Ln = (int64_t)(pb * g.n3p + zln) * g.n2 + yln;
+                        const bool ownn = zn >= z0 && yn >= 0;
+                        constexpr int CH = n1 * 4 / 128;
+                        const int nrow = 20 + (first ? 0 : 9) + ((ownn && apend != 0.f) ? 9 : 0);
+                        for (int e = tid; e < nrow * CH; e += NT) {
+                            const int row = e / CH, qq = e - row * CH;
+                            const float* base = row == 0 ? reinterpret_cast<const float*>(a.vrank)
+                                                : row < 10 ? rg + (int64_t)(row - 1) * V
+                                                : row < 20 ? tg + (int64_t)(row - 10) * V
+                                                : (!first && row < 29) ? pin + (int64_t)(row - 20) * V
+                                                : xg + (int64_t)(row - (first ? 20 : 29)) * V;
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(base + Ln * n1 + qq * 32));
+                        }
+                    }
                 }
                 {
                     // the operand rows and boxel tangents of the voxel line two
@@ -212,16 +188,14 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
                         const int64_t La = (int64_t)(pb * g.n3p + zla) * g.n2 + yla;
                         const bool owna = za >= z0 && ya >= 0;
                         constexpr int CH = n1 * 4 / 128;  // 128-byte chunks per row
-                        // (STAGED: the x rows only; the rest is copied a line ahead)
-                        const int nst = STAGED ? 0 : 20 + (first ? 0 : 9);
-                        const int nrow = nst + ((owna && apend != 0.f) ? 9 : 0);
+                        const int nrow = 20 + (first ? 0 : 9) + ((owna && apend != 0.f) ? 9 : 0);
                         for (int e = tid; e < nrow * CH; e += NT) {
                             const int row = e / CH, qq = e - row * CH;
-                            const float* base = row >= nst ? xg + (int64_t)(row - nst) * V
-                                                : row == 0 ? reinterpret_cast<const float*>(a.vrank)
+                            const float* base = row == 0 ? reinterpret_cast<const float*>(a.vrank)
                                                 : row < 10 ? rg + (int64_t)(row - 1) * V
                                                 : row < 20 ? tg + (int64_t)(row - 10) * V
-                                                : pin + (int64_t)(row - 20) * V;
+                                                : (!first && row < 29) ? pin + (int64_t)(row - 20) * V
+                                                : xg + (int64_t)(row - (first ? 20 : 29)) * V;
                             asm volatile("prefetch.global.L2 [%0];" ::"l"(base + La * n1 + qq * 32));
                         }
                         const int b0 = a.lofs[La], b1 = a.lofs[La + 1];
@@ -242,13 +216,13 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
                 for (int v = 0; v < VPT; v++) {
                     const int xx = tid + v * NT;
                     const int64_t vox = L * n1 + xx;
-                    const int vr = STAGED ? __float_as_int(st[xx]) : a.vrank[vox];
+                    const int vr = a.vrank[vox];
                     float p[9], po[9], xo[9];
 #pragma unroll
-                    for (int c = 0; c < 9; c++) p[c] = STAGED ? st[(1 + c) * n1 + xx] : rg[c * V + vox];
+                    for (int c = 0; c < 9; c++) p[c] = rg[c * V + vox];
                     if (!first) {
 #pragma unroll
-                        for (int c = 0; c < 9; c++) po[c] = STAGED ? st[(10 + c) * n1 + xx] : pin[c * V + vox];
+                        for (int c = 0; c < 9; c++) po[c] = pin[c * V + vox];
                         if (own && apend != 0.f) {
 #pragma unroll
                             for (int c = 0; c < 9; c++) xo[c] = xg[c * V + vox];
@@ -278,7 +252,7 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
                         const int ph = -1 - vr;
                         float t[10];
 #pragma unroll
-                        for (int c = 0; c < 10; c++) t[c] = STAGED ? st[(19 + c) * n1 + xx] : tg[c * V + vox];
+                        for (int c = 0; c < 10; c++) t[c] = tg[c * V + vox];
                         nh_tangent<float>(t, t[9], mu[ph], lam[ph], p, y);
                     }
                     if (own) {
@@ -380,7 +354,7 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
 template <int M, int TY, int C> static void xfwd_nodal_launch(NodalArgs a, cudaStream_t st)
 {
     constexpr int threads = nodal_threads<M>();
-    constexpr size_t sm = nodal_smem<M, TY, C>();
+    constexpr size_t sm = nodal_smem<M, TY>();
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaFuncSetAttribute(k_xfwd_nodal<M, TY, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -413,7 +387,7 @@ template <int C> static void xfwd_nodal_pick(const NodalArgs& a, cudaStream_t st
     }
 }
 
-// candidate 0: the staged variant; 1: two blocks per SM
+// candidate 0: with the L1 prefetch of the next line; 1: without
 void launch_xfwd_nodal(NodalArgs a, cudaStream_t st)
 {
     if (a.cfg == 1)
