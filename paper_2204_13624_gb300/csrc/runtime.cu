@@ -487,11 +487,11 @@ template <typename T> struct Engine {
         lines = lines_fwd = xpass_lines(g, sizeof(cx<T>));
         if (sizeof(cx<T>) == 16) {
             // x-forward passes in FP64 or double-float words: groups of lines
-            // large enough (>= 1024 voxels) that the FFT phase keeps a
-            // 256-thread block busy; these register-heavy blocks run one per
-            // SM anyway, so the larger shared buffers cost no residency (the
-            // x-inverse keeps its groups: it runs two blocks per SM)
-            while (lines_fwd * g.n1 < 1024 && xpass_smem(g, lines_fwd * 2, sizeof(cx<T>)) <= 160 * 1024 &&
+            // as large (up to 1024 voxels) as two resident blocks per SM allow
+            // (the kernel is register-capped for two), so that the FFT phase
+            // keeps more of a 256-thread block busy (the x-inverse keeps its
+            // groups)
+            while (lines_fwd * g.n1 < 1024 && xpass_smem(g, lines_fwd * 2, sizeof(cx<T>)) <= 110 * 1024 &&
                    (g.n2 * g.n3p) % (lines_fwd * 2) == 0)
                 lines_fwd *= 2;
         }

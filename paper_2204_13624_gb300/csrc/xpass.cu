@@ -126,7 +126,7 @@ __device__ __forceinline__ bool nh_stress(const double F[9], double mu, double l
 // The same stress with the cofactors, J, F^{-1}, ln J (df_log) and P in
 // double-float; G and m, the tangent cache of the FP32 Krylov iterations, are
 // rounded to FP32.  False if J <= 0.
-__device__ __forceinline__ bool nh_stress_df(const double Fd[9], double mu, double lam, df32 P[9], float G[9],
+__device__ __forceinline__ bool nh_stress_df(const double Fd[9], df32 mud, df32 lamd, df32 P[9], float G[9],
                                              float& m)
 {
     df32 F[9];
@@ -148,8 +148,8 @@ __device__ __forceinline__ bool nh_stress_df(const double Fd[9], double mu, doub
     Gi[6] = c2 * iJ;
     Gi[7] = (F[1] * F[6] - F[0] * F[7]) * iJ;
     Gi[8] = (F[0] * F[4] - F[1] * F[3]) * iJ;
-    const df32 lnJ = df_log(J), mud = df32(mu);
-    const df32 k = df32(lam) * lnJ - mud;
+    const df32 lnJ = df_log(J);
+    const df32 k = lamd * lnJ - mud;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -190,9 +190,12 @@ __device__ __forceinline__ void xfwd_body(const XfwdArgs<T, Tc>& a, int guard, i
     const int64_t V = g.V;
     double acc = 0.0;
     double mu[2], lam[2];
+    df32 mu_df[2], lam_df[2];  // their double-float splits (once per block, off the per-voxel FP64 pipe)
     for (int i = 0; i < 2; i++) {
         mu[i] = a.matp ? a.matp[4 * pb + i] : a.mu[i];
         lam[i] = a.matp ? a.matp[4 * pb + 2 + i] : a.lam[i];
+        mu_df[i] = df32(mu[i]);
+        lam_df[i] = df32(lam[i]);
     }
 
     const bool first = (a.mode == XF_TANGENT) ? (sc->cg_iter == 0) : false;
@@ -247,7 +250,7 @@ __device__ __forceinline__ void xfwd_body(const XfwdArgs<T, Tc>& a, int guard, i
                     }
                 } else if constexpr (std::is_same<T, df32>::value) {
                     float G[9], m;
-                    if (!nh_stress_df(F, mu[ph], lam[ph], o, G, m)) {
+                    if (!nh_stress_df(F, mu_df[ph], lam_df[ph], o, G, m)) {
                         raise_status(sc, finite9(F) ? COMBO_E_INADMISSIBLE : COMBO_E_NAN);
 #pragma unroll
                         for (int c = 0; c < 9; c++) {
@@ -430,8 +433,15 @@ __device__ __forceinline__ void xfwd_body(const XfwdArgs<T, Tc>& a, int guard, i
     }
 }
 
+// blocks per SM the x-forward is register-capped for: FP32 tangent pass 4,
+// FP64 / double-float constitutive pass 2, else 1
+template <typename T, bool TAN> constexpr int xfwd_minb()
+{
+    return (TAN && sizeof(T) == 4) ? 4 : ((!TAN && sizeof(T) == 8) ? 2 : 1);
+}
+
 template <typename T, typename Tc, int MF, bool TAN>
-__global__ void __launch_bounds__(256, (TAN && sizeof(T) == 4) ? 4 : 1) k_xfwd(XfwdArgs<T, Tc> a, int guard)
+__global__ void __launch_bounds__(256, (xfwd_minb<T, TAN>())) k_xfwd(XfwdArgs<T, Tc> a, int guard)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     xfwd_body<T, Tc, MF, TAN>(a, guard, blockIdx.x, gridDim.x, smem_raw);
