@@ -53,10 +53,9 @@ int num_sms_nodal()
 
 // threads per block (one or two voxels of a line per thread) and blocks per SM
 template <int M> __host__ __device__ constexpr int nodal_threads() { return M == 64 ? 128 : 256; }
-// variants (two blocks per SM, up to 128 registers): C = 1, the operand rows
-// of the voxel line two steps ahead are prefetched into L2; C = 2, also those
-// of the next line into L1
-template <int M, int C> __host__ __device__ constexpr int nodal_minb() { return 2; }
+// candidates: C = 1, two blocks per SM (registers capped at 128, a few
+// spill); C = 2, one block per SM (no cap)
+template <int M, int C> __host__ __device__ constexpr int nodal_minb() { return C == 2 ? 1 : 2; }
 // threads that transform the 3 TY nodal lines of a plane (named barrier 1)
 template <int M, int TY> __host__ __device__ constexpr int nodal_fft_threads()
 {
@@ -138,6 +137,12 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
         lin += z1 - z0;
         const int y0 = col * TY;
         float accp = 0.f;
+        int vrc[VPT];  // vrank of this thread's voxels on the current voxel line
+        {
+            const int64_t L0 = (int64_t)(pb * g.n3p + (z0 == 0 ? g.n3p - 1 : z0 - 1)) * g.n2 + (y0 == 0 ? g.n2 - 1 : y0 - 1);
+#pragma unroll
+            for (int v = 0; v < VPT; v++) vrc[v] = a.vrank[L0 * n1 + tid + v * NT];
+        }
         for (int zv = z0 - 1; zv < z1; zv++) {
             const bool zown = zv >= z0;
             const int zl = zv < 0 ? zv + g.n3p : zv;
@@ -148,8 +153,8 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
                 const bool own = zown && yy >= 0;
                 const int64_t L = zrow + yl;
                 float* LB = lbuf + (s & 1) * 9 * n1;
-                if constexpr (C == 2) {
-                    // the operand rows of the next voxel line of the run into L1
+                int64_t Lnext = -1;  // the next voxel line of this run
+                {
                     int yn = yy + 1, zn = zv;
                     if (yn >= TY) {
                         yn = -1;
@@ -158,19 +163,7 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
                     if (zn < z1) {
                         const int zln = zn < 0 ? zn + g.n3p : zn;
                         const int yln = (y0 + yn < 0) ? y0 + yn + g.n2 : y0 + yn;
-                        const int64_t Ln = (int64_t)(pb * g.n3p + zln) * g.n2 + yln;
-                        const bool ownn = zn >= z0 && yn >= 0;
-                        constexpr int CH = n1 * 4 / 128;
-                        const int nrow = 20 + (first ? 0 : 9) + ((ownn && apend != 0.f) ? 9 : 0);
-                        for (int e = tid; e < nrow * CH; e += NT) {
-                            const int row = e / CH, qq = e - row * CH;
-                            const float* base = row == 0 ? reinterpret_cast<const float*>(a.vrank)
-                                                : row < 10 ? rg + (int64_t)(row - 1) * V
-                                                : row < 20 ? tg + (int64_t)(row - 10) * V
-                                                : (!first && row < 29) ? pin + (int64_t)(row - 20) * V
-                                                : xg + (int64_t)(row - (first ? 20 : 29)) * V;
-                            asm volatile("prefetch.global.L1 [%0];" ::"l"(base + Ln * n1 + qq * 32));
-                        }
+                        Lnext = (int64_t)(pb * g.n3p + zln) * g.n2 + yln;
                     }
                 }
                 {
@@ -216,31 +209,36 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
                 for (int v = 0; v < VPT; v++) {
                     const int xx = tid + v * NT;
                     const int64_t vox = L * n1 + xx;
-                    const int vr = a.vrank[vox];
-                    float p[9], po[9], xo[9];
+                    // this line's vrank was loaded one line ahead, so every
+                    // operand load -- the boxel tangent's too, and the tangent
+                    // cache, unused at boxels -- is issued before the first
+                    // use: one memory latency per line; the stores follow
+                    const int vr = vrc[v];
+                    const bool xup = own && !first && apend != 0.f;
+                    float p[9], po[9], xo[9], t[10], Ak[45];
 #pragma unroll
                     for (int c = 0; c < 9; c++) p[c] = rg[c * V + vox];
+#pragma unroll
+                    for (int c = 0; c < 10; c++) t[c] = tg[c * V + vox];
                     if (!first) {
 #pragma unroll
                         for (int c = 0; c < 9; c++) po[c] = pin[c * V + vox];
-                        if (own && apend != 0.f) {
+                    }
+                    if (xup) {
 #pragma unroll
-                            for (int c = 0; c < 9; c++) xo[c] = xg[c * V + vox];
+                        for (int c = 0; c < 9; c++) xo[c] = xg[c * V + vox];
+                    }
+                    if (vr >= 0) {
 #pragma unroll
-                            for (int c = 0; c < 9; c++) xg[c * V + vox] = xo[c] + apend * po[c];
-                        }
+                        for (int j = 0; j < 45; j++) Ak[j] = a.bA[(int64_t)j * a.nb + vr];
+                    }
+                    vrc[v] = Lnext >= 0 ? a.vrank[Lnext * n1 + xx] : 0;
+                    if (!first) {
 #pragma unroll
                         for (int c = 0; c < 9; c++) p[c] += beta * po[c];
                     }
-                    if (own) {
-#pragma unroll
-                        for (int c = 0; c < 9; c++) pout[c * V + vox] = p[c];
-                    }
                     float y[9];
                     if (vr >= 0) {
-                        float Ak[45];
-#pragma unroll
-                        for (int j = 0; j < 45; j++) Ak[j] = a.bA[(int64_t)j * a.nb + vr];
 #pragma unroll
                         for (int r = 0; r < 9; r++) {
                             float yr = 0.f;
@@ -250,9 +248,6 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
                         }
                     } else {
                         const int ph = -1 - vr;
-                        float t[10];
-#pragma unroll
-                        for (int c = 0; c < 10; c++) t[c] = tg[c * V + vox];
                         nh_tangent<float>(t, t[9], mu[ph], lam[ph], p, y);
                     }
                     if (own) {
@@ -260,6 +255,12 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
 #pragma unroll
                         for (int c = 0; c < 9; c++) sp += p[c] * y[c];
                         accp += sp;
+#pragma unroll
+                        for (int c = 0; c < 9; c++) pout[c * V + vox] = p[c];
+                    }
+                    if (xup) {
+#pragma unroll
+                        for (int c = 0; c < 9; c++) xg[c * V + vox] = xo[c] + apend * po[c];
                     }
 #pragma unroll
                     for (int i = 0; i < 3; i++) {
@@ -387,7 +388,7 @@ template <int C> static void xfwd_nodal_pick(const NodalArgs& a, cudaStream_t st
     }
 }
 
-// candidate 0: with the L1 prefetch of the next line; 1: without
+// candidate 0: one block per SM; 1: two
 void launch_xfwd_nodal(NodalArgs a, cudaStream_t st)
 {
     if (a.cfg == 1)
