@@ -242,11 +242,32 @@ __host__ __device__ constexpr bool fast3_size_x(int m)
 }
 
 // Radix of stage s of the forward (INV = false) or inverse (reversed) plan.
-template <int N, bool INV, int S> struct StageR {
-    using P = FastPlan<N>;
+template <class P, bool INV, int S> struct StageRP {
     static constexpr int FWD = (S == 0) ? P::R0 : ((S == 1) ? P::R1 : P::R2);
     static constexpr int RS = INV ? ((P::NST - 1 - S == 0) ? P::R0 : ((P::NST - 1 - S == 1) ? P::R1 : P::R2)) : FWD;
 };
+template <int N, bool INV, int S> struct StageR : StageRP<FastPlan<N>, INV, S> {};
+
+// Plans for 8-byte words (FP64, double-float): at N = 128 and 256 the radix-16
+// register DFTs of those words are long enough that the z-pass stalled on
+// instruction fetch; radix 8 / 4 stages with the same threads per line
+struct FastPlanW128 {
+    static constexpr int NST = 3, R0 = 8, R1 = 4, R2 = 4, TPL = 8;
+};
+struct FastPlanW256 {
+    static constexpr int NST = 3, R0 = 8, R1 = 8, R2 = 4, TPL = 16;
+};
+template <int N> struct WidePlan {
+    using type = FastPlan<N>;
+};
+template <> struct WidePlan<128> {
+    using type = FastPlanW128;
+};
+template <> struct WidePlan<256> {
+    using type = FastPlanW256;
+};
+template <typename T, int N>
+using PlanOf = typename std::conditional<(sizeof(T) >= 8), typename WidePlan<N>::type, FastPlan<N>>::type;
 
 // Load phase of one stage (radix R, NS = product of the earlier radices):
 // inputs j + t (N/R) of butterflies j = tau + TPL u, twiddled and transformed.
@@ -316,11 +337,11 @@ template <typename T, int N, bool INV, bool SYNC_FIRST = false, bool SYNC_LAST =
 __device__ __forceinline__ void fft_fast(const LG& lg, const SG& sg, const LX& lx, const SX& sx, int tau,
                                          const cx<T>* __restrict__ tw)
 {
-    using P = FastPlan<N>;
+    using P = PlanOf<T, N>;
     constexpr int TPL = P::TPL;
-    constexpr int RA = StageR<N, INV, 0>::RS;
+    constexpr int RA = StageRP<P, INV, 0>::RS;
     if constexpr (P::NST == 2) {
-        constexpr int RB = StageR<N, INV, 1>::RS;
+        constexpr int RB = StageRP<P, INV, 1>::RS;
         {
             cx<T> v[(N / RA) / TPL][RA];
             stage_load<T, N, RA, 1, TPL, INV>(v, lg, tau, tw);
@@ -335,8 +356,8 @@ __device__ __forceinline__ void fft_fast(const LG& lg, const SG& sg, const LX& l
             stage_store<T, N, RB, RA, TPL>(v, sg, tau);
         }
     } else {
-        constexpr int RB = StageR<N, INV, 1>::RS;
-        constexpr int RC = StageR<N, INV, 2>::RS;
+        constexpr int RB = StageRP<P, INV, 1>::RS;
+        constexpr int RC = StageRP<P, INV, 2>::RS;
         {
             cx<T> v[(N / RA) / TPL][RA];
             stage_load<T, N, RA, 1, TPL, INV>(v, lg, tau, tw);
@@ -375,15 +396,15 @@ template <int N> struct LastStage {
 template <typename T, int N, bool INV>
 __device__ cx<T>* fft_lines_fast(cx<T>* b0, cx<T>* b1, int nl, int ls, const cx<T>* __restrict__ tw)
 {
-    using P = FastPlan<N>;
+    using P = PlanOf<T, N>;
     constexpr int TPL = P::TPL;
     const int tid = threadIdx.x, nthr = blockDim.x;
     cx<T>* src = b0;
     cx<T>* dst = b1;
     auto one = [&](auto stage_tag) {
         constexpr int S = decltype(stage_tag)::value;
-        constexpr int R = StageR<N, INV, S>::RS;
-        constexpr int NS = (S == 0) ? 1 : ((S == 1) ? StageR<N, INV, 0>::RS : StageR<N, INV, 0>::RS * StageR<N, INV, 1>::RS);
+        constexpr int R = StageRP<P, INV, S>::RS;
+        constexpr int NS = (S == 0) ? 1 : ((S == 1) ? StageRP<P, INV, 0>::RS : StageRP<P, INV, 0>::RS * StageRP<P, INV, 1>::RS);
         for (int p = tid; p < nl * TPL; p += nthr) {
             const int q = p % nl, tau = p / nl;
             const cx<T>* s = src + (size_t)q * ls;

@@ -489,11 +489,15 @@ template <typename T> struct Engine {
             // x-forward passes in FP64 or double-float words: groups of lines
             // as large (up to 1024 voxels) as two resident blocks per SM allow
             // (the kernel is register-capped for two), so that the FFT phase
-            // keeps more of a 256-thread block busy (the x-inverse keeps its
-            // groups)
+            // keeps more of a 256-thread block busy
             while (lines_fwd * g.n1 < 1024 && xpass_smem(g, lines_fwd * 2, sizeof(cx<T>)) <= 110 * 1024 &&
                    (g.n2 * g.n3p) % (lines_fwd * 2) == 0)
                 lines_fwd *= 2;
+            // and the x-inverse (two blocks per SM by registers): groups of up
+            // to 512 voxels within the same shared-memory budget
+            while (lines * g.n1 < 512 && xpass_smem(g, lines * 2, sizeof(cx<T>)) <= 110 * 1024 &&
+                   (g.n2 * g.n3p) % (lines * 2) == 0)
+                lines *= 2;
         }
         txy = ypass_tx(g.n2, sizeof(cx<T>));
         txz = zpass_tx(g.n3p, sizeof(cx<T>));
