@@ -168,6 +168,9 @@ def algorithmic_bytes(kernel, p, krylov_bytes, disp=False, nodal=False):
     if kernel == "grad_cg":
         # nodal fields read, r read + written
         return 3 * V * w + V * 18 * w
+    if kernel == "xinv_grad_cg":
+        # three spectra read; r read + written (the nodal fields stay on chip)
+        return (spec_c // 3) * 2 * w + V * 18 * w
     if kernel in ("yfwd_krylov", "zgamma_krylov", "yinv_krylov"):
         return 2 * spec_c * 2 * w
     if kernel in ("yfwd_fp64", "zgamma_fp64", "yinv_fp64"):
@@ -463,7 +466,8 @@ def timed_window(combo, ctx, p, prec, steps, warmup, stream, dist=None, clk=None
     return ms, ops, residuals, prof, done
 
 
-KRYLOV = ("xfwd_tangent", "xfwd_nodal", "yfwd_krylov", "zgamma_krylov", "yinv_krylov", "xinv_cg", "grad_cg")
+KRYLOV = ("xfwd_tangent", "xfwd_nodal", "yfwd_krylov", "zgamma_krylov", "yinv_krylov", "xinv_cg", "grad_cg",
+          "xinv_grad_cg")
 
 
 def kernel_table(combo, prof, p, prec, ops, peak, peak_kind):
@@ -473,7 +477,8 @@ def kernel_table(combo, prof, p, prec, ops, peak, peak_kind):
     for k, (kms, cnt) in prof.items():
         if cnt == 0:
             continue
-        b = algorithmic_bytes(k, p, kb, disp=prof.get("grad_cg", (0.0, 0))[1] > 0,
+        b = algorithmic_bytes(k, p, kb,
+                              disp=prof.get("grad_cg", (0.0, 0))[1] > 0 or prof.get("xinv_grad_cg", (0.0, 0))[1] > 0,
                               nodal=prof.get("xfwd_nodal", (0.0, 0))[1] > 0)
         # CG kernels are launched in graph chunks of 8 iterations; launches
         # past the converged iteration return at once and do no work, so the

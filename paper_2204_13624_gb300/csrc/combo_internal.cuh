@@ -616,6 +616,9 @@ bool disp_x_ok(const GridDims& g);  // sizes the two x kernels take
 void launch_xinv_disp(const DispArgs& a, cudaStream_t st);
 void launch_disp_grad_cg(const DispArgs& a, cudaStream_t st);
 int disp_grad_partials_max();  // largest grid of the gradient pass (its partials)
+// the two in one pass (the nodal fields stay in shared memory)
+bool xinv_grad_ok(const GridDims& g);
+void launch_xinv_grad(const DispArgs& a, cudaStream_t st);
 
 // Record msg as the calling thread's last error; returns code.
 int set_error(int code, const char* msg);

@@ -325,12 +325,13 @@ enum KClass {
     K_DFMG_CG,
     K_DISP_GRAD,
     K_XFWD_NODAL,
+    K_XINV_GRAD,
     K_NCLASS
 };
 static const char* kclass_name[K_NCLASS] = {"boxel_laminate", "xfwd_resid_fp64", "yfwd_fp64", "zgamma_fp64",
                                              "yinv_fp64", "xinv_fp64", "xfwd_tangent", "yfwd_krylov",
                                              "zgamma_krylov", "yinv_krylov", "xinv_cg", "finalize", "update_F",
-                                             "dfmg_pure", "dfmg_gather", "dfmg_cg_tangent", "grad_cg", "xfwd_nodal"};
+                                             "dfmg_pure", "dfmg_gather", "dfmg_cg_tangent", "grad_cg", "xfwd_nodal", "xinv_grad_cg"};
 
 struct Profiler {
     bool on = false;
@@ -1851,6 +1852,12 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
                 d.cg_max = opt.cg_max_iter;
                 d.cg_fixed = opt.cg_fixed_iterations;
                 d.wait_cap = ec.wait_cap;
+                if (xinv_grad_ok(g)) {
+                    prof.begin(K_XINV_GRAD);
+                    launch_xinv_grad(d, st);
+                    prof.end();
+                    return;
+                }
                 prof.begin(K_XINV_CG);
                 launch_xinv_disp(d, st);
                 prof.end();

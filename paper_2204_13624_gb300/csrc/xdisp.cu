@@ -266,6 +266,199 @@ __global__ void __launch_bounds__(256, 2) k_disp_grad_cg(DispArgs a)
     }
 }
 
+// ------------------------------------------------------------- fused x-inverse + gradient
+// The two kernels above in one pass, without the round trip of the nodal
+// fields through global memory.  A block takes an even share of the problem's
+// (column, plane) pairs in column-major order, a column being TY voxel lines
+// y0 .. y0 + TY - 1: runs of planes, each marched along z.  For each node
+// plane it turns the TY + 1 node lines y0 .. y0 + TY of the three fields into
+// real lines (packed half-length inverse in place in the stage, output into
+// a ring of two node planes in shared memory), then forms the gradient of the
+// voxel plane between that node plane and the previous one with the CG
+// update.  The spectrum rows of the next node plane are copied into the stage
+// (bulk copies, mbarrier, bounded wait) while the gradient is formed.  The
+// node line y0 + TY and the node plane after a run's last are formed twice
+// (by this run and by the neighbour's).
+template <int M> __host__ __device__ constexpr int fused_ty() { return M == 256 ? 4 : 8; }
+template <int M, int TY> __host__ __device__ constexpr size_t fused_smem()
+{
+    // stage [3 (TY + 1)][lsx] complex; node planes [2][3][TY + 1][n1] floats;
+    // w2 [M], twiddles [M]; reduction [256] doubles; flag; barrier
+    return (size_t)3 * (TY + 1) * ((M + 2) / 2 * 2) * 8 + (size_t)2 * 3 * (TY + 1) * 2 * M * 4 + (size_t)2 * M * 8 +
+           256 * 8 + 16 + 16;
+}
+
+template <int M, int TY>
+__global__ void __launch_bounds__(256, 2) k_xinv_grad(DispArgs a)
+{
+    int pb, pj, gp;
+    prob_block(a.g, blockIdx.x, gridDim.x, pb, pj, gp);
+    Scalars* scp = a.sc + pb;
+    if (scp->cg_done) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int n1 = 2 * M;
+    constexpr int lsx = (M + 2) / 2 * 2;
+    constexpr int TPL = FastPlan<M>::TPL;
+    constexpr int NL = 3 * (TY + 1);  // node lines per node plane
+    constexpr int NBAR = (NL * TPL + 31) / 32 * 32;
+    constexpr int LPB = 256 / M;      // voxel lines of the gradient at a time
+    static_assert(NBAR <= 256 && M % 32 == 0, "block shape");
+    constexpr size_t SB = (size_t)NL * lsx * 8;
+    const GridDims g = a.g;
+    float2* stage = reinterpret_cast<float2*>(smem_raw);
+    float* up = reinterpret_cast<float*>(smem_raw + SB);  // [2][3][TY + 1][n1]
+    float2* w2 = reinterpret_cast<float2*>(up + 2 * NL * n1);
+    float2* tws = w2 + M;
+    double* red = reinterpret_cast<double*>(tws + M);
+    int* flag = reinterpret_cast<int*>(red + 256);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(flag + 4);
+    const int tid = threadIdx.x;
+    for (int k = tid; k < M; k += blockDim.x) {
+        w2[k] = a.tw2[k];
+        tws[k] = a.tw[k];
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        fence_proxy_async();
+    }
+    __syncthreads();
+
+    const int ncol = g.n2 / TY;
+    const int64_t total = (int64_t)ncol * g.n3p;
+    const int64_t lin_b = total * pj / gp, lin_e = total * (pj + 1) / gp;
+    const float alpha = (float)scp->alpha;
+    const float cx0 = a.cJ[0], cx1 = a.cJ[1], cx2 = a.cJ[2];
+    float* __restrict__ r = a.r;
+    const int64_t V = g.V;
+    // spectrum rows of node plane zn (local index, wraps) of the column at y0
+    auto issue = [&](int y0, int zn) {
+        const int zl = zn >= g.n3p ? zn - g.n3p : zn;
+        mbar_arrive_expect_tx(&bar[0], (uint32_t)SB);
+        for (int c = 0; c < 3; c++)
+            for (int ly = 0; ly <= TY; ly++) {
+                const int y = (y0 + ly >= g.n2) ? y0 + ly - g.n2 : y0 + ly;
+                const int64_t L = (int64_t)(pb * g.n3p + zl) * g.n2 + y;
+                bulk_g2s(stage + (size_t)(c * (TY + 1) + ly) * lsx, a.spec + 3 * c * g.Vs + L * g.nhp, lsx * 8,
+                         &bar[0]);
+            }
+    };
+    // FFT roles: line q of the node plane, tau of its TPL threads
+    const int q = tid / TPL, tau = tid - (tid / TPL) * TPL;
+    const bool act = q < NL;
+    // gradient roles: x pair tx of voxel lines lg, lg + LPB, ...
+    const int lg = tid / M, tx = tid - (tid / M) * M, x0 = 2 * tx;
+    const int x2 = (x0 + 2) & (n1 - 1);
+
+    double acc = 0.0;
+    uint32_t phase = 0;
+    bool timed_out = false;
+    for (int64_t lin = lin_b; lin < lin_e && !timed_out;) {
+        const int col = (int)(lin / g.n3p), z0 = (int)(lin - (int64_t)col * g.n3p);
+        const int z1 = (int)min((int64_t)g.n3p, z0 + (lin_e - lin));
+        lin += z1 - z0;
+        const int y0 = col * TY;
+        float accp = 0.f;
+        if (tid == 0) issue(y0, z0);
+        for (int zn = z0; zn <= z1; zn++) {
+            const int sl = (zn - z0) & 1;  // ring slot of this node plane
+            const bool ok = mbar_wait_bounded(&bar[0], phase, wait_cap_of(a.wait_cap));
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                timed_out = true;
+                break;
+            }
+            // node plane zn: packed inverse in place in the stage, real pairs
+            // into the ring
+            if (tid < NBAR) {
+                float2* X = stage + (size_t)(act ? q : 0) * lsx;
+                float* ug = up + ((size_t)sl * NL + (act ? q : 0)) * n1;
+                auto lgz = [&](int k) -> float2 {
+                    if (!act) return float2{0.f, 0.f};
+                    const float2 A = X[k];
+                    const float2 Bc = c_conj(X[M - k]);
+                    const float2 Ze = c_scale(c_add(A, Bc), 0.5f);
+                    const float2 Zo = c_mul(c_scale(c_sub(A, Bc), 0.5f), c_conj(w2[k]));
+                    return float2{Ze.x - Zo.y, Ze.y + Zo.x};
+                };
+                auto lx = [&](int e) -> float2 { return act ? X[e] : float2{0.f, 0.f}; };
+                auto sx = [&](int e, float2 v) {
+                    if (act) X[e] = v;
+                };
+                auto sg = [&](int e, float2 v) {
+                    if (act) *reinterpret_cast<float2*>(ug + 2 * e) = v;
+                };
+                fft_fast<float, M, true, true, false, NBAR>(lgz, sg, lx, sx, act ? tau : 0, tws);
+            }
+            fence_proxy_async();  // the stage's generic writes, before the next bulk copy
+            __syncthreads();
+            if (tid == 0 && zn < z1) issue(y0, zn + 1);
+            if (zn == z0) continue;
+            // voxel plane zn - 1 between ring slots sl ^ 1 (z) and sl (z + 1)
+            const int zv = zn - 1;
+            const int64_t zrow = (int64_t)(pb * g.n3p + zv) * g.n2;
+            const float* P0 = up + (size_t)(sl ^ 1) * NL * n1;
+            const float* P1 = up + (size_t)sl * NL * n1;
+            for (int ly = lg; ly < TY; ly += LPB) {
+                const int64_t o = (zrow + y0 + ly) * n1 + x0;
+                float2 rv[9];
+#pragma unroll
+                for (int c = 0; c < 9; c++) rv[c] = *reinterpret_cast<const float2*>(r + c * V + o);
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    const int ra = (i * (TY + 1) + ly) * n1, rb = ra + n1;  // node lines y, y + 1
+                    float A3[3], B3[3], C3[3], D3[3];  // (y, z), (y, z + 1), (y + 1, z), (y + 1, z + 1)
+                    A3[0] = P0[ra + x0], A3[1] = P0[ra + x0 + 1], A3[2] = P0[ra + x2];
+                    B3[0] = P1[ra + x0], B3[1] = P1[ra + x0 + 1], B3[2] = P1[ra + x2];
+                    C3[0] = P0[rb + x0], C3[1] = P0[rb + x0 + 1], C3[2] = P0[rb + x2];
+                    D3[0] = P1[rb + x0], D3[1] = P1[rb + x0 + 1], D3[2] = P1[rb + x2];
+                    float s0[3], s1[3], t0[3], t1[3];
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        s0[k] = A3[k] + B3[k];
+                        s1[k] = C3[k] + D3[k];
+                        t0[k] = A3[k] + C3[k];
+                        t1[k] = B3[k] + D3[k];
+                    }
+                    float F[3][2];
+#pragma unroll
+                    for (int p = 0; p < 2; p++) {
+                        F[0][p] = cx0 * ((s0[p + 1] + s1[p + 1]) - (s0[p] + s1[p]));
+                        F[1][p] = cx1 * ((s1[p] + s1[p + 1]) - (s0[p] + s0[p + 1]));
+                        F[2][p] = cx2 * ((t1[p] + t1[p + 1]) - (t0[p] + t0[p + 1]));
+                    }
+#pragma unroll
+                    for (int J = 0; J < 3; J++) {
+                        float2& qv = rv[3 * i + J];
+                        qv.x -= alpha * F[J][0];
+                        qv.y -= alpha * F[J][1];
+                        accp += qv.x * qv.x + qv.y * qv.y;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 9; c++) *reinterpret_cast<float2*>(r + c * V + o) = rv[c];
+            }
+            // (the ring slot read here is rewritten two node planes on, after
+            // the barrier that follows the next transform)
+        }
+        acc += (double)accp;
+    }
+    if (timed_out) {
+        if (tid == 0) {
+            raise_status(scp, COMBO_E_TIMEOUT);
+            mbar_wait_bounded(&bar[0], phase ^ 1u);  // the copy waited on, if it is still in flight
+        }
+        return;
+    }
+    if (a.partial) {
+        const double sacc = block_sum(acc, red);
+        if (tid == 0) a.partial[blockIdx.x] = sacc;
+        if (a.fuse && last_block(&scp->ticket[1], flag, gp)) {
+            const double tot = sum_partials_fixed(a.partial + (size_t)pb * gp, gp, red);
+            if (tid == 0) cg_beta(scp, tot, a.cg_tol, a.cg_max, a.cg_fixed);
+        }
+    }
+}
+
 // ------------------------------------------------------------- launchers
 template <int M> static void xinv_disp_launch(const DispArgs& a, cudaStream_t st)
 {
@@ -317,6 +510,36 @@ void launch_disp_grad_cg(const DispArgs& a, cudaStream_t st)
         case 64: disp_grad_launch<64>(a, st); break;
         case 128: disp_grad_launch<128>(a, st); break;
         default: disp_grad_launch<256>(a, st); break;
+    }
+}
+
+template <int M, int TY> static void xinv_grad_launch(const DispArgs& a, cudaStream_t st)
+{
+    constexpr size_t sm = fused_smem<M, TY>();
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(k_xinv_grad<M, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xinv_grad<M, TY>, 256, sm) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        per_sm = std::min(per_sm, 4);
+    }
+    const int64_t total = (int64_t)(a.g.n2 / TY) * a.g.n3p;
+    const int gp = (int)std::max<int64_t>(1, std::min<int64_t>(total, std::max(1, per_sm * num_sms_disp() / a.g.nprob)));
+    k_xinv_grad<M, TY><<<a.g.nprob * gp, 256, sm, st>>>(a);
+}
+
+bool xinv_grad_ok(const GridDims& g)
+{
+    return disp_x_ok(g) && g.n2 % (g.M == 256 ? 4 : 8) == 0;
+}
+
+void launch_xinv_grad(const DispArgs& a, cudaStream_t st)
+{
+    switch (a.g.M) {
+        case 64: xinv_grad_launch<64, fused_ty<64>()>(a, st); break;
+        case 128: xinv_grad_launch<128, fused_ty<128>()>(a, st); break;
+        default: xinv_grad_launch<256, fused_ty<256>()>(a, st); break;
     }
 }
 

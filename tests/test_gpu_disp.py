@@ -4,7 +4,7 @@ nine-component form of the same solve:
 
 * displacement form: the z-pass leaves one nodal spectrum per row, the
   y-inverse and x-inverse take three components, the HEX8R gradient is fused
-  with the CG update;
+  with the CG update (with the x-inverse too, where n2 allows its columns);
 * nodal form: in addition the tangent pass assembles the nodal forces
   D^T (A : p) in real space (halo lines and planes, two direction buffers),
   the y-forward takes three components and the z-pass divides by |kr|^2.
@@ -51,7 +51,7 @@ def classes(cb, p, **o):
 
 
 def form_of(cls):
-    return NODAL if "xfwd_nodal" in cls else (DISP if "grad_cg" in cls else 0)
+    return NODAL if "xfwd_nodal" in cls else (DISP if ("grad_cg" in cls or "xinv_grad_cg" in cls) else 0)
 
 
 def balls(n, seed=19, r=3.0):
@@ -69,7 +69,8 @@ def oracle_fixed(orc, p, kspace=0):
 
 # grids of every x size the forms take (n1 = 128, 256, 512), compile-time y
 # and z plans of both radix families, n2 = 108 (a multiple of 4, not of 8:
-# the nodal pass's 4-line columns at n1 = 256), and z = 512 (the 5-D tensor
+# the nodal pass's 4-line columns at n1 = 256, and the separate x-inverse and
+# gradient kernels instead of the fused one), and z = 512 (the 5-D tensor
 # maps of the one-component stores)
 GRIDS = [(128, 48, 72), (256, 64, 48), (512, 48, 48), (256, 108, 48), (128, 48, 512), (128, 96, 144)]
 
