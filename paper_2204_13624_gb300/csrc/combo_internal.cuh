@@ -599,7 +599,8 @@ struct NodalArgs {
     const int32_t* lofs;   // [n2 n3 + 1] first boxel (voxel order) of each x-line (L2 prefetch)
     int64_t nb;
     float cJ[3];           // 1 / (4 h_J)
-    int cfg;               // launch-shape candidate (0: one block per SM, 1: two)
+    int cfg;               // launch-shape candidate (0: equal plane chunks per column, 1: even shares)
+    int nch;               // (set by the launcher) plane chunks per column, or 0: even shares
     double* partial;       // pAp partials
     Scalars* sc;
     int fuse;              // the last block turns the pAp partials into alpha

@@ -13,10 +13,10 @@
 //   f_i(n) = sum over the 8 voxels v = n - b (b in {0,1}^3) of
 //            sum_J c_J s(b_J) (A : p)_iJ(v),   s(1) = +1, s(0) = -1, c_J = 1/(4 h_J)
 //
-// A block takes an even share of the problem's (column, plane) pairs in
-// column-major order, a column being TY node lines y0 .. y0 + TY - 1: one or
-// more runs of planes, each of which it marches along z; for each voxel plane
-// it sweeps the voxel
+// A block takes runs of planes of columns, a column being TY node lines
+// y0 .. y0 + TY - 1 -- equal chunks of planes per column, or an even share of
+// the problem's (column, plane) pairs -- and marches each run along z; for
+// each voxel plane it sweeps the voxel
 // lines y0 - 1 .. y0 + TY - 1 (the first one, and the plane below its first,
 // are halo: their A : p is formed but neither p, x nor pAp is written).  Per
 // voxel line: (1) the voxels' direction update p = r + beta p_old, the
@@ -53,9 +53,8 @@ int num_sms_nodal()
 
 // threads per block (one or two voxels of a line per thread) and blocks per SM
 template <int M> __host__ __device__ constexpr int nodal_threads() { return M == 64 ? 128 : 256; }
-// candidates: C = 1, two blocks per SM (registers capped at 128, a few
-// spill); C = 2, one block per SM (no cap)
-template <int M, int C> __host__ __device__ constexpr int nodal_minb() { return C == 2 ? 1 : 2; }
+// two blocks per SM (registers capped at 128, a few spill)
+template <int M, int C> __host__ __device__ constexpr int nodal_minb() { return 2; }
 // threads that transform the 3 TY nodal lines of a plane (named barrier 1)
 template <int M, int TY> __host__ __device__ constexpr int nodal_fft_threads()
 {
@@ -131,10 +130,30 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
 
     double acc = 0.0;
     int s = 0;  // voxel lines swept (line buffer parity)
-    for (int64_t lin = lin_b; lin < lin_e;) {
-        const int col = (int)(lin / g.n3p), z0 = (int)(lin - (int64_t)col * g.n3p);
-        const int z1 = (int)min((int64_t)g.n3p, z0 + (lin_e - lin));
-        lin += z1 - z0;
+    // this block's runs: its even share (nch == 0), or, with nch chunks of
+    // planes per column, items (chunk, column) in chunk-major order, so that
+    // neighbouring columns march through the same planes at the same time and
+    // a halo line is read while its owner's copy is still in L2
+    const int nitems = a.nch > 0 ? ncol * a.nch : 0;
+    int64_t lin = lin_b;
+    int item = pj;
+    for (;;) {
+        int col, z0, z1;
+        if (a.nch > 0) {
+            if (item >= nitems) break;
+            col = item % ncol;
+            const int ch = item / ncol;
+            z0 = (int)((int64_t)ch * g.n3p / a.nch);
+            z1 = (int)((int64_t)(ch + 1) * g.n3p / a.nch);
+            item += gp;
+            if (z1 <= z0) continue;
+        } else {
+            if (lin >= lin_e) break;
+            col = (int)(lin / g.n3p);
+            z0 = (int)(lin - (int64_t)col * g.n3p);
+            z1 = (int)min((int64_t)g.n3p, z0 + (lin_e - lin));
+            lin += z1 - z0;
+        }
         const int y0 = col * TY;
         float accp = 0.f;
         int vrc[VPT];  // vrank of this thread's voxels on the current voxel line
@@ -369,8 +388,18 @@ template <int M, int TY, int C> static void xfwd_nodal_launch(NodalArgs a, cudaS
     const int slots = per_sm * num_sms_nodal();
     // one resident block per share (each run of planes re-forms the voxel
     // plane below it as halo)
-    const int64_t total = (int64_t)(g.n2 / TY) * g.n3p;
-    const int gp = (int)std::max<int64_t>(1, std::min<int64_t>(total, std::max(1, slots / g.nprob)));
+    const int ncol = g.n2 / TY;
+    const int64_t total = (int64_t)ncol * g.n3p;
+    const int cap = std::max(1, slots / g.nprob);  // blocks per problem (partials: nodal_partials_max)
+    int gp;
+    if (a.cfg != 1 && ncol <= cap) {
+        // equal chunks of planes per column, one item per block
+        a.nch = std::max(1, std::min(g.n3p, cap / ncol));
+        gp = ncol * a.nch;
+    } else {
+        a.nch = 0;  // even shares, one block per resident slot
+        gp = (int)std::max<int64_t>(1, std::min<int64_t>(total, cap));
+    }
     k_xfwd_nodal<M, TY, C><<<g.nprob * gp, threads, sm, st>>>(a);
 }
 
@@ -388,13 +417,8 @@ template <int C> static void xfwd_nodal_pick(const NodalArgs& a, cudaStream_t st
     }
 }
 
-// candidate 0: one block per SM; 1: two
-void launch_xfwd_nodal(NodalArgs a, cudaStream_t st)
-{
-    if (a.cfg == 1)
-        xfwd_nodal_pick<1>(a, st);
-    else
-        xfwd_nodal_pick<2>(a, st);
-}
+// candidate 0: equal chunks of planes per column (neighbouring columns in
+// step); 1: an even share of the (column, plane) pairs per block
+void launch_xfwd_nodal(NodalArgs a, cudaStream_t st) { xfwd_nodal_pick<1>(a, st); }
 
 }  // namespace combo
