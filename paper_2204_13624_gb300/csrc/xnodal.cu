@@ -51,10 +51,11 @@ int num_sms_nodal()
     return nsm;
 }
 
-// threads per block (one or two voxels of a line per thread) and blocks per SM
-template <int M> __host__ __device__ constexpr int nodal_threads() { return M == 64 ? 128 : 256; }
-// two blocks per SM (registers capped at 128, a few spill)
-template <int M, int C> __host__ __device__ constexpr int nodal_minb() { return 2; }
+// threads per block: one voxel of a line per thread
+template <int M> __host__ __device__ constexpr int nodal_threads() { return 2 * M; }
+// blocks per SM: two of 256 (or 128) threads (registers capped at 128); one of
+// 512 at n1 = 512
+template <int M, int C> __host__ __device__ constexpr int nodal_minb() { return M == 256 ? 1 : 2; }
 // threads that transform the 3 TY nodal lines of a plane (named barrier 1)
 template <int M, int TY> __host__ __device__ constexpr int nodal_fft_threads()
 {
@@ -63,9 +64,9 @@ template <int M, int TY> __host__ __device__ constexpr int nodal_fft_threads()
 template <int M, int TY> __host__ __device__ constexpr size_t nodal_smem()
 {
     // line buffers [2][9][n1], T [3][TY][n1] floats; nodal lines [3 TY][M + 1]
-    // complex; twiddles [M]; reduction [256] doubles; flag
+    // complex; twiddles [M]; reduction [max(256, threads)] doubles; flag
     return (size_t)2 * 9 * 2 * M * 4 + (size_t)3 * TY * 2 * M * 4 + (size_t)3 * TY * (M + 1) * 8 + (size_t)M * 8 +
-           256 * 8 + 16;
+           (size_t)(2 * M > 256 ? 2 * M : 256) * 8 + 16;
 }
 
 }  // namespace
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(nodal_threads<M>(), (nodal_minb<M, C>())) k_xf
     float2* W = reinterpret_cast<float2*>(tp + 3 * TY * n1);  // [NLF][lsw]
     float2* tws = W + (size_t)NLF * lsw;  // exp(-2 pi i t / M)
     double* red = reinterpret_cast<double*>(tws + M);
-    int* flag = reinterpret_cast<int*>(red + 256);
+    int* flag = reinterpret_cast<int*>(red + (NT > 256 ? NT : 256));
     for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = a.tw[i];
 
     const GridDims g = a.g;
@@ -413,7 +414,12 @@ template <int C> static void xfwd_nodal_pick(const NodalArgs& a, cudaStream_t st
             else
                 xfwd_nodal_launch<128, 4, C>(a, st);
             break;
-        default: xfwd_nodal_launch<256, 4, C>(a, st); break;
+        default:
+            if (a.g.n2 % 8 == 0)
+                xfwd_nodal_launch<256, 8, C>(a, st);
+            else
+                xfwd_nodal_launch<256, 4, C>(a, st);
+            break;
     }
 }
 
