@@ -599,8 +599,9 @@ struct NodalArgs {
     const int32_t* lofs;   // [n2 n3 + 1] first boxel (voxel order) of each x-line (L2 prefetch)
     int64_t nb;
     float cJ[3];           // 1 / (4 h_J)
-    int cfg;               // launch-shape candidate (0: equal plane chunks per column, 1: even shares)
+    int cfg;               // launch-shape candidate (0: even shares, 1: equal plane chunks per column)
     int nch;               // (set by the launcher) plane chunks per column, or 0: even shares
+    int pfd;               // (set by the launcher) voxel lines ahead of the L2 prefetch
     double* partial;       // pAp partials
     Scalars* sc;
     int fuse;              // the last block turns the pAp partials into alpha
