@@ -534,6 +534,11 @@ int xpass_lines(const GridDims& g, size_t cxbytes);
 int xpass_grid(const GridDims& g, int lines);  // x-pass blocks (= partial count)
 int xpass_partials_max(const GridDims& g);     // upper bound of any x-pass grid
 int xpass_gp(const GridDims& g, int lines, int cap);  // x-pass blocks per problem (grid = nprob * gp)
+// Newton right-hand side r = -G[P] of the double-float residual, transformed in
+// FP32 (xpass.cu); tw32 / tw2_32: the FP32 engine's twiddles of the same grid
+bool xinv_rhs32_ok(const GridDims& g);
+void launch_xinv_rhs32(const XinvArgs<df32, float>& a, const cx<float>* tw32, const cx<float>* tw2_32, int guard,
+                       cudaStream_t st);
 int ypass_tx(int n, size_t cxbytes);  // columns per y-pass block (must match the launcher)
 int zpass_tx(int n, size_t cxbytes);  // columns per z-pass block (sets the partial count)
 int zpass_blocks(const GridDims& g, int tx, size_t cxbytes);  // non-TMA z-pass blocks (= partials) per problem

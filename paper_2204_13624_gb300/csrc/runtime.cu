@@ -1745,7 +1745,15 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         fin_resid(xi_mode);
         const auto xi = resid_xi(xi_mode);
         prof.begin(K_XINV_64);
-        launch_xinv<Rt, Tc>(xi, guard, st);
+        bool done = false;
+        if constexpr (std::is_same<Rt, df32>::value && std::is_same<Tc, float>::value) {
+            // the Newton right-hand side is an FP32 field: its transform in FP32
+            if (xi_mode == XI_RHS && xinv_rhs32_ok(g)) {
+                launch_xinv_rhs32(xi, ec.tab.twM, ec.tab.tw2, guard, st);
+                done = true;
+            }
+        }
+        if (!done) launch_xinv<Rt, Tc>(xi, guard, st);
         prof.end();
         if (xi_mode == XI_RHS) fin_rhs();
     }

@@ -655,6 +655,114 @@ template <typename T, typename Tc, int MF> static void xinv_launch(const XinvArg
     k_xinv<T, Tc, MF><<<grid, 256, sm, st>>>(a, guard);
 }
 
+// ------------------------------------------------------------- Newton right-hand side, FP32
+// The c2r of the double-float residual spectrum in the Newton right-hand-side
+// mode: r = -G[P] and x = 0 are FP32 words (the Krylov precision), so the
+// inverse transform runs in FP32 arithmetic on the double-float spectrum
+// rounded to FP32 (the residual norm that decides convergence is summed in
+// double-float by the z-pass).  Same groups, grid and partial sums as the
+// double-float x-inverse it replaces.
+template <int M>
+__global__ void __launch_bounds__(256) k_xinv_rhs32(XinvArgs<df32, float> a, const float2* __restrict__ tw32,
+                                                    const float2* __restrict__ tw2_32, int guard)
+{
+    const GridDims g = a.g;
+    int pb, pj, gp;
+    prob_block(g, blockIdx.x, gridDim.x, pb, pj, gp);
+    Scalars* sc = a.sc + pb;
+    if (guard == 1 && sc->cg_done) return;
+    if (guard == 2 && sc->outer_done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int LB = a.lines_per_block;
+    constexpr int ls = M + 1;
+    float2* buf0 = reinterpret_cast<float2*>(smem_raw);
+    float2* buf1 = buf0 + (size_t)9 * LB * ls;
+    double* red = reinterpret_cast<double*>(buf1 + (size_t)9 * LB * ls);
+    int* flag = reinterpret_cast<int*>(red + 256);
+    float2* tws = reinterpret_cast<float2*>(flag + 4);
+    for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = tw32[i];
+    const int nlp = g.n2 * g.n3p;
+    const int Lbase = pb * nlp, Lend = Lbase + nlp;
+    const int ngroups = (nlp + LB - 1) / LB;
+    const int nl = 9 * LB;
+    const int64_t V = g.V;
+    double acc = 0.0;
+    for (int grp = pj; grp < ngroups; grp += gp) {
+        const int L0 = Lbase + grp * LB;
+        // Z[k] = Ze + i Zo,  Ze = (X[k] + conj X[M-k]) / 2,  Zo = (X[k] - conj X[M-k]) W^{-k} / 2,
+        // from the spectrum rounded to FP32
+        for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
+            const int q = e / M, k = e - q * M;
+            const int c = q / LB, l = q - c * LB;
+            const int L = L0 + l;
+            float2 z{0.f, 0.f};
+            if (L < Lend) {
+                const cx<df32>* row = a.spec + c * g.Vs + (int64_t)L * g.nhp;
+                const cx<df32> xa = row[k], xb = row[M - k];
+                const float2 A{xa.x.hi + xa.x.lo, xa.y.hi + xa.y.lo};
+                const float2 Bc{xb.x.hi + xb.x.lo, -(xb.y.hi + xb.y.lo)};
+                const float2 Ze = c_scale(c_add(A, Bc), 0.5f);
+                const float2 Zo = c_mul(c_scale(c_sub(A, Bc), 0.5f), c_conj(tw2_32[k]));
+                z = float2{Ze.x - Zo.y, Ze.y + Zo.x};
+            }
+            buf1[(size_t)q * ls + k] = z;
+        }
+        __syncthreads();
+        const float2* Zr = fft_lines_fast<float, M, true>(buf1, buf0, nl, ls, tws);
+        const float* rb = reinterpret_cast<const float*>(Zr);
+        float accp = 0.f;
+        for (int e = threadIdx.x; e < LB * g.n1; e += blockDim.x) {
+            const int l = e / g.n1, x = e - l * g.n1;
+            const int L = L0 + l;
+            if (L >= Lend) continue;
+            const int64_t v = (int64_t)L * g.n1 + x;
+#pragma unroll
+            for (int c = 0; c < 9; c++) {
+                const float rn = -rb[(size_t)2 * (c * LB + l) * ls + x];
+                a.r[c * V + v] = rn;
+                a.x[c * V + v] = 0.f;
+                accp += rn * rn;
+            }
+        }
+        acc += (double)accp;
+        __syncthreads();  // the next group reuses the shared buffers
+    }
+    if (a.partial) {
+        const double s2 = block_sum(acc, red);
+        if (threadIdx.x == 0) a.partial[blockIdx.x] = s2;
+    }
+}
+
+template <int M> static void xinv_rhs32_launch(const XinvArgs<df32, float>& a, const cx<float>* tw32,
+                                               const cx<float>* tw2_32, int guard, cudaStream_t st)
+{
+    const int grid = xpass_grid(a.g, a.lines_per_block);
+    const size_t sm = xpass_smem(a.g, a.lines_per_block, sizeof(cx<float>));
+    static bool attr = false;
+    allow_smem(k_xinv_rhs32<M>, attr);
+    k_xinv_rhs32<M><<<grid, 256, sm, st>>>(a, tw32, tw2_32, guard);
+}
+
+bool xinv_rhs32_ok(const GridDims& g) { return fast_size_x(g.M) || fast3_size_x(g.M); }
+
+void launch_xinv_rhs32(const XinvArgs<df32, float>& a, const cx<float>* tw32, const cx<float>* tw2_32, int guard,
+                       cudaStream_t st)
+{
+    switch (a.g.M) {
+        case 24: xinv_rhs32_launch<24>(a, tw32, tw2_32, guard, st); break;
+        case 32: xinv_rhs32_launch<32>(a, tw32, tw2_32, guard, st); break;
+        case 36: xinv_rhs32_launch<36>(a, tw32, tw2_32, guard, st); break;
+        case 48: xinv_rhs32_launch<48>(a, tw32, tw2_32, guard, st); break;
+        case 54: xinv_rhs32_launch<54>(a, tw32, tw2_32, guard, st); break;
+        case 64: xinv_rhs32_launch<64>(a, tw32, tw2_32, guard, st); break;
+        case 72: xinv_rhs32_launch<72>(a, tw32, tw2_32, guard, st); break;
+        case 96: xinv_rhs32_launch<96>(a, tw32, tw2_32, guard, st); break;
+        case 108: xinv_rhs32_launch<108>(a, tw32, tw2_32, guard, st); break;
+        case 128: xinv_rhs32_launch<128>(a, tw32, tw2_32, guard, st); break;
+        default: xinv_rhs32_launch<256>(a, tw32, tw2_32, guard, st); break;
+    }
+}
+
 template <typename T, typename Tc> void launch_xinv(const XinvArgs<T, Tc>& a, int guard, cudaStream_t st)
 {
     if constexpr (std::is_same<T, float>::value && std::is_same<Tc, float>::value) {
