@@ -473,6 +473,11 @@ template <typename T> struct YArgs {
     int cfg;           // launch-shape candidate (autotuner; 0 = default)
     uint32_t wait_cap;  // poll cap of the tile waits (wait_cap_of: 0 = default)
     int disp;           // TMA y-inverse: only components 0, 3, 6 (displacement form)
+    // (double-float words, inverse) the transform in FP32 arithmetic on the
+    // values rounded to FP32, stored back as double-float with a zero low
+    // word: the Newton right-hand side, an FP32 field; tw32: FP32 twiddles
+    int inv32;
+    const cx<float>* tw32;
 };
 
 template <typename T> struct ZArgs {
@@ -499,6 +504,10 @@ template <typename T> struct ZArgs {
     int disp;
     const void* tmap_u;
     const cx<T>* rph[3];
+    // (double-float words) the inverse z transform in FP32 arithmetic, as the
+    // y-pass's inv32; the projection and the norm stay double-float
+    int inv32;
+    const cx<float>* tw32;
 };
 
 // Grouped launches: one persistent launch runs the work items of several

@@ -590,11 +590,18 @@ template <typename T> struct Engine {
         return z;
     }
     // y forward, z forward + projection + z inverse, y inverse
+    // inv32 (double-float words): the inverse z and y transforms in FP32
+    // arithmetic (the output feeds an FP32 field); tw32y / tw32z: FP32
+    // twiddles of the same sides
     void yz(Scalars* sc, int guard, bool want_norm, double* partial, cudaStream_t st, Profiler* pr = nullptr,
-            int kbase = 0) const
+            int kbase = 0, bool inv32 = false, const cx<float>* tw32y = nullptr, const cx<float>* tw32z = nullptr) const
     {
-        const ZArgs<T> z = zargs(sc, guard, want_norm, partial);
+        ZArgs<T> z = zargs(sc, guard, want_norm, partial);
         YArgs<T> y = yargs(sc, guard);
+        if (inv32 && tw32y && tw32z) {
+            z.inv32 = 1;
+            z.tw32 = tw32z;
+        }
         y.disp = (z.disp == 2) ? 1 : 0;  // the nodal form's forward spectrum: components 0, 3, 6
         if (pr) pr->begin(kbase);
         launch_ypass<T, false>(y, st);
@@ -611,6 +618,10 @@ template <typename T> struct Engine {
         if (pr) pr->end();
         YArgs<T> yi = y;
         yi.disp = z.disp ? 1 : 0;  // the displacement and nodal forms leave components 0, 3, 6 only
+        if (inv32 && tw32y && tw32z) {
+            yi.inv32 = 1;
+            yi.tw32 = tw32y;
+        }
         if (pr) pr->begin(kbase + 2);
         launch_ypass<T, true>(yi, st);
         if (pr) pr->end();
@@ -1741,7 +1752,15 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         prof.begin(K_XFWD_RESID);
         launch_xfwd<Rt, Tc>(xf, guard, st);
         prof.end();
-        e64.yz(d_sc, guard, true, d_part, st, &prof, K_YFWD_64);
+        // the Newton right-hand side is an FP32 field: in the double-float
+        // form its inverse transforms run in FP32 (the norm stays double-float)
+        bool inv32 = false;
+        if constexpr (std::is_same<Rt, df32>::value && std::is_same<Tc, float>::value)
+            inv32 = xi_mode == XI_RHS && xinv_rhs32_ok(g);
+        if constexpr (std::is_same<Tc, float>::value)
+            e64.yz(d_sc, guard, true, d_part, st, &prof, K_YFWD_64, inv32, ec.tab.twy, ec.tab.twz);
+        else
+            e64.yz(d_sc, guard, true, d_part, st, &prof, K_YFWD_64);
         fin_resid(xi_mode);
         const auto xi = resid_xi(xi_mode);
         prof.begin(K_XINV_64);

@@ -75,6 +75,23 @@ __device__ __forceinline__ void ypass_fast_body(const YArgs<T>& a, const VBlock&
     const bool valid = x0 + line < g.nh;
     cx<T>* base = a.spec + bi.z * g.Vs + (int64_t)bi.y * N * g.nhp + x0 + line;
     const int64_t st = g.nhp;
+    if constexpr (std::is_same<T, df32>::value && INV) {
+        if (a.inv32) {
+            float2* ex32 = reinterpret_cast<float2*>(smem_raw);
+            fft_fast<float, N, true>(
+                [&](int e) {
+                    if (!valid) return float2{0.f, 0.f};
+                    const cx<df32> v = base[e * st];
+                    return float2{v.x.hi + v.x.lo, v.y.hi + v.y.lo};
+                },
+                [&](int e, float2 v) {
+                    if (valid) base[e * st] = cx<df32>{df32(v.x, 0.f), df32(v.y, 0.f)};
+                },
+                [&](int e) { return ex32[e * TX + line]; }, [&](int e, float2 v) { ex32[e * TX + line] = v; }, tau,
+                a.tw32);
+            return;
+        }
+    }
     fft_fast<T, N, INV>([&](int e) { return valid ? base[e * st] : cx<T>{(T)0, (T)0}; },
                         [&](int e, cx<T> v) {
                             if (valid) base[e * st] = v;
@@ -284,11 +301,31 @@ __device__ __forceinline__ void zpass_fast_body(const ZArgs<T>& a, const VBlock&
     __syncthreads();
 
     // inverse along z from the tile (in place: barrier inside the first stage)
-    fft_fast<T, N, true, true, false>(lp,
-                                      [&](int e, cx<T> v) {
-                                          if (valid) bc[e * zst] = v;
-                                      },
-                                      lp, sp, tau, a.tw);
+    bool inv_done = false;
+    if constexpr (std::is_same<T, df32>::value) {
+        if (a.inv32) {
+            // in FP32 on the rounded values: the first stage converts from the
+            // double-float tile, the later ones use an FP32 view of it (the
+            // barrier inside the first stage orders every load before it)
+            float2* pc32 = reinterpret_cast<float2*>(park) + c * N * TX + line;
+            fft_fast<float, N, true, true, false>(
+                [&](int e) {
+                    const cx<df32> v = pc[e * TX];
+                    return float2{v.x.hi + v.x.lo, v.y.hi + v.y.lo};
+                },
+                [&](int e, float2 v) {
+                    if (valid) bc[e * zst] = cx<df32>{df32(v.x, 0.f), df32(v.y, 0.f)};
+                },
+                [&](int e) { return pc32[e * TX]; }, [&](int e, float2 v) { pc32[e * TX] = v; }, tau, a.tw32);
+            inv_done = true;
+        }
+    }
+    if (!inv_done)
+        fft_fast<T, N, true, true, false>(lp,
+                                          [&](int e, cx<T> v) {
+                                              if (valid) bc[e * zst] = v;
+                                          },
+                                          lp, sp, tau, a.tw);
     if (a.want_norm && a.partial) {
         const double s = block_sum(acc, red);
         if (threadIdx.x == 0) a.partial[bi.linear()] = s;
