@@ -250,6 +250,45 @@ __device__ __forceinline__ bool hessian_inv(const LamEvalD& e, double cp, double
     return true;
 }
 
+// The same FP32 inverse from an FP64 laminate state: the Delta^{-1} of the
+// FP32 boxel tangent (the tangent only feeds the FP32 Krylov iterations).
+// False where hessian_inv is false; the caller then inverts in FP64.
+__device__ __forceinline__ bool hessian_inv32(const LamEval& e, double cp, double cm, const double mu[2],
+                                              const double lam[2], double Di[9])
+{
+    const float wp = (float)(1.0 / cp), wm = (float)(1.0 / cm);
+    const float d = (float)mu[1] * wp + (float)mu[0] * wm;
+    const float id0 = 1.f / d;
+    const float sp = ((float)lam[1] + (float)mu[1] - (float)lam[1] * (float)e.p.lnJ) * wp * id0;
+    const float sm = ((float)lam[0] + (float)mu[0] - (float)lam[0] * (float)e.m.lnJ) * wm * id0;
+    const float gp[3] = {(float)e.p.g[0], (float)e.p.g[1], (float)e.p.g[2]};
+    const float gm[3] = {(float)e.m.g[0], (float)e.m.g[1], (float)e.m.g[2]};
+    const float gp2 = gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2];
+    const float gm2 = gm[0] * gm[0] + gm[1] * gm[1] + gm[2] * gm[2];
+    if (!(fabsf(sp) * gp2 <= 1e4f && fabsf(sm) * gm2 <= 1e4f)) return false;
+    float A[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) A[3 * i + k] = (i == k ? 1.f : 0.f) + sp * gp[i] * gp[k] + sm * gm[i] * gm[k];
+    const float c0 = A[4] * A[8] - A[5] * A[7];
+    const float c1 = A[5] * A[6] - A[3] * A[8];
+    const float c2 = A[3] * A[7] - A[4] * A[6];
+    const float det = A[0] * c0 + A[1] * c1 + A[2] * c2;
+    if (det == 0.f || !isfinite(det)) return false;
+    const float id = id0 / det;
+    Di[0] = c0 * id;
+    Di[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    Di[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    Di[3] = c1 * id;
+    Di[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    Di[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    Di[6] = c2 * id;
+    Di[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    Di[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    return true;
+}
+
 // One Neo-Hookean phase's tangent data in precision S:
 //   A_iJkL     = mu d_ik d_JL + lam G_Ji G_Lk + m G_Jk G_Li,   m = mu - lam ln J
 //   (A D)_(iJ),k = mu d_ik N_J + lam G_Ji g_k + m G_Jk g_i,     g = G^T N
@@ -494,9 +533,15 @@ template <typename Tc, bool DFM> __device__ __forceinline__ void boxel_body(cons
 #pragma unroll
             for (int i = 0; i < 3; i++) A.ba[3 * b + i] = a[i];
             if (A.bA) {
+                // (an FP32 tangent takes Delta^{-1} in FP32, off the FP64 pipe)
+                bool inv_ok = false;
+                if (!df_done) {
+                    if constexpr (sizeof(Tc) == 4) inv_ok = hessian_inv32(e, cp, cm, mu, lam, Di);
+                    if (!inv_ok) inv_ok = inv64(e, Di);
+                }
                 if (df_done) {
                     tangent(ed.p, ed.m);
-                } else if (!inv64(e, Di)) {
+                } else if (!inv_ok) {
                     raise_status(sc, COMBO_E_LAMINATE);
                 } else {
                     tangent(e.p, e.m);
