@@ -409,8 +409,9 @@ int combo_server_stats(combo_server* s, combo_serving_stats* st);
  * the process times the candidate launch shapes of each FP32 Krylov pass
  * (pass 0 tangent x-forward: 128- or 256-thread blocks, or in the nodal
  * form of the operator even shares of the (column, plane) pairs per block
- * or equal chunks of planes per column; 1 y-pass and 2
- * z-pass: two TMA tile widths; 3 CG x-inverse: one or two x-lines per group)
+ * or equal chunks of planes per column; 1 y-pass and 2 z-pass: two TMA
+ * tile widths, of the scalar z-pass in the nodal form; 3 CG x-inverse: one
+ * or two x-lines per group)
  * on the solve's own buffers before its first iteration, and every later
  * solve of that grid uses the fastest.  Shapes change no result beyond
  * floating-point summation order.

@@ -626,7 +626,8 @@ int nodal_partials_max();  // largest grid of the nodal tangent pass
 // z-pass of the nodal form: one component per tile (components 0, 3, 6),
 // forward z FFT, scale / |kr|^2, inverse z FFT (tmap_u: one-component box)
 void launch_zpass_scalar(const ZArgs<float>& a, cudaStream_t st);
-bool zpass_scalar_encode(void* map, const GridDims& g, const void* spec);  // its map (box {16 or 8, 1, n3, 1})
+// its map for tile-width candidate cand (box {16 or 8 (at 512), 1, n3, 1}, halved for cand 1)
+bool zpass_scalar_encode(void* map, const GridDims& g, const void* spec, int cand);
 
 bool disp_x_ok(const GridDims& g);  // sizes the two x kernels take
 void launch_xinv_disp(const DispArgs& a, cudaStream_t st);

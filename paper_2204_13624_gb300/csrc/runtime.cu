@@ -461,8 +461,8 @@ template <typename T> struct Engine {
     int use_disp = 0;
     // nodal form (the tangent pass assembles nodal forces): the scalar
     // z-pass's map and the switch (set per solve)
-    CUtensorMap zsmap;
-    bool zsmap_ok = false;
+    CUtensorMap zsmap[2];
+    bool zsmap_ok[2] = {false, false};
     int use_nodal = 0;
     // launch-shape candidates chosen by the autotuner: x-forward, y, z, x-inverse
     int cfg_xf = 0, cfg_y = 0, cfg_z = 0, cfg_xi = 0;
@@ -475,7 +475,8 @@ template <typename T> struct Engine {
             ymap_ok[c] = (sizeof(T) == 4) && ypass_tma_encode(&ymap[c], g, s, c);
             zumap_ok[c] = (sizeof(T) == 4) && tab.rph[0] && zpass_tma_encode_u(&zumap[c], g, s, c);
         }
-        zsmap_ok = (sizeof(T) == 4) && tab.rph[0] && zpass_scalar_encode(&zsmap, g, s);
+        for (int c = 0; c < 2; c++)
+            zsmap_ok[c] = (sizeof(T) == 4) && tab.rph[0] && zpass_scalar_encode(&zsmap[c], g, s, c);
         if (!zmap_ok[cfg_z]) cfg_z = 0;
         if (!ymap_ok[cfg_y]) cfg_y = 0;
     }
@@ -515,7 +516,7 @@ template <typename T> struct Engine {
     // FP32 spectrum (free once the z-pass has read them), V floats each
     float* disp_u() const { return reinterpret_cast<float*>(spec + g.Vs); }
     // the nodal form applies on top: its tangent pass and scalar z-pass
-    bool nodal_capable() const { return disp_capable() && zsmap_ok && nodal_ok(g); }
+    bool nodal_capable() const { return disp_capable() && zsmap_ok[cfg_z] && nodal_ok(g); }
     int64_t disp_ustride() const { return 3 * 2 * g.Vs; }
 
     template <typename Tc> XfwdArgs<T, Tc> xf() const
@@ -579,9 +580,9 @@ template <typename T> struct Engine {
         z.cfg = cfg_z;
         z.tmap = zmap_ok[cfg_z] ? &zmap[cfg_z] : nullptr;
         z.wait_cap = wait_cap;
-        if (use_nodal && guard == 1 && !want_norm && zsmap_ok) {
+        if (use_nodal && guard == 1 && !want_norm && zsmap_ok[cfg_z]) {
             z.disp = 2;  // nodal form: scalar z-pass on components 0, 3, 6
-            z.tmap_u = &zsmap;
+            z.tmap_u = &zsmap[cfg_z];
         } else if (use_disp && guard == 1 && !want_norm && z.tmap && zumap_ok[cfg_z]) {
             z.disp = 1;
             z.tmap_u = &zumap[cfg_z];
@@ -1395,7 +1396,7 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
         ec.bind_spec(d_spec);
         // the nodal form's second direction buffer, where that form may apply
         if (newton() && !dfmg() && (!member || own_launches) && g_krylov_form.load() >= COMBO_KRYLOV_NODAL &&
-            ec.zsmap_ok && nodal_ok(g))
+            ec.zsmap_ok[0] && nodal_ok(g))
         {
             CK(dev_malloc(&d_p2, sizeof(Tc) * 9 * V));
             CK(dev_malloc(&d_vrank, 4 * V));
@@ -1569,8 +1570,19 @@ template <typename Tc, typename Rt = double> struct Solve : SolveBase {
             z0.tmap = ec.zmap_ok[0] ? &ec.zmap[0] : nullptr;
             z1.cfg = 1;
             z1.tmap = ec.zmap_ok[1] ? &ec.zmap[1] : nullptr;
-            time_pair([&] { launch_zpass<Tc>(z0, st); }, [&] { launch_zpass<Tc>(z1, st); }, z1.tmap != nullptr,
-                      rec.ms[2]);
+            if (nodal_pass) {
+                // the nodal form's scalar z-pass: its two tile widths
+                ZArgs<Tc> s0 = z0, s1 = z1;
+                s0.disp = s1.disp = 2;
+                s0.tmap_u = ec.zsmap_ok[0] ? &ec.zsmap[0] : nullptr;
+                s1.tmap_u = ec.zsmap_ok[1] ? &ec.zsmap[1] : nullptr;
+                if (s0.tmap_u)
+                    time_pair([&] { launch_zpass_scalar(s0, st); }, [&] { launch_zpass_scalar(s1, st); },
+                              s1.tmap_u != nullptr, rec.ms[2]);
+            } else {
+                time_pair([&] { launch_zpass<Tc>(z0, st); }, [&] { launch_zpass<Tc>(z1, st); }, z1.tmap != nullptr,
+                          rec.ms[2]);
+            }
             // CG x-inverse
             auto xi = ec.template xi<Tc>();
             xi.mode = XI_CG;

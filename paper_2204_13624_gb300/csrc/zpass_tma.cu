@@ -514,13 +514,14 @@ void launch_zpass_tma(const ZArgs<float>& a, const void* map, cudaStream_t st)
 // nodal forces f_i), all N z-planes, one y and TX x-frequencies (box {TX, 1,
 // N, 1}); forward z FFT, multiplication by scale / |kr|^2 (zero where |kr| is
 // zero), inverse z FFT, in place, then one TMA store.
-__host__ __device__ constexpr int tma_txs(int n) { return n > 256 ? 8 : 16; }
+// tile width: candidate 0 (default) or 1 (half as wide; autotuner)
+__host__ __device__ constexpr int tma_txs(int n, int c = 0) { return (n > 256 ? 8 : 16) >> c; }
 
-bool zpass_scalar_encode(void* map, const GridDims& g, const void* spec)
+bool zpass_scalar_encode(void* map, const GridDims& g, const void* spec, int cand)
 {
     if (!zpass_tma_size(g.n3p) || !spec) return false;
     if ((g.nhp * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(spec) & 15) != 0) return false;
-    const cuuint32_t box[4] = {(cuuint32_t)tma_txs(g.n3p), 1, (cuuint32_t)g.n3p, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)tma_txs(g.n3p, cand), 1, (cuuint32_t)g.n3p, 1};
     return encode_spec_map(map, g, spec, box, g.n3p > 256 ? 2 : -1);
 }
 
@@ -629,9 +630,9 @@ __global__ void __launch_bounds__(TX * FastPlan<N>::TPL)
     }
 }
 
-template <int N> static void zpass_scalar_launch(const ZArgs<float>& a, cudaStream_t st)
+template <int N, int C> static void zpass_scalar_launch(const ZArgs<float>& a, cudaStream_t st)
 {
-    constexpr int TX = tma_txs(N);
+    constexpr int TX = tma_txs(N, C);
     constexpr int threads = TX * FastPlan<N>::TPL;
     const size_t sm = (size_t)2 * N * TX * 8 + 16 + (size_t)N * 8;
     static int grid_per_sm = 0;
@@ -652,21 +653,30 @@ template <int N> static void zpass_scalar_launch(const ZArgs<float>& a, cudaStre
     k_zpass_scalar<N, TX><<<grid, threads, sm, st>>>(*reinterpret_cast<const CUtensorMap*>(a.tmap_u), a);
 }
 
-void launch_zpass_scalar(const ZArgs<float>& a, cudaStream_t st)
+template <int C> static void zpass_scalar_pick(const ZArgs<float>& a, cudaStream_t st)
 {
     switch (a.g.n3p) {
-        case 48: zpass_scalar_launch<48>(a, st); break;
-        case 64: zpass_scalar_launch<64>(a, st); break;
-        case 72: zpass_scalar_launch<72>(a, st); break;
-        case 96: zpass_scalar_launch<96>(a, st); break;
-        case 108: zpass_scalar_launch<108>(a, st); break;
-        case 128: zpass_scalar_launch<128>(a, st); break;
-        case 144: zpass_scalar_launch<144>(a, st); break;
-        case 192: zpass_scalar_launch<192>(a, st); break;
-        case 216: zpass_scalar_launch<216>(a, st); break;
-        case 256: zpass_scalar_launch<256>(a, st); break;
-        default: zpass_scalar_launch<512>(a, st); break;
+        case 48: zpass_scalar_launch<48, C>(a, st); break;
+        case 64: zpass_scalar_launch<64, C>(a, st); break;
+        case 72: zpass_scalar_launch<72, C>(a, st); break;
+        case 96: zpass_scalar_launch<96, C>(a, st); break;
+        case 108: zpass_scalar_launch<108, C>(a, st); break;
+        case 128: zpass_scalar_launch<128, C>(a, st); break;
+        case 144: zpass_scalar_launch<144, C>(a, st); break;
+        case 192: zpass_scalar_launch<192, C>(a, st); break;
+        case 216: zpass_scalar_launch<216, C>(a, st); break;
+        case 256: zpass_scalar_launch<256, C>(a, st); break;
+        default: zpass_scalar_launch<512, C>(a, st); break;
     }
+}
+
+// (a.tmap_u: the map encoded for the candidate a.cfg selects)
+void launch_zpass_scalar(const ZArgs<float>& a, cudaStream_t st)
+{
+    if (a.cfg == 1)
+        zpass_scalar_pick<1>(a, st);
+    else
+        zpass_scalar_pick<0>(a, st);
 }
 
 }  // namespace combo
