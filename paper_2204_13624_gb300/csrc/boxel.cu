@@ -61,17 +61,20 @@ struct LamEval {
     double err, eps;
 };
 
-__device__ __forceinline__ bool lam_eval(LamEval& e, const double Fb[9], const double N[3], double cp, double cm,
+// (icp, icm = 1/c+, 1/c-: the jump enters as (a/c) (x) N)
+__device__ __forceinline__ bool lam_eval(LamEval& e, const double Fb[9], const double N[3], double icp, double icm,
                                          const double a[3], const double mu[2], const double lam[2], double tol_rel,
                                          double tol_abs)
 {
 #pragma unroll
-    for (int i = 0; i < 3; i++)
+    for (int i = 0; i < 3; i++) {
+        const double ap = a[i] * icp, am = a[i] * icm;
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            e.p.F[3 * i + j] = Fb[3 * i + j] + a[i] * N[j] / cp;
-            e.m.F[3 * i + j] = Fb[3 * i + j] - a[i] * N[j] / cm;
+            e.p.F[3 * i + j] = Fb[3 * i + j] + ap * N[j];
+            e.m.F[3 * i + j] = Fb[3 * i + j] - am * N[j];
         }
+    }
     if (!nh_phase(e.p, mu[1], lam[1], N)) return false;
     if (!nh_phase(e.m, mu[0], lam[0], N)) return false;
     double tp = 0.0, tm = 0.0, ff = 0.0;
@@ -89,11 +92,10 @@ __device__ __forceinline__ bool lam_eval(LamEval& e, const double Fb[9], const d
     return true;
 }
 
-// Delta = sum_phase (1/c) [mu I + (lam + mu - lam ln J) g g^T]   (|N| = 1)
-__device__ __forceinline__ void hessian(const LamEval& e, double cp, double cm, const double mu[2],
+// Delta = sum_phase (1/c) [mu I + (lam + mu - lam ln J) g g^T]   (|N| = 1; wp, wm = 1/c+, 1/c-)
+__device__ __forceinline__ void hessian(const LamEval& e, double wp, double wm, const double mu[2],
                                         const double lam[2], double D[9])
 {
-    const double wp = 1.0 / cp, wm = 1.0 / cm;
     const double sp = (lam[1] + mu[1] - lam[1] * e.p.lnJ) * wp;
     const double sm = (lam[0] + mu[0] - lam[0] * e.m.lnJ) * wm;
     const double d = mu[1] * wp + mu[0] * wm;
@@ -125,18 +127,42 @@ __device__ __forceinline__ bool inv3(const double A[9], double B[9])
 }
 
 // ---- double-float form of the laminate solve (refined precision form with
-// double-float residuals): the phase states F, F^{-1}, J and P and the
-// traction residual f in df32, ln J in df32 (df_log, kept as FP64), the Hessian and its inverse in
-// FP32 (a Newton direction needs no more), the jump a and the back-projection
-// in FP64.  These iterations stop at the rounding level of the df32 residual;
-// the FP64 residual then decides convergence.
+// double-float residuals): the jump a, the phase states F, F^{-1}, J, ln J
+// and P and the traction residual f in df32 (ln J by df_log), the Hessian,
+// its inverse, the Newton direction and the admissibility test of
+// Algorithm 2 in FP32.  The iterations run on the FP32 pipe alone (the
+// per-boxel constants are split once) and stop at the rounding level of the
+// df32 residual; the FP64 residual then decides convergence.
 struct PhaseD {
-    df32 F[9], G[9], P[9], J;
+    df32 F[9], G[9], P[9], J, lnJ;
     float g[3];  // G^T N
-    double lnJ;
 };
 
-__device__ __forceinline__ bool nh_phase_df(PhaseD& s, double mu, double lam, const df32 N[3], double* gd = nullptr)
+// Per-boxel constants of the double-float iterations: the phase constants
+// (0 matrix, 1 inclusion) split into df32, and the stopping test
+// |f| <= tol_rel (|P+ N| + |P- N|) + eps_abs with the rounding level
+// floor_scale (1 + |P+ N| + |P- N|) of f.
+struct DfLam {
+    df32 mu[2], lam[2];
+    float tol_rel, eps_abs, floor_scale;
+};
+
+__device__ __forceinline__ DfLam df_lam(const double mu[2], const double lam[2], double tol_rel, double tol_abs)
+{
+    DfLam k;
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        k.mu[i] = df32(mu[i]);
+        k.lam[i] = df32(lam[i]);
+    }
+    k.tol_rel = (float)tol_rel;
+    k.eps_abs = (float)(tol_abs * fmax(mu[0], mu[1]));
+    // P = mu F + k F^{-T} is formed from terms of size ~(mu + lam) |F|: 2^-44 of that
+    k.floor_scale = (float)(0x1p-44 * (fmax(mu[0], mu[1]) + fmax(lam[0], lam[1])));
+    return k;
+}
+
+__device__ __forceinline__ bool nh_phase_df(PhaseD& s, df32 mud, df32 lamd, const df32 N[3], double* gd = nullptr)
 {
     const df32* F = s.F;
     const df32 c0 = F[4] * F[8] - F[5] * F[7];
@@ -155,9 +181,8 @@ __device__ __forceinline__ bool nh_phase_df(PhaseD& s, double mu, double lam, co
     s.G[6] = c2 * iJ;
     s.G[7] = (F[1] * F[6] - F[0] * F[7]) * iJ;
     s.G[8] = (F[0] * F[4] - F[1] * F[3]) * iJ;
-    const df32 lnJd = df_log(J), mud = df32(mu);
-    s.lnJ = (double)lnJd;
-    const df32 k = df32(lam) * lnJd - mud;
+    s.lnJ = df_log(J);
+    const df32 k = lamd * s.lnJ - mud;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
 #pragma unroll
@@ -171,98 +196,71 @@ __device__ __forceinline__ bool nh_phase_df(PhaseD& s, double mu, double lam, co
 
 struct LamEvalD {
     PhaseD p, m;
-    double f[3];
-    double err, eps;
-    double tol;    // the laminate tolerance (eps before the rounding-level floor)
-    double floor;  // rounding level of f in double-float: below it only FP64 can decide
+    float f[3];
+    float err, eps;
+    float tol;    // the laminate tolerance (eps before the rounding-level floor)
+    float floor;  // rounding level of f in double-float: below it only FP64 can decide
 };
 
 __device__ __forceinline__ bool lam_eval(LamEvalD& e, const df32 Fb[9], const df32 N[3], df32 icp, df32 icm,
-                                         const double a[3], const double mu[2], const double lam[2], double tol_rel,
-                                         double tol_abs)
+                                         const df32 a[3], const DfLam& k)
 {
-    const df32 ad[3] = {df32(a[0]), df32(a[1]), df32(a[2])};
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            const df32 t = ad[i] * N[j];
+            const df32 t = a[i] * N[j];
             e.p.F[3 * i + j] = Fb[3 * i + j] + t * icp;
             e.m.F[3 * i + j] = Fb[3 * i + j] - t * icm;
         }
-    if (!nh_phase_df(e.p, mu[1], lam[1], N)) return false;
-    if (!nh_phase_df(e.m, mu[0], lam[0], N)) return false;
+    if (!nh_phase_df(e.p, k.mu[1], k.lam[1], N)) return false;
+    if (!nh_phase_df(e.m, k.mu[0], k.lam[0], N)) return false;
     float tp = 0.f, tm = 0.f, ff = 0.f;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         const df32 a1 = e.p.P[3 * i] * N[0] + e.p.P[3 * i + 1] * N[1] + e.p.P[3 * i + 2] * N[2];
         const df32 a2 = e.m.P[3 * i] * N[0] + e.m.P[3 * i + 1] * N[1] + e.m.P[3 * i + 2] * N[2];
         const df32 fi = a1 - a2;
-        e.f[i] = (double)fi;
+        e.f[i] = (float)fi;
         tp += a1.hi * a1.hi;
         tm += a2.hi * a2.hi;
         ff += fi.hi * fi.hi;
     }
-    e.err = (double)sqrtf(ff);
-    e.eps = tol_rel * ((double)sqrtf(tp) + (double)sqrtf(tm)) + tol_abs * fmax(mu[0], mu[1]);
-    e.tol = e.eps;
-    // P = mu F + k F^{-T} is formed from terms of size ~(mu + lam) |F|: 2^-44 of that
-    e.floor = 0x1p-44 * (fmax(mu[0], mu[1]) + fmax(lam[0], lam[1])) * (1.0 + (double)sqrtf(tp) + (double)sqrtf(tm));
+    const float nt = sqrtf(tp) + sqrtf(tm);
+    e.err = sqrtf(ff);
+    e.eps = e.tol = k.tol_rel * nt + k.eps_abs;
+    e.floor = k.floor_scale * (1.f + nt);
     return true;
 }
 
-// Delta (as in the FP64 form) and its inverse, in FP32, scaled by 1/d.  False
-// when the rank-one parts outweigh the isotropic part d I by more than 1e4
-// (a phase close to collapse, J -> 0): an FP32 inverse would not give a
-// Newton direction there, and the caller continues in FP64.
-__device__ __forceinline__ bool hessian_inv(const LamEvalD& e, double cp, double cm, const double mu[2],
-                                            const double lam[2], double Di[9])
+// The laminate Hessian in FP32, scaled by 1/d (d = mu+/c+ + mu-/c-):
+//   Delta / d = I + s+ g+ g+^T + s- g- g-^T,  s = K - L ln J,
+//   K = (lam + mu) / (c d), L = lam / (c d)  (per phase; formed once per boxel)
+struct HessF {
+    float Kp, Lp, Km, Lm, id0;
+};
+
+__device__ __forceinline__ HessF hess_f(const double mu[2], const double lam[2], double wp, double wm)
 {
-    const float wp = (float)(1.0 / cp), wm = (float)(1.0 / cm);
-    const float d = (float)mu[1] * wp + (float)mu[0] * wm;
-    const float id0 = 1.f / d;
-    const float sp = (float)(lam[1] + mu[1] - lam[1] * e.p.lnJ) * wp * id0;
-    const float sm = (float)(lam[0] + mu[0] - lam[0] * e.m.lnJ) * wm * id0;
-    const float gp2 = e.p.g[0] * e.p.g[0] + e.p.g[1] * e.p.g[1] + e.p.g[2] * e.p.g[2];
-    const float gm2 = e.m.g[0] * e.m.g[0] + e.m.g[1] * e.m.g[1] + e.m.g[2] * e.m.g[2];
-    if (!(fabsf(sp) * gp2 <= 1e4f && fabsf(sm) * gm2 <= 1e4f)) return false;
-    float A[9];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int k = 0; k < 3; k++)
-            A[3 * i + k] = (i == k ? 1.f : 0.f) + sp * e.p.g[i] * e.p.g[k] + sm * e.m.g[i] * e.m.g[k];
-    const float c0 = A[4] * A[8] - A[5] * A[7];
-    const float c1 = A[5] * A[6] - A[3] * A[8];
-    const float c2 = A[3] * A[7] - A[4] * A[6];
-    const float det = A[0] * c0 + A[1] * c1 + A[2] * c2;
-    if (det == 0.f || !isfinite(det)) return false;
-    const float id = id0 / det;  // Delta^{-1} = (Delta / d)^{-1} / d
-    Di[0] = c0 * id;
-    Di[1] = (A[2] * A[7] - A[1] * A[8]) * id;
-    Di[2] = (A[1] * A[5] - A[2] * A[4]) * id;
-    Di[3] = c1 * id;
-    Di[4] = (A[0] * A[8] - A[2] * A[6]) * id;
-    Di[5] = (A[2] * A[3] - A[0] * A[5]) * id;
-    Di[6] = c2 * id;
-    Di[7] = (A[1] * A[6] - A[0] * A[7]) * id;
-    Di[8] = (A[0] * A[4] - A[1] * A[3]) * id;
-    return true;
+    const double id = 1.0 / (mu[1] * wp + mu[0] * wm);
+    HessF h;
+    h.Kp = (float)((lam[1] + mu[1]) * wp * id);
+    h.Lp = (float)(lam[1] * wp * id);
+    h.Km = (float)((lam[0] + mu[0]) * wm * id);
+    h.Lm = (float)(lam[0] * wm * id);
+    h.id0 = (float)id;
+    return h;
 }
 
-// The same FP32 inverse from an FP64 laminate state: the Delta^{-1} of the
-// FP32 boxel tangent (the tangent only feeds the FP32 Krylov iterations).
-// False where hessian_inv is false; the caller then inverts in FP64.
-__device__ __forceinline__ bool hessian_inv32(const LamEval& e, double cp, double cm, const double mu[2],
-                                              const double lam[2], double Di[9])
+// Delta^{-1} = (Delta / d)^{-1} / d in FP32.  False when the rank-one parts
+// outweigh the isotropic part by more than 1e4 (a phase close to collapse,
+// J -> 0): an FP32 inverse would not give a Newton direction there, and the
+// caller continues in FP64.
+__device__ __forceinline__ bool hess_inv_f(const HessF& h, float lnJp, float lnJm, const float gp[3],
+                                           const float gm[3], float Di[9])
 {
-    const float wp = (float)(1.0 / cp), wm = (float)(1.0 / cm);
-    const float d = (float)mu[1] * wp + (float)mu[0] * wm;
-    const float id0 = 1.f / d;
-    const float sp = ((float)lam[1] + (float)mu[1] - (float)lam[1] * (float)e.p.lnJ) * wp * id0;
-    const float sm = ((float)lam[0] + (float)mu[0] - (float)lam[0] * (float)e.m.lnJ) * wm * id0;
-    const float gp[3] = {(float)e.p.g[0], (float)e.p.g[1], (float)e.p.g[2]};
-    const float gm[3] = {(float)e.m.g[0], (float)e.m.g[1], (float)e.m.g[2]};
+    const float sp = h.Kp - h.Lp * lnJp;
+    const float sm = h.Km - h.Lm * lnJm;
     const float gp2 = gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2];
     const float gm2 = gm[0] * gm[0] + gm[1] * gm[1] + gm[2] * gm[2];
     if (!(fabsf(sp) * gp2 <= 1e4f && fabsf(sm) * gm2 <= 1e4f)) return false;
@@ -276,7 +274,7 @@ __device__ __forceinline__ bool hessian_inv32(const LamEval& e, double cp, doubl
     const float c2 = A[3] * A[7] - A[4] * A[6];
     const float det = A[0] * c0 + A[1] * c1 + A[2] * c2;
     if (det == 0.f || !isfinite(det)) return false;
-    const float id = id0 / det;
+    const float id = h.id0 / det;
     Di[0] = c0 * id;
     Di[1] = (A[2] * A[7] - A[1] * A[8]) * id;
     Di[2] = (A[1] * A[5] - A[2] * A[4]) * id;
@@ -287,6 +285,21 @@ __device__ __forceinline__ bool hessian_inv32(const LamEval& e, double cp, doubl
     Di[7] = (A[1] * A[6] - A[0] * A[7]) * id;
     Di[8] = (A[0] * A[4] - A[1] * A[3]) * id;
     return true;
+}
+
+// from a double-float laminate state (the Newton direction of its iterations)
+__device__ __forceinline__ bool hessian_inv(const LamEvalD& e, const HessF& h, float Di[9])
+{
+    return hess_inv_f(h, (float)e.p.lnJ, (float)e.m.lnJ, e.p.g, e.m.g, Di);
+}
+
+// from an FP64 laminate state: the Delta^{-1} of an FP32 boxel tangent, and
+// the direction of the certifying FP64 steps of the double-float form
+__device__ __forceinline__ bool hessian_inv32(const LamEval& e, const HessF& h, float Di[9])
+{
+    const float gp[3] = {(float)e.p.g[0], (float)e.p.g[1], (float)e.p.g[2]};
+    const float gm[3] = {(float)e.m.g[0], (float)e.m.g[1], (float)e.m.g[2]};
+    return hess_inv_f(h, (float)e.p.lnJ, (float)e.m.lnJ, gp, gm, Di);
 }
 
 // One Neo-Hookean phase's tangent data in precision S:
@@ -312,7 +325,7 @@ template <typename S> struct TanPhase {
         for (int q = 0; q < 3; q++) g[q] = (S)s.g[q];
         mu = (S)mu_;
         lam = (S)lam_;
-        m = (S)(mu_ - lam_ * s.lnJ);
+        m = (S)(mu_ - lam_ * (double)s.lnJ);
     }
 
     __device__ __forceinline__ S AD(const S N[3], int i, int Jx, int k) const
@@ -355,6 +368,41 @@ __device__ __forceinline__ int nr_loop(LE& e, double a[3], const double m[3], do
         a[0] = a1[0];
         a[1] = a1[1];
         a[2] = a1[2];
+        it++;
+        if (!evaluate(e)) return 2;
+    }
+    return 0;
+}
+
+// The same iterations in the double-float form, on the FP32 pipe: the jump
+// in df32, the direction Delta^{-1} f from the FP32 Hessian inverse, the
+// admissibility test and the back-projection of Algorithm 2 on the FP32
+// values of m_beta . a; until |f| <= max(eps, its rounding level).  Returns
+// as nr_loop.
+template <class EV>
+__device__ __forceinline__ int nr_loop_df(LamEvalD& e, df32 a[3], const float m[3], float bcp, float bcm, int& it,
+                                          int max_iter, double& nbp, const HessF& h, const EV& evaluate)
+{
+    if (!evaluate(e)) return 2;
+    while (e.err > fmaxf(e.eps, e.floor)) {
+        if (it >= max_iter) return 4;
+        float Di[9];
+        if (!hessian_inv(e, h, Di)) return 3;
+        df32 a1[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+            a1[i] = a[i] - df32(Di[3 * i] * e.f[0] + Di[3 * i + 1] * e.f[1] + Di[3 * i + 2] * e.f[2], 0.f);
+        const float b1 = (float)a1[0] * m[0] + (float)a1[1] * m[1] + (float)a1[2] * m[2];
+        if (!(b1 > bcp && b1 < bcm)) {
+            const float b0 = (float)a[0] * m[0] + (float)a[1] * m[1] + (float)a[2] * m[2];
+            const float bc = (b1 <= bcp) ? bcp : bcm;
+            const float db = 0.5f * (b0 + bc) - b1;
+#pragma unroll
+            for (int i = 0; i < 3; i++) a1[i] = a1[i] + df32(db * m[i], 0.f);
+            nbp += 1.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 3; i++) a[i] = a1[i];
         it++;
         if (!evaluate(e)) return 2;
     }
@@ -432,18 +480,23 @@ template <typename Tc, bool DFM> __device__ __forceinline__ void boxel_body(cons
         int status = 0, reason = 0;
         // m_beta = F^{-T} N / |F^{-T} N|, beta_c(+/-) = -/+ c(+/-) / |F^{-T} N|  (Sec. 4.2)
         double gbox[3];
+        // 1/c+-, once (the iterations multiply by them)
+        const double icp64 = 1.0 / cp, icm64 = 1.0 / cm;
+        const HessF hf = hess_f(mu, lam, icp64, icm64);
         df32 Fd[9], Nd[3], icp, icm;
+        DfLam dk;
         if constexpr (DFM) {
 #pragma unroll
             for (int c = 0; c < 9; c++) Fd[c] = df32(Fb[c]);
 #pragma unroll
             for (int i = 0; i < 3; i++) Nd[i] = df32(N[i]);
-            icp = df32(1.0 / cp);
-            icm = df32(1.0 / cm);
+            icp = df32(icp64);
+            icm = df32(icm64);
+            dk = df_lam(mu, lam, A.tol_rel, A.tol_abs);
             PhaseD box;
 #pragma unroll
             for (int c = 0; c < 9; c++) box.F[c] = Fd[c];
-            if (!nh_phase_df(box, mu[0], lam[0], Nd, gbox)) status = finite9(Fb) ? COMBO_E_INADMISSIBLE : COMBO_E_NAN;
+            if (!nh_phase_df(box, dk.mu[0], dk.lam[0], Nd, gbox)) status = finite9(Fb) ? COMBO_E_INADMISSIBLE : COMBO_E_NAN;
         } else {
             Phase box;
 #pragma unroll
@@ -453,11 +506,22 @@ template <typename Tc, bool DFM> __device__ __forceinline__ void boxel_body(cons
             for (int i = 0; i < 3; i++) gbox[i] = box.g[i];
         }
         LamEval e;
-        auto eval64 = [&](LamEval& x) { return lam_eval(x, Fb, N, cp, cm, a, mu, lam, A.tol_rel, A.tol_abs); };
+        auto eval64 = [&](LamEval& x) {
+            return lam_eval(x, Fb, N, icp64, icm64, a, mu, lam, A.tol_rel, A.tol_abs);
+        };
         auto inv64 = [&](const LamEval& x, double Di[9]) {
             double Dl[9];
-            hessian(x, cp, cm, mu, lam, Dl);
+            hessian(x, icp64, icm64, mu, lam, Dl);
             return inv3(Dl, Di);
+        };
+        // the FP64 steps that follow double-float iterations take the FP32
+        // inverse (their residual is already at the df32 rounding level)
+        auto inv_cert = [&](const LamEval& x, double Di[9]) {
+            float Df[9];
+            if (!hessian_inv32(x, hf, Df)) return inv64(x, Di);
+#pragma unroll
+            for (int q = 0; q < 9; q++) Di[q] = Df[q];
+            return true;
         };
         double Di[9];
         LamEvalD ed;           // (double-float form) the last double-float evaluation
@@ -473,27 +537,28 @@ template <typename Tc, bool DFM> __device__ __forceinline__ void boxel_body(cons
                 // double-float iterations from a copy of the start; if they
                 // stop early (a phase near collapse, an ill-conditioned
                 // Hessian), the FP64 iterations start over from a
-                double ad[3] = {a[0], a[1], a[2]};
-                const int rdf = nr_loop(
-                    ed, ad, m, bcp, bcm, 0.0, it_df, A.max_iter, nbp,
-                    [&](LamEvalD& x) {
-                        if (!lam_eval(x, Fd, Nd, icp, icm, ad, mu, lam, A.tol_rel, A.tol_abs)) return false;
-                        x.eps = fmax(x.eps, x.floor);
-                        return true;
-                    },
-                    [&](const LamEvalD& x, double Dv[9]) { return hessian_inv(x, cp, cm, mu, lam, Dv); });
+                df32 ad[3] = {df32(a[0]), df32(a[1]), df32(a[2])};
+                const float mf[3] = {(float)m[0], (float)m[1], (float)m[2]};
+                const int rdf = nr_loop_df(ed, ad, mf, (float)bcp, (float)bcm, it_df, A.max_iter, nbp, hf,
+                                           [&](LamEvalD& x) { return lam_eval(x, Fd, Nd, icp, icm, ad, dk); });
                 if (rdf == 0) {
-                    a[0] = ad[0];
-                    a[1] = ad[1];
-                    a[2] = ad[2];
+#pragma unroll
+                    for (int i = 0; i < 3; i++) a[i] = (double)ad[i];
                     // the double-float residual lies below the tolerance by
                     // more than its own rounding level: the FP64 residual
                     // passes the same test, and the FP64 evaluation is skipped
-                    df_done = ed.err + ed.floor <= 0.99 * ed.tol && hessian_inv(ed, cp, cm, mu, lam, Di);
+                    float Df[9];
+                    df_done = ed.err + ed.floor <= 0.99f * ed.tol && hessian_inv(ed, hf, Df);
+                    if (df_done)
+#pragma unroll
+                        for (int q = 0; q < 9; q++) Di[q] = Df[q];
                 }
             }
             if (!df_done) {
-                reason = nr_loop(e, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp, eval64, inv64);
+                if constexpr (DFM)
+                    reason = nr_loop(e, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp, eval64, inv_cert);
+                else
+                    reason = nr_loop(e, a, m, bcp, bcm, 0.0, it, A.max_iter, nbp, eval64, inv64);
                 if (reason) status = COMBO_E_LAMINATE;
             }
             its = it + it_df;
@@ -536,7 +601,13 @@ template <typename Tc, bool DFM> __device__ __forceinline__ void boxel_body(cons
                 // (an FP32 tangent takes Delta^{-1} in FP32, off the FP64 pipe)
                 bool inv_ok = false;
                 if (!df_done) {
-                    if constexpr (sizeof(Tc) == 4) inv_ok = hessian_inv32(e, cp, cm, mu, lam, Di);
+                    if constexpr (sizeof(Tc) == 4) {
+                        float Df[9];
+                        inv_ok = hessian_inv32(e, hf, Df);
+                        if (inv_ok)
+#pragma unroll
+                            for (int q = 0; q < 9; q++) Di[q] = Df[q];
+                    }
                     if (!inv_ok) inv_ok = inv64(e, Di);
                 }
                 if (df_done) {
@@ -788,18 +859,23 @@ template <bool DFM> __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArg
         const double lam[2] = {mp ? mp[2] : A.lam[0], mp ? mp[3] : A.lam[1]};
         int status = 0, reason = 0;
         double gbox[3];
+        // 1/c+-, once (the iterations multiply by them)
+        const double icp64 = 1.0 / cp, icm64 = 1.0 / cm;
+        const HessF hf = hess_f(mu, lam, icp64, icm64);
         df32 Fd[9], Nd[3], icp, icm;
+        DfLam dk;
         if constexpr (DFM) {
 #pragma unroll
             for (int c = 0; c < 9; c++) Fd[c] = df32(Fb[c]);
 #pragma unroll
             for (int q = 0; q < 3; q++) Nd[q] = df32(N[q]);
-            icp = df32(1.0 / cp);
-            icm = df32(1.0 / cm);
+            icp = df32(icp64);
+            icm = df32(icm64);
+            dk = df_lam(mu, lam, A.tol_rel, A.tol_abs);
             PhaseD box;
 #pragma unroll
             for (int c = 0; c < 9; c++) box.F[c] = Fd[c];
-            if (!nh_phase_df(box, mu[0], lam[0], Nd, gbox)) status = finite9(Fb) ? COMBO_E_INADMISSIBLE : COMBO_E_NAN;
+            if (!nh_phase_df(box, dk.mu[0], dk.lam[0], Nd, gbox)) status = finite9(Fb) ? COMBO_E_INADMISSIBLE : COMBO_E_NAN;
         } else {
             Phase box;
 #pragma unroll
@@ -809,10 +885,12 @@ template <bool DFM> __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArg
             for (int q = 0; q < 3; q++) gbox[q] = box.g[q];
         }
         LamEval e;
-        auto eval64 = [&](LamEval& x) { return lam_eval(x, Fb, N, cp, cm, a, mu, lam, A.tol_rel, A.tol_abs); };
+        auto eval64 = [&](LamEval& x) {
+            return lam_eval(x, Fb, N, icp64, icm64, a, mu, lam, A.tol_rel, A.tol_abs);
+        };
         auto inv64 = [&](const LamEval& x, double Di[9]) {
             double Dl[9];
-            hessian(x, cp, cm, mu, lam, Dl);
+            hessian(x, icp64, icm64, mu, lam, Dl);
             return inv3(Dl, Di);
         };
         LamEvalD ed;
@@ -829,19 +907,13 @@ template <bool DFM> __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArg
                 // double-float residual down to its rounding level; FP64
                 // iterations only where they stop early (a phase near
                 // collapse, an ill-conditioned Hessian)
-                double ad[3] = {a[0], a[1], a[2]};
-                const int rdf = nr_loop(
-                    ed, ad, m, bcp, bcm, 0.0, it_df, A.max_iter, nbp,
-                    [&](LamEvalD& x) {
-                        if (!lam_eval(x, Fd, Nd, icp, icm, ad, mu, lam, A.tol_rel, A.tol_abs)) return false;
-                        x.eps = fmax(x.eps, x.floor);
-                        return true;
-                    },
-                    [&](const LamEvalD& x, double Dv[9]) { return hessian_inv(x, cp, cm, mu, lam, Dv); });
+                df32 ad[3] = {df32(a[0]), df32(a[1]), df32(a[2])};
+                const float mf[3] = {(float)m[0], (float)m[1], (float)m[2]};
+                const int rdf = nr_loop_df(ed, ad, mf, (float)bcp, (float)bcm, it_df, A.max_iter, nbp, hf,
+                                           [&](LamEvalD& x) { return lam_eval(x, Fd, Nd, icp, icm, ad, dk); });
                 if (rdf == 0) {
-                    a[0] = ad[0];
-                    a[1] = ad[1];
-                    a[2] = ad[2];
+#pragma unroll
+                    for (int q = 0; q < 3; q++) a[q] = (double)ad[q];
                     df_done = true;
                 }
             }
@@ -885,9 +957,12 @@ template <bool DFM> __global__ void __launch_bounds__(128) k_boxel_dfmg(BoxelArg
                 // the sub-cell's tangent for the doubly-fine Newton-CG, in
                 // the Krylov precision, from the converged state
                 double Di[9];
+                float Df[9];
                 bool ok;
-                if (df_done && hessian_inv(ed, cp, cm, mu, lam, Di)) {
+                if (df_done && hessian_inv(ed, hf, Df)) {
                     ok = true;
+#pragma unroll
+                    for (int q = 0; q < 9; q++) Di[q] = Df[q];
                     if (A.sub_f32)
                         boxel_tangent_store<float>(ed.p, ed.m, N, cp, cm, mu, lam, Di, (float*)A.bAsub, 8 * A.nb, t);
                     else
