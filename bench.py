@@ -391,6 +391,13 @@ def main():
     if not args.no_normals and rank == 0:
         normals = normals_bench(combo, ctx, stream, peak, peak_kind, cpu=not args.no_cpu_baseline and world == 1)
 
+    arith = None
+    if rank == 0:
+        # FP64 / FP32 FMA rates of this GPU: the ceilings of the kernels bound by arithmetic
+        r64, r32 = combo.arith_rates(ctx)
+        arith = {"fp64_tflops": r64, "fp32_tflops": r32, "fp32_over_fp64": (r32 / r64) if r64 > 0 else None,
+                 "method": "combo_arith_rates: 8 dependent FMA chains per thread, 2048 threads per SM, "
+                           "CUDA events, best of 3"}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / max(ops, 1),
@@ -420,7 +427,7 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "batch": batch,
                 "fibres_512": fibres,
                 "normal_detection": normals, "variants": variants, "gpu_launches": launches,
-                "clocks": clocks, "kernels": table}
+                "clocks": clocks, "kernels": table, "arith_rates": arith}
         if args.profile_json:
             json.dump(line, open(args.profile_json, "w"), indent=1)
         print(json.dumps(line))

@@ -521,6 +521,18 @@ int combo_laminate_eval(combo_ctx* ctx, const double F[9], const double N[3], do
 int combo_df_log(combo_ctx* ctx, const double* x, double* y, int64_t n);
 
 /*
+ * combo_arith_rates: the device's FMA throughput (no counterpart in the
+ * paper; the denominators of the rooflines of the kernels bound by
+ * arithmetic rather than memory, such as the laminate solve).  Launches
+ * 2048 threads per SM, each running 8 independent chains of dependent FMAs
+ * (no memory traffic), on the context's stream, timed with CUDA events
+ * (best of three after a warm-up, a few ms each).  tflops: host array of 2
+ * doubles, written with the FP64 and FP32 rates in TFLOP/s (an FMA counts
+ * as 2 FLOPs).  Synchronises the context's stream.
+ */
+int combo_arith_rates(combo_ctx* ctx, double* tflops);
+
+/*
  * combo_coarse_grain: composite boxels from a binary fine image (Sec. 5).
  *
  * The fine image of n1 x n2 x n3 voxels (edges h) is cut into coarse voxels

@@ -64,7 +64,7 @@ EXPORTS = ["combo_ctx_create", "combo_ctx_destroy", "combo_last_error", "combo_o
            "combo_constitutive", "combo_apply_G_noalloc", "combo_server_create", "combo_server_destroy",
            "combo_submit", "combo_poll", "combo_wait", "combo_cancel", "combo_server_stats",
            "combo_autotune_enable", "combo_autotune_force", "combo_autotune_report", "combo_coarse_grain",
-           "combo_coarse_grain_profile", "combo_coarse_grain_profile_read", "combo_df_log",
+           "combo_coarse_grain_profile", "combo_coarse_grain_profile_read", "combo_df_log", "combo_arith_rates",
            "combo_solve_advance_steps", "combo_state_export", "combo_state_import", "combo_neohooke_eval",
            "combo_laminate_eval", "combo_fault_inject_alloc", "combo_krylov_form"]
 
@@ -126,6 +126,8 @@ def load(path: str = LIB_PATH):
     L.combo_coarse_grain_profile_read.restype = C.c_int
     L.combo_df_log.argtypes = [vp, vp, vp, C.c_int64]
     L.combo_df_log.restype = C.c_int
+    L.combo_arith_rates.argtypes = [vp, vp]
+    L.combo_arith_rates.restype = C.c_int
     L.combo_solve_advance_steps.argtypes = [vp, i32]
     L.combo_solve_advance_steps.restype = C.c_int
     L.combo_state_export.argtypes = [vp, vp, C.POINTER(C.c_int64)]
@@ -527,6 +529,15 @@ def fault_inject_alloc(after: int):
     """Test hook: the device allocation after `after` more successful ones
     fails as out of memory (then the hook disarms); after < 0 disarms it."""
     _check(load().combo_fault_inject_alloc(int(after)))
+
+
+def arith_rates(ctx: Context | None = None):
+    """combo_arith_rates: the device's FP64 and FP32 FMA throughput in
+    TFLOP/s (dependent FMA chains timed with CUDA events)."""
+    ctx = ctx or default_context()
+    r = np.zeros(2)
+    _check(load().combo_arith_rates(ctx.h, _ptr(r)))
+    return float(r[0]), float(r[1])
 
 
 def df_log(x, ctx: Context | None = None):

@@ -12,7 +12,7 @@
 // norm-wise FFT error analysis uses).  Every step goes through the _rn
 // intrinsics so the compiler cannot contract or reorder it.
 //
-// FP32 runs ~68x faster than FP64 on this GPU; a df32 add or multiply costs
+// FP32 runs ~63x faster than FP64 on this GPU (combo_arith_rates); a df32 add or multiply costs
 // 7-11 FP32 instructions, so transforms in df32 run several times faster than
 // in FP64 while their rounding error stays far below the 1e-8 equilibrium
 // tolerance the residual is compared against.

@@ -3746,6 +3746,75 @@ extern "C" int combo_df_log(combo_ctx* ctx, const double* x, double* y, int64_t 
     return rc ? fail(rc, "combo_df_log: CUDA error") : COMBO_OK;
 }
 
+// Arithmetic-rate probe: every thread runs 8 independent chains of dependent
+// FMAs x <- x b + c (b < 1, so the chains stay bounded); the result is stored
+// only under a condition that never holds, which keeps the chains live
+// without memory traffic.  FLOPs = 2 * 8 * 16 * iters per thread.
+template <typename T> __global__ void __launch_bounds__(256) k_fma_rate(T* out, int iters, T b, T c)
+{
+    T x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = (T)(threadIdx.x & 7) + (T)k;
+#pragma unroll 1
+    for (int i = 0; i < iters; i++)
+#pragma unroll
+        for (int u = 0; u < 16; u++)
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if constexpr (sizeof(T) == 8)
+                    x[k] = __fma_rn(x[k], b, c);
+                else
+                    x[k] = __fmaf_rn(x[k], b, c);
+            }
+    T s = (T)0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += x[k];
+    if (s == (T)-1) out[blockIdx.x] = s;  // the chains stay near c / (1 - b) > 0
+}
+
+extern "C" int combo_arith_rates(combo_ctx* ctx, double* tflops)
+{
+    if (!ctx || !tflops) return fail(COMBO_E_INVALID_ARG, "null argument");
+    CK(cudaSetDevice(ctx->device));
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int grid = 8 * nsm;  // 2048 threads per SM
+    double* buf = nullptr;
+    CK(dev_malloc(&buf, sizeof(double) * grid));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = COMBO_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = COMBO_E_CUDA;
+    // best of three launches after one warm-up, each a few ms long
+    auto rate = [&](auto launch, double flops) -> double {
+        float best = 0.f;
+        for (int r = 0; r < 4 && !rc; r++) {
+            if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) rc = COMBO_E_CUDA;
+            launch();
+            if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, ctx->stream) != cudaSuccess ||
+                cudaEventSynchronize(e1) != cudaSuccess)
+                rc = COMBO_E_CUDA;
+            float ms = 0.f;
+            if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = COMBO_E_CUDA;
+            if (r > 0 && ms > 0.f && (best == 0.f || ms < best)) best = ms;
+        }
+        return (rc || best <= 0.f) ? 0.0 : flops / (best * 1e-3) / 1e12;
+    };
+    const double per_iter = 2.0 * 8 * 16 * 256.0 * grid;
+    const int it64 = 32, it32 = 2048;
+    const double r64 = rate([&] { k_fma_rate<double><<<grid, 256, 0, ctx->stream>>>(buf, it64, 0.999, 1e-3); },
+                            per_iter * it64);
+    const double r32 = rate(
+        [&] { k_fma_rate<float><<<grid, 256, 0, ctx->stream>>>((float*)buf, it32, 0.999f, 1e-3f); },
+        per_iter * it32);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (rc) return fail(rc, "combo_arith_rates: CUDA error");
+    tflops[0] = r64;
+    tflops[1] = r32;
+    return COMBO_OK;
+}
+
 extern "C" int combo_constitutive(combo_ctx* ctx, const combo_problem* p, const combo_options* o_in, const double* F,
                                   double* a_io, double* P, int32_t mem)
 {
