@@ -279,13 +279,6 @@ template <typename T> static void free_tables(DevTables<T>& t)
     }
 }
 
-static int tx_for(int n, size_t cxbytes, size_t budget, int comps)
-{
-    int tx = 16;
-    while (tx > 1 && 2 * (size_t)comps * n * tx * cxbytes > budget) tx /= 2;
-    return tx;
-}
-
 // grid of nprob stacked problems of n1 x n2 x n3 each (z axis: problem-major)
 static GridDims make_dims(const int32_t n[3], int nprob = 1)
 {
