@@ -623,8 +623,8 @@ int combo_fault_inject_alloc(int64_t after);
  *   stream  cudaStream_t (NULL = the default stream).
  *   sumsq   optional host pointer: receives sum_x |Y(x)|^2; when given, the
  *           call synchronises the stream before it returns.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  Every call on a device shares the
+ * The first call on a device looks up the array's device address (a
+ * synchronous runtime query).  Every call on a device shares the
  * array and finds the previous call's contents there (it clears what must
  * start at zero): calls that overlap on the GPU -- on different streams, or
  * from several threads -- race and must be serialised by the caller.
