@@ -32,7 +32,11 @@ def test_replicas_aggregate(world):
 
         assert bench.replicas_aggregate(12.5, 300, None, "cpu") == (12.5, 300)
         return
-    port = 29500 + (os.getpid() % 1000)
+    import socket
+
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as sk:  # a port that is free now
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
     with mp.Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
