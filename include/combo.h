@@ -62,9 +62,15 @@ extern "C" {
 /* precision */
 #define COMBO_FP64 0          /* every field and operator in FP64 */
 #define COMBO_FP32_REFINED 1  /* FP32 Krylov iterations, FP64 residual, F, laminates, norms */
-/* as COMBO_FP32_REFINED, but the transforms of the residual G[P(F)] run in
-   double-float arithmetic (pairs of FP32, 48-bit significand); P(F), the
-   laminates, F and the norms stay FP64.  No counterpart in the paper: an
+/* as COMBO_FP32_REFINED, but the residual G[P(F)] is evaluated in
+   double-float arithmetic (pairs of FP32, 48-bit significand): the
+   Neo-Hookean stress of the pure voxels (ln J included), the forward
+   transforms and the projection; the inverse transforms, which only form the
+   FP32 right-hand side of the Krylov solve, run in FP32.  The laminate
+   Newton iterations run in double-float too, and an FP64 evaluation of the
+   traction residual decides their convergence wherever the double-float
+   rounding level does not lie clearly below the tolerance.  F stays FP64;
+   the residual norms accumulate in FP64.  No counterpart in the paper: an
    arithmetic choice for GPUs whose FP64 rate is a small fraction of FP32. */
 #define COMBO_FP32_REFINED_DF 2
 /* kspace: discrete derivative of the Green operator */
